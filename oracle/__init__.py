@@ -1,0 +1,229 @@
+"""CPU FP64 oracle for the CUDAHM sampler (arXiv:2105.08026).
+
+TEST INFRASTRUCTURE ONLY: the plain single-threaded reference that the CUDA
+path is checked against. Only the test suite, ``__graft_entry__.smoke()`` and
+the CPU-baseline / reference legs of ``bench.py`` may import this package. It
+shares no code with the CUDA library (``paper_2105_08026_gb300``) and never
+imports it; the CUDA library never imports this package.
+
+The arithmetic lives in ``cudahm_oracle.c`` (built with ``-O2
+-ffp-contract=off``, no fast-math); this module is ctypes marshalling plus the
+pure-numpy Monte Carlo statistics in :mod:`oracle.stats`.
+
+Parity status of each function is listed in the module docstring of
+``cudahm_oracle.c`` and pinned by ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cudahm_oracle.c")
+_LIB = os.path.join(_HERE, "libcudahm_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NN1, MVN3, LF = 0, 1, 2
+MODEL_D = {NN1: 1, MVN3: 3, LF: 1}
+MODEL_P = {NN1: 2, MVN3: 9, LF: 3}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (plain C99, strict FP64)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+            L.orc_uniform.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+            L.orc_uniform.restype = ctypes.c_double
+            L.orc_draw.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                   ctypes.c_int, _dp, _dp]
+            L.orc_neumaier_sum.argtypes = [_dp, ctypes.c_int64]
+            L.orc_neumaier_sum.restype = ctypes.c_double
+            L.orc_cholesky.argtypes = [ctypes.c_int, _dp, _dp]
+            L.orc_ram_update.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double]
+            L.orc_gauss_legendre.argtypes = [ctypes.c_int, _dp, _dp]
+            L.orc_lf_etabar.argtypes = [_dp, _dp]
+            L.orc_lf_etabar.restype = ctypes.c_double
+            L.orc_lf_H.argtypes = [ctypes.c_double, _dp]
+            L.orc_lf_H.restype = ctypes.c_double
+            L.orc_member_logdens.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp,
+                                             _dp]
+            L.orc_run.argtypes = ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp,
+                                   ctypes.c_uint64, _dp, _dp, _dp, _dp, _i64p, _dp,
+                                   ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _dp, _i64p, _i64p, _i64p,
+                                   ctypes.c_int64, _dp, _dp, _u8p, _dp, _dp, _dp, _dp, _u8p, _dp])
+            L.orc_run.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _p(a, t=_dp):
+    if a is None:
+        return None
+    return a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------- RNG ------
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 block for one 4-word counter and 2-word key (Salmon et al. SC'11)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_p(c, _u32p), _p(k, _u32p), _p(out, _u32p))
+    return out
+
+
+def uniform(wa: int, wb: int) -> float:
+    return lib().orc_uniform(wa, wb)
+
+
+def draw(seed: int, stream: int, index: int, sweep: int, d: int):
+    """d standard normals and the accept uniform of one RAM step."""
+    z = np.zeros(max(d, 1), dtype=np.float64)
+    u = ctypes.c_double(0.0)
+    lib().orc_draw(seed, stream, index, sweep, d, _p(z), ctypes.byref(u))
+    return z[:d], u.value
+
+
+# ---------------------------------------------------------------- numerics -
+def neumaier_sum(v) -> float:
+    v = _f64(v)
+    return lib().orc_neumaier_sum(_p(v), v.size)
+
+
+def cholesky(A):
+    A = _f64(A)
+    d = A.shape[0]
+    L = np.zeros_like(A)
+    rc = lib().orc_cholesky(d, _p(A), _p(L))
+    if rc != 0:
+        raise np.linalg.LinAlgError("not positive definite")
+    return L
+
+
+def ram_update(S, U, alpha, alpha_star, eta):
+    """RAM factor update (Sec. 2.2 step 3); returns the new lower factor."""
+    S = _f64(S).copy()
+    U = _f64(U)
+    d = U.size
+    rc = lib().orc_ram_update(d, _p(S), _p(U), alpha, alpha_star, eta)
+    if rc != 0:
+        raise np.linalg.LinAlgError("RAM update lost positive definiteness")
+    return S
+
+
+def gauss_legendre(n: int):
+    x = np.zeros(n)
+    w = np.zeros(n)
+    lib().orc_gauss_legendre(n, _p(x), _p(w))
+    return x, w
+
+
+def lf_consts(sigma_F, F_th, r_max, nL=1024, nr=1024, ln_upper=float(np.log(60.0))):
+    """Constants vector of the luminosity model: sigma_F, F_th, r_max, n_L, n_r, ln(upper/L*)."""
+    return np.array([sigma_F, F_th, r_max, nL, nr, ln_upper], dtype=np.float64)
+
+
+def lf_etabar(theta, consts) -> float:
+    th = _f64(theta)
+    c = _f64(consts)
+    return lib().orc_lf_etabar(_p(th), _p(c))
+
+
+def lf_H(L, consts) -> float:
+    c = _f64(consts)
+    return lib().orc_lf_H(float(L), _p(c))
+
+
+def member_logdens(model, y, aux, consts, chi, theta):
+    d = MODEL_D[model]
+    y, aux, chi, theta = _f64(y), _f64(aux), _f64(chi), _f64(theta)
+    consts = _f64(consts if consts is not None else np.zeros(1))
+    n = chi.size // d
+    out = np.zeros(n)
+    lib().orc_member_logdens(model, d, n, _p(y), _p(aux), _p(consts), _p(chi), _p(theta), _p(out))
+    return out
+
+
+# ---------------------------------------------------------------- chain ----
+class Chain:
+    """State of one MWG chain run by the oracle (Sec. 2.1-2.2)."""
+
+    def __init__(self, model, y, aux, consts, theta_init, theta_prop_scale, seed, chi0,
+                 chi_init_scale=1.0, target_accept=0.4, adapt_exponent=2.0 / 3.0,
+                 theta_target_accept=0.4, adapt_theta=True):
+        self.model = model
+        self.d = MODEL_D[model]
+        self.p = MODEL_P[model]
+        self.y = _f64(y)
+        self.aux = _f64(aux)
+        self.n = self.y.size // self.d
+        self.consts = _f64(consts if consts is not None else np.zeros(1))
+        self.seed = int(seed)
+        self.params = np.array([target_accept, adapt_exponent, theta_target_accept, 1.0 if adapt_theta else 0.0])
+        self.chi = _f64(chi0).copy().reshape(-1)
+        assert self.chi.size == self.n * self.d
+        self.S = np.zeros((self.n, self.d, self.d))
+        for a in range(self.d):
+            self.S[:, a, a] = chi_init_scale
+        self.S = self.S.reshape(-1).copy()
+        self.theta = _f64(theta_init).copy()
+        self.S_theta = np.diag(_f64(theta_prop_scale)).reshape(-1).copy()
+        self.sweep = ctypes.c_int64(0)
+        self.etabar = ctypes.c_double(0.0)
+        self.member_accepts = ctypes.c_int64(0)
+        self.theta_accepts = ctypes.c_int64(0)
+
+    def run(self, n_burn, n_iter, thin=1, trace_sweeps=0):
+        n, p = self.n, self.p
+        total = n_burn + n_iter
+        cap = (n_iter // thin) if thin > 0 else 0
+        rows = np.zeros((max(cap, 1), p))
+        rows_out = ctypes.c_int64(0)
+        T = int(min(trace_sweeps, total))
+        tr = None
+        args_tr = [None] * 9
+        if T > 0:
+            tr = dict(delta=np.zeros((T, n)), u=np.zeros((T, n)), acc=np.zeros((T, n), np.uint8),
+                      theta_prop=np.zeros((T, p)), D=np.zeros(T), logalpha=np.zeros(T), utheta=np.zeros(T),
+                      tacc=np.zeros(T, np.uint8), etabar=np.zeros(T))
+            args_tr = [_p(tr["delta"]), _p(tr["u"]), _p(tr["acc"], _u8p), _p(tr["theta_prop"]), _p(tr["D"]),
+                       _p(tr["logalpha"]), _p(tr["utheta"]), _p(tr["tacc"], _u8p), _p(tr["etabar"])]
+        rc = lib().orc_run(self.model, self.d, p, n, _p(self.y), _p(self.aux), _p(self.consts), _p(self.params),
+                           self.seed, _p(self.chi), _p(self.S), _p(self.theta), _p(self.S_theta),
+                           ctypes.byref(self.sweep), ctypes.byref(self.etabar), n_burn, n_iter, thin, _p(rows),
+                           ctypes.byref(rows_out), ctypes.byref(self.member_accepts),
+                           ctypes.byref(self.theta_accepts), T, *args_tr)
+        if rc != 0:
+            raise RuntimeError(f"oracle run failed: {rc}")
+        return rows[: rows_out.value].copy(), tr
+
+    def member_logdens(self, theta=None):
+        return member_logdens(self.model, self.y, self.aux, self.consts, self.chi,
+                              self.theta if theta is None else theta)

@@ -1,0 +1,194 @@
+"""Seeded synthetic populations shaped like the paper's demonstrations.
+
+This module only generates inputs (simulated catalogs and run settings). It
+holds none of the sampler's arithmetic: no member log-densities, no selection
+integral, no RAM or MH step. Both the CUDA path and the CPU oracle consume what
+it produces; it imports neither.
+
+Workloads (all numpy ``Generator(PCG64(seed))``):
+
+- ``nn1_data``: normal-normal population, d = 1 (Sec. 3 reduced to one
+  characteristic): chi_i ~ N(mu, tau^2), sigma_i ~ U[lo, hi], y_i ~ N(chi_i, sigma_i^2).
+- ``lf_data``: thinned luminosity-function catalog (Sec. 4-5): L from a
+  Schechter-form density (L/L*)^beta exp(-L/L*) truncated to L > L_low, distance
+  r with density ~ r^2 on [0, r_max], flux F = L/(4 pi r^2) (Sec. 4.1), measured
+  flux Fhat = F + N(0, sigma_F^2) with sigma_F = sigma_frac * F_th, kept iff
+  Fhat > F_th (Sec. 5.2); F_th is chosen by Monte Carlo so that a fraction
+  ``detect_frac`` of the population is detected.
+- ``mvn3_data``: d = 3 normal population with condition-number-20 covariance and
+  heteroscedastic diagonal measurement errors (Sec. 3 with unknown C_pop).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+# ----------------------------------------------------------------- NN1 -----
+@dataclass
+class NN1Data:
+    y: np.ndarray
+    sigma: np.ndarray
+    chi_true: np.ndarray
+    mu: float
+    tau: float
+
+
+def nn1_data(n: int, mu: float = 2.0, tau: float = 0.8, sig_lo: float = 0.5, sig_hi: float = 1.5,
+             seed: int = 1001) -> NN1Data:
+    g = _rng(seed)
+    chi = mu + tau * g.standard_normal(n)
+    sigma = g.uniform(sig_lo, sig_hi, n)
+    y = chi + sigma * g.standard_normal(n)
+    return NN1Data(y=y, sigma=sigma, chi_true=chi, mu=mu, tau=tau)
+
+
+# ----------------------------------------------------------------- LF ------
+@dataclass
+class LFData:
+    fhat: np.ndarray
+    r: np.ndarray
+    L_true: np.ndarray
+    F_th: float
+    sigma_F: float
+    r_max: float
+    beta: float
+    L_star: float
+    L_low: float
+    n_drawn: int
+
+
+def _schechter_draw(g: np.random.Generator, m: int, beta: float, L_star: float, L_low: float) -> np.ndarray:
+    """m draws of L with density ~ (L/L*)^beta exp(-L/L*) on L > L_low (rejection sampling)."""
+    out = np.empty(0)
+    while out.size < m:
+        k = max(2 * (m - out.size), 1024)
+        if beta < -1.0:
+            # Pareto proposal ~ L^beta on [L_low, inf), accepted with exp(-(L - L_low)/L*)
+            v = 1.0 - g.random(k)  # (0, 1]
+            L = L_low * v ** (1.0 / (beta + 1.0))
+            keep = g.random(k) < np.exp(-(L - L_low) / L_star)
+        else:
+            # gamma(beta+1, L*) proposal restricted to L > L_low
+            L = g.gamma(beta + 1.0, L_star, k)
+            keep = L > L_low
+        out = np.concatenate([out, L[keep]])
+    return out[:m]
+
+
+def _population(g, m, beta, L_star, L_low, r_max):
+    L = _schechter_draw(g, m, beta, L_star, L_low)
+    r = r_max * g.random(m) ** (1.0 / 3.0)
+    r = np.maximum(r, 1e-300)
+    return L, r
+
+
+def solve_threshold(beta: float, L_star: float, L_low: float, r_max: float, detect_frac: float,
+                    sigma_frac: float, seed: int, m: int = 400_000) -> float:
+    """F_th with P(Fhat > F_th) = detect_frac over the population, by bisection on a fixed
+    Monte Carlo sample (sigma_F = sigma_frac * F_th inside the criterion)."""
+    g = _rng(seed + 7_000_003)
+    L, r = _population(g, m, beta, L_star, L_low, r_max)
+    F = L / (4.0 * math.pi * r * r)
+    z = g.standard_normal(m)
+    lo, hi = np.log(np.quantile(F, 1e-3)), np.log(np.quantile(F, 1.0 - 1e-4))
+
+    def frac(lf):
+        fth = math.exp(lf)
+        return float(np.mean(F + sigma_frac * fth * z > fth))
+
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        if frac(mid) > detect_frac:
+            lo = mid
+        else:
+            hi = mid
+    return math.exp(0.5 * (lo + hi))
+
+
+def lf_data(n: int, beta: float = -1.2, L_star: float = 1e10, L_low: float = 1e8, r_max: float = 4000.0,
+            detect_frac: float = 0.30, sigma_frac: float = 0.2, seed: int = 1002) -> LFData:
+    F_th = solve_threshold(beta, L_star, L_low, r_max, detect_frac, sigma_frac, seed)
+    sigma_F = sigma_frac * F_th
+    g = _rng(seed)
+    fh, rr, LL = [], [], []
+    got, drawn = 0, 0
+    while got < n:
+        m = int((n - got) / max(detect_frac, 1e-3) * 1.2) + 1024
+        L, r = _population(g, m, beta, L_star, L_low, r_max)
+        F = L / (4.0 * math.pi * r * r)
+        fhat = F + sigma_F * g.standard_normal(m)
+        keep = fhat > F_th
+        idx = np.nonzero(keep)[0]
+        need = n - got
+        if idx.size > need:
+            drawn += int(idx[need - 1]) + 1
+            idx = idx[:need]
+        else:
+            drawn += m
+        fh.append(fhat[idx]); rr.append(r[idx]); LL.append(L[idx])
+        got += idx.size
+    return LFData(fhat=np.concatenate(fh), r=np.concatenate(rr), L_true=np.concatenate(LL), F_th=F_th,
+                  sigma_F=sigma_F, r_max=r_max, beta=beta, L_star=L_star, L_low=L_low, n_drawn=drawn)
+
+
+# ----------------------------------------------------------------- MVN3 ----
+@dataclass
+class MVN3Data:
+    y: np.ndarray       # (n, 3)
+    s: np.ndarray       # (n, 3)
+    chi_true: np.ndarray
+    mu: np.ndarray
+    C_pop: np.ndarray
+
+
+def mvn3_data(n: int, mu=(0.0, 1.0, -1.0), cond: float = 20.0, s_lo: float = 0.3, s_hi: float = 1.0,
+              seed: int = 1003) -> MVN3Data:
+    g = _rng(seed)
+    Q, _ = np.linalg.qr(g.standard_normal((3, 3)))
+    ev = np.array([1.0, math.sqrt(cond), cond])
+    C = (Q * ev) @ Q.T
+    C = 0.5 * (C + C.T)
+    Lc = np.linalg.cholesky(C)
+    mu = np.asarray(mu, dtype=np.float64)
+    chi = mu + g.standard_normal((n, 3)) @ Lc.T
+    s = g.uniform(s_lo, s_hi, (n, 3))
+    y = chi + s * g.standard_normal((n, 3))
+    return MVN3Data(y=y, s=s, chi_true=chi, mu=mu, C_pop=C)
+
+
+def mvn3_theta_from(mu, C) -> np.ndarray:
+    """theta layout of the d = 3 model: mu[3], then the Cholesky factor of C packed
+    row-major (L11, L21, L22, L31, L32, L33) with the diagonal stored as logs."""
+    L = np.linalg.cholesky(np.asarray(C, dtype=np.float64))
+    return np.array([mu[0], mu[1], mu[2], math.log(L[0, 0]), L[1, 0], math.log(L[1, 1]), L[2, 0], L[2, 1],
+                     math.log(L[2, 2])])
+
+
+# ----------------------------------------------------------- run settings --
+def nn1_settings(data: NN1Data):
+    """theta_init, theta_prop_scale, consts for the NN1 model (flat mu, flat ln tau on [-10, 10])."""
+    theta0 = np.array([float(np.mean(data.y)), math.log(max(float(np.std(data.y)), 1e-3))])
+    scale = np.array([0.05, 0.05])
+    consts = np.array([-10.0, 10.0])
+    return theta0, scale, consts
+
+
+def lf_settings(data: LFData, nL: int = 1024, nr: int = 1024, ln_upper: float = math.log(60.0)):
+    """theta_init (truth), theta_prop_scale, consts for the luminosity model."""
+    theta0 = np.array([data.beta, math.log(data.L_star), math.log(data.L_low)])
+    scale = np.array([0.01, 0.01, 0.01])
+    consts = np.array([data.sigma_F, data.F_th, data.r_max, float(nL), float(nr), ln_upper])
+    return theta0, scale, consts
+
+
+def lf_chi_init(data: LFData, theta) -> np.ndarray:
+    """Default start: chi_i = ln(4 pi r_i^2 max(Fhat_i, F_th)), raised to ln L_low + 1e-6."""
+    chi = np.log(4.0 * math.pi * data.r * data.r * np.maximum(data.fhat, data.F_th))
+    return np.maximum(chi, theta[2] + 1e-6)
