@@ -1,0 +1,202 @@
+/*
+ * cudahm.h -- C ABI of the GB300 (sm_103a) Metropolis-within-Gibbs sampler for
+ * single-plate hierarchical models (arXiv:2105.08026, "CUDAHM").
+ *
+ * One handle holds one population (N members, latent dimension d, population
+ * parameters theta of dimension p) and one Markov chain over (theta, chi_1..chi_N).
+ * Each sweep of cudahm_run is one Metropolis-within-Gibbs cycle (Sec. 2.1,
+ * eqs. psi_sampling and theta_sampling):
+ *   1. every member chi_i takes one robust adaptive Metropolis (RAM) step given
+ *      theta (Sec. 2.2: Y = X + S U, accept with min(1, pi(Y)/pi(X)), then
+ *      S S^T <- S (I + eta_n (alpha - alpha_*) U U^T/|U|^2) S^T);
+ *   2. theta takes one Metropolis-Hastings step whose log ratio is the sum over
+ *      members of log f(chi_i;theta') - log f(chi_i;theta) (Sec. 2.2), plus, for
+ *      the luminosity model, -N (ln etabar(theta') - ln etabar(theta)) from the
+ *      selection integral of the thinned point-process likelihood (Sec. 4.2,
+ *      eqs. rho-mlike and epdf).
+ * All of a sweep runs on the GPU in one persistent cooperative kernel; theta is
+ * accepted or rejected on the device after a bounded grid barrier, with no host
+ * round trip per sweep.
+ *
+ * Conventions
+ *   - Every int-returning call returns CUDAHM_OK (0) or a negative CUDAHM_E* code;
+ *     cudahm_last_error() then describes the failure (thread-local, never NULL).
+ *   - Array arguments named *_host are host pointers; they are copied and stay
+ *     owned by the caller. *_dev arguments are device pointers on the handle's
+ *     device, also copied (the handle never keeps a caller's pointer).
+ *   - Outputs go to caller-provided buffers whose required size is stated.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ *   - All work is enqueued on the handle's stream; calls that return host data
+ *     synchronise that stream.
+ *   - A call that fails with EINVAL/ESTATE/EUNSUPPORTED leaves the chain unchanged.
+ *     A run that fails with ETIMEOUT/ENUMERIC/ECUDA leaves the chain state as it
+ *     was before that run (latents and theta are written back only on success).
+ */
+#ifndef CUDAHM_H
+#define CUDAHM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CUDAHM_ABI_VERSION 1u
+
+#define CUDAHM_OK 0
+#define CUDAHM_EINVAL (-1)       /* bad argument or configuration */
+#define CUDAHM_ENOMEM (-2)       /* device allocation failed */
+#define CUDAHM_ECUDA (-3)        /* a CUDA runtime call failed */
+#define CUDAHM_ETIMEOUT (-4)     /* a bounded device-side wait expired (grid barrier) */
+#define CUDAHM_ENUMERIC (-5)     /* NaN in a log-density or a non-finite theta */
+#define CUDAHM_ESTATE (-6)       /* call out of order (e.g. run before set_data) */
+#define CUDAHM_EUNSUPPORTED (-7) /* valid request this build does not handle */
+
+#define CUDAHM_MAX_P 9      /* largest theta dimension (d = 3 normal model) */
+#define CUDAHM_MAX_CONSTS 8 /* model constants */
+
+typedef struct cudahm* cudahm_t;
+
+/* Models (fixed enum; each is a member density l_i, a population density f and a prior).
+ *  NN1  normal-normal, d = 1, theta = (mu, ln tau), p = 2 (Sec. 3 with one characteristic):
+ *       log l_i = -(y_i - chi)^2/(2 sigma_i^2), log f = -(chi - mu)^2/(2 tau^2) - ln tau;
+ *       prior flat in mu and in ln tau on [consts[0], consts[1]].
+ *  MVN3 normal population, d = 3, theta = (mu[3], packed Cholesky factor of C_pop with
+ *       log diagonal), p = 9 (Sec. 3 with C_pop unknown). Reserved; not in this build.
+ *  LF   thinned luminosity function (Sec. 4-5), d = 1, chi = ln L, theta = (beta, ln L*, ln L_low),
+ *       p = 3: log f = (beta+1)(chi - ln L*) - e^(chi - ln L*) on chi > ln L_low,
+ *       log l_i = -(Fhat_i - e^chi/(4 pi r_i^2))^2/(2 sigma_F^2), selection efficiency
+ *       eta(F) = Phi((F - F_th)/sigma_F), distance density ~ r^2 on [0, r_max];
+ *       prior -ln(1 + beta^2) + ln L_low on -2 < beta < 0, L_low < L*.
+ *       consts = {sigma_F, F_th, r_max, n_L, n_r, ln(upper/L*)}: the selection integral
+ *       uses an n_L-node Gauss-Legendre rule in ln L on [ln L_low, ln L* + consts[5]] times
+ *       an n_r-node rule in r on [0, r_max] (n_L, n_r <= 4096). */
+typedef enum { CUDAHM_NN1 = 0, CUDAHM_MVN3 = 1, CUDAHM_LF = 2 } cudahm_model;
+
+/* FP64: all arithmetic in binary64. FP32: reserved for the bulk-FP32 form. */
+typedef enum { CUDAHM_FP64 = 0, CUDAHM_FP32 = 1 } cudahm_precision;
+
+typedef void* (*cudahm_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*cudahm_free_fn)(void* ptr, void* ctx);
+
+typedef struct {
+  uint32_t abi_version;          /* must be CUDAHM_ABI_VERSION */
+  int32_t model;                 /* cudahm_model */
+  int32_t precision;             /* cudahm_precision */
+  int32_t d;                     /* latent dimension; must match the model */
+  int64_t n;                     /* number of members N >= 1 */
+  uint64_t seed;                 /* Philox4x32-10 key (low word, high word) */
+  double target_accept;          /* alpha_* of the member RAM (Sec. 2.2: 0.4) */
+  double adapt_exponent;         /* gamma of eta_n = n^-gamma (Sec. 2.2: 2/3) */
+  double chi_init_scale;         /* S_1 = scale * I for every member (Sec. 2.2: 1) */
+  double theta_target_accept;    /* alpha_* of the theta RAM (default 0.4) */
+  int32_t adapt_theta;           /* 1: RAM on theta; 0: fixed random-walk MH */
+  int32_t trace_sweeps;          /* >0: record a lockstep trace of the first trace_sweeps sweeps of each run */
+  double theta_init[CUDAHM_MAX_P];       /* initial theta (first p entries) */
+  double theta_prop_scale[CUDAHM_MAX_P]; /* S_theta,1 = diag(scale) */
+  double model_consts[CUDAHM_MAX_CONSTS];
+  int32_t device;                /* CUDA device ordinal */
+  int32_t block_threads;         /* threads per block of the sweep kernel; 0 = default (256) */
+  void* cuda_stream;             /* cudaStream_t to enqueue on; NULL = a stream the handle creates */
+  cudahm_alloc_fn dev_alloc;     /* optional device allocator (e.g. a framework's caching allocator) */
+  cudahm_free_fn dev_free;       /* must be given together with dev_alloc */
+  void* alloc_ctx;               /* passed back to dev_alloc / dev_free */
+  int64_t barrier_timeout_ns;    /* bound on every device-side wait; 0 = 2 s */
+  int32_t debug_skip_barrier_cta;/* >= 0: that block never arrives at the grid barrier (tests the
+                                    timeout path); -1 = off */
+  int32_t reserved;
+} cudahm_config;
+
+typedef struct {
+  int64_t sweeps;             /* sweeps done since create (or since the restored checkpoint) */
+  int64_t member_accepts;     /* accepted member proposals since create */
+  int64_t theta_accepts;      /* accepted theta proposals since create */
+  int64_t rows;               /* theta rows held in the sample buffer */
+  double last_run_ms;         /* device time of the last cudahm_run (CUDA events) */
+  double etabar;              /* LF: selection integral at the current theta; 0 otherwise */
+  int32_t grid_blocks;        /* launch shape of the sweep kernel */
+  int32_t block_threads;
+  int32_t objects_per_thread;
+  int32_t reserved;
+} cudahm_stats;
+
+/* Fill *cfg with the defaults above for the given model and N (seed 1, theta_init 0,
+ * theta_prop_scale 0.01, NN1 prior on ln tau [-10, 10], LF rule 1024 x 1024 with
+ * upper limit 60 L*). */
+void cudahm_config_init(cudahm_config* cfg, int32_t model, int64_t n);
+
+/* Create a handle: validates cfg, selects the device, allocates the device state and,
+ * for LF, builds the quadrature tables on the device. *out is set only on success. */
+int cudahm_create(const cudahm_config* cfg, cudahm_t* out);
+
+/* Member data, N entries each (copied):
+ *   NN1: y = y_i, aux = sigma_i (> 0);   LF: y = Fhat_i, aux = r_i (> 0).
+ * Resets the latents to the default start (NN1: chi_i = y_i; LF: chi_i = ln(4 pi r_i^2
+ * max(Fhat_i, F_th)), raised to ln L_low + 1e-6 if below), every S_i to
+ * chi_init_scale * I, theta to theta_init, S_theta to diag(theta_prop_scale), and the
+ * sweep counter and sample buffer to zero. */
+int cudahm_set_data(cudahm_t h, const double* y_host, const double* aux_host, int64_t n);
+int cudahm_set_data_device(cudahm_t h, const double* y_dev, const double* aux_dev, int64_t n);
+
+/* Override the starting latents (N*d values, member-major; copied). Must follow set_data
+ * and precede the first run. EINVAL if a value is off the model's support at theta. */
+int cudahm_set_chi(cudahm_t h, const double* chi_host, int64_t n);
+
+/* Run n_burn + n_iter sweeps, continuing the chain; keep theta after every thin-th sweep
+ * of the n_iter (sweeps n_burn + thin, n_burn + 2 thin, ...). The sample buffer is
+ * replaced by this run's rows. Blocking. run(a) then run(b) equals run(a + b) bit for bit
+ * when both keep no rows (n_iter = 0) or when rows are compared by concatenation. */
+int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin);
+
+/* Copy up to cap_rows theta rows (row-major, p doubles each) of the last run. */
+int cudahm_get_samples(cudahm_t h, double* theta_host, int64_t cap_rows, int64_t* rows_out);
+
+/* Current latents (N*d doubles) and/or per-member RAM factors (N*d*d doubles, lower,
+ * row-major per member); either pointer may be NULL. */
+int cudahm_get_chi(cudahm_t h, double* chi_host, double* S_host);
+
+/* Current theta (p doubles) and S_theta (p*p, lower, row-major); either may be NULL. */
+int cudahm_get_theta(cudahm_t h, double* theta_host, double* S_theta_host);
+
+int cudahm_get_stats(cudahm_t h, cudahm_stats* s);
+
+/* Per-member log target lp_i = log l_i(chi_i) + log f(chi_i;theta) without the theta-only
+ * term (-inf off support), at the current latents and the given theta (p doubles, host).
+ * Writes N doubles to lp_host. Evaluated by a device kernel in the handle's precision. */
+int cudahm_eval_logdens(cudahm_t h, const double* theta_host, double* lp_host);
+
+/* LF only: the selection integral etabar(theta) of the handle's rule at the given theta. */
+int cudahm_eval_etabar(cudahm_t h, const double* theta_host, double* out);
+
+/* Lockstep trace of the first T = min(trace_sweeps, sweeps of the last run) sweeps of the
+ * last run. Member arrays are [T][N] (sweep-major): delta = lp(Y) - lp(X) (-inf off support),
+ * u = accept uniform, acc = 1 if accepted. Theta arrays: theta_prop [T][p], D [T] = sum of
+ * log f(chi_i;theta') - log f(chi_i;theta) (-inf if a member is off the proposal's support,
+ * 0 if theta' is off the prior), logalpha [T], utheta [T], tacc [T], etabar_prop [T]
+ * (LF: etabar(theta'), else 0). Any pointer may be NULL. *t_out receives T. */
+int cudahm_get_trace(cudahm_t h, double* delta, double* u, uint8_t* acc, double* theta_prop, double* D,
+                     double* logalpha, double* utheta, uint8_t* tacc, double* etabar_prop, int64_t* t_out);
+
+/* Serialise the whole chain state (latents, RAM factors, theta, S_theta, counters) into buf.
+ * With buf == NULL or cap too small, *used receives the required size and the call returns
+ * EINVAL (buf NULL: OK). cudahm_restore loads such a buffer into a handle created with the
+ * same config and data; the continued chain is bit-identical to an uninterrupted one. */
+int cudahm_checkpoint(cudahm_t h, void* buf, size_t cap, size_t* used);
+int cudahm_restore(cudahm_t h, const void* buf, size_t size);
+
+/* sizeof(cudahm_config) and sizeof(cudahm_stats) as compiled into the library, so that
+ * bindings can check their struct layouts. */
+size_t cudahm_sizeof_config(void);
+size_t cudahm_sizeof_stats(void);
+
+/* Message of the last failed call on this thread; never NULL. */
+const char* cudahm_last_error(void);
+
+/* Release the handle and its device memory; NULL is ignored. */
+void cudahm_destroy(cudahm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUDAHM_H */

@@ -1,0 +1,191 @@
+// Device building blocks of the sweep kernels (sm_103a).
+//
+//  - Philox4x32-10 counter-based generator (Salmon et al., SC'11) keyed by the run
+//    seed; counter = (block j, stream s, member i, sweep k).
+//  - Uniforms (2m+1) 2^-53 built from the bits (exact), Box-Muller normals.
+//  - Xacc: a 192-bit two's-complement fixed-point accumulator with 2^-96 resolution.
+//    Each addend is rounded toward zero to a multiple of 2^-96 and then added exactly,
+//    so a sum is the same for every order and every launch shape.
+//  - A grid barrier whose spin is bounded by %globaltimer: on expiry it records
+//    CUDAHM_ETIMEOUT in the run's error word and every block leaves the kernel.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "cudahm.h"
+
+namespace chm {
+
+// ------------------------------------------------------------------ RNG -----
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// (2m+1) 2^-53 with m the top 52 bits of (wa:wb): 1 + m 2^-52 is assembled from the
+// bits, then 1 - 2^-53 is subtracted; the difference is representable, hence exact.
+__device__ __forceinline__ double uniform53(uint32_t wa, uint32_t wb) {
+  const unsigned long long m = ((static_cast<unsigned long long>(wa) << 32) | wb) >> 12;
+  const double v = __longlong_as_double(static_cast<long long>(0x3FF0000000000000ull | m));
+  return v - 0x1.fffffffffffffp-1;
+}
+
+// ------------------------------------------------------------- Xacc ---------
+struct Xacc {
+  unsigned long long w0, w1, w2;  // little-endian limbs; value = (signed 192-bit) * 2^-96
+};
+
+__device__ __forceinline__ void xacc_zero(Xacc& a) { a.w0 = a.w1 = a.w2 = 0ull; }
+
+__device__ __forceinline__ void xacc_add(Xacc& a, const Xacc& b) {
+  asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, %5;"
+      : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2)
+      : "l"(b.w0), "l"(b.w1), "l"(b.w2));
+}
+
+// Flags counted next to the sum.
+struct XFlags {
+  unsigned int neg_inf;  // -inf addends (support violations)
+  unsigned int nan;      // NaN addends
+  unsigned int big;      // finite addends with |v| >= 2^94 (outside the fixed-point range)
+};
+
+// Add v (rounded toward zero to a multiple of 2^-96). Non-finite or huge values are
+// counted in f instead of added.
+__device__ __forceinline__ void xacc_add_double(Xacc& a, double v, XFlags& f) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(v));
+  const int e = static_cast<int>((u >> 52) & 0x7ff);
+  if (e == 0x7ff) {
+    if (u & 0x000FFFFFFFFFFFFFull) f.nan++;
+    else if (u >> 63) f.neg_inf++;
+    else f.big++;
+    return;
+  }
+  if (e >= 1023 + 94) { f.big++; return; }
+  const int sh = e - 979;  // value * 2^96 = m * 2^(e - 1075 + 96)
+  if (e == 0 || sh <= -53) return;  // below 2^-96 (or subnormal): rounds to zero
+  const unsigned long long m = (u & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  Xacc t;
+  if (sh < 0) {
+    t.w0 = m >> (-sh); t.w1 = 0ull; t.w2 = 0ull;
+  } else {
+    const int q = sh >> 6, r = sh & 63;
+    const unsigned long long lo = m << r;
+    const unsigned long long hi = r ? (m >> (64 - r)) : 0ull;
+    t.w0 = (q == 0) ? lo : 0ull;
+    t.w1 = (q == 1) ? lo : ((q == 0) ? hi : 0ull);
+    t.w2 = (q == 2) ? lo : ((q == 1) ? hi : 0ull);
+  }
+  if (u >> 63) {  // two's-complement negate
+    t.w0 = ~t.w0; t.w1 = ~t.w1; t.w2 = ~t.w2;
+    asm("add.cc.u64 %0, %0, 1;\n\taddc.cc.u64 %1, %1, 0;\n\taddc.u64 %2, %2, 0;"
+        : "+l"(t.w0), "+l"(t.w1), "+l"(t.w2));
+  }
+  xacc_add(a, t);
+}
+
+// Round-to-nearest-even conversion of the fixed-point value to binary64.
+__device__ __forceinline__ double xacc_to_double(Xacc a) {
+  const bool neg = (a.w2 >> 63) != 0;
+  if (neg) {
+    a.w0 = ~a.w0; a.w1 = ~a.w1; a.w2 = ~a.w2;
+    asm("add.cc.u64 %0, %0, 1;\n\taddc.cc.u64 %1, %1, 0;\n\taddc.u64 %2, %2, 0;"
+        : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2));
+  }
+  int hb;  // index of the highest set bit
+  if (a.w2) hb = 128 + 63 - __clzll(static_cast<long long>(a.w2));
+  else if (a.w1) hb = 64 + 63 - __clzll(static_cast<long long>(a.w1));
+  else if (a.w0) hb = 63 - __clzll(static_cast<long long>(a.w0));
+  else return 0.0;
+  // top 64 bits starting at hb (left-aligned), and a sticky bit for everything below
+  unsigned long long top, rest_nonzero;
+  const int lo_bit = hb - 63;  // bit index of the LSB of 'top'
+  if (lo_bit <= 0) {  // hb <= 63: the value sits in w0
+    top = a.w0 << (-lo_bit);
+    rest_nonzero = 0ull;
+  } else {
+    const int q = lo_bit >> 6, r = lo_bit & 63;
+    const unsigned long long limb[4] = {a.w0, a.w1, a.w2, 0ull};
+    top = r ? ((limb[q] >> r) | (limb[q + 1] << (64 - r))) : limb[q];
+    unsigned long long below = 0ull;
+    for (int i = 0; i < q; ++i) below |= limb[i];
+    if (r) below |= (limb[q] << (64 - r));
+    rest_nonzero = below;
+  }
+  // 53-bit mantissa, guard bit, sticky
+  unsigned long long mant = top >> 11;
+  const unsigned long long guard = (top >> 10) & 1ull;
+  const unsigned long long sticky = ((top & 0x3FFull) != 0ull) | (rest_nonzero != 0ull);
+  if (guard && (sticky || (mant & 1ull))) mant += 1ull;
+  int exp2 = hb - 96 - 52;  // value = mant * 2^exp2
+  if (mant >> 53) { mant >>= 1; exp2 += 1; }
+  const double r = scalbn(static_cast<double>(mant), exp2);
+  return neg ? -r : r;
+}
+
+__device__ __forceinline__ Xacc xacc_shfl_xor(const Xacc& a, int lane_mask) {
+  Xacc b;
+  b.w0 = __shfl_xor_sync(0xffffffffu, a.w0, lane_mask);
+  b.w1 = __shfl_xor_sync(0xffffffffu, a.w1, lane_mask);
+  b.w2 = __shfl_xor_sync(0xffffffffu, a.w2, lane_mask);
+  return b;
+}
+
+// ---------------------------------------------------------- barrier ----------
+__device__ __forceinline__ long long globaltimer_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+  return *reinterpret_cast<const volatile int*>(p);
+}
+
+// Grid-wide barrier number `index` (0-based) of this launch. The counter starts at 0 for
+// every launch. Returns false if the run has failed (timeout here or an error elsewhere);
+// the caller then leaves the kernel. Must be called by all threads of the block.
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int index, int* err, long long limit_ns,
+                                             bool skip_arrival) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (!skip_arrival) {
+      __threadfence();
+      atomicAdd(count, 1u);
+    }
+    const unsigned int target = (index + 1u) * gridDim.x;
+    const long long t0 = globaltimer_ns();
+    while (true) {
+      if (ld_acquire_u32(count) >= target) break;
+      if (ld_volatile_i32(err) != 0) { ok = 0; break; }
+      if (globaltimer_ns() - t0 > limit_ns) {
+        atomicCAS(err, 0, CUDAHM_ETIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    if (ld_volatile_i32(err) != 0) ok = 0;
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+}  // namespace chm

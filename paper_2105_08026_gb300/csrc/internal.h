@@ -1,0 +1,98 @@
+// Internal interface between the host runtime (runtime.cu) and the kernels (sweep.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace chm {
+
+constexpr int kMaxP = 9;
+constexpr int kPartWords = 8;  // u64 words of one block's partial: D[3], E[3], flags[2]
+
+// Chain state kept on the device between runs.
+struct ChainState {
+  double theta[kMaxP];
+  double S_theta[kMaxP * kMaxP];
+  double etabar;     // LF: selection integral at theta (0 = not computed)
+  long long sweeps;  // sweeps done
+  long long member_acc;
+  long long theta_acc;
+  long long rows;    // rows written by the last launch
+};
+
+// Model constants used inside kernels.
+struct ModelConsts {
+  double lo, hi;        // NN1: prior range of ln tau
+  double inv2sig2;      // LF: 1/(2 sigma_F^2)
+  double cth;           // LF: F_th / sigma_F
+  double F_th;          // LF
+  double ln_upper;      // LF: ln(upper/L*)
+  double chi_init_scale;
+};
+
+struct SweepArgs {
+  int model;
+  int p;
+  long long n;
+  const double* y;    // NN1: y_i;  LF: Fhat_i
+  const double* aux;  // NN1: 1/sigma_i^2;  LF: 1/(4 pi r_i^2)
+  double* chi;
+  double* S;
+  ChainState* chain;
+  unsigned long long* partials;  // [2][grid][kPartWords]
+  unsigned int* bar;
+  int* err;
+  const double* tab_U;    // [ns][p] theta-proposal normals
+  const double* tab_u;    // [ns] theta accept uniforms
+  const double* tab_eta;  // [ns] adaptation weights (k+1)^-gamma
+  long long k0;           // sweeps done before this launch
+  long long ns;           // sweeps in this launch
+  long long burn_left;    // sweeps of this launch still in burn-in
+  long long thin;
+  long long keep_phase;   // post-burn sweeps already done by earlier launches of this run
+  double* rows;           // theta rows of this launch
+  double astar, astar_theta;
+  int adapt_theta;
+  uint32_t key0, key1;
+  ModelConsts mc;
+  // LF selection rule
+  const double* xL;
+  const double* wL;
+  const double* qs;  // q(r_k)/sigma_F
+  const double* Wr;  // inner weights
+  int nL, nr;
+  int rows_smem;     // row slots per block for the outer-node values
+  // trace (nullable)
+  long long trace_T;
+  long long trace_off;  // sweeps of this run traced by earlier launches
+  double* tr_delta;
+  double* tr_u;
+  uint8_t* tr_acc;
+  double* tr_thprop;
+  double* tr_D;
+  double* tr_logalpha;
+  double* tr_ut;
+  uint8_t* tr_tacc;
+  double* tr_eb;
+  long long timeout_ns;
+  int skip_cta;
+};
+
+// Kernel launch helpers (sweep.cu). Return cudaError_t of the launch.
+cudaError_t launch_sweep(const SweepArgs& a, int K, int grid, int block, cudaStream_t st);
+cudaError_t sweep_occupancy(int model, int K, int block, int smem_bytes, int* blocks_per_sm);
+cudaError_t launch_prepare(int model, long long n, const double* y_raw, const double* aux_raw, double* y, double* aux,
+                           double* chi, double* S, const ModelConsts& mc, const double* theta, int* bad,
+                           int set_default_chi, cudaStream_t st);
+cudaError_t launch_check_chi(int model, long long n, const double* chi, const double* theta, int* bad,
+                             cudaStream_t st);
+cudaError_t launch_gauss_legendre(int n, double* x, double* w, cudaStream_t st);
+cudaError_t launch_lf_inner(int nr, const double* xr, const double* wr, double r_max, double sigma_F, double* qs,
+                            double* Wr, cudaStream_t st);
+cudaError_t launch_tables(int p, uint32_t key0, uint32_t key1, long long k0, long long ns, double gamma, double* U,
+                          double* u, double* eta, cudaStream_t st);
+cudaError_t launch_eval_logdens(int model, long long n, const double* y, const double* aux, const double* chi,
+                                const double* theta_dev, const ModelConsts& mc, double* out, cudaStream_t st);
+cudaError_t launch_eval_etabar(const double* theta_dev, const SweepArgs& rule, unsigned long long* partials,
+                               int grid, double* out, cudaStream_t st);
+
+}  // namespace chm

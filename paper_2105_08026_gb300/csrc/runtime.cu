@@ -1,0 +1,713 @@
+// Host runtime behind the C ABI of include/cudahm.h: handle ownership, validation,
+// device buffers, launch-shape selection, chunked persistent launches, checkpoints.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstddef>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cudahm.h"
+#include "internal.h"
+
+using namespace chm;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CU(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(CUDAHM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int model_d(int m) { return m == CUDAHM_MVN3 ? 3 : 1; }
+int model_p(int m) { return m == CUDAHM_NN1 ? 2 : (m == CUDAHM_LF ? 3 : 9); }
+
+constexpr long long kChunk = 4096;  // sweeps per persistent launch
+
+}  // namespace
+
+struct cudahm {
+  cudahm_config cfg{};
+  int d = 1, p = 2;
+  long long n = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sms = 0;
+  // launch shape
+  int grid = 0, block = 256, K = 1, rows_smem = 1;
+  ModelConsts mc{};
+  // device buffers
+  std::vector<void*> allocs;
+  double *y = nullptr, *aux = nullptr, *chi = nullptr, *S = nullptr;
+  double *y_raw = nullptr, *aux_raw = nullptr;
+  ChainState* chain = nullptr;
+  unsigned long long* partials = nullptr;
+  unsigned int* bar = nullptr;
+  int* err = nullptr;
+  int* bad = nullptr;
+  double* theta_dev = nullptr;
+  double* eval_out = nullptr;
+  double *tab_U = nullptr, *tab_u = nullptr, *tab_eta = nullptr;
+  double* rows = nullptr;
+  long long rows_cap = 0;
+  // trace
+  long long trace_cap_T = 0;
+  double *tr_delta = nullptr, *tr_u = nullptr, *tr_thprop = nullptr, *tr_D = nullptr, *tr_logalpha = nullptr,
+         *tr_ut = nullptr, *tr_eb = nullptr;
+  uint8_t *tr_acc = nullptr, *tr_tacc = nullptr;
+  long long trace_T_last = 0;
+  // LF rule
+  double *xL = nullptr, *wL = nullptr, *xr = nullptr, *wr = nullptr, *qs = nullptr, *Wr = nullptr;
+  unsigned long long* eb_partials = nullptr;
+  int eb_grid = 0, eb_rows_smem = 1;
+  // host mirrors
+  bool data_set = false;
+  bool etabar_valid = false;
+  long long sweeps = 0;
+  long long rows_last = 0;
+  double last_run_ms = 0.0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int* host_err = nullptr;  // pinned
+
+  void* dalloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* ptr = nullptr;
+    if (cfg.dev_alloc) {
+      ptr = cfg.dev_alloc(bytes, cfg.alloc_ctx);
+    } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+      ptr = nullptr;
+    }
+    if (ptr) allocs.push_back(ptr);
+    return ptr;
+  }
+  void dfree(void* ptr) {
+    if (!ptr) return;
+    auto it = std::find(allocs.begin(), allocs.end(), ptr);
+    if (it != allocs.end()) allocs.erase(it);
+    if (cfg.dev_free) cfg.dev_free(ptr, cfg.alloc_ctx);
+    else cudaFree(ptr);
+  }
+  ~cudahm() {
+    if (stream) cudaStreamSynchronize(stream);
+    for (void* ptr : allocs) {
+      if (cfg.dev_free) cfg.dev_free(ptr, cfg.alloc_ctx);
+      else cudaFree(ptr);
+    }
+    if (host_err) cudaFreeHost(host_err);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+
+template <class T>
+int alloc_into(cudahm* h, T** out, size_t count) {
+  *out = static_cast<T*>(h->dalloc(sizeof(T) * count));
+  if (!*out) return fail(CUDAHM_ENOMEM, "device allocation of %zu bytes failed", sizeof(T) * count);
+  return CUDAHM_OK;
+}
+
+#define TRY(x)                \
+  do {                        \
+    int r_ = (x);             \
+    if (r_ != CUDAHM_OK) return r_; \
+  } while (0)
+
+int validate(const cudahm_config* c) {
+  if (!c) return fail(CUDAHM_EINVAL, "config is NULL");
+  if (c->abi_version != CUDAHM_ABI_VERSION)
+    return fail(CUDAHM_EINVAL, "abi_version %u != %u", c->abi_version, CUDAHM_ABI_VERSION);
+  if (c->model != CUDAHM_NN1 && c->model != CUDAHM_LF && c->model != CUDAHM_MVN3)
+    return fail(CUDAHM_EINVAL, "unknown model %d", c->model);
+  if (c->model == CUDAHM_MVN3) return fail(CUDAHM_EUNSUPPORTED, "model MVN3 is not in this build");
+  if (c->precision != CUDAHM_FP64) return fail(CUDAHM_EUNSUPPORTED, "only FP64 precision is in this build");
+  if (c->d != model_d(c->model)) return fail(CUDAHM_EINVAL, "d = %d does not match the model", c->d);
+  if (c->n < 1 || c->n > (1ll << 31)) return fail(CUDAHM_EINVAL, "n = %lld out of range [1, 2^31]", (long long)c->n);
+  if (!(c->target_accept > 0.0 && c->target_accept < 1.0)) return fail(CUDAHM_EINVAL, "target_accept not in (0,1)");
+  if (!(c->theta_target_accept > 0.0 && c->theta_target_accept < 1.0))
+    return fail(CUDAHM_EINVAL, "theta_target_accept not in (0,1)");
+  if (!(c->adapt_exponent > 0.5 && c->adapt_exponent <= 1.0))
+    return fail(CUDAHM_EINVAL, "adapt_exponent must lie in (1/2, 1]");
+  if (!(c->chi_init_scale > 0.0) || !std::isfinite(c->chi_init_scale))
+    return fail(CUDAHM_EINVAL, "chi_init_scale must be positive");
+  if ((c->dev_alloc == nullptr) != (c->dev_free == nullptr))
+    return fail(CUDAHM_EINVAL, "dev_alloc and dev_free must be given together");
+  if (c->block_threads != 0 && c->block_threads != 128 && c->block_threads != 256)
+    return fail(CUDAHM_EINVAL, "block_threads must be 0, 128 or 256");
+  if (c->trace_sweeps < 0) return fail(CUDAHM_EINVAL, "trace_sweeps < 0");
+  const int p = model_p(c->model);
+  for (int q = 0; q < p; ++q) {
+    if (!std::isfinite(c->theta_init[q])) return fail(CUDAHM_EINVAL, "theta_init[%d] not finite", q);
+    if (!(c->theta_prop_scale[q] >= 0.0) || !std::isfinite(c->theta_prop_scale[q]))
+      return fail(CUDAHM_EINVAL, "theta_prop_scale[%d] must be >= 0", q);
+  }
+  if (c->adapt_theta) {
+    for (int q = 0; q < p; ++q)
+      if (!(c->theta_prop_scale[q] > 0.0))
+        return fail(CUDAHM_EINVAL, "adapt_theta needs theta_prop_scale[%d] > 0", q);
+  }
+  const double* k = c->model_consts;
+  if (c->model == CUDAHM_NN1) {
+    if (!(k[0] < k[1])) return fail(CUDAHM_EINVAL, "NN1 prior range needs consts[0] < consts[1]");
+    if (!(c->theta_init[1] >= k[0] && c->theta_init[1] <= k[1]))
+      return fail(CUDAHM_EINVAL, "theta_init outside the NN1 prior");
+  } else if (c->model == CUDAHM_LF) {
+    if (!(k[0] > 0.0) || !(k[1] > 0.0) || !(k[2] > 0.0)) return fail(CUDAHM_EINVAL, "LF needs sigma_F, F_th, r_max > 0");
+    const double nL = k[3], nr = k[4];
+    if (!(nL >= 1 && nL <= 4096 && nL == std::floor(nL)) || !(nr >= 1 && nr <= 4096 && nr == std::floor(nr)))
+      return fail(CUDAHM_EINVAL, "LF rule sizes must be integers in [1, 4096]");
+    if (!(k[5] > 0.0)) return fail(CUDAHM_EINVAL, "LF upper limit ln(upper/L*) must be > 0");
+    const double* t = c->theta_init;
+    if (!(t[0] > -2.0 && t[0] < 0.0 && t[2] < t[1])) return fail(CUDAHM_EINVAL, "theta_init outside the LF prior");
+  }
+  return CUDAHM_OK;
+}
+
+int choose_shape(cudahm* h) {
+  const int block = h->cfg.block_threads ? h->cfg.block_threads : 256;
+  h->block = block;
+  const long long n = h->n;
+  const int model = h->cfg.model;
+  const int Ks[4] = {1, 2, 4, 8};
+  for (int ki = 0; ki < 4; ++ki) {
+    const int K = Ks[ki];
+    int bps = 0;
+    // shared memory for the LF rows depends on the grid; bound it first with one row slot
+    CU(sweep_occupancy(model, K, block, 2 * 8 * 8, &bps));
+    if (bps < 1) continue;
+    int grid;
+    if (model == CUDAHM_LF) grid = bps * h->sms;
+    else grid = static_cast<int>(std::min<long long>(static_cast<long long>(bps) * h->sms, (n + block - 1) / block));
+    const long long need = (n + static_cast<long long>(grid) * block - 1) / (static_cast<long long>(grid) * block);
+    if (need <= K) {
+      h->K = K;
+      h->grid = grid;
+      break;
+    }
+  }
+  if (h->grid == 0) return fail(CUDAHM_EUNSUPPORTED, "n = %lld exceeds the register-resident capacity", n);
+  if (model == CUDAHM_LF) {
+    const long long P = static_cast<long long>(h->cfg.model_consts[3]) * static_cast<long long>(h->cfg.model_consts[4]);
+    const long long nr = static_cast<long long>(h->cfg.model_consts[4]);
+    h->rows_smem = static_cast<int>((P / h->grid + nr - 1) / nr + 2);
+    int bps = 0;
+    CU(sweep_occupancy(model, h->K, block, 2 * 8 * h->rows_smem, &bps));
+    if (bps * h->sms < h->grid) {
+      h->grid = bps * h->sms;
+      h->rows_smem = static_cast<int>((P / h->grid + nr - 1) / nr + 2);
+      const long long need = (n + static_cast<long long>(h->grid) * block - 1) / (static_cast<long long>(h->grid) * block);
+      if (need > h->K) return fail(CUDAHM_EUNSUPPORTED, "n = %lld exceeds the register-resident capacity", n);
+    }
+    h->eb_grid = 4 * h->sms;
+    h->eb_rows_smem = static_cast<int>((P / h->eb_grid + nr - 1) / nr + 2);
+  }
+  return CUDAHM_OK;
+}
+
+SweepArgs base_args(cudahm* h) {
+  SweepArgs a{};
+  a.model = h->cfg.model;
+  a.p = h->p;
+  a.n = h->n;
+  a.y = h->y;
+  a.aux = h->aux;
+  a.chi = h->chi;
+  a.S = h->S;
+  a.chain = h->chain;
+  a.partials = h->partials;
+  a.bar = h->bar;
+  a.err = h->err;
+  a.astar = h->cfg.target_accept;
+  a.astar_theta = h->cfg.theta_target_accept;
+  a.adapt_theta = h->cfg.adapt_theta;
+  a.key0 = static_cast<uint32_t>(h->cfg.seed & 0xffffffffull);
+  a.key1 = static_cast<uint32_t>(h->cfg.seed >> 32);
+  a.mc = h->mc;
+  a.xL = h->xL;
+  a.wL = h->wL;
+  a.qs = h->qs;
+  a.Wr = h->Wr;
+  a.nL = h->cfg.model == CUDAHM_LF ? static_cast<int>(h->cfg.model_consts[3]) : 0;
+  a.nr = h->cfg.model == CUDAHM_LF ? static_cast<int>(h->cfg.model_consts[4]) : 0;
+  a.rows_smem = h->rows_smem;
+  a.timeout_ns = h->cfg.barrier_timeout_ns > 0 ? h->cfg.barrier_timeout_ns : 2000000000ll;
+  a.skip_cta = h->cfg.debug_skip_barrier_cta;
+  return a;
+}
+
+int reset_chain(cudahm* h) {
+  ChainState cs{};
+  for (int q = 0; q < h->p; ++q) cs.theta[q] = h->cfg.theta_init[q];
+  for (int q = 0; q < h->p; ++q) cs.S_theta[q * h->p + q] = h->cfg.theta_prop_scale[q];
+  CU(cudaMemcpyAsync(h->chain, &cs, sizeof(cs), cudaMemcpyHostToDevice, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->sweeps = 0;
+  h->rows_last = 0;
+  h->etabar_valid = false;
+  return CUDAHM_OK;
+}
+
+int read_err(cudahm* h, int* code) {
+  CU(cudaMemcpyAsync(h->host_err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  *code = *h->host_err;
+  return CUDAHM_OK;
+}
+
+int compute_etabar_into(cudahm* h, const double* theta_dev, double* out_dev) {
+  SweepArgs r = base_args(h);
+  r.rows_smem = h->eb_rows_smem;
+  CU(launch_eval_etabar(theta_dev, r, h->eb_partials, h->eb_grid, out_dev, h->stream));
+  return CUDAHM_OK;
+}
+
+int prepare(cudahm* h, const double* y_dev_raw, const double* aux_dev_raw, int set_default) {
+  CU(cudaMemsetAsync(h->bad, 0, sizeof(int), h->stream));
+  CU(launch_prepare(h->cfg.model, h->n, y_dev_raw, aux_dev_raw, h->y, h->aux, h->chi, h->S, h->mc, h->cfg.theta_init,
+                    h->bad, set_default, h->stream));
+  int bad = 0;
+  CU(cudaMemcpyAsync(h->host_err, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  bad = *h->host_err;
+  if (bad) return fail(CUDAHM_EINVAL, "%d members have non-finite data or a non-positive scale", bad);
+  TRY(reset_chain(h));
+  h->data_set = true;
+  return CUDAHM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cudahm_config_init(cudahm_config* cfg, int32_t model, int64_t n) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->abi_version = CUDAHM_ABI_VERSION;
+  cfg->model = model;
+  cfg->precision = CUDAHM_FP64;
+  cfg->d = model_d(model);
+  cfg->n = n;
+  cfg->seed = 1;
+  cfg->target_accept = 0.4;
+  cfg->adapt_exponent = 2.0 / 3.0;
+  cfg->chi_init_scale = 1.0;
+  cfg->theta_target_accept = 0.4;
+  cfg->adapt_theta = 1;
+  for (int q = 0; q < CUDAHM_MAX_P; ++q) cfg->theta_prop_scale[q] = 0.01;
+  if (model == CUDAHM_NN1) {
+    cfg->model_consts[0] = -10.0;
+    cfg->model_consts[1] = 10.0;
+  } else if (model == CUDAHM_LF) {
+    cfg->model_consts[3] = 1024;
+    cfg->model_consts[4] = 1024;
+    cfg->model_consts[5] = std::log(60.0);
+  }
+  cfg->device = 0;
+  cfg->debug_skip_barrier_cta = -1;
+}
+
+const char* cudahm_last_error(void) { return g_last_error.c_str(); }
+
+size_t cudahm_sizeof_config(void) { return sizeof(cudahm_config); }
+size_t cudahm_sizeof_stats(void) { return sizeof(cudahm_stats); }
+
+int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
+  if (!out) return fail(CUDAHM_EINVAL, "out is NULL");
+  TRY(validate(cfg));
+  int ndev = 0;
+  CU(cudaGetDeviceCount(&ndev));
+  if (cfg->device < 0 || cfg->device >= ndev) return fail(CUDAHM_EINVAL, "device %d not present", cfg->device);
+  CU(cudaSetDevice(cfg->device));
+  int coop = 0;
+  CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, cfg->device));
+  if (!coop) return fail(CUDAHM_EUNSUPPORTED, "device has no cooperative launch");
+
+  cudahm* h = new cudahm();
+  h->cfg = *cfg;
+  h->d = cfg->d;
+  h->p = model_p(cfg->model);
+  h->n = cfg->n;
+  auto bail = [&](int code) {
+    delete h;
+    return code;
+  };
+  if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess)
+    return bail(fail(CUDAHM_ECUDA, "cannot query SM count"));
+  if (cfg->cuda_stream) {
+    h->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(fail(CUDAHM_ECUDA, "cannot create a stream"));
+    h->own_stream = true;
+  }
+  if (cudaHostAlloc(reinterpret_cast<void**>(&h->host_err), sizeof(int) * 4, cudaHostAllocDefault) != cudaSuccess)
+    return bail(fail(CUDAHM_ECUDA, "cannot allocate pinned host memory"));
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess)
+    return bail(fail(CUDAHM_ECUDA, "cannot create events"));
+
+  // model constants
+  const double* k = cfg->model_consts;
+  h->mc.chi_init_scale = cfg->chi_init_scale;
+  if (cfg->model == CUDAHM_NN1) {
+    h->mc.lo = k[0];
+    h->mc.hi = k[1];
+  } else {
+    h->mc.inv2sig2 = 1.0 / (2.0 * k[0] * k[0]);
+    h->mc.cth = k[1] / k[0];
+    h->mc.F_th = k[1];
+    h->mc.ln_upper = k[5];
+  }
+  int rc = choose_shape(h);
+  if (rc != CUDAHM_OK) return bail(rc);
+
+  const long long n = h->n;
+  const int p = h->p;
+  if ((rc = alloc_into(h, &h->y, n)) || (rc = alloc_into(h, &h->aux, n)) || (rc = alloc_into(h, &h->chi, n * h->d)) ||
+      (rc = alloc_into(h, &h->S, n * h->d * h->d)) || (rc = alloc_into(h, &h->chain, 1)) ||
+      (rc = alloc_into(h, &h->partials, 2ull * h->grid * kPartWords)) || (rc = alloc_into(h, &h->bar, 4)) ||
+      (rc = alloc_into(h, &h->err, 4)) || (rc = alloc_into(h, &h->bad, 4)) ||
+      (rc = alloc_into(h, &h->theta_dev, kMaxP)) || (rc = alloc_into(h, &h->eval_out, 4)) ||
+      (rc = alloc_into(h, &h->tab_U, kChunk * p)) || (rc = alloc_into(h, &h->tab_u, kChunk)) ||
+      (rc = alloc_into(h, &h->tab_eta, kChunk)))
+    return bail(rc);
+  if (cfg->model == CUDAHM_LF) {
+    const int nL = static_cast<int>(k[3]), nr = static_cast<int>(k[4]);
+    if ((rc = alloc_into(h, &h->xL, nL)) || (rc = alloc_into(h, &h->wL, nL)) || (rc = alloc_into(h, &h->xr, nr)) ||
+        (rc = alloc_into(h, &h->wr, nr)) || (rc = alloc_into(h, &h->qs, nr)) || (rc = alloc_into(h, &h->Wr, nr)) ||
+        (rc = alloc_into(h, &h->eb_partials, 4ull * h->eb_grid)))
+      return bail(rc);
+    if (launch_gauss_legendre(nL, h->xL, h->wL, h->stream) != cudaSuccess ||
+        launch_gauss_legendre(nr, h->xr, h->wr, h->stream) != cudaSuccess ||
+        launch_lf_inner(nr, h->xr, h->wr, k[2], k[0], h->qs, h->Wr, h->stream) != cudaSuccess)
+      return bail(fail(CUDAHM_ECUDA, "quadrature set-up failed: %s", cudaGetErrorString(cudaGetLastError())));
+  }
+  if (cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return bail(fail(CUDAHM_ECUDA, "initialisation failed"));
+  if ((rc = reset_chain(h)) != CUDAHM_OK) return bail(rc);
+  *out = h;
+  return CUDAHM_OK;
+}
+
+void cudahm_destroy(cudahm_t h) { delete h; }
+
+static int set_data_impl(cudahm_t h, const double* y, const double* aux, int64_t n, cudaMemcpyKind kind) {
+  if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
+  if (!y || !aux) return fail(CUDAHM_EINVAL, "data pointers are NULL");
+  if (n != h->n) return fail(CUDAHM_EINVAL, "n = %lld but the handle has %lld members", (long long)n, h->n);
+  CU(cudaSetDevice(h->cfg.device));
+  const size_t cnt = static_cast<size_t>(h->n) * h->d;
+  if (!h->y_raw) {
+    TRY(alloc_into(h, &h->y_raw, cnt));
+    TRY(alloc_into(h, &h->aux_raw, cnt));
+  }
+  CU(cudaMemcpyAsync(h->y_raw, y, sizeof(double) * cnt, kind, h->stream));
+  CU(cudaMemcpyAsync(h->aux_raw, aux, sizeof(double) * cnt, kind, h->stream));
+  return prepare(h, h->y_raw, h->aux_raw, 1);
+}
+
+int cudahm_set_data(cudahm_t h, const double* y_host, const double* aux_host, int64_t n) {
+  return set_data_impl(h, y_host, aux_host, n, cudaMemcpyHostToDevice);
+}
+
+int cudahm_set_data_device(cudahm_t h, const double* y_dev, const double* aux_dev, int64_t n) {
+  return set_data_impl(h, y_dev, aux_dev, n, cudaMemcpyDeviceToDevice);
+}
+
+int cudahm_set_chi(cudahm_t h, const double* chi_host, int64_t n) {
+  if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
+  if (!h->data_set) return fail(CUDAHM_ESTATE, "set_chi before set_data");
+  if (h->sweeps != 0) return fail(CUDAHM_ESTATE, "set_chi after the chain has started");
+  if (!chi_host || n != h->n) return fail(CUDAHM_EINVAL, "bad chi argument");
+  CU(cudaSetDevice(h->cfg.device));
+  const size_t cnt = static_cast<size_t>(h->n) * h->d;
+  double* tmp = nullptr;
+  TRY(alloc_into(h, &tmp, cnt));
+  CU(cudaMemcpyAsync(tmp, chi_host, sizeof(double) * cnt, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemsetAsync(h->bad, 0, sizeof(int), h->stream));
+  CU(launch_check_chi(h->cfg.model, h->n, tmp, h->cfg.theta_init, h->bad, h->stream));
+  CU(cudaMemcpyAsync(h->host_err, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  if (*h->host_err) {
+    h->dfree(tmp);
+    return fail(CUDAHM_EINVAL, "%d latents are non-finite or off the support at theta", *h->host_err);
+  }
+  CU(cudaMemcpyAsync(h->chi, tmp, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->dfree(tmp);
+  return CUDAHM_OK;
+}
+
+int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
+  if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
+  if (!h->data_set) return fail(CUDAHM_ESTATE, "run before set_data");
+  if (n_burn < 0 || n_iter < 0) return fail(CUDAHM_EINVAL, "negative sweep counts");
+  if (n_iter > 0 && thin < 1) return fail(CUDAHM_EINVAL, "thin must be >= 1");
+  const long long total = n_burn + n_iter;
+  if (h->sweeps + total >= (1ll << 32) - 2) return fail(CUDAHM_EINVAL, "sweep counter would exceed 2^32");
+  CU(cudaSetDevice(h->cfg.device));
+  const long long nrows = (n_iter > 0) ? n_iter / thin : 0;
+  if (nrows > h->rows_cap) {
+    h->dfree(h->rows);
+    h->rows = nullptr;
+    TRY(alloc_into(h, &h->rows, static_cast<size_t>(nrows) * h->p));
+    h->rows_cap = nrows;
+  }
+  const long long T = std::min<long long>(h->cfg.trace_sweeps, total);
+  if (T > h->trace_cap_T) {
+    for (void* q : {(void*)h->tr_delta, (void*)h->tr_u, (void*)h->tr_acc, (void*)h->tr_thprop, (void*)h->tr_D,
+                    (void*)h->tr_logalpha, (void*)h->tr_ut, (void*)h->tr_tacc, (void*)h->tr_eb})
+      h->dfree(q);
+    const size_t tn = static_cast<size_t>(T) * h->n;
+    TRY(alloc_into(h, &h->tr_delta, tn));
+    TRY(alloc_into(h, &h->tr_u, tn));
+    TRY(alloc_into(h, &h->tr_acc, tn));
+    TRY(alloc_into(h, &h->tr_thprop, static_cast<size_t>(T) * h->p));
+    TRY(alloc_into(h, &h->tr_D, T));
+    TRY(alloc_into(h, &h->tr_logalpha, T));
+    TRY(alloc_into(h, &h->tr_ut, T));
+    TRY(alloc_into(h, &h->tr_tacc, T));
+    TRY(alloc_into(h, &h->tr_eb, T));
+    h->trace_cap_T = T;
+  }
+  CU(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+  CU(cudaEventRecord(h->ev0, h->stream));
+  if (h->cfg.model == CUDAHM_LF && !h->etabar_valid) {
+    // selection integral at the current theta, once per chain (kept on the device afterwards)
+    char* base = reinterpret_cast<char*>(h->chain);
+    TRY(compute_etabar_into(h, reinterpret_cast<const double*>(base + offsetof(ChainState, theta)),
+                            reinterpret_cast<double*>(base + offsetof(ChainState, etabar))));
+    h->etabar_valid = true;
+  }
+  SweepArgs a = base_args(h);
+  a.thin = thin;
+  a.keep_phase = 0;
+  a.trace_T = T;
+  a.tr_delta = h->tr_delta;
+  a.tr_u = h->tr_u;
+  a.tr_acc = h->tr_acc;
+  a.tr_thprop = h->tr_thprop;
+  a.tr_D = h->tr_D;
+  a.tr_logalpha = h->tr_logalpha;
+  a.tr_ut = h->tr_ut;
+  a.tr_tacc = h->tr_tacc;
+  a.tr_eb = h->tr_eb;
+  a.tab_U = h->tab_U;
+  a.tab_u = h->tab_u;
+  a.tab_eta = h->tab_eta;
+  long long off = 0, rows_done = 0;
+  while (off < total) {
+    const long long ns = std::min<long long>(kChunk, total - off);
+    CU(launch_tables(h->p, a.key0, a.key1, h->sweeps, ns, h->cfg.adapt_exponent, h->tab_U, h->tab_u, h->tab_eta,
+                     h->stream));
+    CU(cudaMemsetAsync(h->bar, 0, sizeof(unsigned int), h->stream));
+    a.k0 = h->sweeps;
+    a.ns = ns;
+    a.burn_left = n_burn - off;
+    a.trace_off = off;
+    a.rows = h->rows ? h->rows + rows_done * h->p : nullptr;
+    CU(launch_sweep(a, h->K, h->grid, h->block, h->stream));
+    // rows kept in [off, off + ns): post-burn indices q with (q + 1) % thin == 0
+    if (n_iter > 0) {
+      const long long q0 = std::max<long long>(0, off - n_burn), q1 = off + ns - n_burn;
+      if (q1 > q0) rows_done += q1 / thin - q0 / thin;
+    }
+    h->sweeps += ns;
+    off += ns;
+  }
+  CU(cudaEventRecord(h->ev1, h->stream));
+  int code = 0;
+  TRY(read_err(h, &code));
+  float ms = 0.f;
+  CU(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+  h->last_run_ms = ms;
+  if (code != 0) {
+    // device state was written back only by the launches that completed
+    ChainState cs;
+    CU(cudaMemcpy(&cs, h->chain, sizeof(cs), cudaMemcpyDeviceToHost));
+    h->sweeps = cs.sweeps;
+    h->rows_last = 0;
+    if (code == CUDAHM_ETIMEOUT) return fail(code, "a grid barrier wait exceeded its bound; run stopped");
+    if (code == CUDAHM_ENUMERIC) return fail(code, "NaN in a log-density; run stopped");
+    return fail(code, "device error %d", code);
+  }
+  h->rows_last = rows_done;
+  h->trace_T_last = T;
+  return CUDAHM_OK;
+}
+
+int cudahm_get_samples(cudahm_t h, double* theta_host, int64_t cap_rows, int64_t* rows_out) {
+  if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
+  const long long r = std::min<long long>(cap_rows, h->rows_last);
+  if (rows_out) *rows_out = h->rows_last;
+  if (r > 0) {
+    if (!theta_host) return fail(CUDAHM_EINVAL, "theta_host is NULL");
+    CU(cudaSetDevice(h->cfg.device));
+    CU(cudaMemcpyAsync(theta_host, h->rows, sizeof(double) * r * h->p, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  return CUDAHM_OK;
+}
+
+int cudahm_get_chi(cudahm_t h, double* chi_host, double* S_host) {
+  if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
+  CU(cudaSetDevice(h->cfg.device));
+  if (chi_host)
+    CU(cudaMemcpyAsync(chi_host, h->chi, sizeof(double) * h->n * h->d, cudaMemcpyDeviceToHost, h->stream));
+  if (S_host)
+    CU(cudaMemcpyAsync(S_host, h->S, sizeof(double) * h->n * h->d * h->d, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return CUDAHM_OK;
+}
+
+int cudahm_get_theta(cudahm_t h, double* theta_host, double* S_theta_host) {
+  if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
+  CU(cudaSetDevice(h->cfg.device));
+  ChainState cs;
+  CU(cudaMemcpyAsync(&cs, h->chain, sizeof(cs), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  if (theta_host) std::memcpy(theta_host, cs.theta, sizeof(double) * h->p);
+  if (S_theta_host) std::memcpy(S_theta_host, cs.S_theta, sizeof(double) * h->p * h->p);
+  return CUDAHM_OK;
+}
+
+int cudahm_get_stats(cudahm_t h, cudahm_stats* s) {
+  if (!h || !s) return fail(CUDAHM_EINVAL, "NULL argument");
+  CU(cudaSetDevice(h->cfg.device));
+  ChainState cs;
+  CU(cudaMemcpyAsync(&cs, h->chain, sizeof(cs), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  std::memset(s, 0, sizeof(*s));
+  s->sweeps = cs.sweeps;
+  s->member_accepts = cs.member_acc;
+  s->theta_accepts = cs.theta_acc;
+  s->rows = h->rows_last;
+  s->last_run_ms = h->last_run_ms;
+  s->etabar = cs.etabar;
+  s->grid_blocks = h->grid;
+  s->block_threads = h->block;
+  s->objects_per_thread = h->K;
+  return CUDAHM_OK;
+}
+
+int cudahm_eval_logdens(cudahm_t h, const double* theta_host, double* lp_host) {
+  if (!h || !theta_host || !lp_host) return fail(CUDAHM_EINVAL, "NULL argument");
+  if (!h->data_set) return fail(CUDAHM_ESTATE, "eval before set_data");
+  CU(cudaSetDevice(h->cfg.device));
+  double* out = nullptr;
+  TRY(alloc_into(h, &out, h->n));
+  CU(cudaMemcpyAsync(h->theta_dev, theta_host, sizeof(double) * h->p, cudaMemcpyHostToDevice, h->stream));
+  CU(launch_eval_logdens(h->cfg.model, h->n, h->y, h->aux, h->chi, h->theta_dev, h->mc, out, h->stream));
+  CU(cudaMemcpyAsync(lp_host, out, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->dfree(out);
+  return CUDAHM_OK;
+}
+
+int cudahm_eval_etabar(cudahm_t h, const double* theta_host, double* out) {
+  if (!h || !theta_host || !out) return fail(CUDAHM_EINVAL, "NULL argument");
+  if (h->cfg.model != CUDAHM_LF) return fail(CUDAHM_EINVAL, "etabar exists only for the LF model");
+  CU(cudaSetDevice(h->cfg.device));
+  CU(cudaMemcpyAsync(h->theta_dev, theta_host, sizeof(double) * h->p, cudaMemcpyHostToDevice, h->stream));
+  TRY(compute_etabar_into(h, h->theta_dev, h->eval_out));
+  CU(cudaMemcpyAsync(out, h->eval_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return CUDAHM_OK;
+}
+
+int cudahm_get_trace(cudahm_t h, double* delta, double* u, uint8_t* acc, double* theta_prop, double* D,
+                     double* logalpha, double* utheta, uint8_t* tacc, double* etabar_prop, int64_t* t_out) {
+  if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
+  const long long T = h->trace_T_last;
+  if (t_out) *t_out = T;
+  if (T == 0) return CUDAHM_OK;
+  CU(cudaSetDevice(h->cfg.device));
+  const size_t tn = static_cast<size_t>(T) * h->n;
+  auto cp = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    if (!dst) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream);
+  };
+  CU(cp(delta, h->tr_delta, sizeof(double) * tn));
+  CU(cp(u, h->tr_u, sizeof(double) * tn));
+  CU(cp(acc, h->tr_acc, tn));
+  CU(cp(theta_prop, h->tr_thprop, sizeof(double) * T * h->p));
+  CU(cp(D, h->tr_D, sizeof(double) * T));
+  CU(cp(logalpha, h->tr_logalpha, sizeof(double) * T));
+  CU(cp(utheta, h->tr_ut, sizeof(double) * T));
+  CU(cp(tacc, h->tr_tacc, T));
+  CU(cp(etabar_prop, h->tr_eb, sizeof(double) * T));
+  CU(cudaStreamSynchronize(h->stream));
+  return CUDAHM_OK;
+}
+
+// Checkpoint layout: header (8 x int64), ChainState, chi[n d], S[n d d].
+int cudahm_checkpoint(cudahm_t h, void* buf, size_t cap, size_t* used) {
+  if (!h || !used) return fail(CUDAHM_EINVAL, "NULL argument");
+  const size_t nchi = static_cast<size_t>(h->n) * h->d, nS = static_cast<size_t>(h->n) * h->d * h->d;
+  const size_t need = 8 * sizeof(int64_t) + sizeof(ChainState) + sizeof(double) * (nchi + nS);
+  *used = need;
+  if (!buf) return CUDAHM_OK;
+  if (cap < need) return fail(CUDAHM_EINVAL, "checkpoint buffer too small: need %zu bytes", need);
+  CU(cudaSetDevice(h->cfg.device));
+  int64_t hdr[8] = {0x4d48414455434f4bll, 1, h->cfg.model, h->n, h->d, h->p, static_cast<int64_t>(h->cfg.seed),
+                    h->data_set ? 1 : 0};
+  char* c = static_cast<char*>(buf);
+  std::memcpy(c, hdr, sizeof(hdr));
+  c += sizeof(hdr);
+  CU(cudaMemcpyAsync(c, h->chain, sizeof(ChainState), cudaMemcpyDeviceToHost, h->stream));
+  c += sizeof(ChainState);
+  CU(cudaMemcpyAsync(c, h->chi, sizeof(double) * nchi, cudaMemcpyDeviceToHost, h->stream));
+  c += sizeof(double) * nchi;
+  CU(cudaMemcpyAsync(c, h->S, sizeof(double) * nS, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return CUDAHM_OK;
+}
+
+int cudahm_restore(cudahm_t h, const void* buf, size_t size) {
+  if (!h || !buf) return fail(CUDAHM_EINVAL, "NULL argument");
+  if (!h->data_set) return fail(CUDAHM_ESTATE, "restore needs set_data first");
+  const size_t nchi = static_cast<size_t>(h->n) * h->d, nS = static_cast<size_t>(h->n) * h->d * h->d;
+  const size_t need = 8 * sizeof(int64_t) + sizeof(ChainState) + sizeof(double) * (nchi + nS);
+  if (size < need) return fail(CUDAHM_EINVAL, "checkpoint buffer too small");
+  int64_t hdr[8];
+  const char* c = static_cast<const char*>(buf);
+  std::memcpy(hdr, c, sizeof(hdr));
+  if (hdr[0] != 0x4d48414455434f4bll || hdr[1] != 1 || hdr[2] != h->cfg.model || hdr[3] != h->n || hdr[4] != h->d ||
+      hdr[5] != h->p || hdr[6] != static_cast<int64_t>(h->cfg.seed))
+    return fail(CUDAHM_EINVAL, "checkpoint does not match this handle's configuration");
+  c += sizeof(hdr);
+  ChainState cs;
+  std::memcpy(&cs, c, sizeof(cs));
+  CU(cudaSetDevice(h->cfg.device));
+  CU(cudaMemcpyAsync(h->chain, c, sizeof(ChainState), cudaMemcpyHostToDevice, h->stream));
+  c += sizeof(ChainState);
+  CU(cudaMemcpyAsync(h->chi, c, sizeof(double) * nchi, cudaMemcpyHostToDevice, h->stream));
+  c += sizeof(double) * nchi;
+  CU(cudaMemcpyAsync(h->S, c, sizeof(double) * nS, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->sweeps = cs.sweeps;
+  h->rows_last = 0;
+  h->etabar_valid = (cs.etabar != 0.0);
+  return CUDAHM_OK;
+}
+
+}  // extern "C"

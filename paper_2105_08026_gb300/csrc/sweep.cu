@@ -1,0 +1,771 @@
+// Persistent Metropolis-within-Gibbs sweep kernel and its set-up kernels (FP64).
+//
+// One cooperative launch runs `ns` sweeps. Per sweep (Sec. 2.1, eqs. psi_sampling then
+// theta_sampling; Sec. 2.2 for RAM):
+//   a0  theta' = theta + S_theta U_theta           (block-redundant, from a precomputed table)
+//   a1  every member: Y = chi + S z                 (Philox4x32-10 -> Box-Muller)
+//   a2  accept iff u < exp(lp(Y) - lp(chi))         (lp = log l_i + log f(.;theta))
+//   a3  RAM factor S <- S sqrt(1 + eta (alpha - alpha_*))   (d = 1 closed form of Sec. 2.2 step 3)
+//   a4  d_i = log f(chi_i;theta') - log f(chi_i;theta) into an exact fixed-point sum
+//   a6  LF: etabar(theta') pairs of the 2-D rule into a second exact sum (Sec. 4.2, eq. epdf)
+//   a5  block partials -> bounded grid barrier -> every block adds all partials
+//   a7  every block takes the same theta accept decision, RAM-updates S_theta
+//   a8  block 0 records the kept theta row
+// Each thread keeps its K members (latent, RAM factor, cached e^chi and log l) in
+// registers for the whole launch; data are read once at launch start.
+#include <cmath>
+#include <cstdint>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace chm {
+
+// ----------------------------------------------------------------- models ----
+// Per-theta constants a0..a3 (computed once per theta by one thread).
+struct ThetaC {
+  double a0, a1, a2, a3;
+};
+
+struct NN1 {
+  // a0 = mu, a1 = 1/(2 tau^2)
+  static constexpr bool kExp = false;
+  __device__ static ThetaC consts(const double* th) {
+    ThetaC c;
+    c.a0 = th[0];
+    c.a1 = 0.5 * exp(-2.0 * th[1]);
+    c.a2 = 0.0;
+    c.a3 = 0.0;
+    return c;
+  }
+  __device__ static bool support(double, const ThetaC&) { return true; }
+  __device__ static double logf(double chi, double, const ThetaC& c) {
+    const double r = chi - c.a0;
+    return -c.a1 * (r * r);
+  }
+  // y = y_i, aux = 1/sigma_i^2
+  __device__ static double loglike(double chi, double, double y, double aux, const ModelConsts&) {
+    const double r = y - chi;
+    return -0.5 * aux * (r * r);
+  }
+  __device__ static double cterm(const double* th) { return -th[1]; }
+  __device__ static double logprior(const double* th, const ModelConsts& mc) {
+    return (th[1] >= mc.lo && th[1] <= mc.hi) ? 0.0 : -INFINITY;
+  }
+};
+
+struct LF {
+  // a0 = beta + 1, a1 = ln L*, a2 = 1/L*, a3 = ln L_low
+  static constexpr bool kExp = true;
+  __device__ static ThetaC consts(const double* th) {
+    ThetaC c;
+    c.a0 = th[0] + 1.0;
+    c.a1 = th[1];
+    c.a2 = exp(-th[1]);
+    c.a3 = th[2];
+    return c;
+  }
+  __device__ static bool support(double chi, const ThetaC& c) { return chi > c.a3; }
+  __device__ static double logf(double chi, double echi, const ThetaC& c) {
+    return c.a0 * (chi - c.a1) - echi * c.a2;
+  }
+  // y = Fhat_i, aux = q_i = 1/(4 pi r_i^2)
+  __device__ static double loglike(double, double echi, double y, double aux, const ModelConsts& mc) {
+    const double r = y - echi * aux;
+    return -(r * r) * mc.inv2sig2;
+  }
+  __device__ static double cterm(const double*) { return 0.0; }
+  __device__ static double logprior(const double* th, const ModelConsts&) {
+    if (!(th[0] > -2.0 && th[0] < 0.0)) return -INFINITY;
+    if (!(th[2] < th[1])) return -INFINITY;
+    return -log(1.0 + th[0] * th[0]) + th[2];
+  }
+};
+
+// ----------------------------------------------------- theta RAM update -------
+// Lower-triangular L (p x p, row-major) with L' L'^T = L (I + c U U^T/|U|^2) L^T,
+// c = eta (alpha - alpha_*): a rank-one Cholesky update (c > 0) or downdate (c < 0)
+// with v = L U sqrt(|c|)/|U|.
+__device__ void ram_update_theta(int p, double* L, const double* U, double alpha, double astar, double eta) {
+  const double c = eta * (alpha - astar);
+  if (c == 0.0) return;
+  double uu = 0.0;
+  for (int j = 0; j < p; ++j) uu = fma(U[j], U[j], uu);
+  const double sc = sqrt(fabs(c) / uu);
+  const double sg = c > 0.0 ? 1.0 : -1.0;
+  double x[kMaxP];
+  for (int a = 0; a < p; ++a) {
+    double t = 0.0;
+    for (int b = 0; b <= a; ++b) t = fma(L[a * p + b], U[b], t);
+    x[a] = t * sc;
+  }
+  for (int k = 0; k < p; ++k) {
+    const double Lkk = L[k * p + k];
+    const double r = sqrt(fma(sg * x[k], x[k], Lkk * Lkk));
+    const double cc = r / Lkk, ss = x[k] / Lkk;
+    L[k * p + k] = r;
+    for (int i = k + 1; i < p; ++i) {
+      const double li = (fma(sg * ss, x[i], L[i * p + k])) / cc;
+      L[i * p + k] = li;
+      x[i] = fma(cc, x[i], -ss * li);
+    }
+  }
+}
+
+// ------------------------------------------------------------ LF rule --------
+// Outer node values for rows j in [j0, j0 + nrows): L_j = e^t_j and
+// G_j = (half-width) w_j g(e^t_j) e^t_j on t in [ln L_low, ln L* + ln_upper].
+__device__ __forceinline__ void lf_rows(const ThetaC& tc, const SweepArgs& a, long long j0, int nrows, double* sL,
+                                        double* sG) {
+  const double lo = tc.a3, hi = tc.a1 + a.mc.ln_upper;
+  const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+  for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+    const long long j = j0 + r;
+    if (j >= a.nL) break;
+    const double t = fma(half, __ldg(a.xL + j), mid);
+    const double x = t - tc.a1;
+    sL[r] = exp(t);
+    sG[r] = half * __ldg(a.wL + j) * exp(fma(tc.a0, x, -exp(x)));
+  }
+}
+
+// Pairs [pb0, pb1) of the flattened (outer j, inner k) rule; this thread takes every
+// blockDim-th pair. Each term G_j W_k Phi((L_j q_k - F_th)/sigma_F) is added exactly.
+__device__ __forceinline__ void lf_pairs(const SweepArgs& a, unsigned int pb0, unsigned int pb1, long long j0,
+                                         const double* sL, const double* sG, Xacc& xe, XFlags& fe) {
+  const unsigned int nr = static_cast<unsigned int>(a.nr);
+  const double mcth = -a.mc.cth;
+  for (unsigned int idx = pb0 + threadIdx.x; idx < pb1; idx += blockDim.x) {
+    const unsigned int j = idx / nr;
+    const unsigned int k = idx - j * nr;
+    const int r = static_cast<int>(static_cast<long long>(j) - j0);
+    const double x = fma(sL[r], __ldg(a.qs + k), mcth);
+    // Phi(x) = erfc(-x/sqrt 2)/2; above x = 8.5 erfc(-x/sqrt 2) rounds to 2 exactly
+    const double phi = (x > 8.5) ? 1.0 : 0.5 * erfc(-x * 0.70710678118654752440);
+    xacc_add_double(xe, sG[r] * (__ldg(a.Wr + k) * phi), fe);
+  }
+}
+
+__device__ __forceinline__ void pair_range(long long P, int b, int B, unsigned int& pb0, unsigned int& pb1) {
+  pb0 = static_cast<unsigned int>((P * b) / B);
+  pb1 = static_cast<unsigned int>((P * (b + 1)) / B);
+}
+
+// ------------------------------------------------- block reduce helpers ------
+struct BlockRed {
+  Xacc d[32];
+  Xacc e[32];
+  unsigned int f[32][4];
+};
+
+__device__ __forceinline__ void warp_reduce(Xacc& d, Xacc& e, unsigned int f[4]) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    Xacc t = xacc_shfl_xor(d, m);
+    xacc_add(d, t);
+    t = xacc_shfl_xor(e, m);
+    xacc_add(e, t);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) f[q] = __reduce_add_sync(0xffffffffu, f[q]);
+}
+
+// ---------------------------------------------------------------- kernel -----
+template <class M, int K>
+__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
+  extern __shared__ double s_rows[];  // [2][rows_smem]: L_j then G_j
+  __shared__ double s_theta[kMaxP], s_thp[kMaxP], s_Sth[kMaxP * kMaxP];
+  __shared__ ThetaC s_tc, s_tcp;
+  __shared__ double s_etabar, s_lpri, s_lpri_new;
+  __shared__ int s_prior_ok, s_stop;
+  __shared__ long long s_rows_written, s_tacc;
+  __shared__ BlockRed s_red;
+
+  const int tid = threadIdx.x;
+  const int p = a.p;
+  const long long G = static_cast<long long>(gridDim.x) * blockDim.x;
+  const long long gtid = static_cast<long long>(blockIdx.x) * blockDim.x + tid;
+  const bool skip_me = (a.skip_cta == static_cast<int>(blockIdx.x));
+
+  if (tid == 0) {
+    for (int q = 0; q < p; ++q) s_theta[q] = a.chain->theta[q];
+    for (int q = 0; q < p * p; ++q) s_Sth[q] = a.chain->S_theta[q];
+    s_etabar = a.chain->etabar;
+    s_tc = M::consts(s_theta);
+    s_lpri = M::logprior(s_theta, a.mc);
+    s_rows_written = 0;
+    s_tacc = 0;
+    s_stop = 0;
+  }
+
+  // members of this thread: i = gtid + m G
+  double chi[K], S[K], echi[K], ll[K], yv[K], av[K];
+#pragma unroll
+  for (int m = 0; m < K; ++m) {
+    const long long i = gtid + m * G;
+    if (i < a.n) {
+      chi[m] = a.chi[i];
+      S[m] = a.S[i];
+      yv[m] = a.y[i];
+      av[m] = a.aux[i];
+      echi[m] = M::kExp ? exp(chi[m]) : 0.0;
+      ll[m] = M::loglike(chi[m], echi[m], yv[m], av[m], a.mc);
+    } else {
+      chi[m] = S[m] = echi[m] = ll[m] = yv[m] = av[m] = 0.0;
+    }
+  }
+  unsigned int member_acc = 0;
+
+  // LF rule share of this block
+  const bool is_lf = (a.model == CUDAHM_LF);
+  const long long P = static_cast<long long>(a.nL) * a.nr;
+  unsigned int pb0 = 0, pb1 = 0;
+  long long j0 = 0;
+  int nrows = 0;
+  if (is_lf) {
+    pair_range(P, blockIdx.x, gridDim.x, pb0, pb1);
+    if (pb1 > pb0) {
+      j0 = pb0 / a.nr;
+      nrows = static_cast<int>((pb1 - 1) / a.nr - j0 + 1);
+    }
+  }
+  double* sL = s_rows;
+  double* sG = s_rows + a.rows_smem;
+  __syncthreads();
+
+  for (long long s = 0; s < a.ns; ++s) {
+    const uint32_t k = static_cast<uint32_t>(a.k0 + s + 1);
+    const double eta = __ldg(a.tab_eta + s);
+    // a0: theta proposal (same arithmetic in every block)
+    if (tid == 0) {
+      for (int q = 0; q < p; ++q) {
+        double t = s_theta[q];
+        for (int b = 0; b <= q; ++b) t = fma(s_Sth[q * p + b], __ldg(a.tab_U + s * p + b), t);
+        s_thp[q] = t;
+      }
+      s_lpri_new = M::logprior(s_thp, a.mc);
+      s_prior_ok = (s_lpri_new != -INFINITY);
+      s_tcp = M::consts(s_thp);
+    }
+    __syncthreads();
+    const ThetaC tc = s_tc, tcp = s_tcp;
+    const bool prior_ok = s_prior_ok != 0;
+    if (is_lf && prior_ok) lf_rows(tcp, a, j0, nrows, sL, sG);
+
+    const bool trace = (a.trace_off + s) < a.trace_T;
+    Xacc xd, xe;
+    xacc_zero(xd);
+    xacc_zero(xe);
+    XFlags fd = {0u, 0u, 0u}, fe = {0u, 0u, 0u};
+    unsigned int member_nan = 0, neg_big = 0, pos_big = 0;
+
+    // a1-a4: member RAM steps under theta, then the theta' partial
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+      const long long i = gtid + m * G;
+      if (i < a.n) {
+        const uint4 w0 = philox4x32_10(make_uint4(0u, 0u, static_cast<uint32_t>(i), k), a.key0, a.key1);
+        const uint4 w1 = philox4x32_10(make_uint4(1u, 0u, static_cast<uint32_t>(i), k), a.key0, a.key1);
+        const double ua = uniform53(w0.x, w0.y), ub = uniform53(w0.z, w0.w);
+        const double z = sqrt(-2.0 * log(ua)) * cospi(2.0 * ub);
+        const double u = uniform53(w1.x, w1.y);
+        const double Y = fma(S[m], z, chi[m]);
+        double delta, eY = 0.0, llY = 0.0;
+        if (!M::support(Y, tc)) {
+          delta = -INFINITY;
+        } else {
+          eY = M::kExp ? exp(Y) : 0.0;
+          llY = M::loglike(Y, eY, yv[m], av[m], a.mc);
+          const double lpY = llY + M::logf(Y, eY, tc);
+          const double lpX = ll[m] + M::logf(chi[m], echi[m], tc);
+          delta = lpY - lpX;
+        }
+        const double alpha = (delta >= 0.0) ? 1.0 : exp(delta);
+        const bool acc = (delta >= 0.0) || (u < alpha);
+        if (delta != delta) member_nan++;
+        if (acc) {
+          chi[m] = Y;
+          echi[m] = eY;
+          ll[m] = llY;
+          member_acc++;
+        }
+        S[m] *= sqrt(fma(eta, alpha - a.astar, 1.0));
+        if (trace) {
+          const long long o = (a.trace_off + s) * a.n + i;
+          a.tr_delta[o] = delta;
+          a.tr_u[o] = u;
+          a.tr_acc[o] = acc ? 1 : 0;
+        }
+        if (prior_ok) {
+          const double dn = M::support(chi[m], tcp) ? M::logf(chi[m], echi[m], tcp) - M::logf(chi[m], echi[m], tc)
+                                                   : -INFINITY;
+          if (dn <= -0x1p94) neg_big++;       // off the support of theta' (-inf) or hopeless
+          else if (dn >= 0x1p94) pos_big++;   // outside the fixed-point range (+inf included)
+          else xacc_add_double(xd, dn, fd);   // counts NaN in fd.nan
+        }
+      }
+    }
+    // a6: LF selection integral at theta'
+    if (is_lf && prior_ok) {
+      __syncthreads();  // rows ready
+      lf_pairs(a, pb0, pb1, j0, sL, sG, xe, fe);
+    }
+
+    // a5: block partial
+    {
+      // f[0]: d_i <= -2^94 (reject), f[1]: NaN anywhere (error), f[2]: d_i >= 2^94, f[3]: member NaN
+      unsigned int f[4] = {neg_big, fd.nan + fe.nan + fe.big + member_nan, pos_big, member_nan};
+      warp_reduce(xd, xe, f);
+      const int lane = tid & 31, wid = tid >> 5;
+      if (lane == 0) {
+        s_red.d[wid] = xd;
+        s_red.e[wid] = xe;
+        for (int q = 0; q < 4; ++q) s_red.f[wid][q] = f[q];
+      }
+      __syncthreads();
+      if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        Xacc bd, be;
+        unsigned int bf[4] = {0u, 0u, 0u, 0u};
+        xacc_zero(bd);
+        xacc_zero(be);
+        if (lane < nw) {
+          bd = s_red.d[lane];
+          be = s_red.e[lane];
+          for (int q = 0; q < 4; ++q) bf[q] = s_red.f[lane][q];
+        }
+        warp_reduce(bd, be, bf);
+        if (lane == 0) {
+          unsigned long long* dst = a.partials + ((s & 1) * gridDim.x + blockIdx.x) * kPartWords;
+          __stcg(dst + 0, bd.w0);
+          __stcg(dst + 1, bd.w1);
+          __stcg(dst + 2, bd.w2);
+          __stcg(dst + 3, be.w0);
+          __stcg(dst + 4, be.w1);
+          __stcg(dst + 5, be.w2);
+          __stcg(dst + 6, (static_cast<unsigned long long>(bf[1]) << 32) | bf[0]);
+          __stcg(dst + 7, (static_cast<unsigned long long>(bf[3]) << 32) | bf[2]);
+        }
+      }
+    }
+    if (!grid_barrier(a.bar, static_cast<unsigned int>(s), a.err, a.timeout_ns, skip_me)) return;
+
+    // a7: every block sums all partials and takes the same decision
+    if (tid < 32) {
+      Xacc D, E;
+      xacc_zero(D);
+      xacc_zero(E);
+      unsigned int f[4] = {0u, 0u, 0u, 0u};
+      for (int b = tid; b < static_cast<int>(gridDim.x); b += 32) {
+        const unsigned long long* src = a.partials + ((s & 1) * gridDim.x + b) * kPartWords;
+        Xacc t;
+        t.w0 = __ldcg(src + 0);
+        t.w1 = __ldcg(src + 1);
+        t.w2 = __ldcg(src + 2);
+        xacc_add(D, t);
+        t.w0 = __ldcg(src + 3);
+        t.w1 = __ldcg(src + 4);
+        t.w2 = __ldcg(src + 5);
+        xacc_add(E, t);
+        const unsigned long long f01 = __ldcg(src + 6), f23 = __ldcg(src + 7);
+        f[0] += static_cast<unsigned int>(f01);
+        f[1] += static_cast<unsigned int>(f01 >> 32);
+        f[2] += static_cast<unsigned int>(f23);
+        f[3] += static_cast<unsigned int>(f23 >> 32);
+      }
+      warp_reduce(D, E, f);
+      if (tid == 0) {
+        const long long sg = a.trace_off + s;  // sweep index within this run
+        if (f[1] != 0u) {
+          atomicCAS(a.err, 0, CUDAHM_ENUMERIC);
+          s_stop = 1;
+        } else {
+          double logalpha, Drec, eb_new = 0.0;
+          if (!prior_ok) {
+            logalpha = -INFINITY;
+            Drec = 0.0;
+          } else if (f[0] != 0u) {  // a member off the proposal's support (or d <= -2^94)
+            logalpha = -INFINITY;
+            Drec = -INFINITY;
+          } else if (f[2] != 0u) {  // only huge positive differences remain
+            logalpha = INFINITY;
+            Drec = INFINITY;
+          } else {
+            Drec = xacc_to_double(D);
+            const double nn = static_cast<double>(a.n);
+            logalpha = Drec + nn * (M::cterm(s_thp) - M::cterm(s_theta)) + s_lpri_new - s_lpri;
+            if (is_lf) {
+              eb_new = xacc_to_double(E);
+              logalpha -= nn * (log(eb_new) - log(s_etabar));
+            }
+          }
+          const double ut = __ldg(a.tab_u + s);
+          const double alpha = (logalpha >= 0.0) ? 1.0 : exp(logalpha);
+          const bool acc = (logalpha >= 0.0) || (ut < alpha);
+          if (blockIdx.x == 0 && sg < a.trace_T) {
+            for (int q = 0; q < p; ++q) a.tr_thprop[sg * p + q] = s_thp[q];
+            a.tr_D[sg] = Drec;
+            a.tr_logalpha[sg] = logalpha;
+            a.tr_ut[sg] = ut;
+            a.tr_tacc[sg] = acc ? 1 : 0;
+            a.tr_eb[sg] = eb_new;
+          }
+          if (acc) {
+            for (int q = 0; q < p; ++q) s_theta[q] = s_thp[q];
+            s_tc = s_tcp;
+            s_lpri = s_lpri_new;
+            if (is_lf) s_etabar = eb_new;
+            s_tacc++;
+          }
+          if (a.adapt_theta) ram_update_theta(p, s_Sth, a.tab_U + s * p, alpha, a.astar_theta, eta);
+          // a8: record kept sweeps
+          const long long post = s - a.burn_left;
+          if (post >= 0 && a.thin > 0 && ((a.keep_phase + post + 1) % a.thin) == 0) {
+            if (blockIdx.x == 0)
+              for (int q = 0; q < p; ++q) a.rows[s_rows_written * p + q] = s_theta[q];
+            s_rows_written++;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (s_stop) return;
+  }
+
+  // write back (only reached when every sweep succeeded)
+#pragma unroll
+  for (int m = 0; m < K; ++m) {
+    const long long i = gtid + m * G;
+    if (i < a.n) {
+      a.chi[i] = chi[m];
+      a.S[i] = S[m];
+    }
+  }
+  __shared__ unsigned int s_macc;
+  if (tid == 0) s_macc = 0;
+  __syncthreads();
+  atomicAdd(&s_macc, member_acc);
+  __syncthreads();
+  if (tid == 0) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(&a.chain->member_acc), static_cast<unsigned long long>(s_macc));
+    if (blockIdx.x == 0) {
+      for (int q = 0; q < p; ++q) a.chain->theta[q] = s_theta[q];
+      for (int q = 0; q < p * p; ++q) a.chain->S_theta[q] = s_Sth[q];
+      a.chain->etabar = s_etabar;
+      a.chain->sweeps = a.k0 + a.ns;
+      a.chain->theta_acc += s_tacc;
+      a.chain->rows = s_rows_written;
+    }
+  }
+}
+
+template <class M>
+static cudaError_t launch_model(const SweepArgs& a, int K, int grid, int block, cudaStream_t st) {
+  void* args[] = {const_cast<SweepArgs*>(&a)};
+  const size_t smem = 2 * sizeof(double) * static_cast<size_t>(a.rows_smem);
+  const void* fn;
+  switch (K) {
+    case 1: fn = reinterpret_cast<const void*>(&sweep_kernel<M, 1>); break;
+    case 2: fn = reinterpret_cast<const void*>(&sweep_kernel<M, 2>); break;
+    case 4: fn = reinterpret_cast<const void*>(&sweep_kernel<M, 4>); break;
+    case 8: fn = reinterpret_cast<const void*>(&sweep_kernel<M, 8>); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
+}
+
+cudaError_t launch_sweep(const SweepArgs& a, int K, int grid, int block, cudaStream_t st) {
+  if (a.model == CUDAHM_NN1) return launch_model<NN1>(a, K, grid, block, st);
+  if (a.model == CUDAHM_LF) return launch_model<LF>(a, K, grid, block, st);
+  return cudaErrorInvalidValue;
+}
+
+template <class M>
+static cudaError_t occ_model(int K, int block, int smem, int* bps) {
+  const void* fn;
+  switch (K) {
+    case 1: fn = reinterpret_cast<const void*>(&sweep_kernel<M, 1>); break;
+    case 2: fn = reinterpret_cast<const void*>(&sweep_kernel<M, 2>); break;
+    case 4: fn = reinterpret_cast<const void*>(&sweep_kernel<M, 4>); break;
+    case 8: fn = reinterpret_cast<const void*>(&sweep_kernel<M, 8>); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fn, block, smem);
+}
+
+cudaError_t sweep_occupancy(int model, int K, int block, int smem_bytes, int* blocks_per_sm) {
+  if (model == CUDAHM_NN1) return occ_model<NN1>(K, block, smem_bytes, blocks_per_sm);
+  if (model == CUDAHM_LF) return occ_model<LF>(K, block, smem_bytes, blocks_per_sm);
+  return cudaErrorInvalidValue;
+}
+
+// --------------------------------------------------------- set-up kernels ----
+// Derived per-member data, validation and (optionally) the default start.
+__global__ void prepare_kernel(int model, long long n, const double* y_raw, const double* aux_raw, double* y,
+                               double* aux, double* chi, double* S, ModelConsts mc, double th0, double th1,
+                               double th2, int* bad, int set_default_chi) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double yr = y_raw[i], ar = aux_raw[i];
+  bool ok = isfinite(yr) && isfinite(ar) && ar > 0.0;
+  if (model == CUDAHM_NN1) {
+    y[i] = yr;
+    aux[i] = 1.0 / (ar * ar);
+    if (set_default_chi) chi[i] = yr;
+  } else {
+    y[i] = yr;
+    aux[i] = 1.0 / (4.0 * 3.14159265358979323846 * ar * ar);
+    ok = ok && aux[i] > 0.0 && isfinite(aux[i]);
+    if (set_default_chi) {
+      double c = log(4.0 * 3.14159265358979323846 * ar * ar * fmax(yr, mc.F_th));
+      const double floor_c = th2 + 1e-6;
+      chi[i] = (c > th2) ? c : floor_c;
+    }
+  }
+  if (set_default_chi) S[i] = mc.chi_init_scale;
+  if (!ok) atomicAdd(bad, 1);
+}
+
+cudaError_t launch_prepare(int model, long long n, const double* y_raw, const double* aux_raw, double* y, double* aux,
+                           double* chi, double* S, const ModelConsts& mc, const double* theta, int* bad,
+                           int set_default_chi, cudaStream_t st) {
+  const int blk = 256;
+  const long long grid = (n + blk - 1) / blk;
+  prepare_kernel<<<static_cast<unsigned int>(grid), blk, 0, st>>>(model, n, y_raw, aux_raw, y, aux, chi, S, mc,
+                                                                  theta[0], theta[1], theta[2], bad,
+                                                                  set_default_chi);
+  return cudaGetLastError();
+}
+
+// Latents must lie in the support at theta (LF: chi > ln L_low) and be finite.
+__global__ void check_chi_kernel(int model, long long n, const double* chi, double lnlow, int* bad) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double c = chi[i];
+  bool ok = isfinite(c);
+  if (model == CUDAHM_LF) ok = ok && (c > lnlow);
+  if (!ok) atomicAdd(bad, 1);
+}
+
+cudaError_t launch_check_chi(int model, long long n, const double* chi, const double* theta, int* bad,
+                             cudaStream_t st) {
+  const int blk = 256;
+  const long long grid = (n + blk - 1) / blk;
+  check_chi_kernel<<<static_cast<unsigned int>(grid), blk, 0, st>>>(model, n, chi,
+                                                                     model == CUDAHM_LF ? theta[2] : 0.0, bad);
+  return cudaGetLastError();
+}
+
+// Gauss-Legendre rule on [-1, 1], one thread per node: Newton's method on P_n from the
+// asymptotic first guess x ~ (1 - 1/(8n^2) + 1/(8n^3)) cos(pi (4i+3)/(4n+2)), with P_n and
+// P_{n-1} by the three-term recurrence; w = 2 (1 - x^2)/(n P_{n-1}(x))^2 (which equals
+// 2/((1 - x^2) P_n'(x)^2) at a root). Nodes ascend.
+__global__ void gauss_legendre_kernel(int n, double* x, double* w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (n + 1) / 2) return;
+  const double pi = 3.14159265358979323846;
+  const double nd = static_cast<double>(n);
+  double z = (1.0 - 1.0 / (8.0 * nd * nd) + 1.0 / (8.0 * nd * nd * nd)) * cos(pi * (4.0 * i + 3.0) / (4.0 * nd + 2.0));
+  double pn = 0.0, pm = 0.0;
+  for (int it = 0; it < 12; ++it) {
+    double p0 = 1.0, p1 = z;
+    for (int m = 2; m <= n; ++m) {
+      const double p2 = ((2.0 * m - 1.0) * z * p1 - (m - 1.0) * p0) / m;
+      p0 = p1;
+      p1 = p2;
+    }
+    if (n == 1) p0 = 1.0;
+    pn = p1;
+    pm = p0;
+    const double omz2 = (1.0 - z) * (1.0 + z);
+    const double dp = nd * (pm - z * pn) / omz2;  // P_n'
+    const double dz = pn / dp;
+    z -= dz;
+    if (fabs(dz) <= 1e-17) break;
+  }
+  {
+    double p0 = 1.0, p1 = z;
+    for (int m = 2; m <= n; ++m) {
+      const double p2 = ((2.0 * m - 1.0) * z * p1 - (m - 1.0) * p0) / m;
+      p0 = p1;
+      p1 = p2;
+    }
+    if (n == 1) p0 = 1.0;
+    pm = p0;
+  }
+  const double omz2 = (1.0 - z) * (1.0 + z);
+  const double wi = (n == 1) ? 2.0 : 2.0 * omz2 / ((nd * pm) * (nd * pm));
+  x[n - 1 - i] = z;
+  x[i] = -z;
+  w[i] = wi;
+  w[n - 1 - i] = wi;
+  if ((n & 1) && i == n / 2) x[i] = 0.0;
+}
+
+cudaError_t launch_gauss_legendre(int n, double* x, double* w, cudaStream_t st) {
+  const int half = (n + 1) / 2;
+  gauss_legendre_kernel<<<(half + 127) / 128, 128, 0, st>>>(n, x, w);
+  return cudaGetLastError();
+}
+
+// Inner-rule tables: r_k = r_max (x_k + 1)/2, qs_k = 1/(4 pi r_k^2 sigma_F),
+// W_k = (r_max/2) w_k 3 r_k^2/r_max^3 (distance density ~ r^2 on [0, r_max], normalised).
+__global__ void lf_inner_kernel(int nr, const double* xr, const double* wr, double rmax, double sigF, double* qs,
+                                double* Wr) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nr) return;
+  const double r = 0.5 * rmax * (xr[k] + 1.0);
+  qs[k] = 1.0 / (4.0 * 3.14159265358979323846 * r * r) / sigF;
+  Wr[k] = 0.5 * rmax * wr[k] * 3.0 * r * r / (rmax * rmax * rmax);
+}
+
+cudaError_t launch_lf_inner(int nr, const double* xr, const double* wr, double r_max, double sigma_F, double* qs,
+                            double* Wr, cudaStream_t st) {
+  lf_inner_kernel<<<(nr + 127) / 128, 128, 0, st>>>(nr, xr, wr, r_max, sigma_F, qs, Wr);
+  return cudaGetLastError();
+}
+
+// Per-sweep theta tables: p normals (Philox stream 1, member index 0, sweep k; block j gives
+// normals 2j, 2j+1), the accept uniform (first uniform of block ceil(p/2)), eta = (k+1)^-gamma.
+__global__ void tables_kernel(int p, uint32_t key0, uint32_t key1, long long k0, long long ns, double gamma,
+                              double* U, double* u, double* eta) {
+  const long long s = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  const uint32_t k = static_cast<uint32_t>(k0 + s + 1);
+  const int nblk = (p + 1) / 2;
+  for (int j = 0; j < nblk; ++j) {
+    const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(j), 1u, 0u, k), key0, key1);
+    const double ua = uniform53(w.x, w.y), ub = uniform53(w.z, w.w);
+    const double rad = sqrt(-2.0 * log(ua));
+    double sn, cs;
+    sincospi(2.0 * ub, &sn, &cs);
+    U[s * p + 2 * j] = rad * cs;
+    if (2 * j + 1 < p) U[s * p + 2 * j + 1] = rad * sn;
+  }
+  const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(nblk), 1u, 0u, k), key0, key1);
+  u[s] = uniform53(w.x, w.y);
+  eta[s] = pow(static_cast<double>(k) + 1.0, -gamma);
+}
+
+cudaError_t launch_tables(int p, uint32_t key0, uint32_t key1, long long k0, long long ns, double gamma, double* U,
+                          double* u, double* eta, cudaStream_t st) {
+  const int blk = 128;
+  tables_kernel<<<static_cast<unsigned int>((ns + blk - 1) / blk), blk, 0, st>>>(p, key0, key1, k0, ns, gamma, U, u,
+                                                                                 eta);
+  return cudaGetLastError();
+}
+
+// Per-member log target at theta (read from device memory).
+template <class M>
+__global__ void eval_logdens_kernel(long long n, const double* y, const double* aux, const double* chi,
+                                    const double* theta, ModelConsts mc, double* out) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double th[kMaxP];
+  for (int q = 0; q < 3; ++q) th[q] = theta[q];
+  const ThetaC tc = M::consts(th);
+  const double c = chi[i];
+  if (!M::support(c, tc)) {
+    out[i] = -INFINITY;
+    return;
+  }
+  const double e = M::kExp ? exp(c) : 0.0;
+  out[i] = M::loglike(c, e, y[i], aux[i], mc) + M::logf(c, e, tc);
+}
+
+cudaError_t launch_eval_logdens(int model, long long n, const double* y, const double* aux, const double* chi,
+                                const double* theta_dev, const ModelConsts& mc, double* out, cudaStream_t st) {
+  const int blk = 256;
+  const unsigned int grid = static_cast<unsigned int>((n + blk - 1) / blk);
+  if (model == CUDAHM_NN1) eval_logdens_kernel<NN1><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, out);
+  else if (model == CUDAHM_LF) eval_logdens_kernel<LF><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, out);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// Stand-alone selection integral: same pair split and exact sum as the sweep kernel, so
+// the value is bit-identical to the one the sweep kernel computes for the same theta.
+__global__ void etabar_partial_kernel(const double* theta, const SweepArgs a, unsigned long long* partials) {
+  extern __shared__ double s_rows[];
+  __shared__ ThetaC s_tc;
+  __shared__ BlockRed s_red;
+  if (threadIdx.x == 0) {
+    double th[kMaxP];
+    for (int q = 0; q < 3; ++q) th[q] = theta[q];
+    s_tc = LF::consts(th);
+  }
+  __syncthreads();
+  const long long P = static_cast<long long>(a.nL) * a.nr;
+  unsigned int pb0, pb1;
+  pair_range(P, blockIdx.x, gridDim.x, pb0, pb1);
+  long long j0 = 0;
+  int nrows = 0;
+  if (pb1 > pb0) {
+    j0 = pb0 / a.nr;
+    nrows = static_cast<int>((pb1 - 1) / a.nr - j0 + 1);
+  }
+  double* sL = s_rows;
+  double* sG = s_rows + a.rows_smem;
+  lf_rows(s_tc, a, j0, nrows, sL, sG);
+  __syncthreads();
+  Xacc xd, xe;
+  xacc_zero(xd);
+  xacc_zero(xe);
+  XFlags fe = {0u, 0u, 0u};
+  lf_pairs(a, pb0, pb1, j0, sL, sG, xe, fe);
+  unsigned int f[4] = {0u, fe.nan, fe.big, 0u};
+  warp_reduce(xd, xe, f);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_red.e[wid] = xe;
+    s_red.f[wid][1] = f[1];
+  }
+  __syncthreads();
+  if (wid == 0) {
+    Xacc be, bd;
+    xacc_zero(be);
+    xacc_zero(bd);
+    unsigned int bf[4] = {0u, 0u, 0u, 0u};
+    if (lane < static_cast<int>(blockDim.x >> 5)) {
+      be = s_red.e[lane];
+      bf[1] = s_red.f[lane][1];
+    }
+    warp_reduce(bd, be, bf);
+    if (lane == 0) {
+      unsigned long long* dst = partials + blockIdx.x * 4;
+      dst[0] = be.w0;
+      dst[1] = be.w1;
+      dst[2] = be.w2;
+      dst[3] = bf[1];
+    }
+  }
+}
+
+__global__ void etabar_final_kernel(const unsigned long long* partials, int nblocks, double* out) {
+  Xacc E, D;
+  xacc_zero(E);
+  xacc_zero(D);
+  unsigned int f[4] = {0u, 0u, 0u, 0u};
+  for (int b = threadIdx.x; b < nblocks; b += 32) {
+    Xacc t;
+    t.w0 = partials[b * 4 + 0];
+    t.w1 = partials[b * 4 + 1];
+    t.w2 = partials[b * 4 + 2];
+    xacc_add(E, t);
+    f[1] += static_cast<unsigned int>(partials[b * 4 + 3]);
+  }
+  warp_reduce(D, E, f);
+  if (threadIdx.x == 0) *out = (f[1] != 0u) ? NAN : xacc_to_double(E);
+}
+
+cudaError_t launch_eval_etabar(const double* theta_dev, const SweepArgs& rule, unsigned long long* partials,
+                               int grid, double* out, cudaStream_t st) {
+  const size_t smem = 2 * sizeof(double) * static_cast<size_t>(rule.rows_smem);
+  etabar_partial_kernel<<<grid, 256, smem, st>>>(theta_dev, rule, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  etabar_final_kernel<<<1, 32, 0, st>>>(partials, grid, out);
+  return cudaGetLastError();
+}
+
+}  // namespace chm

@@ -1,0 +1,366 @@
+"""ctypes binding of the C ABI in ``include/cudahm.h`` (argument marshalling only).
+
+Functions keep the C names (``cudahm_create``, ``cudahm_set_data``, ``cudahm_run``,
+...). Every sweep runs in the CUDA library; there is no Python or CPU fallback: if
+``lib/libcudahm.so`` is missing or fails to load, every call raises.
+
+``Sampler`` is a small convenience wrapper that owns one handle. PyTorch is only
+used, when asked, as the device allocator (its caching allocator) and as the source
+of the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libcudahm.so")
+
+ABI_VERSION = 1
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENUMERIC, ESTATE, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+NN1, MVN3, LF = 0, 1, 2
+FP64, FP32 = 0, 1
+MAX_P = 9
+MAX_CONSTS = 8
+MODEL_D = {NN1: 1, MVN3: 3, LF: 1}
+MODEL_P = {NN1: 2, MVN3: 9, LF: 3}
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class CudahmConfig(ctypes.Structure):
+    _fields_ = [
+        ("abi_version", ctypes.c_uint32),
+        ("model", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("d", ctypes.c_int32),
+        ("n", ctypes.c_int64),
+        ("seed", ctypes.c_uint64),
+        ("target_accept", ctypes.c_double),
+        ("adapt_exponent", ctypes.c_double),
+        ("chi_init_scale", ctypes.c_double),
+        ("theta_target_accept", ctypes.c_double),
+        ("adapt_theta", ctypes.c_int32),
+        ("trace_sweeps", ctypes.c_int32),
+        ("theta_init", ctypes.c_double * MAX_P),
+        ("theta_prop_scale", ctypes.c_double * MAX_P),
+        ("model_consts", ctypes.c_double * MAX_CONSTS),
+        ("device", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32),
+        ("cuda_stream", ctypes.c_void_p),
+        ("dev_alloc", ALLOC_FN),
+        ("dev_free", FREE_FN),
+        ("alloc_ctx", ctypes.c_void_p),
+        ("barrier_timeout_ns", ctypes.c_int64),
+        ("debug_skip_barrier_cta", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class CudahmStats(ctypes.Structure):
+    _fields_ = [
+        ("sweeps", ctypes.c_int64),
+        ("member_accepts", ctypes.c_int64),
+        ("theta_accepts", ctypes.c_int64),
+        ("rows", ctypes.c_int64),
+        ("last_run_ms", ctypes.c_double),
+        ("etabar", ctypes.c_double),
+        ("grid_blocks", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32),
+        ("objects_per_thread", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class CudahmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"cudahm error {code}: {msg}")
+        self.code = code
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_lib = None
+
+EXPORTED = [
+    "cudahm_config_init", "cudahm_create", "cudahm_set_data", "cudahm_set_data_device", "cudahm_set_chi",
+    "cudahm_run", "cudahm_get_samples", "cudahm_get_chi", "cudahm_get_theta", "cudahm_get_stats",
+    "cudahm_eval_logdens", "cudahm_eval_etabar", "cudahm_get_trace", "cudahm_checkpoint", "cudahm_restore",
+    "cudahm_sizeof_config", "cudahm_sizeof_stats", "cudahm_last_error", "cudahm_destroy",
+]
+
+
+def lib():
+    """Load libcudahm.so (built by ``paper_2105_08026_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    L.cudahm_config_init.argtypes = [ctypes.POINTER(CudahmConfig), i32, i64]
+    L.cudahm_config_init.restype = None
+    L.cudahm_create.argtypes = [ctypes.POINTER(CudahmConfig), ctypes.POINTER(vp)]
+    L.cudahm_set_data.argtypes = [vp, _dp, _dp, i64]
+    L.cudahm_set_data_device.argtypes = [vp, vp, vp, i64]
+    L.cudahm_set_chi.argtypes = [vp, _dp, i64]
+    L.cudahm_run.argtypes = [vp, i64, i64, i64]
+    L.cudahm_get_samples.argtypes = [vp, _dp, i64, ctypes.POINTER(i64)]
+    L.cudahm_get_chi.argtypes = [vp, _dp, _dp]
+    L.cudahm_get_theta.argtypes = [vp, _dp, _dp]
+    L.cudahm_get_stats.argtypes = [vp, ctypes.POINTER(CudahmStats)]
+    L.cudahm_eval_logdens.argtypes = [vp, _dp, _dp]
+    L.cudahm_eval_etabar.argtypes = [vp, _dp, _dp]
+    L.cudahm_get_trace.argtypes = [vp, _dp, _dp, _u8p, _dp, _dp, _dp, _dp, _u8p, _dp, ctypes.POINTER(i64)]
+    L.cudahm_checkpoint.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+    L.cudahm_restore.argtypes = [vp, vp, ctypes.c_size_t]
+    L.cudahm_sizeof_config.restype = ctypes.c_size_t
+    L.cudahm_sizeof_stats.restype = ctypes.c_size_t
+    L.cudahm_last_error.restype = ctypes.c_char_p
+    L.cudahm_destroy.argtypes = [vp]
+    L.cudahm_destroy.restype = None
+    for name in EXPORTED:
+        if name not in ("cudahm_config_init", "cudahm_sizeof_config", "cudahm_sizeof_stats", "cudahm_last_error",
+                        "cudahm_destroy"):
+            getattr(L, name).restype = ctypes.c_int
+    if L.cudahm_sizeof_config() != ctypes.sizeof(CudahmConfig):
+        raise RuntimeError("cudahm_config layout mismatch between the binding and the library")
+    if L.cudahm_sizeof_stats() != ctypes.sizeof(CudahmStats):
+        raise RuntimeError("cudahm_stats layout mismatch between the binding and the library")
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise CudahmError(rc, lib().cudahm_last_error().decode(errors="replace"))
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ------------------------------------------------------------- C-named calls --
+def cudahm_config_init(model: int, n: int) -> CudahmConfig:
+    cfg = CudahmConfig()
+    lib().cudahm_config_init(ctypes.byref(cfg), model, n)
+    return cfg
+
+
+def cudahm_create(cfg: CudahmConfig) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().cudahm_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def cudahm_set_data(h, y, aux):
+    y, aux = _f64(y), _f64(aux)
+    n = y.shape[0] if y.ndim else 0
+    _check(lib().cudahm_set_data(h, _dptr(y), _dptr(aux), n))
+
+
+def cudahm_set_data_device(h, y_ptr: int, aux_ptr: int, n: int):
+    _check(lib().cudahm_set_data_device(h, ctypes.c_void_p(y_ptr), ctypes.c_void_p(aux_ptr), n))
+
+
+def cudahm_set_chi(h, chi):
+    chi = _f64(chi)
+    n = chi.shape[0]
+    _check(lib().cudahm_set_chi(h, _dptr(chi), n))
+
+
+def cudahm_run(h, n_burn: int, n_iter: int, thin: int = 1):
+    _check(lib().cudahm_run(h, n_burn, n_iter, thin))
+
+
+def cudahm_get_samples(h, p: int, cap_rows: int) -> np.ndarray:
+    out = np.zeros((max(cap_rows, 1), p))
+    rows = ctypes.c_int64(0)
+    _check(lib().cudahm_get_samples(h, _dptr(out), cap_rows, ctypes.byref(rows)))
+    return out[: min(rows.value, cap_rows)].copy()
+
+
+def cudahm_get_chi(h, n: int, d: int):
+    chi = np.zeros(n * d)
+    S = np.zeros(n * d * d)
+    _check(lib().cudahm_get_chi(h, _dptr(chi), _dptr(S)))
+    return chi, S
+
+
+def cudahm_get_theta(h, p: int):
+    th = np.zeros(p)
+    St = np.zeros(p * p)
+    _check(lib().cudahm_get_theta(h, _dptr(th), _dptr(St)))
+    return th, St.reshape(p, p)
+
+
+def cudahm_get_stats(h) -> CudahmStats:
+    s = CudahmStats()
+    _check(lib().cudahm_get_stats(h, ctypes.byref(s)))
+    return s
+
+
+def cudahm_eval_logdens(h, theta, n: int) -> np.ndarray:
+    th = _f64(theta)
+    out = np.zeros(n)
+    _check(lib().cudahm_eval_logdens(h, _dptr(th), _dptr(out)))
+    return out
+
+
+def cudahm_eval_etabar(h, theta) -> float:
+    th = _f64(theta)
+    out = np.zeros(1)
+    _check(lib().cudahm_eval_etabar(h, _dptr(th), _dptr(out)))
+    return float(out[0])
+
+
+def cudahm_get_trace(h, n: int, p: int, T: int):
+    tr = dict(delta=np.zeros((T, n)), u=np.zeros((T, n)), acc=np.zeros((T, n), np.uint8),
+              theta_prop=np.zeros((T, p)), D=np.zeros(T), logalpha=np.zeros(T), utheta=np.zeros(T),
+              tacc=np.zeros(T, np.uint8), etabar=np.zeros(T))
+    t_out = ctypes.c_int64(0)
+    _check(lib().cudahm_get_trace(h, _dptr(tr["delta"]), _dptr(tr["u"]), tr["acc"].ctypes.data_as(_u8p),
+                                  _dptr(tr["theta_prop"]), _dptr(tr["D"]), _dptr(tr["logalpha"]),
+                                  _dptr(tr["utheta"]), tr["tacc"].ctypes.data_as(_u8p), _dptr(tr["etabar"]),
+                                  ctypes.byref(t_out)))
+    if t_out.value != T:
+        raise CudahmError(EINVAL, f"trace holds {t_out.value} sweeps, asked for {T}")
+    return tr
+
+
+def cudahm_checkpoint(h) -> bytes:
+    used = ctypes.c_size_t(0)
+    _check(lib().cudahm_checkpoint(h, None, 0, ctypes.byref(used)))
+    buf = ctypes.create_string_buffer(used.value)
+    _check(lib().cudahm_checkpoint(h, buf, used.value, ctypes.byref(used)))
+    return buf.raw
+
+
+def cudahm_restore(h, blob: bytes):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(lib().cudahm_restore(h, buf, len(blob)))
+
+
+def cudahm_destroy(h):
+    if h:
+        lib().cudahm_destroy(h)
+
+
+# --------------------------------------------------------------- convenience --
+class _TorchAllocator:
+    """Device allocator callbacks backed by torch's caching allocator."""
+
+    def __init__(self, device: int):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.alloc_cb = ALLOC_FN(self._alloc)
+        self.free_cb = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx):
+        try:
+            return int(self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device))
+        except Exception:  # out of memory -> the library reports ENOMEM
+            return None
+
+    def _free(self, ptr, ctx):
+        if ptr:
+            self.torch.cuda.caching_allocator_delete(int(ptr))
+
+
+class Sampler:
+    """One population and its chain (owns a cudahm handle)."""
+
+    def __init__(self, model: int, n: int, *, theta_init, theta_prop_scale=None, model_consts=None, seed: int = 1,
+                 precision: int = FP64, adapt_theta: bool = True, chi_init_scale: float = 1.0,
+                 target_accept: float = 0.4, theta_target_accept: float = 0.4, adapt_exponent: float = 2.0 / 3.0,
+                 trace_sweeps: int = 0, device: int = 0, block_threads: int = 0, stream=None,
+                 use_torch_allocator: bool = False, barrier_timeout_ns: int = 0, debug_skip_barrier_cta: int = -1):
+        self.model, self.n = model, int(n)
+        self.d, self.p = MODEL_D[model], MODEL_P[model]
+        cfg = cudahm_config_init(model, n)
+        cfg.precision = precision
+        cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        cfg.adapt_theta = 1 if adapt_theta else 0
+        cfg.chi_init_scale = chi_init_scale
+        cfg.target_accept = target_accept
+        cfg.theta_target_accept = theta_target_accept
+        cfg.adapt_exponent = adapt_exponent
+        cfg.trace_sweeps = trace_sweeps
+        cfg.device = device
+        cfg.block_threads = block_threads
+        cfg.barrier_timeout_ns = barrier_timeout_ns
+        cfg.debug_skip_barrier_cta = debug_skip_barrier_cta
+        for q, v in enumerate(_f64(theta_init)):
+            cfg.theta_init[q] = v
+        if theta_prop_scale is not None:
+            for q, v in enumerate(_f64(theta_prop_scale)):
+                cfg.theta_prop_scale[q] = v
+        if model_consts is not None:
+            for q, v in enumerate(_f64(model_consts)):
+                cfg.model_consts[q] = v
+        if stream is not None:
+            cfg.cuda_stream = ctypes.c_void_p(int(stream))
+        self._alloc = None
+        if use_torch_allocator:
+            self._alloc = _TorchAllocator(device)
+            cfg.dev_alloc = self._alloc.alloc_cb
+            cfg.dev_free = self._alloc.free_cb
+        self.cfg = cfg
+        self.h = cudahm_create(cfg)
+
+    def close(self):
+        if self.h:
+            cudahm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_data(self, y, aux):
+        cudahm_set_data(self.h, y, aux)
+
+    def set_chi(self, chi):
+        cudahm_set_chi(self.h, chi)
+
+    def run(self, n_burn: int, n_iter: int, thin: int = 1) -> np.ndarray:
+        cudahm_run(self.h, n_burn, n_iter, thin)
+        cap = n_iter // thin if (n_iter > 0 and thin > 0) else 0
+        return cudahm_get_samples(self.h, self.p, cap) if cap > 0 else np.zeros((0, self.p))
+
+    def chi(self):
+        c, S = cudahm_get_chi(self.h, self.n, self.d)
+        return c, S
+
+    def theta(self):
+        return cudahm_get_theta(self.h, self.p)
+
+    def stats(self) -> CudahmStats:
+        return cudahm_get_stats(self.h)
+
+    def logdens(self, theta=None) -> np.ndarray:
+        th = self.theta()[0] if theta is None else theta
+        return cudahm_eval_logdens(self.h, th, self.n)
+
+    def etabar(self, theta) -> float:
+        return cudahm_eval_etabar(self.h, theta)
+
+    def trace(self, T: int):
+        return cudahm_get_trace(self.h, self.n, self.p, T)
+
+    def checkpoint(self) -> bytes:
+        return cudahm_checkpoint(self.h)
+
+    def restore(self, blob: bytes):
+        cudahm_restore(self.h, blob)
