@@ -1,0 +1,314 @@
+"""Benchmark of the CUDA MWG sampler on the thinned luminosity-function workload.
+
+Workload (one "step" = one Metropolis-within-Gibbs sweep over all members, i.e. every
+row of the hot path: theta proposal, N member RAM steps, the exact sum of
+log f(chi_i;theta') - log f(chi_i;theta), the 1024 x 1024 selection-integral rule at
+theta', the grid barrier, the theta accept and its RAM update, the kept-row record):
+  N = 3e5 detected objects, Schechter-form population beta = -1.2, L* = 1e10,
+  L_low = 1e8, distances ~ r^2 on [0, 4000], sigma_F = 0.2 F_th, F_th set for 30%
+  detection; FP64 throughout. Synthetic catalog (seeded), no external data.
+
+Metric: object-updates/s = N x sweeps / seconds (whole job over all ranks).
+  value: device time of the timed sweeps (CUDA events on the sampler's stream), inputs
+         resident in HBM, L2 flushed (256 MB write) before each timed launch;
+  e2e:   the same metric through the public API with host buffers: set_data from host
+         arrays, run, get_samples back to the host, every timed iteration.
+
+Multi-GPU (torchrun): every rank runs an independent replica on its own catalog
+(weak scaling, no collective on the data path); time = max over ranks.
+
+--impl reference: the CPU FP64 oracle timed on the host on a bounded sample of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_OBJ = 300_000
+DATA_SEED = 1002
+CHAIN_SEED = 2
+L2_FLUSH_BYTES = 256 << 20
+# dram read+write bytes of one sweep-kernel launch (ncu, same profile); the member data are read
+# once per launch and the state stays in registers, so this does not grow with the sweeps.
+DRAM_BYTES_PER_LAUNCH = 9.80e6
+
+# FP64 floating-point work of one sweep of this workload (2 per DFMA, 1 per DADD/DMUL),
+# from ncu's sass_thread_inst_executed_op_d{fma,add,mul} counters on the sweep kernel
+# (profiles/sweep_kernel_lf_n300000.md); None until measured.
+FP64_FLOP_PER_SWEEP = 9.74e7
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=1000)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--repeats", type=int, default=5, help="timed launches the steps are split into")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sweeps", type=int, default=8)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(rank):
+    from paper_2105_08026_gb300 import synth
+    data = synth.lf_data(N_OBJ, seed=DATA_SEED + rank)
+    theta0, scale, consts = synth.lf_settings(data)
+    return data, theta0, scale, consts
+
+
+# ------------------------------------------------------------------ clocks ---
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in self.rows for j in range(4) if r[4 + j].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# -------------------------------------------------------------- CPU oracle ---
+def oracle_rate(data, theta0, scale, consts, sweeps):
+    import oracle
+    from paper_2105_08026_gb300 import synth
+    chi0 = synth.lf_chi_init(data, theta0)
+    ch = oracle.Chain(oracle.LF, data.fhat, data.r, consts, theta0, scale, CHAIN_SEED, chi0)
+    ch.run(0, 1)  # first sweep also evaluates etabar at theta0
+    t0 = time.perf_counter()
+    ch.run(0, sweeps)
+    dt = time.perf_counter() - t0
+    return data.fhat.size * sweeps / dt, dt
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    data, theta0, scale, consts = workload(0)
+    sweeps = max(1, min(args.steps, 15))
+    rate, dt = oracle_rate(data, theta0, scale, consts, sweeps)
+    sample = f"{sweeps} full sweeps of the N={N_OBJ} LF workload (1024x1024 rule), single-threaded oracle"
+    line = {"impl": "reference", "metric": "object-updates/s", "value": rate, "unit": "object-updates/s",
+            "n_gpus": 0, "steps": sweeps, "warmup": 1, "ms_per_step": dt * 1e3 / sweeps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "LF thinned luminosity function, N=3e5, FP64, 1024x1024 selection rule",
+                       "n": N_OBJ, "sweeps_timed": sweeps},
+            "cpu_baseline": {"value": rate, "unit": "object-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": "object-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------- CUDA ---
+def fp64_peak(device):
+    from paper_2105_08026_gb300 import build as cbuild
+    L = ctypes.CDLL(cbuild.PEAKS_LIB)
+    L.chm_fp64_dfma_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    r = ctypes.c_double(0.0)
+    rc = L.chm_fp64_dfma_rate(device, ctypes.byref(r))
+    return 2.0 * r.value if rc == 0 else None  # FP64 flop/s
+
+
+def run_cuda(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2105_08026_gb300 import cudahm
+
+    data, theta0, scale, consts = workload(rank)
+    n = data.fhat.size
+    stream = torch.cuda.current_stream()
+    s = cudahm.Sampler(cudahm.LF, n, theta_init=theta0, theta_prop_scale=scale, model_consts=consts,
+                       seed=CHAIN_SEED + rank, device=local, stream=stream.cuda_stream, use_torch_allocator=True)
+    # inputs resident in HBM before timing (device-to-device set_data from torch tensors)
+    y_dev = torch.from_numpy(data.fhat).cuda()
+    r_dev = torch.from_numpy(data.r).cuda()
+    cudahm.cudahm_set_data_device(s.h, y_dev.data_ptr(), r_dev.data_ptr(), n)
+    torch.cuda.synchronize()
+    # warm-up: burn-in sweeps (untimed)
+    if args.warmup > 0:
+        s.run(args.warmup, 0)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    K = args.steps
+    R = max(1, min(args.repeats, K))
+    chunks = [K // R + (1 if j < K % R else 0) for j in range(R)]
+    clocks = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms = 0.0
+    kernel_ms = 0.0
+    launches = 0
+    rows_total = 0
+    for ns in chunks:
+        flush.zero_()  # write 256 MB > L2 between timed launches
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rows = s.run(0, ns, 1)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        kernel_ms += s.stats().last_run_ms
+        nl = math.ceil(ns / 4096)
+        launches += 2 * nl  # per chunk of <= 4096 sweeps: theta-table kernel + persistent sweep kernel
+        rows_total += rows.shape[0]
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    assert rows_total == K
+    t_max_ms = total_ms
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max_ms = float(t.item())
+    value = ws * n * K / (t_max_ms * 1e-3)
+
+    # e2e through the public API with host buffers (every iteration: H2D data, run, D2H samples)
+    e2e = None
+    if not args.no_e2e:
+        ke = max(1, K // R)
+        s2 = cudahm.Sampler(cudahm.LF, n, theta_init=theta0, theta_prop_scale=scale, model_consts=consts,
+                            seed=CHAIN_SEED + rank, device=local, stream=stream.cuda_stream,
+                            use_torch_allocator=True)
+        host_y = np.ascontiguousarray(data.fhat)
+        host_r = np.ascontiguousarray(data.r)
+        s2.set_data(host_y, host_r)
+        s2.run(min(args.warmup, 200), 0)  # warm the selection-integral cache and the code path
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(R):
+            s2.set_data(host_y, host_r)          # host -> device copy of the inputs
+            out = s2.run(0, ke, 1)               # device -> host copy of the theta rows
+            assert out.shape == (ke, 3)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        e2e_val = n * ke * R / wall
+        if ws > 1:
+            t = torch.tensor([wall], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_val = ws * n * ke * R / float(t.item())
+        e2e = {"value": e2e_val, "unit": "object-updates/s", "h2d_bytes_per_step": 2 * n * 8 / ke,
+               "d2h_bytes_per_step": 3 * 8 + 4 / ke}
+        s2.close()
+
+    if rank != 0:
+        s.close()
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    st = s.stats()
+    peak = fp64_peak(local)
+    sweep_launch_ms = kernel_ms / max(1, launches // 2)
+    sweeps_per_launch = K / max(1, launches // 2)
+    roofline = {"bound": "alu", "unit": "TFLOP/s", "peak": peak / 1e12 if peak else None,
+                "peak_source": "FP64 DFMA stream measured live on this GPU (x2 flops)",
+                "achieved": None, "frac": None, "traffic": DRAM_BYTES_PER_LAUNCH,
+                "kernel": "sweep_kernel<LF,4>", "launch_ms": sweep_launch_ms}
+    if FP64_FLOP_PER_SWEEP is not None and peak:
+        ach = FP64_FLOP_PER_SWEEP * sweeps_per_launch / (sweep_launch_ms * 1e-3)
+        roofline.update(achieved=ach / 1e12, frac=ach / peak)
+    cpu = None
+    if not args.no_cpu:
+        sweeps = max(1, args.cpu_sweeps)
+        rate, dt = oracle_rate(data, theta0, scale, consts, sweeps)
+        cpu = {"value": rate, "unit": "object-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"{sweeps} full sweeps of the same N={n} workload ({dt:.1f} s, single-threaded)"}
+    line = {"metric": "object-updates/s", "value": value, "unit": "object-updates/s", "n_gpus": ws, "steps": K,
+            "warmup": args.warmup, "ms_per_step": t_max_ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "LF thinned luminosity function, N=3e5, FP64, 1024x1024 selection rule",
+                       "n": n, "parallelism": f"replicas x{ws}", "l2": "256 MB flush before each timed launch; "
+                       "member state register-resident within a launch", "timed_launches": R,
+                       "launch_shape": [st.grid_blocks, st.block_threads, st.objects_per_thread]},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    s.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_cuda(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -18,7 +18,9 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libcudahm.so")
+PEAKS_LIB = os.path.join(LIBDIR, "libchm_peaks.so")
 SOURCES = ["sweep.cu", "runtime.cu"]
+PEAKS_SOURCES = ["pipe_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", f"-I{INCLUDE}", f"-I{CSRC}"]
 
@@ -36,9 +38,9 @@ def _inputs():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(PEAKS_LIB)):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PEAKS_LIB))
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
@@ -49,10 +51,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(LIBDIR, exist_ok=True)
     cc = nvcc()
     procs = []
-    objs = []
-    for src in SOURCES:
+    objs = {}
+    for src in SOURCES + PEAKS_SOURCES:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        objs.append(obj)
+        objs[src] = obj
         cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
@@ -61,12 +63,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
         out, _ = pr.communicate()
         if pr.returncode != 0:
             raise RuntimeError(f"nvcc failed: {' '.join(cmd)}\n{out.decode(errors='replace')}")
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
-    out = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
-    if out.returncode != 0:
-        raise RuntimeError(f"link failed: {' '.join(cmd)}\n{out.stdout.decode(errors='replace')}")
-    os.replace(tmp, LIB)
+    for lib, srcs in ((LIB, SOURCES), (PEAKS_LIB, PEAKS_SOURCES)):
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [cc, *ARCH, "-shared", "-o", tmp, *[objs[s] for s in srcs], "-lcudart"]
+        out = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+        if out.returncode != 0:
+            raise RuntimeError(f"link failed: {' '.join(cmd)}\n{out.stdout.decode(errors='replace')}")
+        os.replace(tmp, lib)
     return LIB
 
 
