@@ -169,6 +169,10 @@ int cudahm_eval_logdens(cudahm_t h, const double* theta_host, double* lp_host);
 /* LF only: the selection integral etabar(theta) of the handle's rule at the given theta. */
 int cudahm_eval_etabar(cudahm_t h, const double* theta_host, double* out);
 
+/* LF only: detection efficiency eta(F) = Phi((F - F_th)/sigma_F) (Sec. 5.2, eq. key) for n
+ * fluxes, evaluated by the same device routine the selection integral uses. */
+int cudahm_eval_detection(cudahm_t h, const double* F_host, double* eta_host, int64_t n);
+
 /* Lockstep trace of the first T = min(trace_sweeps, sweeps of the last run) sweeps of the
  * last run. Member arrays are [T][N] (sweep-major): delta = lp(Y) - lp(X) (-inf off support),
  * u = accept uniform, acc = 1 if accepted. Theta arrays: theta_prop [T][p], D [T] = sum of

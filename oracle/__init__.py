@@ -66,6 +66,8 @@ def lib():
             L.orc_gauss_legendre.argtypes = [ctypes.c_int, _dp, _dp]
             L.orc_lf_etabar.argtypes = [_dp, _dp]
             L.orc_lf_etabar.restype = ctypes.c_double
+            L.orc_lf_detection.argtypes = [ctypes.c_double, _dp]
+            L.orc_lf_detection.restype = ctypes.c_double
             L.orc_lf_H.argtypes = [ctypes.c_double, _dp]
             L.orc_lf_H.restype = ctypes.c_double
             L.orc_member_logdens.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp,
@@ -154,6 +156,12 @@ def lf_etabar(theta, consts) -> float:
     th = _f64(theta)
     c = _f64(consts)
     return lib().orc_lf_etabar(_p(th), _p(c))
+
+
+def lf_detection(F, consts) -> np.ndarray:
+    """eta(F) = Phi((F - F_th)/sigma_F) for an array of fluxes."""
+    c = _f64(consts)
+    return np.array([lib().orc_lf_detection(float(f), _p(c)) for f in np.atleast_1d(F)])
 
 
 def lf_H(L, consts) -> float:

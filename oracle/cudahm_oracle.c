@@ -325,6 +325,9 @@ double orc_lf_etabar(const double* th, const double* consts) {
   return v;
 }
 
+/* Detection efficiency eta(F) = Phi((F - F_th)/sigma_F) (Sec. 5.2, eq. key). */
+double orc_lf_detection(double F, const double* consts) { return phi_cdf((F - consts[1]) / consts[0]); }
+
 double orc_lf_H(double L, const double* consts) {
   gl_rule R;
   gl_rule_init(&R, (int)consts[3], (int)consts[4]);

@@ -43,6 +43,7 @@ struct SweepArgs {
   int* err;
   const double* tab_U;    // [ns][p] theta-proposal normals
   const double* tab_u;    // [ns] theta accept uniforms
+  const double* tab_lnu;  // [ns] their logarithms
   const double* tab_eta;  // [ns] adaptation weights (k+1)^-gamma
   long long k0;           // sweeps done before this launch
   long long ns;           // sweeps in this launch
@@ -59,8 +60,10 @@ struct SweepArgs {
   const double* wL;
   const double* qs;  // q(r_k)/sigma_F
   const double* Wr;  // inner weights
+  const double* phi_coef;  // Taylor table of the normal CDF
   int nL, nr;
-  int rows_smem;     // row slots per block for the outer-node values
+  int rows_smem;     // segment slots per block for the outer-node values
+  int mpb;           // members of the largest block (shared-memory slots for y, aux)
   // trace (nullable)
   long long trace_T;
   long long trace_off;  // sweeps of this run traced by earlier launches
@@ -80,6 +83,12 @@ struct SweepArgs {
 // Kernel launch helpers (sweep.cu). Return cudaError_t of the launch.
 cudaError_t launch_sweep(const SweepArgs& a, int K, int grid, int block, cudaStream_t st);
 cudaError_t sweep_occupancy(int model, int K, int block, int smem_bytes, int* blocks_per_sm);
+size_t sweep_smem_bytes(int model, int mpb, int rows_smem);
+cudaError_t launch_phi_table(double* coef, cudaStream_t st);
+int phi_table_words();
+cudaError_t launch_detection(long long n, const double* F, double F_th, double sigma_F, const double* coef,
+                             double* out, cudaStream_t st);
+cudaError_t sweep_set_smem(int model, int K, int smem_bytes);
 cudaError_t launch_prepare(int model, long long n, const double* y_raw, const double* aux_raw, double* y, double* aux,
                            double* chi, double* S, const ModelConsts& mc, const double* theta, int* bad,
                            int set_default_chi, cudaStream_t st);
@@ -89,7 +98,7 @@ cudaError_t launch_gauss_legendre(int n, double* x, double* w, cudaStream_t st);
 cudaError_t launch_lf_inner(int nr, const double* xr, const double* wr, double r_max, double sigma_F, double* qs,
                             double* Wr, cudaStream_t st);
 cudaError_t launch_tables(int p, uint32_t key0, uint32_t key1, long long k0, long long ns, double gamma, double* U,
-                          double* u, double* eta, cudaStream_t st);
+                          double* u, double* lnu, double* eta, cudaStream_t st);
 cudaError_t launch_eval_logdens(int model, long long n, const double* y, const double* aux, const double* chi,
                                 const double* theta_dev, const ModelConsts& mc, double* out, cudaStream_t st);
 cudaError_t launch_eval_etabar(const double* theta_dev, const SweepArgs& rule, unsigned long long* partials,

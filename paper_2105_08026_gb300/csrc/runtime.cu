@@ -51,7 +51,7 @@ struct cudahm {
   bool own_stream = false;
   int sms = 0;
   // launch shape
-  int grid = 0, block = 256, K = 1, rows_smem = 1;
+  int grid = 0, block = 256, K = 1, rows_smem = 1, mpb = 1;
   ModelConsts mc{};
   // device buffers
   std::vector<void*> allocs;
@@ -64,7 +64,7 @@ struct cudahm {
   int* bad = nullptr;
   double* theta_dev = nullptr;
   double* eval_out = nullptr;
-  double *tab_U = nullptr, *tab_u = nullptr, *tab_eta = nullptr;
+  double *tab_U = nullptr, *tab_u = nullptr, *tab_lnu = nullptr, *tab_eta = nullptr;
   double* rows = nullptr;
   long long rows_cap = 0;
   // trace
@@ -75,6 +75,7 @@ struct cudahm {
   long long trace_T_last = 0;
   // LF rule
   double *xL = nullptr, *wL = nullptr, *xr = nullptr, *wr = nullptr, *qs = nullptr, *Wr = nullptr;
+  double* phi_coef = nullptr;
   unsigned long long* eb_partials = nullptr;
   int eb_grid = 0, eb_rows_smem = 1;
   // host mirrors
@@ -187,38 +188,43 @@ int choose_shape(cudahm* h) {
   h->block = block;
   const long long n = h->n;
   const int model = h->cfg.model;
+  const bool lf = (model == CUDAHM_LF);
+  // LF: segments of 128 inner nodes, G = n_L * ceil(n_r / 128), dealt round-robin to the blocks
+  const long long G = lf ? static_cast<long long>(h->cfg.model_consts[3]) *
+                               ((static_cast<long long>(h->cfg.model_consts[4]) + 127) / 128)
+                         : 0;
   const int Ks[4] = {1, 2, 4, 8};
-  for (int ki = 0; ki < 4; ++ki) {
+  for (int ki = 0; ki < 4 && h->grid == 0; ++ki) {
     const int K = Ks[ki];
+    // the grid depends on the occupancy, which depends on the shared memory, which depends on
+    // the grid: iterate from the register-limited occupancy down until it is consistent
     int bps = 0;
-    // shared memory for the LF rows depends on the grid; bound it first with one row slot
-    CU(sweep_occupancy(model, K, block, 2 * 8 * 8, &bps));
-    if (bps < 1) continue;
-    int grid;
-    if (model == CUDAHM_LF) grid = bps * h->sms;
-    else grid = static_cast<int>(std::min<long long>(static_cast<long long>(bps) * h->sms, (n + block - 1) / block));
-    const long long need = (n + static_cast<long long>(grid) * block - 1) / (static_cast<long long>(grid) * block);
-    if (need <= K) {
-      h->K = K;
-      h->grid = grid;
-      break;
+    CU(sweep_occupancy(model, K, block, 0, &bps));
+    for (; bps >= 1; --bps) {
+      int grid = lf ? bps * h->sms
+                    : static_cast<int>(std::min<long long>(static_cast<long long>(bps) * h->sms,
+                                                           (n + block - 1) / block));
+      const long long mpb = (n + grid - 1) / grid;  // members of the largest block
+      if ((mpb + block - 1) / block > K) break;     // needs a larger K
+      const int rows = lf ? static_cast<int>((G + grid - 1) / grid) : 1;
+      const size_t smem = sweep_smem_bytes(model, static_cast<int>(mpb), rows);
+      if (smem > 200 * 1024) break;
+      int fit = 0;
+      CU(sweep_occupancy(model, K, block, static_cast<int>(smem), &fit));
+      if (fit * h->sms >= grid) {
+        CU(sweep_set_smem(model, K, static_cast<int>(smem)));
+        h->K = K;
+        h->grid = grid;
+        h->mpb = static_cast<int>(mpb);
+        h->rows_smem = rows;
+        break;
+      }
     }
   }
   if (h->grid == 0) return fail(CUDAHM_EUNSUPPORTED, "n = %lld exceeds the register-resident capacity", n);
-  if (model == CUDAHM_LF) {
-    const long long P = static_cast<long long>(h->cfg.model_consts[3]) * static_cast<long long>(h->cfg.model_consts[4]);
-    const long long nr = static_cast<long long>(h->cfg.model_consts[4]);
-    h->rows_smem = static_cast<int>((P / h->grid + nr - 1) / nr + 2);
-    int bps = 0;
-    CU(sweep_occupancy(model, h->K, block, 2 * 8 * h->rows_smem, &bps));
-    if (bps * h->sms < h->grid) {
-      h->grid = bps * h->sms;
-      h->rows_smem = static_cast<int>((P / h->grid + nr - 1) / nr + 2);
-      const long long need = (n + static_cast<long long>(h->grid) * block - 1) / (static_cast<long long>(h->grid) * block);
-      if (need > h->K) return fail(CUDAHM_EUNSUPPORTED, "n = %lld exceeds the register-resident capacity", n);
-    }
+  if (lf) {
     h->eb_grid = 4 * h->sms;
-    h->eb_rows_smem = static_cast<int>((P / h->eb_grid + nr - 1) / nr + 2);
+    h->eb_rows_smem = static_cast<int>((G + h->eb_grid - 1) / h->eb_grid);
   }
   return CUDAHM_OK;
 }
@@ -246,9 +252,11 @@ SweepArgs base_args(cudahm* h) {
   a.wL = h->wL;
   a.qs = h->qs;
   a.Wr = h->Wr;
+  a.phi_coef = h->phi_coef;
   a.nL = h->cfg.model == CUDAHM_LF ? static_cast<int>(h->cfg.model_consts[3]) : 0;
   a.nr = h->cfg.model == CUDAHM_LF ? static_cast<int>(h->cfg.model_consts[4]) : 0;
   a.rows_smem = h->rows_smem;
+  a.mpb = h->mpb;
   a.timeout_ns = h->cfg.barrier_timeout_ns > 0 ? h->cfg.barrier_timeout_ns : 2000000000ll;
   a.skip_cta = h->cfg.debug_skip_barrier_cta;
   return a;
@@ -387,14 +395,18 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
       (rc = alloc_into(h, &h->err, 4)) || (rc = alloc_into(h, &h->bad, 4)) ||
       (rc = alloc_into(h, &h->theta_dev, kMaxP)) || (rc = alloc_into(h, &h->eval_out, 4)) ||
       (rc = alloc_into(h, &h->tab_U, kChunk * p)) || (rc = alloc_into(h, &h->tab_u, kChunk)) ||
+      (rc = alloc_into(h, &h->tab_lnu, kChunk)) ||
       (rc = alloc_into(h, &h->tab_eta, kChunk)))
     return bail(rc);
   if (cfg->model == CUDAHM_LF) {
     const int nL = static_cast<int>(k[3]), nr = static_cast<int>(k[4]);
     if ((rc = alloc_into(h, &h->xL, nL)) || (rc = alloc_into(h, &h->wL, nL)) || (rc = alloc_into(h, &h->xr, nr)) ||
         (rc = alloc_into(h, &h->wr, nr)) || (rc = alloc_into(h, &h->qs, nr)) || (rc = alloc_into(h, &h->Wr, nr)) ||
-        (rc = alloc_into(h, &h->eb_partials, 4ull * h->eb_grid)))
+        (rc = alloc_into(h, &h->eb_partials, 4ull * h->eb_grid)) ||
+        (rc = alloc_into(h, &h->phi_coef, static_cast<size_t>(phi_table_words()))))
       return bail(rc);
+    if (launch_phi_table(h->phi_coef, h->stream) != cudaSuccess)
+      return bail(fail(CUDAHM_ECUDA, "normal-CDF table set-up failed: %s", cudaGetErrorString(cudaGetLastError())));
     if (launch_gauss_legendre(nL, h->xL, h->wL, h->stream) != cudaSuccess ||
         launch_gauss_legendre(nr, h->xr, h->wr, h->stream) != cudaSuccess ||
         launch_lf_inner(nr, h->xr, h->wr, k[2], k[0], h->qs, h->Wr, h->stream) != cudaSuccess)
@@ -513,12 +525,13 @@ int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
   a.tr_eb = h->tr_eb;
   a.tab_U = h->tab_U;
   a.tab_u = h->tab_u;
+  a.tab_lnu = h->tab_lnu;
   a.tab_eta = h->tab_eta;
   long long off = 0, rows_done = 0;
   while (off < total) {
     const long long ns = std::min<long long>(kChunk, total - off);
-    CU(launch_tables(h->p, a.key0, a.key1, h->sweeps, ns, h->cfg.adapt_exponent, h->tab_U, h->tab_u, h->tab_eta,
-                     h->stream));
+    CU(launch_tables(h->p, a.key0, a.key1, h->sweeps, ns, h->cfg.adapt_exponent, h->tab_U, h->tab_u, h->tab_lnu,
+                     h->tab_eta, h->stream));
     CU(cudaMemsetAsync(h->bar, 0, sizeof(unsigned int), h->stream));
     a.k0 = h->sweeps;
     a.ns = ns;
@@ -631,6 +644,29 @@ int cudahm_eval_etabar(cudahm_t h, const double* theta_host, double* out) {
   TRY(compute_etabar_into(h, h->theta_dev, h->eval_out));
   CU(cudaMemcpyAsync(out, h->eval_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
+  return CUDAHM_OK;
+}
+
+int cudahm_eval_detection(cudahm_t h, const double* F_host, double* eta_host, int64_t n) {
+  if (!h || !F_host || !eta_host || n < 0) return fail(CUDAHM_EINVAL, "bad argument");
+  if (h->cfg.model != CUDAHM_LF) return fail(CUDAHM_EINVAL, "detection efficiency exists only for the LF model");
+  if (n == 0) return CUDAHM_OK;
+  CU(cudaSetDevice(h->cfg.device));
+  double *F = nullptr, *out = nullptr;
+  TRY(alloc_into(h, &F, n));
+  int rc = alloc_into(h, &out, n);
+  if (rc != CUDAHM_OK) {
+    h->dfree(F);
+    return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(F, F_host, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = launch_detection(n, F, h->cfg.model_consts[1], h->cfg.model_consts[0], h->phi_coef, out, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(eta_host, out, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  h->dfree(F);
+  h->dfree(out);
+  if (e != cudaSuccess) return fail(CUDAHM_ECUDA, "eval_detection: %s", cudaGetErrorString(e));
   return CUDAHM_OK;
 }
 

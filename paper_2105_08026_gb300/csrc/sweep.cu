@@ -112,43 +112,119 @@ __device__ void ram_update_theta(int p, double* L, const double* U, double alpha
   }
 }
 
+// ------------------------------------------------------- normal CDF Phi -------
+// Phi(x) = erfc(-x/sqrt 2)/2 (Sec. 5.2, eq. key) by a table of local Taylor polynomials:
+// intervals centred at c_i = -8 + i/8 (i = 0..kPhiN-1), |x - c_i| <= 1/16, degree kPhiDeg.
+// With phi = Phi' and d^n Phi/dx^n = (-1)^(n-1) He_(n-1)(x) phi(x) (He = probabilists'
+// Hermite polynomials), the coefficients are a_0 = Phi(c), a_n = (-1)^(n-1) He_(n-1)(c) phi(c)/n!.
+// For c > 0 the table holds the upper tail Q = 1 - Phi (a_0 = erfc(c/sqrt 2)/2, a_n negated)
+// and Phi = 1 - Q, so that values near 1 keep full absolute accuracy. The remainder of the
+// degree-10 series on |t| <= 1/16 is below 1e-18; the table is built once per handle on the
+// device from CUDA's erfc and exp. Above x = 8.5, Phi rounds to 1 exactly; below x = -8
+// (Phi < 7e-16) erfc is called directly.
+constexpr int kPhiN = 133;
+constexpr int kPhiDeg = 10;
+constexpr int kPhiWords = kPhiN * (kPhiDeg + 1);  // coefficient-major: coef[n * kPhiN + i]
+
+__device__ __forceinline__ double phi_table(double x, const double* __restrict__ coef) {
+  if (x > 8.5) return 1.0;
+  if (x < -8.0) return 0.5 * erfc(-x * 0.70710678118654752440);
+  const double magic = 6755399441055744.0;        // 1.5 * 2^52
+  const double r = fma(x, 8.0, 64.0 + magic);     // round(8x + 64) sits in the low mantissa bits
+  const int i = __double2loint(r);
+  const double c = fma(r - magic, 0.125, -8.0);   // centre, exact
+  const double t = x - c;                         // exact (|t| <= 1/16, c a multiple of 1/8)
+  double q = coef[kPhiDeg * kPhiN + i];
+#pragma unroll
+  for (int n = kPhiDeg - 1; n >= 0; --n) q = fma(q, t, coef[n * kPhiN + i]);
+  return (i <= 64) ? q : 1.0 - q;
+}
+
+__global__ void phi_table_kernel(double* coef) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kPhiN) return;
+  const double c = -8.0 + 0.125 * i;
+  const bool upper = (i > 64);
+  const double dens = exp(-0.5 * (c * c)) * 0.39894228040143267794;  // phi(c)
+  coef[i] = upper ? 0.5 * erfc(c * 0.70710678118654752440) : 0.5 * erfc(-c * 0.70710678118654752440);
+  double hm1 = 0.0, h = 1.0;  // He_(n-2), He_(n-1) at c
+  double fact = 1.0;
+  for (int n = 1; n <= kPhiDeg; ++n) {
+    fact *= n;
+    double an = ((n - 1) & 1 ? -h : h) * dens / fact;  // (-1)^(n-1) He_(n-1)(c) phi(c)/n!
+    coef[n * kPhiN + i] = upper ? -an : an;
+    const double hn = c * h - (n - 1) * hm1;  // He_n = c He_(n-1) - (n-1) He_(n-2)
+    hm1 = h;
+    h = hn;
+  }
+}
+
+cudaError_t launch_phi_table(double* coef, cudaStream_t st) {
+  phi_table_kernel<<<(kPhiN + 127) / 128, 128, 0, st>>>(coef);
+  return cudaGetLastError();
+}
+
+int phi_table_words() { return kPhiWords; }
+
+// Detection efficiency eta(F) = Phi((F - F_th)/sigma_F) for a list of fluxes.
+__global__ void detection_kernel(long long n, const double* F, double F_th, double sigma_F, const double* coef,
+                                 double* out) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = phi_table((F[i] - F_th) / sigma_F, coef);
+}
+
+cudaError_t launch_detection(long long n, const double* F, double F_th, double sigma_F, const double* coef,
+                             double* out, cudaStream_t st) {
+  const int blk = 256;
+  detection_kernel<<<static_cast<unsigned int>((n + blk - 1) / blk), blk, 0, st>>>(n, F, F_th, sigma_F, coef, out);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ LF rule --------
-// Outer node values for rows j in [j0, j0 + nrows): L_j = e^t_j and
-// G_j = (half-width) w_j g(e^t_j) e^t_j on t in [ln L_low, ln L* + ln_upper].
-__device__ __forceinline__ void lf_rows(const ThetaC& tc, const SweepArgs& a, long long j0, int nrows, double* sL,
-                                        double* sG) {
+// The 2-D rule is cut into segments of kSeg consecutive inner nodes of one outer node:
+// segment g = s * nL + j covers outer node j and inner nodes [s kSeg, (s+1) kSeg). Block b
+// of B takes segments b, b + B, b + 2B, ...: every block sees the whole range of L and of r,
+// so blocks get the same mix of pairs that need erfc and pairs where Phi = 1 exactly.
+constexpr int kSegShift = 7;
+constexpr int kSeg = 1 << kSegShift;
+
+__device__ __forceinline__ int lf_block_segments(const SweepArgs& a, int b, int B) {
+  const int spr = (a.nr + kSeg - 1) >> kSegShift;
+  const int G = a.nL * spr;
+  return (b < G) ? (G - b + B - 1) / B : 0;
+}
+
+// Per-segment outer-node values: L_j = e^t_j and G_j = (half-width) w_j g(e^t_j) e^t_j on
+// t in [ln L_low, ln L* + ln_upper], and the first inner node of the segment.
+__device__ __forceinline__ void lf_segment_rows(const ThetaC& tc, const SweepArgs& a, int b, int B, int nseg,
+                                                double* sL, double* sG, int* sK) {
   const double lo = tc.a3, hi = tc.a1 + a.mc.ln_upper;
   const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
-  for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
-    const long long j = j0 + r;
-    if (j >= a.nL) break;
-    const double t = fma(half, __ldg(a.xL + j), mid);
-    const double x = t - tc.a1;
-    sL[r] = exp(t);
-    sG[r] = half * __ldg(a.wL + j) * exp(fma(tc.a0, x, -exp(x)));
+  for (int t = threadIdx.x; t < nseg; t += blockDim.x) {
+    const int g = b + t * B;
+    const int j = g % a.nL;
+    const double tt = fma(half, __ldg(a.xL + j), mid);
+    const double x = tt - tc.a1;
+    sL[t] = exp(tt);
+    sG[t] = half * __ldg(a.wL + j) * exp(fma(tc.a0, x, -exp(x)));
+    sK[t] = (g / a.nL) << kSegShift;
   }
 }
 
-// Pairs [pb0, pb1) of the flattened (outer j, inner k) rule; this thread takes every
-// blockDim-th pair. Each term G_j W_k Phi((L_j q_k - F_th)/sigma_F) is added exactly.
-__device__ __forceinline__ void lf_pairs(const SweepArgs& a, unsigned int pb0, unsigned int pb1, long long j0,
-                                         const double* sL, const double* sG, Xacc& xe, XFlags& fe) {
-  const unsigned int nr = static_cast<unsigned int>(a.nr);
+// Pairs of this block's segments; each term G_j W_k Phi((L_j q_k - F_th)/sigma_F) is added exactly.
+__device__ __forceinline__ void lf_segment_pairs(const SweepArgs& a, int nseg, const double* sL, const double* sG,
+                                                 const int* sK, const double* s_phi, Xacc& xe, XFlags& fe) {
+  const int total = nseg << kSegShift;
   const double mcth = -a.mc.cth;
-  for (unsigned int idx = pb0 + threadIdx.x; idx < pb1; idx += blockDim.x) {
-    const unsigned int j = idx / nr;
-    const unsigned int k = idx - j * nr;
-    const int r = static_cast<int>(static_cast<long long>(j) - j0);
-    const double x = fma(sL[r], __ldg(a.qs + k), mcth);
-    // Phi(x) = erfc(-x/sqrt 2)/2; above x = 8.5 erfc(-x/sqrt 2) rounds to 2 exactly
-    const double phi = (x > 8.5) ? 1.0 : 0.5 * erfc(-x * 0.70710678118654752440);
-    xacc_add_double(xe, sG[r] * (__ldg(a.Wr + k) * phi), fe);
+  for (int q = threadIdx.x; q < total; q += blockDim.x) {
+    const int t = q >> kSegShift;
+    const int k = sK[t] + (q & (kSeg - 1));
+    if (k < a.nr) {
+      const double x = fma(sL[t], __ldg(a.qs + k), mcth);
+      xacc_add_double(xe, sG[t] * (__ldg(a.Wr + k) * phi_table(x, s_phi)), fe);
+    }
   }
-}
-
-__device__ __forceinline__ void pair_range(long long P, int b, int B, unsigned int& pb0, unsigned int& pb1) {
-  pb0 = static_cast<unsigned int>((P * b) / B);
-  pb1 = static_cast<unsigned int>((P * (b + 1)) / B);
 }
 
 // ------------------------------------------------- block reduce helpers ------
@@ -171,99 +247,140 @@ __device__ __forceinline__ void warp_reduce(Xacc& d, Xacc& e, unsigned int f[4])
 }
 
 // ---------------------------------------------------------------- kernel -----
+// Work that only the next theta proposal needs (the S_theta RAM update of the previous sweep,
+// theta' = theta + S_theta U, its prior and constants, the rule's outer-node values at theta')
+// runs on the last warp while every warp does its member steps; only the accept decision
+// itself sits between the grid barrier and the next member phase.
+template <class M>
+__device__ __forceinline__ void propose_theta(const SweepArgs& a, long long s, int p, const double* theta, double* Sth,
+                                              double* thp, double& lpri_new, ThetaC& tcp) {
+  for (int q = 0; q < p; ++q) {
+    double t = theta[q];
+    for (int b = 0; b <= q; ++b) t = fma(Sth[q * p + b], __ldg(a.tab_U + s * p + b), t);
+    thp[q] = t;
+  }
+  lpri_new = M::logprior(thp, a.mc);
+  tcp = M::consts(thp);
+}
+
 template <class M, int K>
-__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
-  extern __shared__ double s_rows[];  // [2][rows_smem]: L_j then G_j
+__global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
+  // dynamic shared memory: [mpb] y, [mpb] aux of this block's members, then the rule segment
+  // values [rows_smem] L_j, [rows_smem] G_j, [rows_smem] int first inner node
+  extern __shared__ double s_dyn[];
   __shared__ double s_theta[kMaxP], s_thp[kMaxP], s_Sth[kMaxP * kMaxP];
   __shared__ ThetaC s_tc, s_tcp;
-  __shared__ double s_etabar, s_lpri, s_lpri_new;
-  __shared__ int s_prior_ok, s_stop;
+  __shared__ double s_etabar, s_logeb, s_lpri, s_lpri_new, s_logalpha_prev;
+  __shared__ int s_stop, s_pending_ram;
   __shared__ long long s_rows_written, s_tacc;
   __shared__ BlockRed s_red;
 
   const int tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int ctrl_warp = (blockDim.x >> 5) - 1;  // the warp that runs the deferred theta work
   const int p = a.p;
-  const long long G = static_cast<long long>(gridDim.x) * blockDim.x;
-  const long long gtid = static_cast<long long>(blockIdx.x) * blockDim.x + tid;
+  // members of this block: the contiguous range [nb0, nb1), equal sizes to within one
+  const unsigned int nb0 = static_cast<unsigned int>((a.n * blockIdx.x) / gridDim.x);
+  const unsigned int nb1 = static_cast<unsigned int>((a.n * (blockIdx.x + 1)) / gridDim.x);
   const bool skip_me = (a.skip_cta == static_cast<int>(blockIdx.x));
+  const bool is_lf = (a.model == CUDAHM_LF);
+  double* s_phi = s_dyn;  // [kPhiWords] for LF, else empty
+  double* s_y = s_dyn + (is_lf ? kPhiWords : 0);
+  double* s_aux = s_y + a.mpb;
+  double* s_rows = s_y + 2 * a.mpb;
+  for (unsigned int q = tid; q < nb1 - nb0; q += blockDim.x) {
+    s_y[q] = a.y[nb0 + q];
+    s_aux[q] = a.aux[nb0 + q];
+  }
+  if (is_lf)
+    for (int q = tid; q < kPhiWords; q += blockDim.x) s_phi[q] = a.phi_coef[q];
+  const int nseg = is_lf ? lf_block_segments(a, blockIdx.x, gridDim.x) : 0;
+  double* sL = s_rows;
+  double* sG = s_rows + a.rows_smem;
+  int* sK = reinterpret_cast<int*>(s_rows + 2 * a.rows_smem);
 
   if (tid == 0) {
     for (int q = 0; q < p; ++q) s_theta[q] = a.chain->theta[q];
     for (int q = 0; q < p * p; ++q) s_Sth[q] = a.chain->S_theta[q];
     s_etabar = a.chain->etabar;
+    s_logeb = is_lf ? log(s_etabar) : 0.0;
     s_tc = M::consts(s_theta);
     s_lpri = M::logprior(s_theta, a.mc);
     s_rows_written = 0;
     s_tacc = 0;
     s_stop = 0;
+    s_pending_ram = 0;
+    s_logalpha_prev = 0.0;
+    double lp;
+    ThetaC tcp;
+    propose_theta<M>(a, 0, p, s_theta, s_Sth, s_thp, lp, tcp);
+    s_lpri_new = lp;
+    s_tcp = tcp;
   }
+  __syncthreads();
+  if (is_lf && s_lpri_new != -INFINITY) lf_segment_rows(s_tcp, a, blockIdx.x, gridDim.x, nseg, sL, sG, sK);
 
-  // members of this thread: i = gtid + m G
-  double chi[K], S[K], echi[K], ll[K], yv[K], av[K];
+  // members of this thread: i = nb0 + tid + m blockDim (latent, RAM factor, e^chi, log l in registers)
+  double chi[K], S[K], echi[K], ll[K];
 #pragma unroll
   for (int m = 0; m < K; ++m) {
-    const long long i = gtid + m * G;
-    if (i < a.n) {
+    const unsigned int i = nb0 + tid + m * blockDim.x;
+    if (i < nb1) {
       chi[m] = a.chi[i];
       S[m] = a.S[i];
-      yv[m] = a.y[i];
-      av[m] = a.aux[i];
       echi[m] = M::kExp ? exp(chi[m]) : 0.0;
-      ll[m] = M::loglike(chi[m], echi[m], yv[m], av[m], a.mc);
+      ll[m] = M::loglike(chi[m], echi[m], a.y[i], a.aux[i], a.mc);
     } else {
-      chi[m] = S[m] = echi[m] = ll[m] = yv[m] = av[m] = 0.0;
+      chi[m] = S[m] = echi[m] = ll[m] = 0.0;
     }
   }
   unsigned int member_acc = 0;
-
-  // LF rule share of this block
-  const bool is_lf = (a.model == CUDAHM_LF);
-  const long long P = static_cast<long long>(a.nL) * a.nr;
-  unsigned int pb0 = 0, pb1 = 0;
-  long long j0 = 0;
-  int nrows = 0;
-  if (is_lf) {
-    pair_range(P, blockIdx.x, gridDim.x, pb0, pb1);
-    if (pb1 > pb0) {
-      j0 = pb0 / a.nr;
-      nrows = static_cast<int>((pb1 - 1) / a.nr - j0 + 1);
-    }
-  }
-  double* sL = s_rows;
-  double* sG = s_rows + a.rows_smem;
   __syncthreads();
 
   for (long long s = 0; s < a.ns; ++s) {
     const uint32_t k = static_cast<uint32_t>(a.k0 + s + 1);
     const double eta = __ldg(a.tab_eta + s);
-    // a0: theta proposal (same arithmetic in every block)
-    if (tid == 0) {
-      for (int q = 0; q < p; ++q) {
-        double t = s_theta[q];
-        for (int b = 0; b <= q; ++b) t = fma(s_Sth[q * p + b], __ldg(a.tab_U + s * p + b), t);
-        s_thp[q] = t;
-      }
-      s_lpri_new = M::logprior(s_thp, a.mc);
-      s_prior_ok = (s_lpri_new != -INFINITY);
-      s_tcp = M::consts(s_thp);
-    }
-    __syncthreads();
-    const ThetaC tc = s_tc, tcp = s_tcp;
-    const bool prior_ok = s_prior_ok != 0;
-    if (is_lf && prior_ok) lf_rows(tcp, a, j0, nrows, sL, sG);
-
+    const ThetaC tc = s_tc;
     const bool trace = (a.trace_off + s) < a.trace_T;
-    Xacc xd, xe;
-    xacc_zero(xd);
-    xacc_zero(xe);
-    XFlags fd = {0u, 0u, 0u}, fe = {0u, 0u, 0u};
-    unsigned int member_nan = 0, neg_big = 0, pos_big = 0;
+    unsigned int member_nan = 0;
 
-    // a1-a4: member RAM steps under theta, then the theta' partial
+    // deferred theta work of the previous sweep and the proposal of this one (last warp)
+    if (s > 0 && wid == ctrl_warp) {
+      if (lane == 0) {
+        if (s_pending_ram) {
+          const double lal = s_logalpha_prev;
+          const double alpha = (lal >= 0.0) ? 1.0 : exp(lal);
+          ram_update_theta(p, s_Sth, a.tab_U + (s - 1) * p, alpha, a.astar_theta, __ldg(a.tab_eta + s - 1));
+        }
+        double lp;
+        ThetaC tcp;
+        propose_theta<M>(a, s, p, s_theta, s_Sth, s_thp, lp, tcp);
+        s_lpri_new = lp;
+        s_tcp = tcp;
+      }
+      __syncwarp();
+      if (is_lf && s_lpri_new != -INFINITY) {
+        const ThetaC tcp = s_tcp;
+        const double lo = tcp.a3, hi = tcp.a1 + a.mc.ln_upper;
+        const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+        for (int t = lane; t < nseg; t += 32) {
+          const int g = blockIdx.x + t * gridDim.x;
+          const int j = g % a.nL;
+          const double tt = fma(half, __ldg(a.xL + j), mid);
+          const double x = tt - tcp.a1;
+          sL[t] = exp(tt);
+          sG[t] = half * __ldg(a.wL + j) * exp(fma(tcp.a0, x, -exp(x)));
+          sK[t] = (g / a.nL) << kSegShift;
+        }
+      }
+    }
+
+    // a1-a3: member RAM steps under theta
 #pragma unroll
     for (int m = 0; m < K; ++m) {
-      const long long i = gtid + m * G;
-      if (i < a.n) {
+      const unsigned int i = nb0 + tid + m * blockDim.x;
+      if (i < nb1) {
+        const double yv = s_y[i - nb0], av = s_aux[i - nb0];
         const uint4 w0 = philox4x32_10(make_uint4(0u, 0u, static_cast<uint32_t>(i), k), a.key0, a.key1);
         const uint4 w1 = philox4x32_10(make_uint4(1u, 0u, static_cast<uint32_t>(i), k), a.key0, a.key1);
         const double ua = uniform53(w0.x, w0.y), ub = uniform53(w0.z, w0.w);
@@ -275,7 +392,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
           delta = -INFINITY;
         } else {
           eY = M::kExp ? exp(Y) : 0.0;
-          llY = M::loglike(Y, eY, yv[m], av[m], a.mc);
+          llY = M::loglike(Y, eY, yv, av, a.mc);
           const double lpY = llY + M::logf(Y, eY, tc);
           const double lpX = ll[m] + M::logf(chi[m], echi[m], tc);
           delta = lpY - lpX;
@@ -291,12 +408,28 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
         }
         S[m] *= sqrt(fma(eta, alpha - a.astar, 1.0));
         if (trace) {
-          const long long o = (a.trace_off + s) * a.n + i;
+          const long long o = (a.trace_off + s) * a.n + static_cast<long long>(i);
           a.tr_delta[o] = delta;
           a.tr_u[o] = u;
           a.tr_acc[o] = acc ? 1 : 0;
         }
-        if (prior_ok) {
+      }
+    }
+    __syncthreads();  // theta' and the rule rows are ready
+
+    // a4: theta' partial; a6: selection integral at theta'
+    const ThetaC tcp = s_tcp;
+    const bool prior_ok = (s_lpri_new != -INFINITY);
+    Xacc xd, xe;
+    xacc_zero(xd);
+    xacc_zero(xe);
+    XFlags fd = {0u, 0u, 0u}, fe = {0u, 0u, 0u};
+    unsigned int neg_big = 0, pos_big = 0;
+    if (prior_ok) {
+#pragma unroll
+      for (int m = 0; m < K; ++m) {
+        const unsigned int i = nb0 + tid + m * blockDim.x;
+        if (i < nb1) {
           const double dn = M::support(chi[m], tcp) ? M::logf(chi[m], echi[m], tcp) - M::logf(chi[m], echi[m], tc)
                                                    : -INFINITY;
           if (dn <= -0x1p94) neg_big++;       // off the support of theta' (-inf) or hopeless
@@ -304,11 +437,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
           else xacc_add_double(xd, dn, fd);   // counts NaN in fd.nan
         }
       }
-    }
-    // a6: LF selection integral at theta'
-    if (is_lf && prior_ok) {
-      __syncthreads();  // rows ready
-      lf_pairs(a, pb0, pb1, j0, sL, sG, xe, fe);
+      if (is_lf) lf_segment_pairs(a, nseg, sL, sG, sK, s_phi, xe, fe);
     }
 
     // a5: block partial
@@ -316,7 +445,6 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
       // f[0]: d_i <= -2^94 (reject), f[1]: NaN anywhere (error), f[2]: d_i >= 2^94, f[3]: member NaN
       unsigned int f[4] = {neg_big, fd.nan + fe.nan + fe.big + member_nan, pos_big, member_nan};
       warp_reduce(xd, xe, f);
-      const int lane = tid & 31, wid = tid >> 5;
       if (lane == 0) {
         s_red.d[wid] = xd;
         s_red.e[wid] = xe;
@@ -351,12 +479,12 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
     if (!grid_barrier(a.bar, static_cast<unsigned int>(s), a.err, a.timeout_ns, skip_me)) return;
 
     // a7: every block sums all partials and takes the same decision
-    if (tid < 32) {
+    if (wid == 0) {
       Xacc D, E;
       xacc_zero(D);
       xacc_zero(E);
       unsigned int f[4] = {0u, 0u, 0u, 0u};
-      for (int b = tid; b < static_cast<int>(gridDim.x); b += 32) {
+      for (int b = lane; b < static_cast<int>(gridDim.x); b += 32) {
         const unsigned long long* src = a.partials + ((s & 1) * gridDim.x + b) * kPartWords;
         Xacc t;
         t.w0 = __ldcg(src + 0);
@@ -374,13 +502,13 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
         f[3] += static_cast<unsigned int>(f23 >> 32);
       }
       warp_reduce(D, E, f);
-      if (tid == 0) {
+      if (lane == 0) {
         const long long sg = a.trace_off + s;  // sweep index within this run
         if (f[1] != 0u) {
           atomicCAS(a.err, 0, CUDAHM_ENUMERIC);
           s_stop = 1;
         } else {
-          double logalpha, Drec, eb_new = 0.0;
+          double logalpha, Drec, eb_new = 0.0, logeb_new = 0.0;
           if (!prior_ok) {
             logalpha = -INFINITY;
             Drec = 0.0;
@@ -396,17 +524,17 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
             logalpha = Drec + nn * (M::cterm(s_thp) - M::cterm(s_theta)) + s_lpri_new - s_lpri;
             if (is_lf) {
               eb_new = xacc_to_double(E);
-              logalpha -= nn * (log(eb_new) - log(s_etabar));
+              logeb_new = log(eb_new);
+              logalpha -= nn * (logeb_new - s_logeb);
             }
           }
-          const double ut = __ldg(a.tab_u + s);
-          const double alpha = (logalpha >= 0.0) ? 1.0 : exp(logalpha);
-          const bool acc = (logalpha >= 0.0) || (ut < alpha);
+          const double lnut = __ldg(a.tab_lnu + s);
+          const bool acc = lnut < logalpha;
           if (blockIdx.x == 0 && sg < a.trace_T) {
             for (int q = 0; q < p; ++q) a.tr_thprop[sg * p + q] = s_thp[q];
             a.tr_D[sg] = Drec;
             a.tr_logalpha[sg] = logalpha;
-            a.tr_ut[sg] = ut;
+            a.tr_ut[sg] = __ldg(a.tab_u + s);
             a.tr_tacc[sg] = acc ? 1 : 0;
             a.tr_eb[sg] = eb_new;
           }
@@ -414,10 +542,14 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
             for (int q = 0; q < p; ++q) s_theta[q] = s_thp[q];
             s_tc = s_tcp;
             s_lpri = s_lpri_new;
-            if (is_lf) s_etabar = eb_new;
+            if (is_lf) {
+              s_etabar = eb_new;
+              s_logeb = logeb_new;
+            }
             s_tacc++;
           }
-          if (a.adapt_theta) ram_update_theta(p, s_Sth, a.tab_U + s * p, alpha, a.astar_theta, eta);
+          s_logalpha_prev = logalpha;
+          s_pending_ram = a.adapt_theta;
           // a8: record kept sweeps
           const long long post = s - a.burn_left;
           if (post >= 0 && a.thin > 0 && ((a.keep_phase + post + 1) % a.thin) == 0) {
@@ -435,8 +567,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
   // write back (only reached when every sweep succeeded)
 #pragma unroll
   for (int m = 0; m < K; ++m) {
-    const long long i = gtid + m * G;
-    if (i < a.n) {
+    const unsigned int i = nb0 + tid + m * blockDim.x;
+    if (i < nb1) {
       a.chi[i] = chi[m];
       a.S[i] = S[m];
     }
@@ -449,6 +581,11 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
   if (tid == 0) {
     atomicAdd(reinterpret_cast<unsigned long long*>(&a.chain->member_acc), static_cast<unsigned long long>(s_macc));
     if (blockIdx.x == 0) {
+      if (s_pending_ram && a.ns > 0) {  // RAM update of the last sweep's theta step
+        const double lal = s_logalpha_prev;
+        const double alpha = (lal >= 0.0) ? 1.0 : exp(lal);
+        ram_update_theta(p, s_Sth, a.tab_U + (a.ns - 1) * p, alpha, a.astar_theta, __ldg(a.tab_eta + a.ns - 1));
+      }
       for (int q = 0; q < p; ++q) a.chain->theta[q] = s_theta[q];
       for (int q = 0; q < p * p; ++q) a.chain->S_theta[q] = s_Sth[q];
       a.chain->etabar = s_etabar;
@@ -460,17 +597,27 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a) {
 }
 
 template <class M>
+static const void* kernel_for(int K) {
+  switch (K) {
+    case 1: return reinterpret_cast<const void*>(&sweep_kernel<M, 1>);
+    case 2: return reinterpret_cast<const void*>(&sweep_kernel<M, 2>);
+    case 4: return reinterpret_cast<const void*>(&sweep_kernel<M, 4>);
+    case 8: return reinterpret_cast<const void*>(&sweep_kernel<M, 8>);
+    default: return nullptr;
+  }
+}
+
+size_t sweep_smem_bytes(int model, int mpb, int rows_smem) {
+  return (model == CUDAHM_LF ? sizeof(double) * kPhiWords : 0) + 2 * sizeof(double) * static_cast<size_t>(mpb) +
+         (2 * sizeof(double) + sizeof(int)) * rows_smem;
+}
+
+template <class M>
 static cudaError_t launch_model(const SweepArgs& a, int K, int grid, int block, cudaStream_t st) {
   void* args[] = {const_cast<SweepArgs*>(&a)};
-  const size_t smem = 2 * sizeof(double) * static_cast<size_t>(a.rows_smem);
-  const void* fn;
-  switch (K) {
-    case 1: fn = reinterpret_cast<const void*>(&sweep_kernel<M, 1>); break;
-    case 2: fn = reinterpret_cast<const void*>(&sweep_kernel<M, 2>); break;
-    case 4: fn = reinterpret_cast<const void*>(&sweep_kernel<M, 4>); break;
-    case 8: fn = reinterpret_cast<const void*>(&sweep_kernel<M, 8>); break;
-    default: return cudaErrorInvalidValue;
-  }
+  const size_t smem = sweep_smem_bytes(a.model, a.mpb, a.rows_smem);
+  const void* fn = kernel_for<M>(K);
+  if (!fn) return cudaErrorInvalidValue;
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
 }
 
@@ -480,23 +627,26 @@ cudaError_t launch_sweep(const SweepArgs& a, int K, int grid, int block, cudaStr
   return cudaErrorInvalidValue;
 }
 
-template <class M>
-static cudaError_t occ_model(int K, int block, int smem, int* bps) {
-  const void* fn;
-  switch (K) {
-    case 1: fn = reinterpret_cast<const void*>(&sweep_kernel<M, 1>); break;
-    case 2: fn = reinterpret_cast<const void*>(&sweep_kernel<M, 2>); break;
-    case 4: fn = reinterpret_cast<const void*>(&sweep_kernel<M, 4>); break;
-    case 8: fn = reinterpret_cast<const void*>(&sweep_kernel<M, 8>); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fn, block, smem);
+static const void* sweep_fn(int model, int K) {
+  if (model == CUDAHM_NN1) return kernel_for<NN1>(K);
+  if (model == CUDAHM_LF) return kernel_for<LF>(K);
+  return nullptr;
+}
+
+cudaError_t sweep_set_smem(int model, int K, int smem_bytes) {
+  const void* fn = sweep_fn(model, K);
+  if (!fn) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
 }
 
 cudaError_t sweep_occupancy(int model, int K, int block, int smem_bytes, int* blocks_per_sm) {
-  if (model == CUDAHM_NN1) return occ_model<NN1>(K, block, smem_bytes, blocks_per_sm);
-  if (model == CUDAHM_LF) return occ_model<LF>(K, block, smem_bytes, blocks_per_sm);
-  return cudaErrorInvalidValue;
+  const void* fn = sweep_fn(model, K);
+  if (!fn) return cudaErrorInvalidValue;
+  if (smem_bytes > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem_bytes);
 }
 
 // --------------------------------------------------------- set-up kernels ----
@@ -628,7 +778,7 @@ cudaError_t launch_lf_inner(int nr, const double* xr, const double* wr, double r
 // Per-sweep theta tables: p normals (Philox stream 1, member index 0, sweep k; block j gives
 // normals 2j, 2j+1), the accept uniform (first uniform of block ceil(p/2)), eta = (k+1)^-gamma.
 __global__ void tables_kernel(int p, uint32_t key0, uint32_t key1, long long k0, long long ns, double gamma,
-                              double* U, double* u, double* eta) {
+                              double* U, double* u, double* lnu, double* eta) {
   const long long s = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (s >= ns) return;
   const uint32_t k = static_cast<uint32_t>(k0 + s + 1);
@@ -644,14 +794,15 @@ __global__ void tables_kernel(int p, uint32_t key0, uint32_t key1, long long k0,
   }
   const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(nblk), 1u, 0u, k), key0, key1);
   u[s] = uniform53(w.x, w.y);
+  lnu[s] = log(u[s]);
   eta[s] = pow(static_cast<double>(k) + 1.0, -gamma);
 }
 
 cudaError_t launch_tables(int p, uint32_t key0, uint32_t key1, long long k0, long long ns, double gamma, double* U,
-                          double* u, double* eta, cudaStream_t st) {
+                          double* u, double* lnu, double* eta, cudaStream_t st) {
   const int blk = 128;
   tables_kernel<<<static_cast<unsigned int>((ns + blk - 1) / blk), blk, 0, st>>>(p, key0, key1, k0, ns, gamma, U, u,
-                                                                                 eta);
+                                                                                 lnu, eta);
   return cudaGetLastError();
 }
 
@@ -695,24 +846,19 @@ __global__ void etabar_partial_kernel(const double* theta, const SweepArgs a, un
     s_tc = LF::consts(th);
   }
   __syncthreads();
-  const long long P = static_cast<long long>(a.nL) * a.nr;
-  unsigned int pb0, pb1;
-  pair_range(P, blockIdx.x, gridDim.x, pb0, pb1);
-  long long j0 = 0;
-  int nrows = 0;
-  if (pb1 > pb0) {
-    j0 = pb0 / a.nr;
-    nrows = static_cast<int>((pb1 - 1) / a.nr - j0 + 1);
-  }
-  double* sL = s_rows;
-  double* sG = s_rows + a.rows_smem;
-  lf_rows(s_tc, a, j0, nrows, sL, sG);
+  const int nseg = lf_block_segments(a, blockIdx.x, gridDim.x);
+  double* s_phi = s_rows;
+  double* sL = s_rows + kPhiWords;
+  double* sG = sL + a.rows_smem;
+  int* sK = reinterpret_cast<int*>(sG + a.rows_smem);
+  for (int q = threadIdx.x; q < kPhiWords; q += blockDim.x) s_phi[q] = a.phi_coef[q];
+  lf_segment_rows(s_tc, a, blockIdx.x, gridDim.x, nseg, sL, sG, sK);
   __syncthreads();
   Xacc xd, xe;
   xacc_zero(xd);
   xacc_zero(xe);
   XFlags fe = {0u, 0u, 0u};
-  lf_pairs(a, pb0, pb1, j0, sL, sG, xe, fe);
+  lf_segment_pairs(a, nseg, sL, sG, sK, s_phi, xe, fe);
   unsigned int f[4] = {0u, fe.nan, fe.big, 0u};
   warp_reduce(xd, xe, f);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -760,7 +906,7 @@ __global__ void etabar_final_kernel(const unsigned long long* partials, int nblo
 
 cudaError_t launch_eval_etabar(const double* theta_dev, const SweepArgs& rule, unsigned long long* partials,
                                int grid, double* out, cudaStream_t st) {
-  const size_t smem = 2 * sizeof(double) * static_cast<size_t>(rule.rows_smem);
+  const size_t smem = sizeof(double) * kPhiWords + (2 * sizeof(double) + sizeof(int)) * static_cast<size_t>(rule.rows_smem);
   etabar_partial_kernel<<<grid, 256, smem, st>>>(theta_dev, rule, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -88,7 +88,7 @@ _lib = None
 EXPORTED = [
     "cudahm_config_init", "cudahm_create", "cudahm_set_data", "cudahm_set_data_device", "cudahm_set_chi",
     "cudahm_run", "cudahm_get_samples", "cudahm_get_chi", "cudahm_get_theta", "cudahm_get_stats",
-    "cudahm_eval_logdens", "cudahm_eval_etabar", "cudahm_get_trace", "cudahm_checkpoint", "cudahm_restore",
+    "cudahm_eval_logdens", "cudahm_eval_etabar", "cudahm_eval_detection", "cudahm_get_trace", "cudahm_checkpoint", "cudahm_restore",
     "cudahm_sizeof_config", "cudahm_sizeof_stats", "cudahm_last_error", "cudahm_destroy",
 ]
 
@@ -115,6 +115,7 @@ def lib():
     L.cudahm_get_stats.argtypes = [vp, ctypes.POINTER(CudahmStats)]
     L.cudahm_eval_logdens.argtypes = [vp, _dp, _dp]
     L.cudahm_eval_etabar.argtypes = [vp, _dp, _dp]
+    L.cudahm_eval_detection.argtypes = [vp, _dp, _dp, i64]
     L.cudahm_get_trace.argtypes = [vp, _dp, _dp, _u8p, _dp, _dp, _dp, _dp, _u8p, _dp, ctypes.POINTER(i64)]
     L.cudahm_checkpoint.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     L.cudahm_restore.argtypes = [vp, vp, ctypes.c_size_t]
@@ -220,6 +221,13 @@ def cudahm_eval_etabar(h, theta) -> float:
     out = np.zeros(1)
     _check(lib().cudahm_eval_etabar(h, _dptr(th), _dptr(out)))
     return float(out[0])
+
+
+def cudahm_eval_detection(h, F) -> np.ndarray:
+    F = _f64(F)
+    out = np.zeros(F.size)
+    _check(lib().cudahm_eval_detection(h, _dptr(F), _dptr(out), F.size))
+    return out
 
 
 def cudahm_get_trace(h, n: int, p: int, T: int):
@@ -355,6 +363,9 @@ class Sampler:
 
     def etabar(self, theta) -> float:
         return cudahm_eval_etabar(self.h, theta)
+
+    def detection(self, F) -> np.ndarray:
+        return cudahm_eval_detection(self.h, F)
 
     def trace(self, T: int):
         return cudahm_get_trace(self.h, self.n, self.p, T)

@@ -141,6 +141,22 @@ def test_lf_etabar_matches_oracle_rule():
         assert abs(g - o) <= 1e-13 * o, (th, g, o, (g - o) / o)
 
 
+def test_detection_efficiency_table_matches_oracle():
+    """The device's normal-CDF table (local Taylor series) against the oracle's erfc-based Phi,
+    on a dense grid, at interval centres and edges, and at the ends of the table."""
+    consts = oracle.lf_consts(2.0, 10.0, 4000.0, 8, 8)
+    s = cudahm.Sampler(cudahm.LF, 1, theta_init=[-1.2, 23.0, 18.4], theta_prop_scale=[0.01] * 3,
+                       model_consts=consts)
+    c = np.arange(133) / 8.0 - 8.0
+    x = np.concatenate([np.linspace(-12.0, 12.0, 200_001), c, c + 1 / 16, c - 1 / 16,
+                        [-8.0, -8.0 - 1e-12, 8.5, 8.5 + 1e-12, 0.0, -1e-300, 1e-300]])
+    F = 10.0 + 2.0 * x
+    got = s.detection(F)
+    ref = oracle.lf_detection(F, consts)
+    err = np.abs(got - ref)
+    assert np.all(err <= 2.5e-16 + 2e-15 * ref), (x[np.argmax(err)], err.max())
+
+
 def test_lf_full_size_lockstep_n300000():
     """The benchmark workload (N = 3e5 detected objects, 1024 x 1024 rule) in the benchmark's launch
     shape, 6 sweeps in lockstep with the oracle over every member."""

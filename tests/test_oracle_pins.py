@@ -182,6 +182,17 @@ def _lf_consts(nL=1024, nr=1024, sigF=2.0, Fth=10.0, rmax=4000.0):
     return oracle.lf_consts(sigF, Fth, rmax, nL, nr)
 
 
+def test_detection_efficiency_is_normal_cdf():
+    """eta(F) = Phi((F - F_th)/sigma_F) against scipy's ndtr (Cephes), across the whole range."""
+    sigF, Fth = 2.0, 10.0
+    c = _lf_consts(sigF=sigF, Fth=Fth)
+    x = np.concatenate([np.linspace(-12, 12, 4001), [-38.0, 0.0, 8.5, 40.0]])
+    F = Fth + sigF * x
+    got = oracle.lf_detection(F, c)
+    ref = scipy.special.ndtr((F - Fth) / sigF)
+    assert np.all(np.abs(got - ref) <= 2e-16 + 1e-14 * ref)
+
+
 def test_H_normalisation_all_detected():
     """When every distance gives a certain detection, H(L) = int h(r) dr = 1 (h ~ 3r^2/r_max^3)."""
     c = _lf_consts()
