@@ -189,6 +189,29 @@ int cudahm_get_trace(cudahm_t h, double* delta, double* u, uint8_t* acc, double*
 int cudahm_checkpoint(cudahm_t h, void* buf, size_t cap, size_t* used);
 int cudahm_restore(cudahm_t h, const void* buf, size_t size);
 
+/* LF selection integral etabar(theta) that allocates no device memory. The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc when they need the value
+ * (a process that gives all device memory to its own pool up front and forbids later
+ * allocations, a latency-critical loop that must not pay for the synchronisation an
+ * allocation implies, a caller that is out of device memory). The tables and partial sums
+ * live in one fixed array compiled into the library (about 94 KB on every GPU that loads
+ * it, held until the process exits), which bounds the rule to
+ * n_L, n_r <= CUDAHM_NOALLOC_MAX_NODES.
+ *   theta_dev    3 doubles on the current device: (beta, ln L*, ln L_low)
+ *   consts_host  6 doubles on the host: sigma_F, F_th, r_max, n_L, n_r, ln(upper/L*)
+ *   etabar_dev   1 double on the current device: receives etabar(theta)
+ *   cuda_stream  cudaStream_t to enqueue on (NULL = the default stream); the call returns
+ *                once the work is enqueued; read the result after synchronising.
+ * Returns EINVAL (with a message) for rule sizes above the limit or bad constants. The
+ * value equals cudahm_eval_etabar's for the same theta and constants. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, once per device, with
+ * that device current); make that first call before any stream capture. Every call on a
+ * device shares the array and it keeps the last call's contents (nothing in it must start
+ * at zero: each call rewrites all it reads); calls that overlap on the GPU race on it. */
+#define CUDAHM_NOALLOC_MAX_NODES 1024
+int cudahm_lf_etabar_noalloc(const double* theta_dev, const double* consts_host, double* etabar_dev,
+                             void* cuda_stream);
+
 /* sizeof(cudahm_config) and sizeof(cudahm_stats) as compiled into the library, so that
  * bindings can check their struct layouts. */
 size_t cudahm_sizeof_config(void);

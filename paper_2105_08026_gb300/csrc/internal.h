@@ -80,6 +80,9 @@ struct SweepArgs {
   int skip_cta;
 };
 
+// Records a failure for cudahm_last_error() (runtime.cu); returns code.
+int record_error(int code, const char* msg);
+
 // Kernel launch helpers (sweep.cu). Return cudaError_t of the launch.
 cudaError_t launch_sweep(const SweepArgs& a, int K, int grid, int block, cudaStream_t st);
 cudaError_t sweep_occupancy(int model, int K, int block, int smem_bytes, int* blocks_per_sm);

@@ -37,6 +37,13 @@ int fail(int code, const char* fmt, ...) {
   } while (0)
 
 int model_d(int m) { return m == CUDAHM_MVN3 ? 3 : 1; }
+
+}  // namespace
+
+int chm::record_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+namespace {
+
 int model_p(int m) { return m == CUDAHM_NN1 ? 2 : (m == CUDAHM_LF ? 3 : 9); }
 
 constexpr long long kChunk = 4096;  // sweeps per persistent launch

@@ -90,6 +90,7 @@ EXPORTED = [
     "cudahm_run", "cudahm_get_samples", "cudahm_get_chi", "cudahm_get_theta", "cudahm_get_stats",
     "cudahm_eval_logdens", "cudahm_eval_etabar", "cudahm_eval_detection", "cudahm_get_trace", "cudahm_checkpoint", "cudahm_restore",
     "cudahm_sizeof_config", "cudahm_sizeof_stats", "cudahm_last_error", "cudahm_destroy",
+    "cudahm_lf_etabar_noalloc",
 ]
 
 
@@ -122,6 +123,7 @@ def lib():
     L.cudahm_sizeof_config.restype = ctypes.c_size_t
     L.cudahm_sizeof_stats.restype = ctypes.c_size_t
     L.cudahm_last_error.restype = ctypes.c_char_p
+    L.cudahm_lf_etabar_noalloc.argtypes = [vp, _dp, vp, vp]
     L.cudahm_destroy.argtypes = [vp]
     L.cudahm_destroy.restype = None
     for name in EXPORTED:
@@ -228,6 +230,14 @@ def cudahm_eval_detection(h, F) -> np.ndarray:
     out = np.zeros(F.size)
     _check(lib().cudahm_eval_detection(h, _dptr(F), _dptr(out), F.size))
     return out
+
+
+def cudahm_lf_etabar_noalloc(theta_dev_ptr: int, consts, etabar_dev_ptr: int, stream_ptr: int = 0):
+    """Selection integral into caller-owned device memory, with no device allocation
+    (theta_dev_ptr: 3 doubles, etabar_dev_ptr: 1 double, both on the current device)."""
+    c = _f64(consts)
+    _check(lib().cudahm_lf_etabar_noalloc(ctypes.c_void_p(theta_dev_ptr), _dptr(c), ctypes.c_void_p(etabar_dev_ptr),
+                                          ctypes.c_void_p(stream_ptr) if stream_ptr else None))
 
 
 def cudahm_get_trace(h, n: int, p: int, T: int):
