@@ -61,6 +61,7 @@ struct SweepArgs {
   const double* qs;  // q(r_k)/sigma_F
   const double* Wr;  // inner weights
   const double* phi_coef;  // Taylor table of the normal CDF
+  const double* math_tab;  // exp/log tables
   int nL, nr;
   int rows_smem;     // segment slots per block for the outer-node values
   int mpb;           // members of the largest block (shared-memory slots for y, aux)
@@ -88,6 +89,8 @@ cudaError_t launch_sweep(const SweepArgs& a, int K, int grid, int block, cudaStr
 cudaError_t sweep_occupancy(int model, int K, int block, int smem_bytes, int* blocks_per_sm);
 size_t sweep_smem_bytes(int model, int mpb, int rows_smem);
 cudaError_t launch_phi_table(double* coef, cudaStream_t st);
+cudaError_t launch_math_table(double* t, cudaStream_t st);
+int math_table_words();
 int phi_table_words();
 cudaError_t launch_detection(long long n, const double* F, double F_th, double sigma_F, const double* coef,
                              double* out, cudaStream_t st);

@@ -83,6 +83,7 @@ struct cudahm {
   // LF rule
   double *xL = nullptr, *wL = nullptr, *xr = nullptr, *wr = nullptr, *qs = nullptr, *Wr = nullptr;
   double* phi_coef = nullptr;
+  double* math_tab = nullptr;
   unsigned long long* eb_partials = nullptr;
   int eb_grid = 0, eb_rows_smem = 1;
   // host mirrors
@@ -260,6 +261,7 @@ SweepArgs base_args(cudahm* h) {
   a.qs = h->qs;
   a.Wr = h->Wr;
   a.phi_coef = h->phi_coef;
+  a.math_tab = h->math_tab;
   a.nL = h->cfg.model == CUDAHM_LF ? static_cast<int>(h->cfg.model_consts[3]) : 0;
   a.nr = h->cfg.model == CUDAHM_LF ? static_cast<int>(h->cfg.model_consts[4]) : 0;
   a.rows_smem = h->rows_smem;
@@ -403,6 +405,7 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
       (rc = alloc_into(h, &h->theta_dev, kMaxP)) || (rc = alloc_into(h, &h->eval_out, 4)) ||
       (rc = alloc_into(h, &h->tab_U, kChunk * p)) || (rc = alloc_into(h, &h->tab_u, kChunk)) ||
       (rc = alloc_into(h, &h->tab_lnu, kChunk)) ||
+      (rc = alloc_into(h, &h->math_tab, static_cast<size_t>(math_table_words()))) ||
       (rc = alloc_into(h, &h->tab_eta, kChunk)))
     return bail(rc);
   if (cfg->model == CUDAHM_LF) {
@@ -419,6 +422,8 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
         launch_lf_inner(nr, h->xr, h->wr, k[2], k[0], h->qs, h->Wr, h->stream) != cudaSuccess)
       return bail(fail(CUDAHM_ECUDA, "quadrature set-up failed: %s", cudaGetErrorString(cudaGetLastError())));
   }
+  if (launch_math_table(h->math_tab, h->stream) != cudaSuccess)
+    return bail(fail(CUDAHM_ECUDA, "exp/log table set-up failed: %s", cudaGetErrorString(cudaGetLastError())));
   if (cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess)
     return bail(fail(CUDAHM_ECUDA, "initialisation failed"));

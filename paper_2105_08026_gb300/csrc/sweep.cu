@@ -17,6 +17,7 @@
 #include <cstdint>
 
 #include "device_common.cuh"
+#include "fp64_math.cuh"
 #include "internal.h"
 
 namespace chm {
@@ -284,8 +285,9 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   const unsigned int nb1 = static_cast<unsigned int>((a.n * (blockIdx.x + 1)) / gridDim.x);
   const bool skip_me = (a.skip_cta == static_cast<int>(blockIdx.x));
   const bool is_lf = (a.model == CUDAHM_LF);
-  double* s_phi = s_dyn;  // [kPhiWords] for LF, else empty
-  double* s_y = s_dyn + (is_lf ? kPhiWords : 0);
+  double* s_math = s_dyn;                 // [kMathWords] exp/log tables
+  double* s_phi = s_dyn + kMathWords;     // [kPhiWords] for LF, else empty
+  double* s_y = s_phi + (is_lf ? kPhiWords : 0);
   double* s_aux = s_y + a.mpb;
   double* s_rows = s_y + 2 * a.mpb;
   for (unsigned int q = tid; q < nb1 - nb0; q += blockDim.x) {
@@ -294,6 +296,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   }
   if (is_lf)
     for (int q = tid; q < kPhiWords; q += blockDim.x) s_phi[q] = a.phi_coef[q];
+  for (int q = tid; q < kMathWords; q += blockDim.x) s_math[q] = a.math_tab[q];
   const int nseg = is_lf ? lf_block_segments(a, blockIdx.x, gridDim.x) : 0;
   double* sL = s_rows;
   double* sG = s_rows + a.rows_smem;
@@ -328,7 +331,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     if (i < nb1) {
       chi[m] = a.chi[i];
       S[m] = a.S[i];
-      echi[m] = M::kExp ? exp(chi[m]) : 0.0;
+      echi[m] = M::kExp ? exp_tab(chi[m], s_math) : 0.0;  // same routine as in the sweep
       ll[m] = M::loglike(chi[m], echi[m], a.y[i], a.aux[i], a.mc);
     } else {
       chi[m] = S[m] = echi[m] = ll[m] = 0.0;
@@ -384,20 +387,20 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         const uint4 w0 = philox4x32_10(make_uint4(0u, 0u, static_cast<uint32_t>(i), k), a.key0, a.key1);
         const uint4 w1 = philox4x32_10(make_uint4(1u, 0u, static_cast<uint32_t>(i), k), a.key0, a.key1);
         const double ua = uniform53(w0.x, w0.y), ub = uniform53(w0.z, w0.w);
-        const double z = sqrt(-2.0 * log(ua)) * cospi(2.0 * ub);
+        const double z = sqrt(-2.0 * log_tab(ua, s_math)) * cospi(2.0 * ub);
         const double u = uniform53(w1.x, w1.y);
         const double Y = fma(S[m], z, chi[m]);
         double delta, eY = 0.0, llY = 0.0;
         if (!M::support(Y, tc)) {
           delta = -INFINITY;
         } else {
-          eY = M::kExp ? exp(Y) : 0.0;
+          eY = M::kExp ? exp_tab(Y, s_math) : 0.0;
           llY = M::loglike(Y, eY, yv, av, a.mc);
           const double lpY = llY + M::logf(Y, eY, tc);
           const double lpX = ll[m] + M::logf(chi[m], echi[m], tc);
           delta = lpY - lpX;
         }
-        const double alpha = (delta >= 0.0) ? 1.0 : exp(delta);
+        const double alpha = (delta >= 0.0) ? 1.0 : exp_tab(delta, s_math);
         const bool acc = (delta >= 0.0) || (u < alpha);
         if (delta != delta) member_nan++;
         if (acc) {
@@ -608,9 +611,16 @@ static const void* kernel_for(int K) {
 }
 
 size_t sweep_smem_bytes(int model, int mpb, int rows_smem) {
-  return (model == CUDAHM_LF ? sizeof(double) * kPhiWords : 0) + 2 * sizeof(double) * static_cast<size_t>(mpb) +
-         (2 * sizeof(double) + sizeof(int)) * rows_smem;
+  return sizeof(double) * kMathWords + (model == CUDAHM_LF ? sizeof(double) * kPhiWords : 0) +
+         2 * sizeof(double) * static_cast<size_t>(mpb) + (2 * sizeof(double) + sizeof(int)) * rows_smem;
 }
+
+cudaError_t launch_math_table(double* t, cudaStream_t st) {
+  math_table_kernel<<<2, 128, 0, st>>>(t);
+  return cudaGetLastError();
+}
+
+int math_table_words() { return kMathWords; }
 
 template <class M>
 static cudaError_t launch_model(const SweepArgs& a, int K, int grid, int block, cudaStream_t st) {
