@@ -58,6 +58,7 @@ def lib():
             L.orc_uniform.restype = ctypes.c_double
             L.orc_draw.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                    ctypes.c_int, _dp, _dp]
+            L.orc_draw_member.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, _dp, _dp]
             L.orc_neumaier_sum.argtypes = [_dp, ctypes.c_int64]
             L.orc_neumaier_sum.restype = ctypes.c_double
             L.orc_cholesky.argtypes = [ctypes.c_int, _dp, _dp]
@@ -105,8 +106,16 @@ def uniform(wa: int, wb: int) -> float:
     return lib().orc_uniform(wa, wb)
 
 
+def draw_member(seed: int, index: int, sweep: int, d: int):
+    """d standard normals and the accept uniform of member `index` at sweep `sweep`."""
+    z = np.zeros(max(d, 1), dtype=np.float64)
+    u = ctypes.c_double(0.0)
+    lib().orc_draw_member(seed, index, sweep, d, _p(z), ctypes.byref(u))
+    return z[:d], u.value
+
+
 def draw(seed: int, stream: int, index: int, sweep: int, d: int):
-    """d standard normals and the accept uniform of one RAM step."""
+    """d standard normals and the accept uniform of one theta step (block j: normals 2j, 2j+1)."""
     z = np.zeros(max(d, 1), dtype=np.float64)
     u = ctypes.c_double(0.0)
     lib().orc_draw(seed, stream, index, sweep, d, _p(z), ctypes.byref(u))

@@ -35,9 +35,14 @@
  *   R4 accept iff ln u < Delta (strict), alpha = exp(min(0, Delta)), alpha = 0 off support.
  *   R5 random numbers: Philox4x32-10 (Salmon et al., SC'11), key = (seed lo, seed hi),
  *      counter = (block j, stream s, object i, sweep k); uniform u = (2m+1) 2^-53 with
- *      m the top 52 bits of (w_a:w_b); Box-Muller normals z = sqrt(-2 ln u_a) cos(2 pi u_b),
- *      sqrt(-2 ln u_a) sin(2 pi u_b); block j gives normals 2j, 2j+1; the accept uniform
- *      is the first uniform of block ceil(d/2).
+ *      m the top 52 bits of (w_a:w_b); Box-Muller pairs c = sqrt(-2 ln u_a) cos(2 pi u_b),
+ *      s = sqrt(-2 ln u_a) sin(2 pi u_b) from the words (w0,w1), (w2,w3) of a block.
+ *      Member draws (stream 0): the two normals of one Box-Muller pair serve two consecutive
+ *      sweeps. For the odd sweep k_o = 2m-1 and the even sweep k_o + 1, component a of U
+ *      comes from block (j = a, stream 0, member i, sweep k_o): its cosine for sweep k_o,
+ *      its sine for sweep k_o + 1. The accept uniform of sweep k is the first uniform of
+ *      block (d, 0, i, k). Theta draws (stream 1, index 0): block j gives normals 2j, 2j+1
+ *      of sweep k; the accept uniform is the first uniform of block ceil(p/2).
  *   R6 luminosity model in chi = ln L (Schechter form truncated at L_low), the
  *      normaliser of f cancels against the normalised selection integral, so the
  *      theta step uses the unnormalised integrand (see lf_* below).
@@ -89,7 +94,24 @@ static void block_words(uint64_t seed, uint32_t j, uint32_t s, uint32_t i, uint3
   orc_philox4x32_10(ctr, key, w);
 }
 
-/* R5: d standard normals and the accept uniform for draw (stream s, index i, sweep k). */
+/* R5: member draw of sweep k: d standard normals (shared Box-Muller pairs) and the accept uniform. */
+void orc_draw_member(uint64_t seed, uint32_t i, uint32_t k, int d, double* z, double* u_accept) {
+  const double two_pi = 6.283185307179586476925286766559;
+  uint32_t k_odd = (k & 1u) ? k : k - 1u;
+  for (int a = 0; a < d; ++a) {
+    uint32_t w[4];
+    block_words(seed, (uint32_t)a, 0u, i, k_odd, w);
+    double ua = orc_uniform(w[0], w[1]);
+    double ub = orc_uniform(w[2], w[3]);
+    double rad = sqrt(-2.0 * log(ua));
+    z[a] = (k & 1u) ? rad * cos(two_pi * ub) : rad * sin(two_pi * ub);
+  }
+  uint32_t w[4];
+  block_words(seed, (uint32_t)d, 0u, i, k, w);
+  *u_accept = orc_uniform(w[0], w[1]);
+}
+
+/* R5: theta draw: d standard normals and the accept uniform (stream s, index i, sweep k). */
 void orc_draw(uint64_t seed, uint32_t s, uint32_t i, uint32_t k, int d, double* z, double* u_accept) {
   const double two_pi = 6.283185307179586476925286766559;
   int nblk = (d + 1) / 2;
@@ -471,7 +493,7 @@ int orc_run(int model, int d, int p, int64_t n, const double* y, const double* a
       double* x = chi + (int64_t)d * i;
       double* Si = S + (int64_t)d * d * i;
       double u;
-      orc_draw(prm.seed, 0u, (uint32_t)i, (uint32_t)k, d, U, &u);
+      orc_draw_member(prm.seed, (uint32_t)i, (uint32_t)k, d, U, &u);
       for (int a = 0; a < d; ++a) {
         double t = x[a];
         for (int b = 0; b <= a; ++b) t += Si[a * d + b] * U[b];

@@ -37,6 +37,24 @@ __device__ __forceinline__ double uniform53(uint32_t wa, uint32_t wb) {
   return v - 0x1.fffffffffffffp-1;
 }
 
+// --------------------------------------------------- integer comparisons ----
+// Orderings of doubles decided on the integer pipe (the FP64 pipe is the sampler's bound).
+// dkey maps a double's bits to a signed integer with the same order as the values (-0 sorts
+// just below +0; NaN is never passed here).
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ bool dgt(double x, double y) { return dkey(x) > dkey(y); }
+__device__ __forceinline__ bool dsign(double x) { return __double_as_longlong(x) < 0; }
+__device__ __forceinline__ bool disnan(double x) {
+  return (__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll) > 0x7FF0000000000000ll;
+}
+// |x| >= 2^94 (infinities included)
+__device__ __forceinline__ bool dhuge(double x) {
+  return (__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll) >= 0x45D0000000000000ll;
+}
+
 // ------------------------------------------------------------- Xacc ---------
 struct Xacc {
   unsigned long long w0, w1, w2;  // little-endian limbs; value = (signed 192-bit) * 2^-96

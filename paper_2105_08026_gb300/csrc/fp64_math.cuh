@@ -32,7 +32,10 @@ __global__ void math_table_kernel(double* t) {
 // Taylor polynomial (remainder < 3e-20). Outside (-700, 709), and for NaN and infinities,
 // the library routine is used.
 __device__ __forceinline__ double exp_tab(double x, const double* __restrict__ T) {
-  if (!(x > -700.0 && x < 709.0)) return exp(x);
+  // fast path for -700 < x < 709, tested on the bits: |x| < 700, or 0 <= x < 709
+  const long long b = __double_as_longlong(x);
+  const long long mag = b & 0x7FFFFFFFFFFFFFFFll;
+  if (!(mag < 0x4085E00000000000ll || (b >= 0 && b < 0x4086280000000000ll))) return exp(x);
   const double magic = 0x1.8p52;
   const double km = fma(x, 0x1.71547652b82fep+6, magic);  // 64/ln2
   const int k = __double2loint(km);

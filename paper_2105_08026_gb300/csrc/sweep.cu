@@ -66,7 +66,7 @@ struct LF {
     c.a3 = th[2];
     return c;
   }
-  __device__ static bool support(double chi, const ThetaC& c) { return chi > c.a3; }
+  __device__ static bool support(double chi, const ThetaC& c) { return dgt(chi, c.a3); }
   __device__ static double logf(double chi, double echi, const ThetaC& c) {
     return c.a0 * (chi - c.a1) - echi * c.a2;
   }
@@ -128,8 +128,10 @@ constexpr int kPhiDeg = 10;
 constexpr int kPhiWords = kPhiN * (kPhiDeg + 1);  // coefficient-major: coef[n * kPhiN + i]
 
 __device__ __forceinline__ double phi_table(double x, const double* __restrict__ coef) {
-  if (x > 8.5) return 1.0;
-  if (x < -8.0) return 0.5 * erfc(-x * 0.70710678118654752440);
+  const long long b = __double_as_longlong(x);
+  if (b > 0x4021000000000000ll) return 1.0;  // x > 8.5 (and +inf)
+  if (static_cast<unsigned long long>(b) > 0xC020000000000000ull)  // x < -8 (and -inf)
+    return 0.5 * erfc(-x * 0.70710678118654752440);
   const double magic = 6755399441055744.0;        // 1.5 * 2^52
   const double r = fma(x, 8.0, 64.0 + magic);     // round(8x + 64) sits in the low mantissa bits
   const int i = __double2loint(r);
@@ -289,7 +291,8 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   double* s_phi = s_dyn + kMathWords;     // [kPhiWords] for LF, else empty
   double* s_y = s_phi + (is_lf ? kPhiWords : 0);
   double* s_aux = s_y + a.mpb;
-  double* s_rows = s_y + 2 * a.mpb;
+  double* s_zs = s_y + 2 * a.mpb;  // spare (sine) normal of each member's Box-Muller pair
+  double* s_rows = s_y + 3 * a.mpb;
   for (unsigned int q = tid; q < nb1 - nb0; q += blockDim.x) {
     s_y[q] = a.y[nb0 + q];
     s_aux[q] = a.aux[nb0 + q];
@@ -378,16 +381,29 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
       }
     }
 
-    // a1-a3: member RAM steps under theta
+    // a1-a3: member RAM steps under theta. One Box-Muller pair serves the odd sweep (cosine)
+    // and the next even sweep (sine, kept in shared memory; recomputed if a launch starts on
+    // an even sweep).
+    const bool odd = (k & 1u) != 0u;
 #pragma unroll
     for (int m = 0; m < K; ++m) {
       const unsigned int i = nb0 + tid + m * blockDim.x;
       if (i < nb1) {
         const double yv = s_y[i - nb0], av = s_aux[i - nb0];
-        const uint4 w0 = philox4x32_10(make_uint4(0u, 0u, static_cast<uint32_t>(i), k), a.key0, a.key1);
+        double z;
+        if (odd || s == 0) {
+          const uint4 w0 = philox4x32_10(make_uint4(0u, 0u, static_cast<uint32_t>(i), odd ? k : k - 1u), a.key0,
+                                         a.key1);
+          const double ua = uniform53(w0.x, w0.y), ub = uniform53(w0.z, w0.w);
+          const double rad = sqrt(-2.0 * log_tab(ua, s_math));
+          double sn, cs;
+          sincospi(2.0 * ub, &sn, &cs);
+          z = odd ? rad * cs : rad * sn;
+          if (odd) s_zs[i - nb0] = rad * sn;
+        } else {
+          z = s_zs[i - nb0];
+        }
         const uint4 w1 = philox4x32_10(make_uint4(1u, 0u, static_cast<uint32_t>(i), k), a.key0, a.key1);
-        const double ua = uniform53(w0.x, w0.y), ub = uniform53(w0.z, w0.w);
-        const double z = sqrt(-2.0 * log_tab(ua, s_math)) * cospi(2.0 * ub);
         const double u = uniform53(w1.x, w1.y);
         const double Y = fma(S[m], z, chi[m]);
         double delta, eY = 0.0, llY = 0.0;
@@ -400,9 +416,10 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
           const double lpX = ll[m] + M::logf(chi[m], echi[m], tc);
           delta = lpY - lpX;
         }
-        const double alpha = (delta >= 0.0) ? 1.0 : exp_tab(delta, s_math);
-        const bool acc = (delta >= 0.0) || (u < alpha);
-        if (delta != delta) member_nan++;
+        const bool dneg = dsign(delta);  // -inf and -0 included; NaN is counted below
+        const double alpha = dneg ? exp_tab(delta, s_math) : 1.0;
+        const bool acc = !dneg || (__double_as_longlong(u) < __double_as_longlong(alpha));  // both >= +0
+        if (disnan(delta)) member_nan++;
         if (acc) {
           chi[m] = Y;
           echi[m] = eY;
@@ -435,9 +452,13 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         if (i < nb1) {
           const double dn = M::support(chi[m], tcp) ? M::logf(chi[m], echi[m], tcp) - M::logf(chi[m], echi[m], tc)
                                                    : -INFINITY;
-          if (dn <= -0x1p94) neg_big++;       // off the support of theta' (-inf) or hopeless
-          else if (dn >= 0x1p94) pos_big++;   // outside the fixed-point range (+inf included)
-          else xacc_add_double(xd, dn, fd);   // counts NaN in fd.nan
+          if (disnan(dn)) fd.nan++;
+          else if (dhuge(dn)) {
+            if (dsign(dn)) neg_big++;  // off the support of theta' (-inf) or hopeless
+            else pos_big++;            // outside the fixed-point range (+inf included)
+          } else {
+            xacc_add_double(xd, dn, fd);
+          }
         }
       }
       if (is_lf) lf_segment_pairs(a, nseg, sL, sG, sK, s_phi, xe, fe);
@@ -612,7 +633,7 @@ static const void* kernel_for(int K) {
 
 size_t sweep_smem_bytes(int model, int mpb, int rows_smem) {
   return sizeof(double) * kMathWords + (model == CUDAHM_LF ? sizeof(double) * kPhiWords : 0) +
-         2 * sizeof(double) * static_cast<size_t>(mpb) + (2 * sizeof(double) + sizeof(int)) * rows_smem;
+         3 * sizeof(double) * static_cast<size_t>(mpb) + (2 * sizeof(double) + sizeof(int)) * rows_smem;
 }
 
 cudaError_t launch_math_table(double* t, cudaStream_t st) {

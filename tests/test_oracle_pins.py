@@ -74,8 +74,34 @@ def test_normals_and_accept_uniforms_distribution():
     assert oracle.draw(42, 0, 5, 9, 1)[0][0] != oracle.draw(43, 0, 5, 9, 1)[0][0]
 
 
+def test_member_draw_layout_and_pairing():
+    """Member draws: component a of sweeps k_o (odd) and k_o + 1 are the cosine and the sine of the
+    Box-Muller pair of block (a, 0, i, k_o); the accept uniform of sweep k is block (d, 0, i, k)'s first."""
+    seed, i = 0x0F1E2D3C4B5A6978, 41
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for d in (1, 3):
+        for k_o in (1, 7, 999):
+            zo, uo = oracle.draw_member(seed, i, k_o, d)
+            ze, ue = oracle.draw_member(seed, i, k_o + 1, d)
+            for a in range(d):
+                w = oracle.philox4x32_10([a, 0, i, k_o], key)
+                ua, ub = oracle.uniform(int(w[0]), int(w[1])), oracle.uniform(int(w[2]), int(w[3]))
+                rad = math.sqrt(-2.0 * math.log(ua))
+                assert zo[a] == pytest.approx(rad * math.cos(2 * math.pi * ub), rel=1e-15, abs=1e-15)
+                assert ze[a] == pytest.approx(rad * math.sin(2 * math.pi * ub), rel=1e-15, abs=1e-15)
+            for kk, u in ((k_o, uo), (k_o + 1, ue)):
+                w = oracle.philox4x32_10([d, 0, i, kk], key)
+                assert u == oracle.uniform(int(w[0]), int(w[1]))
+    # paired normals are independent N(0,1): correlation of (cos, sin) parts over many members
+    zo = np.array([oracle.draw_member(5, j, 3, 1)[0][0] for j in range(20000)])
+    ze = np.array([oracle.draw_member(5, j, 4, 1)[0][0] for j in range(20000)])
+    assert abs(np.corrcoef(zo, ze)[0, 1]) < 4 / math.sqrt(zo.size)
+    assert scipy.stats.kstest(ze, "norm").pvalue > 1e-3
+
+
 def test_draw_block_layout():
-    """Normals 2j, 2j+1 come from block j; the accept uniform is the first uniform of block ceil(d/2)."""
+    """Theta draws: normals 2j, 2j+1 come from block j; the accept uniform is the first uniform of
+    block ceil(d/2)."""
     seed, s, i, k = 0x123456789ABCDEF, 0, 17, 4
     key = [seed & 0xFFFFFFFF, seed >> 32]
     w0 = oracle.philox4x32_10([0, s, i, k], key)
