@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--repeats", type=int, default=5, help="timed launches the steps are split into")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--cpu-sweeps", type=int, default=8)
     return ap.parse_args()
 
@@ -237,6 +238,34 @@ def run_cuda(args):
         t_max_ms = float(t.item())
     value = ws * n * K / (t_max_ms * 1e-3)
 
+    # the same workload in the FP32 bulk form (binary32 member terms, binary64 sums/accept/RAM/etabar)
+    fp32 = None
+    if not args.no_fp32:
+        s3 = cudahm.Sampler(cudahm.LF, n, theta_init=theta0, theta_prop_scale=scale, model_consts=consts,
+                            seed=CHAIN_SEED + rank, device=local, stream=stream.cuda_stream,
+                            use_torch_allocator=True, precision=cudahm.FP32)
+        cudahm.cudahm_set_data_device(s3.h, y_dev.data_ptr(), r_dev.data_ptr(), n)
+        if args.warmup > 0:
+            s3.run(args.warmup, 0)
+        f_ms = 0.0
+        for ns in chunks:
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s3.run(0, ns, 1)
+            e1.record(stream)
+            e1.synchronize()
+            f_ms += e0.elapsed_time(e1)
+        if ws > 1:
+            t = torch.tensor([f_ms], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            f_ms = float(t.item())
+        fp32 = {"value": ws * n * K / (f_ms * 1e-3), "unit": "object-updates/s", "ms_per_step": f_ms / K,
+                "dtype": "f32 member terms, f64 sums/accept/RAM/selection integral"}
+        s3.close()
+
     # e2e through the public API with host buffers (every iteration: H2D data, run, D2H samples)
     e2e = None
     if not args.no_e2e:
@@ -295,7 +324,8 @@ def run_cuda(args):
                        "n": n, "parallelism": f"replicas x{ws}", "l2": "256 MB flush before each timed launch; "
                        "member state register-resident within a launch", "timed_launches": R,
                        "launch_shape": [st.grid_blocks, st.block_threads, st.objects_per_thread]},
-            "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk}
+            "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "fp32_bulk": fp32}
     print(json.dumps(line), flush=True)
     s.close()
     if ws > 1:

@@ -74,7 +74,13 @@ typedef struct cudahm* cudahm_t;
  *       an n_r-node rule in r on [0, r_max] (n_L, n_r <= 4096). */
 typedef enum { CUDAHM_NN1 = 0, CUDAHM_MVN3 = 1, CUDAHM_LF = 2 } cudahm_model;
 
-/* FP64: all arithmetic in binary64. FP32: reserved for the bulk-FP32 form. */
+/* FP64: all arithmetic in binary64.
+ * FP32 (bulk form): the member step (proposal, member log target, accept) and the theta
+ * partials log f(chi;theta') - log f(chi;theta) run in binary32, with binary32 draws of their
+ * own (Philox block (0, stream 2, member, odd sweep): a Box-Muller pair from 24-bit uniforms,
+ * cosine for the odd sweep and sine for the next, accept uniforms from words 2 and 3); the
+ * RAM factors S, the exact sum over members, the theta accept and its RAM update, and the
+ * selection integral stay binary64. Latents are binary32 values (held as doubles in the API). */
 typedef enum { CUDAHM_FP64 = 0, CUDAHM_FP32 = 1 } cudahm_precision;
 
 typedef void* (*cudahm_alloc_fn)(size_t bytes, void* ctx);

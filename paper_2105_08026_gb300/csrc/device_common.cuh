@@ -109,6 +109,39 @@ __device__ __forceinline__ void xacc_add_double(Xacc& a, double v, XFlags& f) {
   xacc_add(a, t);
 }
 
+// Add a binary32 value (rounded toward zero to a multiple of 2^-96); same flags.
+__device__ __forceinline__ void xacc_add_float(Xacc& a, float v, XFlags& f) {
+  const unsigned int u = __float_as_uint(v);
+  const int e = static_cast<int>((u >> 23) & 0xff);
+  if (e == 0xff) {
+    if (u & 0x007FFFFFu) f.nan++;
+    else if (u >> 31) f.neg_inf++;
+    else f.big++;
+    return;
+  }
+  if (e >= 127 + 94) { f.big++; return; }
+  const int sh = e - 54;  // value * 2^96 = m * 2^(e - 150 + 96)
+  if (e == 0 || sh <= -24) return;
+  const unsigned long long m = static_cast<unsigned long long>((u & 0x007FFFFFu) | 0x00800000u);
+  Xacc t;
+  if (sh < 0) {
+    t.w0 = m >> (-sh); t.w1 = 0ull; t.w2 = 0ull;
+  } else {
+    const int q = sh >> 6, r = sh & 63;
+    const unsigned long long lo = m << r;
+    const unsigned long long hi = r ? (m >> (64 - r)) : 0ull;
+    t.w0 = (q == 0) ? lo : 0ull;
+    t.w1 = (q == 1) ? lo : ((q == 0) ? hi : 0ull);
+    t.w2 = (q == 2) ? lo : ((q == 1) ? hi : 0ull);
+  }
+  if (u >> 31) {
+    t.w0 = ~t.w0; t.w1 = ~t.w1; t.w2 = ~t.w2;
+    asm("add.cc.u64 %0, %0, 1;\n\taddc.cc.u64 %1, %1, 0;\n\taddc.u64 %2, %2, 0;"
+        : "+l"(t.w0), "+l"(t.w1), "+l"(t.w2));
+  }
+  xacc_add(a, t);
+}
+
 // Round-to-nearest-even conversion of the fixed-point value to binary64.
 __device__ __forceinline__ double xacc_to_double(Xacc a) {
   const bool neg = (a.w2 >> 63) != 0;

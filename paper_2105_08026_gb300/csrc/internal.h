@@ -31,6 +31,7 @@ struct ModelConsts {
 
 struct SweepArgs {
   int model;
+  int f32;  // 1: FP32 bulk member arithmetic
   int p;
   long long n;
   const double* y;    // NN1: y_i;  LF: Fhat_i
@@ -86,7 +87,7 @@ int record_error(int code, const char* msg);
 
 // Kernel launch helpers (sweep.cu). Return cudaError_t of the launch.
 cudaError_t launch_sweep(const SweepArgs& a, int K, int grid, int block, cudaStream_t st);
-cudaError_t sweep_occupancy(int model, int K, int block, int smem_bytes, int* blocks_per_sm);
+cudaError_t sweep_occupancy(int model, int K, bool f32, int block, int smem_bytes, int* blocks_per_sm);
 size_t sweep_smem_bytes(int model, int mpb, int rows_smem);
 cudaError_t launch_phi_table(double* coef, cudaStream_t st);
 cudaError_t launch_math_table(double* t, cudaStream_t st);
@@ -94,7 +95,7 @@ int math_table_words();
 int phi_table_words();
 cudaError_t launch_detection(long long n, const double* F, double F_th, double sigma_F, const double* coef,
                              double* out, cudaStream_t st);
-cudaError_t sweep_set_smem(int model, int K, int smem_bytes);
+cudaError_t sweep_set_smem(int model, int K, bool f32, int smem_bytes);
 cudaError_t launch_prepare(int model, long long n, const double* y_raw, const double* aux_raw, double* y, double* aux,
                            double* chi, double* S, const ModelConsts& mc, const double* theta, int* bad,
                            int set_default_chi, cudaStream_t st);
@@ -105,8 +106,9 @@ cudaError_t launch_lf_inner(int nr, const double* xr, const double* wr, double r
                             double* Wr, cudaStream_t st);
 cudaError_t launch_tables(int p, uint32_t key0, uint32_t key1, long long k0, long long ns, double gamma, double* U,
                           double* u, double* lnu, double* eta, cudaStream_t st);
-cudaError_t launch_eval_logdens(int model, long long n, const double* y, const double* aux, const double* chi,
-                                const double* theta_dev, const ModelConsts& mc, double* out, cudaStream_t st);
+cudaError_t launch_eval_logdens(int model, bool f32, long long n, const double* y, const double* aux,
+                                const double* chi, const double* theta_dev, const ModelConsts& mc, double* out,
+                                cudaStream_t st);
 cudaError_t launch_eval_etabar(const double* theta_dev, const SweepArgs& rule, unsigned long long* partials,
                                int grid, double* out, cudaStream_t st);
 

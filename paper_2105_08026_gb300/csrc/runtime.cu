@@ -148,7 +148,8 @@ int validate(const cudahm_config* c) {
   if (c->model != CUDAHM_NN1 && c->model != CUDAHM_LF && c->model != CUDAHM_MVN3)
     return fail(CUDAHM_EINVAL, "unknown model %d", c->model);
   if (c->model == CUDAHM_MVN3) return fail(CUDAHM_EUNSUPPORTED, "model MVN3 is not in this build");
-  if (c->precision != CUDAHM_FP64) return fail(CUDAHM_EUNSUPPORTED, "only FP64 precision is in this build");
+  if (c->precision != CUDAHM_FP64 && c->precision != CUDAHM_FP32)
+    return fail(CUDAHM_EINVAL, "unknown precision %d", c->precision);
   if (c->d != model_d(c->model)) return fail(CUDAHM_EINVAL, "d = %d does not match the model", c->d);
   if (c->n < 1 || c->n > (1ll << 31)) return fail(CUDAHM_EINVAL, "n = %lld out of range [1, 2^31]", (long long)c->n);
   if (!(c->target_accept > 0.0 && c->target_accept < 1.0)) return fail(CUDAHM_EINVAL, "target_accept not in (0,1)");
@@ -197,6 +198,7 @@ int choose_shape(cudahm* h) {
   const long long n = h->n;
   const int model = h->cfg.model;
   const bool lf = (model == CUDAHM_LF);
+  const bool f32 = (h->cfg.precision == CUDAHM_FP32);
   // LF: segments of 128 inner nodes, G = n_L * ceil(n_r / 128), dealt round-robin to the blocks
   const long long G = lf ? static_cast<long long>(h->cfg.model_consts[3]) *
                                ((static_cast<long long>(h->cfg.model_consts[4]) + 127) / 128)
@@ -207,7 +209,7 @@ int choose_shape(cudahm* h) {
     // the grid depends on the occupancy, which depends on the shared memory, which depends on
     // the grid: iterate from the register-limited occupancy down until it is consistent
     int bps = 0;
-    CU(sweep_occupancy(model, K, block, 0, &bps));
+    CU(sweep_occupancy(model, K, f32, block, 0, &bps));
     for (; bps >= 1; --bps) {
       int grid = lf ? bps * h->sms
                     : static_cast<int>(std::min<long long>(static_cast<long long>(bps) * h->sms,
@@ -218,9 +220,9 @@ int choose_shape(cudahm* h) {
       const size_t smem = sweep_smem_bytes(model, static_cast<int>(mpb), rows);
       if (smem > 200 * 1024) break;
       int fit = 0;
-      CU(sweep_occupancy(model, K, block, static_cast<int>(smem), &fit));
+      CU(sweep_occupancy(model, K, f32, block, static_cast<int>(smem), &fit));
       if (fit * h->sms >= grid) {
-        CU(sweep_set_smem(model, K, static_cast<int>(smem)));
+        CU(sweep_set_smem(model, K, f32, static_cast<int>(smem)));
         h->K = K;
         h->grid = grid;
         h->mpb = static_cast<int>(mpb);
@@ -240,6 +242,7 @@ int choose_shape(cudahm* h) {
 SweepArgs base_args(cudahm* h) {
   SweepArgs a{};
   a.model = h->cfg.model;
+  a.f32 = (h->cfg.precision == CUDAHM_FP32) ? 1 : 0;
   a.p = h->p;
   a.n = h->n;
   a.y = h->y;
@@ -641,7 +644,8 @@ int cudahm_eval_logdens(cudahm_t h, const double* theta_host, double* lp_host) {
   double* out = nullptr;
   TRY(alloc_into(h, &out, h->n));
   CU(cudaMemcpyAsync(h->theta_dev, theta_host, sizeof(double) * h->p, cudaMemcpyHostToDevice, h->stream));
-  CU(launch_eval_logdens(h->cfg.model, h->n, h->y, h->aux, h->chi, h->theta_dev, h->mc, out, h->stream));
+  CU(launch_eval_logdens(h->cfg.model, h->cfg.precision == CUDAHM_FP32, h->n, h->y, h->aux, h->chi, h->theta_dev,
+                         h->mc, out, h->stream));
   CU(cudaMemcpyAsync(lp_host, out, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
   h->dfree(out);

@@ -15,6 +15,7 @@
 // registers for the whole launch; data are read once at launch start.
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "device_common.cuh"
 #include "fp64_math.cuh"
@@ -28,9 +29,56 @@ struct ThetaC {
   double a0, a1, a2, a3;
 };
 
+// binary32 theta constants for the FP32 bulk form; a location parameter is held as a sum of
+// two floats (hi + lo) so that chi - location keeps full binary32 relative accuracy.
+struct ThetaCf {
+  float sc_hi, sc_lo, loc_hi, loc_lo, low_hi, low_lo;  // scale, location, lower bound (hi + lo)
+};
+__device__ __forceinline__ void split_f(double v, float& hi, float& lo) {
+  hi = static_cast<float>(v);
+  lo = static_cast<float>(v - static_cast<double>(hi));
+}
+// chi - (hi + lo): the first subtraction is exact whenever chi is near hi
+__device__ __forceinline__ float sub2(float chi, float hi, float lo) { return (chi - hi) - lo; }
+// chi - (hi + lo) as an unevaluated sum r_hi + r_lo (Knuth's TwoSum for chi - hi). Latents
+// lie on the binary32 grid, so the rounding error of chi - hi repeats from member to member;
+// keeping it avoids a bias that would grow with N in sums over members.
+__device__ __forceinline__ void sub2x(float chi, float hi, float lo, float& r_hi, float& r_lo) {
+  const float s = chi - hi;
+  const float a1 = s + hi;    // chi's share of s
+  const float b1 = s - a1;    // -hi's share of s
+  const float err = (chi - a1) + (-hi - b1);
+  r_hi = s;
+  r_lo = err - lo;
+}
+
 struct NN1 {
   // a0 = mu, a1 = 1/(2 tau^2)
   static constexpr bool kExp = false;
+  // binary32 forms of the member terms (FP32 bulk precision): loc = mu, scale = 1/(2 tau^2)
+  __device__ static ThetaCf consts32(const ThetaC& c) {
+    ThetaCf f{};
+    split_f(c.a0, f.loc_hi, f.loc_lo);
+    split_f(c.a1, f.sc_hi, f.sc_lo);
+    return f;
+  }
+  __device__ static bool support32(float, const ThetaCf&) { return true; }
+  __device__ static float logf32(float chi, const ThetaCf& c) {
+    float rh, rl;
+    sub2x(chi, c.loc_hi, c.loc_lo, rh, rl);
+    const float r2 = fmaf(rh, rh, 2.0f * rh * rl);
+    return -fmaf(c.sc_hi, r2, c.sc_lo * r2);  // the scale's rounding would bias every member alike
+  }
+  // member data d[0], d[1] = y_i as hi + lo, d[2] = 1/(2 sigma_i^2)
+  static constexpr int kData32 = 3;
+  __device__ static void data32(double y, double aux, const ModelConsts&, float* d) {
+    split_f(y, d[0], d[1]);
+    d[2] = static_cast<float>(0.5 * aux);
+  }
+  __device__ static float loglike32(float chi, const float* d) {
+    const float r = (d[0] - chi) + d[1];
+    return -d[2] * (r * r);
+  }
   __device__ static ThetaC consts(const double* th) {
     ThetaC c;
     c.a0 = th[0];
@@ -58,6 +106,45 @@ struct NN1 {
 struct LF {
   // a0 = beta + 1, a1 = ln L*, a2 = 1/L*, a3 = ln L_low
   static constexpr bool kExp = true;
+  // binary32 forms: scale = beta + 1, loc = ln L*, low = ln L_low; log f = scale x - e^x, x = chi - ln L*
+  __device__ static ThetaCf consts32(const ThetaC& c) {
+    ThetaCf f{};
+    split_f(c.a0, f.sc_hi, f.sc_lo);
+    split_f(c.a1, f.loc_hi, f.loc_lo);
+    split_f(c.a3, f.low_hi, f.low_lo);
+    return f;
+  }
+  __device__ static bool support32(float chi, const ThetaCf& c) { return (chi - c.low_hi) > c.low_lo; }
+  __device__ static float logf32(float chi, const ThetaCf& c) {
+    float xh, xl;
+    sub2x(chi, c.loc_hi, c.loc_lo, xh, xl);
+    const float e = expf(xh);
+    const float ex = fmaf(e, xl, e);  // e^(xh + xl) to first order in xl
+    return fmaf(c.sc_hi, xh, fmaf(c.sc_hi, xl, fmaf(c.sc_lo, xh, -ex)));
+  }
+  // member data: d[0], d[1] = ln(Fhat_i/q_i) as hi + lo, d[2] = Fhat_i^2/(2 sigma_F^2), so that
+  // log l_i = -d[2] expm1(chi - ln(Fhat_i/q_i))^2 keeps binary32 relative accuracy however large
+  // Fhat_i/sigma_F is; members with Fhat_i <= 0 use d[3] = Fhat_i, d[4] = q_i directly (d[2] < 0).
+  static constexpr int kData32 = 5;
+  __device__ static void data32(double y, double aux, const ModelConsts& mc, float* d) {
+    if (y > 0.0) {
+      split_f(log(y / aux), d[0], d[1]);
+      d[2] = static_cast<float>(y * y * mc.inv2sig2);
+    } else {  // marker: d[2] < 0 holds -1/(2 sigma_F^2)
+      d[0] = d[1] = 0.0f;
+      d[2] = static_cast<float>(-mc.inv2sig2);
+    }
+    d[3] = static_cast<float>(y);
+    d[4] = static_cast<float>(aux);
+  }
+  __device__ static float loglike32(float chi, const float* d) {
+    if (d[2] > 0.0f) {
+      const float e = expm1f(sub2(chi, d[0], d[1]));
+      return -d[2] * (e * e);
+    }
+    const float r = fmaf(-expf(chi), d[4], d[3]);
+    return (r * r) * d[2];
+  }
   __device__ static ThetaC consts(const double* th) {
     ThetaC c;
     c.a0 = th[0] + 1.0;
@@ -266,13 +353,15 @@ __device__ __forceinline__ void propose_theta(const SweepArgs& a, long long s, i
   tcp = M::consts(thp);
 }
 
-template <class M, int K>
+template <class M, int K, bool F32>
 __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
+  using R = typename std::conditional<F32, float, double>::type;  // member arithmetic
   // dynamic shared memory: [mpb] y, [mpb] aux of this block's members, then the rule segment
   // values [rows_smem] L_j, [rows_smem] G_j, [rows_smem] int first inner node
   extern __shared__ double s_dyn[];
   __shared__ double s_theta[kMaxP], s_thp[kMaxP], s_Sth[kMaxP * kMaxP];
   __shared__ ThetaC s_tc, s_tcp;
+  __shared__ ThetaCf s_tcf, s_tcpf;
   __shared__ double s_etabar, s_logeb, s_lpri, s_lpri_new, s_logalpha_prev;
   __shared__ int s_stop, s_pending_ram;
   __shared__ long long s_rows_written, s_tacc;
@@ -293,9 +382,11 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   double* s_aux = s_y + a.mpb;
   double* s_zs = s_y + 2 * a.mpb;  // spare (sine) normal of each member's Box-Muller pair
   double* s_rows = s_y + 3 * a.mpb;
-  for (unsigned int q = tid; q < nb1 - nb0; q += blockDim.x) {
-    s_y[q] = a.y[nb0 + q];
-    s_aux[q] = a.aux[nb0 + q];
+  if (!F32) {
+    for (unsigned int q = tid; q < nb1 - nb0; q += blockDim.x) {
+      s_y[q] = a.y[nb0 + q];
+      s_aux[q] = a.aux[nb0 + q];
+    }
   }
   if (is_lf)
     for (int q = tid; q < kPhiWords; q += blockDim.x) s_phi[q] = a.phi_coef[q];
@@ -322,22 +413,46 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     propose_theta<M>(a, 0, p, s_theta, s_Sth, s_thp, lp, tcp);
     s_lpri_new = lp;
     s_tcp = tcp;
+    s_tcf = M::consts32(s_tc);
+    s_tcpf = M::consts32(tcp);
   }
   __syncthreads();
   if (is_lf && s_lpri_new != -INFINITY) lf_segment_rows(s_tcp, a, blockIdx.x, gridDim.x, nseg, sL, sG, sK);
 
   // members of this thread: i = nb0 + tid + m blockDim (latent, RAM factor, e^chi, log l in registers)
-  double chi[K], S[K], echi[K], ll[K];
+  R chi[K], echi[K], ll[K];
+  double S[K];
+  // FP32 bulk form: the model's binary32 member data, M::kData32 arrays of mpb floats, in the
+  // region that holds y, aux and the spare normals in the FP64 form (3 mpb doubles = 6 mpb floats)
+  float* s_d32 = reinterpret_cast<float*>(s_y);
+  if (F32) {
+    for (unsigned int q = tid; q < nb1 - nb0; q += blockDim.x) {
+      float d[M::kData32];
+      M::data32(a.y[nb0 + q], a.aux[nb0 + q], a.mc, d);
+#pragma unroll
+      for (int c = 0; c < M::kData32; ++c) s_d32[c * a.mpb + q] = d[c];
+    }
+    __syncthreads();
+  }
 #pragma unroll
   for (int m = 0; m < K; ++m) {
     const unsigned int i = nb0 + tid + m * blockDim.x;
     if (i < nb1) {
-      chi[m] = a.chi[i];
+      chi[m] = static_cast<R>(a.chi[i]);
       S[m] = a.S[i];
-      echi[m] = M::kExp ? exp_tab(chi[m], s_math) : 0.0;  // same routine as in the sweep
-      ll[m] = M::loglike(chi[m], echi[m], a.y[i], a.aux[i], a.mc);
+      if constexpr (F32) {
+        float d[M::kData32];
+#pragma unroll
+        for (int c = 0; c < M::kData32; ++c) d[c] = s_d32[c * a.mpb + (i - nb0)];
+        echi[m] = 0.0f;
+        ll[m] = M::loglike32(chi[m], d);
+      } else {
+        echi[m] = M::kExp ? exp_tab(chi[m], s_math) : 0.0;  // same routine as in the sweep
+        ll[m] = M::loglike(chi[m], echi[m], a.y[i], a.aux[i], a.mc);
+      }
     } else {
-      chi[m] = S[m] = echi[m] = ll[m] = 0.0;
+      chi[m] = echi[m] = ll[m] = R(0);
+      S[m] = 0.0;
     }
   }
   unsigned int member_acc = 0;
@@ -363,6 +478,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         propose_theta<M>(a, s, p, s_theta, s_Sth, s_thp, lp, tcp);
         s_lpri_new = lp;
         s_tcp = tcp;
+        s_tcpf = M::consts32(tcp);
       }
       __syncwarp();
       if (is_lf && s_lpri_new != -INFINITY) {
@@ -381,57 +497,107 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
       }
     }
 
-    // a1-a3: member RAM steps under theta. One Box-Muller pair serves the odd sweep (cosine)
-    // and the next even sweep (sine, kept in shared memory; recomputed if a launch starts on
-    // an even sweep).
-    const bool odd = (k & 1u) != 0u;
+    if constexpr (F32) {
+      // a1-a3 in binary32 (FP32 bulk form). Draws: Philox block (0, stream 2, member i, odd sweep
+      // k_o) gives a Box-Muller pair from 24-bit uniforms of words 0 and 1 (cosine for k_o, sine
+      // for k_o + 1) and the accept uniforms of k_o (word 2) and k_o + 1 (word 3). The RAM factor
+      // S stays binary64.
+      const bool oddf = (k & 1u) != 0u;
+      const ThetaCf tf = s_tcf;
 #pragma unroll
-    for (int m = 0; m < K; ++m) {
-      const unsigned int i = nb0 + tid + m * blockDim.x;
-      if (i < nb1) {
-        const double yv = s_y[i - nb0], av = s_aux[i - nb0];
-        double z;
-        if (odd || s == 0) {
-          const uint4 w0 = philox4x32_10(make_uint4(0u, 0u, static_cast<uint32_t>(i), odd ? k : k - 1u), a.key0,
-                                         a.key1);
-          const double ua = uniform53(w0.x, w0.y), ub = uniform53(w0.z, w0.w);
-          const double rad = sqrt(-2.0 * log_tab(ua, s_math));
-          double sn, cs;
-          sincospi(2.0 * ub, &sn, &cs);
-          z = odd ? rad * cs : rad * sn;
-          if (odd) s_zs[i - nb0] = rad * sn;
-        } else {
-          z = s_zs[i - nb0];
+      for (int m = 0; m < K; ++m) {
+        const unsigned int i = nb0 + tid + m * blockDim.x;
+        if (i < nb1) {
+          float d[M::kData32];
+#pragma unroll
+          for (int c = 0; c < M::kData32; ++c) d[c] = s_d32[c * a.mpb + (i - nb0)];
+          const uint4 w = philox4x32_10(make_uint4(0u, 2u, static_cast<uint32_t>(i), oddf ? k : k - 1u), a.key0,
+                                        a.key1);
+          const float u1 = (static_cast<float>(w.x >> 8) + 0.5f) * 0x1p-24f;
+          const float u2 = (static_cast<float>(w.y >> 8) + 0.5f) * 0x1p-24f;
+          const float u = (static_cast<float>((oddf ? w.z : w.w) >> 8) + 0.5f) * 0x1p-24f;
+          const float rad = sqrtf(-2.0f * logf(u1));
+          float sn, cs;
+          sincospif(2.0f * u2, &sn, &cs);
+          const float z = oddf ? rad * cs : rad * sn;
+          const float Y = fmaf(static_cast<float>(S[m]), z, chi[m]);
+          float delta, llY = 0.0f;
+          if (!M::support32(Y, tf)) {
+            delta = -INFINITY;
+          } else {
+            llY = M::loglike32(Y, d);
+            delta = (llY + M::logf32(Y, tf)) - (ll[m] + M::logf32(chi[m], tf));
+          }
+          const float alpha = (delta >= 0.0f) ? 1.0f : expf(delta);
+          const bool acc = (delta >= 0.0f) || (u < alpha);
+          if (delta != delta) member_nan++;
+          if (acc) {
+            chi[m] = Y;
+            ll[m] = llY;
+            member_acc++;
+          }
+          S[m] *= sqrt(fma(eta, static_cast<double>(alpha) - a.astar, 1.0));
+          if (trace) {
+            const long long o = (a.trace_off + s) * a.n + static_cast<long long>(i);
+            a.tr_delta[o] = delta;
+            a.tr_u[o] = u;
+            a.tr_acc[o] = acc ? 1 : 0;
+          }
         }
-        const uint4 w1 = philox4x32_10(make_uint4(1u, 0u, static_cast<uint32_t>(i), k), a.key0, a.key1);
-        const double u = uniform53(w1.x, w1.y);
-        const double Y = fma(S[m], z, chi[m]);
-        double delta, eY = 0.0, llY = 0.0;
-        if (!M::support(Y, tc)) {
-          delta = -INFINITY;
-        } else {
-          eY = M::kExp ? exp_tab(Y, s_math) : 0.0;
-          llY = M::loglike(Y, eY, yv, av, a.mc);
-          const double lpY = llY + M::logf(Y, eY, tc);
-          const double lpX = ll[m] + M::logf(chi[m], echi[m], tc);
-          delta = lpY - lpX;
-        }
-        const bool dneg = dsign(delta);  // -inf and -0 included; NaN is counted below
-        const double alpha = dneg ? exp_tab(delta, s_math) : 1.0;
-        const bool acc = !dneg || (__double_as_longlong(u) < __double_as_longlong(alpha));  // both >= +0
-        if (disnan(delta)) member_nan++;
-        if (acc) {
-          chi[m] = Y;
-          echi[m] = eY;
-          ll[m] = llY;
-          member_acc++;
-        }
-        S[m] *= sqrt(fma(eta, alpha - a.astar, 1.0));
-        if (trace) {
-          const long long o = (a.trace_off + s) * a.n + static_cast<long long>(i);
-          a.tr_delta[o] = delta;
-          a.tr_u[o] = u;
-          a.tr_acc[o] = acc ? 1 : 0;
+      }
+    } else {
+      // a1-a3: member RAM steps under theta. One Box-Muller pair serves the odd sweep (cosine)
+      // and the next even sweep (sine, kept in shared memory; recomputed if a launch starts on
+      // an even sweep).
+      const bool odd = (k & 1u) != 0u;
+  #pragma unroll
+      for (int m = 0; m < K; ++m) {
+        const unsigned int i = nb0 + tid + m * blockDim.x;
+        if (i < nb1) {
+          const double yv = s_y[i - nb0], av = s_aux[i - nb0];
+          double z;
+          if (odd || s == 0) {
+            const uint4 w0 = philox4x32_10(make_uint4(0u, 0u, static_cast<uint32_t>(i), odd ? k : k - 1u), a.key0,
+                                           a.key1);
+            const double ua = uniform53(w0.x, w0.y), ub = uniform53(w0.z, w0.w);
+            const double rad = sqrt(-2.0 * log_tab(ua, s_math));
+            double sn, cs;
+            sincospi(2.0 * ub, &sn, &cs);
+            z = odd ? rad * cs : rad * sn;
+            if (odd) s_zs[i - nb0] = rad * sn;
+          } else {
+            z = s_zs[i - nb0];
+          }
+          const uint4 w1 = philox4x32_10(make_uint4(1u, 0u, static_cast<uint32_t>(i), k), a.key0, a.key1);
+          const double u = uniform53(w1.x, w1.y);
+          const double Y = fma(S[m], z, chi[m]);
+          double delta, eY = 0.0, llY = 0.0;
+          if (!M::support(Y, tc)) {
+            delta = -INFINITY;
+          } else {
+            eY = M::kExp ? exp_tab(Y, s_math) : 0.0;
+            llY = M::loglike(Y, eY, yv, av, a.mc);
+            const double lpY = llY + M::logf(Y, eY, tc);
+            const double lpX = ll[m] + M::logf(chi[m], echi[m], tc);
+            delta = lpY - lpX;
+          }
+          const bool dneg = dsign(delta);  // -inf and -0 included; NaN is counted below
+          const double alpha = dneg ? exp_tab(delta, s_math) : 1.0;
+          const bool acc = !dneg || (__double_as_longlong(u) < __double_as_longlong(alpha));  // both >= +0
+          if (disnan(delta)) member_nan++;
+          if (acc) {
+            chi[m] = Y;
+            echi[m] = eY;
+            ll[m] = llY;
+            member_acc++;
+          }
+          S[m] *= sqrt(fma(eta, alpha - a.astar, 1.0));
+          if (trace) {
+            const long long o = (a.trace_off + s) * a.n + static_cast<long long>(i);
+            a.tr_delta[o] = delta;
+            a.tr_u[o] = u;
+            a.tr_acc[o] = acc ? 1 : 0;
+          }
         }
       }
     }
@@ -445,13 +611,33 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     xacc_zero(xe);
     XFlags fd = {0u, 0u, 0u}, fe = {0u, 0u, 0u};
     unsigned int neg_big = 0, pos_big = 0;
-    if (prior_ok) {
+    if (prior_ok && F32) {
+      const ThetaCf tf = s_tcf, tpf = s_tcpf;
 #pragma unroll
       for (int m = 0; m < K; ++m) {
         const unsigned int i = nb0 + tid + m * blockDim.x;
         if (i < nb1) {
-          const double dn = M::support(chi[m], tcp) ? M::logf(chi[m], echi[m], tcp) - M::logf(chi[m], echi[m], tc)
-                                                   : -INFINITY;
+          const float c = static_cast<float>(chi[m]);
+          const float dn = M::support32(c, tpf) ? M::logf32(c, tpf) - M::logf32(c, tf) : -INFINITY;
+          if (dn != dn) fd.nan++;
+          else if (fabsf(dn) >= 0x1p94f) {
+            if (dn < 0.0f) neg_big++;
+            else pos_big++;
+          } else {
+            xacc_add_float(xd, dn, fd);
+          }
+        }
+      }
+    }
+    if (prior_ok && !F32) {
+#pragma unroll
+      for (int m = 0; m < K; ++m) {
+        const unsigned int i = nb0 + tid + m * blockDim.x;
+        if (i < nb1) {
+          const double dn = M::support(static_cast<double>(chi[m]), tcp)
+                                ? M::logf(static_cast<double>(chi[m]), static_cast<double>(echi[m]), tcp) -
+                                      M::logf(static_cast<double>(chi[m]), static_cast<double>(echi[m]), tc)
+                                : -INFINITY;
           if (disnan(dn)) fd.nan++;
           else if (dhuge(dn)) {
             if (dsign(dn)) neg_big++;  // off the support of theta' (-inf) or hopeless
@@ -461,8 +647,8 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
           }
         }
       }
-      if (is_lf) lf_segment_pairs(a, nseg, sL, sG, sK, s_phi, xe, fe);
     }
+    if (prior_ok && is_lf) lf_segment_pairs(a, nseg, sL, sG, sK, s_phi, xe, fe);
 
     // a5: block partial
     {
@@ -565,6 +751,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
           if (acc) {
             for (int q = 0; q < p; ++q) s_theta[q] = s_thp[q];
             s_tc = s_tcp;
+            s_tcf = s_tcpf;
             s_lpri = s_lpri_new;
             if (is_lf) {
               s_etabar = eb_new;
@@ -593,7 +780,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   for (int m = 0; m < K; ++m) {
     const unsigned int i = nb0 + tid + m * blockDim.x;
     if (i < nb1) {
-      a.chi[i] = chi[m];
+      a.chi[i] = static_cast<double>(chi[m]);
       a.S[i] = S[m];
     }
   }
@@ -620,15 +807,20 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   }
 }
 
-template <class M>
-static const void* kernel_for(int K) {
+template <class M, bool F32>
+static const void* kernel_for_p(int K) {
   switch (K) {
-    case 1: return reinterpret_cast<const void*>(&sweep_kernel<M, 1>);
-    case 2: return reinterpret_cast<const void*>(&sweep_kernel<M, 2>);
-    case 4: return reinterpret_cast<const void*>(&sweep_kernel<M, 4>);
-    case 8: return reinterpret_cast<const void*>(&sweep_kernel<M, 8>);
+    case 1: return reinterpret_cast<const void*>(&sweep_kernel<M, 1, F32>);
+    case 2: return reinterpret_cast<const void*>(&sweep_kernel<M, 2, F32>);
+    case 4: return reinterpret_cast<const void*>(&sweep_kernel<M, 4, F32>);
+    case 8: return reinterpret_cast<const void*>(&sweep_kernel<M, 8, F32>);
     default: return nullptr;
   }
+}
+
+template <class M>
+static const void* kernel_for(int K, bool f32) {
+  return f32 ? kernel_for_p<M, true>(K) : kernel_for_p<M, false>(K);
 }
 
 size_t sweep_smem_bytes(int model, int mpb, int rows_smem) {
@@ -647,7 +839,7 @@ template <class M>
 static cudaError_t launch_model(const SweepArgs& a, int K, int grid, int block, cudaStream_t st) {
   void* args[] = {const_cast<SweepArgs*>(&a)};
   const size_t smem = sweep_smem_bytes(a.model, a.mpb, a.rows_smem);
-  const void* fn = kernel_for<M>(K);
+  const void* fn = kernel_for<M>(K, a.f32 != 0);
   if (!fn) return cudaErrorInvalidValue;
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
 }
@@ -658,20 +850,20 @@ cudaError_t launch_sweep(const SweepArgs& a, int K, int grid, int block, cudaStr
   return cudaErrorInvalidValue;
 }
 
-static const void* sweep_fn(int model, int K) {
-  if (model == CUDAHM_NN1) return kernel_for<NN1>(K);
-  if (model == CUDAHM_LF) return kernel_for<LF>(K);
+static const void* sweep_fn(int model, int K, bool f32) {
+  if (model == CUDAHM_NN1) return kernel_for<NN1>(K, f32);
+  if (model == CUDAHM_LF) return kernel_for<LF>(K, f32);
   return nullptr;
 }
 
-cudaError_t sweep_set_smem(int model, int K, int smem_bytes) {
-  const void* fn = sweep_fn(model, K);
+cudaError_t sweep_set_smem(int model, int K, bool f32, int smem_bytes) {
+  const void* fn = sweep_fn(model, K, f32);
   if (!fn) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
 }
 
-cudaError_t sweep_occupancy(int model, int K, int block, int smem_bytes, int* blocks_per_sm) {
-  const void* fn = sweep_fn(model, K);
+cudaError_t sweep_occupancy(int model, int K, bool f32, int block, int smem_bytes, int* blocks_per_sm) {
+  const void* fn = sweep_fn(model, K, f32);
   if (!fn) return cudaErrorInvalidValue;
   if (smem_bytes > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
@@ -837,8 +1029,9 @@ cudaError_t launch_tables(int p, uint32_t key0, uint32_t key1, long long k0, lon
   return cudaGetLastError();
 }
 
-// Per-member log target at theta (read from device memory).
-template <class M>
+// Per-member log target at theta (read from device memory), in the handle's precision: the
+// FP32 form evaluates exactly the binary32 expressions its member step uses.
+template <class M, bool F32>
 __global__ void eval_logdens_kernel(long long n, const double* y, const double* aux, const double* chi,
                                     const double* theta, ModelConsts mc, double* out) {
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -846,6 +1039,18 @@ __global__ void eval_logdens_kernel(long long n, const double* y, const double* 
   double th[kMaxP];
   for (int q = 0; q < 3; ++q) th[q] = theta[q];
   const ThetaC tc = M::consts(th);
+  if (F32) {
+    const ThetaCf tf = M::consts32(tc);
+    const float c = static_cast<float>(chi[i]);
+    if (!M::support32(c, tf)) {
+      out[i] = -INFINITY;
+      return;
+    }
+    float d[M::kData32];
+    M::data32(y[i], aux[i], mc, d);
+    out[i] = static_cast<double>(M::loglike32(c, d)) + static_cast<double>(M::logf32(c, tf));
+    return;
+  }
   const double c = chi[i];
   if (!M::support(c, tc)) {
     out[i] = -INFINITY;
@@ -855,13 +1060,20 @@ __global__ void eval_logdens_kernel(long long n, const double* y, const double* 
   out[i] = M::loglike(c, e, y[i], aux[i], mc) + M::logf(c, e, tc);
 }
 
-cudaError_t launch_eval_logdens(int model, long long n, const double* y, const double* aux, const double* chi,
-                                const double* theta_dev, const ModelConsts& mc, double* out, cudaStream_t st) {
+cudaError_t launch_eval_logdens(int model, bool f32, long long n, const double* y, const double* aux,
+                                const double* chi, const double* theta_dev, const ModelConsts& mc, double* out,
+                                cudaStream_t st) {
   const int blk = 256;
   const unsigned int grid = static_cast<unsigned int>((n + blk - 1) / blk);
-  if (model == CUDAHM_NN1) eval_logdens_kernel<NN1><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, out);
-  else if (model == CUDAHM_LF) eval_logdens_kernel<LF><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, out);
-  else return cudaErrorInvalidValue;
+  if (model == CUDAHM_NN1) {
+    if (f32) eval_logdens_kernel<NN1, true><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, out);
+    else eval_logdens_kernel<NN1, false><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, out);
+  } else if (model == CUDAHM_LF) {
+    if (f32) eval_logdens_kernel<LF, true><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, out);
+    else eval_logdens_kernel<LF, false><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, out);
+  } else {
+    return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
