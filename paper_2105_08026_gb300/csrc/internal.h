@@ -62,6 +62,7 @@ struct SweepArgs {
   const double* qs;  // q(r_k)/sigma_F
   const double* Wr;  // inner weights
   const double* phi_coef;  // Taylor table of the normal CDF
+  const double* cw;        // prefix sums of the inner weights (n_r + 1)
   const double* math_tab;  // exp/log tables
   int nL, nr;
   int rows_smem;     // segment slots per block for the outer-node values
@@ -90,6 +91,7 @@ cudaError_t launch_sweep(const SweepArgs& a, int K, int grid, int block, cudaStr
 cudaError_t sweep_occupancy(int model, int K, bool f32, int block, int smem_bytes, int* blocks_per_sm);
 size_t sweep_smem_bytes(int model, int mpb, int rows_smem);
 cudaError_t launch_phi_table(double* coef, cudaStream_t st);
+cudaError_t launch_prefix_weights(int nr, const double* Wr, double* cw, cudaStream_t st);
 cudaError_t launch_math_table(double* t, cudaStream_t st);
 int math_table_words();
 int phi_table_words();

@@ -27,10 +27,10 @@ namespace {
 constexpr int kNoallocMaxNodes = CUDAHM_NOALLOC_MAX_NODES;
 constexpr int kNoallocMaxGrid = 1024;
 constexpr int kPhiWordsMax = 133 * 11;  // normal-CDF Taylor table
-// layout in doubles: xL, wL, xr, wr, qs, Wr (max nodes each), the Phi table, then the
-// per-block partials (4 x u64 per block)
-constexpr size_t kScratchDoubles =
-    6 * static_cast<size_t>(kNoallocMaxNodes) + kPhiWordsMax + 4 * static_cast<size_t>(kNoallocMaxGrid);
+// layout in doubles: xL, wL, xr, wr, qs, Wr (max nodes each), the Phi table, the prefix sums
+// of the inner weights (max nodes + 1), then the per-block partials (4 x u64 per block)
+constexpr size_t kScratchDoubles = 6 * static_cast<size_t>(kNoallocMaxNodes) + kPhiWordsMax +
+                                   (kNoallocMaxNodes + 1) + 4 * static_cast<size_t>(kNoallocMaxGrid);
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
@@ -86,7 +86,8 @@ extern "C" int cudahm_lf_etabar_noalloc(const double* theta_dev, const double* c
   double* qs = wr + kNoallocMaxNodes;
   double* Wr = qs + kNoallocMaxNodes;
   double* phi = Wr + kNoallocMaxNodes;
-  unsigned long long* partials = reinterpret_cast<unsigned long long*>(phi + kPhiWordsMax);
+  double* cw = phi + kPhiWordsMax;
+  unsigned long long* partials = reinterpret_cast<unsigned long long*>(cw + kNoallocMaxNodes + 1);
   if (phi_table_words() > kPhiWordsMax) return noalloc_fail(CUDAHM_ECUDA, "normal-CDF table larger than its slot");
 
   // every table this call reads is rewritten here, on the caller's stream
@@ -94,6 +95,7 @@ extern "C" int cudahm_lf_etabar_noalloc(const double* theta_dev, const double* c
   if (e == cudaSuccess) e = launch_gauss_legendre(nr, xr, wr, st);
   if (e == cudaSuccess) e = launch_lf_inner(nr, xr, wr, rmax, sigF, qs, Wr, st);
   if (e == cudaSuccess) e = launch_phi_table(phi, st);
+  if (e == cudaSuccess) e = launch_prefix_weights(nr, Wr, cw, st);
   if (e != cudaSuccess) return noalloc_fail(CUDAHM_ECUDA, cudaGetErrorString(e));
 
   SweepArgs rule{};
@@ -106,6 +108,7 @@ extern "C" int cudahm_lf_etabar_noalloc(const double* theta_dev, const double* c
   rule.qs = qs;
   rule.Wr = Wr;
   rule.phi_coef = phi;
+  rule.cw = cw;
   rule.mc.cth = Fth / sigF;
   rule.mc.ln_upper = ln_upper;
   const long long G = static_cast<long long>(nL) * ((nr + 127) / 128);

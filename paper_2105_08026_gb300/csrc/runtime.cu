@@ -83,6 +83,7 @@ struct cudahm {
   // LF rule
   double *xL = nullptr, *wL = nullptr, *xr = nullptr, *wr = nullptr, *qs = nullptr, *Wr = nullptr;
   double* phi_coef = nullptr;
+  double* cw = nullptr;
   double* math_tab = nullptr;
   unsigned long long* eb_partials = nullptr;
   int eb_grid = 0, eb_rows_smem = 1;
@@ -264,6 +265,7 @@ SweepArgs base_args(cudahm* h) {
   a.qs = h->qs;
   a.Wr = h->Wr;
   a.phi_coef = h->phi_coef;
+  a.cw = h->cw;
   a.math_tab = h->math_tab;
   a.nL = h->cfg.model == CUDAHM_LF ? static_cast<int>(h->cfg.model_consts[3]) : 0;
   a.nr = h->cfg.model == CUDAHM_LF ? static_cast<int>(h->cfg.model_consts[4]) : 0;
@@ -416,13 +418,15 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
     if ((rc = alloc_into(h, &h->xL, nL)) || (rc = alloc_into(h, &h->wL, nL)) || (rc = alloc_into(h, &h->xr, nr)) ||
         (rc = alloc_into(h, &h->wr, nr)) || (rc = alloc_into(h, &h->qs, nr)) || (rc = alloc_into(h, &h->Wr, nr)) ||
         (rc = alloc_into(h, &h->eb_partials, 4ull * h->eb_grid)) ||
-        (rc = alloc_into(h, &h->phi_coef, static_cast<size_t>(phi_table_words()))))
+        (rc = alloc_into(h, &h->phi_coef, static_cast<size_t>(phi_table_words()))) ||
+        (rc = alloc_into(h, &h->cw, static_cast<size_t>(nr) + 1)))
       return bail(rc);
     if (launch_phi_table(h->phi_coef, h->stream) != cudaSuccess)
       return bail(fail(CUDAHM_ECUDA, "normal-CDF table set-up failed: %s", cudaGetErrorString(cudaGetLastError())));
     if (launch_gauss_legendre(nL, h->xL, h->wL, h->stream) != cudaSuccess ||
         launch_gauss_legendre(nr, h->xr, h->wr, h->stream) != cudaSuccess ||
-        launch_lf_inner(nr, h->xr, h->wr, k[2], k[0], h->qs, h->Wr, h->stream) != cudaSuccess)
+        launch_lf_inner(nr, h->xr, h->wr, k[2], k[0], h->qs, h->Wr, h->stream) != cudaSuccess ||
+        launch_prefix_weights(nr, h->Wr, h->cw, h->stream) != cudaSuccess)
       return bail(fail(CUDAHM_ECUDA, "quadrature set-up failed: %s", cudaGetErrorString(cudaGetLastError())));
   }
   if (launch_math_table(h->math_tab, h->stream) != cudaSuccess)

@@ -285,36 +285,127 @@ __device__ __forceinline__ int lf_block_segments(const SweepArgs& a, int b, int 
   return (b < G) ? (G - b + B - 1) / B : 0;
 }
 
-// Per-segment outer-node values: L_j = e^t_j and G_j = (half-width) w_j g(e^t_j) e^t_j on
-// t in [ln L_low, ln L* + ln_upper], and the first inner node of the segment.
-__device__ __forceinline__ void lf_segment_rows(const ThetaC& tc, const SweepArgs& a, int b, int B, int nseg,
-                                                double* sL, double* sG, int* sK) {
+// Per-block segment table in shared memory, R slots: L_j, G_j, the row's prefix term, the
+// first active inner node kb and the exclusive offsets of the active pair counts (R + 1).
+struct SegTab {
+  double* L;
+  double* G;
+  double* pre;
+  int* kb;
+  int* off;
+};
+__host__ __device__ inline size_t segtab_bytes(int R) {
+  return 3 * sizeof(double) * static_cast<size_t>(R) + sizeof(int) * (2 * static_cast<size_t>(R) + 1);
+}
+__device__ __forceinline__ SegTab segtab_carve(double* base, int R) {
+  SegTab t;
+  t.L = base;
+  t.G = base + R;
+  t.pre = base + 2 * R;
+  t.kb = reinterpret_cast<int*>(base + 3 * R);
+  t.off = t.kb + R;
+  return t;
+}
+
+// Values of segment t (one thread): L_j = e^t_j, G_j = (half-width) w_j g(e^t_j) e^t_j on
+// t in [ln L_low, ln L* + ln_upper]. Since x_jk = L_j qs_k - F_th/sigma_F decreases along the
+// inner nodes (r ascending), the pairs with x > 8.5, where Phi is exactly 1, are a prefix
+// k < k*_j of the row; they contribute G_j CW[k*_j] with CW the prefix sums of the inner
+// weights, added once per row (by its segment s = 0). Only k >= max(k*_j, s kSeg) is left to
+// evaluate; the count goes to off[t] until the block scans it.
+__device__ __forceinline__ void lf_segment_row(const ThetaC& tc, const SweepArgs& a, int b, int B, int t,
+                                               const SegTab& tab) {
   const double lo = tc.a3, hi = tc.a1 + a.mc.ln_upper;
   const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
-  for (int t = threadIdx.x; t < nseg; t += blockDim.x) {
-    const int g = b + t * B;
-    const int j = g % a.nL;
-    const double tt = fma(half, __ldg(a.xL + j), mid);
-    const double x = tt - tc.a1;
-    sL[t] = exp(tt);
-    sG[t] = half * __ldg(a.wL + j) * exp(fma(tc.a0, x, -exp(x)));
-    sK[t] = (g / a.nL) << kSegShift;
+  const int g = b + t * B;
+  const int j = g % a.nL;
+  const int sseg = g / a.nL;
+  const double tt = fma(half, __ldg(a.xL + j), mid);
+  const double x = tt - tc.a1;
+  const double L = exp(tt);
+  const double G = half * __ldg(a.wL + j) * exp(fma(tc.a0, x, -exp(x)));
+  const double mcth = -a.mc.cth;
+  int klo = 0, khi = a.nr;  // first k with x_jk <= 8.5 (bit test, as in phi_table)
+  while (klo < khi) {
+    const int km = (klo + khi) >> 1;
+    if (__double_as_longlong(fma(L, __ldg(a.qs + km), mcth)) > 0x4021000000000000ll) klo = km + 1;
+    else khi = km;
+  }
+  const int k0 = sseg << kSegShift;
+  const int kend = min(k0 + kSeg, a.nr);
+  const int kb = max(k0, klo);
+  tab.L[t] = L;
+  tab.G[t] = G;
+  tab.pre[t] = (sseg == 0 && klo > 0) ? G * __ldg(a.cw + klo) : 0.0;
+  tab.kb[t] = kb;
+  tab.off[t] = max(0, kend - kb);
+}
+
+// Exclusive scan of the active counts (one warp); off[nseg] receives the total.
+__device__ __forceinline__ void lf_segment_scan(int nseg, const SegTab& tab) {
+  const int lane = threadIdx.x & 31;
+  int carry = 0;
+  for (int base = 0; base < nseg; base += 32) {
+    const int t = base + lane;
+    const int c = (t < nseg) ? tab.off[t] : 0;
+    int v = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    if (t < nseg) tab.off[t] = carry + v - c;
+    carry += __shfl_sync(0xffffffffu, v, 31);
+  }
+  if (lane == 0) tab.off[nseg] = carry;
+}
+
+// All segment rows and the scan by the whole block (set-up paths).
+__device__ __forceinline__ void lf_segment_rows(const ThetaC& tc, const SweepArgs& a, int b, int B, int nseg,
+                                                const SegTab& tab) {
+  for (int t = threadIdx.x; t < nseg; t += blockDim.x) lf_segment_row(tc, a, b, B, t, tab);
+  __syncthreads();
+  if (threadIdx.x < 32) lf_segment_scan(nseg, tab);
+}
+
+// The block's active pairs (all lanes busy) and its rows' prefix terms; each term
+// G_j W_k Phi((L_j q_k - F_th)/sigma_F) is added exactly.
+__device__ __forceinline__ void lf_segment_pairs(const SweepArgs& a, int nseg, const SegTab& tab, const double* s_phi,
+                                                 Xacc& xe, XFlags& fe) {
+  const int total = tab.off[nseg];
+  const double mcth = -a.mc.cth;
+  for (int q = threadIdx.x; q < total; q += blockDim.x) {
+    int lo = 0, hi = nseg - 1;  // last segment with off <= q
+    while (lo < hi) {
+      const int m = (lo + hi + 1) >> 1;
+      if (tab.off[m] <= q) lo = m;
+      else hi = m - 1;
+    }
+    const int k = tab.kb[lo] + (q - tab.off[lo]);
+    const double x = fma(tab.L[lo], __ldg(a.qs + k), mcth);
+    xacc_add_double(xe, tab.G[lo] * (__ldg(a.Wr + k) * phi_table(x, s_phi)), fe);
+  }
+  for (int t = threadIdx.x; t < nseg; t += blockDim.x)
+    if (tab.pre[t] != 0.0) xacc_add_double(xe, tab.pre[t], fe);
+}
+
+// Prefix sums of the inner weights, CW[k] = sum_{k' < k} W_k' (k = 0..nr), each rounded once
+// from an exact running sum.
+__global__ void prefix_weights_kernel(int nr, const double* Wr, double* cw) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  Xacc acc;
+  xacc_zero(acc);
+  XFlags f = {0u, 0u, 0u};
+  cw[0] = 0.0;
+  for (int k = 0; k < nr; ++k) {
+    xacc_add_double(acc, Wr[k], f);
+    cw[k + 1] = xacc_to_double(acc);
   }
 }
 
-// Pairs of this block's segments; each term G_j W_k Phi((L_j q_k - F_th)/sigma_F) is added exactly.
-__device__ __forceinline__ void lf_segment_pairs(const SweepArgs& a, int nseg, const double* sL, const double* sG,
-                                                 const int* sK, const double* s_phi, Xacc& xe, XFlags& fe) {
-  const int total = nseg << kSegShift;
-  const double mcth = -a.mc.cth;
-  for (int q = threadIdx.x; q < total; q += blockDim.x) {
-    const int t = q >> kSegShift;
-    const int k = sK[t] + (q & (kSeg - 1));
-    if (k < a.nr) {
-      const double x = fma(sL[t], __ldg(a.qs + k), mcth);
-      xacc_add_double(xe, sG[t] * (__ldg(a.Wr + k) * phi_table(x, s_phi)), fe);
-    }
-  }
+cudaError_t launch_prefix_weights(int nr, const double* Wr, double* cw, cudaStream_t st) {
+  prefix_weights_kernel<<<1, 1, 0, st>>>(nr, Wr, cw);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------- block reduce helpers ------
@@ -392,9 +483,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     for (int q = tid; q < kPhiWords; q += blockDim.x) s_phi[q] = a.phi_coef[q];
   for (int q = tid; q < kMathWords; q += blockDim.x) s_math[q] = a.math_tab[q];
   const int nseg = is_lf ? lf_block_segments(a, blockIdx.x, gridDim.x) : 0;
-  double* sL = s_rows;
-  double* sG = s_rows + a.rows_smem;
-  int* sK = reinterpret_cast<int*>(s_rows + 2 * a.rows_smem);
+  const SegTab tab = segtab_carve(s_rows, a.rows_smem);
 
   if (tid == 0) {
     for (int q = 0; q < p; ++q) s_theta[q] = a.chain->theta[q];
@@ -417,7 +506,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     s_tcpf = M::consts32(tcp);
   }
   __syncthreads();
-  if (is_lf && s_lpri_new != -INFINITY) lf_segment_rows(s_tcp, a, blockIdx.x, gridDim.x, nseg, sL, sG, sK);
+  if (is_lf && s_lpri_new != -INFINITY) lf_segment_rows(s_tcp, a, blockIdx.x, gridDim.x, nseg, tab);
 
   // members of this thread: i = nb0 + tid + m blockDim (latent, RAM factor, e^chi, log l in registers)
   R chi[K], echi[K], ll[K];
@@ -483,17 +572,9 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
       __syncwarp();
       if (is_lf && s_lpri_new != -INFINITY) {
         const ThetaC tcp = s_tcp;
-        const double lo = tcp.a3, hi = tcp.a1 + a.mc.ln_upper;
-        const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
-        for (int t = lane; t < nseg; t += 32) {
-          const int g = blockIdx.x + t * gridDim.x;
-          const int j = g % a.nL;
-          const double tt = fma(half, __ldg(a.xL + j), mid);
-          const double x = tt - tcp.a1;
-          sL[t] = exp(tt);
-          sG[t] = half * __ldg(a.wL + j) * exp(fma(tcp.a0, x, -exp(x)));
-          sK[t] = (g / a.nL) << kSegShift;
-        }
+        for (int t = lane; t < nseg; t += 32) lf_segment_row(tcp, a, blockIdx.x, gridDim.x, t, tab);
+        __syncwarp();
+        lf_segment_scan(nseg, tab);
       }
     }
 
@@ -648,7 +729,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         }
       }
     }
-    if (prior_ok && is_lf) lf_segment_pairs(a, nseg, sL, sG, sK, s_phi, xe, fe);
+    if (prior_ok && is_lf) lf_segment_pairs(a, nseg, tab, s_phi, xe, fe);
 
     // a5: block partial
     {
@@ -825,7 +906,7 @@ static const void* kernel_for(int K, bool f32) {
 
 size_t sweep_smem_bytes(int model, int mpb, int rows_smem) {
   return sizeof(double) * kMathWords + (model == CUDAHM_LF ? sizeof(double) * kPhiWords : 0) +
-         3 * sizeof(double) * static_cast<size_t>(mpb) + (2 * sizeof(double) + sizeof(int)) * rows_smem;
+         3 * sizeof(double) * static_cast<size_t>(mpb) + segtab_bytes(rows_smem);
 }
 
 cudaError_t launch_math_table(double* t, cudaStream_t st) {
@@ -1091,17 +1172,15 @@ __global__ void etabar_partial_kernel(const double* theta, const SweepArgs a, un
   __syncthreads();
   const int nseg = lf_block_segments(a, blockIdx.x, gridDim.x);
   double* s_phi = s_rows;
-  double* sL = s_rows + kPhiWords;
-  double* sG = sL + a.rows_smem;
-  int* sK = reinterpret_cast<int*>(sG + a.rows_smem);
+  const SegTab tab = segtab_carve(s_rows + kPhiWords, a.rows_smem);
   for (int q = threadIdx.x; q < kPhiWords; q += blockDim.x) s_phi[q] = a.phi_coef[q];
-  lf_segment_rows(s_tc, a, blockIdx.x, gridDim.x, nseg, sL, sG, sK);
+  lf_segment_rows(s_tc, a, blockIdx.x, gridDim.x, nseg, tab);
   __syncthreads();
   Xacc xd, xe;
   xacc_zero(xd);
   xacc_zero(xe);
   XFlags fe = {0u, 0u, 0u};
-  lf_segment_pairs(a, nseg, sL, sG, sK, s_phi, xe, fe);
+  lf_segment_pairs(a, nseg, tab, s_phi, xe, fe);
   unsigned int f[4] = {0u, fe.nan, fe.big, 0u};
   warp_reduce(xd, xe, f);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1149,7 +1228,7 @@ __global__ void etabar_final_kernel(const unsigned long long* partials, int nblo
 
 cudaError_t launch_eval_etabar(const double* theta_dev, const SweepArgs& rule, unsigned long long* partials,
                                int grid, double* out, cudaStream_t st) {
-  const size_t smem = sizeof(double) * kPhiWords + (2 * sizeof(double) + sizeof(int)) * static_cast<size_t>(rule.rows_smem);
+  const size_t smem = sizeof(double) * kPhiWords + segtab_bytes(rule.rows_smem);
   etabar_partial_kernel<<<grid, 256, smem, st>>>(theta_dev, rule, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
