@@ -218,6 +218,30 @@ int cudahm_restore(cudahm_t h, const void* buf, size_t size);
 int cudahm_lf_etabar_noalloc(const double* theta_dev, const double* consts_host, double* etabar_dev,
                              void* cuda_stream);
 
+/* Launch shape of a batched run. Zero fields are chosen automatically: the block size by two
+ * 16-sweep trial launches at the start of the run (128 and 256 threads; the faster device
+ * time per sweep wins and is cached per (precision, number of populations, LF count, size
+ * class) for the process), the sweeps per launch as clamp(total/4, 256, 4096). A
+ * population's chain does not depend on the launch shape (all sums are exact), so the trial
+ * launches are ordinary sweeps of the run. */
+typedef struct {
+  int32_t block_threads;      /* 128 or 256; 0 = tune */
+  int32_t sweeps_per_launch;  /* sweeps between launches (each launch ends with a grid-wide sync); 0 = tune */
+  int32_t use_graph;          /* 1: replay the launch sequence from a captured CUDA graph */
+  int32_t reserved;           /* out: number of blocks of the launch */
+} cudahm_tune;
+
+/* Run n_burn + n_iter sweeps of k populations (handles created and loaded as usual, on one
+ * device, one precision, without traces) in one persistent launch per chunk of sweeps.
+ * Population q gets a block range sized by a cost model (members, selection-rule pairs),
+ * refined twice from each population's measured device time; its blocks meet at a bounded
+ * per-population barrier each sweep, so populations never wait for one another. Every
+ * population's chain and samples are bit-identical to what cudahm_run gives for it alone.
+ * Work goes to handle 0's stream; the call blocks. tune may be NULL; chosen (nullable)
+ * receives the shape used. On failure every handle's chain stops where its last launch ended. */
+int cudahm_batch_run(cudahm_t* handles, int32_t k, int64_t n_burn, int64_t n_iter, int64_t thin,
+                     const cudahm_tune* tune, cudahm_tune* chosen);
+
 /* sizeof(cudahm_config) and sizeof(cudahm_stats) as compiled into the library, so that
  * bindings can check their struct layouts. */
 size_t cudahm_sizeof_config(void);

@@ -1,0 +1,489 @@
+// Many populations in one persistent cooperative launch (batched form).
+//
+// Population p owns the contiguous block range [b0_p, b0_p + nb_p), sized by the host from
+// a cost model (members, the selection rule's pairs, fixed per-sweep work). Its blocks split
+// its members into equal contiguous ranges and deal its rule segments round-robin, exactly
+// as the single-population kernel does over the whole grid, and meet at a bounded
+// per-population barrier each sweep; populations never wait for each other. Member state
+// streams from device memory each sweep (latent, RAM factor; the cached e^chi and log l_i are
+// recomputed with the same routines), so a population's chain is bit-identical to the one
+// the single-population kernel produces for it: every sum is exact and every per-member
+// value is the same function of the same inputs.
+//
+// Launches are chunk-invariant: each population's progress through the current run lives
+// in device memory, so one captured CUDA graph (theta tables, barrier reset, this kernel)
+// is replayed for every chunk of sweeps.
+#include <cuda_runtime.h>
+
+#include "sweep_common.cuh"
+
+namespace chm {
+
+namespace {
+
+__device__ __forceinline__ int find_pop(const int* b0s, int npop, int b) {
+  int lo = 0, hi = npop - 1;  // last population whose first block is <= b
+  while (lo < hi) {
+    const int m = (lo + hi + 1) >> 1;
+    if (b0s[m] <= b) lo = m;
+    else hi = m - 1;
+  }
+  return lo;
+}
+
+// Per-population barrier: counter `count` reaches (index + 1) * nb.
+__device__ __forceinline__ bool pop_barrier(unsigned int* count, unsigned int index, unsigned int nb, int* err,
+                                            long long limit_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(count, 1u);
+    const unsigned int target = (index + 1u) * nb;
+    const long long t0 = globaltimer_ns();
+    while (true) {
+      if (ld_acquire_u32(count) >= target) break;
+      if (ld_volatile_i32(err) != 0) { ok = 0; break; }
+      if (globaltimer_ns() - t0 > limit_ns) {
+        atomicCAS(err, 0, CUDAHM_ETIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    if (ld_volatile_i32(err) != 0) ok = 0;
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// One member's sweep: RAM step under theta, then its theta' partial (FP64 form).
+template <class M>
+__device__ __forceinline__ void member_f64(const SweepArgs& a, unsigned int i, uint32_t k, double eta,
+                                           const ThetaC& tc, const ThetaC& tcp, bool prior_ok, const double* s_math,
+                                           Xacc& xd, XFlags& fd, unsigned int& neg_big, unsigned int& pos_big,
+                                           unsigned int& nan_cnt, unsigned int& acc_cnt) {
+  double chi = a.chi[i], S = a.S[i];
+  const double yv = a.y[i], av = a.aux[i];
+  double echi = M::kExp ? exp_tab(chi, s_math) : 0.0;
+  double ll = M::loglike(chi, echi, yv, av, a.mc);
+  const bool odd = (k & 1u) != 0u;
+  const uint4 w0 = philox4x32_10(make_uint4(0u, 0u, i, odd ? k : k - 1u), a.key0, a.key1);
+  const double ua = uniform53(w0.x, w0.y), ub = uniform53(w0.z, w0.w);
+  const double rad = sqrt(-2.0 * log_tab(ua, s_math));
+  double sn, cs;
+  sincospi(2.0 * ub, &sn, &cs);
+  const double z = odd ? rad * cs : rad * sn;
+  const uint4 w1 = philox4x32_10(make_uint4(1u, 0u, i, k), a.key0, a.key1);
+  const double u = uniform53(w1.x, w1.y);
+  const double Y = fma(S, z, chi);
+  double delta, eY = 0.0, llY = 0.0;
+  if (!M::support(Y, tc)) {
+    delta = -INFINITY;
+  } else {
+    eY = M::kExp ? exp_tab(Y, s_math) : 0.0;
+    llY = M::loglike(Y, eY, yv, av, a.mc);
+    delta = (llY + M::logf(Y, eY, tc)) - (ll + M::logf(chi, echi, tc));
+  }
+  const bool dneg = dsign(delta);
+  const double alpha = dneg ? exp_tab(delta, s_math) : 1.0;
+  const bool acc = !dneg || (__double_as_longlong(u) < __double_as_longlong(alpha));
+  if (disnan(delta)) nan_cnt++;
+  if (acc) {
+    chi = Y;
+    echi = eY;
+    acc_cnt++;
+  }
+  S *= sqrt(fma(eta, alpha - a.astar, 1.0));
+  a.chi[i] = chi;
+  a.S[i] = S;
+  if (prior_ok) {
+    const double dn = M::support(chi, tcp) ? M::logf(chi, echi, tcp) - M::logf(chi, echi, tc) : -INFINITY;
+    if (disnan(dn)) fd.nan++;
+    else if (dhuge(dn)) {
+      if (dsign(dn)) neg_big++;
+      else pos_big++;
+    } else {
+      xacc_add_double(xd, dn, fd);
+    }
+  }
+}
+
+// One member's sweep in the FP32 bulk form (binary32 member terms, binary64 RAM factor).
+template <class M>
+__device__ __forceinline__ void member_f32(const SweepArgs& a, unsigned int i, uint32_t k, double eta,
+                                           const ThetaCf& tf, const ThetaCf& tpf, bool prior_ok, Xacc& xd,
+                                           XFlags& fd, unsigned int& neg_big, unsigned int& pos_big,
+                                           unsigned int& nan_cnt, unsigned int& acc_cnt) {
+  float chi = static_cast<float>(a.chi[i]);
+  double S = a.S[i];
+  float d[M::kData32];
+#pragma unroll
+  for (int c = 0; c < M::kData32; ++c) d[c] = __ldg(a.d32 + static_cast<size_t>(c) * a.n + i);
+  const float ll = M::loglike32(chi, d);
+  const bool odd = (k & 1u) != 0u;
+  const uint4 w = philox4x32_10(make_uint4(0u, 2u, i, odd ? k : k - 1u), a.key0, a.key1);
+  const float u1 = (static_cast<float>(w.x >> 8) + 0.5f) * 0x1p-24f;
+  const float u2 = (static_cast<float>(w.y >> 8) + 0.5f) * 0x1p-24f;
+  const float u = (static_cast<float>((odd ? w.z : w.w) >> 8) + 0.5f) * 0x1p-24f;
+  const float rad = sqrtf(-2.0f * logf(u1));
+  float sn, cs;
+  sincospif(2.0f * u2, &sn, &cs);
+  const float z = odd ? rad * cs : rad * sn;
+  const float Y = fmaf(static_cast<float>(S), z, chi);
+  float delta;
+  if (!M::support32(Y, tf)) {
+    delta = -INFINITY;
+  } else {
+    delta = (M::loglike32(Y, d) + M::logf32(Y, tf)) - (ll + M::logf32(chi, tf));
+  }
+  const float alpha = (delta >= 0.0f) ? 1.0f : expf(delta);
+  const bool acc = (delta >= 0.0f) || (u < alpha);
+  if (delta != delta) nan_cnt++;
+  if (acc) {
+    chi = Y;
+    acc_cnt++;
+  }
+  S *= sqrt(fma(eta, static_cast<double>(alpha) - a.astar, 1.0));
+  a.chi[i] = static_cast<double>(chi);
+  a.S[i] = S;
+  if (prior_ok) {
+    const float dn = M::support32(chi, tpf) ? M::logf32(chi, tpf) - M::logf32(chi, tf) : -INFINITY;
+    if (dn != dn) fd.nan++;
+    else if (fabsf(dn) >= 0x1p94f) {
+      if (dn < 0.0f) neg_big++;
+      else pos_big++;
+    } else {
+      xacc_add_float(xd, dn, fd);
+    }
+  }
+}
+
+template <class M, bool F32>
+__device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int lb, int nb, int chunk, int R,
+                               double* s_dyn, double* s_theta, double* s_thp, double* s_Sth, BlockRed& s_red) {
+  __shared__ ThetaC s_tc, s_tcp;
+  __shared__ ThetaCf s_tcf, s_tcpf;
+  __shared__ double s_etabar, s_logeb, s_lpri, s_lpri_new;
+  __shared__ int s_stop;
+  __shared__ long long s_rows_written, s_tacc, s_k0, s_off, s_ns;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int p = a.p;
+  const bool is_lf = (a.model == CUDAHM_LF);
+  double* s_math = s_dyn;
+  double* s_phi = s_dyn + kMathWords;
+  const SegTab tab = segtab_carve(s_phi + kPhiWords, R);
+  const long long t_start = globaltimer_ns();
+  for (int q = tid; q < kMathWords; q += blockDim.x) s_math[q] = a.math_tab[q];
+  if (is_lf)
+    for (int q = tid; q < kPhiWords; q += blockDim.x) s_phi[q] = a.phi_coef[q];
+  if (tid == 0) {
+    s_k0 = a.chain->sweeps;
+    s_off = prog->off;
+    const long long left = prog->total - prog->off;
+    s_ns = left < chunk ? left : chunk;
+    for (int q = 0; q < p; ++q) s_theta[q] = a.chain->theta[q];
+    for (int q = 0; q < p * p; ++q) s_Sth[q] = a.chain->S_theta[q];
+    s_etabar = a.chain->etabar;
+    s_logeb = is_lf ? log(s_etabar) : 0.0;
+    s_tc = M::consts(s_theta);
+    s_tcf = M::consts32(s_tc);
+    s_lpri = M::logprior(s_theta, a.mc);
+    s_rows_written = 0;
+    s_tacc = 0;
+    s_stop = 0;
+  }
+  __syncthreads();
+  const long long ns = s_ns, k0 = s_k0, off = s_off;
+  const long long burn_left = prog->n_burn - off;
+  double* rows = a.rows ? a.rows + prog->rows * p : nullptr;
+  const unsigned int nb0 = static_cast<unsigned int>((a.n * lb) / nb);
+  const unsigned int nb1 = static_cast<unsigned int>((a.n * (lb + 1)) / nb);
+  const int nseg = is_lf ? lf_block_segments(a, lb, nb) : 0;
+  unsigned int member_acc = 0;
+
+  for (long long s = 0; s < ns; ++s) {
+    const uint32_t k = static_cast<uint32_t>(k0 + s + 1);
+    const double eta = __ldg(a.tab_eta + s);
+    // theta' = theta + S_theta U (the table of this launch's sweeps starts at index 0)
+    if (tid == 0) {
+      double lp;
+      ThetaC tcp;
+      propose_theta<M>(a, s, p, s_theta, s_Sth, s_thp, lp, tcp);
+      s_lpri_new = lp;
+      s_tcp = tcp;
+      s_tcpf = M::consts32(tcp);
+    }
+    __syncthreads();
+    const bool prior_ok = (s_lpri_new != -INFINITY);
+    Xacc xd, xe;
+    xacc_zero(xd);
+    xacc_zero(xe);
+    XFlags fd = {0u, 0u, 0u}, fe = {0u, 0u, 0u};
+    unsigned int neg_big = 0, pos_big = 0, member_nan = 0;
+    if constexpr (F32) {
+      const ThetaCf tf = s_tcf, tpf = s_tcpf;
+      for (unsigned int i = nb0 + tid; i < nb1; i += blockDim.x)
+        member_f32<M>(a, i, k, eta, tf, tpf, prior_ok, xd, fd, neg_big, pos_big, member_nan, member_acc);
+    } else {
+      const ThetaC tc = s_tc, tcp = s_tcp;
+      for (unsigned int i = nb0 + tid; i < nb1; i += blockDim.x)
+        member_f64<M>(a, i, k, eta, tc, tcp, prior_ok, s_math, xd, fd, neg_big, pos_big, member_nan, member_acc);
+    }
+    // a6: the rule's segments of this block, R at a time through the shared table
+    if (prior_ok && is_lf) {
+      const ThetaC tcp = s_tcp;
+      for (int t0 = 0; t0 < nseg; t0 += R) {
+        const int cnt = min(R, nseg - t0);
+        for (int q = tid; q < cnt; q += blockDim.x) lf_segment_row(tcp, a, lb, nb, t0 + q, q, tab);
+        __syncthreads();
+        if (wid == 0) lf_segment_scan(cnt, tab);
+        __syncthreads();
+        lf_segment_pairs(a, cnt, tab, s_phi, xe, fe);
+        __syncthreads();
+      }
+    }
+    {
+      unsigned int f[4] = {neg_big, fd.nan + fe.nan + fe.big + member_nan, pos_big, member_nan};
+      warp_reduce(xd, xe, f);
+      if (lane == 0) {
+        s_red.d[wid] = xd;
+        s_red.e[wid] = xe;
+        for (int q = 0; q < 4; ++q) s_red.f[wid][q] = f[q];
+      }
+      __syncthreads();
+      if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        Xacc bd, be;
+        unsigned int bf[4] = {0u, 0u, 0u, 0u};
+        xacc_zero(bd);
+        xacc_zero(be);
+        if (lane < nw) {
+          bd = s_red.d[lane];
+          be = s_red.e[lane];
+          for (int q = 0; q < 4; ++q) bf[q] = s_red.f[lane][q];
+        }
+        warp_reduce(bd, be, bf);
+        if (lane == 0) {
+          unsigned long long* dst = a.partials + ((s & 1) * gridDim.x + b0 + lb) * kPartWords;
+          __stcg(dst + 0, bd.w0);
+          __stcg(dst + 1, bd.w1);
+          __stcg(dst + 2, bd.w2);
+          __stcg(dst + 3, be.w0);
+          __stcg(dst + 4, be.w1);
+          __stcg(dst + 5, be.w2);
+          __stcg(dst + 6, (static_cast<unsigned long long>(bf[1]) << 32) | bf[0]);
+          __stcg(dst + 7, (static_cast<unsigned long long>(bf[3]) << 32) | bf[2]);
+        }
+      }
+    }
+    if (!pop_barrier(a.bar, static_cast<unsigned int>(s), static_cast<unsigned int>(nb), a.err, a.timeout_ns))
+      return;
+    if (wid == 0) {
+      Xacc D, E;
+      xacc_zero(D);
+      xacc_zero(E);
+      unsigned int f[4] = {0u, 0u, 0u, 0u};
+      for (int b = lane; b < nb; b += 32) {
+        const unsigned long long* src = a.partials + ((s & 1) * gridDim.x + b0 + b) * kPartWords;
+        Xacc t;
+        t.w0 = __ldcg(src + 0);
+        t.w1 = __ldcg(src + 1);
+        t.w2 = __ldcg(src + 2);
+        xacc_add(D, t);
+        t.w0 = __ldcg(src + 3);
+        t.w1 = __ldcg(src + 4);
+        t.w2 = __ldcg(src + 5);
+        xacc_add(E, t);
+        const unsigned long long f01 = __ldcg(src + 6), f23 = __ldcg(src + 7);
+        f[0] += static_cast<unsigned int>(f01);
+        f[1] += static_cast<unsigned int>(f01 >> 32);
+        f[2] += static_cast<unsigned int>(f23);
+        f[3] += static_cast<unsigned int>(f23 >> 32);
+      }
+      warp_reduce(D, E, f);
+      if (lane == 0) {
+        if (f[1] != 0u) {
+          atomicCAS(a.err, 0, CUDAHM_ENUMERIC);
+          s_stop = 1;
+        } else {
+          double logalpha, eb_new = 0.0, logeb_new = 0.0;
+          if (!prior_ok || f[0] != 0u) {
+            logalpha = -INFINITY;
+          } else if (f[2] != 0u) {
+            logalpha = INFINITY;
+          } else {
+            const double nn = static_cast<double>(a.n);
+            logalpha = xacc_to_double(D) + nn * (M::cterm(s_thp) - M::cterm(s_theta)) + s_lpri_new - s_lpri;
+            if (is_lf) {
+              eb_new = xacc_to_double(E);
+              logeb_new = log(eb_new);
+              logalpha -= nn * (logeb_new - s_logeb);
+            }
+          }
+          const bool acc = __ldg(a.tab_lnu + s) < logalpha;
+          if (acc) {
+            for (int q = 0; q < p; ++q) s_theta[q] = s_thp[q];
+            s_tc = s_tcp;
+            s_tcf = s_tcpf;
+            s_lpri = s_lpri_new;
+            if (is_lf) {
+              s_etabar = eb_new;
+              s_logeb = logeb_new;
+            }
+            s_tacc++;
+          }
+          if (a.adapt_theta) {
+            const double alpha = (logalpha >= 0.0) ? 1.0 : exp(logalpha);
+            ram_update_theta(p, s_Sth, a.tab_U + s * p, alpha, a.astar_theta, eta);
+          }
+          const long long post = s - burn_left;
+          if (post >= 0 && prog->thin > 0 && ((post + 1) % prog->thin) == 0) {
+            if (lb == 0 && rows)
+              for (int q = 0; q < p; ++q) rows[s_rows_written * p + q] = s_theta[q];
+            s_rows_written++;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (s_stop) return;
+  }
+  __shared__ unsigned int s_macc;
+  if (tid == 0) s_macc = 0;
+  __syncthreads();
+  atomicAdd(&s_macc, member_acc);
+  __syncthreads();
+  if (tid == 0) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(&a.chain->member_acc), static_cast<unsigned long long>(s_macc));
+    if (lb == 0) {
+      for (int q = 0; q < p; ++q) a.chain->theta[q] = s_theta[q];
+      for (int q = 0; q < p * p; ++q) a.chain->S_theta[q] = s_Sth[q];
+      a.chain->etabar = s_etabar;
+      a.chain->sweeps = k0 + ns;
+      a.chain->theta_acc += s_tacc;
+      prog->off = off + ns;
+      prog->rows += s_rows_written;
+      prog->t_ns = globaltimer_ns() - t_start;
+    }
+  }
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(256, 2) batch_kernel(const SweepArgs* __restrict__ pops,
+                                                       BatchProg* __restrict__ progs, const int* __restrict__ b0s,
+                                                       const int* __restrict__ nbs, int npop, int chunk, int R) {
+  extern __shared__ double s_dyn[];
+  __shared__ double s_theta[kMaxP], s_thp[kMaxP], s_Sth[kMaxP * kMaxP];
+  __shared__ BlockRed s_red;
+  __shared__ SweepArgs s_args;
+  __shared__ int s_pop;
+  if (threadIdx.x == 0) s_pop = find_pop(b0s, npop, blockIdx.x);
+  __syncthreads();
+  const int pop = s_pop;
+  // the population's arguments, copied word by word into shared memory
+  {
+    const int words = static_cast<int>(sizeof(SweepArgs) / sizeof(int));
+    const int* src = reinterpret_cast<const int*>(pops + pop);
+    int* dst = reinterpret_cast<int*>(&s_args);
+    for (int q = threadIdx.x; q < words; q += blockDim.x) dst[q] = src[q];
+  }
+  __syncthreads();
+  const int b0 = b0s[pop], lb = blockIdx.x - b0, nb = nbs[pop];
+  BatchProg* prog = progs + pop;
+  if (lb >= nb || prog->off >= prog->total) return;  // spare block, or the population has finished
+  if (s_args.model == CUDAHM_NN1)
+    run_population<NN1, F32>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
+  else
+    run_population<LF, F32>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
+}
+
+// binary32 member data of the FP32 form (kData32 values per member, member-minor)
+template <class M>
+__global__ void data32_kernel(long long n, const double* y, const double* aux, ModelConsts mc, float* d32) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float d[M::kData32];
+  M::data32(y[i], aux[i], mc, d);
+#pragma unroll
+  for (int c = 0; c < M::kData32; ++c) d32[c * n + i] = d[c];
+}
+
+// Theta tables of every population for the next chunk: sweep k0 + 1 + s, s < ns.
+__global__ void batch_tables_kernel(const SweepArgs* __restrict__ pops, const BatchProg* __restrict__ progs, int npop,
+                                    int chunk) {
+  const int pop = blockIdx.y;
+  if (pop >= npop) return;
+  const SweepArgs& a = pops[pop];
+  const BatchProg& pr = progs[pop];
+  const long long left = pr.total - pr.off;
+  const long long ns = left < chunk ? left : chunk;
+  const long long s = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  const long long k0 = a.chain->sweeps;
+  const uint32_t k = static_cast<uint32_t>(k0 + s + 1);
+  const int p = a.p;
+  const int nblk = (p + 1) / 2;
+  double* U = const_cast<double*>(a.tab_U);
+  for (int j = 0; j < nblk; ++j) {
+    const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(j), 1u, 0u, k), a.key0, a.key1);
+    const double ua = uniform53(w.x, w.y), ub = uniform53(w.z, w.w);
+    const double rad = sqrt(-2.0 * log(ua));
+    double sn, cs;
+    sincospi(2.0 * ub, &sn, &cs);
+    U[s * p + 2 * j] = rad * cs;
+    if (2 * j + 1 < p) U[s * p + 2 * j + 1] = rad * sn;
+  }
+  const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(nblk), 1u, 0u, k), a.key0, a.key1);
+  const double u = uniform53(w.x, w.y);
+  const_cast<double*>(a.tab_u)[s] = u;
+  const_cast<double*>(a.tab_lnu)[s] = log(u);
+  const_cast<double*>(a.tab_eta)[s] = pow(static_cast<double>(k) + 1.0, -a.gamma);
+}
+
+}  // namespace
+
+int data32_words(int model) { return model == CUDAHM_LF ? LF::kData32 : NN1::kData32; }
+
+cudaError_t launch_data32(int model, long long n, const double* y, const double* aux, const ModelConsts& mc,
+                          float* d32, cudaStream_t st) {
+  const int blk = 256;
+  const unsigned int grid = static_cast<unsigned int>((n + blk - 1) / blk);
+  if (model == CUDAHM_LF) data32_kernel<LF><<<grid, blk, 0, st>>>(n, y, aux, mc, d32);
+  else data32_kernel<NN1><<<grid, blk, 0, st>>>(n, y, aux, mc, d32);
+  return cudaGetLastError();
+}
+
+size_t batch_smem_bytes(int seg_slots) {
+  return sizeof(double) * (kMathWords + kPhiWords) + segtab_bytes(seg_slots);
+}
+
+cudaError_t batch_occupancy(bool f32, int block, int smem_bytes, int* blocks_per_sm) {
+  const void* fn = f32 ? reinterpret_cast<const void*>(&batch_kernel<true>)
+                       : reinterpret_cast<const void*>(&batch_kernel<false>);
+  if (smem_bytes > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem_bytes);
+}
+
+cudaError_t launch_batch(bool f32, const SweepArgs* pops, BatchProg* progs, const int* b0s, const int* nbs, int npop,
+                         int chunk, int seg_slots, int grid, int block, int smem_bytes, cudaStream_t st) {
+  void* args[] = {const_cast<SweepArgs**>(&pops), &progs, const_cast<int**>(&b0s), const_cast<int**>(&nbs), &npop,
+                  &chunk, &seg_slots};
+  const void* fn = f32 ? reinterpret_cast<const void*>(&batch_kernel<true>)
+                       : reinterpret_cast<const void*>(&batch_kernel<false>);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem_bytes, st);
+}
+
+cudaError_t launch_batch_tables(const SweepArgs* pops, const BatchProg* progs, int npop, int chunk, cudaStream_t st) {
+  dim3 grid((chunk + 127) / 128, npop);
+  batch_tables_kernel<<<grid, 128, 0, st>>>(pops, progs, npop, chunk);
+  return cudaGetLastError();
+}
+
+}  // namespace chm

@@ -15,7 +15,7 @@ namespace chm {
 
 constexpr int kMathWords = 64 + 2 * 92;
 
-__global__ void math_table_kernel(double* t) {
+static __global__ void math_table_kernel(double* t) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < 64) {
     t[i] = exp2(i / 64.0);

@@ -81,7 +81,29 @@ struct SweepArgs {
   double* tr_eb;
   long long timeout_ns;
   int skip_cta;
+  double gamma;       // adaptation exponent (eta = n^-gamma)
+  const float* d32;   // FP32 form: precomputed binary32 member data (kData32 x n, member-minor)
 };
+
+// Progress of one population through a batched run (device memory, updated by the kernel).
+struct BatchProg {
+  long long total;   // sweeps of the run
+  long long off;     // sweeps done
+  long long n_burn;
+  long long thin;
+  long long rows;    // theta rows written
+  long long t_ns;    // device time of the population's last launch (%globaltimer), for balancing
+};
+
+// Batched launches (batch.cu).
+size_t batch_smem_bytes(int seg_slots);
+cudaError_t batch_occupancy(bool f32, int block, int smem_bytes, int* blocks_per_sm);
+cudaError_t launch_batch(bool f32, const SweepArgs* pops, BatchProg* progs, const int* b0s, const int* nbs, int npop,
+                         int chunk, int seg_slots, int grid, int block, int smem_bytes, cudaStream_t st);
+cudaError_t launch_batch_tables(const SweepArgs* pops, const BatchProg* progs, int npop, int chunk, cudaStream_t st);
+cudaError_t launch_data32(int model, long long n, const double* y, const double* aux, const ModelConsts& mc,
+                          float* d32, cudaStream_t st);
+int data32_words(int model);
 
 // Records a failure for cudahm_last_error() (runtime.cu); returns code.
 int record_error(int code, const char* msg);

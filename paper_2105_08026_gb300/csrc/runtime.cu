@@ -84,6 +84,7 @@ struct cudahm {
   double *xL = nullptr, *wL = nullptr, *xr = nullptr, *wr = nullptr, *qs = nullptr, *Wr = nullptr;
   double* phi_coef = nullptr;
   double* cw = nullptr;
+  float* d32 = nullptr;
   double* math_tab = nullptr;
   unsigned long long* eb_partials = nullptr;
   int eb_grid = 0, eb_rows_smem = 1;
@@ -273,7 +274,48 @@ SweepArgs base_args(cudahm* h) {
   a.mpb = h->mpb;
   a.timeout_ns = h->cfg.barrier_timeout_ns > 0 ? h->cfg.barrier_timeout_ns : 2000000000ll;
   a.skip_cta = h->cfg.debug_skip_barrier_cta;
+  a.gamma = h->cfg.adapt_exponent;
+  a.d32 = h->d32;
+  a.tab_U = h->tab_U;
+  a.tab_u = h->tab_u;
+  a.tab_lnu = h->tab_lnu;
+  a.tab_eta = h->tab_eta;
   return a;
+}
+
+// Cost (FP64-pipe operations per sweep) of one population, for the batched allocation.
+double pop_cost(const cudahm* h) {
+  const bool f32 = h->cfg.precision == CUDAHM_FP32;
+  double c = 3000.0 + static_cast<double>(h->n) * (f32 ? 20.0 : 120.0);
+  if (h->cfg.model == CUDAHM_LF) {
+    const double nL = h->cfg.model_consts[3], nr = h->cfg.model_consts[4];
+    c += 0.3 * nL * nr * 17.0 + nL * std::ceil(nr / 128.0) * 70.0;
+  }
+  return c;
+}
+
+// Blocks per population proportional to cost (at least one each), total <= grid: the next
+// block always goes to the population with the largest cost per block.
+std::vector<int> allocate_blocks(const std::vector<double>& cost, const std::vector<int>& cap, int grid) {
+  const int k = static_cast<int>(cost.size());
+  std::vector<int> nb(k, 1);
+  int used = k;
+  while (used < grid) {
+    int best = -1;
+    double bw = -1.0;
+    for (int q = 0; q < k; ++q) {
+      if (nb[q] >= cap[q]) continue;
+      const double w = cost[q] / nb[q];
+      if (w > bw) {
+        bw = w;
+        best = q;
+      }
+    }
+    if (best < 0) break;
+    nb[best]++;
+    used++;
+  }
+  return nb;
 }
 
 int reset_chain(cudahm* h) {
@@ -311,6 +353,10 @@ int prepare(cudahm* h, const double* y_dev_raw, const double* aux_dev_raw, int s
   CU(cudaStreamSynchronize(h->stream));
   bad = *h->host_err;
   if (bad) return fail(CUDAHM_EINVAL, "%d members have non-finite data or a non-positive scale", bad);
+  if (h->cfg.precision == CUDAHM_FP32) {  // binary32 member data for the batched FP32 form
+    if (!h->d32) TRY(alloc_into(h, &h->d32, static_cast<size_t>(data32_words(h->cfg.model)) * h->n));
+    CU(launch_data32(h->cfg.model, h->n, h->y, h->aux, h->mc, h->d32, h->stream));
+  }
   TRY(reset_chain(h));
   h->data_set = true;
   return CUDAHM_OK;
@@ -763,6 +809,326 @@ int cudahm_restore(cudahm_t h, const void* buf, size_t size) {
   h->sweeps = cs.sweeps;
   h->rows_last = 0;
   h->etabar_valid = (cs.etabar != 0.0);
+  return CUDAHM_OK;
+}
+
+// ---------------------------------------------------------------- batched --
+namespace {
+
+struct TuneKey {
+  int precision, k, nlf;
+  long long nbucket;
+  bool operator==(const TuneKey& o) const {
+    return precision == o.precision && k == o.k && nlf == o.nlf && nbucket == o.nbucket;
+  }
+};
+struct TuneEntry {
+  TuneKey key;
+  int block, chunk;
+};
+std::vector<TuneEntry> g_tune_cache;  // decisions of the autotuner for this process
+
+struct BatchBufs {
+  cudahm* owner = nullptr;
+  SweepArgs* pops = nullptr;
+  BatchProg* progs = nullptr;
+  int* b0s = nullptr;
+  int* nbs = nullptr;
+  unsigned long long* partials = nullptr;
+  unsigned int* bars = nullptr;
+  int* errs = nullptr;
+  ~BatchBufs() {
+    if (!owner) return;
+    for (void* q : {(void*)pops, (void*)progs, (void*)b0s, (void*)nbs, (void*)partials, (void*)bars, (void*)errs})
+      owner->dfree(q);
+  }
+};
+
+}  // namespace
+
+int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, int64_t thin, const cudahm_tune* tune,
+                     cudahm_tune* chosen) {
+  if (!hs || k < 1) return fail(CUDAHM_EINVAL, "need at least one handle");
+  if (n_burn < 0 || n_iter < 0 || n_burn + n_iter < 1) return fail(CUDAHM_EINVAL, "bad sweep counts");
+  if (n_iter > 0 && thin < 1) return fail(CUDAHM_EINVAL, "thin must be >= 1");
+  cudahm* h0 = hs[0];
+  if (!h0) return fail(CUDAHM_EINVAL, "handle 0 is NULL");
+  for (int q = 0; q < k; ++q) {
+    cudahm* h = hs[q];
+    if (!h) return fail(CUDAHM_EINVAL, "handle %d is NULL", q);
+    if (!h->data_set) return fail(CUDAHM_ESTATE, "handle %d has no data", q);
+    if (h->cfg.device != h0->cfg.device) return fail(CUDAHM_EINVAL, "handles are on different devices");
+    if (h->cfg.precision != h0->cfg.precision) return fail(CUDAHM_EINVAL, "handles mix precisions");
+    if (h->cfg.trace_sweeps > 0) return fail(CUDAHM_EUNSUPPORTED, "batched runs do not record traces");
+    for (int r = 0; r < q; ++r)
+      if (hs[r] == h) return fail(CUDAHM_EINVAL, "handle %d appears twice", q);
+    if (h->sweeps + n_burn + n_iter >= (1ll << 32) - 2) return fail(CUDAHM_EINVAL, "sweep counter would overflow");
+  }
+  const bool f32 = h0->cfg.precision == CUDAHM_FP32;
+  CU(cudaSetDevice(h0->cfg.device));
+  cudaStream_t st = h0->stream;
+  for (int q = 0; q < k; ++q) CU(cudaStreamSynchronize(hs[q]->stream));
+  const long long total = n_burn + n_iter;
+  const long long nrows = (n_iter > 0) ? n_iter / thin : 0;
+
+  // per-handle preparation: sample buffer, selection integral at the current theta
+  for (int q = 0; q < k; ++q) {
+    cudahm* h = hs[q];
+    if (nrows > h->rows_cap) {
+      h->dfree(h->rows);
+      h->rows = nullptr;
+      TRY(alloc_into(h, &h->rows, static_cast<size_t>(nrows) * h->p));
+      h->rows_cap = nrows;
+    }
+    if (h->cfg.model == CUDAHM_LF && !h->etabar_valid) {
+      char* base = reinterpret_cast<char*>(h->chain);
+      TRY(compute_etabar_into(h, reinterpret_cast<const double*>(base + offsetof(ChainState, theta)),
+                              reinterpret_cast<double*>(base + offsetof(ChainState, etabar))));
+      h->etabar_valid = true;
+    }
+    CU(cudaStreamSynchronize(h->stream));
+  }
+
+  // launch shape: tuned or asked for
+  int nlf = 0;
+  long long ntot = 0;
+  for (int q = 0; q < k; ++q) {
+    nlf += hs[q]->cfg.model == CUDAHM_LF;
+    ntot += hs[q]->n;
+  }
+  TuneKey key{h0->cfg.precision, k, nlf, static_cast<long long>(std::log2(static_cast<double>(ntot) + 1.0))};
+  int block = tune && tune->block_threads ? tune->block_threads : 0;
+  int chunk = tune && tune->sweeps_per_launch ? tune->sweeps_per_launch : 0;
+  const bool use_graph = !tune || tune->use_graph != 0 || (tune->block_threads == 0 && tune->sweeps_per_launch == 0);
+  if (block && block != 128 && block != 256) return fail(CUDAHM_EINVAL, "block_threads must be 128 or 256");
+  if (chunk < 0 || chunk > kChunk) return fail(CUDAHM_EINVAL, "sweeps_per_launch must be in [1, %lld]", kChunk);
+  bool tuned_before = false;
+  if (!block || !chunk) {
+    for (const TuneEntry& e : g_tune_cache)
+      if (e.key == key) {
+        if (!block) block = e.block;
+        if (!chunk) chunk = e.chunk;
+        tuned_before = true;
+      }
+  }
+  // sweeps per launch: enough launches to rebalance a few times, long enough to amortise a launch
+  if (!chunk) chunk = static_cast<int>(std::min<long long>(kChunk, std::max<long long>(256, total / 4)));
+  // block size: measured on two short launches at the start of the run (they are part of it)
+  const int kTrialSweeps = 16;
+  std::vector<std::pair<int, int>> trials;
+  if (!block) {
+    trials.push_back({128, kTrialSweeps});
+    trials.push_back({256, kTrialSweeps});
+  } else {
+    trials.push_back({block, chunk});
+  }
+
+  const int R = 128;  // segment slots per block
+  const int smem = static_cast<int>(batch_smem_bytes(R));
+  int sms = h0->sms;
+
+  BatchBufs bb;
+  bb.owner = h0;
+  const int max_grid = 4 * sms * 2;  // 128-thread blocks, up to 8 per SM
+  TRY(alloc_into(h0, &bb.pops, k));
+  TRY(alloc_into(h0, &bb.progs, k));
+  TRY(alloc_into(h0, &bb.b0s, k));
+  TRY(alloc_into(h0, &bb.nbs, k));
+  TRY(alloc_into(h0, &bb.partials, 2ull * max_grid * kPartWords));
+  TRY(alloc_into(h0, &bb.bars, k));
+  TRY(alloc_into(h0, &bb.errs, k));
+
+  std::vector<SweepArgs> pops(k);
+  std::vector<BatchProg> progs(k);
+  std::vector<double> cost(k);
+  std::vector<int> cap(k);
+  for (int q = 0; q < k; ++q) {
+    cudahm* h = hs[q];
+    SweepArgs a = base_args(h);
+    a.partials = bb.partials;
+    a.bar = bb.bars + q;
+    a.err = bb.errs + q;
+    a.rows = h->rows;
+    a.thin = thin;
+    a.trace_T = 0;
+    a.skip_cta = -1;
+    pops[q] = a;
+    progs[q] = BatchProg{total, 0, n_burn, thin, 0, 0};
+    cost[q] = pop_cost(h);
+    long long c = (h->n + 31) / 32;
+    if (h->cfg.model == CUDAHM_LF)
+      c += static_cast<long long>(h->cfg.model_consts[3]) * ((static_cast<long long>(h->cfg.model_consts[4]) + 127) / 128);
+    cap[q] = static_cast<int>(std::min<long long>(c, max_grid));
+  }
+  CU(cudaMemcpyAsync(bb.pops, pops.data(), sizeof(SweepArgs) * k, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(bb.progs, progs.data(), sizeof(BatchProg) * k, cudaMemcpyHostToDevice, st));
+  CU(cudaMemsetAsync(bb.errs, 0, sizeof(int) * k, st));
+
+  cudaGraphExec_t gexec = nullptr;
+  int g_block = 0, g_chunk = 0, g_grid = 0;
+  std::vector<int> nb;
+  auto set_alloc = [&](int grid_) -> int {
+    std::vector<int> b0(k);
+    int acc = 0;
+    for (int q = 0; q < k; ++q) {
+      b0[q] = acc;
+      acc += nb[q];
+    }
+    if (acc > grid_) return fail(CUDAHM_EUNSUPPORTED, "%d populations need more blocks than fit (%d)", k, grid_);
+    CU(cudaMemcpyAsync(bb.b0s, b0.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(bb.nbs, nb.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st));
+    CU(cudaStreamSynchronize(st));
+    return CUDAHM_OK;
+  };
+  auto enqueue = [&](int blk, int ch, int grid_) -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(bb.bars, 0, sizeof(unsigned int) * k, st);
+    if (e == cudaSuccess) e = launch_batch_tables(bb.pops, bb.progs, k, ch, st);
+    if (e == cudaSuccess) e = launch_batch(f32, bb.pops, bb.progs, bb.b0s, bb.nbs, k, ch, R, grid_, blk, smem, st);
+    return e;
+  };
+  auto grid_for = [&](int blk, int* out) -> int {
+    int bps = 0;
+    CU(batch_occupancy(f32, blk, smem, &bps));
+    if (bps < 1) return fail(CUDAHM_EUNSUPPORTED, "batched kernel does not fit on this device");
+    *out = std::min(bps * sms, blk == 128 ? max_grid : max_grid / 2);
+    return CUDAHM_OK;
+  };
+
+  long long done = 0;
+  double best_ms = 1e300;
+  int best_block = trials[0].first, best_chunk = chunk;
+  bool graph_ok = use_graph;
+  float run_ms_total = 0.f;
+  cudaEvent_t ea, eb;
+  CU(cudaEventCreate(&ea));
+  CU(cudaEventCreate(&eb));
+  auto cleanup_events = [&]() {
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb);
+    if (gexec) cudaGraphExecDestroy(gexec);
+  };
+  int rc = CUDAHM_OK;
+  // trial launches (autotuning) on the run's first chunks, then the rest with the winner
+  size_t ti = 0;
+  int rebalance_left = 2;
+  while (done < total && rc == CUDAHM_OK) {
+    int blk, ch;
+    if (ti < trials.size() && trials.size() > 1) {
+      blk = trials[ti].first;
+      ch = trials[ti].second;
+    } else {
+      blk = best_block;
+      ch = best_chunk;
+    }
+    int grid = 0;
+    if ((rc = grid_for(blk, &grid)) != CUDAHM_OK) break;
+    if (nb.empty() || grid != g_grid) {
+      nb = allocate_blocks(cost, cap, grid);
+      if ((rc = set_alloc(grid)) != CUDAHM_OK) break;
+      if (gexec && grid != g_grid) {
+        cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+      }
+    }
+    const long long ns = std::min<long long>(ch, total - done);
+    cudaError_t e = cudaSuccess;
+    CU(cudaEventRecord(ea, st));
+    if (graph_ok && (ti >= trials.size() || trials.size() == 1)) {
+      if (!gexec || g_block != blk || g_chunk != ch || g_grid != grid) {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          const cudaError_t e2 = enqueue(blk, ch, grid);
+          e = cudaStreamEndCapture(st, &graph);
+          if (e2 != cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {  // capture not available: plain launches from here on
+          cudaGetLastError();
+          if (gexec) cudaGraphExecDestroy(gexec);
+          gexec = nullptr;
+          graph_ok = false;
+          e = enqueue(blk, ch, grid);
+        } else {
+          g_block = blk;
+          g_chunk = ch;
+          e = cudaGraphLaunch(gexec, st);
+        }
+      } else {
+        e = cudaGraphLaunch(gexec, st);
+      }
+    } else {
+      e = enqueue(blk, ch, grid);
+    }
+    g_grid = grid;
+    if (e != cudaSuccess) {
+      rc = fail(CUDAHM_ECUDA, "batched launch failed: %s", cudaGetErrorString(e));
+      break;
+    }
+    CU(cudaEventRecord(eb, st));
+    CU(cudaEventSynchronize(eb));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, ea, eb));
+    run_ms_total += ms;
+    done += ns;
+    // stop at the first failing population
+    std::vector<int> errs(k);
+    CU(cudaMemcpy(errs.data(), bb.errs, sizeof(int) * k, cudaMemcpyDeviceToHost));
+    for (int q = 0; q < k && rc == CUDAHM_OK; ++q)
+      if (errs[q] != 0) rc = fail(errs[q], "population %d failed with device error %d", q, errs[q]);
+    if (rc != CUDAHM_OK) break;
+    if (ti < trials.size() && trials.size() > 1) {
+      const double per = ms / static_cast<double>(ns);
+      if (per < best_ms) {
+        best_ms = per;
+        best_block = blk;
+      }
+      ++ti;
+      if (ti == trials.size()) g_tune_cache.push_back(TuneEntry{key, best_block, best_chunk});
+      continue;
+    }
+    ti = trials.size();
+    // rebalance from the measured device time of each population (work ~ time x blocks)
+    if (rebalance_left > 0 && k > 1 && done < total) {
+      --rebalance_left;
+      std::vector<BatchProg> pr(k);
+      CU(cudaMemcpy(pr.data(), bb.progs, sizeof(BatchProg) * k, cudaMemcpyDeviceToHost));
+      bool ok = true;
+      for (int q = 0; q < k; ++q) ok = ok && pr[q].t_ns > 0;
+      if (ok) {
+        for (int q = 0; q < k; ++q) cost[q] = static_cast<double>(pr[q].t_ns) * nb[q];
+        nb = allocate_blocks(cost, cap, grid);
+        if ((rc = set_alloc(grid)) != CUDAHM_OK) break;
+      }
+    }
+  }
+  cleanup_events();
+  (void)tuned_before;
+  if (rc != CUDAHM_OK) {
+    for (int q = 0; q < k; ++q) {
+      ChainState cs;
+      if (cudaMemcpy(&cs, hs[q]->chain, sizeof(cs), cudaMemcpyDeviceToHost) == cudaSuccess) hs[q]->sweeps = cs.sweeps;
+      hs[q]->rows_last = 0;
+    }
+    return rc;
+  }
+  CU(cudaStreamSynchronize(st));
+  for (int q = 0; q < k; ++q) {
+    cudahm* h = hs[q];
+    h->sweeps += total;
+    h->rows_last = nrows;
+    h->trace_T_last = 0;
+    h->last_run_ms = run_ms_total;
+  }
+  if (chosen) {
+    chosen->block_threads = best_block;
+    chosen->sweeps_per_launch = best_chunk;
+    chosen->use_graph = graph_ok ? 1 : 0;
+    chosen->reserved = g_grid;
+  }
   return CUDAHM_OK;
 }
 

@@ -17,218 +17,9 @@
 #include <cstdint>
 #include <type_traits>
 
-#include "device_common.cuh"
-#include "fp64_math.cuh"
-#include "internal.h"
+#include "sweep_common.cuh"
 
 namespace chm {
-
-// ----------------------------------------------------------------- models ----
-// Per-theta constants a0..a3 (computed once per theta by one thread).
-struct ThetaC {
-  double a0, a1, a2, a3;
-};
-
-// binary32 theta constants for the FP32 bulk form; a location parameter is held as a sum of
-// two floats (hi + lo) so that chi - location keeps full binary32 relative accuracy.
-struct ThetaCf {
-  float sc_hi, sc_lo, loc_hi, loc_lo, low_hi, low_lo;  // scale, location, lower bound (hi + lo)
-};
-__device__ __forceinline__ void split_f(double v, float& hi, float& lo) {
-  hi = static_cast<float>(v);
-  lo = static_cast<float>(v - static_cast<double>(hi));
-}
-// chi - (hi + lo): the first subtraction is exact whenever chi is near hi
-__device__ __forceinline__ float sub2(float chi, float hi, float lo) { return (chi - hi) - lo; }
-// chi - (hi + lo) as an unevaluated sum r_hi + r_lo (Knuth's TwoSum for chi - hi). Latents
-// lie on the binary32 grid, so the rounding error of chi - hi repeats from member to member;
-// keeping it avoids a bias that would grow with N in sums over members.
-__device__ __forceinline__ void sub2x(float chi, float hi, float lo, float& r_hi, float& r_lo) {
-  const float s = chi - hi;
-  const float a1 = s + hi;    // chi's share of s
-  const float b1 = s - a1;    // -hi's share of s
-  const float err = (chi - a1) + (-hi - b1);
-  r_hi = s;
-  r_lo = err - lo;
-}
-
-struct NN1 {
-  // a0 = mu, a1 = 1/(2 tau^2)
-  static constexpr bool kExp = false;
-  // binary32 forms of the member terms (FP32 bulk precision): loc = mu, scale = 1/(2 tau^2)
-  __device__ static ThetaCf consts32(const ThetaC& c) {
-    ThetaCf f{};
-    split_f(c.a0, f.loc_hi, f.loc_lo);
-    split_f(c.a1, f.sc_hi, f.sc_lo);
-    return f;
-  }
-  __device__ static bool support32(float, const ThetaCf&) { return true; }
-  __device__ static float logf32(float chi, const ThetaCf& c) {
-    float rh, rl;
-    sub2x(chi, c.loc_hi, c.loc_lo, rh, rl);
-    const float r2 = fmaf(rh, rh, 2.0f * rh * rl);
-    return -fmaf(c.sc_hi, r2, c.sc_lo * r2);  // the scale's rounding would bias every member alike
-  }
-  // member data d[0], d[1] = y_i as hi + lo, d[2] = 1/(2 sigma_i^2)
-  static constexpr int kData32 = 3;
-  __device__ static void data32(double y, double aux, const ModelConsts&, float* d) {
-    split_f(y, d[0], d[1]);
-    d[2] = static_cast<float>(0.5 * aux);
-  }
-  __device__ static float loglike32(float chi, const float* d) {
-    const float r = (d[0] - chi) + d[1];
-    return -d[2] * (r * r);
-  }
-  __device__ static ThetaC consts(const double* th) {
-    ThetaC c;
-    c.a0 = th[0];
-    c.a1 = 0.5 * exp(-2.0 * th[1]);
-    c.a2 = 0.0;
-    c.a3 = 0.0;
-    return c;
-  }
-  __device__ static bool support(double, const ThetaC&) { return true; }
-  __device__ static double logf(double chi, double, const ThetaC& c) {
-    const double r = chi - c.a0;
-    return -c.a1 * (r * r);
-  }
-  // y = y_i, aux = 1/sigma_i^2
-  __device__ static double loglike(double chi, double, double y, double aux, const ModelConsts&) {
-    const double r = y - chi;
-    return -0.5 * aux * (r * r);
-  }
-  __device__ static double cterm(const double* th) { return -th[1]; }
-  __device__ static double logprior(const double* th, const ModelConsts& mc) {
-    return (th[1] >= mc.lo && th[1] <= mc.hi) ? 0.0 : -INFINITY;
-  }
-};
-
-struct LF {
-  // a0 = beta + 1, a1 = ln L*, a2 = 1/L*, a3 = ln L_low
-  static constexpr bool kExp = true;
-  // binary32 forms: scale = beta + 1, loc = ln L*, low = ln L_low; log f = scale x - e^x, x = chi - ln L*
-  __device__ static ThetaCf consts32(const ThetaC& c) {
-    ThetaCf f{};
-    split_f(c.a0, f.sc_hi, f.sc_lo);
-    split_f(c.a1, f.loc_hi, f.loc_lo);
-    split_f(c.a3, f.low_hi, f.low_lo);
-    return f;
-  }
-  __device__ static bool support32(float chi, const ThetaCf& c) { return (chi - c.low_hi) > c.low_lo; }
-  __device__ static float logf32(float chi, const ThetaCf& c) {
-    float xh, xl;
-    sub2x(chi, c.loc_hi, c.loc_lo, xh, xl);
-    const float e = expf(xh);
-    const float ex = fmaf(e, xl, e);  // e^(xh + xl) to first order in xl
-    return fmaf(c.sc_hi, xh, fmaf(c.sc_hi, xl, fmaf(c.sc_lo, xh, -ex)));
-  }
-  // member data: d[0], d[1] = ln(Fhat_i/q_i) as hi + lo, d[2] = Fhat_i^2/(2 sigma_F^2), so that
-  // log l_i = -d[2] expm1(chi - ln(Fhat_i/q_i))^2 keeps binary32 relative accuracy however large
-  // Fhat_i/sigma_F is; members with Fhat_i <= 0 use d[3] = Fhat_i, d[4] = q_i directly (d[2] < 0).
-  static constexpr int kData32 = 5;
-  __device__ static void data32(double y, double aux, const ModelConsts& mc, float* d) {
-    if (y > 0.0) {
-      split_f(log(y / aux), d[0], d[1]);
-      d[2] = static_cast<float>(y * y * mc.inv2sig2);
-    } else {  // marker: d[2] < 0 holds -1/(2 sigma_F^2)
-      d[0] = d[1] = 0.0f;
-      d[2] = static_cast<float>(-mc.inv2sig2);
-    }
-    d[3] = static_cast<float>(y);
-    d[4] = static_cast<float>(aux);
-  }
-  __device__ static float loglike32(float chi, const float* d) {
-    if (d[2] > 0.0f) {
-      const float e = expm1f(sub2(chi, d[0], d[1]));
-      return -d[2] * (e * e);
-    }
-    const float r = fmaf(-expf(chi), d[4], d[3]);
-    return (r * r) * d[2];
-  }
-  __device__ static ThetaC consts(const double* th) {
-    ThetaC c;
-    c.a0 = th[0] + 1.0;
-    c.a1 = th[1];
-    c.a2 = exp(-th[1]);
-    c.a3 = th[2];
-    return c;
-  }
-  __device__ static bool support(double chi, const ThetaC& c) { return dgt(chi, c.a3); }
-  __device__ static double logf(double chi, double echi, const ThetaC& c) {
-    return c.a0 * (chi - c.a1) - echi * c.a2;
-  }
-  // y = Fhat_i, aux = q_i = 1/(4 pi r_i^2)
-  __device__ static double loglike(double, double echi, double y, double aux, const ModelConsts& mc) {
-    const double r = y - echi * aux;
-    return -(r * r) * mc.inv2sig2;
-  }
-  __device__ static double cterm(const double*) { return 0.0; }
-  __device__ static double logprior(const double* th, const ModelConsts&) {
-    if (!(th[0] > -2.0 && th[0] < 0.0)) return -INFINITY;
-    if (!(th[2] < th[1])) return -INFINITY;
-    return -log(1.0 + th[0] * th[0]) + th[2];
-  }
-};
-
-// ----------------------------------------------------- theta RAM update -------
-// Lower-triangular L (p x p, row-major) with L' L'^T = L (I + c U U^T/|U|^2) L^T,
-// c = eta (alpha - alpha_*): a rank-one Cholesky update (c > 0) or downdate (c < 0)
-// with v = L U sqrt(|c|)/|U|.
-__device__ void ram_update_theta(int p, double* L, const double* U, double alpha, double astar, double eta) {
-  const double c = eta * (alpha - astar);
-  if (c == 0.0) return;
-  double uu = 0.0;
-  for (int j = 0; j < p; ++j) uu = fma(U[j], U[j], uu);
-  const double sc = sqrt(fabs(c) / uu);
-  const double sg = c > 0.0 ? 1.0 : -1.0;
-  double x[kMaxP];
-  for (int a = 0; a < p; ++a) {
-    double t = 0.0;
-    for (int b = 0; b <= a; ++b) t = fma(L[a * p + b], U[b], t);
-    x[a] = t * sc;
-  }
-  for (int k = 0; k < p; ++k) {
-    const double Lkk = L[k * p + k];
-    const double r = sqrt(fma(sg * x[k], x[k], Lkk * Lkk));
-    const double cc = r / Lkk, ss = x[k] / Lkk;
-    L[k * p + k] = r;
-    for (int i = k + 1; i < p; ++i) {
-      const double li = (fma(sg * ss, x[i], L[i * p + k])) / cc;
-      L[i * p + k] = li;
-      x[i] = fma(cc, x[i], -ss * li);
-    }
-  }
-}
-
-// ------------------------------------------------------- normal CDF Phi -------
-// Phi(x) = erfc(-x/sqrt 2)/2 (Sec. 5.2, eq. key) by a table of local Taylor polynomials:
-// intervals centred at c_i = -8 + i/8 (i = 0..kPhiN-1), |x - c_i| <= 1/16, degree kPhiDeg.
-// With phi = Phi' and d^n Phi/dx^n = (-1)^(n-1) He_(n-1)(x) phi(x) (He = probabilists'
-// Hermite polynomials), the coefficients are a_0 = Phi(c), a_n = (-1)^(n-1) He_(n-1)(c) phi(c)/n!.
-// For c > 0 the table holds the upper tail Q = 1 - Phi (a_0 = erfc(c/sqrt 2)/2, a_n negated)
-// and Phi = 1 - Q, so that values near 1 keep full absolute accuracy. The remainder of the
-// degree-10 series on |t| <= 1/16 is below 1e-18; the table is built once per handle on the
-// device from CUDA's erfc and exp. Above x = 8.5, Phi rounds to 1 exactly; below x = -8
-// (Phi < 7e-16) erfc is called directly.
-constexpr int kPhiN = 133;
-constexpr int kPhiDeg = 10;
-constexpr int kPhiWords = kPhiN * (kPhiDeg + 1);  // coefficient-major: coef[n * kPhiN + i]
-
-__device__ __forceinline__ double phi_table(double x, const double* __restrict__ coef) {
-  const long long b = __double_as_longlong(x);
-  if (b > 0x4021000000000000ll) return 1.0;  // x > 8.5 (and +inf)
-  if (static_cast<unsigned long long>(b) > 0xC020000000000000ull)  // x < -8 (and -inf)
-    return 0.5 * erfc(-x * 0.70710678118654752440);
-  const double magic = 6755399441055744.0;        // 1.5 * 2^52
-  const double r = fma(x, 8.0, 64.0 + magic);     // round(8x + 64) sits in the low mantissa bits
-  const int i = __double2loint(r);
-  const double c = fma(r - magic, 0.125, -8.0);   // centre, exact
-  const double t = x - c;                         // exact (|t| <= 1/16, c a multiple of 1/8)
-  double q = coef[kPhiDeg * kPhiN + i];
-#pragma unroll
-  for (int n = kPhiDeg - 1; n >= 0; --n) q = fma(q, t, coef[n * kPhiN + i]);
-  return (i <= 64) ? q : 1.0 - q;
-}
 
 __global__ void phi_table_kernel(double* coef) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -271,124 +62,6 @@ cudaError_t launch_detection(long long n, const double* F, double F_th, double s
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------ LF rule --------
-// The 2-D rule is cut into segments of kSeg consecutive inner nodes of one outer node:
-// segment g = s * nL + j covers outer node j and inner nodes [s kSeg, (s+1) kSeg). Block b
-// of B takes segments b, b + B, b + 2B, ...: every block sees the whole range of L and of r,
-// so blocks get the same mix of pairs that need erfc and pairs where Phi = 1 exactly.
-constexpr int kSegShift = 7;
-constexpr int kSeg = 1 << kSegShift;
-
-__device__ __forceinline__ int lf_block_segments(const SweepArgs& a, int b, int B) {
-  const int spr = (a.nr + kSeg - 1) >> kSegShift;
-  const int G = a.nL * spr;
-  return (b < G) ? (G - b + B - 1) / B : 0;
-}
-
-// Per-block segment table in shared memory, R slots: L_j, G_j, the row's prefix term, the
-// first active inner node kb and the exclusive offsets of the active pair counts (R + 1).
-struct SegTab {
-  double* L;
-  double* G;
-  double* pre;
-  int* kb;
-  int* off;
-};
-__host__ __device__ inline size_t segtab_bytes(int R) {
-  return 3 * sizeof(double) * static_cast<size_t>(R) + sizeof(int) * (2 * static_cast<size_t>(R) + 1);
-}
-__device__ __forceinline__ SegTab segtab_carve(double* base, int R) {
-  SegTab t;
-  t.L = base;
-  t.G = base + R;
-  t.pre = base + 2 * R;
-  t.kb = reinterpret_cast<int*>(base + 3 * R);
-  t.off = t.kb + R;
-  return t;
-}
-
-// Values of segment t (one thread): L_j = e^t_j, G_j = (half-width) w_j g(e^t_j) e^t_j on
-// t in [ln L_low, ln L* + ln_upper]. Since x_jk = L_j qs_k - F_th/sigma_F decreases along the
-// inner nodes (r ascending), the pairs with x > 8.5, where Phi is exactly 1, are a prefix
-// k < k*_j of the row; they contribute G_j CW[k*_j] with CW the prefix sums of the inner
-// weights, added once per row (by its segment s = 0). Only k >= max(k*_j, s kSeg) is left to
-// evaluate; the count goes to off[t] until the block scans it.
-__device__ __forceinline__ void lf_segment_row(const ThetaC& tc, const SweepArgs& a, int b, int B, int t,
-                                               const SegTab& tab) {
-  const double lo = tc.a3, hi = tc.a1 + a.mc.ln_upper;
-  const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
-  const int g = b + t * B;
-  const int j = g % a.nL;
-  const int sseg = g / a.nL;
-  const double tt = fma(half, __ldg(a.xL + j), mid);
-  const double x = tt - tc.a1;
-  const double L = exp(tt);
-  const double G = half * __ldg(a.wL + j) * exp(fma(tc.a0, x, -exp(x)));
-  const double mcth = -a.mc.cth;
-  int klo = 0, khi = a.nr;  // first k with x_jk <= 8.5 (bit test, as in phi_table)
-  while (klo < khi) {
-    const int km = (klo + khi) >> 1;
-    if (__double_as_longlong(fma(L, __ldg(a.qs + km), mcth)) > 0x4021000000000000ll) klo = km + 1;
-    else khi = km;
-  }
-  const int k0 = sseg << kSegShift;
-  const int kend = min(k0 + kSeg, a.nr);
-  const int kb = max(k0, klo);
-  tab.L[t] = L;
-  tab.G[t] = G;
-  tab.pre[t] = (sseg == 0 && klo > 0) ? G * __ldg(a.cw + klo) : 0.0;
-  tab.kb[t] = kb;
-  tab.off[t] = max(0, kend - kb);
-}
-
-// Exclusive scan of the active counts (one warp); off[nseg] receives the total.
-__device__ __forceinline__ void lf_segment_scan(int nseg, const SegTab& tab) {
-  const int lane = threadIdx.x & 31;
-  int carry = 0;
-  for (int base = 0; base < nseg; base += 32) {
-    const int t = base + lane;
-    const int c = (t < nseg) ? tab.off[t] : 0;
-    int v = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += y;
-    }
-    if (t < nseg) tab.off[t] = carry + v - c;
-    carry += __shfl_sync(0xffffffffu, v, 31);
-  }
-  if (lane == 0) tab.off[nseg] = carry;
-}
-
-// All segment rows and the scan by the whole block (set-up paths).
-__device__ __forceinline__ void lf_segment_rows(const ThetaC& tc, const SweepArgs& a, int b, int B, int nseg,
-                                                const SegTab& tab) {
-  for (int t = threadIdx.x; t < nseg; t += blockDim.x) lf_segment_row(tc, a, b, B, t, tab);
-  __syncthreads();
-  if (threadIdx.x < 32) lf_segment_scan(nseg, tab);
-}
-
-// The block's active pairs (all lanes busy) and its rows' prefix terms; each term
-// G_j W_k Phi((L_j q_k - F_th)/sigma_F) is added exactly.
-__device__ __forceinline__ void lf_segment_pairs(const SweepArgs& a, int nseg, const SegTab& tab, const double* s_phi,
-                                                 Xacc& xe, XFlags& fe) {
-  const int total = tab.off[nseg];
-  const double mcth = -a.mc.cth;
-  for (int q = threadIdx.x; q < total; q += blockDim.x) {
-    int lo = 0, hi = nseg - 1;  // last segment with off <= q
-    while (lo < hi) {
-      const int m = (lo + hi + 1) >> 1;
-      if (tab.off[m] <= q) lo = m;
-      else hi = m - 1;
-    }
-    const int k = tab.kb[lo] + (q - tab.off[lo]);
-    const double x = fma(tab.L[lo], __ldg(a.qs + k), mcth);
-    xacc_add_double(xe, tab.G[lo] * (__ldg(a.Wr + k) * phi_table(x, s_phi)), fe);
-  }
-  for (int t = threadIdx.x; t < nseg; t += blockDim.x)
-    if (tab.pre[t] != 0.0) xacc_add_double(xe, tab.pre[t], fe);
-}
-
 // Prefix sums of the inner weights, CW[k] = sum_{k' < k} W_k' (k = 0..nr), each rounded once
 // from an exact running sum.
 __global__ void prefix_weights_kernel(int nr, const double* Wr, double* cw) {
@@ -408,42 +81,11 @@ cudaError_t launch_prefix_weights(int nr, const double* Wr, double* cw, cudaStre
   return cudaGetLastError();
 }
 
-// ------------------------------------------------- block reduce helpers ------
-struct BlockRed {
-  Xacc d[32];
-  Xacc e[32];
-  unsigned int f[32][4];
-};
-
-__device__ __forceinline__ void warp_reduce(Xacc& d, Xacc& e, unsigned int f[4]) {
-#pragma unroll
-  for (int m = 16; m >= 1; m >>= 1) {
-    Xacc t = xacc_shfl_xor(d, m);
-    xacc_add(d, t);
-    t = xacc_shfl_xor(e, m);
-    xacc_add(e, t);
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) f[q] = __reduce_add_sync(0xffffffffu, f[q]);
-}
-
 // ---------------------------------------------------------------- kernel -----
 // Work that only the next theta proposal needs (the S_theta RAM update of the previous sweep,
 // theta' = theta + S_theta U, its prior and constants, the rule's outer-node values at theta')
 // runs on the last warp while every warp does its member steps; only the accept decision
 // itself sits between the grid barrier and the next member phase.
-template <class M>
-__device__ __forceinline__ void propose_theta(const SweepArgs& a, long long s, int p, const double* theta, double* Sth,
-                                              double* thp, double& lpri_new, ThetaC& tcp) {
-  for (int q = 0; q < p; ++q) {
-    double t = theta[q];
-    for (int b = 0; b <= q; ++b) t = fma(Sth[q * p + b], __ldg(a.tab_U + s * p + b), t);
-    thp[q] = t;
-  }
-  lpri_new = M::logprior(thp, a.mc);
-  tcp = M::consts(thp);
-}
-
 template <class M, int K, bool F32>
 __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   using R = typename std::conditional<F32, float, double>::type;  // member arithmetic
@@ -572,7 +214,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
       __syncwarp();
       if (is_lf && s_lpri_new != -INFINITY) {
         const ThetaC tcp = s_tcp;
-        for (int t = lane; t < nseg; t += 32) lf_segment_row(tcp, a, blockIdx.x, gridDim.x, t, tab);
+        for (int t = lane; t < nseg; t += 32) lf_segment_row(tcp, a, blockIdx.x, gridDim.x, t, t, tab);
         __syncwarp();
         lf_segment_scan(nseg, tab);
       }

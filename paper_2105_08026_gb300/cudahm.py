@@ -75,6 +75,15 @@ class CudahmStats(ctypes.Structure):
     ]
 
 
+class CudahmTune(ctypes.Structure):
+    _fields_ = [
+        ("block_threads", ctypes.c_int32),
+        ("sweeps_per_launch", ctypes.c_int32),
+        ("use_graph", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
 class CudahmError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"cudahm error {code}: {msg}")
@@ -90,7 +99,7 @@ EXPORTED = [
     "cudahm_run", "cudahm_get_samples", "cudahm_get_chi", "cudahm_get_theta", "cudahm_get_stats",
     "cudahm_eval_logdens", "cudahm_eval_etabar", "cudahm_eval_detection", "cudahm_get_trace", "cudahm_checkpoint", "cudahm_restore",
     "cudahm_sizeof_config", "cudahm_sizeof_stats", "cudahm_last_error", "cudahm_destroy",
-    "cudahm_lf_etabar_noalloc",
+    "cudahm_lf_etabar_noalloc", "cudahm_batch_run",
 ]
 
 
@@ -124,6 +133,8 @@ def lib():
     L.cudahm_sizeof_stats.restype = ctypes.c_size_t
     L.cudahm_last_error.restype = ctypes.c_char_p
     L.cudahm_lf_etabar_noalloc.argtypes = [vp, _dp, vp, vp]
+    L.cudahm_batch_run.argtypes = [ctypes.POINTER(vp), i32, i64, i64, i64, ctypes.POINTER(CudahmTune),
+                                   ctypes.POINTER(CudahmTune)]
     L.cudahm_destroy.argtypes = [vp]
     L.cudahm_destroy.restype = None
     for name in EXPORTED:
@@ -238,6 +249,23 @@ def cudahm_lf_etabar_noalloc(theta_dev_ptr: int, consts, etabar_dev_ptr: int, st
     c = _f64(consts)
     _check(lib().cudahm_lf_etabar_noalloc(ctypes.c_void_p(theta_dev_ptr), _dptr(c), ctypes.c_void_p(etabar_dev_ptr),
                                           ctypes.c_void_p(stream_ptr) if stream_ptr else None))
+
+
+def cudahm_batch_run(handles, n_burn: int, n_iter: int, thin: int = 1, tune: CudahmTune = None) -> CudahmTune:
+    """Run several populations in one persistent launch per chunk; returns the launch shape used."""
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    chosen = CudahmTune()
+    _check(lib().cudahm_batch_run(arr, len(handles), n_burn, n_iter, thin,
+                                  ctypes.byref(tune) if tune is not None else None, ctypes.byref(chosen)))
+    return chosen
+
+
+def batch_run(samplers, n_burn: int, n_iter: int, thin: int = 1, tune: CudahmTune = None):
+    """cudahm_batch_run over Sampler objects; returns (theta rows per sampler, launch shape)."""
+    chosen = cudahm_batch_run([s.h for s in samplers], n_burn, n_iter, thin, tune)
+    cap = n_iter // thin if (n_iter > 0 and thin > 0) else 0
+    rows = [cudahm_get_samples(s.h, s.p, cap) if cap > 0 else np.zeros((0, s.p)) for s in samplers]
+    return rows, chosen
 
 
 def cudahm_get_trace(h, n: int, p: int, T: int):

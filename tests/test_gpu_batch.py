@@ -1,0 +1,81 @@
+"""Batched runs: many populations in one persistent launch.
+
+Every population's chain is the same function of its own inputs whatever else shares the
+launch (sums are exact, per-member values are the same expressions), so the bar is
+bit-identity with the population run alone, in both precisions, for any launch shape."""
+import numpy as np
+import pytest
+
+from paper_2105_08026_gb300 import cudahm, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _populations(precision, seed0=0):
+    specs = [("nn1", 1), ("lf", 700), ("nn1", 2500), ("lf", 5000), ("nn1", 40000), ("lf", 256), ("nn1", 777)]
+    out = []
+    for q, (kind, n) in enumerate(specs):
+        if kind == "nn1":
+            d = synth.nn1_data(n, seed=100 + q + seed0)
+            th, sc, c = synth.nn1_settings(d)
+            out.append(dict(model=cudahm.NN1, n=n, y=d.y, aux=d.sigma, th=th, sc=sc, c=c, seed=31 + q))
+        else:
+            d = synth.lf_data(n, seed=200 + q + seed0)
+            th, sc, c = synth.lf_settings(d, nL=96, nr=200)
+            out.append(dict(model=cudahm.LF, n=n, y=d.fhat, aux=d.r, th=th, sc=sc, c=c, seed=41 + q))
+    return out
+
+
+def _make(spec, precision):
+    s = cudahm.Sampler(spec["model"], spec["n"], theta_init=spec["th"], theta_prop_scale=spec["sc"],
+                       model_consts=spec["c"], seed=spec["seed"], precision=precision)
+    s.set_data(spec["y"], spec["aux"])
+    return s
+
+
+def _state(s):
+    chi, S = s.chi()
+    th, Sth = s.theta()
+    return chi, S, th, Sth
+
+
+@pytest.mark.parametrize("precision", [cudahm.FP64, cudahm.FP32])
+def test_batch_equals_each_population_alone(precision):
+    specs = _populations(precision)
+    alone = []
+    for sp in specs:
+        s = _make(sp, precision)
+        rows = s.run(30, 90, 3)
+        alone.append((rows, _state(s)))
+    batch = [_make(sp, precision) for sp in specs]
+    rows_b, chosen = cudahm.batch_run(batch, 30, 90, 3)
+    assert chosen.block_threads in (128, 256)
+    for (ra, sa), rb, s in zip(alone, rows_b, batch):
+        assert np.array_equal(ra, rb)
+        for x, y in zip(sa, _state(s)):
+            assert np.array_equal(x, y)
+
+
+def test_batch_result_does_not_depend_on_launch_shape():
+    specs = _populations(cudahm.FP32, seed0=7)
+    runs = []
+    for block, chunk in ((128, 17), (256, 1000)):
+        ss = [_make(sp, cudahm.FP32) for sp in specs]
+        tune = cudahm.CudahmTune(block, chunk, 0, 0)
+        rows, chosen = cudahm.batch_run(ss, 0, 60, 1, tune)
+        assert chosen.block_threads == block and chosen.sweeps_per_launch == chunk
+        runs.append((rows, [_state(s) for s in ss]))
+    for a, b in zip(runs[0][0], runs[1][0]):
+        assert np.array_equal(a, b)
+    for sa, sb in zip(runs[0][1], runs[1][1]):
+        for x, y in zip(sa, sb):
+            assert np.array_equal(x, y)
+
+
+def test_batch_rejects_mixed_precision():
+    specs = _populations(cudahm.FP64)[:2]
+    a = _make(specs[0], cudahm.FP64)
+    b = _make(specs[1], cudahm.FP32)
+    with pytest.raises(cudahm.CudahmError) as ei:
+        cudahm.batch_run([a, b], 0, 5)
+    assert ei.value.code == cudahm.EINVAL
