@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-sweeps", type=int, default=2000)
+    ap.add_argument("--batched-pops", type=int, default=256)
     ap.add_argument("--cpu-sweeps", type=int, default=8)
     return ap.parse_args()
 
@@ -177,6 +180,45 @@ def fp64_peak(device):
     return 2.0 * r.value if rc == 0 else None  # FP64 flop/s
 
 
+def run_batched(args, cudahm, stream, device):
+    """k populations (half NN1, half LF; parameters of the single-population workloads scaled
+    by U[0.8, 1.2]; N log-uniform on [1e3, 1e6]), FP32 bulk form, one batched run timed with
+    CUDA events on the batch stream (its autotuning launches are part of the run)."""
+    import torch
+    from paper_2105_08026_gb300 import synth
+    specs = synth.batch_specs(args.batched_pops, seed=2000)
+    samplers = []
+    for sp in specs:
+        y, aux, th, sc, c = synth.pop_data(sp)
+        s = cudahm.Sampler(cudahm.NN1 if sp.kind == "nn1" else cudahm.LF, sp.n, theta_init=th, theta_prop_scale=sc,
+                           model_consts=c, seed=sp.seed, precision=cudahm.FP32, device=device,
+                           stream=stream.cuda_stream, use_torch_allocator=True)
+        s.set_data(y, aux)
+        samplers.append(s)
+    members = sum(sp.n for sp in specs)
+    K = args.batched_sweeps
+    W = min(args.warmup, 50)
+    if W > 0:
+        cudahm.batch_run(samplers, W, 0)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rows, chosen = cudahm.batch_run(samplers, 0, K, 1)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    assert all(r.shape[0] == K for r in rows)
+    for s in samplers:
+        s.close()
+    return {"value": members * K / (ms * 1e-3), "unit": "object-updates/s", "ms_per_step": ms / K,
+            "populations": len(specs), "members": members, "lf_populations": sum(sp.kind == "lf" for sp in specs),
+            "steps": K, "launch": {"block_threads": chosen.block_threads,
+                                   "sweeps_per_launch": chosen.sweeps_per_launch,
+                                   "graph": bool(chosen.use_graph), "blocks": chosen.reserved},
+            "dtype": "f32 member terms, f64 sums/accept/RAM/selection integral (1024x1024 rule per LF population)"}
+
+
 def run_cuda(args):
     import torch
     ws, rank, local = dist_env()
@@ -266,6 +308,11 @@ def run_cuda(args):
                 "dtype": "f32 member terms, f64 sums/accept/RAM/selection integral"}
         s3.close()
 
+    # batched FP32 form: 256 NN1/LF populations of uneven size in one persistent launch per chunk
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = run_batched(args, cudahm, stream, local)
+
     # e2e through the public API with host buffers (every iteration: H2D data, run, D2H samples)
     e2e = None
     if not args.no_e2e:
@@ -325,7 +372,7 @@ def run_cuda(args):
                        "member state register-resident within a launch", "timed_launches": R,
                        "launch_shape": [st.grid_blocks, st.block_threads, st.objects_per_thread]},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
-            "fp32_bulk": fp32}
+            "fp32_bulk": fp32, "batched_fp32": batched}
     print(json.dumps(line), flush=True)
     s.close()
     if ws > 1:

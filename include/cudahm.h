@@ -150,9 +150,11 @@ int cudahm_set_data_device(cudahm_t h, const double* y_dev, const double* aux_de
 int cudahm_set_chi(cudahm_t h, const double* chi_host, int64_t n);
 
 /* Run n_burn + n_iter sweeps, continuing the chain; keep theta after every thin-th sweep
- * of the n_iter (sweeps n_burn + thin, n_burn + 2 thin, ...). The sample buffer is
- * replaced by this run's rows. Blocking. run(a) then run(b) equals run(a + b) bit for bit
- * when both keep no rows (n_iter = 0) or when rows are compared by concatenation. */
+ * of the n_iter (sweeps n_burn + thin, n_burn + 2 thin, ...). The sample buffer is replaced
+ * by this run's rows. Blocking. run(a) then run(b) gives the same chain as run(a + b), and
+ * the rows of the second call continue those of the first. Populations small enough keep
+ * every member in registers for a whole launch; larger ones (beyond ~6e5 members) stream
+ * member state from device memory through the batched kernel, with the same chain. */
 int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin);
 
 /* Copy up to cap_rows theta rows (row-major, p doubles each) of the last run. */

@@ -233,7 +233,9 @@ int choose_shape(cudahm* h) {
       }
     }
   }
-  if (h->grid == 0) return fail(CUDAHM_EUNSUPPORTED, "n = %lld exceeds the register-resident capacity", n);
+  // Too many members to keep in registers: cudahm_run streams the state through the batched
+  // kernel (a batch of one) instead; K = 0 marks that.
+  if (h->grid == 0) h->K = 0;
   if (lf) {
     h->eb_grid = 4 * h->sms;
     h->eb_rows_smem = static_cast<int>((G + h->eb_grid - 1) / h->eb_grid);
@@ -537,6 +539,13 @@ int cudahm_set_chi(cudahm_t h, const double* chi_host, int64_t n) {
 int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
   if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
   if (!h->data_set) return fail(CUDAHM_ESTATE, "run before set_data");
+  if (h->K == 0) {  // streaming form: a batch of one population
+    if (h->cfg.trace_sweeps > 0) return fail(CUDAHM_EUNSUPPORTED, "traces need a register-resident population");
+    cudahm_t one[1] = {h};
+    CU(cudaEventRecord(h->ev0, h->stream));
+    const int rc = cudahm_batch_run(one, 1, n_burn, n_iter, thin, nullptr, nullptr);
+    return rc;
+  }
   if (n_burn < 0 || n_iter < 0) return fail(CUDAHM_EINVAL, "negative sweep counts");
   if (n_iter > 0 && thin < 1) return fail(CUDAHM_EINVAL, "thin must be >= 1");
   const long long total = n_burn + n_iter;

@@ -72,7 +72,8 @@ def _schechter_draw(g: np.random.Generator, m: int, beta: float, L_star: float, 
         if beta < -1.0:
             # Pareto proposal ~ L^beta on [L_low, inf), accepted with exp(-(L - L_low)/L*)
             v = 1.0 - g.random(k)  # (0, 1]
-            L = L_low * v ** (1.0 / (beta + 1.0))
+            with np.errstate(over="ignore"):  # overflow -> inf, rejected below
+                L = L_low * v ** (1.0 / (beta + 1.0))
             keep = g.random(k) < np.exp(-(L - L_low) / L_star)
         else:
             # gamma(beta+1, L*) proposal restricted to L > L_low
@@ -113,8 +114,8 @@ def solve_threshold(beta: float, L_star: float, L_low: float, r_max: float, dete
 
 
 def lf_data(n: int, beta: float = -1.2, L_star: float = 1e10, L_low: float = 1e8, r_max: float = 4000.0,
-            detect_frac: float = 0.30, sigma_frac: float = 0.2, seed: int = 1002) -> LFData:
-    F_th = solve_threshold(beta, L_star, L_low, r_max, detect_frac, sigma_frac, seed)
+            detect_frac: float = 0.30, sigma_frac: float = 0.2, seed: int = 1002, mc: int = 400_000) -> LFData:
+    F_th = solve_threshold(beta, L_star, L_low, r_max, detect_frac, sigma_frac, seed, m=mc)
     sigma_F = sigma_frac * F_th
     g = _rng(seed)
     fh, rr, LL = [], [], []
@@ -192,3 +193,41 @@ def lf_chi_init(data: LFData, theta) -> np.ndarray:
     """Default start: chi_i = ln(4 pi r_i^2 max(Fhat_i, F_th)), raised to ln L_low + 1e-6."""
     chi = np.log(4.0 * math.pi * data.r * data.r * np.maximum(data.fhat, data.F_th))
     return np.maximum(chi, theta[2] + 1e-6)
+
+
+# ------------------------------------------------------ batched workloads --
+@dataclass
+class PopSpec:
+    kind: str            # "nn1" or "lf"
+    n: int
+    seed: int
+    params: dict
+
+
+def batch_specs(k: int = 256, seed: int = 2000, n_lo: float = 1e3, n_hi: float = 1e6) -> list:
+    """k populations, half normal-normal and half luminosity-function, each parameter of the
+    single-population workloads scaled by U[0.8, 1.2], N log-uniform on [n_lo, n_hi]."""
+    g = _rng(seed)
+    out = []
+    for q in range(k):
+        n = int(round(math.exp(g.uniform(math.log(n_lo), math.log(n_hi)))))
+        f = g.uniform(0.8, 1.2, 5)
+        if q % 2 == 0:
+            out.append(PopSpec("nn1", n, seed + q, dict(mu=2.0 * f[0], tau=0.8 * f[1])))
+        else:
+            out.append(PopSpec("lf", n, seed + q, dict(beta=-1.2 * f[0], L_star=1e10 * f[1], L_low=1e8 * f[2],
+                                                       r_max=4000.0 * f[3], detect_frac=0.30 * f[4])))
+    return out
+
+
+def pop_data(spec: PopSpec, nL: int = 1024, nr: int = 1024):
+    """(y, aux, theta_init, theta_prop_scale, consts) of one population of batch_specs."""
+    if spec.kind == "nn1":
+        d = nn1_data(spec.n, mu=spec.params["mu"], tau=spec.params["tau"], seed=spec.seed)
+        th, sc, c = nn1_settings(d)
+        return d.y, d.sigma, th, sc, c
+    p = spec.params
+    d = lf_data(spec.n, beta=p["beta"], L_star=p["L_star"], L_low=p["L_low"], r_max=p["r_max"],
+                detect_frac=p["detect_frac"], seed=spec.seed, mc=100_000)
+    th, sc, c = lf_settings(d, nL=nL, nr=nr)
+    return d.fhat, d.r, th, sc, c

@@ -79,3 +79,20 @@ def test_batch_rejects_mixed_precision():
     with pytest.raises(cudahm.CudahmError) as ei:
         cudahm.batch_run([a, b], 0, 5)
     assert ei.value.code == cudahm.EINVAL
+
+
+def test_large_population_streams_with_the_same_chain():
+    """A population too large for register residency (7e5 members, FP32) runs through the streaming
+    kernel; it gives the chain the batched path gives it, and kept rows match a split run."""
+    d = synth.nn1_data(700_000, seed=5)
+    th, sc, c = synth.nn1_settings(d)
+    mk = lambda: cudahm.Sampler(cudahm.NN1, d.y.size, theta_init=th, theta_prop_scale=sc, model_consts=c, seed=3,
+                                precision=cudahm.FP32)
+    a, b = mk(), mk()
+    a.set_data(d.y, d.sigma)
+    b.set_data(d.y, d.sigma)
+    assert a.stats().objects_per_thread == 0
+    ra = a.run(10, 40)
+    rb = np.concatenate([b.run(10, 15), b.run(0, 25)])
+    assert np.array_equal(ra, rb)
+    assert np.array_equal(a.chi()[0], b.chi()[0])
