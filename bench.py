@@ -66,6 +66,11 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-sweeps", type=int, default=2000)
     ap.add_argument("--batched-pops", type=int, default=256)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-sweeps", type=int, default=5000)
+    ap.add_argument("--serve-pool", type=int, default=48)
     ap.add_argument("--cpu-sweeps", type=int, default=8)
     return ap.parse_args()
 
@@ -219,6 +224,72 @@ def run_batched(args, cudahm, stream, device):
             "dtype": "f32 member terms, f64 sums/accept/RAM/selection integral (1024x1024 rule per LF population)"}
 
 
+def run_served(args, cudahm, device):
+    """Poisson request stream (rate 20/s for --serve-seconds) into the continuous-batching server:
+    each request is NN1 or LF with probability 1/2, N log-uniform on [1e3, 3e5], 5000 sweeps,
+    FP32, 60 GB budget. Request data come from a pre-generated pool of catalogs (each request
+    has its own chain seed). Reports completion-latency percentiles and aggregate throughput."""
+    import threading as th_
+    from paper_2105_08026_gb300 import synth
+    g = np.random.default_rng(3000)
+    pool = []
+    for q in range(args.serve_pool):
+        n = int(round(math.exp(g.uniform(math.log(1e3), math.log(3e5)))))
+        kind = "nn1" if q % 2 == 0 else "lf"
+        f = g.uniform(0.8, 1.2, 5)
+        if kind == "nn1":
+            sp = synth.PopSpec("nn1", n, 3100 + q, dict(mu=2.0 * f[0], tau=0.8 * f[1]))
+        else:
+            sp = synth.PopSpec("lf", n, 3100 + q, dict(beta=-1.2 * f[0], L_star=1e10 * f[1], L_low=1e8 * f[2],
+                                                       r_max=4000.0 * f[3], detect_frac=0.30 * f[4]))
+        y, aux, th, sc, c = synth.pop_data(sp)
+        pool.append((sp, y, aux, th, sc, c))
+    sweeps = args.serve_sweeps
+    sv = cudahm.Server(60 << 30, device=device, precision=cudahm.FP32, max_active=512, sweeps_per_step=250)
+    arrivals = []
+    t = 0.0
+    while True:
+        t += g.exponential(1.0 / args.serve_rate)
+        if t > args.serve_seconds:
+            break
+        arrivals.append((t, int(g.integers(0, len(pool))), int(g.integers(1, 2**31))))
+    tickets = []
+
+    def producer():
+        t0 = time.perf_counter()
+        for (ta, pi, seed) in arrivals:
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            sp, y, aux, th, sc, c = pool[pi]
+            cfg = cudahm.make_config(cudahm.NN1 if sp.kind == "nn1" else cudahm.LF, sp.n, theta_init=th,
+                                     theta_prop_scale=sc, model_consts=c, seed=seed, precision=cudahm.FP32,
+                                     device=device)
+            tickets.append((sv.submit(cfg, y, aux, 0, sweeps, sweeps), sp.n))
+    t_start = time.perf_counter()
+    prod = th_.Thread(target=producer)
+    prod.start()
+    prod.join()
+    lat = []
+    work = 0.0
+    for tk, n in tickets:
+        sv.wait(tk, -1)
+        rows, ms = sv.result(tk)
+        lat.append(ms)
+        work += n * sweeps
+    wall = time.perf_counter() - t_start
+    st = sv.stats()
+    sv.close()
+    lat = np.array(lat)
+    offered = args.serve_rate * float(np.mean([pool[pi][0].n for _, pi, _ in arrivals])) * sweeps
+    return {"value": work / wall, "unit": "object-updates/s", "requests": len(tickets),
+            "arrival_rate_per_s": args.serve_rate, "window_s": args.serve_seconds, "sweeps_per_request": sweeps,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p95": float(np.percentile(lat, 95)),
+                           "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+            "offered_object_updates_per_s": offered, "wall_s": wall, "device_busy_s": st["busy_ms"] / 1e3,
+            "dtype": "f32 member terms, f64 sums/accept/RAM/selection integral", "budget_bytes": 60 << 30}
+
+
 def run_cuda(args):
     import torch
     ws, rank, local = dist_env()
@@ -313,6 +384,10 @@ def run_cuda(args):
     if not args.no_batched and rank == 0:
         batched = run_batched(args, cudahm, stream, local)
 
+    served = None
+    if not args.no_serve and rank == 0:
+        served = run_served(args, cudahm, local)
+
     # e2e through the public API with host buffers (every iteration: H2D data, run, D2H samples)
     e2e = None
     if not args.no_e2e:
@@ -372,7 +447,7 @@ def run_cuda(args):
                        "member state register-resident within a launch", "timed_launches": R,
                        "launch_shape": [st.grid_blocks, st.block_threads, st.objects_per_thread]},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
-            "fp32_bulk": fp32, "batched_fp32": batched}
+            "fp32_bulk": fp32, "batched_fp32": batched, "served_fp32": served}
     print(json.dumps(line), flush=True)
     s.close()
     if ws > 1:

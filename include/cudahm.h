@@ -244,6 +244,38 @@ typedef struct {
 int cudahm_batch_run(cudahm_t* handles, int32_t k, int64_t n_burn, int64_t n_iter, int64_t thin,
                      const cudahm_tune* tune, cudahm_tune* chosen);
 
+/* Serving: a request loop with continuous batching.
+ * A server owns a worker thread and a stream on one device. Requests (a config, member data
+ * and run lengths; the data are copied) queue in arrival order; the worker admits them while
+ * fewer than max_active are on the device and their estimated device memory fits the budget,
+ * creates their chain state, and advances every admitted request by sweeps_per_step sweeps
+ * per batched launch, each at its own stage. A finished request's theta rows are copied out
+ * and its memory released, which lets the next queued request in. A request's result is
+ * bit-identical to running it alone with cudahm_run (batched chains do not depend on what
+ * shares the launch). All requests of a server use its precision. */
+typedef struct cudahm_server* cudahm_server_t;
+
+int cudahm_server_create(size_t mem_budget_bytes, int32_t device, int32_t precision, int32_t max_active,
+                         int32_t sweeps_per_step, cudahm_server_t* out);
+/* ENOMEM if the request alone would exceed the budget; *ticket identifies it afterwards. */
+int cudahm_server_submit(cudahm_server_t s, const cudahm_config* cfg, const double* y_host,
+                         const double* aux_host, int64_t n_burn, int64_t n_iter, int64_t thin, uint64_t* ticket);
+/* *done = 1 once the request has finished (successfully or not). */
+int cudahm_server_poll(cudahm_server_t s, uint64_t ticket, int32_t* done);
+/* Block until the request has finished; ETIMEOUT after timeout_ms (< 0: no limit). */
+int cudahm_server_wait(cudahm_server_t s, uint64_t ticket, int64_t timeout_ms);
+/* Copy up to cap_rows theta rows of a finished request and release it (the ticket becomes
+ * unknown); latency_ms = completion time - submission time (host clock). Returns the
+ * request's error if it failed. */
+int cudahm_server_result(cudahm_server_t s, uint64_t ticket, double* theta_host, int64_t cap_rows,
+                         int64_t* rows_out, double* latency_ms);
+/* Completed requests, sum of members x sweeps over them, time spent in launches, queue and
+ * active counts (any pointer may be NULL). */
+int cudahm_server_stats(cudahm_server_t s, int64_t* completed, double* member_sweeps, double* busy_ms,
+                        int64_t* queued, int64_t* active);
+/* Stop the worker (after its current launch), release everything; NULL is ignored. */
+int cudahm_server_destroy(cudahm_server_t s);
+
 /* sizeof(cudahm_config) and sizeof(cudahm_stats) as compiled into the library, so that
  * bindings can check their struct layouts. */
 size_t cudahm_sizeof_config(void);

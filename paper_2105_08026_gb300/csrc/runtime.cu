@@ -3,7 +3,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
 #include <cstdarg>
 #include <cstdio>
 #include <cstddef>
@@ -1138,6 +1144,399 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
     chosen->use_graph = graph_ok ? 1 : 0;
     chosen->reserved = g_grid;
   }
+  return CUDAHM_OK;
+}
+
+// ---------------------------------------------------------------- serving --
+namespace {
+
+// One chunk of sweeps for handles at their own stages (progs: host mirrors, updated).
+int batch_step(const std::vector<cudahm*>& hs, std::vector<BatchProg>& progs, int chunk, int block, BatchBufs& bb,
+               int max_grid, cudaStream_t st, bool f32) {
+  const int k = static_cast<int>(hs.size());
+  const int R = 128;
+  const int smem = static_cast<int>(batch_smem_bytes(R));
+  int bps = 0;
+  CU(batch_occupancy(f32, block, smem, &bps));
+  if (bps < 1) return fail(CUDAHM_EUNSUPPORTED, "batched kernel does not fit on this device");
+  const int grid = std::min(bps * hs[0]->sms, block == 128 ? max_grid : max_grid / 2);
+  std::vector<SweepArgs> pops(k);
+  std::vector<double> cost(k);
+  std::vector<int> cap(k);
+  for (int q = 0; q < k; ++q) {
+    cudahm* h = hs[q];
+    SweepArgs a = base_args(h);
+    a.partials = bb.partials;
+    a.bar = bb.bars + q;
+    a.err = bb.errs + q;
+    a.rows = h->rows;
+    a.thin = progs[q].thin;
+    a.trace_T = 0;
+    a.skip_cta = -1;
+    pops[q] = a;
+    cost[q] = pop_cost(h);
+    long long c = (h->n + 31) / 32;
+    if (h->cfg.model == CUDAHM_LF)
+      c += static_cast<long long>(h->cfg.model_consts[3]) * ((static_cast<long long>(h->cfg.model_consts[4]) + 127) / 128);
+    cap[q] = static_cast<int>(std::min<long long>(c, max_grid));
+  }
+  std::vector<int> nb = allocate_blocks(cost, cap, grid), b0(k);
+  int acc = 0;
+  for (int q = 0; q < k; ++q) {
+    b0[q] = acc;
+    acc += nb[q];
+  }
+  if (acc > grid) return fail(CUDAHM_EUNSUPPORTED, "%d populations need more blocks than fit (%d)", k, grid);
+  CU(cudaMemcpyAsync(bb.pops, pops.data(), sizeof(SweepArgs) * k, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(bb.progs, progs.data(), sizeof(BatchProg) * k, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(bb.b0s, b0.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(bb.nbs, nb.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st));
+  CU(cudaMemsetAsync(bb.errs, 0, sizeof(int) * k, st));
+  CU(cudaMemsetAsync(bb.bars, 0, sizeof(unsigned int) * k, st));
+  CU(launch_batch_tables(bb.pops, bb.progs, k, chunk, st));
+  CU(launch_batch(f32, bb.pops, bb.progs, bb.b0s, bb.nbs, k, chunk, R, grid, block, smem, st));
+  CU(cudaMemcpyAsync(progs.data(), bb.progs, sizeof(BatchProg) * k, cudaMemcpyDeviceToHost, st));
+  std::vector<int> errs(k);
+  CU(cudaMemcpyAsync(errs.data(), bb.errs, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  for (int q = 0; q < k; ++q)
+    if (errs[q] != 0) return fail(errs[q], "population %d failed with device error %d", q, errs[q]);
+  return CUDAHM_OK;
+}
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+  uint64_t ticket = 0;
+  cudahm_config cfg{};
+  std::vector<double> y, aux;
+  long long n_burn = 0, n_iter = 0, thin = 1;
+  size_t bytes = 0;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  cudahm* h = nullptr;
+  BatchProg prog{};
+  std::vector<double> rows;
+  int state = 0;  // 0 queued, 1 active, 2 done
+  int err = 0;
+  std::string msg;
+};
+
+size_t request_bytes(const cudahm_config& c, long long n_iter, long long thin) {
+  const size_t n = static_cast<size_t>(c.n), d = c.d;
+  const size_t p = c.model == CUDAHM_NN1 ? 2 : (c.model == CUDAHM_LF ? 3 : 9);
+  size_t b = n * (4 * 8 + d * 8 + d * d * 8) + (c.precision == CUDAHM_FP32 ? n * 5 * 4 : 0);
+  b += static_cast<size_t>(n_iter / std::max<long long>(thin, 1)) * p * 8;
+  b += static_cast<size_t>(kChunk) * (p + 3) * 8 + 64 * 1024;
+  if (c.model == CUDAHM_LF) b += static_cast<size_t>(8 * 4096 + 2048) * 8;
+  return b;
+}
+
+}  // namespace
+
+struct cudahm_server {
+  size_t budget = 0, in_use = 0;
+  int device = 0, max_active = 0, chunk = 0, precision = 0, block = 128;
+  cudaStream_t stream = nullptr;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Request*> pending;
+  std::vector<Request*> active;
+  std::map<uint64_t, Request*> all;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  std::thread worker;
+  cudahm* owner = nullptr;  // buffer owner (a tiny handle that only provides the allocator)
+  BatchBufs bb;
+  int max_grid = 0;
+  long long done_count = 0;
+  double member_sweeps = 0.0;  // sum of n x sweeps over completed requests
+  double busy_ms = 0.0;
+};
+
+namespace {
+
+void serve_loop(cudahm_server* sv) {
+  cudaSetDevice(sv->device);
+  std::vector<Request*> admitted;
+  while (true) {
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      sv->cv.wait_for(lk, std::chrono::milliseconds(20),
+                      [&] { return sv->stop || !sv->pending.empty() || !sv->active.empty(); });
+      if (sv->stop) return;
+      // continuous batching: admit in arrival order while a slot and the memory budget allow
+      while (!sv->pending.empty() && static_cast<int>(sv->active.size() + admitted.size()) < sv->max_active &&
+             sv->in_use + sv->pending.front()->bytes <= sv->budget) {
+        Request* r = sv->pending.front();
+        sv->pending.pop_front();
+        sv->in_use += r->bytes;
+        r->t_admit = now_ms();
+        admitted.push_back(r);
+      }
+      if (sv->active.empty() && admitted.empty()) continue;
+    }
+    for (Request* r : admitted) {  // create and load outside the lock
+      cudahm_t h = nullptr;
+      r->cfg.cuda_stream = sv->stream;
+      int rc = cudahm_create(&r->cfg, &h);
+      if (rc == CUDAHM_OK) rc = cudahm_set_data(h, r->y.data(), r->aux.data(), r->cfg.n);
+      if (rc == CUDAHM_OK && r->cfg.model == CUDAHM_LF) {
+        char* base = reinterpret_cast<char*>(h->chain);
+        rc = compute_etabar_into(h, reinterpret_cast<const double*>(base + offsetof(ChainState, theta)),
+                                 reinterpret_cast<double*>(base + offsetof(ChainState, etabar)));
+        h->etabar_valid = true;
+      }
+      const long long nrows = r->n_iter > 0 ? r->n_iter / r->thin : 0;
+      if (rc == CUDAHM_OK && nrows > 0) {
+        rc = alloc_into(h, &h->rows, static_cast<size_t>(nrows) * h->p);
+        h->rows_cap = nrows;
+      }
+      std::lock_guard<std::mutex> lk(sv->mu);
+      if (rc != CUDAHM_OK) {
+        r->err = rc;
+        r->msg = cudahm_last_error();
+        r->state = 2;
+        r->t_done = now_ms();
+        sv->in_use -= r->bytes;
+        if (h) cudahm_destroy(h);
+        r->y.clear();
+        r->aux.clear();
+        sv->cv.notify_all();
+        continue;
+      }
+      r->h = h;
+      r->prog = BatchProg{r->n_burn + r->n_iter, 0, r->n_burn, r->thin, 0, 0};
+      r->state = 1;
+      r->y.clear();
+      r->y.shrink_to_fit();
+      r->aux.clear();
+      r->aux.shrink_to_fit();
+      sv->active.push_back(r);
+    }
+    admitted.clear();
+    std::vector<cudahm*> hs;
+    std::vector<BatchProg> progs;
+    std::vector<Request*> act;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      act = sv->active;
+    }
+    if (act.empty()) continue;
+    for (Request* r : act) {
+      hs.push_back(r->h);
+      progs.push_back(r->prog);
+    }
+    const double t0 = now_ms();
+    const int rc = batch_step(hs, progs, sv->chunk, sv->block, sv->bb, sv->max_grid, sv->stream,
+                              sv->precision == CUDAHM_FP32);
+    const double t1 = now_ms();
+    std::vector<Request*> finished;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->busy_ms += t1 - t0;
+      for (size_t q = 0; q < act.size(); ++q) {
+        Request* r = act[q];
+        if (rc != CUDAHM_OK) {
+          r->err = rc;
+          r->msg = cudahm_last_error();
+        } else {
+          r->prog = progs[q];
+        }
+        if (rc != CUDAHM_OK || r->prog.off >= r->prog.total) finished.push_back(r);
+      }
+      for (Request* r : finished) sv->active.erase(std::find(sv->active.begin(), sv->active.end(), r));
+    }
+    for (Request* r : finished) {  // collect results and release memory outside the lock
+      if (r->err == 0 && r->prog.rows > 0) {
+        r->rows.resize(static_cast<size_t>(r->prog.rows) * r->h->p);
+        cudaMemcpy(r->rows.data(), r->h->rows, sizeof(double) * r->rows.size(), cudaMemcpyDeviceToHost);
+      }
+      const double ms = now_ms();
+      cudahm_destroy(r->h);
+      r->h = nullptr;
+      std::lock_guard<std::mutex> lk(sv->mu);
+      r->t_done = ms;
+      r->state = 2;
+      sv->in_use -= r->bytes;
+      if (r->err == 0) {
+        sv->done_count++;
+        sv->member_sweeps += static_cast<double>(r->cfg.n) * static_cast<double>(r->prog.total);
+      }
+      sv->cv.notify_all();
+    }
+  }
+}
+
+}  // namespace
+
+int cudahm_server_create(size_t mem_budget_bytes, int32_t device, int32_t precision, int32_t max_active,
+                         int32_t sweeps_per_step, cudahm_server_t* out) {
+  if (!out) return fail(CUDAHM_EINVAL, "out is NULL");
+  if (precision != CUDAHM_FP64 && precision != CUDAHM_FP32) return fail(CUDAHM_EINVAL, "unknown precision");
+  if (max_active < 1 || max_active > 4096) return fail(CUDAHM_EINVAL, "max_active must be in [1, 4096]");
+  if (sweeps_per_step < 1 || sweeps_per_step > kChunk) return fail(CUDAHM_EINVAL, "bad sweeps_per_step");
+  if (mem_budget_bytes == 0) return fail(CUDAHM_EINVAL, "memory budget is zero");
+  int ndev = 0;
+  CU(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(CUDAHM_EINVAL, "device %d not present", device);
+  CU(cudaSetDevice(device));
+  auto* sv = new cudahm_server();
+  sv->budget = mem_budget_bytes;
+  sv->device = device;
+  sv->precision = precision;
+  sv->max_active = max_active;
+  sv->chunk = sweeps_per_step;
+  if (cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete sv;
+    return fail(CUDAHM_ECUDA, "cannot create the server stream");
+  }
+  // a one-member handle provides the allocator and device properties for the server's buffers
+  cudahm_config oc;
+  cudahm_config_init(&oc, CUDAHM_NN1, 1);
+  oc.device = device;
+  oc.adapt_theta = 0;
+  oc.cuda_stream = sv->stream;
+  int rc = cudahm_create(&oc, &sv->owner);
+  if (rc == CUDAHM_OK) {
+    sv->bb.owner = sv->owner;
+    sv->max_grid = 8 * sv->owner->sms;
+    if ((rc = alloc_into(sv->owner, &sv->bb.pops, max_active)) == CUDAHM_OK &&
+        (rc = alloc_into(sv->owner, &sv->bb.progs, max_active)) == CUDAHM_OK &&
+        (rc = alloc_into(sv->owner, &sv->bb.b0s, max_active)) == CUDAHM_OK &&
+        (rc = alloc_into(sv->owner, &sv->bb.nbs, max_active)) == CUDAHM_OK &&
+        (rc = alloc_into(sv->owner, &sv->bb.partials, 2ull * sv->max_grid * kPartWords)) == CUDAHM_OK &&
+        (rc = alloc_into(sv->owner, &sv->bb.bars, max_active)) == CUDAHM_OK)
+      rc = alloc_into(sv->owner, &sv->bb.errs, max_active);
+  }
+  if (rc != CUDAHM_OK) {
+    sv->bb.owner = nullptr;
+    if (sv->owner) cudahm_destroy(sv->owner);
+    cudaStreamDestroy(sv->stream);
+    delete sv;
+    return rc;
+  }
+  sv->worker = std::thread(serve_loop, sv);
+  *out = sv;
+  return CUDAHM_OK;
+}
+
+int cudahm_server_submit(cudahm_server_t sv, const cudahm_config* cfg, const double* y_host, const double* aux_host,
+                         int64_t n_burn, int64_t n_iter, int64_t thin, uint64_t* ticket) {
+  if (!sv || !cfg || !y_host || !aux_host || !ticket) return fail(CUDAHM_EINVAL, "NULL argument");
+  TRY(validate(cfg));
+  if (cfg->precision != sv->precision) return fail(CUDAHM_EINVAL, "request precision differs from the server's");
+  if (cfg->device != sv->device) return fail(CUDAHM_EINVAL, "request device differs from the server's");
+  if (cfg->trace_sweeps > 0) return fail(CUDAHM_EUNSUPPORTED, "served requests do not record traces");
+  if (n_burn < 0 || n_iter < 0 || n_burn + n_iter < 1 || (n_iter > 0 && thin < 1))
+    return fail(CUDAHM_EINVAL, "bad sweep counts");
+  auto* r = new Request();
+  r->cfg = *cfg;
+  r->cfg.dev_alloc = nullptr;
+  r->cfg.dev_free = nullptr;
+  r->n_burn = n_burn;
+  r->n_iter = n_iter;
+  r->thin = n_iter > 0 ? thin : 1;
+  r->bytes = request_bytes(*cfg, n_iter, r->thin);
+  if (r->bytes > sv->budget) {
+    delete r;
+    return fail(CUDAHM_ENOMEM, "request needs about %zu bytes, more than the whole budget", r->bytes);
+  }
+  const size_t cnt = static_cast<size_t>(cfg->n) * cfg->d;
+  r->y.assign(y_host, y_host + cnt);
+  r->aux.assign(aux_host, aux_host + cnt);
+  std::lock_guard<std::mutex> lk(sv->mu);
+  r->ticket = sv->next_ticket++;
+  r->t_submit = now_ms();
+  sv->pending.push_back(r);
+  sv->all[r->ticket] = r;
+  *ticket = r->ticket;
+  sv->cv.notify_all();
+  return CUDAHM_OK;
+}
+
+int cudahm_server_poll(cudahm_server_t sv, uint64_t ticket, int32_t* done) {
+  if (!sv || !done) return fail(CUDAHM_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->all.find(ticket);
+  if (it == sv->all.end()) return fail(CUDAHM_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+  *done = it->second->state == 2 ? 1 : 0;
+  return CUDAHM_OK;
+}
+
+int cudahm_server_wait(cudahm_server_t sv, uint64_t ticket, int64_t timeout_ms) {
+  if (!sv) return fail(CUDAHM_EINVAL, "NULL argument");
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->all.find(ticket);
+  if (it == sv->all.end()) return fail(CUDAHM_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+  Request* r = it->second;
+  const bool ok = sv->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? (1ll << 40) : timeout_ms),
+                                  [&] { return r->state == 2; });
+  if (!ok) return fail(CUDAHM_ETIMEOUT, "request %llu not done within %lld ms", (unsigned long long)ticket,
+                       (long long)timeout_ms);
+  return CUDAHM_OK;
+}
+
+int cudahm_server_result(cudahm_server_t sv, uint64_t ticket, double* theta_host, int64_t cap_rows,
+                         int64_t* rows_out, double* latency_ms) {
+  if (!sv) return fail(CUDAHM_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->all.find(ticket);
+  if (it == sv->all.end()) return fail(CUDAHM_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+  Request* r = it->second;
+  if (r->state != 2) return fail(CUDAHM_ESTATE, "request %llu is not done", (unsigned long long)ticket);
+  if (r->err != 0) {
+    const int e = r->err;
+    const std::string m = r->msg;
+    sv->all.erase(it);
+    delete r;
+    return fail(e, "request failed: %s", m.c_str());
+  }
+  const int p = r->cfg.model == CUDAHM_NN1 ? 2 : (r->cfg.model == CUDAHM_LF ? 3 : 9);
+  const long long rows = static_cast<long long>(r->rows.size()) / p;
+  if (rows_out) *rows_out = rows;
+  if (latency_ms) *latency_ms = r->t_done - r->t_submit;
+  if (theta_host && cap_rows > 0)
+    std::memcpy(theta_host, r->rows.data(), sizeof(double) * std::min<long long>(rows, cap_rows) * p);
+  sv->all.erase(it);
+  delete r;
+  return CUDAHM_OK;
+}
+
+int cudahm_server_stats(cudahm_server_t sv, int64_t* completed, double* member_sweeps, double* busy_ms,
+                        int64_t* queued, int64_t* active) {
+  if (!sv) return fail(CUDAHM_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (completed) *completed = sv->done_count;
+  if (member_sweeps) *member_sweeps = sv->member_sweeps;
+  if (busy_ms) *busy_ms = sv->busy_ms;
+  if (queued) *queued = static_cast<int64_t>(sv->pending.size());
+  if (active) *active = static_cast<int64_t>(sv->active.size());
+  return CUDAHM_OK;
+}
+
+int cudahm_server_destroy(cudahm_server_t sv) {
+  if (!sv) return CUDAHM_OK;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+  }
+  sv->cv.notify_all();
+  if (sv->worker.joinable()) sv->worker.join();
+  cudaSetDevice(sv->device);
+  for (Request* r : sv->active)
+    if (r->h) cudahm_destroy(r->h);
+  for (auto& kv : sv->all) delete kv.second;
+  // the batch buffers go back through their owner, then the owner itself
+  for (void* q : {(void*)sv->bb.pops, (void*)sv->bb.progs, (void*)sv->bb.b0s, (void*)sv->bb.nbs,
+                  (void*)sv->bb.partials, (void*)sv->bb.bars, (void*)sv->bb.errs})
+    sv->owner->dfree(q);
+  sv->bb.owner = nullptr;
+  cudahm_destroy(sv->owner);
+  cudaStreamDestroy(sv->stream);
+  delete sv;
   return CUDAHM_OK;
 }
 

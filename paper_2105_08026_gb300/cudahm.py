@@ -99,7 +99,9 @@ EXPORTED = [
     "cudahm_run", "cudahm_get_samples", "cudahm_get_chi", "cudahm_get_theta", "cudahm_get_stats",
     "cudahm_eval_logdens", "cudahm_eval_etabar", "cudahm_eval_detection", "cudahm_get_trace", "cudahm_checkpoint", "cudahm_restore",
     "cudahm_sizeof_config", "cudahm_sizeof_stats", "cudahm_last_error", "cudahm_destroy",
-    "cudahm_lf_etabar_noalloc", "cudahm_batch_run",
+    "cudahm_lf_etabar_noalloc", "cudahm_batch_run", "cudahm_server_create", "cudahm_server_submit",
+    "cudahm_server_poll", "cudahm_server_wait", "cudahm_server_result", "cudahm_server_stats",
+    "cudahm_server_destroy",
 ]
 
 
@@ -133,6 +135,14 @@ def lib():
     L.cudahm_sizeof_stats.restype = ctypes.c_size_t
     L.cudahm_last_error.restype = ctypes.c_char_p
     L.cudahm_lf_etabar_noalloc.argtypes = [vp, _dp, vp, vp]
+    L.cudahm_server_create.argtypes = [ctypes.c_size_t, i32, i32, i32, i32, ctypes.POINTER(vp)]
+    L.cudahm_server_submit.argtypes = [vp, ctypes.POINTER(CudahmConfig), _dp, _dp, i64, i64, i64,
+                                       ctypes.POINTER(ctypes.c_uint64)]
+    L.cudahm_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i32)]
+    L.cudahm_server_wait.argtypes = [vp, ctypes.c_uint64, i64]
+    L.cudahm_server_result.argtypes = [vp, ctypes.c_uint64, _dp, i64, ctypes.POINTER(i64), _dp]
+    L.cudahm_server_stats.argtypes = [vp, ctypes.POINTER(i64), _dp, _dp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.cudahm_server_destroy.argtypes = [vp]
     L.cudahm_batch_run.argtypes = [ctypes.POINTER(vp), i32, i64, i64, i64, ctypes.POINTER(CudahmTune),
                                    ctypes.POINTER(CudahmTune)]
     L.cudahm_destroy.argtypes = [vp]
@@ -266,6 +276,78 @@ def batch_run(samplers, n_burn: int, n_iter: int, thin: int = 1, tune: CudahmTun
     cap = n_iter // thin if (n_iter > 0 and thin > 0) else 0
     rows = [cudahm_get_samples(s.h, s.p, cap) if cap > 0 else np.zeros((0, s.p)) for s in samplers]
     return rows, chosen
+
+
+def make_config(model: int, n: int, *, theta_init, theta_prop_scale=None, model_consts=None, seed: int = 1,
+                precision: int = FP64, adapt_theta: bool = True, device: int = 0) -> CudahmConfig:
+    cfg = cudahm_config_init(model, n)
+    cfg.precision = precision
+    cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    cfg.adapt_theta = 1 if adapt_theta else 0
+    cfg.device = device
+    for q, v in enumerate(_f64(theta_init)):
+        cfg.theta_init[q] = v
+    if theta_prop_scale is not None:
+        for q, v in enumerate(_f64(theta_prop_scale)):
+            cfg.theta_prop_scale[q] = v
+    if model_consts is not None:
+        for q, v in enumerate(_f64(model_consts)):
+            cfg.model_consts[q] = v
+    return cfg
+
+
+class Server:
+    """Request loop with continuous batching (cudahm_server_*)."""
+
+    def __init__(self, mem_budget_bytes: int, device: int = 0, precision: int = FP32, max_active: int = 256,
+                 sweeps_per_step: int = 250):
+        self.h = ctypes.c_void_p()
+        self.precision = precision
+        _check(lib().cudahm_server_create(int(mem_budget_bytes), device, precision, max_active, sweeps_per_step,
+                                          ctypes.byref(self.h)))
+        self.p_of = {}
+
+    def submit(self, cfg: CudahmConfig, y, aux, n_burn: int, n_iter: int, thin: int = 1) -> int:
+        y, aux = _f64(y), _f64(aux)
+        t = ctypes.c_uint64(0)
+        _check(lib().cudahm_server_submit(self.h, ctypes.byref(cfg), _dptr(y), _dptr(aux), n_burn, n_iter, thin,
+                                          ctypes.byref(t)))
+        self.p_of[t.value] = (MODEL_P[cfg.model], n_iter // thin if n_iter > 0 else 0)
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        d = ctypes.c_int32(0)
+        _check(lib().cudahm_server_poll(self.h, ticket, ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        _check(lib().cudahm_server_wait(self.h, ticket, timeout_ms))
+
+    def result(self, ticket: int):
+        p, cap = self.p_of.pop(ticket)
+        out = np.zeros((max(cap, 1), p))
+        rows = ctypes.c_int64(0)
+        lat = ctypes.c_double(0.0)
+        _check(lib().cudahm_server_result(self.h, ticket, _dptr(out), cap, ctypes.byref(rows), ctypes.byref(lat)))
+        return out[: rows.value].copy(), lat.value
+
+    def stats(self):
+        c, q, a = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        ms, busy = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _check(lib().cudahm_server_stats(self.h, ctypes.byref(c), ctypes.byref(ms), ctypes.byref(busy),
+                                         ctypes.byref(q), ctypes.byref(a)))
+        return dict(completed=c.value, member_sweeps=ms.value, busy_ms=busy.value, queued=q.value, active=a.value)
+
+    def close(self):
+        if self.h:
+            lib().cudahm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def cudahm_get_trace(h, n: int, p: int, T: int):
