@@ -62,8 +62,11 @@ typedef struct cudahm* cudahm_t;
  *  NN1  normal-normal, d = 1, theta = (mu, ln tau), p = 2 (Sec. 3 with one characteristic):
  *       log l_i = -(y_i - chi)^2/(2 sigma_i^2), log f = -(chi - mu)^2/(2 tau^2) - ln tau;
  *       prior flat in mu and in ln tau on [consts[0], consts[1]].
- *  MVN3 normal population, d = 3, theta = (mu[3], packed Cholesky factor of C_pop with
- *       log diagonal), p = 9 (Sec. 3 with C_pop unknown). Reserved; not in this build.
+ *  MVN3 normal population, d = 3 (Sec. 3 with C_pop unknown), theta = (mu[3], L11, L21, L22,
+ *       L31, L32, L33), p = 9, with L the lower Cholesky factor of C_pop and its diagonal
+ *       entries given as logs: log f = -|L^-1 (chi - mu)|^2/2 - sum_j ln L_jj,
+ *       log l_i = -sum_j (y_ij - chi_j)^2/(2 s_ij^2); prior flat in every theta component.
+ *       Member state always streams from device memory (batched kernel), per component.
  *  LF   thinned luminosity function (Sec. 4-5), d = 1, chi = ln L, theta = (beta, ln L*, ln L_low),
  *       p = 3: log f = (beta+1)(chi - ln L*) - e^(chi - ln L*) on chi > ln L_low,
  *       log l_i = -(Fhat_i - e^chi/(4 pi r_i^2))^2/(2 sigma_F^2), selection efficiency
@@ -80,7 +83,11 @@ typedef enum { CUDAHM_NN1 = 0, CUDAHM_MVN3 = 1, CUDAHM_LF = 2 } cudahm_model;
  * own (Philox block (0, stream 2, member, odd sweep): a Box-Muller pair from 24-bit uniforms,
  * cosine for the odd sweep and sine for the next, accept uniforms from words 2 and 3); the
  * RAM factors S, the exact sum over members, the theta accept and its RAM update, and the
- * selection integral stay binary64. Latents are binary32 values (held as doubles in the API). */
+ * selection integral stay binary64. Latents are binary32 values (held as doubles in the API).
+ * MVN3 in FP32 draws from Philox blocks (0, 2, member, odd sweep) and (1, 2, member, odd sweep):
+ * pairs from words (0,1), (2,3) of the first and (0,1) of the second give U's three components,
+ * words 2 and 3 of the second the odd and even sweep's accept uniforms; v = S U and the RAM
+ * update of its 3 x 3 factor are binary64. */
 typedef enum { CUDAHM_FP64 = 0, CUDAHM_FP32 = 1 } cudahm_precision;
 
 typedef void* (*cudahm_alloc_fn)(size_t bytes, void* ctx);
@@ -136,9 +143,10 @@ void cudahm_config_init(cudahm_config* cfg, int32_t model, int64_t n);
  * for LF, builds the quadrature tables on the device. *out is set only on success. */
 int cudahm_create(const cudahm_config* cfg, cudahm_t* out);
 
-/* Member data, N entries each (copied):
- *   NN1: y = y_i, aux = sigma_i (> 0);   LF: y = Fhat_i, aux = r_i (> 0).
- * Resets the latents to the default start (NN1: chi_i = y_i; LF: chi_i = ln(4 pi r_i^2
+/* Member data, N entries each (N*d for MVN3, member-major; copied):
+ *   NN1: y = y_i, aux = sigma_i (> 0);   LF: y = Fhat_i, aux = r_i (> 0);
+ *   MVN3: y = y_i[3], aux = s_i[3] (> 0, the measurement sd of each component).
+ * Resets the latents to the default start (NN1, MVN3: chi_i = y_i; LF: chi_i = ln(4 pi r_i^2
  * max(Fhat_i, F_th)), raised to ln L_low + 1e-6 if below), every S_i to
  * chi_init_scale * I, theta to theta_init, S_theta to diag(theta_prop_scale), and the
  * sweep counter and sample buffer to zero. */
@@ -153,8 +161,9 @@ int cudahm_set_chi(cudahm_t h, const double* chi_host, int64_t n);
  * of the n_iter (sweeps n_burn + thin, n_burn + 2 thin, ...). The sample buffer is replaced
  * by this run's rows. Blocking. run(a) then run(b) gives the same chain as run(a + b), and
  * the rows of the second call continue those of the first. Populations small enough keep
- * every member in registers for a whole launch; larger ones (beyond ~6e5 members) stream
- * member state from device memory through the batched kernel, with the same chain. */
+ * every member in registers for a whole launch; larger ones (beyond ~6e5 members) and every
+ * MVN3 population stream member state from device memory through the batched kernel, with
+ * the same chain. */
 int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin);
 
 /* Copy up to cap_rows theta rows (row-major, p doubles each) of the last run. */
@@ -234,7 +243,7 @@ typedef struct {
 } cudahm_tune;
 
 /* Run n_burn + n_iter sweeps of k populations (handles created and loaded as usual, on one
- * device, one precision, without traces) in one persistent launch per chunk of sweeps.
+ * device, one precision; a trace only for k = 1) in one persistent launch per chunk of sweeps.
  * Population q gets a block range sized by a cost model (members, selection-rule pairs),
  * refined twice from each population's measured device time; its blocks meet at a bounded
  * per-population barrier each sweep, so populations never wait for one another. Every

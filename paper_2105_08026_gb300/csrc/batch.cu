@@ -65,7 +65,7 @@ template <class M>
 __device__ __forceinline__ void member_f64(const SweepArgs& a, unsigned int i, uint32_t k, double eta,
                                            const ThetaC& tc, const ThetaC& tcp, bool prior_ok, const double* s_math,
                                            Xacc& xd, XFlags& fd, unsigned int& neg_big, unsigned int& pos_big,
-                                           unsigned int& nan_cnt, unsigned int& acc_cnt) {
+                                           unsigned int& nan_cnt, unsigned int& acc_cnt, long long tro) {
   double chi = a.chi[i], S = a.S[i];
   const double yv = a.y[i], av = a.aux[i];
   double echi = M::kExp ? exp_tab(chi, s_math) : 0.0;
@@ -100,6 +100,11 @@ __device__ __forceinline__ void member_f64(const SweepArgs& a, unsigned int i, u
   S *= sqrt(fma(eta, alpha - a.astar, 1.0));
   a.chi[i] = chi;
   a.S[i] = S;
+  if (tro >= 0) {
+    a.tr_delta[tro + i] = delta;
+    a.tr_u[tro + i] = u;
+    a.tr_acc[tro + i] = acc ? 1 : 0;
+  }
   if (prior_ok) {
     const double dn = M::support(chi, tcp) ? M::logf(chi, echi, tcp) - M::logf(chi, echi, tc) : -INFINITY;
     if (disnan(dn)) fd.nan++;
@@ -117,7 +122,7 @@ template <class M>
 __device__ __forceinline__ void member_f32(const SweepArgs& a, unsigned int i, uint32_t k, double eta,
                                            const ThetaCf& tf, const ThetaCf& tpf, bool prior_ok, Xacc& xd,
                                            XFlags& fd, unsigned int& neg_big, unsigned int& pos_big,
-                                           unsigned int& nan_cnt, unsigned int& acc_cnt) {
+                                           unsigned int& nan_cnt, unsigned int& acc_cnt, long long tro) {
   float chi = static_cast<float>(a.chi[i]);
   double S = a.S[i];
   float d[M::kData32];
@@ -150,8 +155,166 @@ __device__ __forceinline__ void member_f32(const SweepArgs& a, unsigned int i, u
   S *= sqrt(fma(eta, static_cast<double>(alpha) - a.astar, 1.0));
   a.chi[i] = static_cast<double>(chi);
   a.S[i] = S;
+  if (tro >= 0) {
+    a.tr_delta[tro + i] = static_cast<double>(delta);
+    a.tr_u[tro + i] = static_cast<double>(u);
+    a.tr_acc[tro + i] = acc ? 1 : 0;
+  }
   if (prior_ok) {
     const float dn = M::support32(chi, tpf) ? M::logf32(chi, tpf) - M::logf32(chi, tf) : -INFINITY;
+    if (dn != dn) fd.nan++;
+    else if (fabsf(dn) >= 0x1p94f) {
+      if (dn < 0.0f) neg_big++;
+      else pos_big++;
+    } else {
+      xacc_add_float(xd, dn, fd);
+    }
+  }
+}
+
+// One member's sweep for the d = 3 model (FP64 form). State and data are stored per component
+// (structure of arrays, component j of member i at j n + i; the RAM factor as six packed rows).
+// Draws as the oracle defines them: component c of U from the Box-Muller pair of Philox block
+// (c, stream 0, i, odd sweep) (cosine for the odd sweep, sine for the next), the accept
+// uniform from block (3, 0, i, k).
+template <class M>
+__device__ __forceinline__ void member3_f64(const SweepArgs& a, unsigned int i, uint32_t k, double eta,
+                                            const ThetaC3& tc, const ThetaC3& tcp, bool prior_ok,
+                                            const double* s_math, Xacc& xd, XFlags& fd, unsigned int& neg_big,
+                                            unsigned int& pos_big, unsigned int& nan_cnt, unsigned int& acc_cnt,
+                                            long long tro) {
+  const size_t n = static_cast<size_t>(a.n);
+  double x[3], y[3], w[3], S[6];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    x[j] = a.chi[j * n + i];
+    y[j] = __ldg(a.y + j * n + i);
+    w[j] = __ldg(a.aux + j * n + i);
+  }
+#pragma unroll
+  for (int q = 0; q < 6; ++q) S[q] = a.S[q * n + i];
+  const bool odd = (k & 1u) != 0u;
+  const uint32_t ko = odd ? k : k - 1u;
+  double z[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const uint4 b = philox4x32_10(make_uint4(static_cast<uint32_t>(c), 0u, i, ko), a.key0, a.key1);
+    const double ua = uniform53(b.x, b.y), ub = uniform53(b.z, b.w);
+    const double rad = sqrt(-2.0 * log_tab(ua, s_math));
+    double sn, cs;
+    sincospi(2.0 * ub, &sn, &cs);
+    z[c] = odd ? rad * cs : rad * sn;
+  }
+  const uint4 bu = philox4x32_10(make_uint4(3u, 0u, i, k), a.key0, a.key1);
+  const double u = uniform53(bu.x, bu.y);
+  // v = S z (lower triangular), proposal Y = chi + v
+  const double v0 = S[0] * z[0];
+  const double v1 = fma(S[1], z[0], S[2] * z[1]);
+  const double v2 = fma(S[3], z[0], fma(S[4], z[1], S[5] * z[2]));
+  const double Y[3] = {x[0] + v0, x[1] + v1, x[2] + v2};
+  const double lfX = M::logf(x, tc), lfY = M::logf(Y, tc);
+  const double delta = (M::loglike(Y, y, w) + lfY) - (M::loglike(x, y, w) + lfX);
+  const bool dneg = dsign(delta);
+  const double alpha = dneg ? exp_tab(delta, s_math) : 1.0;
+  const bool acc = !dneg || (__double_as_longlong(u) < __double_as_longlong(alpha));
+  if (disnan(delta)) nan_cnt++;
+  double lf_cur = lfX;
+  if (acc) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) x[j] = Y[j];
+    lf_cur = lfY;
+    acc_cnt++;
+  }
+  const double zz = fma(z[0], z[0], fma(z[1], z[1], z[2] * z[2]));
+  ram3_update(S, v0, v1, v2, (eta * (alpha - a.astar)) / zz);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) a.chi[j * n + i] = x[j];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) a.S[q * n + i] = S[q];
+  if (tro >= 0) {
+    a.tr_delta[tro + i] = delta;
+    a.tr_u[tro + i] = u;
+    a.tr_acc[tro + i] = acc ? 1 : 0;
+  }
+  if (prior_ok) {
+    const double dn = M::logf(x, tcp) - lf_cur;
+    if (disnan(dn)) fd.nan++;
+    else if (dhuge(dn)) {
+      if (dsign(dn)) neg_big++;
+      else pos_big++;
+    } else {
+      xacc_add_double(xd, dn, fd);
+    }
+  }
+}
+
+// 24-bit uniform in (0, 1) from one Philox word
+__device__ __forceinline__ float uniform24(uint32_t w) { return (static_cast<float>(w >> 8) + 0.5f) * 0x1p-24f; }
+
+// Standard normal of sweep k from one Box-Muller pair of binary32 uniforms
+__device__ __forceinline__ float bm24(uint32_t wa, uint32_t wb, bool odd) {
+  const float rad = sqrtf(-2.0f * logf(uniform24(wa)));
+  float sn, cs;
+  sincospif(2.0f * uniform24(wb), &sn, &cs);
+  return odd ? rad * cs : rad * sn;
+}
+
+// One member's sweep for the d = 3 model in the FP32 bulk form: binary32 draws (Philox blocks
+// (0, stream 2, i, odd sweep) and (1, 2, i, odd sweep): Box-Muller pairs from words (0,1), (2,3)
+// of the first and (0,1) of the second give components 0, 1, 2, cosine for the odd sweep and
+// sine for the next; words 2 and 3 of the second are the odd and even sweep's accept uniforms),
+// binary32 member log targets, binary64 v = S z and RAM factor update.
+template <class M>
+__device__ __forceinline__ void member3_f32(const SweepArgs& a, unsigned int i, uint32_t k, double eta,
+                                            const ThetaC3f& tf, const ThetaC3f& tpf, bool prior_ok, Xacc& xd,
+                                            XFlags& fd, unsigned int& neg_big, unsigned int& pos_big,
+                                            unsigned int& nan_cnt, unsigned int& acc_cnt, long long tro) {
+  const size_t n = static_cast<size_t>(a.n);
+  float x[3], d[M::kData32];
+  double S[6];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) x[j] = static_cast<float>(a.chi[j * n + i]);
+#pragma unroll
+  for (int c = 0; c < M::kData32; ++c) d[c] = __ldg(a.d32 + c * n + i);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) S[q] = a.S[q * n + i];
+  const bool odd = (k & 1u) != 0u;
+  const uint32_t ko = odd ? k : k - 1u;
+  const uint4 b0 = philox4x32_10(make_uint4(0u, 2u, i, ko), a.key0, a.key1);
+  const uint4 b1 = philox4x32_10(make_uint4(1u, 2u, i, ko), a.key0, a.key1);
+  const float z0 = bm24(b0.x, b0.y, odd), z1 = bm24(b0.z, b0.w, odd), z2 = bm24(b1.x, b1.y, odd);
+  const float u = uniform24(odd ? b1.z : b1.w);
+  const double zd0 = z0, zd1 = z1, zd2 = z2;
+  const double v0 = S[0] * zd0;
+  const double v1 = fma(S[1], zd0, S[2] * zd1);
+  const double v2 = fma(S[3], zd0, fma(S[4], zd1, S[5] * zd2));
+  const float Y[3] = {__fadd_rn(x[0], static_cast<float>(v0)), __fadd_rn(x[1], static_cast<float>(v1)),
+                      __fadd_rn(x[2], static_cast<float>(v2))};
+  const float lfX = M::logf32(x, tf), lfY = M::logf32(Y, tf);
+  const float delta = __fsub_rn(__fadd_rn(M::loglike32(Y, d), lfY), __fadd_rn(M::loglike32(x, d), lfX));
+  const float alpha = (delta >= 0.0f) ? 1.0f : expf(delta);
+  const bool acc = (delta >= 0.0f) || (u < alpha);
+  if (delta != delta) nan_cnt++;
+  float lf_cur = lfX;
+  if (acc) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) x[j] = Y[j];
+    lf_cur = lfY;
+    acc_cnt++;
+  }
+  const double zz = fma(zd0, zd0, fma(zd1, zd1, zd2 * zd2));
+  ram3_update(S, v0, v1, v2, (eta * (static_cast<double>(alpha) - a.astar)) / zz);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) a.chi[j * n + i] = static_cast<double>(x[j]);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) a.S[q * n + i] = S[q];
+  if (tro >= 0) {
+    a.tr_delta[tro + i] = static_cast<double>(delta);
+    a.tr_u[tro + i] = static_cast<double>(u);
+    a.tr_acc[tro + i] = acc ? 1 : 0;
+  }
+  if (prior_ok) {
+    const float dn = __fsub_rn(M::logf32(x, tpf), lf_cur);
     if (dn != dn) fd.nan++;
     else if (fabsf(dn) >= 0x1p94f) {
       if (dn < 0.0f) neg_big++;
@@ -165,8 +328,10 @@ __device__ __forceinline__ void member_f32(const SweepArgs& a, unsigned int i, u
 template <class M, bool F32>
 __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int lb, int nb, int chunk, int R,
                                double* s_dyn, double* s_theta, double* s_thp, double* s_Sth, BlockRed& s_red) {
-  __shared__ ThetaC s_tc, s_tcp;
-  __shared__ ThetaCf s_tcf, s_tcpf;
+  using TC = typename M::TC;
+  using TCf = typename M::TCf;
+  __shared__ TC s_tc, s_tcp;
+  __shared__ TCf s_tcf, s_tcpf;
   __shared__ double s_etabar, s_logeb, s_lpri, s_lpri_new;
   __shared__ int s_stop;
   __shared__ long long s_rows_written, s_tacc, s_k0, s_off, s_ns;
@@ -211,7 +376,7 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
     // theta' = theta + S_theta U (the table of this launch's sweeps starts at index 0)
     if (tid == 0) {
       double lp;
-      ThetaC tcp;
+      TC tcp;
       propose_theta<M>(a, s, p, s_theta, s_Sth, s_thp, lp, tcp);
       s_lpri_new = lp;
       s_tcp = tcp;
@@ -224,26 +389,41 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
     xacc_zero(xe);
     XFlags fd = {0u, 0u, 0u}, fe = {0u, 0u, 0u};
     unsigned int neg_big = 0, pos_big = 0, member_nan = 0;
-    if constexpr (F32) {
-      const ThetaCf tf = s_tcf, tpf = s_tcpf;
+    const long long sg = off + s;  // sweep index within this run
+    const long long tro = (sg < a.trace_T) ? sg * a.n : -1;
+    if constexpr (M::kD == 3) {
+      if constexpr (F32) {
+        for (unsigned int i = nb0 + tid; i < nb1; i += blockDim.x)
+          member3_f32<M>(a, i, k, eta, s_tcf, s_tcpf, prior_ok, xd, fd, neg_big, pos_big, member_nan, member_acc,
+                         tro);
+      } else {
+        for (unsigned int i = nb0 + tid; i < nb1; i += blockDim.x)
+          member3_f64<M>(a, i, k, eta, s_tc, s_tcp, prior_ok, s_math, xd, fd, neg_big, pos_big, member_nan,
+                         member_acc, tro);
+      }
+    } else if constexpr (F32) {
+      const TCf tf = s_tcf, tpf = s_tcpf;
       for (unsigned int i = nb0 + tid; i < nb1; i += blockDim.x)
-        member_f32<M>(a, i, k, eta, tf, tpf, prior_ok, xd, fd, neg_big, pos_big, member_nan, member_acc);
+        member_f32<M>(a, i, k, eta, tf, tpf, prior_ok, xd, fd, neg_big, pos_big, member_nan, member_acc, tro);
     } else {
-      const ThetaC tc = s_tc, tcp = s_tcp;
+      const TC tc = s_tc, tcp = s_tcp;
       for (unsigned int i = nb0 + tid; i < nb1; i += blockDim.x)
-        member_f64<M>(a, i, k, eta, tc, tcp, prior_ok, s_math, xd, fd, neg_big, pos_big, member_nan, member_acc);
+        member_f64<M>(a, i, k, eta, tc, tcp, prior_ok, s_math, xd, fd, neg_big, pos_big, member_nan, member_acc,
+                      tro);
     }
     // a6: the rule's segments of this block, R at a time through the shared table
-    if (prior_ok && is_lf) {
-      const ThetaC tcp = s_tcp;
-      for (int t0 = 0; t0 < nseg; t0 += R) {
-        const int cnt = min(R, nseg - t0);
-        for (int q = tid; q < cnt; q += blockDim.x) lf_segment_row(tcp, a, lb, nb, t0 + q, q, tab);
-        __syncthreads();
-        if (wid == 0) lf_segment_scan(cnt, tab);
-        __syncthreads();
-        lf_segment_pairs(a, cnt, tab, s_phi, xe, fe);
-        __syncthreads();
+    if constexpr (std::is_same<M, LF>::value) {
+      if (prior_ok) {
+        const ThetaC tcp = s_tcp;
+        for (int t0 = 0; t0 < nseg; t0 += R) {
+          const int cnt = min(R, nseg - t0);
+          for (int q = tid; q < cnt; q += blockDim.x) lf_segment_row(tcp, a, lb, nb, t0 + q, q, tab);
+          __syncthreads();
+          if (wid == 0) lf_segment_scan(cnt, tab);
+          __syncthreads();
+          lf_segment_pairs(a, cnt, tab, s_phi, xe, fe);
+          __syncthreads();
+        }
       }
     }
     {
@@ -310,14 +490,20 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
           atomicCAS(a.err, 0, CUDAHM_ENUMERIC);
           s_stop = 1;
         } else {
-          double logalpha, eb_new = 0.0, logeb_new = 0.0;
-          if (!prior_ok || f[0] != 0u) {
+          double logalpha, Drec, eb_new = 0.0, logeb_new = 0.0;
+          if (!prior_ok) {
             logalpha = -INFINITY;
-          } else if (f[2] != 0u) {
+            Drec = 0.0;
+          } else if (f[0] != 0u) {  // a member off the proposal's support (or d <= -2^94)
+            logalpha = -INFINITY;
+            Drec = -INFINITY;
+          } else if (f[2] != 0u) {  // only huge positive differences remain
             logalpha = INFINITY;
+            Drec = INFINITY;
           } else {
             const double nn = static_cast<double>(a.n);
-            logalpha = xacc_to_double(D) + nn * (M::cterm(s_thp) - M::cterm(s_theta)) + s_lpri_new - s_lpri;
+            Drec = xacc_to_double(D);
+            logalpha = Drec + nn * (M::cterm(s_thp) - M::cterm(s_theta)) + s_lpri_new - s_lpri;
             if (is_lf) {
               eb_new = xacc_to_double(E);
               logeb_new = log(eb_new);
@@ -325,6 +511,14 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
             }
           }
           const bool acc = __ldg(a.tab_lnu + s) < logalpha;
+          if (lb == 0 && sg < a.trace_T) {
+            for (int q = 0; q < p; ++q) a.tr_thprop[sg * p + q] = s_thp[q];
+            a.tr_D[sg] = Drec;
+            a.tr_logalpha[sg] = logalpha;
+            a.tr_ut[sg] = __ldg(a.tab_u + s);
+            a.tr_tacc[sg] = acc ? 1 : 0;
+            a.tr_eb[sg] = eb_new;
+          }
           if (acc) {
             for (int q = 0; q < p; ++q) s_theta[q] = s_thp[q];
             s_tc = s_tcp;
@@ -397,8 +591,10 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const SweepArgs* __restri
   if (lb >= nb || prog->off >= prog->total) return;  // spare block, or the population has finished
   if (s_args.model == CUDAHM_NN1)
     run_population<NN1, F32>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
-  else
+  else if (s_args.model == CUDAHM_LF)
     run_population<LF, F32>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
+  else
+    run_population<MVN3, F32>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
 }
 
 // binary32 member data of the FP32 form (kData32 values per member, member-minor)
@@ -410,6 +606,19 @@ __global__ void data32_kernel(long long n, const double* y, const double* aux, M
   M::data32(y[i], aux[i], mc, d);
 #pragma unroll
   for (int c = 0; c < M::kData32; ++c) d32[c * n + i] = d[c];
+}
+
+// binary32 member data of the d = 3 model: y_ij as hi + lo, 1/(2 s_ij^2) (inputs stored per component)
+__global__ void data32_mvn3_kernel(long long n, const double* y, const double* aux, float* d32) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int j = 0; j < 3; ++j) {
+    float hi, lo;
+    split_f(y[j * n + i], hi, lo);
+    d32[(2 * j) * n + i] = hi;
+    d32[(2 * j + 1) * n + i] = lo;
+    d32[(6 + j) * n + i] = static_cast<float>(0.5 * aux[j * n + i]);
+  }
 }
 
 // Theta tables of every population for the next chunk: sweep k0 + 1 + s, s < ns.
@@ -446,13 +655,16 @@ __global__ void batch_tables_kernel(const SweepArgs* __restrict__ pops, const Ba
 
 }  // namespace
 
-int data32_words(int model) { return model == CUDAHM_LF ? LF::kData32 : NN1::kData32; }
+int data32_words(int model) {
+  return model == CUDAHM_LF ? LF::kData32 : (model == CUDAHM_MVN3 ? MVN3::kData32 : NN1::kData32);
+}
 
 cudaError_t launch_data32(int model, long long n, const double* y, const double* aux, const ModelConsts& mc,
                           float* d32, cudaStream_t st) {
   const int blk = 256;
   const unsigned int grid = static_cast<unsigned int>((n + blk - 1) / blk);
   if (model == CUDAHM_LF) data32_kernel<LF><<<grid, blk, 0, st>>>(n, y, aux, mc, d32);
+  else if (model == CUDAHM_MVN3) data32_mvn3_kernel<<<grid, blk, 0, st>>>(n, y, aux, d32);
   else data32_kernel<NN1><<<grid, blk, 0, st>>>(n, y, aux, mc, d32);
   return cudaGetLastError();
 }

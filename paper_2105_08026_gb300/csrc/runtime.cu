@@ -43,6 +43,8 @@ int fail(int code, const char* fmt, ...) {
   } while (0)
 
 int model_d(int m) { return m == CUDAHM_MVN3 ? 3 : 1; }
+// doubles of one member's RAM factor as stored on the device (d = 3: six packed rows)
+int factor_words(int d) { return d == 3 ? 6 : 1; }
 
 }  // namespace
 
@@ -80,6 +82,7 @@ struct cudahm {
   double *tab_U = nullptr, *tab_u = nullptr, *tab_lnu = nullptr, *tab_eta = nullptr;
   double* rows = nullptr;
   long long rows_cap = 0;
+  long long factor_n = 0;  // doubles of the RAM factors on the device (n * factor_words(d))
   // trace
   long long trace_cap_T = 0;
   double *tr_delta = nullptr, *tr_u = nullptr, *tr_thprop = nullptr, *tr_D = nullptr, *tr_logalpha = nullptr,
@@ -155,7 +158,6 @@ int validate(const cudahm_config* c) {
     return fail(CUDAHM_EINVAL, "abi_version %u != %u", c->abi_version, CUDAHM_ABI_VERSION);
   if (c->model != CUDAHM_NN1 && c->model != CUDAHM_LF && c->model != CUDAHM_MVN3)
     return fail(CUDAHM_EINVAL, "unknown model %d", c->model);
-  if (c->model == CUDAHM_MVN3) return fail(CUDAHM_EUNSUPPORTED, "model MVN3 is not in this build");
   if (c->precision != CUDAHM_FP64 && c->precision != CUDAHM_FP32)
     return fail(CUDAHM_EINVAL, "unknown precision %d", c->precision);
   if (c->d != model_d(c->model)) return fail(CUDAHM_EINVAL, "d = %d does not match the model", c->d);
@@ -212,7 +214,8 @@ int choose_shape(cudahm* h) {
                                ((static_cast<long long>(h->cfg.model_consts[4]) + 127) / 128)
                          : 0;
   const int Ks[4] = {1, 2, 4, 8};
-  for (int ki = 0; ki < 4 && h->grid == 0; ++ki) {
+  // the d = 3 model always streams its member state through the batched kernel
+  for (int ki = (model == CUDAHM_MVN3 ? 4 : 0); ki < 4 && h->grid == 0; ++ki) {
     const int K = Ks[ki];
     // the grid depends on the occupancy, which depends on the shared memory, which depends on
     // the grid: iterate from the register-limited occupancy down until it is consistent
@@ -294,7 +297,7 @@ SweepArgs base_args(cudahm* h) {
 // Cost (FP64-pipe operations per sweep) of one population, for the batched allocation.
 double pop_cost(const cudahm* h) {
   const bool f32 = h->cfg.precision == CUDAHM_FP32;
-  double c = 3000.0 + static_cast<double>(h->n) * (f32 ? 20.0 : 120.0);
+  double c = 3000.0 + static_cast<double>(h->n) * (h->d == 3 ? (f32 ? 80.0 : 260.0) : (f32 ? 20.0 : 120.0));
   if (h->cfg.model == CUDAHM_LF) {
     const double nL = h->cfg.model_consts[3], nr = h->cfg.model_consts[4];
     c += 0.3 * nL * nr * 17.0 + nL * std::ceil(nr / 128.0) * 70.0;
@@ -342,6 +345,29 @@ int read_err(cudahm* h, int* code) {
   CU(cudaMemcpyAsync(h->host_err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
   *code = *h->host_err;
+  return CUDAHM_OK;
+}
+
+// Lockstep trace buffers for the first T sweeps of a run.
+int ensure_trace(cudahm* h, long long T) {
+  if (T <= h->trace_cap_T) return CUDAHM_OK;
+  for (void** q : {(void**)&h->tr_delta, (void**)&h->tr_u, (void**)&h->tr_acc, (void**)&h->tr_thprop, (void**)&h->tr_D,
+                   (void**)&h->tr_logalpha, (void**)&h->tr_ut, (void**)&h->tr_tacc, (void**)&h->tr_eb}) {
+    h->dfree(*q);
+    *q = nullptr;
+  }
+  h->trace_cap_T = 0;
+  const size_t tn = static_cast<size_t>(T) * h->n;
+  TRY(alloc_into(h, &h->tr_delta, tn));
+  TRY(alloc_into(h, &h->tr_u, tn));
+  TRY(alloc_into(h, &h->tr_acc, tn));
+  TRY(alloc_into(h, &h->tr_thprop, static_cast<size_t>(T) * h->p));
+  TRY(alloc_into(h, &h->tr_D, T));
+  TRY(alloc_into(h, &h->tr_logalpha, T));
+  TRY(alloc_into(h, &h->tr_ut, T));
+  TRY(alloc_into(h, &h->tr_tacc, T));
+  TRY(alloc_into(h, &h->tr_eb, T));
+  h->trace_cap_T = T;
   return CUDAHM_OK;
 }
 
@@ -457,8 +483,10 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
 
   const long long n = h->n;
   const int p = h->p;
-  if ((rc = alloc_into(h, &h->y, n)) || (rc = alloc_into(h, &h->aux, n)) || (rc = alloc_into(h, &h->chi, n * h->d)) ||
-      (rc = alloc_into(h, &h->S, n * h->d * h->d)) || (rc = alloc_into(h, &h->chain, 1)) ||
+  h->factor_n = n * factor_words(h->d);
+  if ((rc = alloc_into(h, &h->y, n * h->d)) || (rc = alloc_into(h, &h->aux, n * h->d)) ||
+      (rc = alloc_into(h, &h->chi, n * h->d)) || (rc = alloc_into(h, &h->S, h->factor_n)) ||
+      (rc = alloc_into(h, &h->chain, 1)) ||
       (rc = alloc_into(h, &h->partials, 2ull * h->grid * kPartWords)) || (rc = alloc_into(h, &h->bar, 4)) ||
       (rc = alloc_into(h, &h->err, 4)) || (rc = alloc_into(h, &h->bad, 4)) ||
       (rc = alloc_into(h, &h->theta_dev, kMaxP)) || (rc = alloc_into(h, &h->eval_out, 4)) ||
@@ -525,11 +553,18 @@ int cudahm_set_chi(cudahm_t h, const double* chi_host, int64_t n) {
   if (!chi_host || n != h->n) return fail(CUDAHM_EINVAL, "bad chi argument");
   CU(cudaSetDevice(h->cfg.device));
   const size_t cnt = static_cast<size_t>(h->n) * h->d;
+  std::vector<double> soa;
+  if (h->d > 1) {  // member-major in the API, per component on the device
+    soa.resize(cnt);
+    for (size_t i = 0; i < static_cast<size_t>(h->n); ++i)
+      for (int j = 0; j < h->d; ++j) soa[j * h->n + i] = chi_host[i * h->d + j];
+    chi_host = soa.data();
+  }
   double* tmp = nullptr;
   TRY(alloc_into(h, &tmp, cnt));
   CU(cudaMemcpyAsync(tmp, chi_host, sizeof(double) * cnt, cudaMemcpyHostToDevice, h->stream));
   CU(cudaMemsetAsync(h->bad, 0, sizeof(int), h->stream));
-  CU(launch_check_chi(h->cfg.model, h->n, tmp, h->cfg.theta_init, h->bad, h->stream));
+  CU(launch_check_chi(h->cfg.model, static_cast<long long>(cnt), tmp, h->cfg.theta_init, h->bad, h->stream));
   CU(cudaMemcpyAsync(h->host_err, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
   if (*h->host_err) {
@@ -546,7 +581,6 @@ int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
   if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
   if (!h->data_set) return fail(CUDAHM_ESTATE, "run before set_data");
   if (h->K == 0) {  // streaming form: a batch of one population
-    if (h->cfg.trace_sweeps > 0) return fail(CUDAHM_EUNSUPPORTED, "traces need a register-resident population");
     cudahm_t one[1] = {h};
     CU(cudaEventRecord(h->ev0, h->stream));
     const int rc = cudahm_batch_run(one, 1, n_burn, n_iter, thin, nullptr, nullptr);
@@ -565,22 +599,7 @@ int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
     h->rows_cap = nrows;
   }
   const long long T = std::min<long long>(h->cfg.trace_sweeps, total);
-  if (T > h->trace_cap_T) {
-    for (void* q : {(void*)h->tr_delta, (void*)h->tr_u, (void*)h->tr_acc, (void*)h->tr_thprop, (void*)h->tr_D,
-                    (void*)h->tr_logalpha, (void*)h->tr_ut, (void*)h->tr_tacc, (void*)h->tr_eb})
-      h->dfree(q);
-    const size_t tn = static_cast<size_t>(T) * h->n;
-    TRY(alloc_into(h, &h->tr_delta, tn));
-    TRY(alloc_into(h, &h->tr_u, tn));
-    TRY(alloc_into(h, &h->tr_acc, tn));
-    TRY(alloc_into(h, &h->tr_thprop, static_cast<size_t>(T) * h->p));
-    TRY(alloc_into(h, &h->tr_D, T));
-    TRY(alloc_into(h, &h->tr_logalpha, T));
-    TRY(alloc_into(h, &h->tr_ut, T));
-    TRY(alloc_into(h, &h->tr_tacc, T));
-    TRY(alloc_into(h, &h->tr_eb, T));
-    h->trace_cap_T = T;
-  }
+  TRY(ensure_trace(h, T));
   CU(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
   CU(cudaEventRecord(h->ev0, h->stream));
   if (h->cfg.model == CUDAHM_LF && !h->etabar_valid) {
@@ -664,6 +683,28 @@ int cudahm_get_samples(cudahm_t h, double* theta_host, int64_t cap_rows, int64_t
 int cudahm_get_chi(cudahm_t h, double* chi_host, double* S_host) {
   if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
   CU(cudaSetDevice(h->cfg.device));
+  if (h->d == 3) {  // per-component device arrays to member-major host arrays
+    const size_t n = static_cast<size_t>(h->n);
+    if (chi_host) {
+      std::vector<double> t(3 * n);
+      CU(cudaMemcpyAsync(t.data(), h->chi, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+      CU(cudaStreamSynchronize(h->stream));
+      for (size_t i = 0; i < n; ++i)
+        for (int j = 0; j < 3; ++j) chi_host[3 * i + j] = t[j * n + i];
+    }
+    if (S_host) {
+      std::vector<double> t(6 * n);
+      CU(cudaMemcpyAsync(t.data(), h->S, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, h->stream));
+      CU(cudaStreamSynchronize(h->stream));
+      const int at[6] = {0, 3, 4, 6, 7, 8};  // packed rows -> row-major 3 x 3 positions
+      for (size_t i = 0; i < n; ++i) {
+        double* m = S_host + 9 * i;
+        for (int q = 0; q < 9; ++q) m[q] = 0.0;
+        for (int q = 0; q < 6; ++q) m[at[q]] = t[q * n + i];
+      }
+    }
+    return CUDAHM_OK;
+  }
   if (chi_host)
     CU(cudaMemcpyAsync(chi_host, h->chi, sizeof(double) * h->n * h->d, cudaMemcpyDeviceToHost, h->stream));
   if (S_host)
@@ -776,10 +817,11 @@ int cudahm_get_trace(cudahm_t h, double* delta, double* u, uint8_t* acc, double*
   return CUDAHM_OK;
 }
 
-// Checkpoint layout: header (8 x int64), ChainState, chi[n d], S[n d d].
+// Checkpoint layout: header (8 x int64), ChainState, then the latents and RAM factors as the
+// device holds them (d = 1: chi[n], S[n]; d = 3: chi[3][n], S[6][n]).
 int cudahm_checkpoint(cudahm_t h, void* buf, size_t cap, size_t* used) {
   if (!h || !used) return fail(CUDAHM_EINVAL, "NULL argument");
-  const size_t nchi = static_cast<size_t>(h->n) * h->d, nS = static_cast<size_t>(h->n) * h->d * h->d;
+  const size_t nchi = static_cast<size_t>(h->n) * h->d, nS = static_cast<size_t>(h->factor_n);
   const size_t need = 8 * sizeof(int64_t) + sizeof(ChainState) + sizeof(double) * (nchi + nS);
   *used = need;
   if (!buf) return CUDAHM_OK;
@@ -802,7 +844,7 @@ int cudahm_checkpoint(cudahm_t h, void* buf, size_t cap, size_t* used) {
 int cudahm_restore(cudahm_t h, const void* buf, size_t size) {
   if (!h || !buf) return fail(CUDAHM_EINVAL, "NULL argument");
   if (!h->data_set) return fail(CUDAHM_ESTATE, "restore needs set_data first");
-  const size_t nchi = static_cast<size_t>(h->n) * h->d, nS = static_cast<size_t>(h->n) * h->d * h->d;
+  const size_t nchi = static_cast<size_t>(h->n) * h->d, nS = static_cast<size_t>(h->factor_n);
   const size_t need = 8 * sizeof(int64_t) + sizeof(ChainState) + sizeof(double) * (nchi + nS);
   if (size < need) return fail(CUDAHM_EINVAL, "checkpoint buffer too small");
   int64_t hdr[8];
@@ -874,7 +916,8 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
     if (!h->data_set) return fail(CUDAHM_ESTATE, "handle %d has no data", q);
     if (h->cfg.device != h0->cfg.device) return fail(CUDAHM_EINVAL, "handles are on different devices");
     if (h->cfg.precision != h0->cfg.precision) return fail(CUDAHM_EINVAL, "handles mix precisions");
-    if (h->cfg.trace_sweeps > 0) return fail(CUDAHM_EUNSUPPORTED, "batched runs do not record traces");
+    if (h->cfg.trace_sweeps > 0 && k > 1)
+      return fail(CUDAHM_EUNSUPPORTED, "only a batch of one population records a trace");
     for (int r = 0; r < q; ++r)
       if (hs[r] == h) return fail(CUDAHM_EINVAL, "handle %d appears twice", q);
     if (h->sweeps + n_burn + n_iter >= (1ll << 32) - 2) return fail(CUDAHM_EINVAL, "sweep counter would overflow");
@@ -901,6 +944,7 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
                               reinterpret_cast<double*>(base + offsetof(ChainState, etabar))));
       h->etabar_valid = true;
     }
+    TRY(ensure_trace(h, std::min<long long>(h->cfg.trace_sweeps, total)));
     CU(cudaStreamSynchronize(h->stream));
   }
 
@@ -965,7 +1009,16 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
     a.err = bb.errs + q;
     a.rows = h->rows;
     a.thin = thin;
-    a.trace_T = 0;
+    a.trace_T = std::min<long long>(h->cfg.trace_sweeps, total);
+    a.tr_delta = h->tr_delta;
+    a.tr_u = h->tr_u;
+    a.tr_acc = h->tr_acc;
+    a.tr_thprop = h->tr_thprop;
+    a.tr_D = h->tr_D;
+    a.tr_logalpha = h->tr_logalpha;
+    a.tr_ut = h->tr_ut;
+    a.tr_tacc = h->tr_tacc;
+    a.tr_eb = h->tr_eb;
     a.skip_cta = -1;
     pops[q] = a;
     progs[q] = BatchProg{total, 0, n_burn, thin, 0, 0};
@@ -1135,7 +1188,7 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
     cudahm* h = hs[q];
     h->sweeps += total;
     h->rows_last = nrows;
-    h->trace_T_last = 0;
+    h->trace_T_last = std::min<long long>(h->cfg.trace_sweeps, total);
     h->last_run_ms = run_ms_total;
   }
   if (chosen) {

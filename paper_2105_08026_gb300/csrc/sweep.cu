@@ -622,18 +622,44 @@ __global__ void prepare_kernel(int model, long long n, const double* y_raw, cons
   if (!ok) atomicAdd(bad, 1);
 }
 
+// d = 3 model: member-major inputs y_raw[3 i + j], s = aux_raw[3 i + j] to per-component arrays
+// y[j n + i], aux[j n + i] = 1/s^2; default start chi_i = y_i and S_i = scale I (six packed rows).
+__global__ void prepare3_kernel(long long n, const double* y_raw, const double* aux_raw, double* y, double* aux,
+                                double* chi, double* S, double scale, int* bad, int set_default_chi) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  bool ok = true;
+  for (int j = 0; j < 3; ++j) {
+    const double yr = y_raw[3 * i + j], sr = aux_raw[3 * i + j];
+    const double w = 1.0 / (sr * sr);
+    ok = ok && isfinite(yr) && isfinite(sr) && sr > 0.0 && isfinite(w) && w > 0.0;
+    y[j * n + i] = yr;
+    aux[j * n + i] = w;
+    if (set_default_chi) chi[j * n + i] = yr;
+  }
+  if (set_default_chi)
+    for (int q = 0; q < 6; ++q) S[q * n + i] = (q == 0 || q == 2 || q == 5) ? scale : 0.0;
+  if (!ok) atomicAdd(bad, 1);
+}
+
 cudaError_t launch_prepare(int model, long long n, const double* y_raw, const double* aux_raw, double* y, double* aux,
                            double* chi, double* S, const ModelConsts& mc, const double* theta, int* bad,
                            int set_default_chi, cudaStream_t st) {
   const int blk = 256;
   const long long grid = (n + blk - 1) / blk;
+  if (model == CUDAHM_MVN3) {
+    prepare3_kernel<<<static_cast<unsigned int>(grid), blk, 0, st>>>(n, y_raw, aux_raw, y, aux, chi, S,
+                                                                      mc.chi_init_scale, bad, set_default_chi);
+    return cudaGetLastError();
+  }
   prepare_kernel<<<static_cast<unsigned int>(grid), blk, 0, st>>>(model, n, y_raw, aux_raw, y, aux, chi, S, mc,
                                                                   theta[0], theta[1], theta[2], bad,
                                                                   set_default_chi);
   return cudaGetLastError();
 }
 
-// Latents must lie in the support at theta (LF: chi > ln L_low) and be finite.
+// Latents must lie in the support at theta (LF: chi > ln L_low) and be finite (n values; the
+// d = 3 model passes all 3 N components).
 __global__ void check_chi_kernel(int model, long long n, const double* chi, double lnlow, int* bad) {
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -783,12 +809,44 @@ __global__ void eval_logdens_kernel(long long n, const double* y, const double* 
   out[i] = M::loglike(c, e, y[i], aux[i], mc) + M::logf(c, e, tc);
 }
 
+// d = 3 model: the same binary64 or binary32 expressions as its member step (per-component arrays).
+template <bool F32>
+__global__ void eval_logdens3_kernel(long long n, const double* y, const double* aux, const double* chi,
+                                     const double* theta, double* out) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double th[kMaxP];
+  for (int q = 0; q < 9; ++q) th[q] = theta[q];
+  const ThetaC3 tc = MVN3::consts(th);
+  if (F32) {
+    const ThetaC3f tf = MVN3::consts32(tc);
+    float x[3], d[MVN3::kData32];
+    for (int j = 0; j < 3; ++j) {
+      x[j] = static_cast<float>(chi[j * n + i]);
+      split_f(y[j * n + i], d[2 * j], d[2 * j + 1]);
+      d[6 + j] = static_cast<float>(0.5 * aux[j * n + i]);
+    }
+    out[i] = static_cast<double>(MVN3::loglike32(x, d)) + static_cast<double>(MVN3::logf32(x, tf));
+    return;
+  }
+  double x[3], yy[3], w[3];
+  for (int j = 0; j < 3; ++j) {
+    x[j] = chi[j * n + i];
+    yy[j] = y[j * n + i];
+    w[j] = aux[j * n + i];
+  }
+  out[i] = MVN3::loglike(x, yy, w) + MVN3::logf(x, tc);
+}
+
 cudaError_t launch_eval_logdens(int model, bool f32, long long n, const double* y, const double* aux,
                                 const double* chi, const double* theta_dev, const ModelConsts& mc, double* out,
                                 cudaStream_t st) {
   const int blk = 256;
   const unsigned int grid = static_cast<unsigned int>((n + blk - 1) / blk);
-  if (model == CUDAHM_NN1) {
+  if (model == CUDAHM_MVN3) {
+    if (f32) eval_logdens3_kernel<true><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, out);
+    else eval_logdens3_kernel<false><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, out);
+  } else if (model == CUDAHM_NN1) {
     if (f32) eval_logdens_kernel<NN1, true><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, out);
     else eval_logdens_kernel<NN1, false><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, out);
   } else if (model == CUDAHM_LF) {

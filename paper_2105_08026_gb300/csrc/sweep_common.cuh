@@ -43,6 +43,9 @@ __device__ __forceinline__ void sub2x(float chi, float hi, float lo, float& r_hi
 
 struct NN1 {
   // a0 = mu, a1 = 1/(2 tau^2)
+  using TC = ThetaC;
+  using TCf = ThetaCf;
+  static constexpr int kD = 1;
   static constexpr bool kExp = false;
   // binary32 forms of the member terms (FP32 bulk precision): loc = mu, scale = 1/(2 tau^2)
   __device__ static ThetaCf consts32(const ThetaC& c) {
@@ -94,6 +97,9 @@ struct NN1 {
 
 struct LF {
   // a0 = beta + 1, a1 = ln L*, a2 = 1/L*, a3 = ln L_low
+  using TC = ThetaC;
+  using TCf = ThetaCf;
+  static constexpr int kD = 1;
   static constexpr bool kExp = true;
   // binary32 forms: scale = beta + 1, loc = ln L*, low = ln L_low; log f = scale x - e^x, x = chi - ln L*
   __device__ static ThetaCf consts32(const ThetaC& c) {
@@ -158,6 +164,126 @@ struct LF {
     return -log(1.0 + th[0] * th[0]) + th[2];
   }
 };
+
+// d = 3 normal population (Sec. 3 with C_pop unknown). theta = (mu[3], L11, L21, L22, L31, L32,
+// L33) with L the lower Cholesky factor of C_pop, its diagonal entries stored as logs. The
+// per-theta constants hold mu and the packed inverse factor Li = L^-1 (lower, row-major:
+// li0 = Li00, li1 = Li10, li2 = Li11, li3 = Li20, li4 = Li21, li5 = Li22), so that
+// log f = -|Li (chi - mu)|^2 / 2 needs no division per member. Member data are stored per
+// component (structure of arrays): y_ij and aux_ij = 1/s_ij^2.
+struct ThetaC3 {
+  double mu[3];
+  double li[6];
+};
+// binary32 form: every constant as hi + lo, since each one is shared by all members and its
+// rounding would otherwise bias the sum over members
+struct ThetaC3f {
+  float mu_hi[3], mu_lo[3];
+  float li_hi[6], li_lo[6];
+};
+
+struct MVN3 {
+  using TC = ThetaC3;
+  using TCf = ThetaC3f;
+  static constexpr int kD = 3;
+  static constexpr bool kExp = false;
+  __device__ static ThetaC3 consts(const double* th) {
+    const double L00 = exp(th[3]), L10 = th[4], L11 = exp(th[5]), L20 = th[6], L21 = th[7], L22 = exp(th[8]);
+    ThetaC3 c;
+    c.mu[0] = th[0];
+    c.mu[1] = th[1];
+    c.mu[2] = th[2];
+    c.li[0] = 1.0 / L00;
+    c.li[2] = 1.0 / L11;
+    c.li[5] = 1.0 / L22;
+    c.li[1] = -(L10 * c.li[0]) * c.li[2];
+    c.li[4] = -(L21 * c.li[2]) * c.li[5];
+    c.li[3] = -(L20 * c.li[0] + L21 * c.li[1]) * c.li[5];
+    return c;
+  }
+  __device__ static double logf(const double* x, const ThetaC3& c) {
+    const double r0 = __dsub_rn(x[0], c.mu[0]), r1 = __dsub_rn(x[1], c.mu[1]), r2 = __dsub_rn(x[2], c.mu[2]);
+    const double z0 = __dmul_rn(c.li[0], r0);
+    const double z1 = __fma_rn(c.li[1], r0, __dmul_rn(c.li[2], r1));
+    const double z2 = __fma_rn(c.li[3], r0, __fma_rn(c.li[4], r1, __dmul_rn(c.li[5], r2)));
+    return __dmul_rn(-0.5, __fma_rn(z0, z0, __fma_rn(z1, z1, __dmul_rn(z2, z2))));
+  }
+  // y[j], w[j] = 1/s_j^2
+  __device__ static double loglike(const double* x, const double* y, const double* w) {
+    const double e0 = __dsub_rn(y[0], x[0]), e1 = __dsub_rn(y[1], x[1]), e2 = __dsub_rn(y[2], x[2]);
+    const double q = __fma_rn(__dmul_rn(w[0], e0), e0,
+                              __fma_rn(__dmul_rn(w[1], e1), e1, __dmul_rn(__dmul_rn(w[2], e2), e2)));
+    return __dmul_rn(-0.5, q);
+  }
+  __device__ static double cterm(const double* th) { return -((th[3] + th[5]) + th[8]); }
+  // flat in mu, in the off-diagonal entries and in the log-diagonal entries (improper)
+  __device__ static double logprior(const double*, const ModelConsts&) { return 0.0; }
+
+  __device__ static ThetaC3f consts32(const ThetaC3& c) {
+    ThetaC3f f;
+    for (int j = 0; j < 3; ++j) split_f(c.mu[j], f.mu_hi[j], f.mu_lo[j]);
+    for (int j = 0; j < 6; ++j) split_f(c.li[j], f.li_hi[j], f.li_lo[j]);
+    return f;
+  }
+  // -|Li (chi - mu)|^2/2 in binary32 with chi - mu and Li carried as hi + lo pairs: each z_j is
+  // the sum of the hi products plus the first-order cross terms, rounded once per fma.
+  __device__ static float logf32(const float* x, const ThetaC3f& c) {
+    float rh[3], rl[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) sub2x(x[j], c.mu_hi[j], c.mu_lo[j], rh[j], rl[j]);
+    const float* h = c.li_hi;
+    const float* l = c.li_lo;
+    const float e0 = __fmaf_rn(h[0], rl[0], __fmul_rn(l[0], rh[0]));
+    const float z0 = __fmaf_rn(h[0], rh[0], e0);
+    const float e1 = __fmaf_rn(h[1], rl[0], __fmaf_rn(l[1], rh[0], __fmaf_rn(h[2], rl[1], __fmul_rn(l[2], rh[1]))));
+    const float z1 = __fmaf_rn(h[1], rh[0], __fmaf_rn(h[2], rh[1], e1));
+    const float e2 = __fmaf_rn(h[3], rl[0], __fmaf_rn(l[3], rh[0], __fmaf_rn(h[4], rl[1],
+                     __fmaf_rn(l[4], rh[1], __fmaf_rn(h[5], rl[2], __fmul_rn(l[5], rh[2]))))));
+    const float z2 = __fmaf_rn(h[3], rh[0], __fmaf_rn(h[4], rh[1], __fmaf_rn(h[5], rh[2], e2)));
+    return __fmul_rn(-0.5f, __fmaf_rn(z0, z0, __fmaf_rn(z1, z1, __fmul_rn(z2, z2))));
+  }
+  // member data: d[2j], d[2j+1] = y_ij as hi + lo, d[6 + j] = 1/(2 s_ij^2)
+  static constexpr int kData32 = 9;
+  __device__ static float loglike32(const float* x, const float* d) {
+    const float e0 = __fadd_rn(__fsub_rn(d[0], x[0]), d[1]);
+    const float e1 = __fadd_rn(__fsub_rn(d[2], x[1]), d[3]);
+    const float e2 = __fadd_rn(__fsub_rn(d[4], x[2]), d[5]);
+    const float q = __fmaf_rn(__fmul_rn(d[6], e0), e0,
+                              __fmaf_rn(__fmul_rn(d[7], e1), e1, __fmul_rn(__fmul_rn(d[8], e2), e2)));
+    return -q;
+  }
+};
+
+// RAM factor update for d = 3 (Sec. 2.2): S' S'^T = S (I + c U U^T/|U|^2) S^T
+// = S S^T + sig w w^T with w = S U and sig = c/|U|^2, as a rank-one Cholesky modification
+// of the packed lower factor S = (S00, S10, S11, S20, S21, S22). Column k: with a = S_kk,
+// b = w_k and r = sqrt(a^2 + sig b^2), S'_kk = r, S'_ik = (a S_ik + sig b w_i)/r and the
+// vector carried to the next column is w_i' = (a w_i - b S_ik)/r (i > k). The diagonal
+// stays positive because 1 + c >= 1 - alpha_* > 0.
+__device__ __forceinline__ void ram3_update(double (&S)[6], double w0, double w1, double w2, double sig) {
+  {
+    const double a = S[0], b = w0, sb = sig * b;
+    const double t = fma(sb, b, a * a);
+    const double ir = rsqrt(t);
+    const double n1 = fma(a, S[1], sb * w1) * ir, v1 = fma(a, w1, -b * S[1]) * ir;
+    const double n3 = fma(a, S[3], sb * w2) * ir, v2 = fma(a, w2, -b * S[3]) * ir;
+    S[0] = t * ir;
+    S[1] = n1;
+    S[3] = n3;
+    w1 = v1;
+    w2 = v2;
+  }
+  {
+    const double a = S[2], b = w1, sb = sig * b;
+    const double t = fma(sb, b, a * a);
+    const double ir = rsqrt(t);
+    const double n4 = fma(a, S[4], sb * w2) * ir, v2 = fma(a, w2, -b * S[4]) * ir;
+    S[2] = t * ir;
+    S[4] = n4;
+    w2 = v2;
+  }
+  S[5] = sqrt(fma(sig * w2, w2, S[5] * S[5]));
+}
 
 // ----------------------------------------------------- theta RAM update -------
 // Lower-triangular L (p x p, row-major) with L' L'^T = L (I + c U U^T/|U|^2) L^T,
@@ -358,7 +484,7 @@ __device__ __forceinline__ void warp_reduce(Xacc& d, Xacc& e, unsigned int f[4])
 
 template <class M>
 __device__ __forceinline__ void propose_theta(const SweepArgs& a, long long s, int p, const double* theta, double* Sth,
-                                              double* thp, double& lpri_new, ThetaC& tcp) {
+                                              double* thp, double& lpri_new, typename M::TC& tcp) {
   for (int q = 0; q < p; ++q) {
     double t = theta[q];
     for (int b = 0; b <= q; ++b) t = fma(Sth[q * p + b], __ldg(a.tab_U + s * p + b), t);

@@ -189,6 +189,16 @@ def lf_settings(data: LFData, nL: int = 1024, nr: int = 1024, ln_upper: float = 
     return theta0, scale, consts
 
 
+def mvn3_settings(data: MVN3Data, scale: float = 0.005):
+    """theta_init, theta_prop_scale, consts for the d = 3 model: start from the sample mean
+    of y and the Cholesky factor of the sample covariance of y (which is C_pop plus the mean
+    measurement covariance, positive definite); the chain moves from there."""
+    ybar = data.y.mean(axis=0)
+    C = np.cov(data.y, rowvar=False) if data.y.shape[0] > 3 else np.eye(3)
+    theta0 = mvn3_theta_from(ybar, C)
+    return theta0, np.full(9, scale), np.zeros(1)
+
+
 def lf_chi_init(data: LFData, theta) -> np.ndarray:
     """Default start: chi_i = ln(4 pi r_i^2 max(Fhat_i, F_th)), raised to ln L_low + 1e-6."""
     chi = np.log(4.0 * math.pi * data.r * data.r * np.maximum(data.fhat, data.F_th))

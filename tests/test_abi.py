@@ -59,7 +59,7 @@ def test_config_defaults(lib):
     (lambda c: setattr(c, "target_accept", 1.5), cudahm.EINVAL),
     (lambda c: setattr(c, "adapt_exponent", 0.3), cudahm.EINVAL),
     (lambda c: setattr(c, "precision", 7), cudahm.EINVAL),
-    (lambda c: setattr(c, "model", cudahm.MVN3) or setattr(c, "d", 3), cudahm.EUNSUPPORTED),
+    (lambda c: setattr(c, "model", cudahm.MVN3), cudahm.EINVAL),  # d = 1 does not match MVN3
     (lambda c: c.theta_init.__setitem__(1, 50.0), cudahm.EINVAL),
 ])
 def test_invalid_configs_rejected(lib, mutate, code):
