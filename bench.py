@@ -43,14 +43,20 @@ N_OBJ = 300_000
 DATA_SEED = 1002
 CHAIN_SEED = 2
 L2_FLUSH_BYTES = 256 << 20
-# dram read+write bytes of one sweep-kernel launch (ncu, same profile); the member data are read
-# once per launch and the state stays in registers, so this does not grow with the sweeps.
-DRAM_BYTES_PER_LAUNCH = 9.80e6
+# dram read+write bytes of one sweep-kernel launch (ncu, profiles/sweep_kernel_lf_n300000.md): the
+# member data are read once per launch and the state stays in registers, so this does not grow
+# with the sweeps of the launch.
+DRAM_BYTES_PER_LAUNCH = 9.88e6
 
-# FP64 floating-point work of one sweep of this workload (2 per DFMA, 1 per DADD/DMUL),
-# from ncu's sass_thread_inst_executed_op_d{fma,add,mul} counters on the sweep kernel
-# (profiles/sweep_kernel_lf_n300000.md); None until measured.
-FP64_FLOP_PER_SWEEP = 9.74e7
+# FP64 floating-point work of one sweep of the LF workload (2 per DFMA, 1 per DADD/DMUL), from
+# ncu's smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on counters on the sweep kernel
+# (profiles/sweep_kernel_lf_n300000.md): 161.8 per object-update including the selection rule.
+FP64_FLOP_PER_SWEEP = 4.853e7
+
+# FP64 work and DRAM traffic of one member-update of the d = 3 workload in the FP32 bulk form
+# (profiles/batch_kernel_mvn3_n1000000_fp32.md).
+MVN3_F32_FP64_FLOP_PER_UPDATE = 98.9
+MVN3_F32_DRAM_BYTES_PER_UPDATE = 125.7
 
 
 def parse():
@@ -72,6 +78,8 @@ def parse():
     ap.add_argument("--serve-sweeps", type=int, default=5000)
     ap.add_argument("--serve-pool", type=int, default=48)
     ap.add_argument("--cpu-sweeps", type=int, default=8)
+    ap.add_argument("--no-mvn3", action="store_true")
+    ap.add_argument("--mvn3-sweeps", type=int, default=3000)
     return ap.parse_args()
 
 
@@ -222,6 +230,53 @@ def run_batched(args, cudahm, stream, device):
                                    "sweeps_per_launch": chosen.sweeps_per_launch,
                                    "graph": bool(chosen.use_graph), "blocks": chosen.reserved},
             "dtype": "f32 member terms, f64 sums/accept/RAM/selection integral (1024x1024 rule per LF population)"}
+
+
+def run_mvn3(args, cudahm, stream, device, flush, peak_fp64):
+    """d = 3 normal population: N = 1e6, mu = (0, 1, -1), C_pop = Q diag(1, sqrt 20, 20) Q^T,
+    s_ij ~ U[0.3, 1]; one run of --mvn3-sweeps sweeps (a third burn-in), inputs resident in HBM,
+    L2 flushed before it, device time by CUDA events on the sampler's stream. FP32 bulk form
+    and plain FP64, each from the same start."""
+    import torch
+    from paper_2105_08026_gb300 import synth
+    data = synth.mvn3_data(1_000_000, seed=1003)
+    theta0, scale, _ = synth.mvn3_settings(data)
+    n = data.y.shape[0]
+    y_dev = torch.from_numpy(np.ascontiguousarray(data.y)).cuda()
+    s_dev = torch.from_numpy(np.ascontiguousarray(data.s)).cuda()
+    K = args.mvn3_sweeps
+    out = {}
+    for name, prec in (("fp32", cudahm.FP32), ("fp64", cudahm.FP64)):
+        sm = cudahm.Sampler(cudahm.MVN3, n, theta_init=theta0, theta_prop_scale=scale, seed=3, precision=prec,
+                            device=device, stream=stream.cuda_stream, use_torch_allocator=True)
+        cudahm.cudahm_set_data_device(sm.h, y_dev.data_ptr(), s_dev.data_ptr(), n)
+        if args.warmup > 0:
+            sm.run(min(args.warmup, 100), 0)
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rows = sm.run(K // 3, K - K // 3, 1)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        assert rows.shape == (K - K // 3, 9)
+        st = sm.stats()
+        out[name] = {"value": n * K / (ms * 1e-3), "unit": "object-updates/s", "ms_per_step": ms / K,
+                     "member_accept": st.member_accepts / (n * (K + min(args.warmup, 100)))}
+        if prec == cudahm.FP32 and peak_fp64:
+            ach = MVN3_F32_FP64_FLOP_PER_UPDATE * n * K / (ms * 1e-3)
+            out[name]["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "achieved": ach / 1e12,
+                                     "peak": peak_fp64 / 1e12, "frac": ach / peak_fp64,
+                                     "peak_source": "FP64 DFMA stream measured live on this GPU (x2 flops)",
+                                     "hbm_GBps": MVN3_F32_DRAM_BYTES_PER_UPDATE * n * K / (ms * 1e-3) / 1e9,
+                                     "kernel": "batch_kernel<FP32> (MVN3 member step)"}
+        sm.close()
+    out.update({"n": n, "d": 3, "steps": K, "workload": "MVN3 d=3 normal population, N=1e6, cond(C_pop)=20",
+                "dtype": {"fp32": "f32 member terms, f64 v = S U, RAM factor, sums, theta step", "fp64": "f64"},
+                "l2": "256 MB flush before the run; state and data (~170 MB) exceed L2"})
+    return out
 
 
 def run_served(args, cudahm, device):
@@ -388,6 +443,11 @@ def run_cuda(args):
     if not args.no_serve and rank == 0:
         served = run_served(args, cudahm, local)
 
+    peak = fp64_peak(local) if rank == 0 else None
+    mvn3 = None
+    if not args.no_mvn3 and rank == 0:
+        mvn3 = run_mvn3(args, cudahm, stream, local, flush, peak)
+
     # e2e through the public API with host buffers (every iteration: H2D data, run, D2H samples)
     e2e = None
     if not args.no_e2e:
@@ -423,7 +483,6 @@ def run_cuda(args):
         return 0
 
     st = s.stats()
-    peak = fp64_peak(local)
     sweep_launch_ms = kernel_ms / max(1, launches // 2)
     sweeps_per_launch = K / max(1, launches // 2)
     roofline = {"bound": "alu", "unit": "TFLOP/s", "peak": peak / 1e12 if peak else None,
@@ -447,7 +506,7 @@ def run_cuda(args):
                        "member state register-resident within a launch", "timed_launches": R,
                        "launch_shape": [st.grid_blocks, st.block_threads, st.objects_per_thread]},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
-            "fp32_bulk": fp32, "batched_fp32": batched, "served_fp32": served}
+            "fp32_bulk": fp32, "batched_fp32": batched, "served_fp32": served, "mvn3": mvn3}
     print(json.dumps(line), flush=True)
     s.close()
     if ws > 1:
