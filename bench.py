@@ -90,9 +90,30 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_seeds(rank: int):
+    """(data seed, chain seed) of rank's replica: every rank samples its own catalog."""
+    return DATA_SEED + rank, CHAIN_SEED + rank
+
+
+def max_over_ranks(x: float, device: str = "cuda") -> float:
+    """Largest x over the ranks of the default process group (x itself without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world_size: int, units_per_rank: float, t_max_ms: float) -> float:
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest rank's time."""
+    return world_size * units_per_rank / (t_max_ms * 1e-3)
+
+
 def workload(rank):
     from paper_2105_08026_gb300 import synth
-    data = synth.lf_data(N_OBJ, seed=DATA_SEED + rank)
+    data = synth.lf_data(N_OBJ, seed=replica_seeds(rank)[0])
     theta0, scale, consts = synth.lf_settings(data)
     return data, theta0, scale, consts
 
@@ -357,8 +378,9 @@ def run_cuda(args):
     data, theta0, scale, consts = workload(rank)
     n = data.fhat.size
     stream = torch.cuda.current_stream()
+    chain_seed = replica_seeds(rank)[1]
     s = cudahm.Sampler(cudahm.LF, n, theta_init=theta0, theta_prop_scale=scale, model_consts=consts,
-                       seed=CHAIN_SEED + rank, device=local, stream=stream.cuda_stream, use_torch_allocator=True)
+                       seed=chain_seed, device=local, stream=stream.cuda_stream, use_torch_allocator=True)
     # inputs resident in HBM before timing (device-to-device set_data from torch tensors)
     y_dev = torch.from_numpy(data.fhat).cuda()
     r_dev = torch.from_numpy(data.r).cuda()
@@ -399,18 +421,14 @@ def run_cuda(args):
         torch.distributed.barrier()
     clk = clocks.stop()
     assert rows_total == K
-    t_max_ms = total_ms
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max_ms = float(t.item())
-    value = ws * n * K / (t_max_ms * 1e-3)
+    t_max_ms = max_over_ranks(total_ms)
+    value = replica_value(ws, n * K, t_max_ms)
 
     # the same workload in the FP32 bulk form (binary32 member terms, binary64 sums/accept/RAM/etabar)
     fp32 = None
     if not args.no_fp32:
         s3 = cudahm.Sampler(cudahm.LF, n, theta_init=theta0, theta_prop_scale=scale, model_consts=consts,
-                            seed=CHAIN_SEED + rank, device=local, stream=stream.cuda_stream,
+                            seed=chain_seed, device=local, stream=stream.cuda_stream,
                             use_torch_allocator=True, precision=cudahm.FP32)
         cudahm.cudahm_set_data_device(s3.h, y_dev.data_ptr(), r_dev.data_ptr(), n)
         if args.warmup > 0:
@@ -426,11 +444,8 @@ def run_cuda(args):
             e1.record(stream)
             e1.synchronize()
             f_ms += e0.elapsed_time(e1)
-        if ws > 1:
-            t = torch.tensor([f_ms], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            f_ms = float(t.item())
-        fp32 = {"value": ws * n * K / (f_ms * 1e-3), "unit": "object-updates/s", "ms_per_step": f_ms / K,
+        f_ms = max_over_ranks(f_ms)
+        fp32 = {"value": replica_value(ws, n * K, f_ms), "unit": "object-updates/s", "ms_per_step": f_ms / K,
                 "dtype": "f32 member terms, f64 sums/accept/RAM/selection integral"}
         s3.close()
 
@@ -453,7 +468,7 @@ def run_cuda(args):
     if not args.no_e2e:
         ke = max(1, K // R)
         s2 = cudahm.Sampler(cudahm.LF, n, theta_init=theta0, theta_prop_scale=scale, model_consts=consts,
-                            seed=CHAIN_SEED + rank, device=local, stream=stream.cuda_stream,
+                            seed=chain_seed, device=local, stream=stream.cuda_stream,
                             use_torch_allocator=True)
         host_y = np.ascontiguousarray(data.fhat)
         host_r = np.ascontiguousarray(data.r)
@@ -467,11 +482,7 @@ def run_cuda(args):
             assert out.shape == (ke, 3)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        e2e_val = n * ke * R / wall
-        if ws > 1:
-            t = torch.tensor([wall], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_val = ws * n * ke * R / float(t.item())
+        e2e_val = replica_value(ws, n * ke * R, max_over_ranks(wall * 1e3))
         e2e = {"value": e2e_val, "unit": "object-updates/s", "h2d_bytes_per_step": 2 * n * 8 / ke,
                "d2h_bytes_per_step": 3 * 8 + 4 / ke}
         s2.close()
