@@ -80,18 +80,21 @@ __device__ __forceinline__ void member_f64(const SweepArgs& a, unsigned int i, u
   const uint4 w1 = philox4x32_10(make_uint4(1u, 0u, i, k), a.key0, a.key1);
   const double u = uniform53(w1.x, w1.y);
   const double Y = fma(S, z, chi);
-  double delta, eY = 0.0, llY = 0.0;
+  double delta, eY = 0.0, llY = 0.0, lfY = 0.0;
+  const double lfX = M::logf(chi, echi, tc);
   if (!M::support(Y, tc)) {
     delta = -INFINITY;
   } else {
     eY = M::kExp ? exp_tab(Y, s_math) : 0.0;
     llY = M::loglike(Y, eY, yv, av, a.mc);
-    delta = (llY + M::logf(Y, eY, tc)) - (ll + M::logf(chi, echi, tc));
+    lfY = M::logf(Y, eY, tc);
+    delta = (llY + lfY) - (ll + lfX);
   }
   const bool dneg = dsign(delta);
   const double alpha = dneg ? exp_tab(delta, s_math) : 1.0;
   const bool acc = !dneg || (__double_as_longlong(u) < __double_as_longlong(alpha));
   if (disnan(delta)) nan_cnt++;
+  const double lf_cur = acc ? lfY : lfX;
   if (acc) {
     chi = Y;
     echi = eY;
@@ -106,7 +109,7 @@ __device__ __forceinline__ void member_f64(const SweepArgs& a, unsigned int i, u
     a.tr_acc[tro + i] = acc ? 1 : 0;
   }
   if (prior_ok) {
-    const double dn = M::support(chi, tcp) ? M::logf(chi, echi, tcp) - M::logf(chi, echi, tc) : -INFINITY;
+    const double dn = M::support(chi, tcp) ? M::logf(chi, echi, tcp) - lf_cur : -INFINITY;
     if (disnan(dn)) fd.nan++;
     else if (dhuge(dn)) {
       if (dsign(dn)) neg_big++;
@@ -139,15 +142,18 @@ __device__ __forceinline__ void member_f32(const SweepArgs& a, unsigned int i, u
   sincospif(2.0f * u2, &sn, &cs);
   const float z = odd ? rad * cs : rad * sn;
   const float Y = fmaf(static_cast<float>(S), z, chi);
-  float delta;
+  float delta, lfY = 0.0f;
+  const float lfX = M::logf32(chi, tf);
   if (!M::support32(Y, tf)) {
     delta = -INFINITY;
   } else {
-    delta = (M::loglike32(Y, d) + M::logf32(Y, tf)) - (ll + M::logf32(chi, tf));
+    lfY = M::logf32(Y, tf);
+    delta = (M::loglike32(Y, d) + lfY) - (ll + lfX);
   }
   const float alpha = (delta >= 0.0f) ? 1.0f : expf(delta);
   const bool acc = (delta >= 0.0f) || (u < alpha);
   if (delta != delta) nan_cnt++;
+  const float lf_cur = acc ? lfY : lfX;
   if (acc) {
     chi = Y;
     acc_cnt++;
@@ -161,7 +167,7 @@ __device__ __forceinline__ void member_f32(const SweepArgs& a, unsigned int i, u
     a.tr_acc[tro + i] = acc ? 1 : 0;
   }
   if (prior_ok) {
-    const float dn = M::support32(chi, tpf) ? M::logf32(chi, tpf) - M::logf32(chi, tf) : -INFINITY;
+    const float dn = M::support32(chi, tpf) ? M::logf32(chi, tpf) - lf_cur : -INFINITY;
     if (dn != dn) fd.nan++;
     else if (fabsf(dn) >= 0x1p94f) {
       if (dn < 0.0f) neg_big++;
@@ -345,6 +351,7 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
   for (int q = tid; q < kMathWords; q += blockDim.x) s_math[q] = a.math_tab[q];
   if (is_lf)
     for (int q = tid; q < kPhiWords; q += blockDim.x) s_phi[q] = a.phi_coef[q];
+  __syncthreads();  // tables in place before thread 0 uses them
   if (tid == 0) {
     s_k0 = a.chain->sweeps;
     s_off = prog->off;
@@ -353,7 +360,7 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
     for (int q = 0; q < p; ++q) s_theta[q] = a.chain->theta[q];
     for (int q = 0; q < p * p; ++q) s_Sth[q] = a.chain->S_theta[q];
     s_etabar = a.chain->etabar;
-    s_logeb = is_lf ? log(s_etabar) : 0.0;
+    s_logeb = is_lf ? log_etabar(s_etabar, s_math) : 0.0;
     s_tc = M::consts(s_theta);
     s_tcf = M::consts32(s_tc);
     s_lpri = M::logprior(s_theta, a.mc);
@@ -462,30 +469,11 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
     }
     if (!pop_barrier(a.bar, static_cast<unsigned int>(s), static_cast<unsigned int>(nb), a.err, a.timeout_ns))
       return;
-    if (wid == 0) {
+    {
       Xacc D, E;
-      xacc_zero(D);
-      xacc_zero(E);
-      unsigned int f[4] = {0u, 0u, 0u, 0u};
-      for (int b = lane; b < nb; b += 32) {
-        const unsigned long long* src = a.partials + ((s & 1) * gridDim.x + b0 + b) * kPartWords;
-        Xacc t;
-        t.w0 = __ldcg(src + 0);
-        t.w1 = __ldcg(src + 1);
-        t.w2 = __ldcg(src + 2);
-        xacc_add(D, t);
-        t.w0 = __ldcg(src + 3);
-        t.w1 = __ldcg(src + 4);
-        t.w2 = __ldcg(src + 5);
-        xacc_add(E, t);
-        const unsigned long long f01 = __ldcg(src + 6), f23 = __ldcg(src + 7);
-        f[0] += static_cast<unsigned int>(f01);
-        f[1] += static_cast<unsigned int>(f01 >> 32);
-        f[2] += static_cast<unsigned int>(f23);
-        f[3] += static_cast<unsigned int>(f23 >> 32);
-      }
-      warp_reduce(D, E, f);
-      if (lane == 0) {
+      unsigned int f[4];
+      sum_partials(a.partials + ((s & 1) * gridDim.x + b0) * kPartWords, nb, s_red, D, E, f);
+      if (tid == 0) {
         if (f[1] != 0u) {
           atomicCAS(a.err, 0, CUDAHM_ENUMERIC);
           s_stop = 1;
@@ -506,7 +494,7 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
             logalpha = Drec + nn * (M::cterm(s_thp) - M::cterm(s_theta)) + s_lpri_new - s_lpri;
             if (is_lf) {
               eb_new = xacc_to_double(E);
-              logeb_new = log(eb_new);
+              logeb_new = log_etabar(eb_new, s_math);
               logalpha -= nn * (logeb_new - s_logeb);
             }
           }

@@ -175,10 +175,12 @@ __device__ __forceinline__ double xacc_to_double(Xacc a) {
   const unsigned long long guard = (top >> 10) & 1ull;
   const unsigned long long sticky = ((top & 0x3FFull) != 0ull) | (rest_nonzero != 0ull);
   if (guard && (sticky || (mant & 1ull))) mant += 1ull;
-  int exp2 = hb - 96 - 52;  // value = mant * 2^exp2
+  int exp2 = hb - 96 - 52;  // value = mant * 2^exp2, mant in [2^52, 2^53)
   if (mant >> 53) { mant >>= 1; exp2 += 1; }
-  const double r = scalbn(static_cast<double>(mant), exp2);
-  return neg ? -r : r;
+  // assembled from its fields: exp2 lies in [-148, 44], so the value is a normal binary64
+  const unsigned long long bits = (static_cast<unsigned long long>(exp2 + 1075) << 52) |
+                                  (mant & 0x000FFFFFFFFFFFFFull) | (neg ? 0x8000000000000000ull : 0ull);
+  return __longlong_as_double(static_cast<long long>(bits));
 }
 
 __device__ __forceinline__ Xacc xacc_shfl_xor(const Xacc& a, int lane_mask) {

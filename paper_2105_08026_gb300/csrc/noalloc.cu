@@ -26,7 +26,7 @@ namespace {
 
 constexpr int kNoallocMaxNodes = CUDAHM_NOALLOC_MAX_NODES;
 constexpr int kNoallocMaxGrid = 1024;
-constexpr int kPhiWordsMax = 133 * 11;  // normal-CDF Taylor table
+constexpr int kPhiWordsMax = 265 * 9;  // normal-CDF Taylor table
 // layout in doubles: xL, wL, xr, wr, qs, Wr (max nodes each), the Phi table, the prefix sums
 // of the inner weights (max nodes + 1), then the per-block partials (4 x u64 per block)
 constexpr size_t kScratchDoubles = 6 * static_cast<size_t>(kNoallocMaxNodes) + kPhiWordsMax +

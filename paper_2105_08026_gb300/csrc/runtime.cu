@@ -961,13 +961,11 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
   const bool use_graph = !tune || tune->use_graph != 0 || (tune->block_threads == 0 && tune->sweeps_per_launch == 0);
   if (block && block != 128 && block != 256) return fail(CUDAHM_EINVAL, "block_threads must be 128 or 256");
   if (chunk < 0 || chunk > kChunk) return fail(CUDAHM_EINVAL, "sweeps_per_launch must be in [1, %lld]", kChunk);
-  bool tuned_before = false;
   if (!block || !chunk) {
     for (const TuneEntry& e : g_tune_cache)
       if (e.key == key) {
         if (!block) block = e.block;
         if (!chunk) chunk = e.chunk;
-        tuned_before = true;
       }
   }
   // sweeps per launch: enough launches to rebalance a few times, long enough to amortise a launch
@@ -1174,7 +1172,6 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
     }
   }
   cleanup_events();
-  (void)tuned_before;
   if (rc != CUDAHM_OK) {
     for (int q = 0; q < k; ++q) {
       ChainState cs;

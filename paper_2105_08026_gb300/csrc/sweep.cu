@@ -24,16 +24,15 @@ namespace chm {
 __global__ void phi_table_kernel(double* coef) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kPhiN) return;
-  const double c = -8.0 + 0.125 * i;
-  const bool upper = (i > 64);
+  const double c = -8.0 + 0.0625 * i;
   const double dens = exp(-0.5 * (c * c)) * 0.39894228040143267794;  // phi(c)
-  coef[i] = upper ? 0.5 * erfc(c * 0.70710678118654752440) : 0.5 * erfc(-c * 0.70710678118654752440);
+  coef[i] = (c > 0.0) ? 1.0 - 0.5 * erfc(c * 0.70710678118654752440) : 0.5 * erfc(-c * 0.70710678118654752440);
   double hm1 = 0.0, h = 1.0;  // He_(n-2), He_(n-1) at c
-  double fact = 1.0;
+  double fact = 1.0, scale = 1.0;
   for (int n = 1; n <= kPhiDeg; ++n) {
     fact *= n;
-    double an = ((n - 1) & 1 ? -h : h) * dens / fact;  // (-1)^(n-1) He_(n-1)(c) phi(c)/n!
-    coef[n * kPhiN + i] = upper ? -an : an;
+    scale *= 0.0625;  // 16^-n, exact
+    coef[n * kPhiN + i] = ((n - 1) & 1 ? -h : h) * dens / fact * scale;  // (-1)^(n-1) He_(n-1)(c) phi(c)/(n! 16^n)
     const double hn = c * h - (n - 1) * hm1;  // He_n = c He_(n-1) - (n-1) He_(n-2)
     hm1 = h;
     h = hn;
@@ -114,7 +113,11 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   double* s_y = s_phi + (is_lf ? kPhiWords : 0);
   double* s_aux = s_y + a.mpb;
   double* s_zs = s_y + 2 * a.mpb;  // spare (sine) normal of each member's Box-Muller pair
-  double* s_rows = s_y + 3 * a.mpb;
+  // log f(chi_i;theta) of each member after its step (binary32 in the FP32 form), reused by the
+  // theta' partial
+  double* s_lf = s_y + 3 * a.mpb;
+  float* s_lf32 = reinterpret_cast<float*>(s_lf);
+  double* s_rows = s_y + 4 * a.mpb;
   if (!F32) {
     for (unsigned int q = tid; q < nb1 - nb0; q += blockDim.x) {
       s_y[q] = a.y[nb0 + q];
@@ -126,12 +129,13 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   for (int q = tid; q < kMathWords; q += blockDim.x) s_math[q] = a.math_tab[q];
   const int nseg = is_lf ? lf_block_segments(a, blockIdx.x, gridDim.x) : 0;
   const SegTab tab = segtab_carve(s_rows, a.rows_smem);
+  __syncthreads();  // tables in place before thread 0 uses them
 
   if (tid == 0) {
     for (int q = 0; q < p; ++q) s_theta[q] = a.chain->theta[q];
     for (int q = 0; q < p * p; ++q) s_Sth[q] = a.chain->S_theta[q];
     s_etabar = a.chain->etabar;
-    s_logeb = is_lf ? log(s_etabar) : 0.0;
+    s_logeb = is_lf ? log_etabar(s_etabar, s_math) : 0.0;
     s_tc = M::consts(s_theta);
     s_lpri = M::logprior(s_theta, a.mc);
     s_rows_written = 0;
@@ -244,12 +248,14 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
           sincospif(2.0f * u2, &sn, &cs);
           const float z = oddf ? rad * cs : rad * sn;
           const float Y = fmaf(static_cast<float>(S[m]), z, chi[m]);
-          float delta, llY = 0.0f;
+          float delta, llY = 0.0f, lfY = 0.0f;
+          const float lfX = M::logf32(chi[m], tf);
           if (!M::support32(Y, tf)) {
             delta = -INFINITY;
           } else {
             llY = M::loglike32(Y, d);
-            delta = (llY + M::logf32(Y, tf)) - (ll[m] + M::logf32(chi[m], tf));
+            lfY = M::logf32(Y, tf);
+            delta = (llY + lfY) - (ll[m] + lfX);
           }
           const float alpha = (delta >= 0.0f) ? 1.0f : expf(delta);
           const bool acc = (delta >= 0.0f) || (u < alpha);
@@ -259,6 +265,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
             ll[m] = llY;
             member_acc++;
           }
+          s_lf32[i - nb0] = acc ? lfY : lfX;
           S[m] *= sqrt(fma(eta, static_cast<double>(alpha) - a.astar, 1.0));
           if (trace) {
             const long long o = (a.trace_off + s) * a.n + static_cast<long long>(i);
@@ -294,15 +301,15 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
           const uint4 w1 = philox4x32_10(make_uint4(1u, 0u, static_cast<uint32_t>(i), k), a.key0, a.key1);
           const double u = uniform53(w1.x, w1.y);
           const double Y = fma(S[m], z, chi[m]);
-          double delta, eY = 0.0, llY = 0.0;
+          double delta, eY = 0.0, llY = 0.0, lfY = 0.0;
+          const double lfX = M::logf(chi[m], echi[m], tc);
           if (!M::support(Y, tc)) {
             delta = -INFINITY;
           } else {
             eY = M::kExp ? exp_tab(Y, s_math) : 0.0;
             llY = M::loglike(Y, eY, yv, av, a.mc);
-            const double lpY = llY + M::logf(Y, eY, tc);
-            const double lpX = ll[m] + M::logf(chi[m], echi[m], tc);
-            delta = lpY - lpX;
+            lfY = M::logf(Y, eY, tc);
+            delta = (llY + lfY) - (ll[m] + lfX);
           }
           const bool dneg = dsign(delta);  // -inf and -0 included; NaN is counted below
           const double alpha = dneg ? exp_tab(delta, s_math) : 1.0;
@@ -314,6 +321,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
             ll[m] = llY;
             member_acc++;
           }
+          s_lf[i - nb0] = acc ? lfY : lfX;
           S[m] *= sqrt(fma(eta, alpha - a.astar, 1.0));
           if (trace) {
             const long long o = (a.trace_off + s) * a.n + static_cast<long long>(i);
@@ -335,13 +343,13 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     XFlags fd = {0u, 0u, 0u}, fe = {0u, 0u, 0u};
     unsigned int neg_big = 0, pos_big = 0;
     if (prior_ok && F32) {
-      const ThetaCf tf = s_tcf, tpf = s_tcpf;
+      const ThetaCf tpf = s_tcpf;
 #pragma unroll
       for (int m = 0; m < K; ++m) {
         const unsigned int i = nb0 + tid + m * blockDim.x;
         if (i < nb1) {
           const float c = static_cast<float>(chi[m]);
-          const float dn = M::support32(c, tpf) ? M::logf32(c, tpf) - M::logf32(c, tf) : -INFINITY;
+          const float dn = M::support32(c, tpf) ? M::logf32(c, tpf) - s_lf32[i - nb0] : -INFINITY;
           if (dn != dn) fd.nan++;
           else if (fabsf(dn) >= 0x1p94f) {
             if (dn < 0.0f) neg_big++;
@@ -359,7 +367,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         if (i < nb1) {
           const double dn = M::support(static_cast<double>(chi[m]), tcp)
                                 ? M::logf(static_cast<double>(chi[m]), static_cast<double>(echi[m]), tcp) -
-                                      M::logf(static_cast<double>(chi[m]), static_cast<double>(echi[m]), tc)
+                                      s_lf[i - nb0]
                                 : -INFINITY;
           if (disnan(dn)) fd.nan++;
           else if (dhuge(dn)) {
@@ -412,30 +420,11 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     if (!grid_barrier(a.bar, static_cast<unsigned int>(s), a.err, a.timeout_ns, skip_me)) return;
 
     // a7: every block sums all partials and takes the same decision
-    if (wid == 0) {
+    {
       Xacc D, E;
-      xacc_zero(D);
-      xacc_zero(E);
-      unsigned int f[4] = {0u, 0u, 0u, 0u};
-      for (int b = lane; b < static_cast<int>(gridDim.x); b += 32) {
-        const unsigned long long* src = a.partials + ((s & 1) * gridDim.x + b) * kPartWords;
-        Xacc t;
-        t.w0 = __ldcg(src + 0);
-        t.w1 = __ldcg(src + 1);
-        t.w2 = __ldcg(src + 2);
-        xacc_add(D, t);
-        t.w0 = __ldcg(src + 3);
-        t.w1 = __ldcg(src + 4);
-        t.w2 = __ldcg(src + 5);
-        xacc_add(E, t);
-        const unsigned long long f01 = __ldcg(src + 6), f23 = __ldcg(src + 7);
-        f[0] += static_cast<unsigned int>(f01);
-        f[1] += static_cast<unsigned int>(f01 >> 32);
-        f[2] += static_cast<unsigned int>(f23);
-        f[3] += static_cast<unsigned int>(f23 >> 32);
-      }
-      warp_reduce(D, E, f);
-      if (lane == 0) {
+      unsigned int f[4];
+      sum_partials(a.partials + (s & 1) * gridDim.x * kPartWords, static_cast<int>(gridDim.x), s_red, D, E, f);
+      if (tid == 0) {
         const long long sg = a.trace_off + s;  // sweep index within this run
         if (f[1] != 0u) {
           atomicCAS(a.err, 0, CUDAHM_ENUMERIC);
@@ -457,7 +446,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
             logalpha = Drec + nn * (M::cterm(s_thp) - M::cterm(s_theta)) + s_lpri_new - s_lpri;
             if (is_lf) {
               eb_new = xacc_to_double(E);
-              logeb_new = log(eb_new);
+              logeb_new = log_etabar(eb_new, s_math);
               logalpha -= nn * (logeb_new - s_logeb);
             }
           }
@@ -548,7 +537,7 @@ static const void* kernel_for(int K, bool f32) {
 
 size_t sweep_smem_bytes(int model, int mpb, int rows_smem) {
   return sizeof(double) * kMathWords + (model == CUDAHM_LF ? sizeof(double) * kPhiWords : 0) +
-         3 * sizeof(double) * static_cast<size_t>(mpb) + segtab_bytes(rows_smem);
+         4 * sizeof(double) * static_cast<size_t>(mpb) + segtab_bytes(rows_smem);
 }
 
 cudaError_t launch_math_table(double* t, cudaStream_t st) {
@@ -818,7 +807,7 @@ __global__ void eval_logdens3_kernel(long long n, const double* y, const double*
   double th[kMaxP];
   for (int q = 0; q < 9; ++q) th[q] = theta[q];
   const ThetaC3 tc = MVN3::consts(th);
-  if (F32) {
+  if constexpr (F32) {
     const ThetaC3f tf = MVN3::consts32(tc);
     float x[3], d[MVN3::kData32];
     for (int j = 0; j < 3; ++j) {
@@ -827,15 +816,15 @@ __global__ void eval_logdens3_kernel(long long n, const double* y, const double*
       d[6 + j] = static_cast<float>(0.5 * aux[j * n + i]);
     }
     out[i] = static_cast<double>(MVN3::loglike32(x, d)) + static_cast<double>(MVN3::logf32(x, tf));
-    return;
+  } else {
+    double x[3], yy[3], w[3];
+    for (int j = 0; j < 3; ++j) {
+      x[j] = chi[j * n + i];
+      yy[j] = y[j * n + i];
+      w[j] = aux[j * n + i];
+    }
+    out[i] = MVN3::loglike(x, yy, w) + MVN3::logf(x, tc);
   }
-  double x[3], yy[3], w[3];
-  for (int j = 0; j < 3; ++j) {
-    x[j] = chi[j * n + i];
-    yy[j] = y[j * n + i];
-    w[j] = aux[j * n + i];
-  }
-  out[i] = MVN3::loglike(x, yy, w) + MVN3::logf(x, tc);
 }
 
 cudaError_t launch_eval_logdens(int model, bool f32, long long n, const double* y, const double* aux,

@@ -316,33 +316,38 @@ __device__ inline void ram_update_theta(int p, double* L, const double* U, doubl
 }
 
 // ------------------------------------------------------- normal CDF Phi -------
-// Phi(x) = erfc(-x/sqrt 2)/2 (Sec. 5.2, eq. key) by a table of local Taylor polynomials:
-// intervals centred at c_i = -8 + i/8 (i = 0..kPhiN-1), |x - c_i| <= 1/16, degree kPhiDeg.
-// With phi = Phi' and d^n Phi/dx^n = (-1)^(n-1) He_(n-1)(x) phi(x) (He = probabilists'
-// Hermite polynomials), the coefficients are a_0 = Phi(c), a_n = (-1)^(n-1) He_(n-1)(c) phi(c)/n!.
-// For c > 0 the table holds the upper tail Q = 1 - Phi (a_0 = erfc(c/sqrt 2)/2, a_n negated)
-// and Phi = 1 - Q, so that values near 1 keep full absolute accuracy. The remainder of the
-// degree-10 series on |t| <= 1/16 is below 1e-18; the table is built once per handle on the
-// device from CUDA's erfc and exp. Above x = 8.5, Phi rounds to 1 exactly; below x = -8
-// (Phi < 7e-16) erfc is called directly.
-constexpr int kPhiN = 133;
-constexpr int kPhiDeg = 10;
+// Phi(x) = erfc(-x/sqrt 2)/2 (Sec. 5.2, eq. key) by a table of local Taylor polynomials in the
+// scaled variable v = 16 x: intervals centred at c_i = -8 + i/16 (i = 0..kPhiN-1, so v_i = 16 c_i
+// is the integer i - 128), |x - c_i| <= 1/32, degree kPhiDeg = 8. With phi = Phi' and
+// d^n Phi/dx^n = (-1)^(n-1) He_(n-1)(x) phi(x) (He = probabilists' Hermite polynomials), the
+// Taylor coefficients are a_0 = Phi(c), a_n = (-1)^(n-1) He_(n-1)(c) phi(c)/n!; the table holds
+// b_n = a_n/16^n, the coefficients of the series in u = v - v_i = 16 (x - c_i), |u| <= 1/2.
+// a_0 is Phi(c) itself, taken as 1 - erfc(c/sqrt 2)/2 for c > 0, so values near 1 carry an
+// absolute error of an ulp of 1. The remainder of the degree-8 series on |x - c| <= 1/32 is
+// below 4e-18 (|He_8 phi| <= 42); the table is built once per handle on the device from CUDA's
+// erfc and exp. Above x = 8.5 (v = 136), Phi rounds to 1 exactly; below x = -8 (Phi < 7e-16)
+// erfc is called directly.
+constexpr int kPhiN = 265;
+constexpr int kPhiDeg = 8;
 constexpr int kPhiWords = kPhiN * (kPhiDeg + 1);  // coefficient-major: coef[n * kPhiN + i]
 
-__device__ __forceinline__ double phi_table(double x, const double* __restrict__ coef) {
-  const long long b = __double_as_longlong(x);
-  if (b > 0x4021000000000000ll) return 1.0;  // x > 8.5 (and +inf)
-  if (static_cast<unsigned long long>(b) > 0xC020000000000000ull)  // x < -8 (and -inf)
-    return 0.5 * erfc(-x * 0.70710678118654752440);
-  const double magic = 6755399441055744.0;        // 1.5 * 2^52
-  const double r = fma(x, 8.0, 64.0 + magic);     // round(8x + 64) sits in the low mantissa bits
-  const int i = __double2loint(r);
-  const double c = fma(r - magic, 0.125, -8.0);   // centre, exact
-  const double t = x - c;                         // exact (|t| <= 1/16, c a multiple of 1/8)
+// Phi(v/16): four FP64 operations to reach u, eight for the polynomial.
+__device__ __forceinline__ double phi_table16(double v, const double* __restrict__ coef) {
+  const long long b = __double_as_longlong(v);
+  if (b > 0x4061000000000000ll) return 1.0;  // v > 136 (and +inf)
+  if (static_cast<unsigned long long>(b) > 0xC060000000000000ull)  // v < -128 (and -inf)
+    return 0.5 * erfc(-(v * 0.0625) * 0.70710678118654752440);
+  const double magic = 6755399441055744.0;  // 1.5 * 2^52
+  const double r = v + magic;               // round(v) sits in the low mantissa bits
+  const int i = __double2loint(r) + 128;
+  const double u = v - (r - magic);         // exact, |u| <= 1/2
   double q = coef[kPhiDeg * kPhiN + i];
 #pragma unroll
-  for (int n = kPhiDeg - 1; n >= 0; --n) q = fma(q, t, coef[n * kPhiN + i]);
-  return (i <= 64) ? q : 1.0 - q;
+  for (int n = kPhiDeg - 1; n >= 0; --n) q = fma(q, u, coef[n * kPhiN + i]);
+  return q;
+}
+__device__ __forceinline__ double phi_table(double x, const double* __restrict__ coef) {
+  return phi_table16(16.0 * x, coef);
 }
 
 // ------------------------------------------------------------ LF rule --------
@@ -359,7 +364,7 @@ __device__ __forceinline__ int lf_block_segments(const SweepArgs& a, int b, int 
   return (b < G) ? (G - b + B - 1) / B : 0;
 }
 
-// Per-block segment table in shared memory, R slots: L_j, G_j, the row's prefix term, the
+// Per-block segment table in shared memory, R slots: 16 L_j, G_j, the row's prefix term, the
 // first active inner node kb and the exclusive offsets of the active pair counts (R + 1).
 struct SegTab {
   double* L;
@@ -386,7 +391,8 @@ __device__ __forceinline__ SegTab segtab_carve(double* base, int R) {
 // inner nodes (r ascending), the pairs with x > 8.5, where Phi is exactly 1, are a prefix
 // k < k*_j of the row; they contribute G_j CW[k*_j] with CW the prefix sums of the inner
 // weights, added once per row (by its segment s = 0). Only k >= max(k*_j, s kSeg) is left to
-// evaluate; the count goes to off[t] until the block scans it.
+// evaluate; the count goes to off[t] until the block scans it. The table keeps 16 L_j, so that
+// v = 16 x_jk = fma(16 L_j, qs_k, -16 F_th/sigma_F) is one operation (exactly 16 x_jk).
 __device__ __forceinline__ void lf_segment_row(const ThetaC& tc, const SweepArgs& a, int b, int B, int t, int slot,
                                                const SegTab& tab) {
   const double lo = tc.a3, hi = tc.a1 + a.mc.ln_upper;
@@ -396,19 +402,19 @@ __device__ __forceinline__ void lf_segment_row(const ThetaC& tc, const SweepArgs
   const int sseg = g / a.nL;
   const double tt = fma(half, __ldg(a.xL + j), mid);
   const double x = tt - tc.a1;
-  const double L = exp(tt);
+  const double L16 = 16.0 * exp(tt);
   const double G = half * __ldg(a.wL + j) * exp(fma(tc.a0, x, -exp(x)));
-  const double mcth = -a.mc.cth;
-  int klo = 0, khi = a.nr;  // first k with x_jk <= 8.5 (bit test, as in phi_table)
+  const double mcth16 = -16.0 * a.mc.cth;
+  int klo = 0, khi = a.nr;  // first k with v_jk <= 136 (bit test, as in phi_table16)
   while (klo < khi) {
     const int km = (klo + khi) >> 1;
-    if (__double_as_longlong(fma(L, __ldg(a.qs + km), mcth)) > 0x4021000000000000ll) klo = km + 1;
+    if (__double_as_longlong(fma(L16, __ldg(a.qs + km), mcth16)) > 0x4061000000000000ll) klo = km + 1;
     else khi = km;
   }
   const int k0 = sseg << kSegShift;
   const int kend = min(k0 + kSeg, a.nr);
   const int kb = max(k0, klo);
-  tab.L[slot] = L;
+  tab.L[slot] = L16;
   tab.G[slot] = G;
   tab.pre[slot] = (sseg == 0 && klo > 0) ? G * __ldg(a.cw + klo) : 0.0;
   tab.kb[slot] = kb;
@@ -447,7 +453,7 @@ __device__ __forceinline__ void lf_segment_rows(const ThetaC& tc, const SweepArg
 __device__ __forceinline__ void lf_segment_pairs(const SweepArgs& a, int nseg, const SegTab& tab, const double* s_phi,
                                                  Xacc& xe, XFlags& fe) {
   const int total = tab.off[nseg];
-  const double mcth = -a.mc.cth;
+  const double mcth16 = -16.0 * a.mc.cth;
   for (int q = threadIdx.x; q < total; q += blockDim.x) {
     int lo = 0, hi = nseg - 1;  // last segment with off <= q
     while (lo < hi) {
@@ -456,8 +462,8 @@ __device__ __forceinline__ void lf_segment_pairs(const SweepArgs& a, int nseg, c
       else hi = m - 1;
     }
     const int k = tab.kb[lo] + (q - tab.off[lo]);
-    const double x = fma(tab.L[lo], __ldg(a.qs + k), mcth);
-    xacc_add_double(xe, tab.G[lo] * (__ldg(a.Wr + k) * phi_table(x, s_phi)), fe);
+    const double v = fma(tab.L[lo], __ldg(a.qs + k), mcth16);
+    xacc_add_double(xe, tab.G[lo] * (__ldg(a.Wr + k) * phi_table16(v, s_phi)), fe);
   }
   for (int t = threadIdx.x; t < nseg; t += blockDim.x)
     if (tab.pre[t] != 0.0) xacc_add_double(xe, tab.pre[t], fe);
@@ -480,6 +486,61 @@ __device__ __forceinline__ void warp_reduce(Xacc& d, Xacc& e, unsigned int f[4])
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) f[q] = __reduce_add_sync(0xffffffffu, f[q]);
+}
+
+// Sum of nb consecutive per-block partials (kPartWords words each, from base) by the whole
+// block: every thread loads at most a few partials at once (the loads overlap instead of one
+// warp walking the list), then warp and block reductions. Must be called by every thread of
+// the block; the totals are valid in warp 0. Uses red; syncs the block once.
+__device__ __forceinline__ void sum_partials(const unsigned long long* base, int nb, BlockRed& red, Xacc& D, Xacc& E,
+                                             unsigned int f[4]) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  xacc_zero(D);
+  xacc_zero(E);
+  f[0] = f[1] = f[2] = f[3] = 0u;
+  for (int b = tid; b < nb; b += blockDim.x) {
+    const unsigned long long* src = base + static_cast<size_t>(b) * kPartWords;
+    Xacc t, u;
+    t.w0 = __ldcg(src + 0);
+    t.w1 = __ldcg(src + 1);
+    t.w2 = __ldcg(src + 2);
+    u.w0 = __ldcg(src + 3);
+    u.w1 = __ldcg(src + 4);
+    u.w2 = __ldcg(src + 5);
+    const unsigned long long f01 = __ldcg(src + 6), f23 = __ldcg(src + 7);
+    xacc_add(D, t);
+    xacc_add(E, u);
+    f[0] += static_cast<unsigned int>(f01);
+    f[1] += static_cast<unsigned int>(f01 >> 32);
+    f[2] += static_cast<unsigned int>(f23);
+    f[3] += static_cast<unsigned int>(f23 >> 32);
+  }
+  warp_reduce(D, E, f);
+  if (lane == 0) {
+    red.d[wid] = D;
+    red.e[wid] = E;
+    for (int q = 0; q < 4; ++q) red.f[wid][q] = f[q];
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    xacc_zero(D);
+    xacc_zero(E);
+    f[0] = f[1] = f[2] = f[3] = 0u;
+    if (lane < nw) {
+      D = red.d[lane];
+      E = red.e[lane];
+      for (int q = 0; q < 4; ++q) f[q] = red.f[lane][q];
+    }
+    warp_reduce(D, E, f);
+  }
+}
+
+// ln x for the selection integral: the table routine for positive normal finite x (the value
+// of every theta step), the library routine otherwise (0, subnormal, inf).
+__device__ __forceinline__ double log_etabar(double x, const double* s_math) {
+  const long long b = __double_as_longlong(x);
+  return (b >= 0x0010000000000000ll && b < 0x7FF0000000000000ll) ? log_tab(x, s_math) : log(x);
 }
 
 template <class M>

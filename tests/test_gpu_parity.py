@@ -147,8 +147,8 @@ def test_detection_efficiency_table_matches_oracle():
     consts = oracle.lf_consts(2.0, 10.0, 4000.0, 8, 8)
     s = cudahm.Sampler(cudahm.LF, 1, theta_init=[-1.2, 23.0, 18.4], theta_prop_scale=[0.01] * 3,
                        model_consts=consts)
-    c = np.arange(133) / 8.0 - 8.0
-    x = np.concatenate([np.linspace(-12.0, 12.0, 200_001), c, c + 1 / 16, c - 1 / 16,
+    c = np.arange(265) / 16.0 - 8.0
+    x = np.concatenate([np.linspace(-12.0, 12.0, 200_001), c, c + 1 / 32, c - 1 / 32,
                         [-8.0, -8.0 - 1e-12, 8.5, 8.5 + 1e-12, 0.0, -1e-300, 1e-300]])
     F = 10.0 + 2.0 * x
     got = s.detection(F)
