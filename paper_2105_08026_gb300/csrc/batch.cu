@@ -361,9 +361,9 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
     for (int q = 0; q < p * p; ++q) s_Sth[q] = a.chain->S_theta[q];
     s_etabar = a.chain->etabar;
     s_logeb = is_lf ? log_etabar(s_etabar, s_math) : 0.0;
-    s_tc = M::consts(s_theta);
+    s_tc = M::consts(s_theta, s_math);
     s_tcf = M::consts32(s_tc);
-    s_lpri = M::logprior(s_theta, a.mc);
+    s_lpri = M::logprior(s_theta, a.mc, s_math);
     s_rows_written = 0;
     s_tacc = 0;
     s_stop = 0;
@@ -384,7 +384,7 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
     if (tid == 0) {
       double lp;
       TC tcp;
-      propose_theta<M>(a, s, p, s_theta, s_Sth, s_thp, lp, tcp);
+      propose_theta<M>(a, s, p, s_theta, s_Sth, s_thp, lp, tcp, s_math);
       s_lpri_new = lp;
       s_tcp = tcp;
       s_tcpf = M::consts32(tcp);
@@ -424,7 +424,7 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
         const ThetaC tcp = s_tcp;
         for (int t0 = 0; t0 < nseg; t0 += R) {
           const int cnt = min(R, nseg - t0);
-          for (int q = tid; q < cnt; q += blockDim.x) lf_segment_row(tcp, a, lb, nb, t0 + q, q, tab);
+          for (int q = tid; q < cnt; q += blockDim.x) lf_segment_row(tcp, a, lb, nb, t0 + q, q, tab, s_math);
           __syncthreads();
           if (wid == 0) lf_segment_scan(cnt, tab);
           __syncthreads();
@@ -519,7 +519,7 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
             s_tacc++;
           }
           if (a.adapt_theta) {
-            const double alpha = (logalpha >= 0.0) ? 1.0 : exp(logalpha);
+            const double alpha = (logalpha >= 0.0) ? 1.0 : exp_tab(logalpha, s_math);
             ram_update_theta(p, s_Sth, a.tab_U + s * p, alpha, a.astar_theta, eta);
           }
           const long long post = s - burn_left;

@@ -83,7 +83,11 @@ struct SweepArgs {
   int skip_cta;
   double gamma;       // adaptation exponent (eta = n^-gamma)
   const float* d32;   // FP32 form: precomputed binary32 member data (kData32 x n, member-minor)
+  double* pub;        // theta' of the current sweep, published by block 0 (kPubWords doubles);
+                      // its sequence word is bar[1]
 };
+
+constexpr int kPubWords = 32;
 
 // Progress of one population through a batched run (device memory, updated by the kernel).
 struct BatchProg {
@@ -131,8 +135,8 @@ cudaError_t launch_lf_inner(int nr, const double* xr, const double* wr, double r
 cudaError_t launch_tables(int p, uint32_t key0, uint32_t key1, long long k0, long long ns, double gamma, double* U,
                           double* u, double* lnu, double* eta, cudaStream_t st);
 cudaError_t launch_eval_logdens(int model, bool f32, long long n, const double* y, const double* aux,
-                                const double* chi, const double* theta_dev, const ModelConsts& mc, double* out,
-                                cudaStream_t st);
+                                const double* chi, const double* theta_dev, const ModelConsts& mc,
+                                const double* math_tab, double* out, cudaStream_t st);
 cudaError_t launch_eval_etabar(const double* theta_dev, const SweepArgs& rule, unsigned long long* partials,
                                int grid, double* out, cudaStream_t st);
 

@@ -27,9 +27,11 @@ namespace {
 constexpr int kNoallocMaxNodes = CUDAHM_NOALLOC_MAX_NODES;
 constexpr int kNoallocMaxGrid = 1024;
 constexpr int kPhiWordsMax = 265 * 9;  // normal-CDF Taylor table
-// layout in doubles: xL, wL, xr, wr, qs, Wr (max nodes each), the Phi table, the prefix sums
-// of the inner weights (max nodes + 1), then the per-block partials (4 x u64 per block)
-constexpr size_t kScratchDoubles = 6 * static_cast<size_t>(kNoallocMaxNodes) + kPhiWordsMax +
+constexpr int kMathWordsMax = 248;     // exp/log tables
+// layout in doubles: xL, wL, xr, wr, qs, Wr (max nodes each), the Phi table, the exp/log table,
+// the prefix sums of the inner weights (max nodes + 1), then the per-block partials (4 x u64
+// per block)
+constexpr size_t kScratchDoubles = 6 * static_cast<size_t>(kNoallocMaxNodes) + kPhiWordsMax + kMathWordsMax +
                                    (kNoallocMaxNodes + 1) + 4 * static_cast<size_t>(kNoallocMaxGrid);
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
@@ -86,15 +88,18 @@ extern "C" int cudahm_lf_etabar_noalloc(const double* theta_dev, const double* c
   double* qs = wr + kNoallocMaxNodes;
   double* Wr = qs + kNoallocMaxNodes;
   double* phi = Wr + kNoallocMaxNodes;
-  double* cw = phi + kPhiWordsMax;
+  double* mtab = phi + kPhiWordsMax;
+  double* cw = mtab + kMathWordsMax;
   unsigned long long* partials = reinterpret_cast<unsigned long long*>(cw + kNoallocMaxNodes + 1);
   if (phi_table_words() > kPhiWordsMax) return noalloc_fail(CUDAHM_ECUDA, "normal-CDF table larger than its slot");
+  if (math_table_words() > kMathWordsMax) return noalloc_fail(CUDAHM_ECUDA, "exp/log table larger than its slot");
 
   // every table this call reads is rewritten here, on the caller's stream
   cudaError_t e = launch_gauss_legendre(nL, xL, wL, st);
   if (e == cudaSuccess) e = launch_gauss_legendre(nr, xr, wr, st);
   if (e == cudaSuccess) e = launch_lf_inner(nr, xr, wr, rmax, sigF, qs, Wr, st);
   if (e == cudaSuccess) e = launch_phi_table(phi, st);
+  if (e == cudaSuccess) e = launch_math_table(mtab, st);
   if (e == cudaSuccess) e = launch_prefix_weights(nr, Wr, cw, st);
   if (e != cudaSuccess) return noalloc_fail(CUDAHM_ECUDA, cudaGetErrorString(e));
 
@@ -108,6 +113,7 @@ extern "C" int cudahm_lf_etabar_noalloc(const double* theta_dev, const double* c
   rule.qs = qs;
   rule.Wr = Wr;
   rule.phi_coef = phi;
+  rule.math_tab = mtab;
   rule.cw = cw;
   rule.mc.cth = Fth / sigF;
   rule.mc.ln_upper = ln_upper;

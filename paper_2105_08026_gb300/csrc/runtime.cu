@@ -95,6 +95,7 @@ struct cudahm {
   double* cw = nullptr;
   float* d32 = nullptr;
   double* math_tab = nullptr;
+  double* pub = nullptr;  // theta' published by block 0 of the sweep kernel
   unsigned long long* eb_partials = nullptr;
   int eb_grid = 0, eb_rows_smem = 1;
   // host mirrors
@@ -279,6 +280,7 @@ SweepArgs base_args(cudahm* h) {
   a.phi_coef = h->phi_coef;
   a.cw = h->cw;
   a.math_tab = h->math_tab;
+  a.pub = h->pub;
   a.nL = h->cfg.model == CUDAHM_LF ? static_cast<int>(h->cfg.model_consts[3]) : 0;
   a.nr = h->cfg.model == CUDAHM_LF ? static_cast<int>(h->cfg.model_consts[4]) : 0;
   a.rows_smem = h->rows_smem;
@@ -493,6 +495,7 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
       (rc = alloc_into(h, &h->tab_U, kChunk * p)) || (rc = alloc_into(h, &h->tab_u, kChunk)) ||
       (rc = alloc_into(h, &h->tab_lnu, kChunk)) ||
       (rc = alloc_into(h, &h->math_tab, static_cast<size_t>(math_table_words()))) ||
+      (rc = alloc_into(h, &h->pub, kPubWords)) ||
       (rc = alloc_into(h, &h->tab_eta, kChunk)))
     return bail(rc);
   if (cfg->model == CUDAHM_LF) {
@@ -631,7 +634,7 @@ int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
     const long long ns = std::min<long long>(kChunk, total - off);
     CU(launch_tables(h->p, a.key0, a.key1, h->sweeps, ns, h->cfg.adapt_exponent, h->tab_U, h->tab_u, h->tab_lnu,
                      h->tab_eta, h->stream));
-    CU(cudaMemsetAsync(h->bar, 0, sizeof(unsigned int), h->stream));
+    CU(cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned int), h->stream));  // barrier count, theta' sequence
     a.k0 = h->sweeps;
     a.ns = ns;
     a.burn_left = n_burn - off;
@@ -751,7 +754,7 @@ int cudahm_eval_logdens(cudahm_t h, const double* theta_host, double* lp_host) {
   TRY(alloc_into(h, &out, h->n));
   CU(cudaMemcpyAsync(h->theta_dev, theta_host, sizeof(double) * h->p, cudaMemcpyHostToDevice, h->stream));
   CU(launch_eval_logdens(h->cfg.model, h->cfg.precision == CUDAHM_FP32, h->n, h->y, h->aux, h->chi, h->theta_dev,
-                         h->mc, out, h->stream));
+                         h->mc, h->math_tab, out, h->stream));
   CU(cudaMemcpyAsync(lp_host, out, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
   h->dfree(out);

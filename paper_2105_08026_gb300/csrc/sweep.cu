@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   __shared__ ThetaC s_tc, s_tcp;
   __shared__ ThetaCf s_tcf, s_tcpf;
   __shared__ double s_etabar, s_logeb, s_lpri, s_lpri_new, s_logalpha_prev;
-  __shared__ int s_stop, s_pending_ram;
+  __shared__ int s_stop, s_pending_ram, s_fail;
   __shared__ long long s_rows_written, s_tacc;
   __shared__ BlockRed s_red;
 
@@ -136,23 +136,35 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     for (int q = 0; q < p * p; ++q) s_Sth[q] = a.chain->S_theta[q];
     s_etabar = a.chain->etabar;
     s_logeb = is_lf ? log_etabar(s_etabar, s_math) : 0.0;
-    s_tc = M::consts(s_theta);
-    s_lpri = M::logprior(s_theta, a.mc);
+    s_tc = M::consts(s_theta, s_math);
+    s_lpri = M::logprior(s_theta, a.mc, s_math);
     s_rows_written = 0;
     s_tacc = 0;
     s_stop = 0;
     s_pending_ram = 0;
     s_logalpha_prev = 0.0;
-    double lp;
-    ThetaC tcp;
-    propose_theta<M>(a, 0, p, s_theta, s_Sth, s_thp, lp, tcp);
+    s_fail = 0;
+    s_tcf = M::consts32(s_tc);
+    // theta' of the first sweep: FP64 form, proposed by block 0 and fetched by the others;
+    // FP32 form (short member phase, where the fetch would sit on the critical path), proposed
+    // by every block
+    double lp = -INFINITY;
+    ThetaC tcp{};
+    ThetaCf tcpf{};
+    if (F32 || blockIdx.x == 0) {
+      propose_theta<M>(a, 0, p, s_theta, s_Sth, s_thp, lp, tcp, s_math);
+      tcpf = M::consts32(tcp);
+      if (!F32) publish_theta(a, 1u, s_thp, p, lp, tcp, tcpf);
+    } else if (!fetch_theta(a, 1u, s_thp, p, lp, tcp, tcpf)) {
+      s_fail = 1;
+    }
     s_lpri_new = lp;
     s_tcp = tcp;
-    s_tcf = M::consts32(s_tc);
-    s_tcpf = M::consts32(tcp);
+    s_tcpf = tcpf;
   }
   __syncthreads();
-  if (is_lf && s_lpri_new != -INFINITY) lf_segment_rows(s_tcp, a, blockIdx.x, gridDim.x, nseg, tab);
+  if (s_fail) return;
+  if (is_lf && s_lpri_new != -INFINITY) lf_segment_rows(s_tcp, a, blockIdx.x, gridDim.x, nseg, tab, s_math);
 
   // members of this thread: i = nb0 + tid + m blockDim (latent, RAM factor, e^chi, log l in registers)
   R chi[K], echi[K], ll[K];
@@ -203,22 +215,31 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     // deferred theta work of the previous sweep and the proposal of this one (last warp)
     if (s > 0 && wid == ctrl_warp) {
       if (lane == 0) {
-        if (s_pending_ram) {
-          const double lal = s_logalpha_prev;
-          const double alpha = (lal >= 0.0) ? 1.0 : exp(lal);
-          ram_update_theta(p, s_Sth, a.tab_U + (s - 1) * p, alpha, a.astar_theta, __ldg(a.tab_eta + s - 1));
+        // FP64 form: one proposal (and one RAM update of S_theta) per sweep for the grid, made
+        // and published by block 0, fetched by the other blocks; FP32 form: every block
+        double lp = -INFINITY;
+        ThetaC tcp{};
+        ThetaCf tcpf{};
+        if (F32 || blockIdx.x == 0) {
+          if (s_pending_ram) {
+            const double lal = s_logalpha_prev;
+            const double alpha = (lal >= 0.0) ? 1.0 : exp_tab(lal, s_math);
+            ram_update_theta(p, s_Sth, a.tab_U + (s - 1) * p, alpha, a.astar_theta, __ldg(a.tab_eta + s - 1));
+          }
+          propose_theta<M>(a, s, p, s_theta, s_Sth, s_thp, lp, tcp, s_math);
+          tcpf = M::consts32(tcp);
+          if (!F32) publish_theta(a, static_cast<unsigned int>(s + 1), s_thp, p, lp, tcp, tcpf);
+        } else if (!fetch_theta(a, static_cast<unsigned int>(s + 1), s_thp, p, lp, tcp, tcpf)) {
+          lp = -INFINITY;  // the run has failed; the next barrier returns
         }
-        double lp;
-        ThetaC tcp;
-        propose_theta<M>(a, s, p, s_theta, s_Sth, s_thp, lp, tcp);
         s_lpri_new = lp;
         s_tcp = tcp;
-        s_tcpf = M::consts32(tcp);
+        s_tcpf = tcpf;
       }
       __syncwarp();
       if (is_lf && s_lpri_new != -INFINITY) {
         const ThetaC tcp = s_tcp;
-        for (int t = lane; t < nseg; t += 32) lf_segment_row(tcp, a, blockIdx.x, gridDim.x, t, t, tab);
+        for (int t = lane; t < nseg; t += 32) lf_segment_row(tcp, a, blockIdx.x, gridDim.x, t, t, tab, s_math);
         __syncwarp();
         lf_segment_scan(nseg, tab);
       }
@@ -506,7 +527,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     if (blockIdx.x == 0) {
       if (s_pending_ram && a.ns > 0) {  // RAM update of the last sweep's theta step
         const double lal = s_logalpha_prev;
-        const double alpha = (lal >= 0.0) ? 1.0 : exp(lal);
+        const double alpha = (lal >= 0.0) ? 1.0 : exp_tab(lal, s_math);
         ram_update_theta(p, s_Sth, a.tab_U + (a.ns - 1) * p, alpha, a.astar_theta, __ldg(a.tab_eta + a.ns - 1));
       }
       for (int q = 0; q < p; ++q) a.chain->theta[q] = s_theta[q];
@@ -771,12 +792,12 @@ cudaError_t launch_tables(int p, uint32_t key0, uint32_t key1, long long k0, lon
 // FP32 form evaluates exactly the binary32 expressions its member step uses.
 template <class M, bool F32>
 __global__ void eval_logdens_kernel(long long n, const double* y, const double* aux, const double* chi,
-                                    const double* theta, ModelConsts mc, double* out) {
+                                    const double* theta, ModelConsts mc, const double* T, double* out) {
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double th[kMaxP];
   for (int q = 0; q < 3; ++q) th[q] = theta[q];
-  const ThetaC tc = M::consts(th);
+  const ThetaC tc = M::consts(th, T);
   if (F32) {
     const ThetaCf tf = M::consts32(tc);
     const float c = static_cast<float>(chi[i]);
@@ -801,12 +822,12 @@ __global__ void eval_logdens_kernel(long long n, const double* y, const double* 
 // d = 3 model: the same binary64 or binary32 expressions as its member step (per-component arrays).
 template <bool F32>
 __global__ void eval_logdens3_kernel(long long n, const double* y, const double* aux, const double* chi,
-                                     const double* theta, double* out) {
+                                     const double* theta, const double* T, double* out) {
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double th[kMaxP];
   for (int q = 0; q < 9; ++q) th[q] = theta[q];
-  const ThetaC3 tc = MVN3::consts(th);
+  const ThetaC3 tc = MVN3::consts(th, T);
   if constexpr (F32) {
     const ThetaC3f tf = MVN3::consts32(tc);
     float x[3], d[MVN3::kData32];
@@ -828,19 +849,19 @@ __global__ void eval_logdens3_kernel(long long n, const double* y, const double*
 }
 
 cudaError_t launch_eval_logdens(int model, bool f32, long long n, const double* y, const double* aux,
-                                const double* chi, const double* theta_dev, const ModelConsts& mc, double* out,
-                                cudaStream_t st) {
+                                const double* chi, const double* theta_dev, const ModelConsts& mc,
+                                const double* math_tab, double* out, cudaStream_t st) {
   const int blk = 256;
   const unsigned int grid = static_cast<unsigned int>((n + blk - 1) / blk);
   if (model == CUDAHM_MVN3) {
-    if (f32) eval_logdens3_kernel<true><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, out);
-    else eval_logdens3_kernel<false><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, out);
+    if (f32) eval_logdens3_kernel<true><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, math_tab, out);
+    else eval_logdens3_kernel<false><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, math_tab, out);
   } else if (model == CUDAHM_NN1) {
-    if (f32) eval_logdens_kernel<NN1, true><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, out);
-    else eval_logdens_kernel<NN1, false><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, out);
+    if (f32) eval_logdens_kernel<NN1, true><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, math_tab, out);
+    else eval_logdens_kernel<NN1, false><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, math_tab, out);
   } else if (model == CUDAHM_LF) {
-    if (f32) eval_logdens_kernel<LF, true><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, out);
-    else eval_logdens_kernel<LF, false><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, out);
+    if (f32) eval_logdens_kernel<LF, true><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, math_tab, out);
+    else eval_logdens_kernel<LF, false><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, math_tab, out);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -856,14 +877,14 @@ __global__ void etabar_partial_kernel(const double* theta, const SweepArgs a, un
   if (threadIdx.x == 0) {
     double th[kMaxP];
     for (int q = 0; q < 3; ++q) th[q] = theta[q];
-    s_tc = LF::consts(th);
+    s_tc = LF::consts(th, a.math_tab);
   }
   __syncthreads();
   const int nseg = lf_block_segments(a, blockIdx.x, gridDim.x);
   double* s_phi = s_rows;
   const SegTab tab = segtab_carve(s_rows + kPhiWords, a.rows_smem);
   for (int q = threadIdx.x; q < kPhiWords; q += blockDim.x) s_phi[q] = a.phi_coef[q];
-  lf_segment_rows(s_tc, a, blockIdx.x, gridDim.x, nseg, tab);
+  lf_segment_rows(s_tc, a, blockIdx.x, gridDim.x, nseg, tab, a.math_tab);
   __syncthreads();
   Xacc xd, xe;
   xacc_zero(xd);

@@ -71,10 +71,11 @@ struct NN1 {
     const float r = __fadd_rn(__fsub_rn(d[0], chi), d[1]);
     return __fmul_rn(-d[2], __fmul_rn(r, r));
   }
-  __device__ static ThetaC consts(const double* th) {
+  // per-theta constants; T is the exp/log table (the theta step runs these on its serial path)
+  __device__ static ThetaC consts(const double* th, const double* T) {
     ThetaC c;
     c.a0 = th[0];
-    c.a1 = 0.5 * exp(-2.0 * th[1]);
+    c.a1 = 0.5 * exp_tab(-2.0 * th[1], T);
     c.a2 = 0.0;
     c.a3 = 0.0;
     return c;
@@ -90,7 +91,7 @@ struct NN1 {
     return __dmul_rn(__dmul_rn(-0.5, aux), __dmul_rn(r, r));
   }
   __device__ static double cterm(const double* th) { return -th[1]; }
-  __device__ static double logprior(const double* th, const ModelConsts& mc) {
+  __device__ static double logprior(const double* th, const ModelConsts& mc, const double*) {
     return (th[1] >= mc.lo && th[1] <= mc.hi) ? 0.0 : -INFINITY;
   }
 };
@@ -140,11 +141,11 @@ struct LF {
     const float r = __fmaf_rn(-expf(chi), d[4], d[3]);
     return __fmul_rn(__fmul_rn(r, r), d[2]);
   }
-  __device__ static ThetaC consts(const double* th) {
+  __device__ static ThetaC consts(const double* th, const double* T) {
     ThetaC c;
     c.a0 = th[0] + 1.0;
     c.a1 = th[1];
-    c.a2 = exp(-th[1]);
+    c.a2 = exp_tab(-th[1], T);
     c.a3 = th[2];
     return c;
   }
@@ -158,10 +159,10 @@ struct LF {
     return -__dmul_rn(__dmul_rn(r, r), mc.inv2sig2);
   }
   __device__ static double cterm(const double*) { return 0.0; }
-  __device__ static double logprior(const double* th, const ModelConsts&) {
+  __device__ static double logprior(const double* th, const ModelConsts&, const double* T) {
     if (!(th[0] > -2.0 && th[0] < 0.0)) return -INFINITY;
     if (!(th[2] < th[1])) return -INFINITY;
-    return -log(1.0 + th[0] * th[0]) + th[2];
+    return -log_tab(1.0 + th[0] * th[0], T) + th[2];  // 1 + beta^2 in [1, 5): a normal argument
   }
 };
 
@@ -187,8 +188,9 @@ struct MVN3 {
   using TCf = ThetaC3f;
   static constexpr int kD = 3;
   static constexpr bool kExp = false;
-  __device__ static ThetaC3 consts(const double* th) {
-    const double L00 = exp(th[3]), L10 = th[4], L11 = exp(th[5]), L20 = th[6], L21 = th[7], L22 = exp(th[8]);
+  __device__ static ThetaC3 consts(const double* th, const double* T) {
+    const double L00 = exp_tab(th[3], T), L10 = th[4], L11 = exp_tab(th[5], T), L20 = th[6], L21 = th[7],
+                 L22 = exp_tab(th[8], T);
     ThetaC3 c;
     c.mu[0] = th[0];
     c.mu[1] = th[1];
@@ -217,7 +219,7 @@ struct MVN3 {
   }
   __device__ static double cterm(const double* th) { return -((th[3] + th[5]) + th[8]); }
   // flat in mu, in the off-diagonal entries and in the log-diagonal entries (improper)
-  __device__ static double logprior(const double*, const ModelConsts&) { return 0.0; }
+  __device__ static double logprior(const double*, const ModelConsts&, const double*) { return 0.0; }
 
   __device__ static ThetaC3f consts32(const ThetaC3& c) {
     ThetaC3f f;
@@ -286,31 +288,34 @@ __device__ __forceinline__ void ram3_update(double (&S)[6], double w0, double w1
 }
 
 // ----------------------------------------------------- theta RAM update -------
-// Lower-triangular L (p x p, row-major) with L' L'^T = L (I + c U U^T/|U|^2) L^T,
-// c = eta (alpha - alpha_*): a rank-one Cholesky update (c > 0) or downdate (c < 0)
-// with v = L U sqrt(|c|)/|U|.
+// Lower-triangular L (p x p, row-major) with L' L'^T = L (I + c U U^T/|U|^2) L^T
+// = L L^T + sig w w^T, c = eta (alpha - alpha_*), w = L U, sig = c/|U|^2: the rank-one Cholesky
+// modification of ram3_update for any p. Column k: a = L_kk, b = w_k, t = a^2 + sig b^2,
+// L'_kk = sqrt t, L'_ik = (a L_ik + sig b w_i)/sqrt t, w_i <- (a w_i - b L_ik)/sqrt t (i > k).
+// t > 0 because 1 + c >= 1 - alpha_* > 0. This runs once per sweep on the theta step's serial
+// path, so it is written with one reciprocal square root per column and no divisions there.
 __device__ inline void ram_update_theta(int p, double* L, const double* U, double alpha, double astar, double eta) {
   const double c = eta * (alpha - astar);
   if (c == 0.0) return;
   double uu = 0.0;
   for (int j = 0; j < p; ++j) uu = fma(U[j], U[j], uu);
-  const double sc = sqrt(fabs(c) / uu);
-  const double sg = c > 0.0 ? 1.0 : -1.0;
-  double x[kMaxP];
+  const double sig = c / uu;
+  double w[kMaxP];
   for (int a = 0; a < p; ++a) {
     double t = 0.0;
     for (int b = 0; b <= a; ++b) t = fma(L[a * p + b], U[b], t);
-    x[a] = t * sc;
+    w[a] = t;
   }
   for (int k = 0; k < p; ++k) {
-    const double Lkk = L[k * p + k];
-    const double r = sqrt(fma(sg * x[k], x[k], Lkk * Lkk));
-    const double cc = r / Lkk, ss = x[k] / Lkk;
-    L[k * p + k] = r;
+    const double a = L[k * p + k], b = w[k], sb = sig * b;
+    const double t = fma(sb, b, a * a);
+    const double ir = rsqrt(t);
+    L[k * p + k] = t * ir;
+    const double air = a * ir, bir = b * ir, sbir = sb * ir;
     for (int i = k + 1; i < p; ++i) {
-      const double li = (fma(sg * ss, x[i], L[i * p + k])) / cc;
-      L[i * p + k] = li;
-      x[i] = fma(cc, x[i], -ss * li);
+      const double lik = L[i * p + k];
+      L[i * p + k] = fma(air, lik, sbir * w[i]);
+      w[i] = fma(air, w[i], -bir * lik);
     }
   }
 }
@@ -386,7 +391,7 @@ __device__ __forceinline__ SegTab segtab_carve(double* base, int R) {
   return t;
 }
 
-// Values of segment t (one thread): L_j = e^t_j, G_j = (half-width) w_j g(e^t_j) e^t_j on
+// Values of segment t (one thread; T is the exp/log table): L_j = e^t_j, G_j = (half-width) w_j g(e^t_j) e^t_j on
 // t in [ln L_low, ln L* + ln_upper]. Since x_jk = L_j qs_k - F_th/sigma_F decreases along the
 // inner nodes (r ascending), the pairs with x > 8.5, where Phi is exactly 1, are a prefix
 // k < k*_j of the row; they contribute G_j CW[k*_j] with CW the prefix sums of the inner
@@ -394,7 +399,7 @@ __device__ __forceinline__ SegTab segtab_carve(double* base, int R) {
 // evaluate; the count goes to off[t] until the block scans it. The table keeps 16 L_j, so that
 // v = 16 x_jk = fma(16 L_j, qs_k, -16 F_th/sigma_F) is one operation (exactly 16 x_jk).
 __device__ __forceinline__ void lf_segment_row(const ThetaC& tc, const SweepArgs& a, int b, int B, int t, int slot,
-                                               const SegTab& tab) {
+                                               const SegTab& tab, const double* __restrict__ T) {
   const double lo = tc.a3, hi = tc.a1 + a.mc.ln_upper;
   const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
   const int g = b + t * B;
@@ -402,13 +407,15 @@ __device__ __forceinline__ void lf_segment_row(const ThetaC& tc, const SweepArgs
   const int sseg = g / a.nL;
   const double tt = fma(half, __ldg(a.xL + j), mid);
   const double x = tt - tc.a1;
-  const double L16 = 16.0 * exp(tt);
-  const double G = half * __ldg(a.wL + j) * exp(fma(tc.a0, x, -exp(x)));
-  const double mcth16 = -16.0 * a.mc.cth;
-  int klo = 0, khi = a.nr;  // first k with v_jk <= 136 (bit test, as in phi_table16)
+  const double L16 = 16.0 * exp_tab(tt, T);
+  const double G = half * __ldg(a.wL + j) * exp_tab(fma(tc.a0, x, -exp_tab(x, T)), T);
+  // first k with qs_k <= (136 + 16 F_th/sigma_F)/(16 L_j), i.e. v_jk <= 136 up to rounding (both
+  // sides of that boundary give Phi = 1 exactly); positive doubles compared as integers
+  const long long thr = __double_as_longlong((136.0 + 16.0 * a.mc.cth) / L16);
+  int klo = 0, khi = a.nr;
   while (klo < khi) {
     const int km = (klo + khi) >> 1;
-    if (__double_as_longlong(fma(L16, __ldg(a.qs + km), mcth16)) > 0x4061000000000000ll) klo = km + 1;
+    if (__double_as_longlong(__ldg(a.qs + km)) > thr) klo = km + 1;
     else khi = km;
   }
   const int k0 = sseg << kSegShift;
@@ -442,8 +449,8 @@ __device__ __forceinline__ void lf_segment_scan(int nseg, const SegTab& tab) {
 
 // All segment rows and the scan by the whole block (set-up paths).
 __device__ __forceinline__ void lf_segment_rows(const ThetaC& tc, const SweepArgs& a, int b, int B, int nseg,
-                                                const SegTab& tab) {
-  for (int t = threadIdx.x; t < nseg; t += blockDim.x) lf_segment_row(tc, a, b, B, t, t, tab);
+                                                const SegTab& tab, const double* __restrict__ T) {
+  for (int t = threadIdx.x; t < nseg; t += blockDim.x) lf_segment_row(tc, a, b, B, t, t, tab, T);
   __syncthreads();
   if (threadIdx.x < 32) lf_segment_scan(nseg, tab);
 }
@@ -543,16 +550,70 @@ __device__ __forceinline__ double log_etabar(double x, const double* s_math) {
   return (b >= 0x0010000000000000ll && b < 0x7FF0000000000000ll) ? log_tab(x, s_math) : log(x);
 }
 
+// theta' of one sweep as block 0 publishes it for the other blocks of a launch (one proposal
+// and one RAM update of S_theta per sweep for the whole grid instead of one per block).
+struct ThetaPub {
+  double thp[kMaxP];
+  double lpri_new;
+  ThetaC tcp;
+  ThetaCf tcpf;
+};
+static_assert(sizeof(ThetaPub) <= sizeof(double) * kPubWords, "ThetaPub does not fit its buffer");
+
+// Block 0: write theta' of the launch's sweep s1 (1-based), then release its sequence number.
+__device__ __forceinline__ void publish_theta(const SweepArgs& a, unsigned int s1, const double* thp, int p,
+                                              double lpri_new, const ThetaC& tcp, const ThetaCf& tcpf) {
+  ThetaPub* pub = reinterpret_cast<ThetaPub*>(a.pub);
+  for (int q = 0; q < p; ++q) __stcg(pub->thp + q, thp[q]);
+  __stcg(&pub->lpri_new, lpri_new);
+  __stcg(&pub->tcp.a0, tcp.a0);
+  __stcg(&pub->tcp.a1, tcp.a1);
+  __stcg(&pub->tcp.a2, tcp.a2);
+  __stcg(&pub->tcp.a3, tcp.a3);
+  const float* f = &tcpf.sc_hi;
+  float* g = &pub->tcpf.sc_hi;
+  for (int q = 0; q < 6; ++q) __stcg(g + q, f[q]);
+  __threadfence();
+  st_release_u32(a.bar + 1, s1);
+}
+
+// Other blocks: wait (bounded) until block 0 has published sweep s1, then read it. Returns false
+// if the run failed meanwhile or the wait ran out (the run's error word then says why).
+__device__ __forceinline__ bool fetch_theta(const SweepArgs& a, unsigned int s1, double* thp, int p, double& lpri_new,
+                                            ThetaC& tcp, ThetaCf& tcpf) {
+  const long long t0 = globaltimer_ns();
+  while (ld_acquire_u32(a.bar + 1) < s1) {
+    if (ld_volatile_i32(a.err) != 0) return false;
+    if (globaltimer_ns() - t0 > a.timeout_ns) {
+      atomicCAS(a.err, 0, CUDAHM_ETIMEOUT);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  const ThetaPub* pub = reinterpret_cast<const ThetaPub*>(a.pub);
+  for (int q = 0; q < p; ++q) thp[q] = __ldcg(pub->thp + q);
+  lpri_new = __ldcg(&pub->lpri_new);
+  tcp.a0 = __ldcg(&pub->tcp.a0);
+  tcp.a1 = __ldcg(&pub->tcp.a1);
+  tcp.a2 = __ldcg(&pub->tcp.a2);
+  tcp.a3 = __ldcg(&pub->tcp.a3);
+  const float* g = &pub->tcpf.sc_hi;
+  float* f = &tcpf.sc_hi;
+  for (int q = 0; q < 6; ++q) f[q] = __ldcg(g + q);
+  return true;
+}
+
 template <class M>
 __device__ __forceinline__ void propose_theta(const SweepArgs& a, long long s, int p, const double* theta, double* Sth,
-                                              double* thp, double& lpri_new, typename M::TC& tcp) {
+                                              double* thp, double& lpri_new, typename M::TC& tcp,
+                                              const double* T) {
   for (int q = 0; q < p; ++q) {
     double t = theta[q];
     for (int b = 0; b <= q; ++b) t = fma(Sth[q * p + b], __ldg(a.tab_U + s * p + b), t);
     thp[q] = t;
   }
-  lpri_new = M::logprior(thp, a.mc);
-  tcp = M::consts(thp);
+  lpri_new = M::logprior(thp, a.mc, T);
+  tcp = M::consts(thp, T);
 }
 
 }  // namespace chm
