@@ -28,9 +28,9 @@ _LIB = os.path.join(_HERE, "libcudahm_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-NN1, MVN3, LF = 0, 1, 2
-MODEL_D = {NN1: 1, MVN3: 3, LF: 1}
-MODEL_P = {NN1: 2, MVN3: 9, LF: 3}
+NN1, MVN3, LF, BB1 = 0, 1, 2, 3
+MODEL_D = {NN1: 1, MVN3: 3, LF: 1, BB1: 1}
+MODEL_P = {NN1: 2, MVN3: 9, LF: 3, BB1: 3}
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _u8p = ctypes.POINTER(ctypes.c_uint8)
@@ -71,6 +71,16 @@ def lib():
             L.orc_lf_detection.restype = ctypes.c_double
             L.orc_lf_H.argtypes = [ctypes.c_double, _dp]
             L.orc_lf_H.restype = ctypes.c_double
+            L.orc_bb1_threshold.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            L.orc_bb1_threshold.restype = ctypes.c_double
+            L.orc_bb1_detection.argtypes = [ctypes.c_double, _dp]
+            L.orc_bb1_detection.restype = ctypes.c_double
+            L.orc_bb1_H.argtypes = [ctypes.c_double, _dp]
+            L.orc_bb1_H.restype = ctypes.c_double
+            L.orc_bb1_etabar.argtypes = [_dp, _dp]
+            L.orc_bb1_etabar.restype = ctypes.c_double
+            L.orc_logf_obj.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
+            L.orc_logf_obj.restype = ctypes.c_double
             L.orc_member_logdens.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp,
                                              _dp]
             L.orc_run.argtypes = ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp,
@@ -176,6 +186,40 @@ def lf_detection(F, consts) -> np.ndarray:
 def lf_H(L, consts) -> float:
     c = _f64(consts)
     return lib().orc_lf_H(float(L), _p(c))
+
+
+def bb1_consts(sigma0, alpha, nu, r_max, nL=1024, nr=1024, ln_upper=float(np.log(60.0)), ln_lower=-40.0):
+    """Constants of the BB1 model: sigma0, alpha, nu, r_max, n_L, n_r, ln(upper/u), ln(lower/l)."""
+    return np.array([sigma0, alpha, nu, r_max, nL, nr, ln_upper, ln_lower], dtype=np.float64)
+
+
+def bb1_threshold(sigma0, alpha, nu) -> float:
+    """F_th = nu sigma0/sqrt(1 - alpha^2) (Sec. 5.2, eq. Fth)."""
+    return lib().orc_bb1_threshold(sigma0, alpha, nu)
+
+
+def bb1_detection(F, consts) -> np.ndarray:
+    """eta(F) = Phi((F - F_th)/sigma(F)), sigma(F)^2 = sigma0^2 + (alpha F)^2."""
+    c = _f64(consts)
+    return np.array([lib().orc_bb1_detection(float(f), _p(c)) for f in np.atleast_1d(F)])
+
+
+def bb1_H(L, consts) -> float:
+    c = _f64(consts)
+    return lib().orc_bb1_H(float(L), _p(c))
+
+
+def bb1_etabar(theta, consts) -> float:
+    th = _f64(theta)
+    c = _f64(consts)
+    return lib().orc_bb1_etabar(_p(th), _p(c))
+
+
+def logf_obj(model, chi, theta) -> float:
+    """log f_obj(chi;theta) of one member (the population term of its target)."""
+    c = _f64(np.atleast_1d(chi))
+    th = _f64(theta)
+    return lib().orc_logf_obj(model, MODEL_D[model], _p(c), _p(th))
 
 
 def member_logdens(model, y, aux, consts, chi, theta):

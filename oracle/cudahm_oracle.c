@@ -45,7 +45,8 @@
  *      of sweep k; the accept uniform is the first uniform of block ceil(p/2).
  *   R6 luminosity model in chi = ln L (Schechter form truncated at L_low), the
  *      normaliser of f cancels against the normalised selection integral, so the
- *      theta step uses the unnormalised integrand (see lf_* below).
+ *      theta step uses the unnormalised integrand (see lf_* below). The same holds for the
+ *      paper's BB1 model with its flux-dependent measurement error (see bb1_* below).
  */
 #include <math.h>
 #include <stdint.h>
@@ -55,6 +56,7 @@
 #define ORC_NN1 0
 #define ORC_MVN3 1
 #define ORC_LF 2
+#define ORC_BB1 3
 
 /* ------------------------------------------------------------------------- */
 /* R5: Philox4x32-10 block cipher (Salmon, Moraes, Dror, Shaw, SC'11).         */
@@ -358,6 +360,93 @@ double orc_lf_H(double L, const double* consts) {
   return v;
 }
 
+/* ------------------------------------------------------------------------- */
+/* BB1 luminosity function (Sec. 5.1, App. B eq. lumPDF), the paper's simulation model.    */
+/* Latent chi = ln L, theta = (beta, ln l, ln u). Unnormalised population                 */
+/*   g(L) = (1 - e^{-L/l}) (L/u)^beta e^{-L/u};                                          */
+/* the normaliser C(beta,u,l)/u (App. B eq. normLumPDF) depends on theta only and cancels  */
+/* against the normalised selection integral exactly as for the Schechter model (R6), so  */
+/* the theta step uses g and the selection integral of g. With the Jacobian e^chi:         */
+/*   log f_obj = ln(1 - e^{-L/l}) + beta (chi - ln u) - L/u + chi,  L = e^chi (all chi).   */
+/* Measurement (Sec. 5.2, eq. sig-F): sigma(F)^2 = sigma0^2 + (alpha F)^2, and the member  */
+/* likelihood is the sampling density of Fhat_i as a function of F (the g(n_obs;F) form):  */
+/*   log l_i = -ln sigma(F) - (Fhat_i - F)^2/(2 sigma(F)^2),  F = e^chi q_i.               */
+/* Detection (eq. Fth, eq. key): F_th = nu sigma0/sqrt(1 - alpha^2),                      */
+/*   eta(F) = Phi((F - F_th)/sigma(F)).                                                    */
+/* Prior (Sec. 5.1): truncated Cauchy in beta on (-2, 0), log-flat in u, flat in l with    */
+/* l < u; in (beta, ln l, ln u): -ln(1 + beta^2) + ln l.                                   */
+/* consts: [0] sigma0, [1] alpha, [2] nu, [3] r_max, [4] n_L, [5] n_r, [6] ln(upper/u),    */
+/* [7] ln(lower/l) (the outer rule runs over t = ln L in [ln l + [7], ln u + [6]]).        */
+/* ------------------------------------------------------------------------- */
+double orc_bb1_threshold(double sigma0, double alpha, double nu) { return nu * sigma0 / sqrt(1.0 - alpha * alpha); }
+
+static double bb1_sigma2(double F, const double* consts) {
+  return consts[0] * consts[0] + (consts[1] * F) * (consts[1] * F);
+}
+/* ln(1 - e^{-x}) for x > 0 (Maechler's two branches: accurate for small and large x) */
+static double log1mexp(double x) {
+  return (x <= 0.69314718055994530942) ? log(-expm1(-x)) : log1p(-exp(-x));
+}
+static double bb1_logf_obj(double chi, const double* th) {
+  double L = exp(chi);
+  double lg = log1mexp(L / exp(th[1]));
+  if (lg == -INFINITY) return -INFINITY;
+  return lg + th[0] * (chi - th[2]) - L / exp(th[2]) + chi;
+}
+static double bb1_loglike(double chi, double fhat, double r, const double* consts) {
+  double F = exp(chi) * lf_q(r);
+  double s2 = bb1_sigma2(F, consts);
+  double res = fhat - F;
+  return -0.5 * log(s2) - (res * res) / (2.0 * s2);
+}
+static double bb1_logprior(const double* th) {
+  if (!(th[0] > -2.0 && th[0] < 0.0)) return -INFINITY;
+  if (!(th[1] < th[2])) return -INFINITY;
+  return -log(1.0 + th[0] * th[0]) + th[1];
+}
+double orc_bb1_detection(double F, const double* consts) {
+  double Fth = orc_bb1_threshold(consts[0], consts[1], consts[2]);
+  return phi_cdf((F - Fth) / sqrt(bb1_sigma2(F, consts)));
+}
+static double bb1_H(double L, const gl_rule* R, const double* consts) {
+  double rmax = consts[3];
+  ksum h = {0.0, 0.0};
+  for (int k = 0; k < R->nr; ++k) {
+    double r = 0.5 * rmax * (R->xr[k] + 1.0);
+    double wk = 0.5 * rmax * R->wr[k] * 3.0 * r * r / (rmax * rmax * rmax);
+    ks_add(&h, wk * orc_bb1_detection(L * lf_q(r), consts));
+  }
+  return ks_val(&h);
+}
+/* etabar(theta) = int g(L) H(L) dL: n_L-node rule in t = ln L on [ln l + consts[7],
+ * ln u + consts[6]] (integrand g(e^t) e^t H(e^t)) times the n_r-node rule of H in r. */
+static double bb1_etabar_rule(const double* th, const gl_rule* R, const double* consts) {
+  double a = th[1] + consts[7], b = th[2] + consts[6];
+  double half = 0.5 * (b - a), mid = 0.5 * (b + a);
+  ksum s = {0.0, 0.0};
+  for (int j = 0; j < R->nL; ++j) {
+    double t = half * R->xL[j] + mid;
+    double L = exp(t);
+    double gl = exp(log1mexp(L / exp(th[1])) + th[0] * (t - th[2]) - L / exp(th[2]) + t); /* g(e^t) e^t */
+    ks_add(&s, half * R->wL[j] * gl * bb1_H(L, R, consts));
+  }
+  return ks_val(&s);
+}
+double orc_bb1_etabar(const double* th, const double* consts) {
+  gl_rule R;
+  gl_rule_init(&R, (int)consts[4], (int)consts[5]);
+  double v = bb1_etabar_rule(th, &R, consts);
+  gl_rule_free(&R);
+  return v;
+}
+double orc_bb1_H(double L, const double* consts) {
+  gl_rule R;
+  gl_rule_init(&R, (int)consts[4], (int)consts[5]);
+  double v = bb1_H(L, &R, consts);
+  gl_rule_free(&R);
+  return v;
+}
+
 /* Multivariate normal, d = 3 (Sec. 3 with C_pop unknown): theta = (mu[3], lower-triangular
  * Cholesky factor L_C of C_pop packed row-major (L11, L21, L22, L31, L32, L33) with the
  * diagonal entries stored as logs). log f_obj = -|L_C^{-1}(chi - mu)|^2/2,
@@ -402,6 +491,7 @@ static double logf_obj(const problem* P, const double* chi, const double* th) {
   switch (P->model) {
     case ORC_NN1: return nn1_logf_obj(chi[0], th);
     case ORC_LF: return lf_logf_obj(chi[0], th);
+    case ORC_BB1: return bb1_logf_obj(chi[0], th);
     default: return mvn3_logf_obj(chi, th);
   }
 }
@@ -409,6 +499,7 @@ static double loglike(const problem* P, int64_t i, const double* chi) {
   switch (P->model) {
     case ORC_NN1: return nn1_loglike(chi[0], P->y[i], P->aux[i]);
     case ORC_LF: return lf_loglike(chi[0], P->y[i], P->aux[i], P->consts);
+    case ORC_BB1: return bb1_loglike(chi[0], P->y[i], P->aux[i], P->consts);
     default: return mvn3_loglike(chi, P->y + 3 * i, P->aux + 3 * i);
   }
 }
@@ -422,6 +513,7 @@ static double c_theta(const problem* P, const double* th) {
   switch (P->model) {
     case ORC_NN1: return nn1_c(th);
     case ORC_LF: return 0.0;
+    case ORC_BB1: return 0.0;
     default: return mvn3_c(th);
   }
 }
@@ -429,8 +521,17 @@ static double logprior(const problem* P, const double* th) {
   switch (P->model) {
     case ORC_NN1: return nn1_logprior(th, P->consts);
     case ORC_LF: return lf_logprior(th);
+    case ORC_BB1: return bb1_logprior(th);
     default: return 0.0;
   }
+}
+
+/* log f_obj(chi;theta) alone (the population term of the member target), for the pins. */
+double orc_logf_obj(int model, int d, const double* chi, const double* theta) {
+  problem P;
+  memset(&P, 0, sizeof(P));
+  P.model = model; P.d = d;
+  return logf_obj(&P, chi, theta);
 }
 
 /* Per-object log target at the current state (the quantity compared in parity). */
@@ -475,8 +576,11 @@ int orc_run(int model, int d, int p, int64_t n, const double* y, const double* a
   problem P;
   P.model = model; P.d = d; P.p = p; P.n = n; P.y = y; P.aux = aux; P.consts = consts;
   if (model == ORC_LF) gl_rule_init(&P.rule, (int)consts[3], (int)consts[4]);
+  if (model == ORC_BB1) gl_rule_init(&P.rule, (int)consts[4], (int)consts[5]);
+  const int has_rule = (model == ORC_LF || model == ORC_BB1);
 
-  if (model == ORC_LF && *etabar_cur == 0.0) *etabar_cur = lf_etabar_rule(theta, &P.rule, consts);
+  if (has_rule && *etabar_cur == 0.0)
+    *etabar_cur = (model == ORC_LF) ? lf_etabar_rule(theta, &P.rule, consts) : bb1_etabar_rule(theta, &P.rule, consts);
 
   int64_t total = n_burn + n_iter;
   int64_t rows = 0;
@@ -536,8 +640,9 @@ int orc_run(int model, int d, int p, int64_t n, const double* y, const double* a
         if (!off) {
           D = ks_val(&acc_sum);
           logalpha = D + (double)n * (c_theta(&P, th_prop) - c_theta(&P, theta)) + lpri_new - logprior(&P, theta);
-          if (model == ORC_LF) {
-            eb_new = lf_etabar_rule(th_prop, &P.rule, consts);
+          if (has_rule) {
+            eb_new = (model == ORC_LF) ? lf_etabar_rule(th_prop, &P.rule, consts)
+                                       : bb1_etabar_rule(th_prop, &P.rule, consts);
             logalpha -= (double)n * (log(eb_new) - log(*etabar_cur));
           }
         } else {
@@ -553,7 +658,7 @@ int orc_run(int model, int d, int p, int64_t n, const double* y, const double* a
       }
       if (acc) {
         for (int a = 0; a < p; ++a) theta[a] = th_prop[a];
-        if (model == ORC_LF) *etabar_cur = eb_new;
+        if (has_rule) *etabar_cur = eb_new;
         ++tacc;
       }
       if (prm.adapt_theta) orc_ram_update(p, S_theta, U, alpha, prm.theta_target_accept, eta);
@@ -569,6 +674,6 @@ int orc_run(int model, int d, int p, int64_t n, const double* y, const double* a
   if (rows_out) *rows_out = rows;
   if (member_accepts) *member_accepts += macc;
   if (theta_accepts) *theta_accepts += tacc;
-  if (model == ORC_LF) gl_rule_free(&P.rule);
+  if (has_rule) gl_rule_free(&P.rule);
   return 0;
 }

@@ -17,6 +17,8 @@ Workloads (all numpy ``Generator(PCG64(seed))``):
   ``detect_frac`` of the population is detected.
 - ``mvn3_data``: d = 3 normal population with condition-number-20 covariance and
   heteroscedastic diagonal measurement errors (Sec. 3 with unknown C_pop).
+- ``bb1_data``: the paper's own simulation (Sec. 5.1-5.2): BB1 luminosity function, r ~ r^2 on
+  [0, r_max], flux-dependent measurement error sigma(F), detection at nu = 5 times the error.
 """
 from __future__ import annotations
 
@@ -137,6 +139,95 @@ def lf_data(n: int, beta: float = -1.2, L_star: float = 1e10, L_low: float = 1e8
         got += idx.size
     return LFData(fhat=np.concatenate(fh), r=np.concatenate(rr), L_true=np.concatenate(LL), F_th=F_th,
                   sigma_F=sigma_F, r_max=r_max, beta=beta, L_star=L_star, L_low=L_low, n_drawn=drawn)
+
+
+# ----------------------------------------------------------------- BB1 -----
+@dataclass
+class BB1Data:
+    fhat: np.ndarray
+    r: np.ndarray
+    L_true: np.ndarray
+    sigma0: float
+    alpha: float
+    nu: float
+    F_th: float
+    r_max: float
+    beta: float
+    l: float
+    u: float
+    n_drawn: int
+
+
+def _bb1_draw(g: np.random.Generator, m: int, beta: float, l: float, u: float) -> np.ndarray:
+    """m draws of L with density ~ (1 - e^{-L/l}) (L/u)^beta e^{-L/u} (the BB1 form), -2 < beta < -1,
+    by rejection from the envelope min(1, L/l) L^beta: a power law L^(beta+1) on (0, l) and a Pareto
+    L^beta on [l, inf), accepted with probability (1 - e^{-L/l})/min(1, L/l) * e^{-L/u} (>= 0.63 e^{-L/u})."""
+    assert -2.0 < beta < -1.0
+    mA = l ** (beta + 1.0) / (beta + 2.0)    # int_0^l L^(beta+1)/l dL
+    mB = l ** (beta + 1.0) / (-beta - 1.0)   # int_l^inf L^beta dL
+    out = np.empty(0)
+    while out.size < m:
+        k = max(2 * (m - out.size), 4096)
+        first = g.random(k) < mA / (mA + mB)
+        v = 1.0 - g.random(k)  # (0, 1]
+        with np.errstate(over="ignore", divide="ignore"):
+            L = np.where(first, l * v ** (1.0 / (beta + 2.0)), l * v ** (1.0 / (beta + 1.0)))
+            x = L / l
+            ratio = np.where(x < 1.0, -np.expm1(-x) / x, -np.expm1(-x)) * np.exp(-L / u)
+        keep = np.isfinite(L) & (L > 0.0) & (g.random(k) < ratio)
+        out = np.concatenate([out, L[keep]])
+    return out[:m]
+
+
+def bb1_threshold(sigma0: float, alpha: float, nu: float) -> float:
+    """F_th = nu sigma0/sqrt(1 - alpha^2): the flux whose estimate is nu times its error (Sec. 5.2)."""
+    return nu * sigma0 / math.sqrt(1.0 - alpha * alpha)
+
+
+def bb1_data(n: int, beta: float = -1.5, l: float = 1e8, u: float = 1e10, r_max: float = 1.0, alpha: float = 1e-2,
+             nu: float = 5.0, seed: int = 1004) -> BB1Data:
+    """Detected catalog of the paper's BB1 simulation (Sec. 5.1-5.2): L from the BB1 form, r with density
+    ~ r^2 on [0, r_max], F = L/(4 pi r^2), Fhat = F + sigma(F) N(0, 1) with sigma(F)^2 = sigma0^2 + (alpha F)^2,
+    kept iff Fhat > F_th = nu sigma0/sqrt(1 - alpha^2). sigma0 is set, as the paper chooses it, so that a
+    source with L = 20 u at r = r_max sits at the threshold: F_th = 20 u/(4 pi r_max^2). Units: L in solar
+    luminosities, r in Gpc, fluxes in L_sun/Gpc^2."""
+    F_th = 20.0 * u / (4.0 * math.pi * r_max * r_max)
+    sigma0 = F_th * math.sqrt(1.0 - alpha * alpha) / nu
+    g = _rng(seed)
+    fh, rr, LL = [], [], []
+    got, drawn = 0, 0
+    while got < n:
+        m = 2_000_000
+        L = _bb1_draw(g, m, beta, l, u)
+        r = np.maximum(r_max * g.random(m) ** (1.0 / 3.0), 1e-300)
+        F = L / (4.0 * math.pi * r * r)
+        sig = np.sqrt(sigma0 * sigma0 + (alpha * F) ** 2)
+        fhat = F + sig * g.standard_normal(m)
+        idx = np.nonzero(fhat > F_th)[0]
+        need = n - got
+        if idx.size > need:
+            drawn += int(idx[need - 1]) + 1
+            idx = idx[:need]
+        else:
+            drawn += m
+        fh.append(fhat[idx]); rr.append(r[idx]); LL.append(L[idx])
+        got += idx.size
+    return BB1Data(fhat=np.concatenate(fh), r=np.concatenate(rr), L_true=np.concatenate(LL), sigma0=sigma0,
+                   alpha=alpha, nu=nu, F_th=F_th, r_max=r_max, beta=beta, l=l, u=u, n_drawn=drawn)
+
+
+def bb1_settings(data: BB1Data, nL: int = 1024, nr: int = 1024, ln_upper: float = math.log(60.0),
+                 ln_lower: float = -40.0):
+    """theta_init (truth: beta, ln l, ln u), theta_prop_scale, consts of the BB1 model."""
+    theta0 = np.array([data.beta, math.log(data.l), math.log(data.u)])
+    scale = np.array([0.01, 0.01, 0.01])
+    consts = np.array([data.sigma0, data.alpha, data.nu, data.r_max, float(nL), float(nr), ln_upper, ln_lower])
+    return theta0, scale, consts
+
+
+def bb1_chi_init(data: BB1Data) -> np.ndarray:
+    """Default start: chi_i = ln(4 pi r_i^2 max(Fhat_i, F_th))."""
+    return np.log(4.0 * math.pi * data.r * data.r * np.maximum(data.fhat, data.F_th))
 
 
 # ----------------------------------------------------------------- MVN3 ----

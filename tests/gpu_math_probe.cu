@@ -27,3 +27,52 @@ extern "C" int probe_fp64_math(int which, const double* x_host, double* y_host, 
   cudaFree(T);
   return e == cudaSuccess ? 0 : -2;
 }
+
+// The sampler's Philox4x32-10 block next to cuRAND's Philox4_32_10 generator (its device API),
+// for the same key and 128-bit counter: curand_init(seed = key1:key0, subsequence = c3:c2,
+// offset = 4 (c1:c0)) puts the generator at counter (c0, c1, c2, c3) (c1 < 2^30, so that the
+// offset fits 64 bits), and curand4 returns that block.
+#include <cstdint>
+#include <curand_kernel.h>
+
+#include "device_common.cuh"
+
+namespace {
+__global__ void philox_kernel(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* mine, uint32_t* ref, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+  const uint4 m = chm::philox4x32_10(c, k0, k1);
+  mine[4 * i] = m.x;
+  mine[4 * i + 1] = m.y;
+  mine[4 * i + 2] = m.z;
+  mine[4 * i + 3] = m.w;
+  curandStatePhilox4_32_10_t st;
+  const unsigned long long seed = (static_cast<unsigned long long>(k1) << 32) | k0;
+  const unsigned long long subseq = (static_cast<unsigned long long>(c.w) << 32) | c.z;
+  const unsigned long long off = ((static_cast<unsigned long long>(c.y) << 32) | c.x) * 4ull;
+  curand_init(seed, subseq, off, &st);
+  const uint4 r = curand4(&st);
+  ref[4 * i] = r.x;
+  ref[4 * i + 1] = r.y;
+  ref[4 * i + 2] = r.z;
+  ref[4 * i + 3] = r.w;
+}
+}  // namespace
+
+extern "C" int probe_philox(const uint32_t* ctr_host, uint32_t k0, uint32_t k1, uint32_t* mine_host, uint32_t* ref_host,
+                            int n) {
+  uint32_t *ctr = nullptr, *mine = nullptr, *ref = nullptr;
+  if (cudaMalloc(&ctr, sizeof(uint32_t) * 4 * n) != cudaSuccess) return -1;
+  if (cudaMalloc(&mine, sizeof(uint32_t) * 4 * n) != cudaSuccess) return -1;
+  if (cudaMalloc(&ref, sizeof(uint32_t) * 4 * n) != cudaSuccess) return -1;
+  cudaMemcpy(ctr, ctr_host, sizeof(uint32_t) * 4 * n, cudaMemcpyHostToDevice);
+  philox_kernel<<<(n + 127) / 128, 128>>>(ctr, k0, k1, mine, ref, n);
+  cudaMemcpy(mine_host, mine, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost);
+  cudaMemcpy(ref_host, ref, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost);
+  const cudaError_t e = cudaGetLastError();
+  cudaFree(ctr);
+  cudaFree(mine);
+  cudaFree(ref);
+  return e == cudaSuccess ? 0 : -2;
+}

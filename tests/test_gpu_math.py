@@ -1,4 +1,5 @@
-"""The sampler's table-driven FP64 exp and log (Tang's methods) against the host libm.
+"""The sampler's table-driven FP64 exp and log (Tang's methods) against the host libm, and its
+Philox4x32-10 against cuRAND's generator.
 
 The host's exp and log are within 0.52 ulp of the exact values; the device versions must
 stay within 2.5 ulp of them (so within ~3 ulp of exact) on their ranges of use (exp: the
@@ -23,16 +24,20 @@ def probe(tmp_path_factory):
     out = tmp_path_factory.mktemp("probe") / "libprobe.so"
     subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-shared",
                            "-Xcompiler", "-fPIC", f"-I{os.path.join(ROOT, 'paper_2105_08026_gb300', 'csrc')}",
+                           f"-I{os.path.join(ROOT, 'include')}",
                            "-o", str(out), os.path.join(HERE, "gpu_math_probe.cu")])
     L = ctypes.CDLL(str(out))
     dp = ctypes.POINTER(ctypes.c_double)
     L.probe_fp64_math.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int]
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    L.probe_philox.argtypes = [u32p, ctypes.c_uint32, ctypes.c_uint32, u32p, u32p, ctypes.c_int]
 
     def run(which, x):
         x = np.ascontiguousarray(x, dtype=np.float64)
         y = np.zeros_like(x)
         assert L.probe_fp64_math(which, x.ctypes.data_as(dp), y.ctypes.data_as(dp), x.size) == 0
         return y
+    run.lib = L
     return run
 
 
@@ -68,3 +73,25 @@ def test_log_table_within_2ulp(probe):
     wide = np.exp(g.uniform(-700, 700, 2000))
     err = _ulp_err(probe(1, wide), np.array([math.log(v) for v in wide]))
     assert err.max() <= 2.5
+
+
+def test_philox_matches_curand(probe):
+    """Every word of the device Philox4x32-10 block equals cuRAND's Philox4_32_10 output for the
+    same key and counter (random counters, the counter layouts the sampler uses, extremes)."""
+    L = probe.lib
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    g = np.random.default_rng(11)
+    # cuRAND reaches counter word 1 through a 64-bit offset of 4 (c1:c0), so c1 < 2^30 here (the
+    # sampler's word 1 is its stream, 0..2)
+    ctr = [np.array([g.integers(0, 2**32), g.integers(0, 2**30), g.integers(0, 2**32), g.integers(0, 2**32)],
+                    dtype=np.uint64) for _ in range(4000)]
+    ctr += [np.array(c, dtype=np.uint64) for c in ([0, 0, 0, 0], [0xFFFFFFFF, 0x3FFFFFFF, 0xFFFFFFFF, 0xFFFFFFFF],
+                                                   [1, 0, 299999, 5001], [3, 1, 0, 77], [0, 2, 999999, 2999],
+                                                   [0xFFFFFFFF, 0, 0, 1])]
+    c = np.ascontiguousarray(np.stack(ctr).astype(np.uint32))
+    n = c.shape[0]
+    for k0, k1 in ((1, 0), (2, 0), (0xDEADBEEF, 0x12345678), (0xFFFFFFFF, 0xFFFFFFFF)):
+        mine = np.zeros((n, 4), dtype=np.uint32)
+        ref = np.zeros((n, 4), dtype=np.uint32)
+        assert L.probe_philox(c.ctypes.data_as(u32p), k0, k1, mine.ctypes.data_as(u32p), ref.ctypes.data_as(u32p), n) == 0
+        assert np.array_equal(mine, ref), (k0, k1, np.argwhere(mine != ref)[:3])
