@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--serve-pool", type=int, default=48)
     ap.add_argument("--cpu-sweeps", type=int, default=8)
     ap.add_argument("--no-mvn3", action="store_true")
+    ap.add_argument("--no-bb1", action="store_true")
+    ap.add_argument("--bb1-sweeps", type=int, default=1000)
     ap.add_argument("--mvn3-sweeps", type=int, default=3000)
     return ap.parse_args()
 
@@ -300,6 +302,42 @@ def run_mvn3(args, cudahm, stream, device, flush, peak_fp64):
     return out
 
 
+def run_bb1(args, cudahm, stream, device, flush, peak_fp64):
+    """The paper's own simulation model (BB1 luminosity function, flux-dependent measurement error,
+    detection at nu = 5 times the error; Sec. 5.1-5.2) at its case-study size, N = 1e5 detected
+    objects, FP64, 1024 x 1024 selection rule with sigma(F) inside Phi; one run of --bb1-sweeps
+    sweeps, inputs resident in HBM, L2 flushed before it, CUDA events on the sampler's stream."""
+    import torch
+    from paper_2105_08026_gb300 import synth
+    data = synth.bb1_data(100_000, seed=1004)
+    theta0, scale, consts = synth.bb1_settings(data)
+    n = data.fhat.size
+    s = cudahm.Sampler(cudahm.BB1, n, theta_init=theta0, theta_prop_scale=scale, model_consts=consts, seed=5,
+                       device=device, stream=stream.cuda_stream, use_torch_allocator=True)
+    y_dev = torch.from_numpy(data.fhat).cuda()
+    r_dev = torch.from_numpy(data.r).cuda()
+    cudahm.cudahm_set_data_device(s.h, y_dev.data_ptr(), r_dev.data_ptr(), n)
+    if args.warmup > 0:
+        s.run(min(args.warmup, 200), 0)
+    K = args.bb1_sweeps
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rows = s.run(0, K, 1)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = s.stats()
+    s.close()
+    return {"value": n * K / (ms * 1e-3), "unit": "object-updates/s", "ms_per_step": ms / K, "n": n, "steps": K,
+            "theta_mean": rows.mean(axis=0).tolist(), "theta_true": theta0.tolist(),
+            "launch_shape": [st.grid_blocks, st.block_threads, st.objects_per_thread],
+            "workload": "BB1 luminosity function (paper Sec. 5), N=1e5, FP64, 1024x1024 rule with sigma(F)",
+            "dtype": "f64"}
+
+
 def run_served(args, cudahm, device):
     """Poisson request stream (rate 20/s for --serve-seconds) into the continuous-batching server:
     each request is NN1 or LF with probability 1/2, N log-uniform on [1e3, 3e5], 5000 sweeps,
@@ -463,6 +501,10 @@ def run_cuda(args):
     if not args.no_mvn3 and rank == 0:
         mvn3 = run_mvn3(args, cudahm, stream, local, flush, peak)
 
+    bb1 = None
+    if not args.no_bb1 and rank == 0:
+        bb1 = run_bb1(args, cudahm, stream, local, flush, peak)
+
     # e2e through the public API with host buffers (every iteration: H2D data, run, D2H samples)
     e2e = None
     if not args.no_e2e:
@@ -517,7 +559,7 @@ def run_cuda(args):
                        "member state register-resident within a launch", "timed_launches": R,
                        "launch_shape": [st.grid_blocks, st.block_threads, st.objects_per_thread]},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
-            "fp32_bulk": fp32, "batched_fp32": batched, "served_fp32": served, "mvn3": mvn3}
+            "fp32_bulk": fp32, "batched_fp32": batched, "served_fp32": served, "mvn3": mvn3, "bb1": bb1}
     print(json.dumps(line), flush=True)
     s.close()
     if ws > 1:

@@ -74,8 +74,17 @@ typedef struct cudahm* cudahm_t;
  *       prior -ln(1 + beta^2) + ln L_low on -2 < beta < 0, L_low < L*.
  *       consts = {sigma_F, F_th, r_max, n_L, n_r, ln(upper/L*)}: the selection integral
  *       uses an n_L-node Gauss-Legendre rule in ln L on [ln L_low, ln L* + consts[5]] times
- *       an n_r-node rule in r on [0, r_max] (n_L, n_r <= 4096). */
-typedef enum { CUDAHM_NN1 = 0, CUDAHM_MVN3 = 1, CUDAHM_LF = 2 } cudahm_model;
+ *       an n_r-node rule in r on [0, r_max] (n_L, n_r <= 4096).
+ *  BB1  the paper's simulation model (Sec. 5.1-5.2, App. B), d = 1, chi = ln L,
+ *       theta = (beta, ln l, ln u), p = 3, FP64 only:
+ *       log f = ln(1 - e^(-L/l)) + beta (chi - ln u) - L/u + chi (all chi; BB1 form, its normaliser
+ *       C(beta,u,l)/u cancels against the normalised selection integral),
+ *       log l_i = -ln sigma(F) - (Fhat_i - F)^2/(2 sigma(F)^2), F = e^chi/(4 pi r_i^2),
+ *       sigma(F)^2 = sigma0^2 + (alpha F)^2 (eq. sig-F), detection F_th = nu sigma0/sqrt(1 - alpha^2)
+ *       (eq. Fth), eta(F) = Phi((F - F_th)/sigma(F)); prior -ln(1 + beta^2) + ln l on
+ *       -2 < beta < 0, l < u. consts = {sigma0, alpha, nu, r_max, n_L, n_r, ln(upper/u),
+ *       ln(lower/l)}: the outer rule runs over ln L in [ln l + consts[7], ln u + consts[6]]. */
+typedef enum { CUDAHM_NN1 = 0, CUDAHM_MVN3 = 1, CUDAHM_LF = 2, CUDAHM_BB1 = 3 } cudahm_model;
 
 /* FP64: all arithmetic in binary64.
  * FP32 (bulk form): the member step (proposal, member log target, accept) and the theta
@@ -144,10 +153,10 @@ void cudahm_config_init(cudahm_config* cfg, int32_t model, int64_t n);
 int cudahm_create(const cudahm_config* cfg, cudahm_t* out);
 
 /* Member data, N entries each (N*d for MVN3, member-major; copied):
- *   NN1: y = y_i, aux = sigma_i (> 0);   LF: y = Fhat_i, aux = r_i (> 0);
+ *   NN1: y = y_i, aux = sigma_i (> 0);   LF, BB1: y = Fhat_i, aux = r_i (> 0);
  *   MVN3: y = y_i[3], aux = s_i[3] (> 0, the measurement sd of each component).
- * Resets the latents to the default start (NN1, MVN3: chi_i = y_i; LF: chi_i = ln(4 pi r_i^2
- * max(Fhat_i, F_th)), raised to ln L_low + 1e-6 if below), every S_i to
+ * Resets the latents to the default start (NN1, MVN3: chi_i = y_i; LF, BB1: chi_i = ln(4 pi r_i^2
+ * max(Fhat_i, F_th)), for LF raised to ln L_low + 1e-6 if below), every S_i to
  * chi_init_scale * I, theta to theta_init, S_theta to diag(theta_prop_scale), and the
  * sweep counter and sample buffer to zero. */
 int cudahm_set_data(cudahm_t h, const double* y_host, const double* aux_host, int64_t n);
@@ -183,11 +192,12 @@ int cudahm_get_stats(cudahm_t h, cudahm_stats* s);
  * Writes N doubles to lp_host. Evaluated by a device kernel in the handle's precision. */
 int cudahm_eval_logdens(cudahm_t h, const double* theta_host, double* lp_host);
 
-/* LF only: the selection integral etabar(theta) of the handle's rule at the given theta. */
+/* LF and BB1: the selection integral etabar(theta) of the handle's rule at the given theta. */
 int cudahm_eval_etabar(cudahm_t h, const double* theta_host, double* out);
 
-/* LF only: detection efficiency eta(F) = Phi((F - F_th)/sigma_F) (Sec. 5.2, eq. key) for n
- * fluxes, evaluated by the same device routine the selection integral uses. */
+/* LF and BB1: detection efficiency eta(F) = Phi((F - F_th)/sigma) (Sec. 5.2, eq. key; sigma_F for
+ * LF, sigma(F) for BB1) for n fluxes, evaluated by the same device routine the selection integral
+ * uses. */
 int cudahm_eval_detection(cudahm_t h, const double* F_host, double* eta_host, int64_t n);
 
 /* Lockstep trace of the first T = min(trace_sweeps, sweeps of the last run) sweeps of the

@@ -343,7 +343,7 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
   __shared__ long long s_rows_written, s_tacc, s_k0, s_off, s_ns;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int p = a.p;
-  const bool is_lf = (a.model == CUDAHM_LF);
+  constexpr bool is_lf = M::kRule;  // the model has a selection integral (LF, BB1)
   double* s_math = s_dyn;
   double* s_phi = s_dyn + kMathWords;
   const SegTab tab = segtab_carve(s_phi + kPhiWords, R);
@@ -419,16 +419,16 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
                       tro);
     }
     // a6: the rule's segments of this block, R at a time through the shared table
-    if constexpr (std::is_same<M, LF>::value) {
+    if constexpr (M::kRule) {
       if (prior_ok) {
         const ThetaC tcp = s_tcp;
         for (int t0 = 0; t0 < nseg; t0 += R) {
           const int cnt = min(R, nseg - t0);
-          for (int q = tid; q < cnt; q += blockDim.x) lf_segment_row(tcp, a, lb, nb, t0 + q, q, tab, s_math);
+          for (int q = tid; q < cnt; q += blockDim.x) lf_segment_row<M>(tcp, a, lb, nb, t0 + q, q, tab, s_math);
           __syncthreads();
           if (wid == 0) lf_segment_scan(cnt, tab);
           __syncthreads();
-          lf_segment_pairs(a, cnt, tab, s_phi, xe, fe);
+          lf_segment_pairs<M>(a, cnt, tab, s_phi, xe, fe);
           __syncthreads();
         }
       }
@@ -581,7 +581,10 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const SweepArgs* __restri
     run_population<NN1, F32>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
   else if (s_args.model == CUDAHM_LF)
     run_population<LF, F32>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
-  else
+  else if (s_args.model == CUDAHM_BB1) {
+    if constexpr (!F32)  // FP64 form only
+      run_population<BB1, false>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
+  } else
     run_population<MVN3, F32>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
 }
 

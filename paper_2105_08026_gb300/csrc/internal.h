@@ -24,9 +24,14 @@ struct ModelConsts {
   double lo, hi;        // NN1: prior range of ln tau
   double inv2sig2;      // LF: 1/(2 sigma_F^2)
   double cth;           // LF: F_th / sigma_F
-  double F_th;          // LF
-  double ln_upper;      // LF: ln(upper/L*)
+  double F_th;          // LF, BB1
+  double ln_upper;      // LF: ln(upper/L*); BB1: ln(upper/u)
   double chi_init_scale;
+  // BB1
+  double s0sq;          // sigma0^2
+  double alpha;         // slope of the flux-dependent error, sigma(F)^2 = sigma0^2 + (alpha F)^2
+  double F_pre;         // flux above which Phi((F - F_th)/sigma(F)) > Phi(8.5) (rule prefix); inf if none
+  double ln_lower;      // ln(lower/l)
 };
 
 struct SweepArgs {
@@ -121,8 +126,8 @@ cudaError_t launch_prefix_weights(int nr, const double* Wr, double* cw, cudaStre
 cudaError_t launch_math_table(double* t, cudaStream_t st);
 int math_table_words();
 int phi_table_words();
-cudaError_t launch_detection(long long n, const double* F, double F_th, double sigma_F, const double* coef,
-                             double* out, cudaStream_t st);
+cudaError_t launch_detection(int model, long long n, const double* F, const ModelConsts& mc, double sigma_F,
+                             const double* coef, double* out, cudaStream_t st);
 cudaError_t sweep_set_smem(int model, int K, bool f32, int smem_bytes);
 cudaError_t launch_prepare(int model, long long n, const double* y_raw, const double* aux_raw, double* y, double* aux,
                            double* chi, double* S, const ModelConsts& mc, const double* theta, int* bad,

@@ -52,7 +52,11 @@ int chm::record_error(int code, const char* msg) { return fail(code, "%s", msg);
 
 namespace {
 
-int model_p(int m) { return m == CUDAHM_NN1 ? 2 : (m == CUDAHM_LF ? 3 : 9); }
+int model_p(int m) { return m == CUDAHM_NN1 ? 2 : ((m == CUDAHM_LF || m == CUDAHM_BB1) ? 3 : 9); }
+// models with a selection integral, and the positions of their rule sizes in model_consts
+bool has_rule(int m) { return m == CUDAHM_LF || m == CUDAHM_BB1; }
+int rule_nL(const cudahm_config& c) { return static_cast<int>(c.model_consts[c.model == CUDAHM_BB1 ? 4 : 3]); }
+int rule_nr(const cudahm_config& c) { return static_cast<int>(c.model_consts[c.model == CUDAHM_BB1 ? 5 : 4]); }
 
 constexpr long long kChunk = 4096;  // sweeps per persistent launch
 
@@ -157,7 +161,7 @@ int validate(const cudahm_config* c) {
   if (!c) return fail(CUDAHM_EINVAL, "config is NULL");
   if (c->abi_version != CUDAHM_ABI_VERSION)
     return fail(CUDAHM_EINVAL, "abi_version %u != %u", c->abi_version, CUDAHM_ABI_VERSION);
-  if (c->model != CUDAHM_NN1 && c->model != CUDAHM_LF && c->model != CUDAHM_MVN3)
+  if (c->model != CUDAHM_NN1 && c->model != CUDAHM_LF && c->model != CUDAHM_MVN3 && c->model != CUDAHM_BB1)
     return fail(CUDAHM_EINVAL, "unknown model %d", c->model);
   if (c->precision != CUDAHM_FP64 && c->precision != CUDAHM_FP32)
     return fail(CUDAHM_EINVAL, "unknown precision %d", c->precision);
@@ -199,6 +203,16 @@ int validate(const cudahm_config* c) {
     if (!(k[5] > 0.0)) return fail(CUDAHM_EINVAL, "LF upper limit ln(upper/L*) must be > 0");
     const double* t = c->theta_init;
     if (!(t[0] > -2.0 && t[0] < 0.0 && t[2] < t[1])) return fail(CUDAHM_EINVAL, "theta_init outside the LF prior");
+  } else if (c->model == CUDAHM_BB1) {
+    if (c->precision != CUDAHM_FP64) return fail(CUDAHM_EUNSUPPORTED, "BB1 has the FP64 form only");
+    if (!(k[0] > 0.0) || !(k[1] >= 0.0 && k[1] < 1.0) || !(k[2] > 0.0) || !(k[3] > 0.0))
+      return fail(CUDAHM_EINVAL, "BB1 needs sigma0 > 0, 0 <= alpha < 1, nu > 0, r_max > 0");
+    const double nL = k[4], nr = k[5];
+    if (!(nL >= 1 && nL <= 4096 && nL == std::floor(nL)) || !(nr >= 1 && nr <= 4096 && nr == std::floor(nr)))
+      return fail(CUDAHM_EINVAL, "BB1 rule sizes must be integers in [1, 4096]");
+    if (!(k[6] > 0.0) || !(k[7] < 0.0)) return fail(CUDAHM_EINVAL, "BB1 rule limits need ln(upper/u) > 0 > ln(lower/l)");
+    const double* t = c->theta_init;
+    if (!(t[0] > -2.0 && t[0] < 0.0 && t[1] < t[2])) return fail(CUDAHM_EINVAL, "theta_init outside the BB1 prior");
   }
   return CUDAHM_OK;
 }
@@ -208,11 +222,10 @@ int choose_shape(cudahm* h) {
   h->block = block;
   const long long n = h->n;
   const int model = h->cfg.model;
-  const bool lf = (model == CUDAHM_LF);
+  const bool lf = has_rule(model);
   const bool f32 = (h->cfg.precision == CUDAHM_FP32);
-  // LF: segments of 128 inner nodes, G = n_L * ceil(n_r / 128), dealt round-robin to the blocks
-  const long long G = lf ? static_cast<long long>(h->cfg.model_consts[3]) *
-                               ((static_cast<long long>(h->cfg.model_consts[4]) + 127) / 128)
+  // selection rule: segments of 128 inner nodes, G = n_L * ceil(n_r / 128), dealt round-robin
+  const long long G = lf ? static_cast<long long>(rule_nL(h->cfg)) * ((static_cast<long long>(rule_nr(h->cfg)) + 127) / 128)
                          : 0;
   const int Ks[4] = {1, 2, 4, 8};
   // the d = 3 model always streams its member state through the batched kernel
@@ -281,8 +294,8 @@ SweepArgs base_args(cudahm* h) {
   a.cw = h->cw;
   a.math_tab = h->math_tab;
   a.pub = h->pub;
-  a.nL = h->cfg.model == CUDAHM_LF ? static_cast<int>(h->cfg.model_consts[3]) : 0;
-  a.nr = h->cfg.model == CUDAHM_LF ? static_cast<int>(h->cfg.model_consts[4]) : 0;
+  a.nL = has_rule(h->cfg.model) ? rule_nL(h->cfg) : 0;
+  a.nr = has_rule(h->cfg.model) ? rule_nr(h->cfg) : 0;
   a.rows_smem = h->rows_smem;
   a.mpb = h->mpb;
   a.timeout_ns = h->cfg.barrier_timeout_ns > 0 ? h->cfg.barrier_timeout_ns : 2000000000ll;
@@ -300,9 +313,9 @@ SweepArgs base_args(cudahm* h) {
 double pop_cost(const cudahm* h) {
   const bool f32 = h->cfg.precision == CUDAHM_FP32;
   double c = 3000.0 + static_cast<double>(h->n) * (h->d == 3 ? (f32 ? 80.0 : 260.0) : (f32 ? 20.0 : 120.0));
-  if (h->cfg.model == CUDAHM_LF) {
-    const double nL = h->cfg.model_consts[3], nr = h->cfg.model_consts[4];
-    c += 0.3 * nL * nr * 17.0 + nL * std::ceil(nr / 128.0) * 70.0;
+  if (has_rule(h->cfg.model)) {
+    const double nL = rule_nL(h->cfg), nr = rule_nr(h->cfg);
+    c += 0.3 * nL * nr * (h->cfg.model == CUDAHM_BB1 ? 26.0 : 17.0) + nL * std::ceil(nr / 128.0) * 70.0;
   }
   return c;
 }
@@ -424,6 +437,11 @@ void cudahm_config_init(cudahm_config* cfg, int32_t model, int64_t n) {
     cfg->model_consts[3] = 1024;
     cfg->model_consts[4] = 1024;
     cfg->model_consts[5] = std::log(60.0);
+  } else if (model == CUDAHM_BB1) {
+    cfg->model_consts[4] = 1024;
+    cfg->model_consts[5] = 1024;
+    cfg->model_consts[6] = std::log(60.0);
+    cfg->model_consts[7] = -40.0;
   }
   cfg->device = 0;
   cfg->debug_skip_barrier_cta = -1;
@@ -471,14 +489,28 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
   // model constants
   const double* k = cfg->model_consts;
   h->mc.chi_init_scale = cfg->chi_init_scale;
+  h->mc.F_pre = INFINITY;
   if (cfg->model == CUDAHM_NN1) {
     h->mc.lo = k[0];
     h->mc.hi = k[1];
-  } else {
+  } else if (cfg->model == CUDAHM_LF) {
     h->mc.inv2sig2 = 1.0 / (2.0 * k[0] * k[0]);
     h->mc.cth = k[1] / k[0];
     h->mc.F_th = k[1];
     h->mc.ln_upper = k[5];
+  } else if (cfg->model == CUDAHM_BB1) {
+    const double s0 = k[0], al = k[1], nu = k[2];
+    h->mc.s0sq = s0 * s0;
+    h->mc.alpha = al;
+    h->mc.F_th = nu * s0 / std::sqrt(1.0 - al * al);  // eq. Fth
+    // F where (F - F_th)/sigma(F) = 8.5: (1 - 72.25 alpha^2) F^2 - 2 F_th F + F_th^2 - 72.25 sigma0^2 = 0
+    const double A = 1.0 - 72.25 * al * al;
+    if (A > 0.0) {
+      const double Ft = h->mc.F_th;
+      h->mc.F_pre = (Ft + std::sqrt(72.25 * (al * al * Ft * Ft + A * s0 * s0))) / A;
+    }
+    h->mc.ln_upper = k[6];
+    h->mc.ln_lower = k[7];
   }
   int rc = choose_shape(h);
   if (rc != CUDAHM_OK) return bail(rc);
@@ -498,8 +530,10 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
       (rc = alloc_into(h, &h->pub, kPubWords)) ||
       (rc = alloc_into(h, &h->tab_eta, kChunk)))
     return bail(rc);
-  if (cfg->model == CUDAHM_LF) {
-    const int nL = static_cast<int>(k[3]), nr = static_cast<int>(k[4]);
+  if (has_rule(cfg->model)) {
+    const int nL = rule_nL(*cfg), nr = rule_nr(*cfg);
+    const bool bb1 = cfg->model == CUDAHM_BB1;
+    const double r_max = bb1 ? k[3] : k[2], sigma_F = bb1 ? 1.0 : k[0];  // BB1 keeps q_k itself
     if ((rc = alloc_into(h, &h->xL, nL)) || (rc = alloc_into(h, &h->wL, nL)) || (rc = alloc_into(h, &h->xr, nr)) ||
         (rc = alloc_into(h, &h->wr, nr)) || (rc = alloc_into(h, &h->qs, nr)) || (rc = alloc_into(h, &h->Wr, nr)) ||
         (rc = alloc_into(h, &h->eb_partials, 4ull * h->eb_grid)) ||
@@ -510,7 +544,7 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
       return bail(fail(CUDAHM_ECUDA, "normal-CDF table set-up failed: %s", cudaGetErrorString(cudaGetLastError())));
     if (launch_gauss_legendre(nL, h->xL, h->wL, h->stream) != cudaSuccess ||
         launch_gauss_legendre(nr, h->xr, h->wr, h->stream) != cudaSuccess ||
-        launch_lf_inner(nr, h->xr, h->wr, k[2], k[0], h->qs, h->Wr, h->stream) != cudaSuccess ||
+        launch_lf_inner(nr, h->xr, h->wr, r_max, sigma_F, h->qs, h->Wr, h->stream) != cudaSuccess ||
         launch_prefix_weights(nr, h->Wr, h->cw, h->stream) != cudaSuccess)
       return bail(fail(CUDAHM_ECUDA, "quadrature set-up failed: %s", cudaGetErrorString(cudaGetLastError())));
   }
@@ -605,7 +639,7 @@ int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
   TRY(ensure_trace(h, T));
   CU(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
   CU(cudaEventRecord(h->ev0, h->stream));
-  if (h->cfg.model == CUDAHM_LF && !h->etabar_valid) {
+  if (has_rule(h->cfg.model) && !h->etabar_valid) {
     // selection integral at the current theta, once per chain (kept on the device afterwards)
     char* base = reinterpret_cast<char*>(h->chain);
     TRY(compute_etabar_into(h, reinterpret_cast<const double*>(base + offsetof(ChainState, theta)),
@@ -763,7 +797,7 @@ int cudahm_eval_logdens(cudahm_t h, const double* theta_host, double* lp_host) {
 
 int cudahm_eval_etabar(cudahm_t h, const double* theta_host, double* out) {
   if (!h || !theta_host || !out) return fail(CUDAHM_EINVAL, "NULL argument");
-  if (h->cfg.model != CUDAHM_LF) return fail(CUDAHM_EINVAL, "etabar exists only for the LF model");
+  if (!has_rule(h->cfg.model)) return fail(CUDAHM_EINVAL, "etabar exists only for the LF and BB1 models");
   CU(cudaSetDevice(h->cfg.device));
   CU(cudaMemcpyAsync(h->theta_dev, theta_host, sizeof(double) * h->p, cudaMemcpyHostToDevice, h->stream));
   TRY(compute_etabar_into(h, h->theta_dev, h->eval_out));
@@ -774,7 +808,8 @@ int cudahm_eval_etabar(cudahm_t h, const double* theta_host, double* out) {
 
 int cudahm_eval_detection(cudahm_t h, const double* F_host, double* eta_host, int64_t n) {
   if (!h || !F_host || !eta_host || n < 0) return fail(CUDAHM_EINVAL, "bad argument");
-  if (h->cfg.model != CUDAHM_LF) return fail(CUDAHM_EINVAL, "detection efficiency exists only for the LF model");
+  if (!has_rule(h->cfg.model))
+    return fail(CUDAHM_EINVAL, "detection efficiency exists only for the LF and BB1 models");
   if (n == 0) return CUDAHM_OK;
   CU(cudaSetDevice(h->cfg.device));
   double *F = nullptr, *out = nullptr;
@@ -786,7 +821,7 @@ int cudahm_eval_detection(cudahm_t h, const double* F_host, double* eta_host, in
   }
   cudaError_t e = cudaMemcpyAsync(F, F_host, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
-    e = launch_detection(n, F, h->cfg.model_consts[1], h->cfg.model_consts[0], h->phi_coef, out, h->stream);
+    e = launch_detection(h->cfg.model, n, F, h->mc, h->cfg.model_consts[0], h->phi_coef, out, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(eta_host, out, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   h->dfree(F);
@@ -941,7 +976,7 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
       TRY(alloc_into(h, &h->rows, static_cast<size_t>(nrows) * h->p));
       h->rows_cap = nrows;
     }
-    if (h->cfg.model == CUDAHM_LF && !h->etabar_valid) {
+    if (has_rule(h->cfg.model) && !h->etabar_valid) {
       char* base = reinterpret_cast<char*>(h->chain);
       TRY(compute_etabar_into(h, reinterpret_cast<const double*>(base + offsetof(ChainState, theta)),
                               reinterpret_cast<double*>(base + offsetof(ChainState, etabar))));
@@ -955,7 +990,7 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
   int nlf = 0;
   long long ntot = 0;
   for (int q = 0; q < k; ++q) {
-    nlf += hs[q]->cfg.model == CUDAHM_LF;
+    nlf += has_rule(hs[q]->cfg.model);
     ntot += hs[q]->n;
   }
   TuneKey key{h0->cfg.precision, k, nlf, static_cast<long long>(std::log2(static_cast<double>(ntot) + 1.0))};
@@ -1025,8 +1060,8 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
     progs[q] = BatchProg{total, 0, n_burn, thin, 0, 0};
     cost[q] = pop_cost(h);
     long long c = (h->n + 31) / 32;
-    if (h->cfg.model == CUDAHM_LF)
-      c += static_cast<long long>(h->cfg.model_consts[3]) * ((static_cast<long long>(h->cfg.model_consts[4]) + 127) / 128);
+    if (has_rule(h->cfg.model))
+      c += static_cast<long long>(rule_nL(h->cfg)) * ((static_cast<long long>(rule_nr(h->cfg)) + 127) / 128);
     cap[q] = static_cast<int>(std::min<long long>(c, max_grid));
   }
   CU(cudaMemcpyAsync(bb.pops, pops.data(), sizeof(SweepArgs) * k, cudaMemcpyHostToDevice, st));
@@ -1229,8 +1264,8 @@ int batch_step(const std::vector<cudahm*>& hs, std::vector<BatchProg>& progs, in
     pops[q] = a;
     cost[q] = pop_cost(h);
     long long c = (h->n + 31) / 32;
-    if (h->cfg.model == CUDAHM_LF)
-      c += static_cast<long long>(h->cfg.model_consts[3]) * ((static_cast<long long>(h->cfg.model_consts[4]) + 127) / 128);
+    if (has_rule(h->cfg.model))
+      c += static_cast<long long>(rule_nL(h->cfg)) * ((static_cast<long long>(rule_nr(h->cfg)) + 127) / 128);
     cap[q] = static_cast<int>(std::min<long long>(c, max_grid));
   }
   std::vector<int> nb = allocate_blocks(cost, cap, grid), b0(k);
@@ -1279,11 +1314,11 @@ struct Request {
 
 size_t request_bytes(const cudahm_config& c, long long n_iter, long long thin) {
   const size_t n = static_cast<size_t>(c.n), d = c.d;
-  const size_t p = c.model == CUDAHM_NN1 ? 2 : (c.model == CUDAHM_LF ? 3 : 9);
+  const size_t p = model_p(c.model);
   size_t b = n * (4 * 8 + d * 8 + d * d * 8) + (c.precision == CUDAHM_FP32 ? n * 5 * 4 : 0);
   b += static_cast<size_t>(n_iter / std::max<long long>(thin, 1)) * p * 8;
   b += static_cast<size_t>(kChunk) * (p + 3) * 8 + 64 * 1024;
-  if (c.model == CUDAHM_LF) b += static_cast<size_t>(8 * 4096 + 2048) * 8;
+  if (has_rule(c.model)) b += static_cast<size_t>(8 * 4096 + 2048) * 8;
   return b;
 }
 
@@ -1336,7 +1371,7 @@ void serve_loop(cudahm_server* sv) {
       r->cfg.cuda_stream = sv->stream;
       int rc = cudahm_create(&r->cfg, &h);
       if (rc == CUDAHM_OK) rc = cudahm_set_data(h, r->y.data(), r->aux.data(), r->cfg.n);
-      if (rc == CUDAHM_OK && r->cfg.model == CUDAHM_LF) {
+      if (rc == CUDAHM_OK && has_rule(r->cfg.model)) {
         char* base = reinterpret_cast<char*>(h->chain);
         rc = compute_etabar_into(h, reinterpret_cast<const double*>(base + offsetof(ChainState, theta)),
                                  reinterpret_cast<double*>(base + offsetof(ChainState, etabar)));
@@ -1547,7 +1582,7 @@ int cudahm_server_result(cudahm_server_t sv, uint64_t ticket, double* theta_host
     delete r;
     return fail(e, "request failed: %s", m.c_str());
   }
-  const int p = r->cfg.model == CUDAHM_NN1 ? 2 : (r->cfg.model == CUDAHM_LF ? 3 : 9);
+  const int p = model_p(r->cfg.model);
   const long long rows = static_cast<long long>(r->rows.size()) / p;
   if (rows_out) *rows_out = rows;
   if (latency_ms) *latency_ms = r->t_done - r->t_submit;

@@ -47,17 +47,24 @@ cudaError_t launch_phi_table(double* coef, cudaStream_t st) {
 int phi_table_words() { return kPhiWords; }
 
 // Detection efficiency eta(F) = Phi((F - F_th)/sigma_F) for a list of fluxes.
-__global__ void detection_kernel(long long n, const double* F, double F_th, double sigma_F, const double* coef,
-                                 double* out) {
+// LF: sigma_F constant; BB1: sigma(F)^2 = sigma0^2 + (alpha F)^2, evaluated as in the rule's pairs.
+__global__ void detection_kernel(int model, long long n, const double* F, ModelConsts mc, double sigma_F,
+                                 const double* coef, double* out) {
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  out[i] = phi_table((F[i] - F_th) / sigma_F, coef);
+  if (model == CUDAHM_BB1) {
+    const double aF = mc.alpha * F[i];
+    out[i] = phi_table16(16.0 * (F[i] - mc.F_th) * rsqrt(fma(aF, aF, mc.s0sq)), coef);
+  } else {
+    out[i] = phi_table((F[i] - mc.F_th) / sigma_F, coef);
+  }
 }
 
-cudaError_t launch_detection(long long n, const double* F, double F_th, double sigma_F, const double* coef,
-                             double* out, cudaStream_t st) {
+cudaError_t launch_detection(int model, long long n, const double* F, const ModelConsts& mc, double sigma_F,
+                             const double* coef, double* out, cudaStream_t st) {
   const int blk = 256;
-  detection_kernel<<<static_cast<unsigned int>((n + blk - 1) / blk), blk, 0, st>>>(n, F, F_th, sigma_F, coef, out);
+  detection_kernel<<<static_cast<unsigned int>((n + blk - 1) / blk), blk, 0, st>>>(model, n, F, mc, sigma_F, coef,
+                                                                                   out);
   return cudaGetLastError();
 }
 
@@ -107,7 +114,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   const unsigned int nb0 = static_cast<unsigned int>((a.n * blockIdx.x) / gridDim.x);
   const unsigned int nb1 = static_cast<unsigned int>((a.n * (blockIdx.x + 1)) / gridDim.x);
   const bool skip_me = (a.skip_cta == static_cast<int>(blockIdx.x));
-  const bool is_lf = (a.model == CUDAHM_LF);
+  constexpr bool is_lf = M::kRule;  // the model has a selection integral (LF, BB1)
   double* s_math = s_dyn;                 // [kMathWords] exp/log tables
   double* s_phi = s_dyn + kMathWords;     // [kPhiWords] for LF, else empty
   double* s_y = s_phi + (is_lf ? kPhiWords : 0);
@@ -164,7 +171,8 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   }
   __syncthreads();
   if (s_fail) return;
-  if (is_lf && s_lpri_new != -INFINITY) lf_segment_rows(s_tcp, a, blockIdx.x, gridDim.x, nseg, tab, s_math);
+  if constexpr (is_lf)
+    if (s_lpri_new != -INFINITY) lf_segment_rows<M>(s_tcp, a, blockIdx.x, gridDim.x, nseg, tab, s_math);
 
   // members of this thread: i = nb0 + tid + m blockDim (latent, RAM factor, e^chi, log l in registers)
   R chi[K], echi[K], ll[K];
@@ -239,7 +247,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
       __syncwarp();
       if (is_lf && s_lpri_new != -INFINITY) {
         const ThetaC tcp = s_tcp;
-        for (int t = lane; t < nseg; t += 32) lf_segment_row(tcp, a, blockIdx.x, gridDim.x, t, t, tab, s_math);
+        for (int t = lane; t < nseg; t += 32) lf_segment_row<M>(tcp, a, blockIdx.x, gridDim.x, t, t, tab, s_math);
         __syncwarp();
         lf_segment_scan(nseg, tab);
       }
@@ -400,7 +408,8 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         }
       }
     }
-    if (prior_ok && is_lf) lf_segment_pairs(a, nseg, tab, s_phi, xe, fe);
+    if constexpr (is_lf)
+      if (prior_ok) lf_segment_pairs<M>(a, nseg, tab, s_phi, xe, fe);
 
     // a5: block partial
     {
@@ -553,11 +562,15 @@ static const void* kernel_for_p(int K) {
 
 template <class M>
 static const void* kernel_for(int K, bool f32) {
-  return f32 ? kernel_for_p<M, true>(K) : kernel_for_p<M, false>(K);
+  if constexpr (std::is_same<M, BB1>::value) {  // FP64 form only
+    return f32 ? nullptr : kernel_for_p<M, false>(K);
+  } else {
+    return f32 ? kernel_for_p<M, true>(K) : kernel_for_p<M, false>(K);
+  }
 }
 
 size_t sweep_smem_bytes(int model, int mpb, int rows_smem) {
-  return sizeof(double) * kMathWords + (model == CUDAHM_LF ? sizeof(double) * kPhiWords : 0) +
+  return sizeof(double) * kMathWords + ((model == CUDAHM_LF || model == CUDAHM_BB1) ? sizeof(double) * kPhiWords : 0) +
          4 * sizeof(double) * static_cast<size_t>(mpb) + segtab_bytes(rows_smem);
 }
 
@@ -580,12 +593,14 @@ static cudaError_t launch_model(const SweepArgs& a, int K, int grid, int block, 
 cudaError_t launch_sweep(const SweepArgs& a, int K, int grid, int block, cudaStream_t st) {
   if (a.model == CUDAHM_NN1) return launch_model<NN1>(a, K, grid, block, st);
   if (a.model == CUDAHM_LF) return launch_model<LF>(a, K, grid, block, st);
+  if (a.model == CUDAHM_BB1) return launch_model<BB1>(a, K, grid, block, st);
   return cudaErrorInvalidValue;
 }
 
 static const void* sweep_fn(int model, int K, bool f32) {
   if (model == CUDAHM_NN1) return kernel_for<NN1>(K, f32);
   if (model == CUDAHM_LF) return kernel_for<LF>(K, f32);
+  if (model == CUDAHM_BB1) return kernel_for<BB1>(K, f32);
   return nullptr;
 }
 
@@ -624,8 +639,11 @@ __global__ void prepare_kernel(int model, long long n, const double* y_raw, cons
     ok = ok && aux[i] > 0.0 && isfinite(aux[i]);
     if (set_default_chi) {
       double c = log(4.0 * 3.14159265358979323846 * ar * ar * fmax(yr, mc.F_th));
-      const double floor_c = th2 + 1e-6;
-      chi[i] = (c > th2) ? c : floor_c;
+      if (model == CUDAHM_LF) {  // raised into the support chi > ln L_low
+        const double floor_c = th2 + 1e-6;
+        c = (c > th2) ? c : floor_c;
+      }
+      chi[i] = c;
     }
   }
   if (set_default_chi) S[i] = mc.chi_init_scale;
@@ -862,6 +880,8 @@ cudaError_t launch_eval_logdens(int model, bool f32, long long n, const double* 
   } else if (model == CUDAHM_LF) {
     if (f32) eval_logdens_kernel<LF, true><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, math_tab, out);
     else eval_logdens_kernel<LF, false><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, math_tab, out);
+  } else if (model == CUDAHM_BB1 && !f32) {
+    eval_logdens_kernel<BB1, false><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, math_tab, out);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -870,6 +890,7 @@ cudaError_t launch_eval_logdens(int model, bool f32, long long n, const double* 
 
 // Stand-alone selection integral: same pair split and exact sum as the sweep kernel, so
 // the value is bit-identical to the one the sweep kernel computes for the same theta.
+template <class M>
 __global__ void etabar_partial_kernel(const double* theta, const SweepArgs a, unsigned long long* partials) {
   extern __shared__ double s_rows[];
   __shared__ ThetaC s_tc;
@@ -877,20 +898,20 @@ __global__ void etabar_partial_kernel(const double* theta, const SweepArgs a, un
   if (threadIdx.x == 0) {
     double th[kMaxP];
     for (int q = 0; q < 3; ++q) th[q] = theta[q];
-    s_tc = LF::consts(th, a.math_tab);
+    s_tc = M::consts(th, a.math_tab);
   }
   __syncthreads();
   const int nseg = lf_block_segments(a, blockIdx.x, gridDim.x);
   double* s_phi = s_rows;
   const SegTab tab = segtab_carve(s_rows + kPhiWords, a.rows_smem);
   for (int q = threadIdx.x; q < kPhiWords; q += blockDim.x) s_phi[q] = a.phi_coef[q];
-  lf_segment_rows(s_tc, a, blockIdx.x, gridDim.x, nseg, tab, a.math_tab);
+  lf_segment_rows<M>(s_tc, a, blockIdx.x, gridDim.x, nseg, tab, a.math_tab);
   __syncthreads();
   Xacc xd, xe;
   xacc_zero(xd);
   xacc_zero(xe);
   XFlags fe = {0u, 0u, 0u};
-  lf_segment_pairs(a, nseg, tab, s_phi, xe, fe);
+  lf_segment_pairs<M>(a, nseg, tab, s_phi, xe, fe);
   unsigned int f[4] = {0u, fe.nan, fe.big, 0u};
   warp_reduce(xd, xe, f);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -939,7 +960,8 @@ __global__ void etabar_final_kernel(const unsigned long long* partials, int nblo
 cudaError_t launch_eval_etabar(const double* theta_dev, const SweepArgs& rule, unsigned long long* partials,
                                int grid, double* out, cudaStream_t st) {
   const size_t smem = sizeof(double) * kPhiWords + segtab_bytes(rule.rows_smem);
-  etabar_partial_kernel<<<grid, 256, smem, st>>>(theta_dev, rule, partials);
+  if (rule.model == CUDAHM_BB1) etabar_partial_kernel<BB1><<<grid, 256, smem, st>>>(theta_dev, rule, partials);
+  else etabar_partial_kernel<LF><<<grid, 256, smem, st>>>(theta_dev, rule, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   etabar_final_kernel<<<1, 32, 0, st>>>(partials, grid, out);

@@ -13,9 +13,9 @@
 namespace chm {
 
 // ----------------------------------------------------------------- models ----
-// Per-theta constants a0..a3 (computed once per theta by one thread).
+// Per-theta constants a0..a4 (computed once per theta by one thread).
 struct ThetaC {
-  double a0, a1, a2, a3;
+  double a0, a1, a2, a3, a4;
 };
 
 // binary32 theta constants for the FP32 bulk form; a location parameter is held as a sum of
@@ -46,6 +46,7 @@ struct NN1 {
   using TC = ThetaC;
   using TCf = ThetaCf;
   static constexpr int kD = 1;
+  static constexpr bool kRule = false;  // no selection integral
   static constexpr bool kExp = false;
   // binary32 forms of the member terms (FP32 bulk precision): loc = mu, scale = 1/(2 tau^2)
   __device__ static ThetaCf consts32(const ThetaC& c) {
@@ -78,6 +79,7 @@ struct NN1 {
     c.a1 = 0.5 * exp_tab(-2.0 * th[1], T);
     c.a2 = 0.0;
     c.a3 = 0.0;
+    c.a4 = 0.0;
     return c;
   }
   __device__ static bool support(double, const ThetaC&) { return true; }
@@ -101,6 +103,7 @@ struct LF {
   using TC = ThetaC;
   using TCf = ThetaCf;
   static constexpr int kD = 1;
+  static constexpr bool kRule = true;  // selection integral with constant sigma_F
   static constexpr bool kExp = true;
   // binary32 forms: scale = beta + 1, loc = ln L*, low = ln L_low; log f = scale x - e^x, x = chi - ln L*
   __device__ static ThetaCf consts32(const ThetaC& c) {
@@ -147,6 +150,7 @@ struct LF {
     c.a1 = th[1];
     c.a2 = exp_tab(-th[1], T);
     c.a3 = th[2];
+    c.a4 = 0.0;
     return c;
   }
   __device__ static bool support(double chi, const ThetaC& c) { return dgt(chi, c.a3); }
@@ -164,6 +168,59 @@ struct LF {
     if (!(th[2] < th[1])) return -INFINITY;
     return -log_tab(1.0 + th[0] * th[0], T) + th[2];  // 1 + beta^2 in [1, 5): a normal argument
   }
+};
+
+// The paper's BB1 luminosity function (Sec. 5.1-5.2, App. B eq. lumPDF), chi = ln L, theta =
+// (beta, ln l, ln u): log f = ln(1 - e^{-L/l}) + beta (chi - ln u) - L/u + chi (the normaliser
+// C(beta,u,l)/u cancels against the normalised selection integral); member likelihood the normal
+// density of Fhat_i with sd sigma(F), sigma(F)^2 = sigma0^2 + (alpha F)^2, F = e^chi q_i;
+// prior -ln(1 + beta^2) + ln l on -2 < beta < 0, l < u. FP64 form only.
+// a0 = beta, a1 = ln u, a2 = 1/u, a3 = 1/l, a4 = ln l
+struct BB1 {
+  using TC = ThetaC;
+  using TCf = ThetaCf;
+  static constexpr int kD = 1;
+  static constexpr bool kExp = true;
+  static constexpr bool kRule = true;  // selection integral with sigma(F) inside Phi
+  __device__ static ThetaC consts(const double* th, const double* T) {
+    ThetaC c;
+    c.a0 = th[0];
+    c.a1 = th[2];
+    c.a2 = exp_tab(-th[2], T);
+    c.a3 = exp_tab(-th[1], T);
+    c.a4 = th[1];
+    return c;
+  }
+  __device__ static bool support(double, const ThetaC&) { return true; }
+  // ln(1 - e^{-x}), x > 0 (Maechler's two branches)
+  __device__ static double log1mexp(double x) {
+    return (x <= 0.69314718055994530942) ? log(-expm1(-x)) : log1p(-exp(-x));
+  }
+  __device__ static double logf(double chi, double echi, const ThetaC& c) {
+    const double lg = log1mexp(__dmul_rn(echi, c.a3));
+    return __dadd_rn(__dadd_rn(lg, __fma_rn(c.a0, __dsub_rn(chi, c.a1), -__dmul_rn(echi, c.a2))), chi);
+  }
+  // y = Fhat_i, aux = q_i = 1/(4 pi r_i^2)
+  __device__ static double loglike(double, double echi, double y, double aux, const ModelConsts& mc) {
+    const double F = __dmul_rn(echi, aux);
+    const double aF = __dmul_rn(mc.alpha, F);
+    const double s2 = __fma_rn(aF, aF, mc.s0sq);
+    const double r = __dsub_rn(y, F);
+    return __dsub_rn(__dmul_rn(-0.5, log(s2)), __ddiv_rn(__dmul_rn(r, r), __dmul_rn(2.0, s2)));
+  }
+  __device__ static double cterm(const double*) { return 0.0; }
+  __device__ static double logprior(const double* th, const ModelConsts&, const double* T) {
+    if (!(th[0] > -2.0 && th[0] < 0.0)) return -INFINITY;
+    if (!(th[1] < th[2])) return -INFINITY;
+    return -log_tab(1.0 + th[0] * th[0], T) + th[1];
+  }
+  // no binary32 form; these keep the FP32 instantiations of generic code compiling
+  static constexpr int kData32 = 1;
+  __device__ static ThetaCf consts32(const ThetaC&) { return ThetaCf{}; }
+  __device__ static bool support32(float, const ThetaCf&) { return true; }
+  __device__ static float logf32(float, const ThetaCf&) { return 0.0f; }
+  __device__ static void data32(double, double, const ModelConsts&, float* d) { d[0] = 0.0f; }
+  __device__ static float loglike32(float, const float*) { return 0.0f; }
 };
 
 // d = 3 normal population (Sec. 3 with C_pop unknown). theta = (mu[3], L11, L21, L22, L31, L32,
@@ -187,6 +244,7 @@ struct MVN3 {
   using TC = ThetaC3;
   using TCf = ThetaC3f;
   static constexpr int kD = 3;
+  static constexpr bool kRule = false;
   static constexpr bool kExp = false;
   __device__ static ThetaC3 consts(const double* th, const double* T) {
     const double L00 = exp_tab(th[3], T), L10 = th[4], L11 = exp_tab(th[5], T), L20 = th[6], L21 = th[7],
@@ -391,27 +449,43 @@ __device__ __forceinline__ SegTab segtab_carve(double* base, int R) {
   return t;
 }
 
-// Values of segment t (one thread; T is the exp/log table): L_j = e^t_j, G_j = (half-width) w_j g(e^t_j) e^t_j on
-// t in [ln L_low, ln L* + ln_upper]. Since x_jk = L_j qs_k - F_th/sigma_F decreases along the
-// inner nodes (r ascending), the pairs with x > 8.5, where Phi is exactly 1, are a prefix
-// k < k*_j of the row; they contribute G_j CW[k*_j] with CW the prefix sums of the inner
-// weights, added once per row (by its segment s = 0). Only k >= max(k*_j, s kSeg) is left to
-// evaluate; the count goes to off[t] until the block scans it. The table keeps 16 L_j, so that
-// v = 16 x_jk = fma(16 L_j, qs_k, -16 F_th/sigma_F) is one operation (exactly 16 x_jk).
+// Values of segment t (one thread; T is the exp/log table): L_j = e^t_j and G_j = (half-width)
+// w_j g(e^t_j) e^t_j over the outer interval (LF: [ln L_low, ln L* + ln_upper] with the Schechter
+// form; BB1: [ln l + ln_lower, ln u + ln_upper] with the BB1 form). Since x_jk (the argument of Phi)
+// decreases along the inner nodes (r ascending), the pairs with x > 8.5, where Phi is exactly 1,
+// are a prefix k < k*_j of the row; they contribute G_j CW[k*_j] with CW the prefix sums of the
+// inner weights, added once per row (by its segment s = 0). Only k >= max(k*_j, s kSeg) is left to
+// evaluate; the count goes to off[t] until the block scans it. LF keeps 16 L_j, so that
+// v = 16 x_jk = fma(16 L_j, qs_k, -16 F_th/sigma_F) is one operation (qs_k = q_k/sigma_F); BB1 keeps
+// L_j and evaluates x = (L_j q_k - F_th)/sigma(L_j q_k) per pair.
+template <class M>
 __device__ __forceinline__ void lf_segment_row(const ThetaC& tc, const SweepArgs& a, int b, int B, int t, int slot,
                                                const SegTab& tab, const double* __restrict__ T) {
-  const double lo = tc.a3, hi = tc.a1 + a.mc.ln_upper;
+  constexpr bool bb1 = std::is_same<M, BB1>::value;
+  const double lo = bb1 ? tc.a4 + a.mc.ln_lower : tc.a3;
+  const double hi = tc.a1 + a.mc.ln_upper;
   const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
   const int g = b + t * B;
   const int j = g % a.nL;
   const int sseg = g / a.nL;
   const double tt = fma(half, __ldg(a.xL + j), mid);
-  const double x = tt - tc.a1;
-  const double L16 = 16.0 * exp_tab(tt, T);
-  const double G = half * __ldg(a.wL + j) * exp_tab(fma(tc.a0, x, -exp_tab(x, T)), T);
-  // first k with qs_k <= (136 + 16 F_th/sigma_F)/(16 L_j), i.e. v_jk <= 136 up to rounding (both
-  // sides of that boundary give Phi = 1 exactly); positive doubles compared as integers
-  const long long thr = __double_as_longlong((136.0 + 16.0 * a.mc.cth) / L16);
+  double Lrow, G, thr_d;
+  if constexpr (bb1) {
+    const double L = exp_tab(tt, T);
+    const double lg = BB1::log1mexp(L * tc.a3);
+    G = half * __ldg(a.wL + j) * exp_tab(lg + fma(tc.a0, tt - tc.a1, -L * tc.a2) + tt, T);
+    Lrow = L;
+    thr_d = a.mc.F_pre / L;  // q_k > F_pre/L_j  <=>  x_jk > 8.5
+  } else {
+    const double x = tt - tc.a1;
+    const double L16 = 16.0 * exp_tab(tt, T);
+    G = half * __ldg(a.wL + j) * exp_tab(fma(tc.a0, x, -exp_tab(x, T)), T);
+    Lrow = L16;
+    thr_d = (136.0 + 16.0 * a.mc.cth) / L16;  // qs_k > thr  <=>  v_jk > 136, up to rounding
+  }
+  // first k with qs_k <= thr (both sides of that boundary give Phi = 1 exactly); positive doubles
+  // compared as integers
+  const long long thr = __double_as_longlong(thr_d);
   int klo = 0, khi = a.nr;
   while (klo < khi) {
     const int km = (klo + khi) >> 1;
@@ -421,7 +495,7 @@ __device__ __forceinline__ void lf_segment_row(const ThetaC& tc, const SweepArgs
   const int k0 = sseg << kSegShift;
   const int kend = min(k0 + kSeg, a.nr);
   const int kb = max(k0, klo);
-  tab.L[slot] = L16;
+  tab.L[slot] = Lrow;
   tab.G[slot] = G;
   tab.pre[slot] = (sseg == 0 && klo > 0) ? G * __ldg(a.cw + klo) : 0.0;
   tab.kb[slot] = kb;
@@ -448,17 +522,20 @@ __device__ __forceinline__ void lf_segment_scan(int nseg, const SegTab& tab) {
 }
 
 // All segment rows and the scan by the whole block (set-up paths).
+template <class M>
 __device__ __forceinline__ void lf_segment_rows(const ThetaC& tc, const SweepArgs& a, int b, int B, int nseg,
                                                 const SegTab& tab, const double* __restrict__ T) {
-  for (int t = threadIdx.x; t < nseg; t += blockDim.x) lf_segment_row(tc, a, b, B, t, t, tab, T);
+  for (int t = threadIdx.x; t < nseg; t += blockDim.x) lf_segment_row<M>(tc, a, b, B, t, t, tab, T);
   __syncthreads();
   if (threadIdx.x < 32) lf_segment_scan(nseg, tab);
 }
 
 // The block's active pairs (all lanes busy) and its rows' prefix terms; each term
-// G_j W_k Phi((L_j q_k - F_th)/sigma_F) is added exactly.
+// G_j W_k Phi(x_jk) is added exactly.
+template <class M>
 __device__ __forceinline__ void lf_segment_pairs(const SweepArgs& a, int nseg, const SegTab& tab, const double* s_phi,
                                                  Xacc& xe, XFlags& fe) {
+  constexpr bool bb1 = std::is_same<M, BB1>::value;
   const int total = tab.off[nseg];
   const double mcth16 = -16.0 * a.mc.cth;
   for (int q = threadIdx.x; q < total; q += blockDim.x) {
@@ -469,7 +546,14 @@ __device__ __forceinline__ void lf_segment_pairs(const SweepArgs& a, int nseg, c
       else hi = m - 1;
     }
     const int k = tab.kb[lo] + (q - tab.off[lo]);
-    const double v = fma(tab.L[lo], __ldg(a.qs + k), mcth16);
+    double v;
+    if constexpr (bb1) {  // 16 (F - F_th)/sigma(F), F = L_j q_k
+      const double F = tab.L[lo] * __ldg(a.qs + k);
+      const double aF = a.mc.alpha * F;
+      v = 16.0 * (F - a.mc.F_th) * rsqrt(fma(aF, aF, a.mc.s0sq));
+    } else {
+      v = fma(tab.L[lo], __ldg(a.qs + k), mcth16);
+    }
     xacc_add_double(xe, tab.G[lo] * (__ldg(a.Wr + k) * phi_table16(v, s_phi)), fe);
   }
   for (int t = threadIdx.x; t < nseg; t += blockDim.x)
@@ -570,6 +654,7 @@ __device__ __forceinline__ void publish_theta(const SweepArgs& a, unsigned int s
   __stcg(&pub->tcp.a1, tcp.a1);
   __stcg(&pub->tcp.a2, tcp.a2);
   __stcg(&pub->tcp.a3, tcp.a3);
+  __stcg(&pub->tcp.a4, tcp.a4);
   const float* f = &tcpf.sc_hi;
   float* g = &pub->tcpf.sc_hi;
   for (int q = 0; q < 6; ++q) __stcg(g + q, f[q]);
@@ -597,6 +682,7 @@ __device__ __forceinline__ bool fetch_theta(const SweepArgs& a, unsigned int s1,
   tcp.a1 = __ldcg(&pub->tcp.a1);
   tcp.a2 = __ldcg(&pub->tcp.a2);
   tcp.a3 = __ldcg(&pub->tcp.a3);
+  tcp.a4 = __ldcg(&pub->tcp.a4);
   const float* g = &pub->tcpf.sc_hi;
   float* f = &tcpf.sc_hi;
   for (int q = 0; q < 6; ++q) f[q] = __ldcg(g + q);

@@ -60,6 +60,9 @@ def test_config_defaults(lib):
     (lambda c: setattr(c, "adapt_exponent", 0.3), cudahm.EINVAL),
     (lambda c: setattr(c, "precision", 7), cudahm.EINVAL),
     (lambda c: setattr(c, "model", cudahm.MVN3), cudahm.EINVAL),  # d = 1 does not match MVN3
+    (lambda c: setattr(c, "model", cudahm.BB1), cudahm.EINVAL),   # BB1 needs sigma0, alpha, nu, r_max
+    (lambda c: [setattr(c, "model", cudahm.BB1), setattr(c, "precision", cudahm.FP32)] and None,
+     cudahm.EUNSUPPORTED),  # BB1 has the FP64 form only
     (lambda c: c.theta_init.__setitem__(1, 50.0), cudahm.EINVAL),
 ])
 def test_invalid_configs_rejected(lib, mutate, code):
