@@ -221,7 +221,7 @@ int cudahm_restore(cudahm_t h, const void* buf, size_t size);
  * (a process that gives all device memory to its own pool up front and forbids later
  * allocations, a latency-critical loop that must not pay for the synchronisation an
  * allocation implies, a caller that is out of device memory). The tables and partial sums
- * live in one fixed array compiled into the library (about 111 KB on every GPU that loads
+ * live in one fixed array compiled into the library (about 113 KB on every GPU that loads
  * it, held until the process exits), which bounds the rule to
  * n_L, n_r <= CUDAHM_NOALLOC_MAX_NODES.
  *   theta_dev    3 doubles on the current device: (beta, ln L*, ln L_low)

@@ -75,7 +75,7 @@ __device__ __forceinline__ void member_f64(const SweepArgs& a, unsigned int i, u
   const double ua = uniform53(w0.x, w0.y), ub = uniform53(w0.z, w0.w);
   const double rad = sqrt(-2.0 * log_tab(ua, s_math));
   double sn, cs;
-  sincospi(2.0 * ub, &sn, &cs);
+  sincospi_tab(2.0 * ub, s_math, &sn, &cs);
   const double z = odd ? rad * cs : rad * sn;
   const uint4 w1 = philox4x32_10(make_uint4(1u, 0u, i, k), a.key0, a.key1);
   const double u = uniform53(w1.x, w1.y);
@@ -208,7 +208,7 @@ __device__ __forceinline__ void member3_f64(const SweepArgs& a, unsigned int i, 
     const double ua = uniform53(b.x, b.y), ub = uniform53(b.z, b.w);
     const double rad = sqrt(-2.0 * log_tab(ua, s_math));
     double sn, cs;
-    sincospi(2.0 * ub, &sn, &cs);
+    sincospi_tab(2.0 * ub, s_math, &sn, &cs);
     z[c] = odd ? rad * cs : rad * sn;
   }
   const uint4 bu = philox4x32_10(make_uint4(3u, 0u, i, k), a.key0, a.key1);

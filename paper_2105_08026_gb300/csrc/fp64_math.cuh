@@ -8,12 +8,16 @@
 //   [0, 64)     2^(j/64)
 //   [64, 156)   ln F_j,  F_j = (j + 90)/128, j = 0..91
 //   [156, 248)  1/F_j
+//   [248, 377)  sin(pi j/64), j = 0..128
+//   [377, 506)  cos(pi j/64)
 #pragma once
 #include <cuda_runtime.h>
 
 namespace chm {
 
-constexpr int kMathWords = 64 + 2 * 92;
+constexpr int kSinOff = 64 + 2 * 92;
+constexpr int kCosOff = kSinOff + 129;
+constexpr int kMathWords = kCosOff + 129;
 
 static __global__ void math_table_kernel(double* t) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -24,6 +28,12 @@ static __global__ void math_table_kernel(double* t) {
     const double F = (j + 90) / 128.0;
     t[i] = log(F);
     t[i + 92] = 1.0 / F;
+  } else if (i >= 256 && i < 256 + 129) {
+    const int j = i - 256;
+    double sn, cs;
+    sincospi(j / 64.0, &sn, &cs);
+    t[kSinOff + j] = sn;
+    t[kCosOff + j] = cs;
   }
 }
 
@@ -80,6 +90,28 @@ __device__ __forceinline__ double log_tab(double u, const double* __restrict__ T
   const double ed = static_cast<double>(e);
   const double hi = fma(ed, 0x1.62e42fefa4000p-1, T[64 + j]);  // e ln2 (high 40 bits, exact) + ln F
   return hi + fma(ed, -0x1.8432a1b0e2634p-43, p);
+}
+
+// sin(pi a), cos(pi a) for 0 <= a <= 2 (the Box-Muller angle 2 pi u): a = j/64 + r with
+// j = round(64 a), |r| <= 1/128 (r exact), theta = pi r (|theta| <= 0.0246); sin theta by its
+// degree-7 Taylor polynomial (remainder < 1e-20), cos theta by its degree-6 polynomial (remainder
+// < 4e-18), then the angle-sum formulas with the tabulated sin(pi j/64), cos(pi j/64).
+__device__ __forceinline__ void sincospi_tab(double a, const double* __restrict__ T, double* sn, double* cs) {
+  const double magic = 0x1.8p52;
+  const double jm = fma(a, 64.0, magic);
+  const int j = __double2loint(jm);
+  const double r = fma(jm - magic, -0.015625, a);          // exact
+  const double th = fma(r, 0x1.921fb54442d18p+1, r * 0x1.1a62633145c07p-53);  // pi r, pi as hi + lo
+  const double t2 = th * th;
+  double ps = fma(t2, -1.0 / 5040.0, 1.0 / 120.0);
+  ps = fma(ps, t2, -1.0 / 6.0);
+  const double st = fma(th * t2, ps, th);                   // sin theta
+  double pc = fma(t2, -1.0 / 720.0, 1.0 / 24.0);
+  pc = fma(pc, t2, -0.5);
+  const double ct = fma(t2, pc, 1.0);                       // cos theta
+  const double sj = T[kSinOff + j], cj = T[kCosOff + j];
+  *sn = fma(sj, ct, cj * st);
+  *cs = fma(cj, ct, -sj * st);
 }
 
 }  // namespace chm

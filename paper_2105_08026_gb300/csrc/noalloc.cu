@@ -27,7 +27,7 @@ namespace {
 constexpr int kNoallocMaxNodes = CUDAHM_NOALLOC_MAX_NODES;
 constexpr int kNoallocMaxGrid = 1024;
 constexpr int kPhiWordsMax = 265 * 9;  // normal-CDF Taylor table
-constexpr int kMathWordsMax = 248;     // exp/log tables
+constexpr int kMathWordsMax = 506;     // exp/log/sin/cos tables
 // layout in doubles: xL, wL, xr, wr, qs, Wr (max nodes each), the Phi table, the exp/log table,
 // the prefix sums of the inner weights (max nodes + 1), then the per-block partials (4 x u64
 // per block)

@@ -111,8 +111,12 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   const int ctrl_warp = (blockDim.x >> 5) - 1;  // the warp that runs the deferred theta work
   const int p = a.p;
   // members of this block: the contiguous range [nb0, nb1), equal sizes to within one
-  const unsigned int nb0 = static_cast<unsigned int>((a.n * blockIdx.x) / gridDim.x);
-  const unsigned int nb1 = static_cast<unsigned int>((a.n * (blockIdx.x + 1)) / gridDim.x);
+  // In the FP64 form block 0 (which makes the grid's theta proposal on its serial path) holds no
+  // members, so that its FP64 unit is not shared with member work; the other blocks split them.
+  const unsigned int mb0 = (!F32 && gridDim.x > 1) ? 1u : 0u;
+  const unsigned int mgrid = gridDim.x - mb0, mblk = blockIdx.x - mb0;
+  const unsigned int nb0 = (blockIdx.x < mb0) ? 0u : static_cast<unsigned int>((a.n * mblk) / mgrid);
+  const unsigned int nb1 = (blockIdx.x < mb0) ? 0u : static_cast<unsigned int>((a.n * (mblk + 1)) / mgrid);
   const bool skip_me = (a.skip_cta == static_cast<int>(blockIdx.x));
   constexpr bool is_lf = M::kRule;  // the model has a selection integral (LF, BB1)
   double* s_math = s_dyn;                 // [kMathWords] exp/log tables
@@ -321,7 +325,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
             const double ua = uniform53(w0.x, w0.y), ub = uniform53(w0.z, w0.w);
             const double rad = sqrt(-2.0 * log_tab(ua, s_math));
             double sn, cs;
-            sincospi(2.0 * ub, &sn, &cs);
+            sincospi_tab(2.0 * ub, s_math, &sn, &cs);
             z = odd ? rad * cs : rad * sn;
             if (odd) s_zs[i - nb0] = rad * sn;
           } else {
@@ -575,7 +579,7 @@ size_t sweep_smem_bytes(int model, int mpb, int rows_smem) {
 }
 
 cudaError_t launch_math_table(double* t, cudaStream_t st) {
-  math_table_kernel<<<2, 128, 0, st>>>(t);
+  math_table_kernel<<<4, 128, 0, st>>>(t);
   return cudaGetLastError();
 }
 

@@ -1,4 +1,4 @@
-// Test-only probe: evaluates the sampler's table-driven exp/log on given inputs.
+// Test-only probe: evaluates the sampler's table-driven exp/log/sincospi on given inputs.
 // Compiled by tests/test_gpu_math.py with nvcc; not part of the library.
 #include <cuda_runtime.h>
 
@@ -8,7 +8,15 @@ namespace {
 __global__ void probe_kernel(int which, const double* x, double* y, int n, const double* T) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  y[i] = (which == 0) ? chm::exp_tab(x[i], T) : chm::log_tab(x[i], T);
+  double sn, cs;
+  switch (which) {
+    case 0: y[i] = chm::exp_tab(x[i], T); break;
+    case 1: y[i] = chm::log_tab(x[i], T); break;
+    case 2: chm::sincospi_tab(x[i], T, &sn, &cs); y[i] = sn; break;
+    case 3: chm::sincospi_tab(x[i], T, &sn, &cs); y[i] = cs; break;
+    case 4: sincospi(x[i], &sn, &cs); y[i] = sn; break;
+    default: sincospi(x[i], &sn, &cs); y[i] = cs; break;
+  }
 }
 }  // namespace
 
@@ -17,7 +25,7 @@ extern "C" int probe_fp64_math(int which, const double* x_host, double* y_host, 
   if (cudaMalloc(&x, sizeof(double) * n) != cudaSuccess) return -1;
   if (cudaMalloc(&y, sizeof(double) * n) != cudaSuccess) return -1;
   if (cudaMalloc(&T, sizeof(double) * chm::kMathWords) != cudaSuccess) return -1;
-  chm::math_table_kernel<<<2, 128>>>(T);
+  chm::math_table_kernel<<<4, 128>>>(T);
   cudaMemcpy(x, x_host, sizeof(double) * n, cudaMemcpyHostToDevice);
   probe_kernel<<<(n + 255) / 256, 256>>>(which, x, y, n, T);
   cudaMemcpy(y_host, y, sizeof(double) * n, cudaMemcpyDeviceToHost);

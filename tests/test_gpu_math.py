@@ -95,3 +95,45 @@ def test_philox_matches_curand(probe):
         ref = np.zeros((n, 4), dtype=np.uint32)
         assert L.probe_philox(c.ctypes.data_as(u32p), k0, k1, mine.ctypes.data_as(u32p), ref.ctypes.data_as(u32p), n) == 0
         assert np.array_equal(mine, ref), (k0, k1, np.argwhere(mine != ref)[:3])
+
+
+def _sincospi_ref(a):
+    """sin(pi a), cos(pi a) in extended precision: a - k/2 (k = round(2a)) is exact in binary64,
+    so only the reduced angle, |pi r| <= pi/4, meets the long-double sin/cos."""
+    a = np.asarray(a, dtype=np.float64)
+    k = np.rint(2 * a)
+    r = (a - k / 2).astype(np.longdouble)
+    pil = np.longdouble("3.14159265358979323846264338327950288")
+    s, c = np.sin(pil * r), np.cos(pil * r)
+    q = k.astype(np.int64) % 4
+    sn = np.select([q == 0, q == 1, q == 2, q == 3], [s, c, -s, -c])
+    cs = np.select([q == 0, q == 1, q == 2, q == 3], [c, -s, -c, s])
+    return sn, cs
+
+
+def test_sincospi_table(probe):
+    """The Box-Muller angle's table-driven sin/cos(pi a) on [0, 2): within 2.5 ulp of an
+    extended-precision reference (where long double is wider than binary64) and within 3.5 ulp
+    of CUDA's sincospi; exact zeros and ones at the quarter turns."""
+    g = np.random.default_rng(3)
+    edges = np.arange(129) / 64.0
+    a = np.concatenate([g.random(6000) * 2, (edges[:, None] + np.array([-1, 1]) / 128.0).ravel(),
+                        (edges[:, None] + np.array([-3e-16, 3e-16])).ravel(), g.random(500) * 1e-3,
+                        [0.0, 2.0**-52, 0.25, 0.5, 1.0, 1.5, 2.0 - 2.0**-52]])
+    a = a[(a >= 0) & (a < 2)]
+    for which, idx in ((2, 0), (3, 1)):
+        got = probe(which, a)
+        cuda = probe(which + 2, a)
+        nz = cuda != 0
+        err = _ulp_err(got[nz], cuda[nz])
+        assert err.max() <= 3.5, (a[nz][np.argmax(err)], err.max())
+        assert (got[~nz] == 0).all()
+        if np.finfo(np.longdouble).nmant >= 60:
+            ref = _sincospi_ref(a)[idx]
+            nz = ref != 0
+            diff = np.abs(got[nz].astype(np.longdouble) - ref[nz]).astype(np.float64)
+            err = diff / np.spacing(np.abs(ref[nz].astype(np.float64)))
+            assert err.max() <= 2.5, (a[nz][np.argmax(err)], err.max())
+    exact = np.array([0.0, 0.5, 1.0, 1.5])
+    assert probe(2, exact).tolist() == [0.0, 1.0, 0.0, -1.0]
+    assert probe(3, exact).tolist() == [1.0, 0.0, -1.0, 0.0]
