@@ -83,8 +83,13 @@ typedef struct cudahm* cudahm_t;
  *       sigma(F)^2 = sigma0^2 + (alpha F)^2 (eq. sig-F), detection F_th = nu sigma0/sqrt(1 - alpha^2)
  *       (eq. Fth), eta(F) = Phi((F - F_th)/sigma(F)); prior -ln(1 + beta^2) + ln l on
  *       -2 < beta < 0, l < u. consts = {sigma0, alpha, nu, r_max, n_L, n_r, ln(upper/u),
- *       ln(lower/l)}: the outer rule runs over ln L in [ln l + consts[7], ln u + consts[6]]. */
-typedef enum { CUDAHM_NN1 = 0, CUDAHM_MVN3 = 1, CUDAHM_LF = 2, CUDAHM_BB1 = 3 } cudahm_model;
+ *       ln(lower/l)}: the outer rule runs over ln L in [ln l + consts[7], ln u + consts[6]].
+ *  NN3  the paper's normal-normal benchmark (Sec. 3): d = 3, C_pop known, theta = mu, p = 3:
+ *       log f = -|L^-1 (chi - mu)|^2/2 with L L^T = C_pop, log l_i as MVN3 (the benchmark's
+ *       common measurement scales are s_ij = sigma_j for every i); prior flat in mu.
+ *       consts = the packed lower triangle of C_pop {C11, C21, C22, C31, C32, C33}, which must
+ *       be positive definite (else CUDAHM_EINVAL). Member state streams as for MVN3. */
+typedef enum { CUDAHM_NN1 = 0, CUDAHM_MVN3 = 1, CUDAHM_LF = 2, CUDAHM_BB1 = 3, CUDAHM_NN3 = 4 } cudahm_model;
 
 /* FP64: all arithmetic in binary64.
  * FP32 (bulk form): the member step (proposal, member log target, accept) and the theta

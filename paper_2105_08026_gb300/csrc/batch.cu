@@ -361,7 +361,7 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
     for (int q = 0; q < p * p; ++q) s_Sth[q] = a.chain->S_theta[q];
     s_etabar = a.chain->etabar;
     s_logeb = is_lf ? log_etabar(s_etabar, s_math) : 0.0;
-    s_tc = M::consts(s_theta, s_math);
+    s_tc = M::consts(s_theta, a.mc, s_math);
     s_tcf = M::consts32(s_tc);
     s_lpri = M::logprior(s_theta, a.mc, s_math);
     s_rows_written = 0;
@@ -584,7 +584,9 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const SweepArgs* __restri
   else if (s_args.model == CUDAHM_BB1) {
     if constexpr (!F32)  // FP64 form only
       run_population<BB1, false>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
-  } else
+  } else if (s_args.model == CUDAHM_NN3)
+    run_population<NN3, F32>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
+  else
     run_population<MVN3, F32>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
 }
 
@@ -647,7 +649,9 @@ __global__ void batch_tables_kernel(const SweepArgs* __restrict__ pops, const Ba
 }  // namespace
 
 int data32_words(int model) {
-  return model == CUDAHM_LF ? LF::kData32 : (model == CUDAHM_MVN3 ? MVN3::kData32 : NN1::kData32);
+  if (model == CUDAHM_LF) return LF::kData32;
+  if (model == CUDAHM_MVN3 || model == CUDAHM_NN3) return MVN3::kData32;
+  return NN1::kData32;
 }
 
 cudaError_t launch_data32(int model, long long n, const double* y, const double* aux, const ModelConsts& mc,
@@ -655,7 +659,7 @@ cudaError_t launch_data32(int model, long long n, const double* y, const double*
   const int blk = 256;
   const unsigned int grid = static_cast<unsigned int>((n + blk - 1) / blk);
   if (model == CUDAHM_LF) data32_kernel<LF><<<grid, blk, 0, st>>>(n, y, aux, mc, d32);
-  else if (model == CUDAHM_MVN3) data32_mvn3_kernel<<<grid, blk, 0, st>>>(n, y, aux, d32);
+  else if (model == CUDAHM_MVN3 || model == CUDAHM_NN3) data32_mvn3_kernel<<<grid, blk, 0, st>>>(n, y, aux, d32);
   else data32_kernel<NN1><<<grid, blk, 0, st>>>(n, y, aux, mc, d32);
   return cudaGetLastError();
 }

@@ -32,6 +32,8 @@ struct ModelConsts {
   double alpha;         // slope of the flux-dependent error, sigma(F)^2 = sigma0^2 + (alpha F)^2
   double F_pre;         // flux above which Phi((F - F_th)/sigma(F)) > Phi(8.5) (rule prefix); inf if none
   double ln_lower;      // ln(lower/l)
+  // NN3: inverse of the lower Cholesky factor of the known C_pop, packed (00, 10, 11, 20, 21, 22)
+  double li3[6];
 };
 
 struct SweepArgs {

@@ -42,7 +42,7 @@ int fail(int code, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(CUDAHM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
-int model_d(int m) { return m == CUDAHM_MVN3 ? 3 : 1; }
+int model_d(int m) { return (m == CUDAHM_MVN3 || m == CUDAHM_NN3) ? 3 : 1; }
 // doubles of one member's RAM factor as stored on the device (d = 3: six packed rows)
 int factor_words(int d) { return d == 3 ? 6 : 1; }
 
@@ -52,7 +52,33 @@ int chm::record_error(int code, const char* msg) { return fail(code, "%s", msg);
 
 namespace {
 
-int model_p(int m) { return m == CUDAHM_NN1 ? 2 : ((m == CUDAHM_LF || m == CUDAHM_BB1) ? 3 : 9); }
+int model_p(int m) {
+  if (m == CUDAHM_NN1) return 2;
+  return m == CUDAHM_MVN3 ? 9 : 3;
+}
+
+// Inverse of the lower Cholesky factor of the 3x3 covariance C given as its packed lower
+// triangle (C00, C10, C11, C20, C21, C22), packed the same way; false unless C is positive
+// definite.
+bool chol3_inverse(const double* C, double* li) {
+  for (int q = 0; q < 6; ++q)
+    if (!std::isfinite(C[q])) return false;
+  if (!(C[0] > 0.0)) return false;
+  const double L00 = std::sqrt(C[0]), L10 = C[1] / L00, L20 = C[3] / L00;
+  const double d1 = C[2] - L10 * L10;
+  if (!(d1 > 0.0)) return false;
+  const double L11 = std::sqrt(d1), L21 = (C[4] - L20 * L10) / L11;
+  const double d2 = C[5] - L20 * L20 - L21 * L21;
+  if (!(d2 > 0.0)) return false;
+  const double L22 = std::sqrt(d2);
+  li[0] = 1.0 / L00;
+  li[2] = 1.0 / L11;
+  li[5] = 1.0 / L22;
+  li[1] = -(L10 * li[0]) * li[2];
+  li[4] = -(L21 * li[2]) * li[5];
+  li[3] = -(L20 * li[0] + L21 * li[1]) * li[5];
+  return true;
+}
 // models with a selection integral, and the positions of their rule sizes in model_consts
 bool has_rule(int m) { return m == CUDAHM_LF || m == CUDAHM_BB1; }
 int rule_nL(const cudahm_config& c) { return static_cast<int>(c.model_consts[c.model == CUDAHM_BB1 ? 4 : 3]); }
@@ -161,7 +187,8 @@ int validate(const cudahm_config* c) {
   if (!c) return fail(CUDAHM_EINVAL, "config is NULL");
   if (c->abi_version != CUDAHM_ABI_VERSION)
     return fail(CUDAHM_EINVAL, "abi_version %u != %u", c->abi_version, CUDAHM_ABI_VERSION);
-  if (c->model != CUDAHM_NN1 && c->model != CUDAHM_LF && c->model != CUDAHM_MVN3 && c->model != CUDAHM_BB1)
+  if (c->model != CUDAHM_NN1 && c->model != CUDAHM_LF && c->model != CUDAHM_MVN3 && c->model != CUDAHM_BB1 &&
+      c->model != CUDAHM_NN3)
     return fail(CUDAHM_EINVAL, "unknown model %d", c->model);
   if (c->precision != CUDAHM_FP64 && c->precision != CUDAHM_FP32)
     return fail(CUDAHM_EINVAL, "unknown precision %d", c->precision);
@@ -213,6 +240,9 @@ int validate(const cudahm_config* c) {
     if (!(k[6] > 0.0) || !(k[7] < 0.0)) return fail(CUDAHM_EINVAL, "BB1 rule limits need ln(upper/u) > 0 > ln(lower/l)");
     const double* t = c->theta_init;
     if (!(t[0] > -2.0 && t[0] < 0.0 && t[1] < t[2])) return fail(CUDAHM_EINVAL, "theta_init outside the BB1 prior");
+  } else if (c->model == CUDAHM_NN3) {
+    double li[6];
+    if (!chol3_inverse(k, li)) return fail(CUDAHM_EINVAL, "NN3 needs a positive definite C_pop in consts[0..5]");
   }
   return CUDAHM_OK;
 }
@@ -229,7 +259,7 @@ int choose_shape(cudahm* h) {
                          : 0;
   const int Ks[4] = {1, 2, 4, 8};
   // the d = 3 model always streams its member state through the batched kernel
-  for (int ki = (model == CUDAHM_MVN3 ? 4 : 0); ki < 4 && h->grid == 0; ++ki) {
+  for (int ki = (model_d(model) == 3 ? 4 : 0); ki < 4 && h->grid == 0; ++ki) {
     const int K = Ks[ki];
     // the grid depends on the occupancy, which depends on the shared memory, which depends on
     // the grid: iterate from the register-limited occupancy down until it is consistent
@@ -512,6 +542,8 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
     }
     h->mc.ln_upper = k[6];
     h->mc.ln_lower = k[7];
+  } else if (cfg->model == CUDAHM_NN3) {
+    chol3_inverse(k, h->mc.li3);
   }
   int rc = choose_shape(h);
   if (rc != CUDAHM_OK) return bail(rc);

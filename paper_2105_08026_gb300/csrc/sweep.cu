@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     for (int q = 0; q < p * p; ++q) s_Sth[q] = a.chain->S_theta[q];
     s_etabar = a.chain->etabar;
     s_logeb = is_lf ? log_etabar(s_etabar, s_math) : 0.0;
-    s_tc = M::consts(s_theta, s_math);
+    s_tc = M::consts(s_theta, a.mc, s_math);
     s_lpri = M::logprior(s_theta, a.mc, s_math);
     s_rows_written = 0;
     s_tacc = 0;
@@ -679,7 +679,7 @@ cudaError_t launch_prepare(int model, long long n, const double* y_raw, const do
                            int set_default_chi, cudaStream_t st) {
   const int blk = 256;
   const long long grid = (n + blk - 1) / blk;
-  if (model == CUDAHM_MVN3) {
+  if (model == CUDAHM_MVN3 || model == CUDAHM_NN3) {
     prepare3_kernel<<<static_cast<unsigned int>(grid), blk, 0, st>>>(n, y_raw, aux_raw, y, aux, chi, S,
                                                                       mc.chi_init_scale, bad, set_default_chi);
     return cudaGetLastError();
@@ -819,7 +819,7 @@ __global__ void eval_logdens_kernel(long long n, const double* y, const double* 
   if (i >= n) return;
   double th[kMaxP];
   for (int q = 0; q < 3; ++q) th[q] = theta[q];
-  const ThetaC tc = M::consts(th, T);
+  const ThetaC tc = M::consts(th, mc, T);
   if (F32) {
     const ThetaCf tf = M::consts32(tc);
     const float c = static_cast<float>(chi[i]);
@@ -841,24 +841,24 @@ __global__ void eval_logdens_kernel(long long n, const double* y, const double* 
   out[i] = M::loglike(c, e, y[i], aux[i], mc) + M::logf(c, e, tc);
 }
 
-// d = 3 model: the same binary64 or binary32 expressions as its member step (per-component arrays).
-template <bool F32>
+// d = 3 models: the same binary64 or binary32 expressions as their member step (per-component arrays).
+template <class M, bool F32>
 __global__ void eval_logdens3_kernel(long long n, const double* y, const double* aux, const double* chi,
-                                     const double* theta, const double* T, double* out) {
+                                     const double* theta, ModelConsts mc, const double* T, double* out) {
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double th[kMaxP];
-  for (int q = 0; q < 9; ++q) th[q] = theta[q];
-  const ThetaC3 tc = MVN3::consts(th, T);
+  for (int q = 0; q < 9; ++q) th[q] = (q < 3 || !std::is_same<M, NN3>::value) ? theta[q] : 0.0;
+  const ThetaC3 tc = M::consts(th, mc, T);
   if constexpr (F32) {
-    const ThetaC3f tf = MVN3::consts32(tc);
-    float x[3], d[MVN3::kData32];
+    const ThetaC3f tf = M::consts32(tc);
+    float x[3], d[M::kData32];
     for (int j = 0; j < 3; ++j) {
       x[j] = static_cast<float>(chi[j * n + i]);
       split_f(y[j * n + i], d[2 * j], d[2 * j + 1]);
       d[6 + j] = static_cast<float>(0.5 * aux[j * n + i]);
     }
-    out[i] = static_cast<double>(MVN3::loglike32(x, d)) + static_cast<double>(MVN3::logf32(x, tf));
+    out[i] = static_cast<double>(M::loglike32(x, d)) + static_cast<double>(M::logf32(x, tf));
   } else {
     double x[3], yy[3], w[3];
     for (int j = 0; j < 3; ++j) {
@@ -866,7 +866,7 @@ __global__ void eval_logdens3_kernel(long long n, const double* y, const double*
       yy[j] = y[j * n + i];
       w[j] = aux[j * n + i];
     }
-    out[i] = MVN3::loglike(x, yy, w) + MVN3::logf(x, tc);
+    out[i] = M::loglike(x, yy, w) + M::logf(x, tc);
   }
 }
 
@@ -876,8 +876,11 @@ cudaError_t launch_eval_logdens(int model, bool f32, long long n, const double* 
   const int blk = 256;
   const unsigned int grid = static_cast<unsigned int>((n + blk - 1) / blk);
   if (model == CUDAHM_MVN3) {
-    if (f32) eval_logdens3_kernel<true><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, math_tab, out);
-    else eval_logdens3_kernel<false><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, math_tab, out);
+    if (f32) eval_logdens3_kernel<MVN3, true><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, math_tab, out);
+    else eval_logdens3_kernel<MVN3, false><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, math_tab, out);
+  } else if (model == CUDAHM_NN3) {
+    if (f32) eval_logdens3_kernel<NN3, true><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, math_tab, out);
+    else eval_logdens3_kernel<NN3, false><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, math_tab, out);
   } else if (model == CUDAHM_NN1) {
     if (f32) eval_logdens_kernel<NN1, true><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, math_tab, out);
     else eval_logdens_kernel<NN1, false><<<grid, blk, 0, st>>>(n, y, aux, chi, theta_dev, mc, math_tab, out);
@@ -902,7 +905,7 @@ __global__ void etabar_partial_kernel(const double* theta, const SweepArgs a, un
   if (threadIdx.x == 0) {
     double th[kMaxP];
     for (int q = 0; q < 3; ++q) th[q] = theta[q];
-    s_tc = M::consts(th, a.math_tab);
+    s_tc = M::consts(th, a.mc, a.math_tab);
   }
   __syncthreads();
   const int nseg = lf_block_segments(a, blockIdx.x, gridDim.x);

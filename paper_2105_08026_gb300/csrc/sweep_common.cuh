@@ -73,7 +73,7 @@ struct NN1 {
     return __fmul_rn(-d[2], __fmul_rn(r, r));
   }
   // per-theta constants; T is the exp/log table (the theta step runs these on its serial path)
-  __device__ static ThetaC consts(const double* th, const double* T) {
+  __device__ static ThetaC consts(const double* th, const ModelConsts&, const double* T) {
     ThetaC c;
     c.a0 = th[0];
     c.a1 = 0.5 * exp_tab(-2.0 * th[1], T);
@@ -144,7 +144,7 @@ struct LF {
     const float r = __fmaf_rn(-expf(chi), d[4], d[3]);
     return __fmul_rn(__fmul_rn(r, r), d[2]);
   }
-  __device__ static ThetaC consts(const double* th, const double* T) {
+  __device__ static ThetaC consts(const double* th, const ModelConsts&, const double* T) {
     ThetaC c;
     c.a0 = th[0] + 1.0;
     c.a1 = th[1];
@@ -182,7 +182,7 @@ struct BB1 {
   static constexpr int kD = 1;
   static constexpr bool kExp = true;
   static constexpr bool kRule = true;  // selection integral with sigma(F) inside Phi
-  __device__ static ThetaC consts(const double* th, const double* T) {
+  __device__ static ThetaC consts(const double* th, const ModelConsts&, const double* T) {
     ThetaC c;
     c.a0 = th[0];
     c.a1 = th[2];
@@ -240,25 +240,33 @@ struct ThetaC3f {
   float li_hi[6], li_lo[6];
 };
 
-struct MVN3 {
+// d = 3 normal population. kKnown = false: theta = (mu, L_C) with L_C lower-triangular and
+// log-diagonal (p = 9). kKnown = true: the paper's normal-normal benchmark (Sec. 3), C_pop
+// known, theta = mu (p = 3), the inverse factor of C_pop taken from the model constants.
+template <bool kKnown>
+struct MVN3T {
   using TC = ThetaC3;
   using TCf = ThetaC3f;
   static constexpr int kD = 3;
   static constexpr bool kRule = false;
   static constexpr bool kExp = false;
-  __device__ static ThetaC3 consts(const double* th, const double* T) {
-    const double L00 = exp_tab(th[3], T), L10 = th[4], L11 = exp_tab(th[5], T), L20 = th[6], L21 = th[7],
-                 L22 = exp_tab(th[8], T);
+  __device__ static ThetaC3 consts(const double* th, const ModelConsts& mc, const double* T) {
     ThetaC3 c;
     c.mu[0] = th[0];
     c.mu[1] = th[1];
     c.mu[2] = th[2];
-    c.li[0] = 1.0 / L00;
-    c.li[2] = 1.0 / L11;
-    c.li[5] = 1.0 / L22;
-    c.li[1] = -(L10 * c.li[0]) * c.li[2];
-    c.li[4] = -(L21 * c.li[2]) * c.li[5];
-    c.li[3] = -(L20 * c.li[0] + L21 * c.li[1]) * c.li[5];
+    if constexpr (kKnown) {
+      for (int j = 0; j < 6; ++j) c.li[j] = mc.li3[j];
+    } else {
+      const double L00 = exp_tab(th[3], T), L10 = th[4], L11 = exp_tab(th[5], T), L20 = th[6], L21 = th[7],
+                   L22 = exp_tab(th[8], T);
+      c.li[0] = 1.0 / L00;
+      c.li[2] = 1.0 / L11;
+      c.li[5] = 1.0 / L22;
+      c.li[1] = -(L10 * c.li[0]) * c.li[2];
+      c.li[4] = -(L21 * c.li[2]) * c.li[5];
+      c.li[3] = -(L20 * c.li[0] + L21 * c.li[1]) * c.li[5];
+    }
     return c;
   }
   __device__ static double logf(const double* x, const ThetaC3& c) {
@@ -275,8 +283,11 @@ struct MVN3 {
                               __fma_rn(__dmul_rn(w[1], e1), e1, __dmul_rn(__dmul_rn(w[2], e2), e2)));
     return __dmul_rn(-0.5, q);
   }
-  __device__ static double cterm(const double* th) { return -((th[3] + th[5]) + th[8]); }
-  // flat in mu, in the off-diagonal entries and in the log-diagonal entries (improper)
+  __device__ static double cterm(const double* th) {
+    if constexpr (kKnown) return 0.0;  // -ln det L_C is a constant when C_pop is known
+    else return -((th[3] + th[5]) + th[8]);
+  }
+  // flat in mu (and, unknown C_pop, in the off-diagonal and log-diagonal entries); improper
   __device__ static double logprior(const double*, const ModelConsts&, const double*) { return 0.0; }
 
   __device__ static ThetaC3f consts32(const ThetaC3& c) {
@@ -313,6 +324,9 @@ struct MVN3 {
     return -q;
   }
 };
+
+using MVN3 = MVN3T<false>;
+using NN3 = MVN3T<true>;
 
 // RAM factor update for d = 3 (Sec. 2.2): S' S'^T = S (I + c U U^T/|U|^2) S^T
 // = S S^T + sig w w^T with w = S U and sig = c/|U|^2, as a rank-one Cholesky modification
@@ -699,7 +713,7 @@ __device__ __forceinline__ void propose_theta(const SweepArgs& a, long long s, i
     thp[q] = t;
   }
   lpri_new = M::logprior(thp, a.mc, T);
-  tcp = M::consts(thp, T);
+  tcp = M::consts(thp, a.mc, T);
 }
 
 }  // namespace chm

@@ -20,12 +20,12 @@ LIB_PATH = os.path.join(_PKG, "lib", "libcudahm.so")
 
 ABI_VERSION = 1
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENUMERIC, ESTATE, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
-NN1, MVN3, LF, BB1 = 0, 1, 2, 3
+NN1, MVN3, LF, BB1, NN3 = 0, 1, 2, 3, 4
 FP64, FP32 = 0, 1
 MAX_P = 9
 MAX_CONSTS = 8
-MODEL_D = {NN1: 1, MVN3: 3, LF: 1, BB1: 1}
-MODEL_P = {NN1: 2, MVN3: 9, LF: 3, BB1: 3}
+MODEL_D = {NN1: 1, MVN3: 3, LF: 1, BB1: 1, NN3: 3}
+MODEL_P = {NN1: 2, MVN3: 9, LF: 3, BB1: 3, NN3: 3}
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
