@@ -80,6 +80,11 @@ def parse():
     ap.add_argument("--cpu-sweeps", type=int, default=8)
     ap.add_argument("--no-mvn3", action="store_true")
     ap.add_argument("--no-bb1", action="store_true")
+    ap.add_argument("--no-nn3", action="store_true")
+    ap.add_argument("--nn3-sizes", default="100,1000,10000,30000")
+    ap.add_argument("--nn3-burn", type=int, default=40_000)
+    ap.add_argument("--nn3-sweeps", type=int, default=75_000)
+    ap.add_argument("--nn3-chains", type=int, default=64)
     ap.add_argument("--bb1-sweeps", type=int, default=1000)
     ap.add_argument("--mvn3-sweeps", type=int, default=3000)
     return ap.parse_args()
@@ -338,6 +343,79 @@ def run_bb1(args, cudahm, stream, device, flush, peak_fp64):
             "dtype": "f64"}
 
 
+def run_nn3_ess(args, cudahm, stream, device):
+    """The paper's normal-normal benchmark (Sec. 3: d = 3, mu_pop, C_pop = D R D and sigma_j as
+    printed, C_pop and sigma_j known, flat prior on mu) measured as the paper measures it: the
+    post-burn-in time to an effective sample size of 1000 for the slowest of the three mu
+    components. Per population size: --nn3-burn untimed sweeps, then --nn3-sweeps timed ones
+    (the paper's 4e4 burn-in and 7.5e4 kept sweeps), CUDA events on the sampler's stream, ESS of
+    the kept theta rows by the library's estimator. FP64, and FP32 at N = 1e4. Then the same
+    with --nn3-chains independent chains on the same data in one batched run (the paper's Stan
+    protocol pools parallel chains; ESS of the pooled draws = the sum of the chains' ESS)."""
+    import torch
+    from paper_2105_08026_gb300 import synth
+    out = []
+    sizes = [int(float(v)) for v in args.nn3_sizes.split(",") if v]
+    for n in sizes:
+        data = synth.nn3_data(n, seed=1004)
+        theta0, scale, consts = synth.nn3_settings(data)
+        precs = [("f64", cudahm.FP64)] + ([("f32", cudahm.FP32)] if n == 10_000 else [])
+        for name, prec in precs:
+            s = cudahm.Sampler(cudahm.NN3, n, theta_init=theta0, theta_prop_scale=scale, model_consts=consts,
+                               seed=7, precision=prec, device=device, stream=stream.cuda_stream,
+                               use_torch_allocator=True)
+            s.set_data(data.y, data.s)
+            s.run(args.nn3_burn, 0)
+            K = args.nn3_sweeps
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rows = s.run(0, K, 1)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            ess = cudahm.cudahm_ess(rows)
+            st = s.stats()
+            s.close()
+            out.append({"n": n, "dtype": name, "sweeps": K, "burn_in": args.nn3_burn, "ms": ms,
+                        "us_per_sweep": 1e3 * ms / K, "ess": ess.tolist(),
+                        "time_to_ess1000_s": 1e-3 * ms * 1000.0 / float(ess.min()),
+                        "object_updates_per_s": n * K / (ms * 1e-3),
+                        "theta_accept": st.theta_accepts / st.sweeps,
+                        "member_accept": st.member_accepts / (st.sweeps * n),
+                        "launch_shape": [st.grid_blocks, st.block_threads, st.objects_per_thread]})
+        R = args.nn3_chains
+        if R > 1:
+            chains = []
+            for r in range(R):
+                c = cudahm.Sampler(cudahm.NN3, n, theta_init=theta0, theta_prop_scale=scale, model_consts=consts,
+                                   seed=1000 + r, device=device, stream=stream.cuda_stream, use_torch_allocator=True)
+                c.set_data(data.y, data.s)
+                chains.append(c)
+            _, tune = cudahm.batch_run(chains, args.nn3_burn, 0)
+            K = args.nn3_sweeps
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rows, _ = cudahm.batch_run(chains, 0, K, 1, tune=tune)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            ess = np.sum([cudahm.cudahm_ess(r_) for r_ in rows], axis=0)
+            for c in chains:
+                c.close()
+            out.append({"n": n, "dtype": "f64", "chains": R, "sweeps": K, "burn_in": args.nn3_burn, "ms": ms,
+                        "us_per_sweep": 1e3 * ms / K, "ess": ess.tolist(),
+                        "time_to_ess1000_s": 1e-3 * ms * 1000.0 / float(ess.min()),
+                        "object_updates_per_s": R * n * K / (ms * 1e-3),
+                        "launch": {"block_threads": tune.block_threads, "sweeps_per_launch": tune.sweeps_per_launch,
+                                   "graph": bool(tune.use_graph), "blocks": tune.reserved}})
+    return {"workload": "normal-normal benchmark (paper Sec. 3), d=3, C_pop known, theta=mu",
+            "metric": "post-burn-in seconds to ESS=1000 (min over mu components)", "runs": out}
+
+
 def run_served(args, cudahm, device):
     """Poisson request stream (rate 20/s for --serve-seconds) into the continuous-batching server:
     each request is NN1 or LF with probability 1/2, N log-uniform on [1e3, 3e5], 5000 sweeps,
@@ -504,6 +582,9 @@ def run_cuda(args):
     bb1 = None
     if not args.no_bb1 and rank == 0:
         bb1 = run_bb1(args, cudahm, stream, local, flush, peak)
+    nn3 = None
+    if not args.no_nn3 and rank == 0:
+        nn3 = run_nn3_ess(args, cudahm, stream, local)
 
     # e2e through the public API with host buffers (every iteration: H2D data, run, D2H samples)
     e2e = None
@@ -559,7 +640,7 @@ def run_cuda(args):
                        "member state register-resident within a launch", "timed_launches": R,
                        "launch_shape": [st.grid_blocks, st.block_threads, st.objects_per_thread]},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
-            "fp32_bulk": fp32, "batched_fp32": batched, "served_fp32": served, "mvn3": mvn3, "bb1": bb1}
+            "fp32_bulk": fp32, "batched_fp32": batched, "served_fp32": served, "mvn3": mvn3, "bb1": bb1, "nn3_ess": nn3}
     print(json.dumps(line), flush=True)
     s.close()
     if ws > 1:

@@ -192,6 +192,16 @@ int cudahm_get_theta(cudahm_t h, double* theta_host, double* S_theta_host);
 
 int cudahm_get_stats(cudahm_t h, cudahm_stats* s);
 
+/* Effective sample size of each column of a row-major sample matrix x_host (rows x cols,
+ * host, e.g. the theta rows of cudahm_get_samples), written to ess_out (cols doubles, host).
+ * The paper measures samplers by the time to an ESS of about 1000 in the population
+ * parameters after burn-in (Sec. 3). Estimator: Geyer's initial monotone sequence on the
+ * biased autocovariances (pair sums rho_2m + rho_2m+1 summed while positive, each capped by
+ * the previous; tau = 2 sum - 1, at least 1/rows; ESS = rows/tau); rows < 4 or a constant
+ * column give ESS = rows. Host computation, no handle or GPU needed. Returns CUDAHM_EINVAL for
+ * NULL pointers or rows, cols < 1 and CUDAHM_ENUMERIC for a non-finite sample. */
+int cudahm_ess(const double* x_host, int64_t rows, int32_t cols, double* ess_out);
+
 /* Per-member log target lp_i = log l_i(chi_i) + log f(chi_i;theta) without the theta-only
  * term (-inf off support), at the current latents and the given theta (p doubles, host).
  * Writes N doubles to lp_host. Evaluated by a device kernel in the handle's precision. */

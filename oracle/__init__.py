@@ -28,9 +28,9 @@ _LIB = os.path.join(_HERE, "libcudahm_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-NN1, MVN3, LF, BB1 = 0, 1, 2, 3
-MODEL_D = {NN1: 1, MVN3: 3, LF: 1, BB1: 1}
-MODEL_P = {NN1: 2, MVN3: 9, LF: 3, BB1: 3}
+NN1, MVN3, LF, BB1, NN3 = 0, 1, 2, 3, 4
+MODEL_D = {NN1: 1, MVN3: 3, LF: 1, BB1: 1, NN3: 3}
+MODEL_P = {NN1: 2, MVN3: 9, LF: 3, BB1: 3, NN3: 3}
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _u8p = ctypes.POINTER(ctypes.c_uint8)
@@ -79,7 +79,7 @@ def lib():
             L.orc_bb1_H.restype = ctypes.c_double
             L.orc_bb1_etabar.argtypes = [_dp, _dp]
             L.orc_bb1_etabar.restype = ctypes.c_double
-            L.orc_logf_obj.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
+            L.orc_logf_obj.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
             L.orc_logf_obj.restype = ctypes.c_double
             L.orc_member_logdens.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp,
                                              _dp]
@@ -215,11 +215,13 @@ def bb1_etabar(theta, consts) -> float:
     return lib().orc_bb1_etabar(_p(th), _p(c))
 
 
-def logf_obj(model, chi, theta) -> float:
-    """log f_obj(chi;theta) of one member (the population term of its target)."""
+def logf_obj(model, chi, theta, consts=None) -> float:
+    """log f_obj(chi;theta) of one member (the population term of its target); consts are
+    needed by models that read them (NN3: the packed lower triangle of C_pop)."""
     c = _f64(np.atleast_1d(chi))
     th = _f64(theta)
-    return lib().orc_logf_obj(model, MODEL_D[model], _p(c), _p(th))
+    k = _f64(consts if consts is not None else np.zeros(8))
+    return lib().orc_logf_obj(model, MODEL_D[model], _p(c), _p(th), _p(k))
 
 
 def member_logdens(model, y, aux, consts, chi, theta):

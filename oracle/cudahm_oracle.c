@@ -57,6 +57,7 @@
 #define ORC_MVN3 1
 #define ORC_LF 2
 #define ORC_BB1 3
+#define ORC_NN3 4
 
 /* ------------------------------------------------------------------------- */
 /* R5: Philox4x32-10 block cipher (Salmon, Moraes, Dror, Shaw, SC'11).         */
@@ -475,14 +476,38 @@ static double mvn3_loglike(const double* chi, const double* y, const double* s) 
   return acc;
 }
 
+/* Normal-normal benchmark, d = 3 (Sec. 3): C_pop known, theta = mu (flat prior). consts =
+ * the lower triangle of C_pop packed row-major (C11, C21, C22, C31, C32, C33). log f_obj =
+ * -(chi - mu)^T C_pop^{-1} (chi - mu)/2 through the Cholesky factor L of C_pop (L L^T = C_pop)
+ * and a forward substitution; ln det C_pop is a constant, so c(theta) = 0. */
+static void nn3_factor(const double* C, double Lc[9]) {
+  double A[9] = {C[0], C[1], C[3], C[1], C[2], C[4], C[3], C[4], C[5]};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b <= a; ++b) {
+      double v = A[3 * a + b];
+      for (int k = 0; k < b; ++k) v -= Lc[3 * a + k] * Lc[3 * b + k];
+      Lc[3 * a + b] = (a == b) ? sqrt(v) : v / Lc[3 * b + b];
+    }
+  Lc[1] = Lc[2] = Lc[5] = 0.0;
+}
+static double nn3_logf_obj(const double* chi, const double* th, const double* C) {
+  double Lc[9];
+  nn3_factor(C, Lc);
+  double r[3] = {chi[0] - th[0], chi[1] - th[1], chi[2] - th[2]};
+  double z0 = r[0] / Lc[0];
+  double z1 = (r[1] - Lc[3] * z0) / Lc[4];
+  double z2 = (r[2] - Lc[6] * z0 - Lc[7] * z1) / Lc[8];
+  return -0.5 * (z0 * z0 + z1 * z1 + z2 * z2);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Problem dispatch                                                            */
 /* ------------------------------------------------------------------------- */
 typedef struct {
   int model, d, p;
   int64_t n;
-  const double* y;    /* NN1: y[n]; LF: Fhat[n]; MVN3: y[n*3] */
-  const double* aux;  /* NN1: sigma[n]; LF: r[n]; MVN3: s[n*3] */
+  const double* y;    /* NN1: y[n]; LF: Fhat[n]; MVN3, NN3: y[n*3] */
+  const double* aux;  /* NN1: sigma[n]; LF: r[n]; MVN3, NN3: s[n*3] */
   const double* consts;
   gl_rule rule;       /* LF only */
 } problem;
@@ -492,6 +517,7 @@ static double logf_obj(const problem* P, const double* chi, const double* th) {
     case ORC_NN1: return nn1_logf_obj(chi[0], th);
     case ORC_LF: return lf_logf_obj(chi[0], th);
     case ORC_BB1: return bb1_logf_obj(chi[0], th);
+    case ORC_NN3: return nn3_logf_obj(chi, th, P->consts);
     default: return mvn3_logf_obj(chi, th);
   }
 }
@@ -500,7 +526,7 @@ static double loglike(const problem* P, int64_t i, const double* chi) {
     case ORC_NN1: return nn1_loglike(chi[0], P->y[i], P->aux[i]);
     case ORC_LF: return lf_loglike(chi[0], P->y[i], P->aux[i], P->consts);
     case ORC_BB1: return bb1_loglike(chi[0], P->y[i], P->aux[i], P->consts);
-    default: return mvn3_loglike(chi, P->y + 3 * i, P->aux + 3 * i);
+    default: return mvn3_loglike(chi, P->y + 3 * i, P->aux + 3 * i);  /* MVN3, NN3 */
   }
 }
 /* member log target lp_i = log l_i + log f_obj; -inf off support */
@@ -514,6 +540,7 @@ static double c_theta(const problem* P, const double* th) {
     case ORC_NN1: return nn1_c(th);
     case ORC_LF: return 0.0;
     case ORC_BB1: return 0.0;
+    case ORC_NN3: return 0.0;
     default: return mvn3_c(th);
   }
 }
@@ -526,11 +553,12 @@ static double logprior(const problem* P, const double* th) {
   }
 }
 
-/* log f_obj(chi;theta) alone (the population term of the member target), for the pins. */
-double orc_logf_obj(int model, int d, const double* chi, const double* theta) {
+/* log f_obj(chi;theta) alone (the population term of the member target), for the pins;
+ * consts: the model constants (nullable unless the model reads them, as NN3 does). */
+double orc_logf_obj(int model, int d, const double* chi, const double* theta, const double* consts) {
   problem P;
   memset(&P, 0, sizeof(P));
-  P.model = model; P.d = d;
+  P.model = model; P.d = d; P.consts = consts;
   return logf_obj(&P, chi, theta);
 }
 

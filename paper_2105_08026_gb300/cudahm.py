@@ -101,7 +101,7 @@ EXPORTED = [
     "cudahm_sizeof_config", "cudahm_sizeof_stats", "cudahm_last_error", "cudahm_destroy",
     "cudahm_lf_etabar_noalloc", "cudahm_batch_run", "cudahm_server_create", "cudahm_server_submit",
     "cudahm_server_poll", "cudahm_server_wait", "cudahm_server_result", "cudahm_server_stats",
-    "cudahm_server_destroy",
+    "cudahm_server_destroy", "cudahm_ess",
 ]
 
 
@@ -147,6 +147,7 @@ def lib():
                                    ctypes.POINTER(CudahmTune)]
     L.cudahm_destroy.argtypes = [vp]
     L.cudahm_destroy.restype = None
+    L.cudahm_ess.argtypes = [_dp, i64, i32, _dp]
     for name in EXPORTED:
         if name not in ("cudahm_config_init", "cudahm_sizeof_config", "cudahm_sizeof_stats", "cudahm_last_error",
                         "cudahm_destroy"):
@@ -250,6 +251,16 @@ def cudahm_eval_detection(h, F) -> np.ndarray:
     F = _f64(F)
     out = np.zeros(F.size)
     _check(lib().cudahm_eval_detection(h, _dptr(F), _dptr(out), F.size))
+    return out
+
+
+def cudahm_ess(x) -> np.ndarray:
+    """Effective sample size of each column of a sample matrix (rows x cols), host-side."""
+    x = _f64(x)
+    if x.ndim == 1:
+        x = x[:, None]
+    out = np.zeros(x.shape[1])
+    _check(lib().cudahm_ess(_dptr(x), x.shape[0], x.shape[1], _dptr(out)))
     return out
 
 

@@ -19,6 +19,8 @@ Workloads (all numpy ``Generator(PCG64(seed))``):
   heteroscedastic diagonal measurement errors (Sec. 3 with unknown C_pop).
 - ``bb1_data``: the paper's own simulation (Sec. 5.1-5.2): BB1 luminosity function, r ~ r^2 on
   [0, r_max], flux-dependent measurement error sigma(F), detection at nu = 5 times the error.
+- ``nn3_data``: the paper's normal-normal benchmark (Sec. 3): chi_i ~ N(mu_pop, D R D) with the
+  printed mu_pop, D and R, y_ij ~ N(chi_ij, sigma_j^2) with the printed sigma_j for every i.
 """
 from __future__ import annotations
 
@@ -263,7 +265,44 @@ def mvn3_theta_from(mu, C) -> np.ndarray:
                      math.log(L[2, 2])])
 
 
+# Sec. 3 normal-normal benchmark: population means, marginal standard deviations D, correlation
+# matrix R, measurement scales sigma_j (the values printed in that section).
+NN3_MU = (1.2, -0.4, 3.4)
+NN3_D = (2.3, 0.45, 13.4)
+NN3_R = ((1.0, 0.3, -0.5), (0.3, 1.0, 0.54), (-0.5, 0.54, 1.0))
+NN3_SIGMA = (1.2, 0.4, 0.24)
+
+
+def nn3_cov() -> np.ndarray:
+    """C_pop = D R D of the Sec. 3 benchmark."""
+    D = np.diag(NN3_D)
+    return D @ np.array(NN3_R) @ D
+
+
+def nn3_data(n: int, seed: int = 1004) -> MVN3Data:
+    """n members of the Sec. 3 benchmark population, measured with the common scales sigma_j."""
+    g = _rng(seed)
+    C = nn3_cov()
+    Lc = np.linalg.cholesky(C)
+    mu = np.array(NN3_MU)
+    chi = mu + g.standard_normal((n, 3)) @ Lc.T
+    s = np.tile(np.array(NN3_SIGMA), (n, 1))
+    y = chi + s * g.standard_normal((n, 3))
+    return MVN3Data(y=y, s=s, chi_true=chi, mu=mu, C_pop=C)
+
+
+def nn3_consts(C) -> np.ndarray:
+    """Model constants of NN3: C_pop's lower triangle packed row-major (C11, C21, C22, C31, C32, C33)."""
+    C = np.asarray(C, dtype=np.float64)
+    return np.array([C[0, 0], C[1, 0], C[1, 1], C[2, 0], C[2, 1], C[2, 2]])
+
+
 # ----------------------------------------------------------- run settings --
+def nn3_settings(data: MVN3Data, scale: float = 0.05):
+    """theta_init (the sample mean of y), theta_prop_scale, consts (C_pop known) for NN3."""
+    return data.y.mean(axis=0).copy(), np.full(3, scale), nn3_consts(data.C_pop)
+
+
 def nn1_settings(data: NN1Data):
     """theta_init, theta_prop_scale, consts for the NN1 model (flat mu, flat ln tau on [-10, 10])."""
     theta0 = np.array([float(np.mean(data.y)), math.log(max(float(np.std(data.y)), 1e-3))])

@@ -64,6 +64,10 @@ def test_config_defaults(lib):
     (lambda c: [setattr(c, "model", cudahm.BB1), setattr(c, "precision", cudahm.FP32)] and None,
      cudahm.EUNSUPPORTED),  # BB1 has the FP64 form only
     (lambda c: c.theta_init.__setitem__(1, 50.0), cudahm.EINVAL),
+    (lambda c: [setattr(c, "model", cudahm.NN3), setattr(c, "d", 3)] and None, cudahm.EINVAL),  # C_pop = 0
+    (lambda c: [setattr(c, "model", cudahm.NN3), setattr(c, "d", 3),
+                [c.model_consts.__setitem__(q, v) for q, v in enumerate((1.0, 2.0, 1.0, 0.0, 0.0, 1.0))]] and None,
+     cudahm.EINVAL),  # C_pop not positive definite
 ])
 def test_invalid_configs_rejected(lib, mutate, code):
     cfg = cudahm.cudahm_config_init(cudahm.NN1, 100)
