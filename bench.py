@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--nn3-burn", type=int, default=40_000)
     ap.add_argument("--nn3-sweeps", type=int, default=75_000)
     ap.add_argument("--nn3-chains", type=int, default=64)
+    ap.add_argument("--nn3-chain-sweeps", type=int, default=10_000)
+    ap.add_argument("--nn3-chains-max-n", type=int, default=10_000)
     ap.add_argument("--bb1-sweeps", type=int, default=1000)
     ap.add_argument("--mvn3-sweeps", type=int, default=3000)
     return ap.parse_args()
@@ -351,7 +353,8 @@ def run_nn3_ess(args, cudahm, stream, device):
     (the paper's 4e4 burn-in and 7.5e4 kept sweeps), CUDA events on the sampler's stream, ESS of
     the kept theta rows by the library's estimator. FP64, and FP32 at N = 1e4. Then the same
     with --nn3-chains independent chains on the same data in one batched run (the paper's Stan
-    protocol pools parallel chains; ESS of the pooled draws = the sum of the chains' ESS)."""
+    protocol pools parallel chains; ESS of the pooled draws = the sum of the chains' ESS), for
+    N <= --nn3-chains-max-n, each chain --nn3-chain-sweeps timed sweeps after the same burn-in."""
     import torch
     from paper_2105_08026_gb300 import synth
     out = []
@@ -386,7 +389,7 @@ def run_nn3_ess(args, cudahm, stream, device):
                         "member_accept": st.member_accepts / (st.sweeps * n),
                         "launch_shape": [st.grid_blocks, st.block_threads, st.objects_per_thread]})
         R = args.nn3_chains
-        if R > 1:
+        if R > 1 and n <= args.nn3_chains_max_n:
             chains = []
             for r in range(R):
                 c = cudahm.Sampler(cudahm.NN3, n, theta_init=theta0, theta_prop_scale=scale, model_consts=consts,
@@ -394,7 +397,7 @@ def run_nn3_ess(args, cudahm, stream, device):
                 c.set_data(data.y, data.s)
                 chains.append(c)
             _, tune = cudahm.batch_run(chains, args.nn3_burn, 0)
-            K = args.nn3_sweeps
+            K = args.nn3_chain_sweeps
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)

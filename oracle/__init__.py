@@ -88,6 +88,12 @@ def lib():
                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _dp, _i64p, _i64p, _i64p,
                                    ctypes.c_int64, _dp, _dp, _u8p, _dp, _dp, _dp, _dp, _u8p, _dp])
             L.orc_run.restype = ctypes.c_int
+            L.orc_marg_logp.argtypes = [ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp]
+            L.orc_marg_run.argtypes = ([ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp,
+                                        ctypes.c_uint64, _dp, _dp, _dp, _i64p, _dp, ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.c_int64, _dp, _i64p, _i64p, ctypes.c_int64, _dp, _dp, _dp, _dp,
+                                        _u8p, _dp])
+            L.orc_marg_run.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -232,6 +238,59 @@ def member_logdens(model, y, aux, consts, chi, theta):
     out = np.zeros(n)
     lib().orc_member_logdens(model, d, n, _p(y), _p(aux), _p(consts), _p(chi), _p(theta), _p(out))
     return out
+
+
+def marg_logp(model, y, aux, consts, theta):
+    """Per-member log p_i(theta) = log int l_i(chi) f(chi;theta) dchi by the cubature rule of
+    the marginal form (NN1: aux = sigma_i; LF: aux = r_i)."""
+    y, aux, theta = _f64(y), _f64(aux), _f64(theta)
+    consts = _f64(consts if consts is not None else np.zeros(1))
+    out = np.zeros(y.size)
+    lib().orc_marg_logp(model, y.size, _p(y), _p(aux), _p(consts), _p(theta), _p(out))
+    return out
+
+
+class MarginalChain:
+    """theta-only chain on the marginal posterior (latents integrated out by the cubature rule)."""
+
+    def __init__(self, model, y, aux, consts, theta_init, theta_prop_scale, seed, adapt_exponent=2.0 / 3.0,
+                 theta_target_accept=0.4, adapt_theta=True):
+        self.model = model
+        self.p = MODEL_P[model]
+        self.y = _f64(y)
+        self.aux = _f64(aux)
+        self.n = self.y.size
+        self.consts = _f64(consts if consts is not None else np.zeros(1))
+        self.seed = int(seed)
+        self.params = np.array([0.4, adapt_exponent, theta_target_accept, 1.0 if adapt_theta else 0.0])
+        self.theta = _f64(theta_init).copy()
+        self.S_theta = np.diag(_f64(theta_prop_scale)).reshape(-1).copy()
+        self.lp = marg_logp(model, self.y, self.aux, self.consts, self.theta)
+        self.sweep = ctypes.c_int64(0)
+        self.etabar = ctypes.c_double(0.0)
+        self.theta_accepts = ctypes.c_int64(0)
+
+    def run(self, n_burn, n_iter, thin=1, trace_sweeps=0):
+        p = self.p
+        total = n_burn + n_iter
+        cap = (n_iter // thin) if thin > 0 else 0
+        rows = np.zeros((max(cap, 1), p))
+        rows_out = ctypes.c_int64(0)
+        T = int(min(trace_sweeps, total))
+        tr = None
+        args_tr = [None] * 6
+        if T > 0:
+            tr = dict(theta_prop=np.zeros((T, p)), D=np.zeros(T), logalpha=np.zeros(T), utheta=np.zeros(T),
+                      tacc=np.zeros(T, np.uint8), etabar=np.zeros(T))
+            args_tr = [_p(tr["theta_prop"]), _p(tr["D"]), _p(tr["logalpha"]), _p(tr["utheta"]),
+                       _p(tr["tacc"], _u8p), _p(tr["etabar"])]
+        rc = lib().orc_marg_run(self.model, p, self.n, _p(self.y), _p(self.aux), _p(self.consts), _p(self.params),
+                                self.seed, _p(self.theta), _p(self.S_theta), _p(self.lp), ctypes.byref(self.sweep),
+                                ctypes.byref(self.etabar), n_burn, n_iter, thin, _p(rows), ctypes.byref(rows_out),
+                                ctypes.byref(self.theta_accepts), T, *args_tr)
+        if rc != 0:
+            raise RuntimeError(f"oracle marginal run failed: {rc}")
+        return rows[: rows_out.value].copy(), tr
 
 
 # ---------------------------------------------------------------- chain ----

@@ -705,3 +705,177 @@ int orc_run(int model, int d, int p, int64_t n, const double* y, const double* a
   if (has_rule) gl_rule_free(&P.rule);
   return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Latent marginalisation by cubature (Sec. 6: for low-dimensional latents the  */
+/* members can be integrated out by quadrature, leaving an MCMC over theta      */
+/* alone). Reading R9 fixes the rule:                                           */
+/*   log p_i(theta) = log int l_i(chi) f_obj(chi;theta) dchi                    */
+/* by Gauss-Legendre panels in chi:                                             */
+/*   NN1: one 64-node panel on m +- 10 s, with m, s the mean and standard       */
+/*        deviation of the (Gaussian) integrand;                                */
+/*   LF:  with F_b = Fhat + 10 sigma_F and F_c = max(Fhat - 10 sigma_F, Fhat/2), */
+/*        a 64-node panel on [max(ln L_low, ln(F_c/q)), ln(F_b/q)] and a 32-node */
+/*        panel on [ln L_low, ln(F_c/q)] when that is not empty; -inf when       */
+/*        ln L_low >= ln(F_b/q) (no likelihood mass left on the support).        */
+/* The marginal posterior of theta is prod_i p_i(theta) e^{N c(theta)} pi(theta) */
+/* (LF: divided by etabar(theta)^N, as in the member form).                     */
+/* ------------------------------------------------------------------------- */
+#define ORC_MARG_NPEAK 64
+#define ORC_MARG_NTAIL 32
+#define ORC_MARG_K 10.0
+
+typedef struct {
+  double xp[ORC_MARG_NPEAK], wp[ORC_MARG_NPEAK];
+  double xt[ORC_MARG_NTAIL], wt[ORC_MARG_NTAIL];
+} marg_rule;
+
+static void marg_rule_init(marg_rule* R) {
+  orc_gauss_legendre(ORC_MARG_NPEAK, R->xp, R->wp);
+  orc_gauss_legendre(ORC_MARG_NTAIL, R->xt, R->wt);
+}
+
+/* log of sum_j w_j exp(v_j), by the largest v_j */
+static double log_wsum(const double* v, const double* w, int m) {
+  double vmax = -INFINITY;
+  for (int j = 0; j < m; ++j)
+    if (v[j] > vmax) vmax = v[j];
+  if (vmax == -INFINITY) return -INFINITY;
+  ksum s = {0.0, 0.0};
+  for (int j = 0; j < m; ++j) ks_add(&s, w[j] * exp(v[j] - vmax));
+  return vmax + log(ks_val(&s));
+}
+
+static double marg_logp_one(const problem* P, const marg_rule* R, int64_t i, const double* th) {
+  double v[ORC_MARG_NPEAK + ORC_MARG_NTAIL], w[ORC_MARG_NPEAK + ORC_MARG_NTAIL];
+  int m = 0;
+  if (P->model == ORC_NN1) {
+    double y = P->y[i], sig = P->aux[i], tau = exp(th[1]);
+    double s2 = sig * sig, t2 = tau * tau;
+    double mean = (y * t2 + th[0] * s2) / (s2 + t2);
+    double sd = sig * tau / sqrt(s2 + t2);
+    double a = mean - ORC_MARG_K * sd, b = mean + ORC_MARG_K * sd;
+    for (int j = 0; j < ORC_MARG_NPEAK; ++j) {
+      double chi = 0.5 * (a + b) + 0.5 * (b - a) * R->xp[j];
+      v[m] = nn1_loglike(chi, y, sig) + nn1_logf_obj(chi, th);
+      w[m] = 0.5 * (b - a) * R->wp[j];
+      ++m;
+    }
+    return log_wsum(v, w, m);
+  }
+  /* LF */
+  double fhat = P->y[i], q = lf_q(P->aux[i]), sigF = P->consts[0];
+  double Fb = fhat + ORC_MARG_K * sigF;
+  double Fc = fhat - ORC_MARG_K * sigF;
+  if (Fc < 0.5 * fhat) Fc = 0.5 * fhat;
+  double chib = log(Fb / q), chic = log(Fc / q), lo = th[2];
+  double a2 = (chic > lo) ? chic : lo;
+  if (!(a2 < chib)) return -INFINITY;
+  for (int j = 0; j < ORC_MARG_NPEAK; ++j) {
+    double chi = 0.5 * (a2 + chib) + 0.5 * (chib - a2) * R->xp[j];
+    v[m] = lf_loglike(chi, fhat, P->aux[i], P->consts) + lf_logf_obj(chi, th);
+    w[m] = 0.5 * (chib - a2) * R->wp[j];
+    ++m;
+  }
+  if (lo < chic) {
+    for (int j = 0; j < ORC_MARG_NTAIL; ++j) {
+      double chi = 0.5 * (lo + chic) + 0.5 * (chic - lo) * R->xt[j];
+      v[m] = lf_loglike(chi, fhat, P->aux[i], P->consts) + lf_logf_obj(chi, th);
+      w[m] = 0.5 * (chic - lo) * R->wt[j];
+      ++m;
+    }
+  }
+  return log_wsum(v, w, m);
+}
+
+/* Per-member log p_i(theta) of the rule above (NN1: aux = sigma_i; LF: aux = r_i). */
+void orc_marg_logp(int model, int64_t n, const double* y, const double* aux, const double* consts,
+                   const double* theta, double* out) {
+  problem P;
+  memset(&P, 0, sizeof(P));
+  P.model = model; P.d = 1; P.n = n; P.y = y; P.aux = aux; P.consts = consts;
+  marg_rule R;
+  marg_rule_init(&R);
+  for (int64_t i = 0; i < n; ++i) out[i] = marg_logp_one(&P, &R, i, theta);
+}
+
+/* theta-only chain on the marginal posterior: the theta step of orc_run with
+ * D = sum_i [log p_i(theta') - log p_i(theta)] in place of the sum over log f_obj;
+ * the same theta draws (Philox stream 1), RAM on theta (R3) and index (R1).
+ * lp[n]: log p_i at the current theta (updated on accept). Trace arrays nullable. */
+int orc_marg_run(int model, int p, int64_t n, const double* y, const double* aux, const double* consts,
+                 const double* params_vec, uint64_t seed, double* theta, double* S_theta, double* lp,
+                 int64_t* sweep, double* etabar_cur, int64_t n_burn, int64_t n_iter, int64_t thin,
+                 double* theta_rows, int64_t* rows_out, int64_t* theta_accepts, int64_t trace_sweeps,
+                 double* tr_theta_prop, double* tr_D, double* tr_logalpha, double* tr_utheta, uint8_t* tr_tacc,
+                 double* tr_etabar) {
+  problem P;
+  memset(&P, 0, sizeof(P));
+  P.model = model; P.d = 1; P.p = p; P.n = n; P.y = y; P.aux = aux; P.consts = consts;
+  const int has_rule = (model == ORC_LF);
+  if (has_rule) gl_rule_init(&P.rule, (int)consts[3], (int)consts[4]);
+  if (has_rule && *etabar_cur == 0.0) *etabar_cur = lf_etabar_rule(theta, &P.rule, consts);
+  marg_rule R;
+  marg_rule_init(&R);
+  double* lpn = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  const double adapt_exponent = params_vec[1], theta_target_accept = params_vec[2];
+  const int adapt_theta = (int)params_vec[3];
+  int64_t total = n_burn + n_iter, rows = 0, tacc = 0;
+  double U[9], th_prop[9];
+  for (int64_t s = 0; s < total; ++s) {
+    int64_t k = *sweep + 1;
+    double eta = pow((double)(k + 1), -adapt_exponent); /* R1 */
+    double ut;
+    orc_draw(seed, 1u, 0u, (uint32_t)k, p, U, &ut);
+    for (int a = 0; a < p; ++a) {
+      double t = theta[a];
+      for (int b = 0; b <= a; ++b) t += S_theta[a * p + b] * U[b];
+      th_prop[a] = t;
+    }
+    double lpri_new = logprior(&P, th_prop);
+    double logalpha = -INFINITY, D = 0.0, eb_new = 0.0;
+    if (lpri_new != -INFINITY) {
+      ksum acc_sum = {0.0, 0.0};
+      int off = 0;
+      for (int64_t i = 0; i < n; ++i) {
+        lpn[i] = marg_logp_one(&P, &R, i, th_prop);
+        if (lpn[i] == -INFINITY) { off = 1; break; }
+        ks_add(&acc_sum, lpn[i] - lp[i]);
+      }
+      if (!off) {
+        D = ks_val(&acc_sum);
+        logalpha = D + (double)n * (c_theta(&P, th_prop) - c_theta(&P, theta)) + lpri_new - logprior(&P, theta);
+        if (has_rule) {
+          eb_new = lf_etabar_rule(th_prop, &P.rule, consts);
+          logalpha -= (double)n * (log(eb_new) - log(*etabar_cur));
+        }
+      } else {
+        D = -INFINITY;
+      }
+    }
+    int acc = log(ut) < logalpha; /* R4 */
+    double alpha = (logalpha >= 0.0) ? 1.0 : exp(logalpha);
+    if (s < trace_sweeps) {
+      for (int a = 0; a < p; ++a) tr_theta_prop[s * p + a] = th_prop[a];
+      tr_D[s] = D; tr_logalpha[s] = logalpha; tr_utheta[s] = ut; tr_tacc[s] = (uint8_t)acc;
+      tr_etabar[s] = eb_new;
+    }
+    if (acc) {
+      for (int a = 0; a < p; ++a) theta[a] = th_prop[a];
+      for (int64_t i = 0; i < n; ++i) lp[i] = lpn[i];
+      if (has_rule) *etabar_cur = eb_new;
+      ++tacc;
+    }
+    if (adapt_theta) orc_ram_update(p, S_theta, U, alpha, theta_target_accept, eta);
+    if (s >= n_burn && thin > 0 && ((s - n_burn + 1) % thin) == 0 && theta_rows) {
+      for (int a = 0; a < p; ++a) theta_rows[rows * p + a] = theta[a];
+      ++rows;
+    }
+    *sweep = k;
+  }
+  free(lpn);
+  if (rows_out) *rows_out = rows;
+  if (theta_accepts) *theta_accepts += tacc;
+  if (has_rule) gl_rule_free(&P.rule);
+  return 0;
+}
