@@ -58,6 +58,11 @@ FP64_FLOP_PER_SWEEP = 4.197e7
 MVN3_F32_FP64_FLOP_PER_UPDATE = 98.4
 MVN3_F32_DRAM_BYTES_PER_UPDATE = 127.6
 
+# FP64 work of one member integral of the marginal form on the LF workload (96 nodes, with the
+# step's share of the selection rule), from ncu's smsp__sass_thread_inst_executed_op_d{fma,add,mul}
+# counters on marg_kernel<LF> (profiles/marg_kernel_lf_n300000.md): 2 DFMA + DADD + DMUL.
+MARG_FP64_FLOP_PER_MEMBER = 5045.0
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -81,6 +86,9 @@ def parse():
     ap.add_argument("--no-mvn3", action="store_true")
     ap.add_argument("--no-bb1", action="store_true")
     ap.add_argument("--no-nn3", action="store_true")
+    ap.add_argument("--no-marginal", action="store_true")
+    ap.add_argument("--marginal-burn", type=int, default=300)
+    ap.add_argument("--marginal-steps", type=int, default=1500)
     ap.add_argument("--nn3-sizes", default="100,1000,10000,30000")
     ap.add_argument("--nn3-burn", type=int, default=40_000)
     ap.add_argument("--nn3-sweeps", type=int, default=75_000)
@@ -419,6 +427,45 @@ def run_nn3_ess(args, cudahm, stream, device):
             "metric": "post-burn-in seconds to ESS=1000 (min over mu components)", "runs": out}
 
 
+def run_marginal(args, cudahm, stream, device, data, theta0, scale, consts, peak_fp64):
+    """The marginal form on the LF workload (N = 3e5, 1024 x 1024 rule, FP64): every member's
+    latent integrated out by the cubature rule (96 nodes per member) and a theta-only chain.
+    --marginal-burn untimed steps, then --marginal-steps timed (CUDA events on the sampler's
+    stream); reports theta steps/s, member integrals/s and the theta ESS per second."""
+    import torch
+    n = data.fhat.size
+    s = cudahm.Sampler(cudahm.LF, n, theta_init=theta0, theta_prop_scale=scale, model_consts=consts, seed=11,
+                       device=device, stream=stream.cuda_stream, use_torch_allocator=True, marginal=True)
+    y_dev = torch.from_numpy(data.fhat).cuda()
+    r_dev = torch.from_numpy(data.r).cuda()
+    cudahm.cudahm_set_data_device(s.h, y_dev.data_ptr(), r_dev.data_ptr(), n)
+    s.run(args.marginal_burn, 0)
+    K = args.marginal_steps
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rows = s.run(0, K, 1)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    ess = cudahm.cudahm_ess(rows)
+    st = s.stats()
+    s.close()
+    out = {"workload": "LF N=3e5, latents integrated out by cubature (64 + 32 Gauss-Legendre nodes per member), "
+                       "theta-only chain, 1024x1024 selection rule, FP64",
+           "steps": K, "burn_in": args.marginal_burn, "ms_per_step": ms / K, "steps_per_s": K / (ms * 1e-3),
+           "member_integrals_per_s": n * K / (ms * 1e-3), "theta_accept": st.theta_accepts / st.sweeps,
+           "ess": ess.tolist(), "ess_per_s_min": float(ess.min()) / (ms * 1e-3),
+           "launch_shape": [st.grid_blocks, st.block_threads], "dtype": "f64"}
+    if MARG_FP64_FLOP_PER_MEMBER is not None and peak_fp64:
+        ach = MARG_FP64_FLOP_PER_MEMBER * n * K / (ms * 1e-3)
+        out["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "achieved": ach / 1e12, "peak": peak_fp64 / 1e12,
+                           "frac": ach / peak_fp64, "kernel": "marg_kernel<LF>",
+                           "peak_source": "FP64 DFMA stream measured live on this GPU (x2 flops)"}
+    return out
+
+
 def run_served(args, cudahm, device):
     """Poisson request stream (rate 20/s for --serve-seconds) into the continuous-batching server:
     each request is NN1 or LF with probability 1/2, N log-uniform on [1e3, 3e5], 5000 sweeps,
@@ -521,6 +568,7 @@ def run_cuda(args):
     kernel_ms = 0.0
     launches = 0
     rows_total = 0
+    kept = []
     for ns in chunks:
         flush.zero_()  # write 256 MB > L2 between timed launches
         torch.cuda.synchronize()
@@ -535,6 +583,7 @@ def run_cuda(args):
         nl = math.ceil(ns / 4096)
         launches += 2 * nl  # per chunk of <= 4096 sweeps: theta-table kernel + persistent sweep kernel
         rows_total += rows.shape[0]
+        kept.append(rows)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -588,6 +637,13 @@ def run_cuda(args):
     nn3 = None
     if not args.no_nn3 and rank == 0:
         nn3 = run_nn3_ess(args, cudahm, stream, local)
+    marg = None
+    if not args.no_marginal and rank == 0:
+        marg = run_marginal(args, cudahm, stream, local, data, theta0, scale, consts, peak)
+        all_rows = np.concatenate(kept, axis=0)
+        ess = cudahm.cudahm_ess(all_rows)
+        marg["member_form_same_workload"] = {"ess": ess.tolist(), "sweeps": int(all_rows.shape[0]),
+                                             "ess_per_s_min": float(ess.min()) / (total_ms * 1e-3)}
 
     # e2e through the public API with host buffers (every iteration: H2D data, run, D2H samples)
     e2e = None
@@ -643,7 +699,8 @@ def run_cuda(args):
                        "member state register-resident within a launch", "timed_launches": R,
                        "launch_shape": [st.grid_blocks, st.block_threads, st.objects_per_thread]},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
-            "fp32_bulk": fp32, "batched_fp32": batched, "served_fp32": served, "mvn3": mvn3, "bb1": bb1, "nn3_ess": nn3}
+            "fp32_bulk": fp32, "batched_fp32": batched, "served_fp32": served, "mvn3": mvn3, "bb1": bb1, "nn3_ess": nn3,
+            "marginal": marg}
     print(json.dumps(line), flush=True)
     s.close()
     if ws > 1:

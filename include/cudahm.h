@@ -132,7 +132,8 @@ typedef struct {
   int64_t barrier_timeout_ns;    /* bound on every device-side wait; 0 = 2 s */
   int32_t debug_skip_barrier_cta;/* >= 0: that block never arrives at the grid barrier (tests the
                                     timeout path); -1 = off */
-  int32_t reserved;
+  int32_t marginal;              /* 1: integrate each member's latent out by cubature and run the
+                                    chain on theta alone (NN1, LF; FP64; see cudahm_eval_marginal) */
 } cudahm_config;
 
 typedef struct {
@@ -207,6 +208,22 @@ int cudahm_ess(const double* x_host, int64_t rows, int32_t cols, double* ess_out
  * Writes N doubles to lp_host. Evaluated by a device kernel in the handle's precision. */
 int cudahm_eval_logdens(cudahm_t h, const double* theta_host, double* lp_host);
 
+/* Marginal form (Sec. 6: for low-dimensional latents the members can be integrated out by
+ * quadrature, leaving a Markov chain over theta alone). For NN1 and LF handles, writes
+ * lp_host[i] = log int l_i(chi) f(chi;theta) dchi (N doubles, host) at the given theta (p
+ * doubles, host), with l_i and f as in the member form (no theta-only term). The rule is fixed:
+ * NN1, a 64-node Gauss-Legendre panel on the integrand's mean +- 10 sd; LF, with
+ * F_b = Fhat_i + 10 sigma_F and F_c = max(Fhat_i - 10 sigma_F, Fhat_i/2), a 64-node panel in chi
+ * over [max(ln L_low, ln(F_c/q_i)), ln(F_b/q_i)] and a 32-node panel over [ln L_low, ln(F_c/q_i)]
+ * when that is not empty; -inf when ln L_low >= ln(F_b/q_i). A handle created with marginal = 1
+ * runs cudahm_run as a theta-only chain on prod_i p_i(theta) e^{N c(theta)} pi(theta) (LF:
+ * divided by etabar(theta)^N): the member form's theta proposal, RAM adaptation, draws and
+ * accept rule, with D = sum_i [log p_i(theta') - log p_i(theta)] summed exactly. Such a handle
+ * has no latents (set_chi and get_chi give CUDAHM_EUNSUPPORTED), needs Fhat_i > 0 for LF
+ * (CUDAHM_EINVAL at set_data) and runs alone (not in batch_run or the server). Other models:
+ * CUDAHM_EUNSUPPORTED. */
+int cudahm_eval_marginal(cudahm_t h, const double* theta_host, double* lp_host);
+
 /* LF and BB1: the selection integral etabar(theta) of the handle's rule at the given theta. */
 int cudahm_eval_etabar(cudahm_t h, const double* theta_host, double* out);
 
@@ -220,7 +237,9 @@ int cudahm_eval_detection(cudahm_t h, const double* F_host, double* eta_host, in
  * u = accept uniform, acc = 1 if accepted. Theta arrays: theta_prop [T][p], D [T] = sum of
  * log f(chi_i;theta') - log f(chi_i;theta) (-inf if a member is off the proposal's support,
  * 0 if theta' is off the prior), logalpha [T], utheta [T], tacc [T], etabar_prop [T]
- * (LF: etabar(theta'), else 0). Any pointer may be NULL. *t_out receives T. */
+ * (LF: etabar(theta'), else 0). Any pointer may be NULL. *t_out receives T. A marginal-form
+ * handle records no member arrays (delta, u, acc are left untouched) and its D is
+ * sum_i [log p_i(theta') - log p_i(theta)]. */
 int cudahm_get_trace(cudahm_t h, double* delta, double* u, uint8_t* acc, double* theta_prop, double* D,
                      double* logalpha, double* utheta, uint8_t* tacc, double* etabar_prop, int64_t* t_out);
 

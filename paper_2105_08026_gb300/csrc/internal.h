@@ -17,6 +17,8 @@ struct ChainState {
   long long member_acc;
   long long theta_acc;
   long long rows;    // rows written by the last launch
+  int mcur;          // marginal form: which of the two log p_i arrays holds the current theta's
+  int pad;
 };
 
 // Model constants used inside kernels.
@@ -34,6 +36,8 @@ struct ModelConsts {
   double ln_lower;      // ln(lower/l)
   // NN3: inverse of the lower Cholesky factor of the known C_pop, packed (00, 10, 11, 20, 21, 22)
   double li3[6];
+  double sigF;          // LF: sigma_F
+  int marginal;         // 1: latents integrated out by cubature (theta-only chain)
 };
 
 struct SweepArgs {
@@ -92,9 +96,18 @@ struct SweepArgs {
   const float* d32;   // FP32 form: precomputed binary32 member data (kData32 x n, member-minor)
   double* pub;        // theta' of the current sweep, published by block 0 (kPubWords doubles);
                       // its sequence word is bar[1]
+  double* marg_lp;           // marginal form: log p_i at two thetas, [2][n]
+  const double* marg_nodes;  // marginal form: panel nodes and weights (kMargNodeWords)
 };
 
 constexpr int kPubWords = 32;
+
+// Cubature rule of the marginal form: Gauss-Legendre panels of kMargPeak and kMargTail nodes,
+// the likelihood window +- kMargK standard deviations.
+constexpr int kMargPeak = 64;
+constexpr int kMargTail = 32;
+constexpr double kMargK = 10.0;
+constexpr int kMargNodeWords = 2 * (kMargPeak + kMargTail);
 
 // Progress of one population through a batched run (device memory, updated by the kernel).
 struct BatchProg {
@@ -115,6 +128,15 @@ cudaError_t launch_batch_tables(const SweepArgs* pops, const BatchProg* progs, i
 cudaError_t launch_data32(int model, long long n, const double* y, const double* aux, const ModelConsts& mc,
                           float* d32, cudaStream_t st);
 int data32_words(int model);
+
+// Marginal form (marginal.cu).
+size_t marg_smem_bytes(int model, int rows_smem);
+cudaError_t marg_occupancy(int model, int block, int smem_bytes, int* blocks_per_sm);
+cudaError_t launch_marg(const SweepArgs& a, int grid, int block, cudaStream_t st);
+cudaError_t launch_marg_eval(int model, long long n, const double* y, const double* aux, const double* theta_dev,
+                             const ModelConsts& mc, const double* math_tab, const double* nodes, double* out,
+                             cudaStream_t st);
+cudaError_t launch_marg_nodes(double* nodes, cudaStream_t st);
 
 // Records a failure for cudahm_last_error() (runtime.cu); returns code.
 int record_error(int code, const char* msg);

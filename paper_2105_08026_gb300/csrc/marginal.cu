@@ -1,0 +1,351 @@
+// Latent marginalisation by cubature: the theta-only chain (Sec. 6 proposes it for populations
+// whose members have a low-dimensional latent). Each member's latent is integrated out,
+//   log p_i(theta) = log int l_i(chi) f(chi;theta) dchi,
+// by fixed Gauss-Legendre panels in chi (NN1: one 64-node panel on the integrand's mean
+// +- 10 sd; LF: a 64-node panel over the likelihood window [max(ln L_low, ln(F_c/q_i)),
+// ln(F_b/q_i)], F_b = Fhat_i + 10 sigma_F, F_c = max(Fhat_i - 10 sigma_F, Fhat_i/2), and a
+// 32-node panel over [ln L_low, ln(F_c/q_i)] when that is not empty). The theta step is the
+// member form's (Sec. 2.2, last paragraph) with D = sum_i [log p_i(theta') - log p_i(theta)]:
+// one persistent cooperative launch per chunk of steps, each block integrating a contiguous
+// range of members (and its share of the selection rule's segments for LF), an exact
+// fixed-point sum over blocks, one bounded grid barrier per step, and the identical decision
+// in every block. log p_i at the current theta and at the proposal live in two device arrays
+// whose roles swap on acceptance.
+#include <cmath>
+#include <cstdint>
+#include <type_traits>
+
+#include "cudahm.h"
+#include "sweep_common.cuh"
+
+namespace chm {
+
+namespace {
+
+// Member integral of the rule above at the theta constants tc. nd: the panels' nodes and
+// weights on [-1, 1] (xp[64], wp[64], xt[32], wt[32]). The sum runs relative to the log
+// integrand at a point near its peak (the integrand's mean for NN1, the likelihood peak
+// clamped into the window for LF); every term is at most ~e^60 times that reference, so the
+// scaled sum neither overflows nor loses the peak. Returns -inf when the window leaves the
+// support.
+template <class M>
+__device__ double marg_logp(double y, double aux, const ThetaC& tc, const ModelConsts& mc, const double* T,
+                            const double* nd) {
+  const double* xp = nd;
+  const double* wp = nd + kMargPeak;
+  const double* xt = nd + 2 * kMargPeak;
+  const double* wt = nd + 2 * kMargPeak + kMargTail;
+  if constexpr (std::is_same<M, NN1>::value) {
+    // aux = 1/sigma^2, tc.a1 = 1/(2 tau^2): precision of the Gaussian integrand aux + 2 a1
+    const double prec = __dadd_rn(aux, __dmul_rn(2.0, tc.a1));
+    const double mean = __ddiv_rn(__fma_rn(y, aux, __dmul_rn(__dmul_rn(2.0, tc.a1), tc.a0)), prec);
+    const double h = __dmul_rn(kMargK, __dsqrt_rn(__drcp_rn(prec)));
+    const double m0 = __dadd_rn(NN1::loglike(mean, 0.0, y, aux, mc), NN1::logf(mean, 0.0, tc));
+    double s = 0.0;
+#pragma unroll 4
+    for (int j = 0; j < kMargPeak; ++j) {
+      const double chi = __fma_rn(h, xp[j], mean);
+      const double v = __dadd_rn(NN1::loglike(chi, 0.0, y, aux, mc), NN1::logf(chi, 0.0, tc));
+      s = __fma_rn(wp[j], exp_tab(__dsub_rn(v, m0), T), s);
+    }
+    return __dadd_rn(m0, log_tab(__dmul_rn(h, s), T));
+  } else {
+    // LF: y = Fhat_i, aux = q_i; tc.a3 = ln L_low
+    const double Fb = __fma_rn(kMargK, mc.sigF, y);
+    const double Fc = fmax(__fma_rn(-kMargK, mc.sigF, y), __dmul_rn(0.5, y));
+    const double chib = log_tab(__ddiv_rn(Fb, aux), T);
+    const double chic = log_tab(__ddiv_rn(Fc, aux), T);
+    const double lo = tc.a3;
+    const double a2 = fmax(chic, lo);
+    if (!(a2 < chib)) return -INFINITY;
+    const double cref = fmin(fmax(log_tab(__ddiv_rn(y, aux), T), a2), chib);
+    const double eref = exp_tab(cref, T);
+    const double m0 = __dadd_rn(LF::loglike(cref, eref, y, aux, mc), LF::logf(cref, eref, tc));
+    const double c2 = __dmul_rn(0.5, __dadd_rn(a2, chib)), h2 = __dmul_rn(0.5, __dsub_rn(chib, a2));
+    double s2 = 0.0;
+#pragma unroll 4
+    for (int j = 0; j < kMargPeak; ++j) {
+      const double chi = __fma_rn(h2, xp[j], c2);
+      const double e = exp_tab(chi, T);
+      const double v = __dadd_rn(LF::loglike(chi, e, y, aux, mc), LF::logf(chi, e, tc));
+      s2 = __fma_rn(wp[j], exp_tab(__dsub_rn(v, m0), T), s2);
+    }
+    double s = __dmul_rn(h2, s2);
+    if (lo < chic) {
+      const double c1 = __dmul_rn(0.5, __dadd_rn(lo, chic)), h1 = __dmul_rn(0.5, __dsub_rn(chic, lo));
+      double s1 = 0.0;
+#pragma unroll 4
+      for (int j = 0; j < kMargTail; ++j) {
+        const double chi = __fma_rn(h1, xt[j], c1);
+        const double e = exp_tab(chi, T);
+        const double v = __dadd_rn(LF::loglike(chi, e, y, aux, mc), LF::logf(chi, e, tc));
+        s1 = __fma_rn(wt[j], exp_tab(__dsub_rn(v, m0), T), s1);
+      }
+      s = __fma_rn(h1, s1, s);
+    }
+    return __dadd_rn(m0, log_tab(s, T));
+  }
+}
+
+template <class M>
+__global__ void __launch_bounds__(256, 2) marg_kernel(const SweepArgs a) {
+  extern __shared__ double s_dyn[];
+  __shared__ double s_theta[kMaxP], s_thp[kMaxP], s_Sth[kMaxP * kMaxP];
+  __shared__ ThetaC s_tc, s_tcp;
+  __shared__ double s_etabar, s_logeb, s_lpri, s_lpri_new;
+  __shared__ int s_stop, s_cur;
+  __shared__ long long s_rows_written, s_tacc;
+  __shared__ BlockRed s_red;
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int p = a.p;
+  constexpr bool is_lf = M::kRule;
+  const unsigned int nb0 = static_cast<unsigned int>((a.n * blockIdx.x) / gridDim.x);
+  const unsigned int nb1 = static_cast<unsigned int>((a.n * (blockIdx.x + 1)) / gridDim.x);
+  const bool skip_me = (a.skip_cta == static_cast<int>(blockIdx.x));
+  double* s_math = s_dyn;
+  double* s_nodes = s_math + kMathWords;
+  double* s_phi = s_nodes + kMargNodeWords;
+  const SegTab tab = segtab_carve(s_phi + (is_lf ? kPhiWords : 0), a.rows_smem);
+  for (int q = tid; q < kMathWords; q += blockDim.x) s_math[q] = a.math_tab[q];
+  for (int q = tid; q < kMargNodeWords; q += blockDim.x) s_nodes[q] = a.marg_nodes[q];
+  if (is_lf)
+    for (int q = tid; q < kPhiWords; q += blockDim.x) s_phi[q] = a.phi_coef[q];
+  const int nseg = is_lf ? lf_block_segments(a, blockIdx.x, gridDim.x) : 0;
+  __syncthreads();  // tables in place before thread 0 uses them
+
+  if (tid == 0) {
+    for (int q = 0; q < p; ++q) s_theta[q] = a.chain->theta[q];
+    for (int q = 0; q < p * p; ++q) s_Sth[q] = a.chain->S_theta[q];
+    s_etabar = a.chain->etabar;
+    s_logeb = is_lf ? log_etabar(s_etabar, s_math) : 0.0;
+    s_tc = M::consts(s_theta, a.mc, s_math);
+    s_lpri = M::logprior(s_theta, a.mc, s_math);
+    s_cur = a.chain->mcur;
+    s_rows_written = 0;
+    s_tacc = 0;
+    s_stop = 0;
+  }
+  __syncthreads();
+
+  for (long long s = 0; s < a.ns; ++s) {
+    if (tid == 0) {
+      double lp;
+      ThetaC tcp;
+      propose_theta<M>(a, s, p, s_theta, s_Sth, s_thp, lp, tcp, s_math);
+      s_lpri_new = lp;
+      s_tcp = tcp;
+    }
+    __syncthreads();
+    const bool prior_ok = (s_lpri_new != -INFINITY);
+    Xacc xd, xe;
+    xacc_zero(xd);
+    xacc_zero(xe);
+    XFlags fd = {0u, 0u, 0u}, fe = {0u, 0u, 0u};
+    unsigned int neg_big = 0, pos_big = 0;
+    if (prior_ok) {
+      const ThetaC tcp = s_tcp;
+      const double* lpc = a.marg_lp + static_cast<long long>(s_cur) * a.n;
+      double* lpn = a.marg_lp + static_cast<long long>(1 - s_cur) * a.n;
+      for (unsigned int i = nb0 + tid; i < nb1; i += blockDim.x) {
+        const double v = marg_logp<M>(__ldg(a.y + i), __ldg(a.aux + i), tcp, a.mc, s_math, s_nodes);
+        lpn[i] = v;
+        const double dn = (v == -INFINITY) ? -INFINITY : v - lpc[i];
+        if (disnan(dn)) fd.nan++;
+        else if (dhuge(dn)) {
+          if (dsign(dn)) neg_big++;  // no mass left on the proposal's support
+          else pos_big++;
+        } else {
+          xacc_add_double(xd, dn, fd);
+        }
+      }
+      if constexpr (is_lf) {
+        lf_segment_rows<M>(tcp, a, blockIdx.x, gridDim.x, nseg, tab, s_math);
+        __syncthreads();
+        lf_segment_pairs<M>(a, nseg, tab, s_phi, xe, fe);
+      }
+    }
+    // block partial: f[0] d_i <= -2^94 (reject), f[1] NaN (error), f[2] d_i >= 2^94
+    {
+      unsigned int f[4] = {neg_big, fd.nan + fe.nan + fe.big, pos_big, 0u};
+      warp_reduce(xd, xe, f);
+      if (lane == 0) {
+        s_red.d[wid] = xd;
+        s_red.e[wid] = xe;
+        for (int q = 0; q < 4; ++q) s_red.f[wid][q] = f[q];
+      }
+      __syncthreads();
+      if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        Xacc bd, be;
+        unsigned int bf[4] = {0u, 0u, 0u, 0u};
+        xacc_zero(bd);
+        xacc_zero(be);
+        if (lane < nw) {
+          bd = s_red.d[lane];
+          be = s_red.e[lane];
+          for (int q = 0; q < 4; ++q) bf[q] = s_red.f[lane][q];
+        }
+        warp_reduce(bd, be, bf);
+        if (lane == 0) {
+          unsigned long long* dst = a.partials + ((s & 1) * gridDim.x + blockIdx.x) * kPartWords;
+          __stcg(dst + 0, bd.w0);
+          __stcg(dst + 1, bd.w1);
+          __stcg(dst + 2, bd.w2);
+          __stcg(dst + 3, be.w0);
+          __stcg(dst + 4, be.w1);
+          __stcg(dst + 5, be.w2);
+          __stcg(dst + 6, (static_cast<unsigned long long>(bf[1]) << 32) | bf[0]);
+          __stcg(dst + 7, (static_cast<unsigned long long>(bf[3]) << 32) | bf[2]);
+        }
+      }
+    }
+    if (!grid_barrier(a.bar, static_cast<unsigned int>(s), a.err, a.timeout_ns, skip_me)) return;
+    {
+      Xacc D, E;
+      unsigned int f[4];
+      sum_partials(a.partials + (s & 1) * gridDim.x * kPartWords, static_cast<int>(gridDim.x), s_red, D, E, f);
+      if (tid == 0) {
+        const long long sg = a.trace_off + s;
+        if (f[1] != 0u) {
+          atomicCAS(a.err, 0, CUDAHM_ENUMERIC);
+          s_stop = 1;
+        } else {
+          double logalpha, Drec, eb_new = 0.0, logeb_new = 0.0;
+          if (!prior_ok) {
+            logalpha = -INFINITY;
+            Drec = 0.0;
+          } else if (f[0] != 0u) {
+            logalpha = -INFINITY;
+            Drec = -INFINITY;
+          } else if (f[2] != 0u) {
+            logalpha = INFINITY;
+            Drec = INFINITY;
+          } else {
+            Drec = xacc_to_double(D);
+            const double nn = static_cast<double>(a.n);
+            logalpha = Drec + nn * (M::cterm(s_thp) - M::cterm(s_theta)) + s_lpri_new - s_lpri;
+            if (is_lf) {
+              eb_new = xacc_to_double(E);
+              logeb_new = log_etabar(eb_new, s_math);
+              logalpha -= nn * (logeb_new - s_logeb);
+            }
+          }
+          const bool acc = __ldg(a.tab_lnu + s) < logalpha;
+          if (blockIdx.x == 0 && sg < a.trace_T) {
+            for (int q = 0; q < p; ++q) a.tr_thprop[sg * p + q] = s_thp[q];
+            a.tr_D[sg] = Drec;
+            a.tr_logalpha[sg] = logalpha;
+            a.tr_ut[sg] = __ldg(a.tab_u + s);
+            a.tr_tacc[sg] = acc ? 1 : 0;
+            a.tr_eb[sg] = eb_new;
+          }
+          if (acc) {
+            for (int q = 0; q < p; ++q) s_theta[q] = s_thp[q];
+            s_tc = s_tcp;
+            s_lpri = s_lpri_new;
+            s_cur = 1 - s_cur;
+            if (is_lf) {
+              s_etabar = eb_new;
+              s_logeb = logeb_new;
+            }
+            s_tacc++;
+          }
+          if (a.adapt_theta) {
+            const double alpha = (logalpha >= 0.0) ? 1.0 : exp_tab(logalpha, s_math);
+            ram_update_theta(p, s_Sth, a.tab_U + s * p, alpha, a.astar_theta, __ldg(a.tab_eta + s));
+          }
+          const long long post = s - a.burn_left;
+          if (post >= 0 && a.thin > 0 && ((a.keep_phase + post + 1) % a.thin) == 0) {
+            if (blockIdx.x == 0)
+              for (int q = 0; q < p; ++q) a.rows[s_rows_written * p + q] = s_theta[q];
+            s_rows_written++;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (s_stop) return;
+  }
+  if (tid == 0 && blockIdx.x == 0) {
+    for (int q = 0; q < p; ++q) a.chain->theta[q] = s_theta[q];
+    for (int q = 0; q < p * p; ++q) a.chain->S_theta[q] = s_Sth[q];
+    a.chain->etabar = s_etabar;
+    a.chain->sweeps = a.k0 + a.ns;
+    a.chain->theta_acc += s_tacc;
+    a.chain->rows = s_rows_written;
+    a.chain->mcur = s_cur;
+  }
+}
+
+// log p_i(theta) of every member at theta (device, p doubles), into out[n].
+template <class M>
+__global__ void marg_eval_kernel(long long n, const double* y, const double* aux, const double* theta,
+                                 ModelConsts mc, const double* T, const double* nodes, double* out) {
+  __shared__ double s_math[kMathWords];
+  __shared__ double s_nodes[kMargNodeWords];
+  __shared__ ThetaC s_tc;
+  for (int q = threadIdx.x; q < kMathWords; q += blockDim.x) s_math[q] = T[q];
+  for (int q = threadIdx.x; q < kMargNodeWords; q += blockDim.x) s_nodes[q] = nodes[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double th[kMaxP];
+    for (int q = 0; q < 3; ++q) th[q] = (q < 2 || M::kRule) ? theta[q] : 0.0;
+    s_tc = M::consts(th, mc, s_math);
+  }
+  __syncthreads();
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = marg_logp<M>(y[i], aux[i], s_tc, mc, s_math, s_nodes);
+}
+
+template <class M>
+size_t marg_smem(int rows_smem) {
+  return sizeof(double) * (kMathWords + kMargNodeWords + (M::kRule ? kPhiWords : 0)) +
+         (M::kRule ? segtab_bytes(rows_smem) : 0);
+}
+
+}  // namespace
+
+size_t marg_smem_bytes(int model, int rows_smem) {
+  return model == CUDAHM_LF ? marg_smem<LF>(rows_smem) : marg_smem<NN1>(rows_smem);
+}
+
+cudaError_t marg_occupancy(int model, int block, int smem_bytes, int* blocks_per_sm) {
+  const void* fn = (model == CUDAHM_LF) ? reinterpret_cast<const void*>(&marg_kernel<LF>)
+                                        : reinterpret_cast<const void*>(&marg_kernel<NN1>);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem_bytes);
+}
+
+cudaError_t launch_marg(const SweepArgs& a, int grid, int block, cudaStream_t st) {
+  const size_t smem = marg_smem_bytes(a.model, a.rows_smem);
+  void* args[] = {const_cast<SweepArgs*>(&a)};
+  const void* fn = (a.model == CUDAHM_LF) ? reinterpret_cast<const void*>(&marg_kernel<LF>)
+                                          : reinterpret_cast<const void*>(&marg_kernel<NN1>);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
+}
+
+cudaError_t launch_marg_eval(int model, long long n, const double* y, const double* aux, const double* theta_dev,
+                             const ModelConsts& mc, const double* math_tab, const double* nodes, double* out,
+                             cudaStream_t st) {
+  const int blk = 256;
+  const unsigned int grid = static_cast<unsigned int>((n + blk - 1) / blk);
+  if (model == CUDAHM_LF) marg_eval_kernel<LF><<<grid, blk, 0, st>>>(n, y, aux, theta_dev, mc, math_tab, nodes, out);
+  else if (model == CUDAHM_NN1)
+    marg_eval_kernel<NN1><<<grid, blk, 0, st>>>(n, y, aux, theta_dev, mc, math_tab, nodes, out);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// Nodes and weights of the two panels on [-1, 1]: xp[64], wp[64], xt[32], wt[32].
+cudaError_t launch_marg_nodes(double* nodes, cudaStream_t st) {
+  cudaError_t e = launch_gauss_legendre(kMargPeak, nodes, nodes + kMargPeak, st);
+  if (e != cudaSuccess) return e;
+  return launch_gauss_legendre(kMargTail, nodes + 2 * kMargPeak, nodes + 2 * kMargPeak + kMargTail, st);
+}
+
+}  // namespace chm

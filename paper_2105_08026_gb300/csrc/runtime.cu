@@ -128,6 +128,11 @@ struct cudahm {
   double* pub = nullptr;  // theta' published by block 0 of the sweep kernel
   unsigned long long* eb_partials = nullptr;
   int eb_grid = 0, eb_rows_smem = 1;
+  // marginal form (latents integrated out by cubature)
+  double* marg_lp = nullptr;     // [2][n] log p_i at the current theta and at the proposal
+  double* marg_nodes = nullptr;  // panel nodes and weights
+  int mgrid = 0, mrows_smem = 1;
+  bool marg_valid = false;       // marg_lp[mcur] holds log p_i at the chain's theta
   // host mirrors
   bool data_set = false;
   bool etabar_valid = false;
@@ -244,6 +249,12 @@ int validate(const cudahm_config* c) {
     double li[6];
     if (!chol3_inverse(k, li)) return fail(CUDAHM_EINVAL, "NN3 needs a positive definite C_pop in consts[0..5]");
   }
+  if (c->marginal != 0 && c->marginal != 1) return fail(CUDAHM_EINVAL, "marginal must be 0 or 1");
+  if (c->marginal) {
+    if (c->model != CUDAHM_NN1 && c->model != CUDAHM_LF)
+      return fail(CUDAHM_EUNSUPPORTED, "the marginal form integrates one-dimensional latents (NN1, LF)");
+    if (c->precision != CUDAHM_FP64) return fail(CUDAHM_EUNSUPPORTED, "the marginal form is FP64 only");
+  }
   return CUDAHM_OK;
 }
 
@@ -297,6 +308,30 @@ int choose_shape(cudahm* h) {
   return CUDAHM_OK;
 }
 
+// Launch shape of the marginal kernel: a cooperative grid of whole SMs (LF: the selection rule
+// spreads over every block), at most one block per 256 members for NN1.
+int choose_marg_shape(cudahm* h) {
+  const int model = h->cfg.model;
+  const bool lf = has_rule(model);
+  const long long G = lf ? static_cast<long long>(rule_nL(h->cfg)) * ((static_cast<long long>(rule_nr(h->cfg)) + 127) / 128)
+                         : 0;
+  for (int bps = 2; bps >= 1 && h->mgrid == 0; --bps) {
+    const int grid = lf ? bps * h->sms
+                        : static_cast<int>(std::min<long long>(static_cast<long long>(bps) * h->sms, (h->n + 255) / 256));
+    const int rows = lf ? static_cast<int>((G + grid - 1) / grid) : 1;
+    const size_t smem = marg_smem_bytes(model, rows);
+    if (smem > 200 * 1024) continue;
+    int fit = 0;
+    CU(marg_occupancy(model, 256, static_cast<int>(smem), &fit));
+    if (fit * h->sms >= grid) {
+      h->mgrid = grid;
+      h->mrows_smem = rows;
+    }
+  }
+  if (h->mgrid == 0) return fail(CUDAHM_EUNSUPPORTED, "no launch shape fits the marginal kernel");
+  return CUDAHM_OK;
+}
+
 SweepArgs base_args(cudahm* h) {
   SweepArgs a{};
   a.model = h->cfg.model;
@@ -337,6 +372,8 @@ SweepArgs base_args(cudahm* h) {
   a.tab_u = h->tab_u;
   a.tab_lnu = h->tab_lnu;
   a.tab_eta = h->tab_eta;
+  a.marg_lp = h->marg_lp;
+  a.marg_nodes = h->marg_nodes;
   return a;
 }
 
@@ -384,6 +421,7 @@ int reset_chain(cudahm* h) {
   h->sweeps = 0;
   h->rows_last = 0;
   h->etabar_valid = false;
+  h->marg_valid = false;
   return CUDAHM_OK;
 }
 
@@ -403,7 +441,7 @@ int ensure_trace(cudahm* h, long long T) {
     *q = nullptr;
   }
   h->trace_cap_T = 0;
-  const size_t tn = static_cast<size_t>(T) * h->n;
+  const size_t tn = static_cast<size_t>(T) * (h->cfg.marginal ? 1 : h->n);  // no member trace when marginal
   TRY(alloc_into(h, &h->tr_delta, tn));
   TRY(alloc_into(h, &h->tr_u, tn));
   TRY(alloc_into(h, &h->tr_acc, tn));
@@ -432,7 +470,8 @@ int prepare(cudahm* h, const double* y_dev_raw, const double* aux_dev_raw, int s
   CU(cudaMemcpyAsync(h->host_err, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
   bad = *h->host_err;
-  if (bad) return fail(CUDAHM_EINVAL, "%d members have non-finite data or a non-positive scale", bad);
+  if (bad)
+    return fail(CUDAHM_EINVAL, "%d members have non-finite data or a non-positive scale (or, marginal LF, flux)", bad);
   if (h->cfg.precision == CUDAHM_FP32) {  // binary32 member data for the batched FP32 form
     if (!h->d32) TRY(alloc_into(h, &h->d32, static_cast<size_t>(data32_words(h->cfg.model)) * h->n));
     CU(launch_data32(h->cfg.model, h->n, h->y, h->aux, h->mc, h->d32, h->stream));
@@ -525,6 +564,7 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
     h->mc.lo = k[0];
     h->mc.hi = k[1];
   } else if (cfg->model == CUDAHM_LF) {
+    h->mc.sigF = k[0];
     h->mc.inv2sig2 = 1.0 / (2.0 * k[0] * k[0]);
     h->mc.cth = k[1] / k[0];
     h->mc.F_th = k[1];
@@ -545,8 +585,10 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
   } else if (cfg->model == CUDAHM_NN3) {
     chol3_inverse(k, h->mc.li3);
   }
+  h->mc.marginal = cfg->marginal;
   int rc = choose_shape(h);
   if (rc != CUDAHM_OK) return bail(rc);
+  if (cfg->marginal && (rc = choose_marg_shape(h)) != CUDAHM_OK) return bail(rc);
 
   const long long n = h->n;
   const int p = h->p;
@@ -554,7 +596,8 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
   if ((rc = alloc_into(h, &h->y, n * h->d)) || (rc = alloc_into(h, &h->aux, n * h->d)) ||
       (rc = alloc_into(h, &h->chi, n * h->d)) || (rc = alloc_into(h, &h->S, h->factor_n)) ||
       (rc = alloc_into(h, &h->chain, 1)) ||
-      (rc = alloc_into(h, &h->partials, 2ull * h->grid * kPartWords)) || (rc = alloc_into(h, &h->bar, 4)) ||
+      (rc = alloc_into(h, &h->partials, 2ull * std::max(h->grid, h->mgrid) * kPartWords)) ||
+      (rc = alloc_into(h, &h->bar, 4)) ||
       (rc = alloc_into(h, &h->err, 4)) || (rc = alloc_into(h, &h->bad, 4)) ||
       (rc = alloc_into(h, &h->theta_dev, kMaxP)) || (rc = alloc_into(h, &h->eval_out, 4)) ||
       (rc = alloc_into(h, &h->tab_U, kChunk * p)) || (rc = alloc_into(h, &h->tab_u, kChunk)) ||
@@ -583,6 +626,12 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
   }
   if (launch_math_table(h->math_tab, h->stream) != cudaSuccess)
     return bail(fail(CUDAHM_ECUDA, "exp/log table set-up failed: %s", cudaGetErrorString(cudaGetLastError())));
+  if (cfg->model == CUDAHM_NN1 || cfg->model == CUDAHM_LF) {  // the cubature rule (marginal form, eval_marginal)
+    if ((rc = alloc_into(h, &h->marg_nodes, kMargNodeWords))) return bail(rc);
+    if (cfg->marginal && (rc = alloc_into(h, &h->marg_lp, 2ull * n))) return bail(rc);
+    if (launch_marg_nodes(h->marg_nodes, h->stream) != cudaSuccess)
+      return bail(fail(CUDAHM_ECUDA, "cubature set-up failed: %s", cudaGetErrorString(cudaGetLastError())));
+  }
   if (cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess)
     return bail(fail(CUDAHM_ECUDA, "initialisation failed"));
@@ -618,6 +667,7 @@ int cudahm_set_data_device(cudahm_t h, const double* y_dev, const double* aux_de
 
 int cudahm_set_chi(cudahm_t h, const double* chi_host, int64_t n) {
   if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
+  if (h->cfg.marginal) return fail(CUDAHM_EUNSUPPORTED, "the marginal form has no latents");
   if (!h->data_set) return fail(CUDAHM_ESTATE, "set_chi before set_data");
   if (h->sweeps != 0) return fail(CUDAHM_ESTATE, "set_chi after the chain has started");
   if (!chi_host || n != h->n) return fail(CUDAHM_EINVAL, "bad chi argument");
@@ -650,7 +700,7 @@ int cudahm_set_chi(cudahm_t h, const double* chi_host, int64_t n) {
 int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
   if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
   if (!h->data_set) return fail(CUDAHM_ESTATE, "run before set_data");
-  if (h->K == 0) {  // streaming form: a batch of one population
+  if (h->K == 0 && !h->cfg.marginal) {  // streaming form: a batch of one population
     cudahm_t one[1] = {h};
     CU(cudaEventRecord(h->ev0, h->stream));
     const int rc = cudahm_batch_run(one, 1, n_burn, n_iter, thin, nullptr, nullptr);
@@ -679,7 +729,16 @@ int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
                             reinterpret_cast<double*>(base + offsetof(ChainState, etabar))));
     h->etabar_valid = true;
   }
+  if (h->cfg.marginal && !h->marg_valid) {
+    // log p_i at the current theta into array 0, once per chain
+    char* base = reinterpret_cast<char*>(h->chain);
+    CU(launch_marg_eval(h->cfg.model, h->n, h->y, h->aux, reinterpret_cast<const double*>(base + offsetof(ChainState, theta)),
+                        h->mc, h->math_tab, h->marg_nodes, h->marg_lp, h->stream));
+    CU(cudaMemsetAsync(base + offsetof(ChainState, mcur), 0, sizeof(int), h->stream));
+    h->marg_valid = true;
+  }
   SweepArgs a = base_args(h);
+  if (h->cfg.marginal) a.rows_smem = h->mrows_smem;
   a.thin = thin;
   a.keep_phase = 0;
   a.trace_T = T;
@@ -707,7 +766,8 @@ int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
     a.burn_left = n_burn - off;
     a.trace_off = off;
     a.rows = h->rows ? h->rows + rows_done * h->p : nullptr;
-    CU(launch_sweep(a, h->K, h->grid, h->block, h->stream));
+    if (h->cfg.marginal) CU(launch_marg(a, h->mgrid, 256, h->stream));
+    else CU(launch_sweep(a, h->K, h->grid, h->block, h->stream));
     // rows kept in [off, off + ns): post-burn indices q with (q + 1) % thin == 0
     if (n_iter > 0) {
       const long long q0 = std::max<long long>(0, off - n_burn), q1 = off + ns - n_burn;
@@ -752,6 +812,7 @@ int cudahm_get_samples(cudahm_t h, double* theta_host, int64_t cap_rows, int64_t
 
 int cudahm_get_chi(cudahm_t h, double* chi_host, double* S_host) {
   if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
+  if (h->cfg.marginal) return fail(CUDAHM_EUNSUPPORTED, "the marginal form has no latents");
   CU(cudaSetDevice(h->cfg.device));
   if (h->d == 3) {  // per-component device arrays to member-major host arrays
     const size_t n = static_cast<size_t>(h->n);
@@ -807,9 +868,30 @@ int cudahm_get_stats(cudahm_t h, cudahm_stats* s) {
   s->rows = h->rows_last;
   s->last_run_ms = h->last_run_ms;
   s->etabar = cs.etabar;
-  s->grid_blocks = h->grid;
-  s->block_threads = h->block;
-  s->objects_per_thread = h->K;
+  s->grid_blocks = h->cfg.marginal ? h->mgrid : h->grid;
+  s->block_threads = h->cfg.marginal ? 256 : h->block;
+  s->objects_per_thread = h->cfg.marginal ? 0 : h->K;
+  return CUDAHM_OK;
+}
+
+int cudahm_eval_marginal(cudahm_t h, const double* theta_host, double* lp_host) {
+  if (!h || !theta_host || !lp_host) return fail(CUDAHM_EINVAL, "NULL argument");
+  if (h->cfg.model != CUDAHM_NN1 && h->cfg.model != CUDAHM_LF)
+    return fail(CUDAHM_EUNSUPPORTED, "the cubature rule integrates one-dimensional latents (NN1, LF)");
+  if (!h->data_set) return fail(CUDAHM_ESTATE, "eval before set_data");
+  CU(cudaSetDevice(h->cfg.device));
+  double* out = nullptr;
+  TRY(alloc_into(h, &out, h->n));
+  CU(cudaMemcpyAsync(h->theta_dev, theta_host, sizeof(double) * h->p, cudaMemcpyHostToDevice, h->stream));
+  const cudaError_t e = launch_marg_eval(h->cfg.model, h->n, h->y, h->aux, h->theta_dev, h->mc, h->math_tab,
+                                         h->marg_nodes, out, h->stream);
+  if (e != cudaSuccess) {
+    h->dfree(out);
+    return fail(CUDAHM_ECUDA, "marginal evaluation failed: %s", cudaGetErrorString(e));
+  }
+  CU(cudaMemcpyAsync(lp_host, out, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->dfree(out);
   return CUDAHM_OK;
 }
 
@@ -875,9 +957,11 @@ int cudahm_get_trace(cudahm_t h, double* delta, double* u, uint8_t* acc, double*
     if (!dst) return cudaSuccess;
     return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream);
   };
-  CU(cp(delta, h->tr_delta, sizeof(double) * tn));
-  CU(cp(u, h->tr_u, sizeof(double) * tn));
-  CU(cp(acc, h->tr_acc, tn));
+  if (!h->cfg.marginal) {  // the marginal form has no member steps to record
+    CU(cp(delta, h->tr_delta, sizeof(double) * tn));
+    CU(cp(u, h->tr_u, sizeof(double) * tn));
+    CU(cp(acc, h->tr_acc, tn));
+  }
   CU(cp(theta_prop, h->tr_thprop, sizeof(double) * T * h->p));
   CU(cp(D, h->tr_D, sizeof(double) * T));
   CU(cp(logalpha, h->tr_logalpha, sizeof(double) * T));
@@ -937,6 +1021,7 @@ int cudahm_restore(cudahm_t h, const void* buf, size_t size) {
   h->sweeps = cs.sweeps;
   h->rows_last = 0;
   h->etabar_valid = (cs.etabar != 0.0);
+  h->marg_valid = false;  // log p_i is recomputed at the restored theta before the next run
   return CUDAHM_OK;
 }
 
@@ -985,6 +1070,7 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
     cudahm* h = hs[q];
     if (!h) return fail(CUDAHM_EINVAL, "handle %d is NULL", q);
     if (!h->data_set) return fail(CUDAHM_ESTATE, "handle %d has no data", q);
+    if (h->cfg.marginal) return fail(CUDAHM_EUNSUPPORTED, "handle %d uses the marginal form, which runs alone", q);
     if (h->cfg.device != h0->cfg.device) return fail(CUDAHM_EINVAL, "handles are on different devices");
     if (h->cfg.precision != h0->cfg.precision) return fail(CUDAHM_EINVAL, "handles mix precisions");
     if (h->cfg.trace_sweeps > 0 && k > 1)
@@ -1551,6 +1637,7 @@ int cudahm_server_submit(cudahm_server_t sv, const cudahm_config* cfg, const dou
   if (cfg->precision != sv->precision) return fail(CUDAHM_EINVAL, "request precision differs from the server's");
   if (cfg->device != sv->device) return fail(CUDAHM_EINVAL, "request device differs from the server's");
   if (cfg->trace_sweeps > 0) return fail(CUDAHM_EUNSUPPORTED, "served requests do not record traces");
+  if (cfg->marginal) return fail(CUDAHM_EUNSUPPORTED, "served requests use the member form");
   if (n_burn < 0 || n_iter < 0 || n_burn + n_iter < 1 || (n_iter > 0 && thin < 1))
     return fail(CUDAHM_EINVAL, "bad sweep counts");
   auto* r = new Request();

@@ -641,6 +641,7 @@ __global__ void prepare_kernel(int model, long long n, const double* y_raw, cons
     y[i] = yr;
     aux[i] = 1.0 / (4.0 * 3.14159265358979323846 * ar * ar);
     ok = ok && aux[i] > 0.0 && isfinite(aux[i]);
+    if (mc.marginal) ok = ok && yr > 0.0;  // the cubature window sits at Fhat_i > 0
     if (set_default_chi) {
       double c = log(4.0 * 3.14159265358979323846 * ar * ar * fmax(yr, mc.F_th));
       if (model == CUDAHM_LF) {  // raised into the support chi > ln L_low

@@ -56,7 +56,7 @@ class CudahmConfig(ctypes.Structure):
         ("alloc_ctx", ctypes.c_void_p),
         ("barrier_timeout_ns", ctypes.c_int64),
         ("debug_skip_barrier_cta", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("marginal", ctypes.c_int32),
     ]
 
 
@@ -101,7 +101,7 @@ EXPORTED = [
     "cudahm_sizeof_config", "cudahm_sizeof_stats", "cudahm_last_error", "cudahm_destroy",
     "cudahm_lf_etabar_noalloc", "cudahm_batch_run", "cudahm_server_create", "cudahm_server_submit",
     "cudahm_server_poll", "cudahm_server_wait", "cudahm_server_result", "cudahm_server_stats",
-    "cudahm_server_destroy", "cudahm_ess",
+    "cudahm_server_destroy", "cudahm_ess", "cudahm_eval_marginal",
 ]
 
 
@@ -148,6 +148,7 @@ def lib():
     L.cudahm_destroy.argtypes = [vp]
     L.cudahm_destroy.restype = None
     L.cudahm_ess.argtypes = [_dp, i64, i32, _dp]
+    L.cudahm_eval_marginal.argtypes = [vp, _dp, _dp]
     for name in EXPORTED:
         if name not in ("cudahm_config_init", "cudahm_sizeof_config", "cudahm_sizeof_stats", "cudahm_last_error",
                         "cudahm_destroy"):
@@ -237,6 +238,13 @@ def cudahm_eval_logdens(h, theta, n: int) -> np.ndarray:
     th = _f64(theta)
     out = np.zeros(n)
     _check(lib().cudahm_eval_logdens(h, _dptr(th), _dptr(out)))
+    return out
+
+
+def cudahm_eval_marginal(h, theta, n: int) -> np.ndarray:
+    th = _f64(theta)
+    out = np.zeros(n)
+    _check(lib().cudahm_eval_marginal(h, _dptr(th), _dptr(out)))
     return out
 
 
@@ -422,7 +430,8 @@ class Sampler:
                  precision: int = FP64, adapt_theta: bool = True, chi_init_scale: float = 1.0,
                  target_accept: float = 0.4, theta_target_accept: float = 0.4, adapt_exponent: float = 2.0 / 3.0,
                  trace_sweeps: int = 0, device: int = 0, block_threads: int = 0, stream=None,
-                 use_torch_allocator: bool = False, barrier_timeout_ns: int = 0, debug_skip_barrier_cta: int = -1):
+                 use_torch_allocator: bool = False, barrier_timeout_ns: int = 0, debug_skip_barrier_cta: int = -1,
+                 marginal: bool = False):
         self.model, self.n = model, int(n)
         self.d, self.p = MODEL_D[model], MODEL_P[model]
         cfg = cudahm_config_init(model, n)
@@ -438,6 +447,7 @@ class Sampler:
         cfg.block_threads = block_threads
         cfg.barrier_timeout_ns = barrier_timeout_ns
         cfg.debug_skip_barrier_cta = debug_skip_barrier_cta
+        cfg.marginal = 1 if marginal else 0
         for q, v in enumerate(_f64(theta_init)):
             cfg.theta_init[q] = v
         if theta_prop_scale is not None:
@@ -487,6 +497,10 @@ class Sampler:
 
     def stats(self) -> CudahmStats:
         return cudahm_get_stats(self.h)
+
+    def marginal_logp(self, theta=None) -> np.ndarray:
+        th = self.theta()[0] if theta is None else theta
+        return cudahm_eval_marginal(self.h, th, self.n)
 
     def logdens(self, theta=None) -> np.ndarray:
         th = self.theta()[0] if theta is None else theta

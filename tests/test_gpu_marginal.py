@@ -1,0 +1,174 @@
+"""GPU parity of the marginal form (latents integrated out by cubature, theta-only chain;
+Sec. 6) against the oracle.
+
+- Per-member log p_i(theta) of the device rule against the oracle's rule: within
+  |a - b| <= 1e-12 max(1, |a|, |b|) for NN1 members, plus 5e-15 Fhat_i/sigma_F for LF members,
+  at several theta, on ragged sizes and on the full LF workload (N = 3e5); the same -inf where a
+  proposal's L_low leaves no likelihood mass on the support. The LF term is the arithmetic's
+  condition: near the likelihood peak d log l/d ln e^chi = (Fhat - F) F/sigma_F^2 ~ 3 Fhat/sigma_F,
+  so the device's table exp (within 2.5 ulp, the host's within 0.5) moves each node's log
+  integrand by up to ~3 x 6.7e-16 Fhat_i/sigma_F, which reaches 3e-11 for the brightest members
+  (Fhat/sigma_F ~ 1.4e4). Where a proposal's L_low cuts the likelihood window t_i =
+  (L_low q_i - Fhat_i)/sigma_F > 0 standard deviations above its peak, the integrand falls
+  steeply from the cut (slope ~ t_i Fhat_i/sigma_F in chi) and the two sides' node positions,
+  which differ by a few ulp (table versus library log for the window ends, device versus host
+  Gauss-Legendre nodes), move the sum by that slope times the shift: the bound takes the
+  factor 1 + t_i. A cut just below the window's top leaves a panel of width
+  delta_i = ln(F_b/q_i) - ln L_low so narrow that the window end's rounding (a few ulp of
+  |ln(F_b/q_i)|) changes log p_i by ~ that error / delta_i: the bound adds
+  1e-15 |ln(F_b/q_i)|/delta_i (such members sit ~10 sigma_F below the cut, log p_i ~ -60).
+- Lockstep theta chain: identical accept decisions except near ties |log alpha - ln u| < 1e-9,
+  proposals within 1e-12 relative, D = sum_i [log p_i(theta') - log p_i(theta)] within
+  1e-10 max(1, N/1e4) absolute, the selection integral within 1e-12 relative; NN1 N = 1000,
+  LF with a small rule, and the full LF workload (N = 3e5, 1024 x 1024 rule) for a few steps.
+- run(a) + run(b) equals run(a + b), and a checkpoint restores the chain bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_08026_gb300 import cudahm, synth
+
+pytestmark = pytest.mark.gpu
+
+NEAR_TIE = 1e-9
+
+
+def _close(a, b, rel=1e-12, extra=0.0):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    same_inf = (a == b) & ~np.isfinite(a)
+    fin = np.isfinite(a) & np.isfinite(b)
+    bound = rel * np.maximum(1.0, np.maximum(np.abs(a), np.abs(b))) + extra
+    err = np.zeros(a.shape)
+    err[fin] = np.abs(a[fin] - b[fin])
+    ok = same_inf | (fin & (err <= bound))
+    return bool(ok.all()), (err[fin] / np.broadcast_to(bound, a.shape)[fin]).max() if fin.any() else 0.0
+
+
+def _sampler(model, y, aux, consts, th, sc, seed, **kw):
+    s = cudahm.Sampler(model, np.asarray(y).size, theta_init=th, theta_prop_scale=sc, model_consts=consts,
+                       seed=seed, marginal=True, **kw)
+    s.set_data(y, aux)
+    return s
+
+
+@pytest.mark.parametrize("n", [1, 257, 1000])
+def test_nn1_member_integrals(n):
+    d = synth.nn1_data(n, seed=40 + n)
+    th0, sc, c = synth.nn1_settings(d)
+    s = _sampler(cudahm.NN1, d.y, d.sigma, c, th0, sc, 3)
+    g = np.random.default_rng(n)
+    for _ in range(4):
+        th = th0 + g.normal(0.0, 0.3, 2)
+        ok, worst = _close(s.marginal_logp(th), oracle.marg_logp(oracle.NN1, d.y, d.sigma, c, th))
+        assert ok, worst
+
+
+def test_lf_member_integrals_full_size():
+    data = synth.lf_data(300_000, seed=1002)
+    th0, sc, c = synth.lf_settings(data)
+    s = _sampler(cudahm.LF, data.fhat, data.r, c, th0, sc, 2)
+    for dth in ((0.0, 0.0, 0.0), (0.05, 0.3, 0.5), (-0.1, -0.3, -1.0), (0.0, 0.0, 4.0)):
+        th = th0 + np.array(dth)
+        a = s.marginal_logp(th)
+        b = oracle.marg_logp(oracle.LF, data.fhat, data.r, c, th)
+        q = 1.0 / (4.0 * math.pi * data.r**2)
+        t = np.maximum(0.0, (math.exp(th[2]) * q - data.fhat) / data.sigma_F)
+        chib = np.log((data.fhat + 10.0 * data.sigma_F) / q)
+        chic = np.log(np.maximum(data.fhat - 10.0 * data.sigma_F, 0.5 * data.fhat) / q)
+        width = np.maximum(chib - np.maximum(chic, th[2]), 1e-300)
+        extra = 5e-15 * (data.fhat / data.sigma_F) * (1.0 + t) + 1e-15 * np.abs(chib) / width
+        ok, worst = _close(a, b, extra=extra)
+        assert ok, (dth, worst)
+        if dth[2] == 4.0:
+            assert np.isneginf(a).any()
+
+
+def _lockstep(model, y, aux, consts, th, sc, seed, steps):
+    s = _sampler(model, y, aux, consts, th, sc, seed, trace_sweeps=steps)
+    rows = s.run(0, steps)
+    tr = s.trace(steps)
+    ch = oracle.MarginalChain(model, y, aux, consts, th, sc, seed)
+    orows, otr = ch.run(0, steps, trace_sweeps=steps)
+    return s, ch, rows, orows, tr, otr
+
+
+def _check(s, ch, rows, orows, tr, otr):
+    n = s.n
+    diff = tr["tacc"] != otr["tacc"]
+    K = int(np.argwhere(diff)[0][0]) if diff.any() else len(tr["tacc"])
+    if K < len(tr["tacc"]):
+        gap = abs(otr["logalpha"][K] - math.log(otr["utheta"][K]))
+        assert gap < NEAR_TIE, f"theta decision differs at step {K}: |log alpha - ln u| = {gap}"
+    assert np.array_equal(tr["utheta"][:K + 1], otr["utheta"][:K + 1])
+    ok, worst = _close(tr["theta_prop"][:K + 1], otr["theta_prop"][:K + 1])
+    assert ok, worst
+    atol = 1e-10 * max(1.0, n / 1e4)
+    for key in ("D", "logalpha"):
+        a, b = tr[key][:K + 1], otr[key][:K + 1]
+        fin = np.isfinite(a) & np.isfinite(b)
+        assert np.array_equal(np.isfinite(a), np.isfinite(b)), key
+        assert np.all(np.abs(a[fin] - b[fin]) <= atol), (key, np.abs(a[fin] - b[fin]).max())
+    ok, worst = _close(tr["etabar"][:K + 1], otr["etabar"][:K + 1])
+    assert ok, worst
+    if K == len(tr["tacc"]):
+        ok, worst = _close(rows, orows)
+        assert ok, worst
+        th, Sth = s.theta()
+        ok, worst = _close(th, ch.theta)
+        assert ok, worst
+        ok, worst = _close(Sth.reshape(-1), ch.S_theta)
+        assert ok, worst
+    return K
+
+
+def test_nn1_lockstep():
+    d = synth.nn1_data(1000, seed=1001)
+    th0, sc, c = synth.nn1_settings(d)
+    _check(*_lockstep(cudahm.NN1, d.y, d.sigma, c, th0, sc, 1, 1000))
+
+
+def test_lf_lockstep_small_rule():
+    data = synth.lf_data(2000, seed=77)
+    th0, sc, c = synth.lf_settings(data, nL=64, nr=128)
+    _check(*_lockstep(cudahm.LF, data.fhat, data.r, c, th0, sc, 5, 400))
+
+
+def test_lf_lockstep_full_size():
+    data = synth.lf_data(300_000, seed=1002)
+    th0, sc, c = synth.lf_settings(data)
+    _check(*_lockstep(cudahm.LF, data.fhat, data.r, c, th0, sc, 2, 4))
+
+
+def test_run_split_and_checkpoint():
+    data = synth.lf_data(3000, seed=18)
+    th0, sc, c = synth.lf_settings(data, nL=64, nr=64)
+    mk = lambda: _sampler(cudahm.LF, data.fhat, data.r, c, th0, sc, 9)
+    a, b, e = mk(), mk(), mk()
+    ra = a.run(0, 300)
+    rb = np.concatenate([b.run(0, 120), b.run(0, 180)])
+    assert np.array_equal(ra, rb)
+    e.run(0, 120)
+    blob = e.checkpoint()
+    f = mk()
+    f.restore(blob)
+    assert np.array_equal(f.run(0, 180), ra[120:])
+
+
+def test_marginal_handle_rejections():
+    d = synth.nn1_data(100, seed=5)
+    th0, sc, c = synth.nn1_settings(d)
+    s = _sampler(cudahm.NN1, d.y, d.sigma, c, th0, sc, 3)
+    for call in (lambda: s.chi(), lambda: cudahm.batch_run([s], 0, 10)):
+        with pytest.raises(cudahm.CudahmError) as ei:
+            call()
+        assert ei.value.code == cudahm.EUNSUPPORTED
+    lf = synth.lf_data(50, seed=6)
+    th, sc, c = synth.lf_settings(lf, nL=16, nr=16)
+    fh = lf.fhat.copy()
+    fh[3] = -1.0
+    with pytest.raises(cudahm.CudahmError) as ei:
+        _sampler(cudahm.LF, fh, lf.r, c, th, sc, 1)
+    assert ei.value.code == cudahm.EINVAL
