@@ -345,12 +345,8 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
   const int p = a.p;
   constexpr bool is_lf = M::kRule;  // the model has a selection integral (LF, BB1)
   double* s_math = s_dyn;
-  double* s_phi = s_dyn + kMathWords;
-  const SegTab tab = segtab_carve(s_phi + kPhiWords, R);
   const long long t_start = globaltimer_ns();
   for (int q = tid; q < kMathWords; q += blockDim.x) s_math[q] = a.math_tab[q];
-  if (is_lf)
-    for (int q = tid; q < kPhiWords; q += blockDim.x) s_phi[q] = a.phi_coef[q];
   __syncthreads();  // tables in place before thread 0 uses them
   if (tid == 0) {
     s_k0 = a.chain->sweeps;
@@ -374,7 +370,6 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
   double* rows = a.rows ? a.rows + prog->rows * p : nullptr;
   const unsigned int nb0 = static_cast<unsigned int>((a.n * lb) / nb);
   const unsigned int nb1 = static_cast<unsigned int>((a.n * (lb + 1)) / nb);
-  const int nseg = is_lf ? lf_block_segments(a, lb, nb) : 0;
   unsigned int member_acc = 0;
 
   for (long long s = 0; s < ns; ++s) {
@@ -418,21 +413,9 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
         member_f64<M>(a, i, k, eta, tc, tcp, prior_ok, s_math, xd, fd, neg_big, pos_big, member_nan, member_acc,
                       tro);
     }
-    // a6: the rule's segments of this block, R at a time through the shared table
-    if constexpr (M::kRule) {
-      if (prior_ok) {
-        const ThetaC tcp = s_tcp;
-        for (int t0 = 0; t0 < nseg; t0 += R) {
-          const int cnt = min(R, nseg - t0);
-          for (int q = tid; q < cnt; q += blockDim.x) lf_segment_row<M>(tcp, a, lb, nb, t0 + q, q, tab, s_math);
-          __syncthreads();
-          if (wid == 0) lf_segment_scan(cnt, tab);
-          __syncthreads();
-          lf_segment_pairs<M>(a, cnt, tab, s_phi, xe, fe);
-          __syncthreads();
-        }
-      }
-    }
+    // a6: this block's share of the selection rule's outer nodes at theta'
+    if constexpr (M::kRule)
+      if (prior_ok) etabar_terms<M>(s_tcp, a, lb, nb, s_math, xe, fe);
     {
       unsigned int f[4] = {neg_big, fd.nan + fe.nan + fe.big + member_nan, pos_big, member_nan};
       warp_reduce(xd, xe, f);
@@ -664,9 +647,7 @@ cudaError_t launch_data32(int model, long long n, const double* y, const double*
   return cudaGetLastError();
 }
 
-size_t batch_smem_bytes(int seg_slots) {
-  return sizeof(double) * (kMathWords + kPhiWords) + segtab_bytes(seg_slots);
-}
+size_t batch_smem_bytes(int) { return sizeof(double) * kMathWords; }
 
 cudaError_t batch_occupancy(bool f32, int block, int smem_bytes, int* blocks_per_sm) {
   const void* fn = f32 ? reinterpret_cast<const void*>(&batch_kernel<true>)

@@ -98,9 +98,20 @@ struct SweepArgs {
                       // its sequence word is bar[1]
   double* marg_lp;           // marginal form: log p_i at two thetas, [2][n]
   const double* marg_nodes;  // marginal form: panel nodes and weights (kMargNodeWords)
+  // the rule's inner sum H(ln L) tabulated (h_ncell cells of kHDeg + 1 Chebyshev coefficients);
+  // nullptr: evaluate the rule pair by pair
+  const double* htab;
+  double h_ua, h_ub;  // table range in ln L; H = h_lo below it, h_hi above it
+  double h_lo, h_hi;
+  int h_ncell;
 };
 
 constexpr int kPubWords = 32;
+
+// Tabulated inner sum of the selection rule: Chebyshev series of degree kHDeg on cells of
+// width kHDelta in u = ln L.
+constexpr int kHDeg = 12;
+constexpr double kHDelta = 0.125;
 
 // Cubature rule of the marginal form: Gauss-Legendre panels of kMargPeak and kMargTail nodes,
 // the likelihood window +- kMargK standard deviations.
@@ -168,5 +179,8 @@ cudaError_t launch_eval_logdens(int model, bool f32, long long n, const double* 
                                 const double* math_tab, double* out, cudaStream_t st);
 cudaError_t launch_eval_etabar(const double* theta_dev, const SweepArgs& rule, unsigned long long* partials,
                                int grid, double* out, cudaStream_t st);
+// Builds the H table of a handle's rule (LF, BB1): ncell cells from u = ua; coef receives
+// ncell (kHDeg + 1) coefficients, then H(ua) and H(ub) (ub = ua + ncell kHDelta).
+cudaError_t launch_htab_build(const SweepArgs& rule, double ua, int ncell, double* coef, cudaStream_t st);
 
 }  // namespace chm

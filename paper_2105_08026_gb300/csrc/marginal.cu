@@ -7,7 +7,7 @@
 // 32-node panel over [ln L_low, ln(F_c/q_i)] when that is not empty). The theta step is the
 // member form's (Sec. 2.2, last paragraph) with D = sum_i [log p_i(theta') - log p_i(theta)]:
 // one persistent cooperative launch per chunk of steps, each block integrating a contiguous
-// range of members (and its share of the selection rule's segments for LF), an exact
+// range of members (and its share of the selection rule's outer nodes for LF), an exact
 // fixed-point sum over blocks, one bounded grid barrier per step, and the identical decision
 // in every block. log p_i at the current theta and at the proposal live in two device arrays
 // whose roles swap on acceptance.
@@ -106,13 +106,8 @@ __global__ void __launch_bounds__(256, 2) marg_kernel(const SweepArgs a) {
   const bool skip_me = (a.skip_cta == static_cast<int>(blockIdx.x));
   double* s_math = s_dyn;
   double* s_nodes = s_math + kMathWords;
-  double* s_phi = s_nodes + kMargNodeWords;
-  const SegTab tab = segtab_carve(s_phi + (is_lf ? kPhiWords : 0), a.rows_smem);
   for (int q = tid; q < kMathWords; q += blockDim.x) s_math[q] = a.math_tab[q];
   for (int q = tid; q < kMargNodeWords; q += blockDim.x) s_nodes[q] = a.marg_nodes[q];
-  if (is_lf)
-    for (int q = tid; q < kPhiWords; q += blockDim.x) s_phi[q] = a.phi_coef[q];
-  const int nseg = is_lf ? lf_block_segments(a, blockIdx.x, gridDim.x) : 0;
   __syncthreads();  // tables in place before thread 0 uses them
 
   if (tid == 0) {
@@ -160,11 +155,7 @@ __global__ void __launch_bounds__(256, 2) marg_kernel(const SweepArgs a) {
           xacc_add_double(xd, dn, fd);
         }
       }
-      if constexpr (is_lf) {
-        lf_segment_rows<M>(tcp, a, blockIdx.x, gridDim.x, nseg, tab, s_math);
-        __syncthreads();
-        lf_segment_pairs<M>(a, nseg, tab, s_phi, xe, fe);
-      }
+      if constexpr (is_lf) etabar_terms<M>(tcp, a, blockIdx.x, gridDim.x, s_math, xe, fe);
     }
     // block partial: f[0] d_i <= -2^94 (reject), f[1] NaN (error), f[2] d_i >= 2^94
     {
@@ -300,17 +291,11 @@ __global__ void marg_eval_kernel(long long n, const double* y, const double* aux
   out[i] = marg_logp<M>(y[i], aux[i], s_tc, mc, s_math, s_nodes);
 }
 
-template <class M>
-size_t marg_smem(int rows_smem) {
-  return sizeof(double) * (kMathWords + kMargNodeWords + (M::kRule ? kPhiWords : 0)) +
-         (M::kRule ? segtab_bytes(rows_smem) : 0);
-}
+size_t marg_smem() { return sizeof(double) * (kMathWords + kMargNodeWords); }
 
 }  // namespace
 
-size_t marg_smem_bytes(int model, int rows_smem) {
-  return model == CUDAHM_LF ? marg_smem<LF>(rows_smem) : marg_smem<NN1>(rows_smem);
-}
+size_t marg_smem_bytes(int, int) { return marg_smem(); }
 
 cudaError_t marg_occupancy(int model, int block, int smem_bytes, int* blocks_per_sm) {
   const void* fn = (model == CUDAHM_LF) ? reinterpret_cast<const void*>(&marg_kernel<LF>)

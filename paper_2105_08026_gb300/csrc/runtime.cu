@@ -133,6 +133,10 @@ struct cudahm {
   double* marg_nodes = nullptr;  // panel nodes and weights
   int mgrid = 0, mrows_smem = 1;
   bool marg_valid = false;       // marg_lp[mcur] holds log p_i at the chain's theta
+  // the rule's inner sum H(ln L), tabulated (LF, BB1)
+  double* htab = nullptr;
+  double h_ua = 0.0, h_ub = 0.0, h_lo = 0.0, h_hi = 0.0;
+  int h_ncell = 0;
   // host mirrors
   bool data_set = false;
   bool etabar_valid = false;
@@ -374,7 +378,57 @@ SweepArgs base_args(cudahm* h) {
   a.tab_eta = h->tab_eta;
   a.marg_lp = h->marg_lp;
   a.marg_nodes = h->marg_nodes;
+  a.htab = h->htab;
+  a.h_ua = h->h_ua;
+  a.h_ub = h->h_ub;
+  a.h_lo = h->h_lo;
+  a.h_hi = h->h_hi;
+  a.h_ncell = h->h_ncell;
   return a;
+}
+
+// Tabulates the rule's inner sum H(u), u = ln L (LF, BB1), once per handle. Range: below
+// ua = ln(2^-56 F_th/q_max) every x_k equals its value at L = 0 to rounding, so H is constant;
+// above ub every pair has x >= 8.5 (Phi = 1; LF: L q_min >= F_th + 8.5 sigma_F, BB1:
+// L q_min >= F_pre), or, for BB1 when x never reaches 8.5, x has reached its limit 1/alpha to
+// rounding (L q_min >= 2^56 F_th).
+int build_htab(cudahm* h) {
+  const int nr = rule_nr(h->cfg);
+  std::vector<double> qs(static_cast<size_t>(nr));
+  CU(cudaMemcpyAsync(qs.data(), h->qs, sizeof(double) * nr, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  double qmin = qs[0], qmax = qs[0];
+  for (double v : qs) {
+    qmin = std::min(qmin, v);
+    qmax = std::max(qmax, v);
+  }
+  if (!(qmin > 0.0) || !std::isfinite(qmax)) return fail(CUDAHM_EINVAL, "rule distances give no positive flux factors");
+  const bool bb1 = h->cfg.model == CUDAHM_BB1;
+  double ua, ub;
+  if (bb1) {
+    const double Fth = h->mc.F_th;
+    ua = std::log(std::ldexp(Fth, -56) / qmax);
+    ub = std::isfinite(h->mc.F_pre) ? std::log(h->mc.F_pre / qmin) : std::log(std::ldexp(Fth, 56) / qmin);
+  } else {  // qs = q/sigma_F, x = L qs - F_th/sigma_F
+    ua = std::log(std::ldexp(h->mc.cth, -56) / qmax);
+    ub = std::log((h->mc.cth + 8.5) / qmin);
+  }
+  ub += 1e-9;
+  const int ncell = static_cast<int>(std::ceil((ub - ua) / kHDelta));
+  if (ncell < 1 || ncell > (1 << 16)) return fail(CUDAHM_EINVAL, "selection rule range too wide to tabulate");
+  TRY(alloc_into(h, &h->htab, static_cast<size_t>(ncell) * (kHDeg + 1) + 2));
+  SweepArgs r = base_args(h);
+  CU(launch_htab_build(r, ua, ncell, h->htab, h->stream));
+  double ends[2];
+  CU(cudaMemcpyAsync(ends, h->htab + static_cast<size_t>(ncell) * (kHDeg + 1), sizeof(ends), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->h_ua = ua;
+  h->h_ub = ua + kHDelta * ncell;
+  h->h_lo = ends[0];
+  h->h_hi = ends[1];
+  h->h_ncell = ncell;
+  return CUDAHM_OK;
 }
 
 // Cost (FP64-pipe operations per sweep) of one population, for the batched allocation.
@@ -623,6 +677,7 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
         launch_lf_inner(nr, h->xr, h->wr, r_max, sigma_F, h->qs, h->Wr, h->stream) != cudaSuccess ||
         launch_prefix_weights(nr, h->Wr, h->cw, h->stream) != cudaSuccess)
       return bail(fail(CUDAHM_ECUDA, "quadrature set-up failed: %s", cudaGetErrorString(cudaGetLastError())));
+    if ((rc = build_htab(h)) != CUDAHM_OK) return bail(rc);
   }
   if (launch_math_table(h->math_tab, h->stream) != cudaSuccess)
     return bail(fail(CUDAHM_ECUDA, "exp/log table set-up failed: %s", cudaGetErrorString(cudaGetLastError())));

@@ -120,26 +120,20 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   const bool skip_me = (a.skip_cta == static_cast<int>(blockIdx.x));
   constexpr bool is_lf = M::kRule;  // the model has a selection integral (LF, BB1)
   double* s_math = s_dyn;                 // [kMathWords] exp/log tables
-  double* s_phi = s_dyn + kMathWords;     // [kPhiWords] for LF, else empty
-  double* s_y = s_phi + (is_lf ? kPhiWords : 0);
+  double* s_y = s_dyn + kMathWords;
   double* s_aux = s_y + a.mpb;
   double* s_zs = s_y + 2 * a.mpb;  // spare (sine) normal of each member's Box-Muller pair
   // log f(chi_i;theta) of each member after its step (binary32 in the FP32 form), reused by the
   // theta' partial
   double* s_lf = s_y + 3 * a.mpb;
   float* s_lf32 = reinterpret_cast<float*>(s_lf);
-  double* s_rows = s_y + 4 * a.mpb;
   if (!F32) {
     for (unsigned int q = tid; q < nb1 - nb0; q += blockDim.x) {
       s_y[q] = a.y[nb0 + q];
       s_aux[q] = a.aux[nb0 + q];
     }
   }
-  if (is_lf)
-    for (int q = tid; q < kPhiWords; q += blockDim.x) s_phi[q] = a.phi_coef[q];
   for (int q = tid; q < kMathWords; q += blockDim.x) s_math[q] = a.math_tab[q];
-  const int nseg = is_lf ? lf_block_segments(a, blockIdx.x, gridDim.x) : 0;
-  const SegTab tab = segtab_carve(s_rows, a.rows_smem);
   __syncthreads();  // tables in place before thread 0 uses them
 
   if (tid == 0) {
@@ -175,8 +169,6 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   }
   __syncthreads();
   if (s_fail) return;
-  if constexpr (is_lf)
-    if (s_lpri_new != -INFINITY) lf_segment_rows<M>(s_tcp, a, blockIdx.x, gridDim.x, nseg, tab, s_math);
 
   // members of this thread: i = nb0 + tid + m blockDim (latent, RAM factor, e^chi, log l in registers)
   R chi[K], echi[K], ll[K];
@@ -247,13 +239,6 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         s_lpri_new = lp;
         s_tcp = tcp;
         s_tcpf = tcpf;
-      }
-      __syncwarp();
-      if (is_lf && s_lpri_new != -INFINITY) {
-        const ThetaC tcp = s_tcp;
-        for (int t = lane; t < nseg; t += 32) lf_segment_row<M>(tcp, a, blockIdx.x, gridDim.x, t, t, tab, s_math);
-        __syncwarp();
-        lf_segment_scan(nseg, tab);
       }
     }
 
@@ -365,7 +350,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         }
       }
     }
-    __syncthreads();  // theta' and the rule rows are ready
+    __syncthreads();  // theta' is ready
 
     // a4: theta' partial; a6: selection integral at theta'
     const ThetaC tcp = s_tcp;
@@ -413,7 +398,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
       }
     }
     if constexpr (is_lf)
-      if (prior_ok) lf_segment_pairs<M>(a, nseg, tab, s_phi, xe, fe);
+      if (prior_ok) etabar_terms<M>(tcp, a, blockIdx.x, gridDim.x, s_math, xe, fe);
 
     // a5: block partial
     {
@@ -573,9 +558,8 @@ static const void* kernel_for(int K, bool f32) {
   }
 }
 
-size_t sweep_smem_bytes(int model, int mpb, int rows_smem) {
-  return sizeof(double) * kMathWords + ((model == CUDAHM_LF || model == CUDAHM_BB1) ? sizeof(double) * kPhiWords : 0) +
-         4 * sizeof(double) * static_cast<size_t>(mpb) + segtab_bytes(rows_smem);
+size_t sweep_smem_bytes(int, int mpb, int) {
+  return sizeof(double) * kMathWords + 4 * sizeof(double) * static_cast<size_t>(mpb);
 }
 
 cudaError_t launch_math_table(double* t, cudaStream_t st) {
@@ -896,8 +880,9 @@ cudaError_t launch_eval_logdens(int model, bool f32, long long n, const double* 
   return cudaGetLastError();
 }
 
-// Stand-alone selection integral: same pair split and exact sum as the sweep kernel, so
-// the value is bit-identical to the one the sweep kernel computes for the same theta.
+// Stand-alone selection integral. With the handle's H table: the same outer-node terms and
+// exact sum as the sweep kernels, so the value is bit-identical to the one they compute for the
+// same theta. Without a table (the allocation-free entry point): the rule pair by pair.
 template <class M>
 __global__ void etabar_partial_kernel(const double* theta, const SweepArgs a, unsigned long long* partials) {
   extern __shared__ double s_rows[];
@@ -909,17 +894,21 @@ __global__ void etabar_partial_kernel(const double* theta, const SweepArgs a, un
     s_tc = M::consts(th, a.mc, a.math_tab);
   }
   __syncthreads();
-  const int nseg = lf_block_segments(a, blockIdx.x, gridDim.x);
-  double* s_phi = s_rows;
-  const SegTab tab = segtab_carve(s_rows + kPhiWords, a.rows_smem);
-  for (int q = threadIdx.x; q < kPhiWords; q += blockDim.x) s_phi[q] = a.phi_coef[q];
-  lf_segment_rows<M>(s_tc, a, blockIdx.x, gridDim.x, nseg, tab, a.math_tab);
-  __syncthreads();
   Xacc xd, xe;
   xacc_zero(xd);
   xacc_zero(xe);
   XFlags fe = {0u, 0u, 0u};
-  lf_segment_pairs<M>(a, nseg, tab, s_phi, xe, fe);
+  if (a.htab) {
+    etabar_terms<M>(s_tc, a, blockIdx.x, gridDim.x, a.math_tab, xe, fe);
+  } else {
+    const int nseg = lf_block_segments(a, blockIdx.x, gridDim.x);
+    double* s_phi = s_rows;
+    const SegTab tab = segtab_carve(s_rows + kPhiWords, a.rows_smem);
+    for (int q = threadIdx.x; q < kPhiWords; q += blockDim.x) s_phi[q] = a.phi_coef[q];
+    lf_segment_rows<M>(s_tc, a, blockIdx.x, gridDim.x, nseg, tab, a.math_tab);
+    __syncthreads();
+    lf_segment_pairs<M>(a, nseg, tab, s_phi, xe, fe);
+  }
   unsigned int f[4] = {0u, fe.nan, fe.big, 0u};
   warp_reduce(xd, xe, f);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -948,6 +937,68 @@ __global__ void etabar_partial_kernel(const double* theta, const SweepArgs a, un
   }
 }
 
+// H table of the rule (see htab_eval): block c < ncell evaluates the inner sum
+// H(u) = sum_k W_k Phi(x_k(e^u)) exactly (fixed-point sum of the rounded terms, the normal CDF
+// from the device table) at the kHDeg + 1 Chebyshev points of cell c, [ua + c kHDelta,
+// ua + (c + 1) kHDelta], and stores the interpolant's Chebyshev coefficients (discrete cosine
+// transform of the values); block ncell stores H(ua) and H(ua + ncell kHDelta).
+template <class M>
+__global__ void htab_build_kernel(const SweepArgs a, double ua, int ncell, double* coef) {
+  constexpr bool bb1 = std::is_same<M, BB1>::value;
+  __shared__ double s_phi[kPhiWords];
+  __shared__ double s_H[kHDeg + 1];
+  __shared__ BlockRed s_red;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int q = tid; q < kPhiWords; q += blockDim.x) s_phi[q] = a.phi_coef[q];
+  __syncthreads();
+  const int c = blockIdx.x;
+  const int npts = (c < ncell) ? kHDeg + 1 : 2;
+  for (int m = 0; m < npts; ++m) {
+    const double u = (c < ncell) ? ua + kHDelta * (c + 0.5 * (cospi((m + 0.5) / (kHDeg + 1)) + 1.0))
+                                 : ua + (m == 0 ? 0.0 : kHDelta * ncell);
+    const double L = exp(u);
+    Xacc acc, zero;
+    xacc_zero(acc);
+    xacc_zero(zero);
+    XFlags f = {0u, 0u, 0u};
+    for (int k = tid; k < a.nr; k += blockDim.x) {
+      double v;
+      if constexpr (bb1) {
+        const double F = L * __ldg(a.qs + k);
+        const double aF = a.mc.alpha * F;
+        v = 16.0 * (F - a.mc.F_th) * rsqrt(fma(aF, aF, a.mc.s0sq));
+      } else {
+        v = fma(16.0 * L, __ldg(a.qs + k), -16.0 * a.mc.cth);
+      }
+      xacc_add_double(acc, __ldg(a.Wr + k) * phi_table16(v, s_phi), f);
+    }
+    unsigned int fl[4] = {0u, 0u, 0u, 0u};
+    warp_reduce(acc, zero, fl);
+    if (lane == 0) s_red.d[wid] = acc;
+    __syncthreads();
+    if (wid == 0) {
+      Xacc t, z2;
+      xacc_zero(t);
+      xacc_zero(z2);
+      unsigned int g[4] = {0u, 0u, 0u, 0u};
+      if (lane < static_cast<int>(blockDim.x >> 5)) t = s_red.d[lane];
+      warp_reduce(t, z2, g);
+      if (lane == 0) s_H[m] = xacc_to_double(t);
+    }
+    __syncthreads();
+  }
+  if (c < ncell) {
+    if (tid <= kHDeg) {
+      double sum = 0.0;
+      for (int m = 0; m <= kHDeg; ++m) sum = fma(s_H[m], cospi(tid * (m + 0.5) / (kHDeg + 1)), sum);
+      sum *= 2.0 / (kHDeg + 1);
+      coef[c * (kHDeg + 1) + tid] = (tid == 0) ? 0.5 * sum : sum;
+    }
+  } else if (tid < 2) {
+    coef[ncell * (kHDeg + 1) + tid] = s_H[tid];
+  }
+}
+
 __global__ void etabar_final_kernel(const unsigned long long* partials, int nblocks, double* out) {
   Xacc E, D;
   xacc_zero(E);
@@ -965,9 +1016,15 @@ __global__ void etabar_final_kernel(const unsigned long long* partials, int nblo
   if (threadIdx.x == 0) *out = (f[1] != 0u) ? NAN : xacc_to_double(E);
 }
 
+cudaError_t launch_htab_build(const SweepArgs& rule, double ua, int ncell, double* coef, cudaStream_t st) {
+  if (rule.model == CUDAHM_BB1) htab_build_kernel<BB1><<<ncell + 1, 256, 0, st>>>(rule, ua, ncell, coef);
+  else htab_build_kernel<LF><<<ncell + 1, 256, 0, st>>>(rule, ua, ncell, coef);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_eval_etabar(const double* theta_dev, const SweepArgs& rule, unsigned long long* partials,
                                int grid, double* out, cudaStream_t st) {
-  const size_t smem = sizeof(double) * kPhiWords + segtab_bytes(rule.rows_smem);
+  const size_t smem = rule.htab ? 0 : sizeof(double) * kPhiWords + segtab_bytes(rule.rows_smem);
   if (rule.model == CUDAHM_BB1) etabar_partial_kernel<BB1><<<grid, 256, smem, st>>>(theta_dev, rule, partials);
   else etabar_partial_kernel<LF><<<grid, 256, smem, st>>>(theta_dev, rule, partials);
   cudaError_t e = cudaGetLastError();

@@ -574,6 +574,56 @@ __device__ __forceinline__ void lf_segment_pairs(const SweepArgs& a, int nseg, c
     if (tab.pre[t] != 0.0) xacc_add_double(xe, tab.pre[t], fe);
 }
 
+// ------------------------------------------------ tabulated inner sum -------
+// The selection integral is etabar(theta) = sum_j G_j(theta) H(t_j) over the outer nodes t_j
+// (ln L), with the inner sum H(u) = sum_k W_k Phi(x_k(e^u)) of the rule. H depends on L alone,
+// not on theta, so it is tabulated once per handle (htab_build_kernel: each cell's Chebyshev
+// interpolant of degree kHDeg through the rule's exact inner sums at the Chebyshev points; within
+// a few ulp of H over the whole range), and a sweep evaluates n_L table lookups instead of
+// n_L n_r normal CDFs. Below the table H is constant to rounding (every x_k equals its L = 0
+// value), above it every pair has Phi = 1.
+__device__ __forceinline__ double htab_eval(double u, const SweepArgs& a) {
+  if (!(u < a.h_ub)) return a.h_hi;
+  if (!(u > a.h_ua)) return a.h_lo;
+  const double z = (u - a.h_ua) * (1.0 / kHDelta);
+  const int ci = min(static_cast<int>(z), a.h_ncell - 1);
+  const double sx = fma(2.0, z - static_cast<double>(ci), -1.0);
+  const double* c = a.htab + ci * (kHDeg + 1);
+  double b1 = 0.0, b2 = 0.0;  // Clenshaw
+#pragma unroll
+  for (int j = kHDeg; j >= 1; --j) {
+    const double t = fma(2.0 * sx, b1, __ldg(c + j) - b2);
+    b2 = b1;
+    b1 = t;
+  }
+  return fma(sx, b1, __ldg(c) - b2);
+}
+
+// The outer node j's term G_j H(t_j) (LF: G_j = half w_j e^{(beta+1)(t - ln L*) - e^{t - ln L*}};
+// BB1: half w_j (1 - e^{-L/l}) e^{beta (t - ln u) - L/u + t}), the outer nodes spread over the
+// threads of all B blocks (block b, thread t: j = b + B t). Adds them exactly to xe.
+template <class M>
+__device__ __forceinline__ void etabar_terms(const ThetaC& tc, const SweepArgs& a, int b, int B,
+                                             const double* __restrict__ T, Xacc& xe, XFlags& fe) {
+  constexpr bool bb1 = std::is_same<M, BB1>::value;
+  const double lo = bb1 ? tc.a4 + a.mc.ln_lower : tc.a3;
+  const double hi = tc.a1 + a.mc.ln_upper;
+  const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+  for (int j = b + B * static_cast<int>(threadIdx.x); j < a.nL; j += B * static_cast<int>(blockDim.x)) {
+    const double tt = fma(half, __ldg(a.xL + j), mid);
+    double G;
+    if constexpr (bb1) {
+      const double L = exp_tab(tt, T);
+      const double lg = BB1::log1mexp(L * tc.a3);
+      G = half * __ldg(a.wL + j) * exp_tab(lg + fma(tc.a0, tt - tc.a1, -L * tc.a2) + tt, T);
+    } else {
+      const double x = tt - tc.a1;
+      G = half * __ldg(a.wL + j) * exp_tab(fma(tc.a0, x, -exp_tab(x, T)), T);
+    }
+    xacc_add_double(xe, G * htab_eval(tt, a), fe);
+  }
+}
+
 // ------------------------------------------------- block reduce helpers ------
 struct BlockRed {
   Xacc d[32];
