@@ -435,10 +435,7 @@ int build_htab(cudahm* h) {
 double pop_cost(const cudahm* h) {
   const bool f32 = h->cfg.precision == CUDAHM_FP32;
   double c = 3000.0 + static_cast<double>(h->n) * (h->d == 3 ? (f32 ? 80.0 : 260.0) : (f32 ? 20.0 : 120.0));
-  if (has_rule(h->cfg.model)) {
-    const double nL = rule_nL(h->cfg), nr = rule_nr(h->cfg);
-    c += 0.3 * nL * nr * (h->cfg.model == CUDAHM_BB1 ? 26.0 : 17.0) + nL * std::ceil(nr / 128.0) * 70.0;
-  }
+  if (has_rule(h->cfg.model)) c += 80.0 * rule_nL(h->cfg);  // one table lookup per outer node
   return c;
 }
 

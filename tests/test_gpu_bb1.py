@@ -42,7 +42,8 @@ def test_bb1_etabar_and_detection_match_oracle():
     theta0, scale, consts = synth.bb1_settings(data)
     s = cudahm.Sampler(cudahm.BB1, 500, theta_init=theta0, theta_prop_scale=scale, model_consts=consts)
     s.set_data(data.fhat, data.r)
-    for dth in ([0, 0, 0], [0.05, 0.1, -0.2], [-0.3, -0.5, 0.4], [0.25, 1.0, 1.5]):
+    for dth in ([0, 0, 0], [0.05, 0.1, -0.2], [-0.3, -0.5, 0.4], [0.25, 1.0, 1.5], [-0.45, -5.0, 6.0],
+                [0.4, 2.0, 0.5]):
         th = theta0 + np.array(dth)
         g, o = s.etabar(th), oracle.bb1_etabar(th, consts)
         assert abs(g - o) <= 1e-13 * o, (dth, g, o)

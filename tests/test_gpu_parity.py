@@ -142,7 +142,10 @@ def test_lf_etabar_matches_oracle_rule():
     theta0, scale, consts = synth.lf_settings(data)  # 1024 x 1024
     s = cudahm.Sampler(cudahm.LF, 1000, theta_init=theta0, theta_prop_scale=scale, model_consts=consts)
     s.set_data(data.fhat, data.r)
-    for dth in ([0, 0, 0], [0.05, 0.1, -0.2], [-0.3, -0.5, 0.4], [0.25, 1.0, 1.5]):
+    # the last rows reach the ends of the tabulated inner sum: outer nodes down to L ~ 1e-9 L*
+    # (H constant to rounding below the table) and up to ~1e4 L* (every pair past x = 8.5)
+    for dth in ([0, 0, 0], [0.05, 0.1, -0.2], [-0.3, -0.5, 0.4], [0.25, 1.0, 1.5], [-0.7, 5.0, -20.0],
+                [0.6, -6.0, -3.0], [-0.7, 9.0, 4.4]):
         th = theta0 + np.array(dth)
         g = s.etabar(th)
         o = oracle.lf_etabar(th, consts)
