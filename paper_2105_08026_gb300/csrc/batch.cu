@@ -537,8 +537,10 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
   }
 }
 
-template <bool F32>
-__global__ void __launch_bounds__(256, 2) batch_kernel(const SweepArgs* __restrict__ pops,
+// kD1: a batch of one-dimensional latents only (NN1, LF, BB1). Without the d = 3 member code the
+// kernel needs far fewer registers, so more warps per SM hide the latency of the streamed state.
+template <bool F32, bool kD1>
+__global__ void __launch_bounds__(256, (kD1 && F32) ? 4 : 2) batch_kernel(const SweepArgs* __restrict__ pops,
                                                        BatchProg* __restrict__ progs, const int* __restrict__ b0s,
                                                        const int* __restrict__ nbs, int npop, int chunk, int R) {
   extern __shared__ double s_dyn[];
@@ -567,10 +569,19 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const SweepArgs* __restri
   else if (s_args.model == CUDAHM_BB1) {
     if constexpr (!F32)  // FP64 form only
       run_population<BB1, false>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
-  } else if (s_args.model == CUDAHM_NN3)
-    run_population<NN3, F32>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
-  else
-    run_population<MVN3, F32>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
+  } else if constexpr (!kD1) {
+    if (s_args.model == CUDAHM_NN3)
+      run_population<NN3, F32>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
+    else
+      run_population<MVN3, F32>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
+  }
+}
+
+const void* batch_fn(bool f32, bool d1) {
+  if (f32) return d1 ? reinterpret_cast<const void*>(&batch_kernel<true, true>)
+                     : reinterpret_cast<const void*>(&batch_kernel<true, false>);
+  return d1 ? reinterpret_cast<const void*>(&batch_kernel<false, true>)
+            : reinterpret_cast<const void*>(&batch_kernel<false, false>);
 }
 
 // binary32 member data of the FP32 form (kData32 values per member, member-minor)
@@ -649,9 +660,8 @@ cudaError_t launch_data32(int model, long long n, const double* y, const double*
 
 size_t batch_smem_bytes(int) { return sizeof(double) * kMathWords; }
 
-cudaError_t batch_occupancy(bool f32, int block, int smem_bytes, int* blocks_per_sm) {
-  const void* fn = f32 ? reinterpret_cast<const void*>(&batch_kernel<true>)
-                       : reinterpret_cast<const void*>(&batch_kernel<false>);
+cudaError_t batch_occupancy(bool f32, bool d1, int block, int smem_bytes, int* blocks_per_sm) {
+  const void* fn = batch_fn(f32, d1);
   if (smem_bytes > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
@@ -659,12 +669,11 @@ cudaError_t batch_occupancy(bool f32, int block, int smem_bytes, int* blocks_per
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem_bytes);
 }
 
-cudaError_t launch_batch(bool f32, const SweepArgs* pops, BatchProg* progs, const int* b0s, const int* nbs, int npop,
-                         int chunk, int seg_slots, int grid, int block, int smem_bytes, cudaStream_t st) {
+cudaError_t launch_batch(bool f32, bool d1, const SweepArgs* pops, BatchProg* progs, const int* b0s, const int* nbs,
+                         int npop, int chunk, int seg_slots, int grid, int block, int smem_bytes, cudaStream_t st) {
   void* args[] = {const_cast<SweepArgs**>(&pops), &progs, const_cast<int**>(&b0s), const_cast<int**>(&nbs), &npop,
                   &chunk, &seg_slots};
-  const void* fn = f32 ? reinterpret_cast<const void*>(&batch_kernel<true>)
-                       : reinterpret_cast<const void*>(&batch_kernel<false>);
+  const void* fn = batch_fn(f32, d1);
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem_bytes, st);
 }
 

@@ -132,9 +132,10 @@ struct BatchProg {
 
 // Batched launches (batch.cu).
 size_t batch_smem_bytes(int seg_slots);
-cudaError_t batch_occupancy(bool f32, int block, int smem_bytes, int* blocks_per_sm);
-cudaError_t launch_batch(bool f32, const SweepArgs* pops, BatchProg* progs, const int* b0s, const int* nbs, int npop,
-                         int chunk, int seg_slots, int grid, int block, int smem_bytes, cudaStream_t st);
+// d1: every population has a one-dimensional latent (the lighter kernel variant)
+cudaError_t batch_occupancy(bool f32, bool d1, int block, int smem_bytes, int* blocks_per_sm);
+cudaError_t launch_batch(bool f32, bool d1, const SweepArgs* pops, BatchProg* progs, const int* b0s, const int* nbs,
+                         int npop, int chunk, int seg_slots, int grid, int block, int smem_bytes, cudaStream_t st);
 cudaError_t launch_batch_tables(const SweepArgs* pops, const BatchProg* progs, int npop, int chunk, cudaStream_t st);
 cudaError_t launch_data32(int model, long long n, const double* y, const double* aux, const ModelConsts& mc,
                           float* d32, cudaStream_t st);

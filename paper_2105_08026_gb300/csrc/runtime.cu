@@ -1132,6 +1132,8 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
     if (h->sweeps + n_burn + n_iter >= (1ll << 32) - 2) return fail(CUDAHM_EINVAL, "sweep counter would overflow");
   }
   const bool f32 = h0->cfg.precision == CUDAHM_FP32;
+  bool d1 = true;  // one-dimensional latents only: the lighter kernel variant
+  for (int q = 0; q < k; ++q) d1 = d1 && hs[q]->d == 1;
   CU(cudaSetDevice(h0->cfg.device));
   cudaStream_t st = h0->stream;
   for (int q = 0; q < k; ++q) CU(cudaStreamSynchronize(hs[q]->stream));
@@ -1231,8 +1233,7 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
     progs[q] = BatchProg{total, 0, n_burn, thin, 0, 0};
     cost[q] = pop_cost(h);
     long long c = (h->n + 31) / 32;
-    if (has_rule(h->cfg.model))
-      c += static_cast<long long>(rule_nL(h->cfg)) * ((static_cast<long long>(rule_nr(h->cfg)) + 127) / 128);
+    if (has_rule(h->cfg.model)) c += 8;  // the rule's outer nodes need no more than a few blocks
     cap[q] = static_cast<int>(std::min<long long>(c, max_grid));
   }
   CU(cudaMemcpyAsync(bb.pops, pops.data(), sizeof(SweepArgs) * k, cudaMemcpyHostToDevice, st));
@@ -1258,12 +1259,12 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
   auto enqueue = [&](int blk, int ch, int grid_) -> cudaError_t {
     cudaError_t e = cudaMemsetAsync(bb.bars, 0, sizeof(unsigned int) * k, st);
     if (e == cudaSuccess) e = launch_batch_tables(bb.pops, bb.progs, k, ch, st);
-    if (e == cudaSuccess) e = launch_batch(f32, bb.pops, bb.progs, bb.b0s, bb.nbs, k, ch, R, grid_, blk, smem, st);
+    if (e == cudaSuccess) e = launch_batch(f32, d1, bb.pops, bb.progs, bb.b0s, bb.nbs, k, ch, R, grid_, blk, smem, st);
     return e;
   };
   auto grid_for = [&](int blk, int* out) -> int {
     int bps = 0;
-    CU(batch_occupancy(f32, blk, smem, &bps));
+    CU(batch_occupancy(f32, d1, blk, smem, &bps));
     if (bps < 1) return fail(CUDAHM_EUNSUPPORTED, "batched kernel does not fit on this device");
     *out = std::min(bps * sms, blk == 128 ? max_grid : max_grid / 2);
     return CUDAHM_OK;
@@ -1415,8 +1416,10 @@ int batch_step(const std::vector<cudahm*>& hs, std::vector<BatchProg>& progs, in
   const int k = static_cast<int>(hs.size());
   const int R = 128;
   const int smem = static_cast<int>(batch_smem_bytes(R));
+  bool d1 = true;
+  for (const cudahm* h : hs) d1 = d1 && h->d == 1;
   int bps = 0;
-  CU(batch_occupancy(f32, block, smem, &bps));
+  CU(batch_occupancy(f32, d1, block, smem, &bps));
   if (bps < 1) return fail(CUDAHM_EUNSUPPORTED, "batched kernel does not fit on this device");
   const int grid = std::min(bps * hs[0]->sms, block == 128 ? max_grid : max_grid / 2);
   std::vector<SweepArgs> pops(k);
@@ -1435,8 +1438,7 @@ int batch_step(const std::vector<cudahm*>& hs, std::vector<BatchProg>& progs, in
     pops[q] = a;
     cost[q] = pop_cost(h);
     long long c = (h->n + 31) / 32;
-    if (has_rule(h->cfg.model))
-      c += static_cast<long long>(rule_nL(h->cfg)) * ((static_cast<long long>(rule_nr(h->cfg)) + 127) / 128);
+    if (has_rule(h->cfg.model)) c += 8;  // the rule's outer nodes need no more than a few blocks
     cap[q] = static_cast<int>(std::min<long long>(c, max_grid));
   }
   std::vector<int> nb = allocate_blocks(cost, cap, grid), b0(k);
@@ -1453,7 +1455,7 @@ int batch_step(const std::vector<cudahm*>& hs, std::vector<BatchProg>& progs, in
   CU(cudaMemsetAsync(bb.errs, 0, sizeof(int) * k, st));
   CU(cudaMemsetAsync(bb.bars, 0, sizeof(unsigned int) * k, st));
   CU(launch_batch_tables(bb.pops, bb.progs, k, chunk, st));
-  CU(launch_batch(f32, bb.pops, bb.progs, bb.b0s, bb.nbs, k, chunk, R, grid, block, smem, st));
+  CU(launch_batch(f32, d1, bb.pops, bb.progs, bb.b0s, bb.nbs, k, chunk, R, grid, block, smem, st));
   CU(cudaMemcpyAsync(progs.data(), bb.progs, sizeof(BatchProg) * k, cudaMemcpyDeviceToHost, st));
   std::vector<int> errs(k);
   CU(cudaMemcpyAsync(errs.data(), bb.errs, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
