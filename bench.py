@@ -428,41 +428,46 @@ def run_nn3_ess(args, cudahm, stream, device):
 
 
 def run_marginal(args, cudahm, stream, device, data, theta0, scale, consts, peak_fp64):
-    """The marginal form on the LF workload (N = 3e5, 1024 x 1024 rule, FP64): every member's
-    latent integrated out by the cubature rule (96 nodes per member) and a theta-only chain.
-    --marginal-burn untimed steps, then --marginal-steps timed (CUDA events on the sampler's
-    stream); reports theta steps/s, member integrals/s and the theta ESS per second."""
+    """The marginal form on the LF workload (N = 3e5, 1024 x 1024 rule): every member's latent
+    integrated out by the cubature rule (96 nodes per member) and a theta-only chain, in FP64 and
+    in the FP32 bulk form (binary32 node terms). --marginal-burn untimed steps, then
+    --marginal-steps timed (CUDA events on the sampler's stream); reports theta steps/s, member
+    integrals/s and the theta ESS per second."""
     import torch
     n = data.fhat.size
-    s = cudahm.Sampler(cudahm.LF, n, theta_init=theta0, theta_prop_scale=scale, model_consts=consts, seed=11,
-                       device=device, stream=stream.cuda_stream, use_torch_allocator=True, marginal=True)
     y_dev = torch.from_numpy(data.fhat).cuda()
     r_dev = torch.from_numpy(data.r).cuda()
-    cudahm.cudahm_set_data_device(s.h, y_dev.data_ptr(), r_dev.data_ptr(), n)
-    s.run(args.marginal_burn, 0)
-    K = args.marginal_steps
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    rows = s.run(0, K, 1)
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    ess = cudahm.cudahm_ess(rows)
-    st = s.stats()
-    s.close()
     out = {"workload": "LF N=3e5, latents integrated out by cubature (64 + 32 Gauss-Legendre nodes per member), "
-                       "theta-only chain, 1024x1024 selection rule, FP64",
-           "steps": K, "burn_in": args.marginal_burn, "ms_per_step": ms / K, "steps_per_s": K / (ms * 1e-3),
-           "member_integrals_per_s": n * K / (ms * 1e-3), "theta_accept": st.theta_accepts / st.sweeps,
-           "ess": ess.tolist(), "ess_per_s_min": float(ess.min()) / (ms * 1e-3),
-           "launch_shape": [st.grid_blocks, st.block_threads], "dtype": "f64"}
-    if MARG_FP64_FLOP_PER_MEMBER is not None and peak_fp64:
-        ach = MARG_FP64_FLOP_PER_MEMBER * n * K / (ms * 1e-3)
-        out["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "achieved": ach / 1e12, "peak": peak_fp64 / 1e12,
-                           "frac": ach / peak_fp64, "kernel": "marg_kernel<LF>",
-                           "peak_source": "FP64 DFMA stream measured live on this GPU (x2 flops)"}
+                       "theta-only chain, 1024x1024 selection rule"}
+    for name, prec in (("f64", cudahm.FP64), ("f32", cudahm.FP32)):
+        s = cudahm.Sampler(cudahm.LF, n, theta_init=theta0, theta_prop_scale=scale, model_consts=consts, seed=11,
+                           precision=prec, device=device, stream=stream.cuda_stream, use_torch_allocator=True,
+                           marginal=True)
+        cudahm.cudahm_set_data_device(s.h, y_dev.data_ptr(), r_dev.data_ptr(), n)
+        s.run(args.marginal_burn, 0)
+        K = args.marginal_steps * (1 if prec == cudahm.FP64 else 10)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rows = s.run(0, K, 1)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        ess = cudahm.cudahm_ess(rows)
+        st = s.stats()
+        s.close()
+        r = {"steps": K, "burn_in": args.marginal_burn, "ms_per_step": ms / K, "steps_per_s": K / (ms * 1e-3),
+             "member_integrals_per_s": n * K / (ms * 1e-3), "theta_accept": st.theta_accepts / st.sweeps,
+             "ess": ess.tolist(), "ess_per_s_min": float(ess.min()) / (ms * 1e-3),
+             "launch_shape": [st.grid_blocks, st.block_threads],
+             "dtype": "f64" if prec == cudahm.FP64 else "f32 node terms, f64 window/reference/sums/theta step"}
+        if prec == cudahm.FP64 and MARG_FP64_FLOP_PER_MEMBER is not None and peak_fp64:
+            ach = MARG_FP64_FLOP_PER_MEMBER * n * K / (ms * 1e-3)
+            r["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "achieved": ach / 1e12, "peak": peak_fp64 / 1e12,
+                             "frac": ach / peak_fp64, "kernel": "marg_kernel<LF>",
+                             "peak_source": "FP64 DFMA stream measured live on this GPU (x2 flops)"}
+        out[name] = r
     return out
 
 

@@ -133,7 +133,7 @@ typedef struct {
   int32_t debug_skip_barrier_cta;/* >= 0: that block never arrives at the grid barrier (tests the
                                     timeout path); -1 = off */
   int32_t marginal;              /* 1: integrate each member's latent out by cubature and run the
-                                    chain on theta alone (NN1, LF; FP64; see cudahm_eval_marginal) */
+                                    chain on theta alone (NN1, LF; see cudahm_eval_marginal) */
 } cudahm_config;
 
 typedef struct {
@@ -221,7 +221,11 @@ int cudahm_eval_logdens(cudahm_t h, const double* theta_host, double* lp_host);
  * accept rule, with D = sum_i [log p_i(theta') - log p_i(theta)] summed exactly. Such a handle
  * has no latents (set_chi and get_chi give CUDAHM_EUNSUPPORTED), needs Fhat_i > 0 for LF
  * (CUDAHM_EINVAL at set_data) and runs alone (not in batch_run or the server). Other models:
- * CUDAHM_EUNSUPPORTED. */
+ * CUDAHM_EUNSUPPORTED. FP32 handles (LF): each node's log integrand, relative to a binary64
+ * reference at the likelihood peak clamped into the window, and the panel sums are binary32
+ * (log p_i within ~1e-6 of the binary64 rule); the window, the reference, log p_i, the exact
+ * sum over members, the selection integral and the theta step stay binary64. NN1 has no
+ * binary32 variant: its FP32 handles integrate in binary64. */
 int cudahm_eval_marginal(cudahm_t h, const double* theta_host, double* lp_host);
 
 /* LF and BB1: the selection integral etabar(theta) of the handle's rule at the given theta. */

@@ -98,6 +98,7 @@ struct SweepArgs {
                       // its sequence word is bar[1]
   double* marg_lp;           // marginal form: log p_i at two thetas, [2][n]
   const double* marg_nodes;  // marginal form: panel nodes and weights (kMargNodeWords)
+  const double* marg_d32;    // marginal form, FP32 bulk, LF: per-member window data, [kMarg32Words][n]
   // the rule's inner sum H(ln L) tabulated (h_ncell cells of kHDeg + 1 Chebyshev coefficients);
   // nullptr: evaluate the rule pair by pair
   const double* htab;
@@ -119,6 +120,7 @@ constexpr int kMargPeak = 64;
 constexpr int kMargTail = 32;
 constexpr double kMargK = 10.0;
 constexpr int kMargNodeWords = 2 * (kMargPeak + kMargTail);
+constexpr int kMarg32Words = 5;  // ln(Fhat/q), Fhat/q, ln(F_b/q), ln(F_c/q), Fhat^2/(2 sigma_F^2)
 
 // Progress of one population through a batched run (device memory, updated by the kernel).
 struct BatchProg {
@@ -143,11 +145,14 @@ int data32_words(int model);
 
 // Marginal form (marginal.cu).
 size_t marg_smem_bytes(int model, int rows_smem);
-cudaError_t marg_occupancy(int model, int block, int smem_bytes, int* blocks_per_sm);
+cudaError_t marg_occupancy(int model, bool f32, int block, int smem_bytes, int* blocks_per_sm);
 cudaError_t launch_marg(const SweepArgs& a, int grid, int block, cudaStream_t st);
-cudaError_t launch_marg_eval(int model, long long n, const double* y, const double* aux, const double* theta_dev,
-                             const ModelConsts& mc, const double* math_tab, const double* nodes, double* out,
-                             cudaStream_t st);
+// f32: the FP32 bulk form (LF reads md32; NN1 has no binary32 variant and uses binary64)
+cudaError_t launch_marg_eval(int model, bool f32, long long n, const double* y, const double* aux,
+                             const double* theta_dev, const ModelConsts& mc, const double* math_tab,
+                             const double* nodes, const double* md32, double* out, cudaStream_t st);
+cudaError_t launch_marg_data32(long long n, const double* y, const double* aux, const ModelConsts& mc,
+                               const double* math_tab, double* md32, cudaStream_t st);
 cudaError_t launch_marg_nodes(double* nodes, cudaStream_t st);
 
 // Records a failure for cudahm_last_error() (runtime.cu); returns code.

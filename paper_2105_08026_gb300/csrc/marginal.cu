@@ -87,7 +87,82 @@ __device__ double marg_logp(double y, double aux, const ThetaC& tc, const ModelC
   }
 }
 
-template <class M>
+// FP32 bulk form of the LF member integral: the same panels, the log integrand at each node in
+// binary32 relative to a reference point c_r (the likelihood peak chi* = ln(Fhat/q) clamped into
+// the window), written so that nothing cancels: with u = chi - c_r, e1 = expm1(u),
+// R = e^{c_r - chi*}, D0 = 1 - R, A = Fhat^2/(2 sigma_F^2) and E_r = e^{c_r - ln L*},
+//   log l(chi) - log l(c_r) = A R e1 (2 D0 - R e1),
+//   log f(chi) - log f(c_r) = (beta + 1) u - E_r e1.
+// The window, c_r, the reference value and the panel geometry are binary64 (per member, a few
+// operations: chi*, Fhat/q and the window ends are precomputed once, md32); the nodes' terms are
+// binary32, summed with Kahan's compensation (a plain binary32 sum of the 96 terms biased log p_i
+// by ~1e-8 in a host emulation), and log p_i = (binary64 reference) + log(sum) in binary64.
+__device__ double marg_logp32_lf(long long i, long long n, const double* __restrict__ md, const ThetaC& tc,
+                                 const double* T, const float* nd) {
+  const double chis = __ldg(md + i), Lhat = __ldg(md + n + i), chib = __ldg(md + 2 * n + i),
+               chic = __ldg(md + 3 * n + i), A = __ldg(md + 4 * n + i);
+  const double lo = tc.a3;
+  const double a2 = fmax(chic, lo);
+  if (!(a2 < chib)) return -INFINITY;
+  const double cref = fmin(fmax(chis, a2), chib);
+  double R = 1.0, D0 = 0.0, Eref, m0;
+  if (cref == chis) {  // the usual case: the peak lies in the window
+    Eref = Lhat * tc.a2;
+    m0 = fma(tc.a0, chis - tc.a1, -Eref);
+  } else {
+    R = exp_tab(cref - chis, T);
+    D0 = 1.0 - R;
+    Eref = Lhat * R * tc.a2;
+    m0 = fma(-A * D0, D0, fma(tc.a0, cref - tc.a1, -Eref));
+  }
+  const float ARf = static_cast<float>(A * R), Rf = static_cast<float>(R), twoD0 = static_cast<float>(2.0 * D0);
+  const float b1 = static_cast<float>(tc.a0), Ef = static_cast<float>(Eref);
+  const float* xp = nd;
+  const float* wp = nd + kMargPeak;
+  const float* xt = nd + 2 * kMargPeak;
+  const float* wt = nd + 2 * kMargPeak + kMargTail;
+  const double c2 = 0.5 * (a2 + chib), h2 = 0.5 * (chib - a2);
+  const float cf2 = static_cast<float>(c2 - cref), hf2 = static_cast<float>(h2);
+  float s2 = 0.0f, k2 = 0.0f;
+#pragma unroll 8
+  for (int j = 0; j < kMargPeak; ++j) {
+    const float u = fmaf(hf2, xp[j], cf2);
+    const float e1 = expm1f(u);
+    const float dv = fmaf(ARf * e1, fmaf(-Rf, e1, twoD0), fmaf(b1, u, -Ef * e1));
+    const float y = __fsub_rn(__fmul_rn(wp[j], __expf(dv)), k2);
+    const float t = __fadd_rn(s2, y);
+    k2 = __fsub_rn(__fsub_rn(t, s2), y);
+    s2 = t;
+  }
+  double s = h2 * static_cast<double>(s2);
+  if (lo < chic) {
+    const double c1 = 0.5 * (lo + chic), h1 = 0.5 * (chic - lo);
+    const float cf1 = static_cast<float>(c1 - cref), hf1 = static_cast<float>(h1);
+    float s1 = 0.0f, k1 = 0.0f;
+#pragma unroll 8
+    for (int j = 0; j < kMargTail; ++j) {
+      const float u = fmaf(hf1, xt[j], cf1);
+      const float e1 = expm1f(u);
+      const float dv = fmaf(ARf * e1, fmaf(-Rf, e1, twoD0), fmaf(b1, u, -Ef * e1));
+      const float y = __fsub_rn(__fmul_rn(wt[j], __expf(dv)), k1);
+      const float t = __fadd_rn(s1, y);
+      k1 = __fsub_rn(__fsub_rn(t, s1), y);
+      s1 = t;
+    }
+    s = fma(h1, static_cast<double>(s1), s);
+  }
+  return m0 + log_tab(s, T);
+}
+
+// nd: the nodes and weights in binary64, nd32 the same in binary32 (FP32 form)
+template <class M, bool F32>
+__device__ __forceinline__ double marg_member(const SweepArgs& a, long long i, const ThetaC& tc, const double* T,
+                                              const double* nd, const float* nd32) {
+  if constexpr (F32 && M::kRule) return marg_logp32_lf(i, a.n, a.marg_d32, tc, T, nd32);
+  else return marg_logp<M>(__ldg(a.y + i), __ldg(a.aux + i), tc, a.mc, T, nd);
+}
+
+template <class M, bool F32>
 __global__ void __launch_bounds__(256, 2) marg_kernel(const SweepArgs a) {
   extern __shared__ double s_dyn[];
   __shared__ double s_theta[kMaxP], s_thp[kMaxP], s_Sth[kMaxP * kMaxP];
@@ -106,8 +181,12 @@ __global__ void __launch_bounds__(256, 2) marg_kernel(const SweepArgs a) {
   const bool skip_me = (a.skip_cta == static_cast<int>(blockIdx.x));
   double* s_math = s_dyn;
   double* s_nodes = s_math + kMathWords;
+  float* s_nodes32 = reinterpret_cast<float*>(s_nodes + kMargNodeWords);
   for (int q = tid; q < kMathWords; q += blockDim.x) s_math[q] = a.math_tab[q];
-  for (int q = tid; q < kMargNodeWords; q += blockDim.x) s_nodes[q] = a.marg_nodes[q];
+  for (int q = tid; q < kMargNodeWords; q += blockDim.x) {
+    s_nodes[q] = a.marg_nodes[q];
+    s_nodes32[q] = static_cast<float>(a.marg_nodes[q]);
+  }
   __syncthreads();  // tables in place before thread 0 uses them
 
   if (tid == 0) {
@@ -144,7 +223,7 @@ __global__ void __launch_bounds__(256, 2) marg_kernel(const SweepArgs a) {
       const double* lpc = a.marg_lp + static_cast<long long>(s_cur) * a.n;
       double* lpn = a.marg_lp + static_cast<long long>(1 - s_cur) * a.n;
       for (unsigned int i = nb0 + tid; i < nb1; i += blockDim.x) {
-        const double v = marg_logp<M>(__ldg(a.y + i), __ldg(a.aux + i), tcp, a.mc, s_math, s_nodes);
+        const double v = marg_member<M, F32>(a, i, tcp, s_math, s_nodes, s_nodes32);
         lpn[i] = v;
         const double dn = (v == -INFINITY) ? -INFINITY : v - lpc[i];
         if (disnan(dn)) fd.nan++;
@@ -271,14 +350,19 @@ __global__ void __launch_bounds__(256, 2) marg_kernel(const SweepArgs a) {
 }
 
 // log p_i(theta) of every member at theta (device, p doubles), into out[n].
-template <class M>
+template <class M, bool F32>
 __global__ void marg_eval_kernel(long long n, const double* y, const double* aux, const double* theta,
-                                 ModelConsts mc, const double* T, const double* nodes, double* out) {
+                                 ModelConsts mc, const double* T, const double* nodes, const double* md32,
+                                 double* out) {
   __shared__ double s_math[kMathWords];
   __shared__ double s_nodes[kMargNodeWords];
+  __shared__ float s_nodes32[kMargNodeWords];
   __shared__ ThetaC s_tc;
   for (int q = threadIdx.x; q < kMathWords; q += blockDim.x) s_math[q] = T[q];
-  for (int q = threadIdx.x; q < kMargNodeWords; q += blockDim.x) s_nodes[q] = nodes[q];
+  for (int q = threadIdx.x; q < kMargNodeWords; q += blockDim.x) {
+    s_nodes[q] = nodes[q];
+    s_nodes32[q] = static_cast<float>(nodes[q]);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     double th[kMaxP];
@@ -288,18 +372,43 @@ __global__ void marg_eval_kernel(long long n, const double* y, const double* aux
   __syncthreads();
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  out[i] = marg_logp<M>(y[i], aux[i], s_tc, mc, s_math, s_nodes);
+  if constexpr (F32 && M::kRule) out[i] = marg_logp32_lf(i, n, md32, s_tc, s_math, s_nodes32);
+  else out[i] = marg_logp<M>(y[i], aux[i], s_tc, mc, s_math, s_nodes);
 }
 
-size_t marg_smem() { return sizeof(double) * (kMathWords + kMargNodeWords); }
+// Per-member window data of the FP32 LF form (theta-independent): ln(Fhat/q), Fhat/q, the window
+// ends ln(F_b/q), ln(F_c/q) as the binary64 form computes them, Fhat^2/(2 sigma_F^2).
+__global__ void marg_data32_kernel(long long n, const double* y, const double* aux, ModelConsts mc,
+                                   const double* T, double* md) {
+  __shared__ double s_math[kMathWords];
+  for (int q = threadIdx.x; q < kMathWords; q += blockDim.x) s_math[q] = T[q];
+  __syncthreads();
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double F = y[i], q = aux[i];
+  const double Fb = __fma_rn(kMargK, mc.sigF, F);
+  const double Fc = fmax(__fma_rn(-kMargK, mc.sigF, F), __dmul_rn(0.5, F));
+  md[i] = log_tab(__ddiv_rn(F, q), s_math);
+  md[n + i] = F / q;
+  md[2 * n + i] = log_tab(__ddiv_rn(Fb, q), s_math);
+  md[3 * n + i] = log_tab(__ddiv_rn(Fc, q), s_math);
+  md[4 * n + i] = F * F * mc.inv2sig2;
+}
+
+size_t marg_smem() { return sizeof(double) * (kMathWords + kMargNodeWords) + sizeof(float) * kMargNodeWords; }
 
 }  // namespace
 
 size_t marg_smem_bytes(int, int) { return marg_smem(); }
 
-cudaError_t marg_occupancy(int model, int block, int smem_bytes, int* blocks_per_sm) {
-  const void* fn = (model == CUDAHM_LF) ? reinterpret_cast<const void*>(&marg_kernel<LF>)
-                                        : reinterpret_cast<const void*>(&marg_kernel<NN1>);
+static const void* marg_fn(int model, bool f32) {
+  if (model == CUDAHM_LF)
+    return f32 ? reinterpret_cast<const void*>(&marg_kernel<LF, true>) : reinterpret_cast<const void*>(&marg_kernel<LF, false>);
+  return reinterpret_cast<const void*>(&marg_kernel<NN1, false>);  // NN1: binary64 in both forms
+}
+
+cudaError_t marg_occupancy(int model, bool f32, int block, int smem_bytes, int* blocks_per_sm) {
+  const void* fn = marg_fn(model, f32);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem_bytes);
@@ -308,21 +417,30 @@ cudaError_t marg_occupancy(int model, int block, int smem_bytes, int* blocks_per
 cudaError_t launch_marg(const SweepArgs& a, int grid, int block, cudaStream_t st) {
   const size_t smem = marg_smem_bytes(a.model, a.rows_smem);
   void* args[] = {const_cast<SweepArgs*>(&a)};
-  const void* fn = (a.model == CUDAHM_LF) ? reinterpret_cast<const void*>(&marg_kernel<LF>)
-                                          : reinterpret_cast<const void*>(&marg_kernel<NN1>);
+  const void* fn = marg_fn(a.model, a.f32 != 0);
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, st);
 }
 
-cudaError_t launch_marg_eval(int model, long long n, const double* y, const double* aux, const double* theta_dev,
-                             const ModelConsts& mc, const double* math_tab, const double* nodes, double* out,
-                             cudaStream_t st) {
+cudaError_t launch_marg_eval(int model, bool f32, long long n, const double* y, const double* aux,
+                             const double* theta_dev, const ModelConsts& mc, const double* math_tab,
+                             const double* nodes, const double* md32, double* out, cudaStream_t st) {
   const int blk = 256;
   const unsigned int grid = static_cast<unsigned int>((n + blk - 1) / blk);
-  if (model == CUDAHM_LF) marg_eval_kernel<LF><<<grid, blk, 0, st>>>(n, y, aux, theta_dev, mc, math_tab, nodes, out);
+  if (model == CUDAHM_LF && f32)
+    marg_eval_kernel<LF, true><<<grid, blk, 0, st>>>(n, y, aux, theta_dev, mc, math_tab, nodes, md32, out);
+  else if (model == CUDAHM_LF)
+    marg_eval_kernel<LF, false><<<grid, blk, 0, st>>>(n, y, aux, theta_dev, mc, math_tab, nodes, md32, out);
   else if (model == CUDAHM_NN1)
-    marg_eval_kernel<NN1><<<grid, blk, 0, st>>>(n, y, aux, theta_dev, mc, math_tab, nodes, out);
+    marg_eval_kernel<NN1, false><<<grid, blk, 0, st>>>(n, y, aux, theta_dev, mc, math_tab, nodes, md32, out);
   else
     return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_marg_data32(long long n, const double* y, const double* aux, const ModelConsts& mc,
+                               const double* math_tab, double* md32, cudaStream_t st) {
+  const int blk = 256;
+  marg_data32_kernel<<<static_cast<unsigned int>((n + blk - 1) / blk), blk, 0, st>>>(n, y, aux, mc, math_tab, md32);
   return cudaGetLastError();
 }
 

@@ -131,6 +131,7 @@ struct cudahm {
   // marginal form (latents integrated out by cubature)
   double* marg_lp = nullptr;     // [2][n] log p_i at the current theta and at the proposal
   double* marg_nodes = nullptr;  // panel nodes and weights
+  double* marg_d32 = nullptr;    // FP32 form, LF: per-member window data
   int mgrid = 0, mrows_smem = 1;
   bool marg_valid = false;       // marg_lp[mcur] holds log p_i at the chain's theta
   // the rule's inner sum H(ln L), tabulated (LF, BB1)
@@ -257,7 +258,6 @@ int validate(const cudahm_config* c) {
   if (c->marginal) {
     if (c->model != CUDAHM_NN1 && c->model != CUDAHM_LF)
       return fail(CUDAHM_EUNSUPPORTED, "the marginal form integrates one-dimensional latents (NN1, LF)");
-    if (c->precision != CUDAHM_FP64) return fail(CUDAHM_EUNSUPPORTED, "the marginal form is FP64 only");
   }
   return CUDAHM_OK;
 }
@@ -326,7 +326,7 @@ int choose_marg_shape(cudahm* h) {
     const size_t smem = marg_smem_bytes(model, rows);
     if (smem > 200 * 1024) continue;
     int fit = 0;
-    CU(marg_occupancy(model, 256, static_cast<int>(smem), &fit));
+    CU(marg_occupancy(model, h->cfg.precision == CUDAHM_FP32, 256, static_cast<int>(smem), &fit));
     if (fit * h->sms >= grid) {
       h->mgrid = grid;
       h->mrows_smem = rows;
@@ -378,6 +378,7 @@ SweepArgs base_args(cudahm* h) {
   a.tab_eta = h->tab_eta;
   a.marg_lp = h->marg_lp;
   a.marg_nodes = h->marg_nodes;
+  a.marg_d32 = h->marg_d32;
   a.htab = h->htab;
   a.h_ua = h->h_ua;
   a.h_ub = h->h_ub;
@@ -526,6 +527,10 @@ int prepare(cudahm* h, const double* y_dev_raw, const double* aux_dev_raw, int s
   if (h->cfg.precision == CUDAHM_FP32) {  // binary32 member data for the batched FP32 form
     if (!h->d32) TRY(alloc_into(h, &h->d32, static_cast<size_t>(data32_words(h->cfg.model)) * h->n));
     CU(launch_data32(h->cfg.model, h->n, h->y, h->aux, h->mc, h->d32, h->stream));
+    if (h->cfg.marginal && h->cfg.model == CUDAHM_LF) {  // the FP32 marginal form's window data
+      if (!h->marg_d32) TRY(alloc_into(h, &h->marg_d32, static_cast<size_t>(kMarg32Words) * h->n));
+      CU(launch_marg_data32(h->n, h->y, h->aux, h->mc, h->math_tab, h->marg_d32, h->stream));
+    }
   }
   TRY(reset_chain(h));
   h->data_set = true;
@@ -784,8 +789,9 @@ int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
   if (h->cfg.marginal && !h->marg_valid) {
     // log p_i at the current theta into array 0, once per chain
     char* base = reinterpret_cast<char*>(h->chain);
-    CU(launch_marg_eval(h->cfg.model, h->n, h->y, h->aux, reinterpret_cast<const double*>(base + offsetof(ChainState, theta)),
-                        h->mc, h->math_tab, h->marg_nodes, h->marg_lp, h->stream));
+    CU(launch_marg_eval(h->cfg.model, h->cfg.precision == CUDAHM_FP32, h->n, h->y, h->aux,
+                        reinterpret_cast<const double*>(base + offsetof(ChainState, theta)), h->mc, h->math_tab,
+                        h->marg_nodes, h->marg_d32, h->marg_lp, h->stream));
     CU(cudaMemsetAsync(base + offsetof(ChainState, mcur), 0, sizeof(int), h->stream));
     h->marg_valid = true;
   }
@@ -935,8 +941,8 @@ int cudahm_eval_marginal(cudahm_t h, const double* theta_host, double* lp_host) 
   double* out = nullptr;
   TRY(alloc_into(h, &out, h->n));
   CU(cudaMemcpyAsync(h->theta_dev, theta_host, sizeof(double) * h->p, cudaMemcpyHostToDevice, h->stream));
-  const cudaError_t e = launch_marg_eval(h->cfg.model, h->n, h->y, h->aux, h->theta_dev, h->mc, h->math_tab,
-                                         h->marg_nodes, out, h->stream);
+  const cudaError_t e = launch_marg_eval(h->cfg.model, h->cfg.precision == CUDAHM_FP32, h->n, h->y, h->aux,
+                                         h->theta_dev, h->mc, h->math_tab, h->marg_nodes, h->marg_d32, out, h->stream);
   if (e != cudaSuccess) {
     h->dfree(out);
     return fail(CUDAHM_ECUDA, "marginal evaluation failed: %s", cudaGetErrorString(e));

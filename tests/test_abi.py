@@ -69,7 +69,6 @@ def test_config_defaults(lib):
                 [c.model_consts.__setitem__(q, v) for q, v in enumerate((1.0, 2.0, 1.0, 0.0, 0.0, 1.0))]] and None,
      cudahm.EINVAL),  # C_pop not positive definite
     (lambda c: setattr(c, "marginal", 2), cudahm.EINVAL),
-    (lambda c: [setattr(c, "marginal", 1), setattr(c, "precision", cudahm.FP32)] and None, cudahm.EUNSUPPORTED),
     (lambda c: [setattr(c, "marginal", 1), setattr(c, "model", cudahm.NN3), setattr(c, "d", 3),
                 [c.model_consts.__setitem__(q, v) for q, v in enumerate((1.0, 0.0, 1.0, 0.0, 0.0, 1.0))]] and None,
      cudahm.EUNSUPPORTED),  # the marginal form integrates 1-D latents only

@@ -22,6 +22,8 @@ Sec. 6) against the oracle.
   1e-10 max(1, N/1e4) absolute, the selection integral within 1e-12 relative; NN1 N = 1000,
   LF with a small rule, and the full LF workload (N = 3e5, 1024 x 1024 rule) for a few steps.
 - run(a) + run(b) equals run(a + b), and a checkpoint restores the chain bit for bit.
+- FP32 bulk form (LF): per-member integrals within 2e-6 of the binary64 rule, the sum of their
+  theta differences within 1e-3 at N = 3e5, and the chain's posterior against the FP64 chain's.
 """
 import math
 
@@ -172,3 +174,49 @@ def test_marginal_handle_rejections():
     with pytest.raises(cudahm.CudahmError) as ei:
         _sampler(cudahm.LF, fh, lf.r, c, th, sc, 1)
     assert ei.value.code == cudahm.EINVAL
+
+
+def test_lf_fp32_member_integrals_and_differences():
+    """FP32 bulk form of the LF member integral against the oracle's binary64 rule: each
+    log p_i within 2e-6 max(1, |log p_i|) (binary32 node terms, Kahan-summed, binary64 reference
+    and log; a host emulation of the same recipe stays below 4e-7), and the sum over all
+    members of log p_i(theta') - log p_i(theta), the quantity the theta step uses, within 1e-3
+    of the oracle's at N = 3e5."""
+    data = synth.lf_data(300_000, seed=1002)
+    th0, sc, c = synth.lf_settings(data)
+    s = _sampler(cudahm.LF, data.fhat, data.r, c, th0, sc, 2, precision=cudahm.FP32)
+    ths = [th0, th0 + np.array([0.004, 0.01, -0.02]), th0 + np.array([0.05, 0.3, 0.5])]
+    got = [s.marginal_logp(th) for th in ths]
+    ref = [oracle.marg_logp(oracle.LF, data.fhat, data.r, c, th) for th in ths]
+    for a, b in zip(got, ref):
+        assert np.array_equal(np.isfinite(a), np.isfinite(b))
+        fin = np.isfinite(b)
+        err = np.abs(a[fin] - b[fin]) / np.maximum(1.0, np.abs(b[fin]))
+        assert err.max() <= 2e-6, err.max()
+    for q in (1, 2):
+        fin = np.isfinite(ref[q]) & np.isfinite(ref[0])
+        dg = math.fsum(got[q][fin] - got[0][fin])
+        do = math.fsum(ref[q][fin] - ref[0][fin])
+        assert abs(dg - do) <= 1e-3, (q, dg, do)
+
+
+def test_lf_fp32_marginal_chain_matches_fp64():
+    """The FP32 marginal chain's theta posterior against the FP64 marginal chain (itself in
+    lockstep with the oracle): means within 4 combined Monte Carlo standard errors."""
+    data = synth.lf_data(3000, seed=33)
+    th0, sc, c = synth.lf_settings(data, nL=64, nr=64)
+    a = _sampler(cudahm.LF, data.fhat, data.r, c, th0, sc, 41, precision=cudahm.FP32).run(2000, 30000)
+    b = _sampler(cudahm.LF, data.fhat, data.r, c, th0, sc, 42).run(2000, 30000)
+    for j in range(3):
+        se = math.hypot(float(a[:, j].std() / math.sqrt(cudahm.cudahm_ess(a[:, j])[0])),
+                        float(b[:, j].std() / math.sqrt(cudahm.cudahm_ess(b[:, j])[0])))
+        assert abs(a[:, j].mean() - b[:, j].mean()) < 4 * se, (j, a[:, j].mean(), b[:, j].mean(), se)
+
+
+def test_nn1_fp32_marginal_is_binary64():
+    """NN1 has no binary32 variant: an FP32 marginal handle runs the binary64 integrals."""
+    d = synth.nn1_data(500, seed=8)
+    th0, sc, c = synth.nn1_settings(d)
+    r32 = _sampler(cudahm.NN1, d.y, d.sigma, c, th0, sc, 3, precision=cudahm.FP32).run(0, 200)
+    r64 = _sampler(cudahm.NN1, d.y, d.sigma, c, th0, sc, 3).run(0, 200)
+    assert np.array_equal(r32, r64)
