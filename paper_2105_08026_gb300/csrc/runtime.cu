@@ -1709,8 +1709,9 @@ int cudahm_server_submit(cudahm_server_t sv, const cudahm_config* cfg, const dou
   r->thin = n_iter > 0 ? thin : 1;
   r->bytes = request_bytes(*cfg, n_iter, r->thin);
   if (r->bytes > sv->budget) {
+    const size_t need = r->bytes;
     delete r;
-    return fail(CUDAHM_ENOMEM, "request needs about %zu bytes, more than the whole budget", r->bytes);
+    return fail(CUDAHM_ENOMEM, "request needs about %zu bytes, more than the whole budget", need);
   }
   const size_t cnt = static_cast<size_t>(cfg->n) * cfg->d;
   r->y.assign(y_host, y_host + cnt);

@@ -115,8 +115,9 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   // members, so that its FP64 unit is not shared with member work; the other blocks split them.
   const unsigned int mb0 = (!F32 && gridDim.x > 1) ? 1u : 0u;
   const unsigned int mgrid = gridDim.x - mb0, mblk = blockIdx.x - mb0;
-  const unsigned int nb0 = (blockIdx.x < mb0) ? 0u : static_cast<unsigned int>((a.n * mblk) / mgrid);
-  const unsigned int nb1 = (blockIdx.x < mb0) ? 0u : static_cast<unsigned int>((a.n * (mblk + 1)) / mgrid);
+  const bool leader_only = (mb0 == 1u && blockIdx.x == 0);
+  const unsigned int nb0 = leader_only ? 0u : static_cast<unsigned int>((a.n * mblk) / mgrid);
+  const unsigned int nb1 = leader_only ? 0u : static_cast<unsigned int>((a.n * (mblk + 1)) / mgrid);
   const bool skip_me = (a.skip_cta == static_cast<int>(blockIdx.x));
   constexpr bool is_lf = M::kRule;  // the model has a selection integral (LF, BB1)
   double* s_math = s_dyn;                 // [kMathWords] exp/log tables
