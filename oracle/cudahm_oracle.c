@@ -715,24 +715,34 @@ int orc_run(int model, int d, int p, int64_t n, const double* y, const double* a
 /*   NN1: one 64-node panel on m +- 10 s, with m, s the mean and standard       */
 /*        deviation of the (Gaussian) integrand;                                */
 /*   LF:  with F_b = Fhat + 10 sigma_F and F_c = max(Fhat - 10 sigma_F, Fhat/2), */
-/*        a 64-node panel on [max(ln L_low, ln(F_c/q)), ln(F_b/q)] and a 32-node */
-/*        panel on [ln L_low, ln(F_c/q)] when that is not empty; -inf when       */
-/*        ln L_low >= ln(F_b/q) (no likelihood mass left on the support).        */
+/*        a 64-node panel on [max(ln L_low, ln(F_c/q)), ln(F_b/q)] and, for a    */
+/*        faint member (F_c = Fhat/2, whose likelihood keeps e^{-Fhat^2/2sigma^2} */
+/*        of its peak down to F = 0), a 32-node panel on [ln L_low, ln(F_c/q)]   */
+/*        when that is not empty (for the others the likelihood below F_c is     */
+/*        below e^-50 of its peak); -inf when ln L_low >= ln(F_b/q).             */
+/*   BB1: the same panels with the flux-dependent error sigma(F): F_b solves    */
+/*        F_b - Fhat = 10 sigma(F_b) (alpha < 1/10), F_c = max(Fhat - 10         */
+/*        sigma(Fhat), Fhat/2), the lower end ln l + ln(lower/l), the selection  */
+/*        rule's own lower end (BB1 has no truncation), and a 128-node tail      */
+/*        panel (it spans ~40 e-folds of L and the rise of 1 - e^{-L/l}).        */
 /* The marginal posterior of theta is prod_i p_i(theta) e^{N c(theta)} pi(theta) */
 /* (LF: divided by etabar(theta)^N, as in the member form).                     */
 /* ------------------------------------------------------------------------- */
 #define ORC_MARG_NPEAK 64
 #define ORC_MARG_NTAIL 32
+#define ORC_MARG_NTAIL_BB1 128
 #define ORC_MARG_K 10.0
 
 typedef struct {
   double xp[ORC_MARG_NPEAK], wp[ORC_MARG_NPEAK];
   double xt[ORC_MARG_NTAIL], wt[ORC_MARG_NTAIL];
+  double xb[ORC_MARG_NTAIL_BB1], wb[ORC_MARG_NTAIL_BB1];
 } marg_rule;
 
 static void marg_rule_init(marg_rule* R) {
   orc_gauss_legendre(ORC_MARG_NPEAK, R->xp, R->wp);
   orc_gauss_legendre(ORC_MARG_NTAIL, R->xt, R->wt);
+  orc_gauss_legendre(ORC_MARG_NTAIL_BB1, R->xb, R->wb);
 }
 
 /* log of sum_j w_j exp(v_j), by the largest v_j */
@@ -747,7 +757,7 @@ static double log_wsum(const double* v, const double* w, int m) {
 }
 
 static double marg_logp_one(const problem* P, const marg_rule* R, int64_t i, const double* th) {
-  double v[ORC_MARG_NPEAK + ORC_MARG_NTAIL], w[ORC_MARG_NPEAK + ORC_MARG_NTAIL];
+  double v[ORC_MARG_NPEAK + ORC_MARG_NTAIL_BB1], w[ORC_MARG_NPEAK + ORC_MARG_NTAIL_BB1];
   int m = 0;
   if (P->model == ORC_NN1) {
     double y = P->y[i], sig = P->aux[i], tau = exp(th[1]);
@@ -763,32 +773,50 @@ static double marg_logp_one(const problem* P, const marg_rule* R, int64_t i, con
     }
     return log_wsum(v, w, m);
   }
-  /* LF */
-  double fhat = P->y[i], q = lf_q(P->aux[i]), sigF = P->consts[0];
-  double Fb = fhat + ORC_MARG_K * sigF;
-  double Fc = fhat - ORC_MARG_K * sigF;
-  if (Fc < 0.5 * fhat) Fc = 0.5 * fhat;
-  double chib = log(Fb / q), chic = log(Fc / q), lo = th[2];
+  /* LF and BB1 */
+  const int bb1 = (P->model == ORC_BB1);
+  double fhat = P->y[i], q = lf_q(P->aux[i]);
+  double Fb, Fc, lo;
+  if (bb1) {
+    double s0 = P->consts[0], al = P->consts[1], K = ORC_MARG_K;
+    double den = 1.0 - K * K * al * al;
+    Fb = (fhat + K * sqrt(al * al * fhat * fhat + den * s0 * s0)) / den;
+    Fc = fhat - K * sqrt(bb1_sigma2(fhat, P->consts));
+    lo = th[1] + P->consts[7];
+  } else {
+    double sigF = P->consts[0];
+    Fb = fhat + ORC_MARG_K * sigF;
+    Fc = fhat - ORC_MARG_K * sigF;
+    lo = th[2];
+  }
+  const int faint = (Fc < 0.5 * fhat);
+  if (faint) Fc = 0.5 * fhat;
+  double chib = log(Fb / q), chic = log(Fc / q);
   double a2 = (chic > lo) ? chic : lo;
   if (!(a2 < chib)) return -INFINITY;
   for (int j = 0; j < ORC_MARG_NPEAK; ++j) {
     double chi = 0.5 * (a2 + chib) + 0.5 * (chib - a2) * R->xp[j];
-    v[m] = lf_loglike(chi, fhat, P->aux[i], P->consts) + lf_logf_obj(chi, th);
+    v[m] = bb1 ? bb1_loglike(chi, fhat, P->aux[i], P->consts) + bb1_logf_obj(chi, th)
+               : lf_loglike(chi, fhat, P->aux[i], P->consts) + lf_logf_obj(chi, th);
     w[m] = 0.5 * (chib - a2) * R->wp[j];
     ++m;
   }
-  if (lo < chic) {
-    for (int j = 0; j < ORC_MARG_NTAIL; ++j) {
-      double chi = 0.5 * (lo + chic) + 0.5 * (chic - lo) * R->xt[j];
-      v[m] = lf_loglike(chi, fhat, P->aux[i], P->consts) + lf_logf_obj(chi, th);
-      w[m] = 0.5 * (chic - lo) * R->wt[j];
+  if (faint && lo < chic) {
+    const int nt = bb1 ? ORC_MARG_NTAIL_BB1 : ORC_MARG_NTAIL;
+    const double* xt = bb1 ? R->xb : R->xt;
+    const double* wt = bb1 ? R->wb : R->wt;
+    for (int j = 0; j < nt; ++j) {
+      double chi = 0.5 * (lo + chic) + 0.5 * (chic - lo) * xt[j];
+      v[m] = bb1 ? bb1_loglike(chi, fhat, P->aux[i], P->consts) + bb1_logf_obj(chi, th)
+                 : lf_loglike(chi, fhat, P->aux[i], P->consts) + lf_logf_obj(chi, th);
+      w[m] = 0.5 * (chic - lo) * wt[j];
       ++m;
     }
   }
   return log_wsum(v, w, m);
 }
 
-/* Per-member log p_i(theta) of the rule above (NN1: aux = sigma_i; LF: aux = r_i). */
+/* Per-member log p_i(theta) of the rule above (NN1: aux = sigma_i; LF, BB1: aux = r_i). */
 void orc_marg_logp(int model, int64_t n, const double* y, const double* aux, const double* consts,
                    const double* theta, double* out) {
   problem P;
@@ -812,9 +840,11 @@ int orc_marg_run(int model, int p, int64_t n, const double* y, const double* aux
   problem P;
   memset(&P, 0, sizeof(P));
   P.model = model; P.d = 1; P.p = p; P.n = n; P.y = y; P.aux = aux; P.consts = consts;
-  const int has_rule = (model == ORC_LF);
-  if (has_rule) gl_rule_init(&P.rule, (int)consts[3], (int)consts[4]);
-  if (has_rule && *etabar_cur == 0.0) *etabar_cur = lf_etabar_rule(theta, &P.rule, consts);
+  const int has_rule = (model == ORC_LF || model == ORC_BB1);
+  if (model == ORC_LF) gl_rule_init(&P.rule, (int)consts[3], (int)consts[4]);
+  if (model == ORC_BB1) gl_rule_init(&P.rule, (int)consts[4], (int)consts[5]);
+  if (has_rule && *etabar_cur == 0.0)
+    *etabar_cur = (model == ORC_LF) ? lf_etabar_rule(theta, &P.rule, consts) : bb1_etabar_rule(theta, &P.rule, consts);
   marg_rule R;
   marg_rule_init(&R);
   double* lpn = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
@@ -846,7 +876,8 @@ int orc_marg_run(int model, int p, int64_t n, const double* y, const double* aux
         D = ks_val(&acc_sum);
         logalpha = D + (double)n * (c_theta(&P, th_prop) - c_theta(&P, theta)) + lpri_new - logprior(&P, theta);
         if (has_rule) {
-          eb_new = lf_etabar_rule(th_prop, &P.rule, consts);
+          eb_new = (model == ORC_LF) ? lf_etabar_rule(th_prop, &P.rule, consts)
+                                     : bb1_etabar_rule(th_prop, &P.rule, consts);
           logalpha -= (double)n * (log(eb_new) - log(*etabar_cur));
         }
       } else {

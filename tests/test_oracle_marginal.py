@@ -12,6 +12,8 @@ over the latents, Sec. 6), no GPU needed.
   of (mu, ln tau) (one-dimensional quadrature, mu integrated analytically) within 4 MCSE.
 - LF: the marginal chain and the member-by-member MWG chain target the same posterior: their
   theta means agree within 4 combined MCSE.
+- BB1 (the paper's model, sigma(F) in the likelihood, no truncation): the rule against
+  QUADPACK, and the marginal chain against the MWG chain, as for LF.
 """
 import math
 
@@ -97,6 +99,58 @@ def test_lf_marginal_chain_agrees_with_mwg_chain():
     mc = oracle.MarginalChain(oracle.LF, data.fhat, data.r, consts, theta0, scale, 21)
     ra, _ = mc.run(1000, 9000)
     ch = oracle.Chain(oracle.LF, data.fhat, data.r, consts, theta0, scale, 22, synth.lf_chi_init(data, theta0))
+    rb, _ = ch.run(2000, 30000)
+    for j in range(3):
+        a, b = ra[:, j], rb[:, j]
+        se = math.hypot(stats.mcse(a), stats.mcse(b))
+        assert abs(a.mean() - b.mean()) < 4 * se, (j, a.mean(), b.mean(), se)
+
+
+def _bb1_ref(fhat, r, consts, th):
+    s0, al = consts[0], consts[1]
+    q = 1.0 / (4 * math.pi * r * r)
+    b, lnl, lnu = th
+
+    def logint(x):
+        L = math.exp(x)
+        F = L * q
+        s2 = s0 * s0 + (al * F) ** 2
+        z = L / math.exp(lnl)
+        lg = math.log(-math.expm1(-z)) if z <= math.log(2.0) else math.log1p(-math.exp(-z))
+        return -0.5 * math.log(s2) - (fhat - F) ** 2 / (2 * s2) + lg + b * (x - lnu) - L / math.exp(lnu) + x
+
+    lo = lnl + consts[7]
+    hi = math.log((fhat + 60 * math.sqrt(s0 * s0 + (al * fhat) ** 2)) / q)
+    grid = np.linspace(lo, hi, 20001)
+    m = max(logint(x) for x in grid)
+    pk = math.log(fhat / q)
+    v, _ = integrate.quad(lambda x: math.exp(logint(x) - m), lo, hi, points=[pk] if lo < pk < hi else None,
+                          epsabs=0, epsrel=2e-14, limit=500)
+    return m + math.log(v)
+
+
+def test_bb1_member_integral_vs_adaptive_quadrature():
+    """The paper's BB1 model (flux-dependent error sigma(F), no truncation): the rule against
+    QUADPACK over [ln l + ln(lower/l), ln((Fhat + 60 sigma(Fhat))/q)], faint and bright members."""
+    data = synth.bb1_data(3000, seed=22)
+    th0, _, consts = synth.bb1_settings(data, nL=16, nr=16)
+    order = np.argsort(data.fhat)
+    pick = np.concatenate([order[:6], order[-6:], np.random.default_rng(1).choice(data.fhat.size, 16, replace=False)])
+    for dth in ((0.0, 0.0, 0.0), (0.1, 0.3, -0.2), (-0.3, -0.5, 0.4)):
+        th = th0 + np.array(dth)
+        lp = oracle.marg_logp(oracle.BB1, data.fhat[pick], data.r[pick], consts, th)
+        for k, i in enumerate(pick):
+            ref = _bb1_ref(data.fhat[i], data.r[i], consts, th)
+            assert abs(lp[k] - ref) < 5e-12 * max(1.0, abs(ref)), (i, lp[k], ref)
+
+
+@pytest.mark.slow
+def test_bb1_marginal_chain_agrees_with_mwg_chain():
+    data = synth.bb1_data(200, seed=315)
+    theta0, scale, consts = synth.bb1_settings(data, nL=64, nr=64)
+    mc = oracle.MarginalChain(oracle.BB1, data.fhat, data.r, consts, theta0, scale, 23)
+    ra, _ = mc.run(1000, 6000)
+    ch = oracle.Chain(oracle.BB1, data.fhat, data.r, consts, theta0, scale, 24, synth.bb1_chi_init(data))
     rb, _ = ch.run(2000, 30000)
     for j in range(3):
         a, b = ra[:, j], rb[:, j]
