@@ -133,7 +133,7 @@ typedef struct {
   int32_t debug_skip_barrier_cta;/* >= 0: that block never arrives at the grid barrier (tests the
                                     timeout path); -1 = off */
   int32_t marginal;              /* 1: integrate each member's latent out by cubature and run the
-                                    chain on theta alone (NN1, LF; see cudahm_eval_marginal) */
+                                    chain on theta alone (NN1, LF, BB1; see cudahm_eval_marginal) */
 } cudahm_config;
 
 typedef struct {
@@ -209,19 +209,22 @@ int cudahm_ess(const double* x_host, int64_t rows, int32_t cols, double* ess_out
 int cudahm_eval_logdens(cudahm_t h, const double* theta_host, double* lp_host);
 
 /* Marginal form (Sec. 6: for low-dimensional latents the members can be integrated out by
- * quadrature, leaving a Markov chain over theta alone). For NN1 and LF handles, writes
+ * quadrature, leaving a Markov chain over theta alone). For NN1, LF and BB1 handles, writes
  * lp_host[i] = log int l_i(chi) f(chi;theta) dchi (N doubles, host) at the given theta (p
  * doubles, host), with l_i and f as in the member form (no theta-only term). The rule is fixed:
  * NN1, a 64-node Gauss-Legendre panel on the integrand's mean +- 10 sd; LF, with
  * F_b = Fhat_i + 10 sigma_F and F_c = max(Fhat_i - 10 sigma_F, Fhat_i/2), a 64-node panel in chi
- * over [max(ln L_low, ln(F_c/q_i)), ln(F_b/q_i)] and a 32-node panel over [ln L_low, ln(F_c/q_i)]
- * when that is not empty; -inf when ln L_low >= ln(F_b/q_i). A handle created with marginal = 1
+ * over [max(ln L_low, ln(F_c/q_i)), ln(F_b/q_i)] and, for a faint member (F_c = Fhat_i/2), a
+ * 32-node panel over [ln L_low, ln(F_c/q_i)] when that is not empty; -inf when
+ * ln L_low >= ln(F_b/q_i). BB1: the same with sigma(F), F_b solving F_b - Fhat_i = 10 sigma(F_b)
+ * (alpha < 1/10, else CUDAHM_EUNSUPPORTED), F_c = max(Fhat_i - 10 sigma(Fhat_i), Fhat_i/2), the
+ * lower end ln l + consts[7] and a 128-node tail panel. A handle created with marginal = 1
  * runs cudahm_run as a theta-only chain on prod_i p_i(theta) e^{N c(theta)} pi(theta) (LF:
  * divided by etabar(theta)^N): the member form's theta proposal, RAM adaptation, draws and
  * accept rule, with D = sum_i [log p_i(theta') - log p_i(theta)] summed exactly. Such a handle
  * has no latents (set_chi and get_chi give CUDAHM_EUNSUPPORTED), needs Fhat_i > 0 for LF
  * (CUDAHM_EINVAL at set_data) and runs alone (not in batch_run or the server). Other models:
- * CUDAHM_EUNSUPPORTED. FP32 handles (LF): each node's log integrand, relative to a binary64
+ * CUDAHM_EUNSUPPORTED. FP32 handles (LF; BB1 has the FP64 form only): each node's log integrand, relative to a binary64
  * reference at the likelihood peak clamped into the window, and the panel sums are binary32
  * (log p_i within ~1e-6 of the binary64 rule); the window, the reference, log p_i, the exact
  * sum over members, the selection integral and the theta step stay binary64. NN1 has no

@@ -118,9 +118,10 @@ constexpr double kHDelta = 0.125;
 // the likelihood window +- kMargK standard deviations.
 constexpr int kMargPeak = 64;
 constexpr int kMargTail = 32;
+constexpr int kMargTailBB1 = 128;
 constexpr double kMargK = 10.0;
-constexpr int kMargNodeWords = 2 * (kMargPeak + kMargTail);
-constexpr int kMarg32Words = 5;  // ln(Fhat/q), Fhat/q, ln(F_b/q), ln(F_c/q), Fhat^2/(2 sigma_F^2)
+constexpr int kMargNodeWords = 2 * (kMargPeak + kMargTail + kMargTailBB1);
+constexpr int kMarg32Words = 6;  // ln(Fhat/q), Fhat/q, ln(F_b/q), ln(F_c/q), Fhat^2/(2 sigma_F^2), faint (1/0)
 
 // Progress of one population through a batched run (device memory, updated by the kernel).
 struct BatchProg {

@@ -3,8 +3,10 @@
 //   log p_i(theta) = log int l_i(chi) f(chi;theta) dchi,
 // by fixed Gauss-Legendre panels in chi (NN1: one 64-node panel on the integrand's mean
 // +- 10 sd; LF: a 64-node panel over the likelihood window [max(ln L_low, ln(F_c/q_i)),
-// ln(F_b/q_i)], F_b = Fhat_i + 10 sigma_F, F_c = max(Fhat_i - 10 sigma_F, Fhat_i/2), and a
-// 32-node panel over [ln L_low, ln(F_c/q_i)] when that is not empty). The theta step is the
+// ln(F_b/q_i)], F_b = Fhat_i + 10 sigma_F, F_c = max(Fhat_i - 10 sigma_F, Fhat_i/2), and, for a
+// faint member (F_c = Fhat_i/2), a 32-node panel over [ln L_low, ln(F_c/q_i)] when that is not
+// empty; BB1: the same with sigma(F), F_b - Fhat_i = 10 sigma(F_b), the lower end ln l +
+// ln(lower/l) and a 128-node tail panel). The theta step is the
 // member form's (Sec. 2.2, last paragraph) with D = sum_i [log p_i(theta') - log p_i(theta)]:
 // one persistent cooperative launch per chunk of steps, each block integrating a contiguous
 // range of members (and its share of the selection rule's outer nodes for LF), an exact
@@ -33,8 +35,10 @@ __device__ double marg_logp(double y, double aux, const ThetaC& tc, const ModelC
                             const double* nd) {
   const double* xp = nd;
   const double* wp = nd + kMargPeak;
-  const double* xt = nd + 2 * kMargPeak;
-  const double* wt = nd + 2 * kMargPeak + kMargTail;
+  constexpr bool bb1 = std::is_same<M, BB1>::value;
+  constexpr int nt = bb1 ? kMargTailBB1 : kMargTail;
+  const double* xt = nd + 2 * kMargPeak + (bb1 ? 2 * kMargTail : 0);
+  const double* wt = xt + nt;
   if constexpr (std::is_same<M, NN1>::value) {
     // aux = 1/sigma^2, tc.a1 = 1/(2 tau^2): precision of the Gaussian integrand aux + 2 a1
     const double prec = __dadd_rn(aux, __dmul_rn(2.0, tc.a1));
@@ -50,35 +54,45 @@ __device__ double marg_logp(double y, double aux, const ThetaC& tc, const ModelC
     }
     return __dadd_rn(m0, log_tab(__dmul_rn(h, s), T));
   } else {
-    // LF: y = Fhat_i, aux = q_i; tc.a3 = ln L_low
-    const double Fb = __fma_rn(kMargK, mc.sigF, y);
-    const double Fc = fmax(__fma_rn(-kMargK, mc.sigF, y), __dmul_rn(0.5, y));
+    // LF, BB1: y = Fhat_i, aux = q_i; the lower end tc.a3 = ln L_low (LF), tc.a4 + ln(lower/l) (BB1)
+    double Fb, Fc0;
+    if constexpr (bb1) {
+      const double den = 1.0 - kMargK * kMargK * mc.alpha * mc.alpha;
+      const double ay = mc.alpha * y;
+      Fb = (y + kMargK * sqrt(fma(ay, ay, den * mc.s0sq))) / den;
+      Fc0 = y - kMargK * sqrt(fma(ay, ay, mc.s0sq));
+    } else {
+      Fb = __fma_rn(kMargK, mc.sigF, y);
+      Fc0 = __fma_rn(-kMargK, mc.sigF, y);
+    }
+    const bool faint = Fc0 < __dmul_rn(0.5, y);
+    const double Fc = faint ? __dmul_rn(0.5, y) : Fc0;
     const double chib = log_tab(__ddiv_rn(Fb, aux), T);
     const double chic = log_tab(__ddiv_rn(Fc, aux), T);
-    const double lo = tc.a3;
+    const double lo = bb1 ? tc.a4 + mc.ln_lower : tc.a3;
     const double a2 = fmax(chic, lo);
     if (!(a2 < chib)) return -INFINITY;
     const double cref = fmin(fmax(log_tab(__ddiv_rn(y, aux), T), a2), chib);
     const double eref = exp_tab(cref, T);
-    const double m0 = __dadd_rn(LF::loglike(cref, eref, y, aux, mc), LF::logf(cref, eref, tc));
+    const double m0 = __dadd_rn(M::loglike(cref, eref, y, aux, mc), M::logf(cref, eref, tc));
     const double c2 = __dmul_rn(0.5, __dadd_rn(a2, chib)), h2 = __dmul_rn(0.5, __dsub_rn(chib, a2));
     double s2 = 0.0;
 #pragma unroll 4
     for (int j = 0; j < kMargPeak; ++j) {
       const double chi = __fma_rn(h2, xp[j], c2);
       const double e = exp_tab(chi, T);
-      const double v = __dadd_rn(LF::loglike(chi, e, y, aux, mc), LF::logf(chi, e, tc));
+      const double v = __dadd_rn(M::loglike(chi, e, y, aux, mc), M::logf(chi, e, tc));
       s2 = __fma_rn(wp[j], exp_tab(__dsub_rn(v, m0), T), s2);
     }
     double s = __dmul_rn(h2, s2);
-    if (lo < chic) {
+    if (faint && lo < chic) {
       const double c1 = __dmul_rn(0.5, __dadd_rn(lo, chic)), h1 = __dmul_rn(0.5, __dsub_rn(chic, lo));
       double s1 = 0.0;
 #pragma unroll 4
-      for (int j = 0; j < kMargTail; ++j) {
+      for (int j = 0; j < nt; ++j) {
         const double chi = __fma_rn(h1, xt[j], c1);
         const double e = exp_tab(chi, T);
-        const double v = __dadd_rn(LF::loglike(chi, e, y, aux, mc), LF::logf(chi, e, tc));
+        const double v = __dadd_rn(M::loglike(chi, e, y, aux, mc), M::logf(chi, e, tc));
         s1 = __fma_rn(wt[j], exp_tab(__dsub_rn(v, m0), T), s1);
       }
       s = __fma_rn(h1, s1, s);
@@ -101,6 +115,7 @@ __device__ double marg_logp32_lf(long long i, long long n, const double* __restr
                                  const double* T, const float* nd) {
   const double chis = __ldg(md + i), Lhat = __ldg(md + n + i), chib = __ldg(md + 2 * n + i),
                chic = __ldg(md + 3 * n + i), A = __ldg(md + 4 * n + i);
+  const bool faint = __ldg(md + 5 * n + i) != 0.0;
   const double lo = tc.a3;
   const double a2 = fmax(chic, lo);
   if (!(a2 < chib)) return -INFINITY;
@@ -120,7 +135,7 @@ __device__ double marg_logp32_lf(long long i, long long n, const double* __restr
   const float* xp = nd;
   const float* wp = nd + kMargPeak;
   const float* xt = nd + 2 * kMargPeak;
-  const float* wt = nd + 2 * kMargPeak + kMargTail;
+  const float* wt = xt + kMargTail;
   const double c2 = 0.5 * (a2 + chib), h2 = 0.5 * (chib - a2);
   const float cf2 = static_cast<float>(c2 - cref), hf2 = static_cast<float>(h2);
   float s2 = 0.0f, k2 = 0.0f;
@@ -135,7 +150,7 @@ __device__ double marg_logp32_lf(long long i, long long n, const double* __restr
     s2 = t;
   }
   double s = h2 * static_cast<double>(s2);
-  if (lo < chic) {
+  if (faint && lo < chic) {
     const double c1 = 0.5 * (lo + chic), h1 = 0.5 * (chic - lo);
     const float cf1 = static_cast<float>(c1 - cref), hf1 = static_cast<float>(h1);
     float s1 = 0.0f, k1 = 0.0f;
@@ -158,7 +173,7 @@ __device__ double marg_logp32_lf(long long i, long long n, const double* __restr
 template <class M, bool F32>
 __device__ __forceinline__ double marg_member(const SweepArgs& a, long long i, const ThetaC& tc, const double* T,
                                               const double* nd, const float* nd32) {
-  if constexpr (F32 && M::kRule) return marg_logp32_lf(i, a.n, a.marg_d32, tc, T, nd32);
+  if constexpr (F32 && std::is_same<M, LF>::value) return marg_logp32_lf(i, a.n, a.marg_d32, tc, T, nd32);
   else return marg_logp<M>(__ldg(a.y + i), __ldg(a.aux + i), tc, a.mc, T, nd);
 }
 
@@ -372,7 +387,7 @@ __global__ void marg_eval_kernel(long long n, const double* y, const double* aux
   __syncthreads();
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  if constexpr (F32 && M::kRule) out[i] = marg_logp32_lf(i, n, md32, s_tc, s_math, s_nodes32);
+  if constexpr (F32 && std::is_same<M, LF>::value) out[i] = marg_logp32_lf(i, n, md32, s_tc, s_math, s_nodes32);
   else out[i] = marg_logp<M>(y[i], aux[i], s_tc, mc, s_math, s_nodes);
 }
 
@@ -387,12 +402,15 @@ __global__ void marg_data32_kernel(long long n, const double* y, const double* a
   if (i >= n) return;
   const double F = y[i], q = aux[i];
   const double Fb = __fma_rn(kMargK, mc.sigF, F);
-  const double Fc = fmax(__fma_rn(-kMargK, mc.sigF, F), __dmul_rn(0.5, F));
+  const double Fc0 = __fma_rn(-kMargK, mc.sigF, F);
+  const bool faint = Fc0 < __dmul_rn(0.5, F);
+  const double Fc = faint ? __dmul_rn(0.5, F) : Fc0;
   md[i] = log_tab(__ddiv_rn(F, q), s_math);
   md[n + i] = F / q;
   md[2 * n + i] = log_tab(__ddiv_rn(Fb, q), s_math);
   md[3 * n + i] = log_tab(__ddiv_rn(Fc, q), s_math);
   md[4 * n + i] = F * F * mc.inv2sig2;
+  md[5 * n + i] = faint ? 1.0 : 0.0;
 }
 
 size_t marg_smem() { return sizeof(double) * (kMathWords + kMargNodeWords) + sizeof(float) * kMargNodeWords; }
@@ -404,6 +422,7 @@ size_t marg_smem_bytes(int, int) { return marg_smem(); }
 static const void* marg_fn(int model, bool f32) {
   if (model == CUDAHM_LF)
     return f32 ? reinterpret_cast<const void*>(&marg_kernel<LF, true>) : reinterpret_cast<const void*>(&marg_kernel<LF, false>);
+  if (model == CUDAHM_BB1) return reinterpret_cast<const void*>(&marg_kernel<BB1, false>);  // FP64 only
   return reinterpret_cast<const void*>(&marg_kernel<NN1, false>);  // NN1: binary64 in both forms
 }
 
@@ -430,6 +449,8 @@ cudaError_t launch_marg_eval(int model, bool f32, long long n, const double* y, 
     marg_eval_kernel<LF, true><<<grid, blk, 0, st>>>(n, y, aux, theta_dev, mc, math_tab, nodes, md32, out);
   else if (model == CUDAHM_LF)
     marg_eval_kernel<LF, false><<<grid, blk, 0, st>>>(n, y, aux, theta_dev, mc, math_tab, nodes, md32, out);
+  else if (model == CUDAHM_BB1)
+    marg_eval_kernel<BB1, false><<<grid, blk, 0, st>>>(n, y, aux, theta_dev, mc, math_tab, nodes, md32, out);
   else if (model == CUDAHM_NN1)
     marg_eval_kernel<NN1, false><<<grid, blk, 0, st>>>(n, y, aux, theta_dev, mc, math_tab, nodes, md32, out);
   else
@@ -444,11 +465,14 @@ cudaError_t launch_marg_data32(long long n, const double* y, const double* aux, 
   return cudaGetLastError();
 }
 
-// Nodes and weights of the two panels on [-1, 1]: xp[64], wp[64], xt[32], wt[32].
+// Nodes and weights of the panels on [-1, 1]: xp[64], wp[64], xt[32], wt[32], xb[128], wb[128].
 cudaError_t launch_marg_nodes(double* nodes, cudaStream_t st) {
   cudaError_t e = launch_gauss_legendre(kMargPeak, nodes, nodes + kMargPeak, st);
   if (e != cudaSuccess) return e;
-  return launch_gauss_legendre(kMargTail, nodes + 2 * kMargPeak, nodes + 2 * kMargPeak + kMargTail, st);
+  double* t = nodes + 2 * kMargPeak;
+  e = launch_gauss_legendre(kMargTail, t, t + kMargTail, st);
+  if (e != cudaSuccess) return e;
+  return launch_gauss_legendre(kMargTailBB1, t + 2 * kMargTail, t + 2 * kMargTail + kMargTailBB1, st);
 }
 
 }  // namespace chm

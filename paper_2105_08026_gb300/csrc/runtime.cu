@@ -256,8 +256,10 @@ int validate(const cudahm_config* c) {
   }
   if (c->marginal != 0 && c->marginal != 1) return fail(CUDAHM_EINVAL, "marginal must be 0 or 1");
   if (c->marginal) {
-    if (c->model != CUDAHM_NN1 && c->model != CUDAHM_LF)
-      return fail(CUDAHM_EUNSUPPORTED, "the marginal form integrates one-dimensional latents (NN1, LF)");
+    if (c->model != CUDAHM_NN1 && c->model != CUDAHM_LF && c->model != CUDAHM_BB1)
+      return fail(CUDAHM_EUNSUPPORTED, "the marginal form integrates one-dimensional latents (NN1, LF, BB1)");
+    if (c->model == CUDAHM_BB1 && !(k[1] * kMargK < 1.0))
+      return fail(CUDAHM_EUNSUPPORTED, "the BB1 marginal window needs alpha < 1/10");
   }
   return CUDAHM_OK;
 }
@@ -683,7 +685,7 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
   }
   if (launch_math_table(h->math_tab, h->stream) != cudaSuccess)
     return bail(fail(CUDAHM_ECUDA, "exp/log table set-up failed: %s", cudaGetErrorString(cudaGetLastError())));
-  if (cfg->model == CUDAHM_NN1 || cfg->model == CUDAHM_LF) {  // the cubature rule (marginal form, eval_marginal)
+  if (cfg->model == CUDAHM_NN1 || cfg->model == CUDAHM_LF || cfg->model == CUDAHM_BB1) {  // the cubature rule
     if ((rc = alloc_into(h, &h->marg_nodes, kMargNodeWords))) return bail(rc);
     if (cfg->marginal && (rc = alloc_into(h, &h->marg_lp, 2ull * n))) return bail(rc);
     if (launch_marg_nodes(h->marg_nodes, h->stream) != cudaSuccess)
@@ -934,8 +936,10 @@ int cudahm_get_stats(cudahm_t h, cudahm_stats* s) {
 
 int cudahm_eval_marginal(cudahm_t h, const double* theta_host, double* lp_host) {
   if (!h || !theta_host || !lp_host) return fail(CUDAHM_EINVAL, "NULL argument");
-  if (h->cfg.model != CUDAHM_NN1 && h->cfg.model != CUDAHM_LF)
-    return fail(CUDAHM_EUNSUPPORTED, "the cubature rule integrates one-dimensional latents (NN1, LF)");
+  if (h->cfg.model != CUDAHM_NN1 && h->cfg.model != CUDAHM_LF && h->cfg.model != CUDAHM_BB1)
+    return fail(CUDAHM_EUNSUPPORTED, "the cubature rule integrates one-dimensional latents (NN1, LF, BB1)");
+  if (h->cfg.model == CUDAHM_BB1 && !(h->mc.alpha * kMargK < 1.0))
+    return fail(CUDAHM_EUNSUPPORTED, "the BB1 marginal window needs alpha < 1/10");
   if (!h->data_set) return fail(CUDAHM_ESTATE, "eval before set_data");
   CU(cudaSetDevice(h->cfg.device));
   double* out = nullptr;
