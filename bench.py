@@ -346,7 +346,22 @@ def run_bb1(args, cudahm, stream, device, flush, peak_fp64):
     ms = e0.elapsed_time(e1)
     st = s.stats()
     s.close()
+    # the same data in the marginal form (latents integrated out by cubature, FP64)
+    m = cudahm.Sampler(cudahm.BB1, n, theta_init=theta0, theta_prop_scale=scale, model_consts=consts, seed=5,
+                       device=device, stream=stream.cuda_stream, use_torch_allocator=True, marginal=True)
+    cudahm.cudahm_set_data_device(m.h, y_dev.data_ptr(), r_dev.data_ptr(), n)
+    m.run(20, 0)
+    Km = 100
+    torch.cuda.synchronize()
+    e0.record(stream)
+    m.run(0, Km, 1)
+    e1.record(stream)
+    e1.synchronize()
+    mms = e0.elapsed_time(e1)
+    m.close()
+    marg = {"ms_per_step": mms / Km, "member_integrals_per_s": n * Km / (mms * 1e-3), "steps": Km, "dtype": "f64"}
     return {"value": n * K / (ms * 1e-3), "unit": "object-updates/s", "ms_per_step": ms / K, "n": n, "steps": K,
+            "marginal": marg,
             "theta_mean": rows.mean(axis=0).tolist(), "theta_true": theta0.tolist(),
             "launch_shape": [st.grid_blocks, st.block_threads, st.objects_per_thread],
             "workload": "BB1 luminosity function (paper Sec. 5), N=1e5, FP64, 1024x1024 rule with sigma(F)",
