@@ -61,7 +61,7 @@ MVN3_F32_DRAM_BYTES_PER_UPDATE = 127.6
 # FP64 work of one member integral of the marginal form on the LF workload (96 nodes, with the
 # step's share of the selection rule), from ncu's smsp__sass_thread_inst_executed_op_d{fma,add,mul}
 # counters on marg_kernel<LF> (profiles/marg_kernel_lf_n300000.md): 2 DFMA + DADD + DMUL.
-MARG_FP64_FLOP_PER_MEMBER = 5045.0
+MARG_FP64_FLOP_PER_MEMBER = 4483.0
 
 
 def parse():
