@@ -286,7 +286,7 @@ int choose_shape(cudahm* h) {
       int grid = lf ? bps * h->sms
                     : static_cast<int>(std::min<long long>(static_cast<long long>(bps) * h->sms,
                                                            (n + block - 1) / block));
-      const int mgrid = (!f32 && grid > 1) ? grid - 1 : grid;  // FP64: block 0 holds no members
+      const int mgrid = (grid > 1) ? grid - 1 : grid;  // block 0 holds no members
       const long long mpb = (n + mgrid - 1) / mgrid;           // members of the largest block
       if ((mpb + block - 1) / block > K) break;     // needs a larger K
       const int rows = lf ? static_cast<int>((G + grid - 1) / grid) : 1;

@@ -110,10 +110,10 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   const int lane = tid & 31, wid = tid >> 5;
   const int ctrl_warp = (blockDim.x >> 5) - 1;  // the warp that runs the deferred theta work
   const int p = a.p;
-  // members of this block: the contiguous range [nb0, nb1), equal sizes to within one
-  // In the FP64 form block 0 (which makes the grid's theta proposal on its serial path) holds no
-  // members, so that its FP64 unit is not shared with member work; the other blocks split them.
-  const unsigned int mb0 = (!F32 && gridDim.x > 1) ? 1u : 0u;
+  // members of this block: the contiguous range [nb0, nb1), equal sizes to within one.
+  // Block 0 (which makes the grid's theta proposal on its serial path) holds no members, so that
+  // its FP64 unit is not shared with member work; the other blocks split them.
+  const unsigned int mb0 = (gridDim.x > 1) ? 1u : 0u;
   const unsigned int mgrid = gridDim.x - mb0, mblk = blockIdx.x - mb0;
   const bool leader_only = (mb0 == 1u && blockIdx.x == 0);
   const unsigned int nb0 = leader_only ? 0u : static_cast<unsigned int>((a.n * mblk) / mgrid);
@@ -151,16 +151,14 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     s_logalpha_prev = 0.0;
     s_fail = 0;
     s_tcf = M::consts32(s_tc);
-    // theta' of the first sweep: FP64 form, proposed by block 0 and fetched by the others;
-    // FP32 form (short member phase, where the fetch would sit on the critical path), proposed
-    // by every block
+    // theta' of the first sweep: proposed by block 0 and fetched by the others
     double lp = -INFINITY;
     ThetaC tcp{};
     ThetaCf tcpf{};
-    if (F32 || blockIdx.x == 0) {
+    if (blockIdx.x == 0) {
       propose_theta<M>(a, 0, p, s_theta, s_Sth, s_thp, lp, tcp, s_math);
       tcpf = M::consts32(tcp);
-      if (!F32) publish_theta(a, 1u, s_thp, p, lp, tcp, tcpf);
+      publish_theta(a, 1u, s_thp, p, lp, tcp, tcpf);
     } else if (!fetch_theta(a, 1u, s_thp, p, lp, tcp, tcpf)) {
       s_fail = 1;
     }
@@ -220,12 +218,12 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     // deferred theta work of the previous sweep and the proposal of this one (last warp)
     if (s > 0 && wid == ctrl_warp) {
       if (lane == 0) {
-        // FP64 form: one proposal (and one RAM update of S_theta) per sweep for the grid, made
-        // and published by block 0, fetched by the other blocks; FP32 form: every block
+        // one proposal (and one RAM update of S_theta) per sweep for the grid, made and published
+        // by block 0, fetched by the other blocks (whose FP64 units are then left to the members)
         double lp = -INFINITY;
         ThetaC tcp{};
         ThetaCf tcpf{};
-        if (F32 || blockIdx.x == 0) {
+        if (blockIdx.x == 0) {
           if (s_pending_ram) {
             const double lal = s_logalpha_prev;
             const double alpha = (lal >= 0.0) ? 1.0 : exp_tab(lal, s_math);
@@ -233,7 +231,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
           }
           propose_theta<M>(a, s, p, s_theta, s_Sth, s_thp, lp, tcp, s_math);
           tcpf = M::consts32(tcp);
-          if (!F32) publish_theta(a, static_cast<unsigned int>(s + 1), s_thp, p, lp, tcp, tcpf);
+          publish_theta(a, static_cast<unsigned int>(s + 1), s_thp, p, lp, tcp, tcpf);
         } else if (!fetch_theta(a, static_cast<unsigned int>(s + 1), s_thp, p, lp, tcp, tcpf)) {
           lp = -INFINITY;  // the run has failed; the next barrier returns
         }
