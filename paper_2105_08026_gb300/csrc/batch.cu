@@ -182,13 +182,14 @@ __device__ __forceinline__ void member_f32(const SweepArgs& a, unsigned int i, u
 // (structure of arrays, component j of member i at j n + i; the RAM factor as six packed rows).
 // Draws as the oracle defines them: component c of U from the Box-Muller pair of Philox block
 // (c, stream 0, i, odd sweep) (cosine for the odd sweep, sine for the next), the accept
-// uniform from block (3, 0, i, k).
+// uniform from block (3, 0, i, k). The odd sweep keeps the three sines in a.spare3 for the next
+// sweep; a launch that starts on an even sweep (first) recomputes them.
 template <class M>
 __device__ __forceinline__ void member3_f64(const SweepArgs& a, unsigned int i, uint32_t k, double eta,
                                             const ThetaC3& tc, const ThetaC3& tcp, bool prior_ok,
                                             const double* s_math, Xacc& xd, XFlags& fd, unsigned int& neg_big,
                                             unsigned int& pos_big, unsigned int& nan_cnt, unsigned int& acc_cnt,
-                                            long long tro) {
+                                            long long tro, bool first) {
   const size_t n = static_cast<size_t>(a.n);
   double x[3], y[3], w[3], S[6];
 #pragma unroll
@@ -202,14 +203,20 @@ __device__ __forceinline__ void member3_f64(const SweepArgs& a, unsigned int i, 
   const bool odd = (k & 1u) != 0u;
   const uint32_t ko = odd ? k : k - 1u;
   double z[3];
+  if (odd || first) {
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const uint4 b = philox4x32_10(make_uint4(static_cast<uint32_t>(c), 0u, i, ko), a.key0, a.key1);
-    const double ua = uniform53(b.x, b.y), ub = uniform53(b.z, b.w);
-    const double rad = sqrt(-2.0 * log_tab(ua, s_math));
-    double sn, cs;
-    sincospi_tab(2.0 * ub, s_math, &sn, &cs);
-    z[c] = odd ? rad * cs : rad * sn;
+    for (int c = 0; c < 3; ++c) {
+      const uint4 b = philox4x32_10(make_uint4(static_cast<uint32_t>(c), 0u, i, ko), a.key0, a.key1);
+      const double ua = uniform53(b.x, b.y), ub = uniform53(b.z, b.w);
+      const double rad = sqrt(-2.0 * log_tab(ua, s_math));
+      double sn, cs;
+      sincospi_tab(2.0 * ub, s_math, &sn, &cs);
+      z[c] = odd ? rad * cs : rad * sn;
+      if (odd) a.spare3[c * n + i] = rad * sn;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) z[c] = a.spare3[c * n + i];
   }
   const uint4 bu = philox4x32_10(make_uint4(3u, 0u, i, k), a.key0, a.key1);
   const double u = uniform53(bu.x, bu.y);
@@ -401,7 +408,7 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
       } else {
         for (unsigned int i = nb0 + tid; i < nb1; i += blockDim.x)
           member3_f64<M>(a, i, k, eta, s_tc, s_tcp, prior_ok, s_math, xd, fd, neg_big, pos_big, member_nan,
-                         member_acc, tro);
+                         member_acc, tro, s == 0);
       }
     } else if constexpr (F32) {
       const TCf tf = s_tcf, tpf = s_tcpf;

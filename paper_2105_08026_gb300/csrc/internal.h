@@ -99,6 +99,7 @@ struct SweepArgs {
   double* marg_lp;           // marginal form: log p_i at two thetas, [2][n]
   const double* marg_nodes;  // marginal form: panel nodes and weights (kMargNodeWords)
   const double* marg_d32;    // marginal form, FP32 bulk, LF: per-member window data, [kMarg32Words][n]
+  double* spare3;            // d = 3, FP64: the sine halves of the odd sweep's Box-Muller pairs, [3][n]
   // the rule's inner sum H(ln L) tabulated (h_ncell cells of kHDeg + 1 Chebyshev coefficients);
   // nullptr: evaluate the rule pair by pair
   const double* htab;

@@ -132,6 +132,7 @@ struct cudahm {
   double* marg_lp = nullptr;     // [2][n] log p_i at the current theta and at the proposal
   double* marg_nodes = nullptr;  // panel nodes and weights
   double* marg_d32 = nullptr;    // FP32 form, LF: per-member window data
+  double* spare3 = nullptr;      // d = 3, FP64: the odd sweep's Box-Muller sines, [3][n]
   int mgrid = 0, mrows_smem = 1;
   bool marg_valid = false;       // marg_lp[mcur] holds log p_i at the chain's theta
   // the rule's inner sum H(ln L), tabulated (LF, BB1)
@@ -381,6 +382,7 @@ SweepArgs base_args(cudahm* h) {
   a.marg_lp = h->marg_lp;
   a.marg_nodes = h->marg_nodes;
   a.marg_d32 = h->marg_d32;
+  a.spare3 = h->spare3;
   a.htab = h->htab;
   a.h_ua = h->h_ua;
   a.h_ub = h->h_ub;
@@ -685,6 +687,7 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
   }
   if (launch_math_table(h->math_tab, h->stream) != cudaSuccess)
     return bail(fail(CUDAHM_ECUDA, "exp/log table set-up failed: %s", cudaGetErrorString(cudaGetLastError())));
+  if (h->d == 3 && cfg->precision == CUDAHM_FP64 && (rc = alloc_into(h, &h->spare3, 3ull * n))) return bail(rc);
   if (cfg->model == CUDAHM_NN1 || cfg->model == CUDAHM_LF || cfg->model == CUDAHM_BB1) {  // the cubature rule
     if ((rc = alloc_into(h, &h->marg_nodes, kMargNodeWords))) return bail(rc);
     if (cfg->marginal && (rc = alloc_into(h, &h->marg_lp, 2ull * n))) return bail(rc);
@@ -1501,7 +1504,9 @@ size_t request_bytes(const cudahm_config& c, long long n_iter, long long thin) {
   size_t b = n * (4 * 8 + d * 8 + d * d * 8) + (c.precision == CUDAHM_FP32 ? n * 5 * 4 : 0);
   b += static_cast<size_t>(n_iter / std::max<long long>(thin, 1)) * p * 8;
   b += static_cast<size_t>(kChunk) * (p + 3) * 8 + 64 * 1024;
-  if (has_rule(c.model)) b += static_cast<size_t>(8 * 4096 + 2048) * 8;
+  if (has_rule(c.model)) b += static_cast<size_t>(8 * 4096 + 2048 + 1024 * (kHDeg + 1)) * 8;  // rule, H table
+  if (d == 3 && c.precision == CUDAHM_FP64) b += 3 * n * 8;  // Box-Muller spares
+  b += static_cast<size_t>(kMargNodeWords) * 8;
   return b;
 }
 
