@@ -212,6 +212,41 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
   return *reinterpret_cast<const volatile int*>(p);
 }
 
+// A grid-wide barrier in two halves, so that a block can work between its arrival and the
+// others': grid_arrive (all threads of the block; thread 0 publishes the block's writes and
+// counts it in) and grid_wait (all threads; thread 0 waits, bounded, until barrier `index` has
+// every block). grid_barrier below is the two back to back.
+__device__ __forceinline__ void grid_arrive(unsigned int* count, bool skip_arrival) {
+  __syncthreads();
+  if (threadIdx.x == 0 && !skip_arrival) {
+    __threadfence();
+    atomicAdd(count, 1u);
+  }
+}
+__device__ __forceinline__ bool grid_wait(unsigned int* count, unsigned int index, int* err, long long limit_ns) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned int target = (index + 1u) * gridDim.x;
+    const long long t0 = globaltimer_ns();
+    while (true) {
+      if (ld_acquire_u32(count) >= target) break;
+      if (ld_volatile_i32(err) != 0) { ok = 0; break; }
+      if (globaltimer_ns() - t0 > limit_ns) {
+        atomicCAS(err, 0, CUDAHM_ETIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    if (ld_volatile_i32(err) != 0) ok = 0;
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 // Grid-wide barrier number `index` (0-based) of this launch. The counter starts at 0 for
 // every launch. Returns false if the run has failed (timeout here or an error elsewhere);
 // the caller then leaves the kernel. Must be called by all threads of the block.

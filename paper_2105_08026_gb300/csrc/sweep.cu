@@ -92,6 +92,72 @@ cudaError_t launch_prefix_weights(int nr, const double* Wr, double* cw, cudaStre
 // theta' = theta + S_theta U, its prior and constants, the rule's outer-node values at theta')
 // runs on the last warp while every warp does its member steps; only the accept decision
 // itself sits between the grid barrier and the next member phase.
+// The theta-independent half of each member's step for sweep sa of this launch
+// (k = k0 + sa + 1): the draws, the proposal Y = chi + S z and its log-likelihood (with e^Y),
+// stored per member in shared memory (pY, peY, pll, pu). The kernel computes it while the
+// previous sweep's grid barrier completes; the theta-dependent half (log f, the accept, the RAM
+// update) follows the theta decision. Same operations as a whole step, so the same bits.
+template <class M, int K, bool F32, class R>
+__device__ __forceinline__ void sweep_part_a(const SweepArgs& a, long long sa, unsigned int nb0, unsigned int nb1,
+                                             const R (&chi)[K], const double (&S)[K], const double* s_math,
+                                             const double* s_y, const double* s_aux, double* s_zs,
+                                             const float* s_d32, double* s_pY, double* s_peY, double* s_pll,
+                                             double* s_pu) {
+  const uint32_t k = static_cast<uint32_t>(a.k0 + sa + 1);
+  const bool odd = (k & 1u) != 0u;
+#pragma unroll
+  for (int m = 0; m < K; ++m) {
+    const unsigned int i = nb0 + threadIdx.x + m * blockDim.x;
+    if (i < nb1) {
+      const unsigned int q = i - nb0;
+      if constexpr (F32) {
+        // Philox block (0, stream 2, member i, odd sweep k_o): a Box-Muller pair from 24-bit
+        // uniforms of words 0 and 1 (cosine for k_o, sine for k_o + 1), the accept uniforms of
+        // k_o (word 2) and k_o + 1 (word 3)
+        float d[M::kData32];
+#pragma unroll
+        for (int c = 0; c < M::kData32; ++c) d[c] = s_d32[c * a.mpb + q];
+        const uint4 w = philox4x32_10(make_uint4(0u, 2u, static_cast<uint32_t>(i), odd ? k : k - 1u), a.key0,
+                                      a.key1);
+        const float u1 = (static_cast<float>(w.x >> 8) + 0.5f) * 0x1p-24f;
+        const float u2 = (static_cast<float>(w.y >> 8) + 0.5f) * 0x1p-24f;
+        const float u = (static_cast<float>((odd ? w.z : w.w) >> 8) + 0.5f) * 0x1p-24f;
+        const float rad = sqrtf(-2.0f * logf(u1));
+        float sn, cs;
+        sincospif(2.0f * u2, &sn, &cs);
+        const float z = odd ? rad * cs : rad * sn;
+        const float Y = fmaf(static_cast<float>(S[m]), z, chi[m]);
+        s_pY[q] = static_cast<double>(Y);
+        s_pll[q] = static_cast<double>(M::loglike32(Y, d));
+        s_pu[q] = static_cast<double>(u);
+      } else {
+        // One Box-Muller pair serves the odd sweep (cosine) and the next even sweep (sine, kept
+        // in shared memory; recomputed if a launch starts on an even sweep)
+        double z;
+        if (odd || sa == 0) {
+          const uint4 w0 = philox4x32_10(make_uint4(0u, 0u, static_cast<uint32_t>(i), odd ? k : k - 1u), a.key0,
+                                         a.key1);
+          const double ua = uniform53(w0.x, w0.y), ub = uniform53(w0.z, w0.w);
+          const double rad = sqrt(-2.0 * log_tab(ua, s_math));
+          double sn, cs;
+          sincospi_tab(2.0 * ub, s_math, &sn, &cs);
+          z = odd ? rad * cs : rad * sn;
+          if (odd) s_zs[q] = rad * sn;
+        } else {
+          z = s_zs[q];
+        }
+        const uint4 w1 = philox4x32_10(make_uint4(1u, 0u, static_cast<uint32_t>(i), k), a.key0, a.key1);
+        const double Y = fma(S[m], z, chi[m]);
+        const double eY = M::kExp ? exp_tab(Y, s_math) : 0.0;
+        s_pY[q] = Y;
+        s_peY[q] = eY;
+        s_pll[q] = M::loglike(Y, eY, s_y[q], s_aux[q], a.mc);
+        s_pu[q] = uniform53(w1.x, w1.y);
+      }
+    }
+  }
+}
+
 template <class M, int K, bool F32>
 __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   using R = typename std::conditional<F32, float, double>::type;  // member arithmetic
@@ -128,6 +194,11 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   // theta' partial
   double* s_lf = s_y + 3 * a.mpb;
   float* s_lf32 = reinterpret_cast<float*>(s_lf);
+  // the theta-independent half of each member's next step (sweep_part_a)
+  double* s_pY = s_y + 4 * a.mpb;
+  double* s_peY = s_y + 5 * a.mpb;
+  double* s_pll = s_y + 6 * a.mpb;
+  double* s_pu = s_y + 7 * a.mpb;
   if (!F32) {
     for (unsigned int q = tid; q < nb1 - nb0; q += blockDim.x) {
       s_y[q] = a.y[nb0 + q];
@@ -207,9 +278,10 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   }
   unsigned int member_acc = 0;
   __syncthreads();
+  if (a.ns > 0)
+    sweep_part_a<M, K, F32>(a, 0, nb0, nb1, chi, S, s_math, s_y, s_aux, s_zs, s_d32, s_pY, s_peY, s_pll, s_pu);
 
   for (long long s = 0; s < a.ns; ++s) {
-    const uint32_t k = static_cast<uint32_t>(a.k0 + s + 1);
     const double eta = __ldg(a.tab_eta + s);
     const ThetaC tc = s_tc;
     const bool trace = (a.trace_off + s) < a.trace_T;
@@ -242,35 +314,21 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     }
 
     if constexpr (F32) {
-      // a1-a3 in binary32 (FP32 bulk form). Draws: Philox block (0, stream 2, member i, odd sweep
-      // k_o) gives a Box-Muller pair from 24-bit uniforms of words 0 and 1 (cosine for k_o, sine
-      // for k_o + 1) and the accept uniforms of k_o (word 2) and k_o + 1 (word 3). The RAM factor
-      // S stays binary64.
-      const bool oddf = (k & 1u) != 0u;
+      // a1-a3 in binary32 (FP32 bulk form), the theta-dependent half (the draws, Y and its
+      // likelihood come from sweep_part_a). The RAM factor S stays binary64.
       const ThetaCf tf = s_tcf;
 #pragma unroll
       for (int m = 0; m < K; ++m) {
         const unsigned int i = nb0 + tid + m * blockDim.x;
         if (i < nb1) {
-          float d[M::kData32];
-#pragma unroll
-          for (int c = 0; c < M::kData32; ++c) d[c] = s_d32[c * a.mpb + (i - nb0)];
-          const uint4 w = philox4x32_10(make_uint4(0u, 2u, static_cast<uint32_t>(i), oddf ? k : k - 1u), a.key0,
-                                        a.key1);
-          const float u1 = (static_cast<float>(w.x >> 8) + 0.5f) * 0x1p-24f;
-          const float u2 = (static_cast<float>(w.y >> 8) + 0.5f) * 0x1p-24f;
-          const float u = (static_cast<float>((oddf ? w.z : w.w) >> 8) + 0.5f) * 0x1p-24f;
-          const float rad = sqrtf(-2.0f * logf(u1));
-          float sn, cs;
-          sincospif(2.0f * u2, &sn, &cs);
-          const float z = oddf ? rad * cs : rad * sn;
-          const float Y = fmaf(static_cast<float>(S[m]), z, chi[m]);
+          const float Y = static_cast<float>(s_pY[i - nb0]);
+          const float u = static_cast<float>(s_pu[i - nb0]);
           float delta, llY = 0.0f, lfY = 0.0f;
           const float lfX = M::logf32(chi[m], tf);
           if (!M::support32(Y, tf)) {
             delta = -INFINITY;
           } else {
-            llY = M::loglike32(Y, d);
+            llY = static_cast<float>(s_pll[i - nb0]);
             lfY = M::logf32(Y, tf);
             delta = (llY + lfY) - (ll[m] + lfX);
           }
@@ -293,38 +351,21 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         }
       }
     } else {
-      // a1-a3: member RAM steps under theta. One Box-Muller pair serves the odd sweep (cosine)
-      // and the next even sweep (sine, kept in shared memory; recomputed if a launch starts on
-      // an even sweep).
-      const bool odd = (k & 1u) != 0u;
+      // a1-a3: member RAM steps under theta, the theta-dependent half (the draws, Y, e^Y and
+      // log l(Y) come from sweep_part_a).
   #pragma unroll
       for (int m = 0; m < K; ++m) {
         const unsigned int i = nb0 + tid + m * blockDim.x;
         if (i < nb1) {
-          const double yv = s_y[i - nb0], av = s_aux[i - nb0];
-          double z;
-          if (odd || s == 0) {
-            const uint4 w0 = philox4x32_10(make_uint4(0u, 0u, static_cast<uint32_t>(i), odd ? k : k - 1u), a.key0,
-                                           a.key1);
-            const double ua = uniform53(w0.x, w0.y), ub = uniform53(w0.z, w0.w);
-            const double rad = sqrt(-2.0 * log_tab(ua, s_math));
-            double sn, cs;
-            sincospi_tab(2.0 * ub, s_math, &sn, &cs);
-            z = odd ? rad * cs : rad * sn;
-            if (odd) s_zs[i - nb0] = rad * sn;
-          } else {
-            z = s_zs[i - nb0];
-          }
-          const uint4 w1 = philox4x32_10(make_uint4(1u, 0u, static_cast<uint32_t>(i), k), a.key0, a.key1);
-          const double u = uniform53(w1.x, w1.y);
-          const double Y = fma(S[m], z, chi[m]);
+          const double Y = s_pY[i - nb0];
+          const double u = s_pu[i - nb0];
           double delta, eY = 0.0, llY = 0.0, lfY = 0.0;
           const double lfX = M::logf(chi[m], echi[m], tc);
           if (!M::support(Y, tc)) {
             delta = -INFINITY;
           } else {
-            eY = M::kExp ? exp_tab(Y, s_math) : 0.0;
-            llY = M::loglike(Y, eY, yv, av, a.mc);
+            eY = s_peY[i - nb0];
+            llY = s_pll[i - nb0];
             lfY = M::logf(Y, eY, tc);
             delta = (llY + lfY) - (ll[m] + lfX);
           }
@@ -435,7 +476,12 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         }
       }
     }
-    if (!grid_barrier(a.bar, static_cast<unsigned int>(s), a.err, a.timeout_ns, skip_me)) return;
+    // arrive, prepare the next sweep's theta-independent half while the other blocks arrive, wait
+    grid_arrive(a.bar, skip_me);
+    if (s + 1 < a.ns)
+      sweep_part_a<M, K, F32>(a, s + 1, nb0, nb1, chi, S, s_math, s_y, s_aux, s_zs, s_d32, s_pY, s_peY, s_pll,
+                              s_pu);
+    if (!grid_wait(a.bar, static_cast<unsigned int>(s), a.err, a.timeout_ns)) return;
 
     // a7: every block sums all partials and takes the same decision
     {
@@ -558,7 +604,7 @@ static const void* kernel_for(int K, bool f32) {
 }
 
 size_t sweep_smem_bytes(int, int mpb, int) {
-  return sizeof(double) * kMathWords + 4 * sizeof(double) * static_cast<size_t>(mpb);
+  return sizeof(double) * kMathWords + 8 * sizeof(double) * static_cast<size_t>(mpb);
 }
 
 cudaError_t launch_math_table(double* t, cudaStream_t st) {
