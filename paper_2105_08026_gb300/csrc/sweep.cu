@@ -127,9 +127,10 @@ __device__ __forceinline__ void sweep_part_a(const SweepArgs& a, long long sa, u
         sincospif(2.0f * u2, &sn, &cs);
         const float z = odd ? rad * cs : rad * sn;
         const float Y = fmaf(static_cast<float>(S[m]), z, chi[m]);
-        s_pY[q] = static_cast<double>(Y);
-        s_pll[q] = static_cast<double>(M::loglike32(Y, d));
-        s_pu[q] = static_cast<double>(u);
+        // binary32 views of the slots (a conversion to binary64 and back would cost FP64 issue)
+        reinterpret_cast<float*>(s_pY)[q] = Y;
+        reinterpret_cast<float*>(s_pll)[q] = M::loglike32(Y, d);
+        reinterpret_cast<float*>(s_pu)[q] = u;
       } else {
         // One Box-Muller pair serves the odd sweep (cosine) and the next even sweep (sine, kept
         // in shared memory; recomputed if a launch starts on an even sweep)
@@ -321,14 +322,14 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
       for (int m = 0; m < K; ++m) {
         const unsigned int i = nb0 + tid + m * blockDim.x;
         if (i < nb1) {
-          const float Y = static_cast<float>(s_pY[i - nb0]);
-          const float u = static_cast<float>(s_pu[i - nb0]);
+          const float Y = reinterpret_cast<const float*>(s_pY)[i - nb0];
+          const float u = reinterpret_cast<const float*>(s_pu)[i - nb0];
           float delta, llY = 0.0f, lfY = 0.0f;
           const float lfX = M::logf32(chi[m], tf);
           if (!M::support32(Y, tf)) {
             delta = -INFINITY;
           } else {
-            llY = static_cast<float>(s_pll[i - nb0]);
+            llY = reinterpret_cast<const float*>(s_pll)[i - nb0];
             lfY = M::logf32(Y, tf);
             delta = (llY + lfY) - (ll[m] + lfX);
           }
