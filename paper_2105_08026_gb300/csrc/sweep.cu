@@ -92,24 +92,38 @@ cudaError_t launch_prefix_weights(int nr, const double* Wr, double* cw, cudaStre
 // theta' = theta + S_theta U, its prior and constants, the rule's outer-node values at theta')
 // runs on the last warp while every warp does its member steps; only the accept decision
 // itself sits between the grid barrier and the next member phase.
+// The RAM factor update of a member's previous step, S <- S sqrt(1 + eta (alpha - alpha_*))
+// (Sec. 2.2, d = 1), with alpha kept in the member's slot of pu (binary64; binary32 in the upper
+// half of the slot array in the FP32 form).
+template <bool F32>
+__device__ __forceinline__ double ram_pending(const SweepArgs& a, double S, double eta, const double* s_pu,
+                                              unsigned int q) {
+  const double alpha =
+      F32 ? static_cast<double>(reinterpret_cast<const float*>(s_pu)[a.mpb + q]) : s_pu[q];
+  return S * sqrt(fma(eta, alpha - a.astar, 1.0));
+}
+
 // The theta-independent half of each member's step for sweep sa of this launch
-// (k = k0 + sa + 1): the draws, the proposal Y = chi + S z and its log-likelihood (with e^Y),
-// stored per member in shared memory (pY, peY, pll, pu). The kernel computes it while the
-// previous sweep's grid barrier completes; the theta-dependent half (log f, the accept, the RAM
-// update) follows the theta decision. Same operations as a whole step, so the same bits.
+// (k = k0 + sa + 1): the previous step's RAM factor update (sa > 0), the draws, the proposal
+// Y = chi + S z and its log-likelihood (with e^Y), stored per member in shared memory (pY, peY,
+// pll, pu). The kernel computes it while the previous sweep's grid barrier completes; the
+// theta-dependent half (log f, the accept, alpha) follows the theta decision. Same operations
+// as a whole step, so the same bits.
 template <class M, int K, bool F32, class R>
 __device__ __forceinline__ void sweep_part_a(const SweepArgs& a, long long sa, unsigned int nb0, unsigned int nb1,
-                                             const R (&chi)[K], const double (&S)[K], const double* s_math,
+                                             const R (&chi)[K], double (&S)[K], const double* s_math,
                                              const double* s_y, const double* s_aux, double* s_zs,
                                              const float* s_d32, double* s_pY, double* s_peY, double* s_pll,
                                              double* s_pu) {
   const uint32_t k = static_cast<uint32_t>(a.k0 + sa + 1);
   const bool odd = (k & 1u) != 0u;
+  const double eta_prev = (sa > 0) ? __ldg(a.tab_eta + sa - 1) : 0.0;
 #pragma unroll
   for (int m = 0; m < K; ++m) {
     const unsigned int i = nb0 + threadIdx.x + m * blockDim.x;
     if (i < nb1) {
       const unsigned int q = i - nb0;
+      if (sa > 0) S[m] = ram_pending<F32>(a, S[m], eta_prev, s_pu, q);
       if constexpr (F32) {
         // Philox block (0, stream 2, member i, odd sweep k_o): a Box-Muller pair from 24-bit
         // uniforms of words 0 and 1 (cosine for k_o, sine for k_o + 1), the accept uniforms of
@@ -283,7 +297,6 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     sweep_part_a<M, K, F32>(a, 0, nb0, nb1, chi, S, s_math, s_y, s_aux, s_zs, s_d32, s_pY, s_peY, s_pll, s_pu);
 
   for (long long s = 0; s < a.ns; ++s) {
-    const double eta = __ldg(a.tab_eta + s);
     const ThetaC tc = s_tc;
     const bool trace = (a.trace_off + s) < a.trace_T;
     unsigned int member_nan = 0;
@@ -342,7 +355,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
             member_acc++;
           }
           s_lf32[i - nb0] = acc ? lfY : lfX;
-          S[m] *= sqrt(fma(eta, static_cast<double>(alpha) - a.astar, 1.0));
+          reinterpret_cast<float*>(s_pu)[a.mpb + (i - nb0)] = alpha;  // RAM update in the next half-step
           if (trace) {
             const long long o = (a.trace_off + s) * a.n + static_cast<long long>(i);
             a.tr_delta[o] = delta;
@@ -381,7 +394,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
             member_acc++;
           }
           s_lf[i - nb0] = acc ? lfY : lfX;
-          S[m] *= sqrt(fma(eta, alpha - a.astar, 1.0));
+          s_pu[i - nb0] = alpha;  // RAM update in the next half-step (u has been read)
           if (trace) {
             const long long o = (a.trace_off + s) * a.n + static_cast<long long>(i);
             a.tr_delta[o] = delta;
@@ -552,13 +565,14 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     if (s_stop) return;
   }
 
-  // write back (only reached when every sweep succeeded)
+  // write back (only reached when every sweep succeeded), with the last step's RAM update
+  const double eta_last = (a.ns > 0) ? __ldg(a.tab_eta + a.ns - 1) : 0.0;
 #pragma unroll
   for (int m = 0; m < K; ++m) {
     const unsigned int i = nb0 + tid + m * blockDim.x;
     if (i < nb1) {
       a.chi[i] = static_cast<double>(chi[m]);
-      a.S[i] = S[m];
+      a.S[i] = (a.ns > 0) ? ram_pending<F32>(a, S[m], eta_last, s_pu, i - nb0) : S[m];
     }
   }
   __shared__ unsigned int s_macc;
