@@ -87,6 +87,7 @@ def parse():
     ap.add_argument("--no-bb1", action="store_true")
     ap.add_argument("--no-nn3", action="store_true")
     ap.add_argument("--no-marginal", action="store_true")
+    ap.add_argument("--no-nn1", action="store_true")
     ap.add_argument("--marginal-burn", type=int, default=300)
     ap.add_argument("--marginal-steps", type=int, default=1500)
     ap.add_argument("--nn3-sizes", default="100,1000,10000,30000")
@@ -490,6 +491,34 @@ def run_marginal(args, cudahm, stream, device, data, theta0, scale, consts, peak
     return out
 
 
+def run_nn1_small(args, cudahm, stream, device):
+    """The d = 1 normal-normal configuration (N = 1000, mu = 2, tau = 0.8, sigma_i ~ U[0.5, 1.5],
+    data seed 1001, chain seed 1, FP64): 500 burn-in sweeps untimed, 2000 timed. At this N a
+    sweep is latency-bound (one member per thread, the theta step and the grid barrier)."""
+    import torch
+    from paper_2105_08026_gb300 import synth
+    d = synth.nn1_data(1000, seed=1001)
+    th, sc, c = synth.nn1_settings(d)
+    s = cudahm.Sampler(cudahm.NN1, 1000, theta_init=th, theta_prop_scale=sc, model_consts=c, seed=1,
+                       device=device, stream=stream.cuda_stream, use_torch_allocator=True)
+    s.set_data(d.y, d.sigma)
+    s.run(500, 0)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rows = s.run(0, 2000, 1)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = s.stats()
+    s.close()
+    return {"workload": "normal-normal d=1, N=1000, FP64", "value": 1000 * 2000 / (ms * 1e-3),
+            "unit": "object-updates/s", "us_per_sweep": 1e3 * ms / 2000, "steps": 2000, "burn_in": 500,
+            "theta_mean": rows.mean(axis=0).tolist(),
+            "launch_shape": [st.grid_blocks, st.block_threads, st.objects_per_thread]}
+
+
 def run_served(args, cudahm, device):
     """Poisson request stream (rate 20/s for --serve-seconds) into the continuous-batching server:
     each request is NN1 or LF with probability 1/2, N log-uniform on [1e3, 3e5], 5000 sweeps,
@@ -661,6 +690,9 @@ def run_cuda(args):
     nn3 = None
     if not args.no_nn3 and rank == 0:
         nn3 = run_nn3_ess(args, cudahm, stream, local)
+    nn1 = None
+    if not args.no_nn1 and rank == 0:
+        nn1 = run_nn1_small(args, cudahm, stream, local)
     marg = None
     if not args.no_marginal and rank == 0:
         marg = run_marginal(args, cudahm, stream, local, data, theta0, scale, consts, peak)
@@ -724,7 +756,7 @@ def run_cuda(args):
                        "launch_shape": [st.grid_blocks, st.block_threads, st.objects_per_thread]},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "fp32_bulk": fp32, "batched_fp32": batched, "served_fp32": served, "mvn3": mvn3, "bb1": bb1, "nn3_ess": nn3,
-            "marginal": marg}
+            "marginal": marg, "nn1_n1000": nn1}
     print(json.dumps(line), flush=True)
     s.close()
     if ws > 1:

@@ -94,6 +94,10 @@ def lib():
                                         ctypes.c_int64, _dp, _i64p, _i64p, ctypes.c_int64, _dp, _dp, _dp, _dp,
                                         _u8p, _dp])
             L.orc_marg_run.restype = ctypes.c_int
+            L.orc_member_pass.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp,
+                                          ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _dp, _dp,
+                                          _dp, _dp, _dp, _i64p]
+            L.orc_member_pass.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -238,6 +242,20 @@ def member_logdens(model, y, aux, consts, chi, theta):
     out = np.zeros(n)
     lib().orc_member_logdens(model, d, n, _p(y), _p(aux), _p(consts), _p(chi), _p(theta), _p(out))
     return out
+
+
+def member_pass(model, y, aux, consts, params, seed, k, i0, i1, theta, theta_prop, chi, S):
+    """The member half of sweep k over members [i0, i1): updates chi and S (numpy arrays, in
+    place) and returns d_i = log f(chi_i;theta') - log f(chi_i;theta) of the updated members and
+    the number of accepts. params = (target_accept, adapt_exponent, ...)."""
+    d = MODEL_D[model]
+    y, aux, theta, theta_prop, params = _f64(y), _f64(aux), _f64(theta), _f64(theta_prop), _f64(params)
+    consts = _f64(consts if consts is not None else np.zeros(1))
+    out = np.zeros(max(i1 - i0, 1))
+    acc = ctypes.c_int64(0)
+    lib().orc_member_pass(model, d, y.size // d, _p(y), _p(aux), _p(consts), _p(params), int(seed), int(k), int(i0),
+                          int(i1), _p(theta), _p(theta_prop), _p(chi), _p(S), _p(out), ctypes.byref(acc))
+    return out[: i1 - i0], acc.value
 
 
 def marg_logp(model, y, aux, consts, theta):

@@ -910,3 +910,49 @@ int orc_marg_run(int model, int p, int64_t n, const double* y, const double* aux
   if (has_rule) gl_rule_free(&P.rule);
   return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* One member pass of sweep k over the members [i0, i1) (the member half of the  */
+/* MWG sweep, Sec. 2.1; the RAM step of Sec. 2.2 with eta = (k+1)^-gamma, R1),   */
+/* for a driver that splits the members over ranks: updates chi and S of those   */
+/* members in place and writes d_i = log f(chi_i;theta') - log f(chi_i;theta)   */
+/* of the updated chi_i to d_out[i - i0] (-inf off the support of theta'; not    */
+/* written when theta_prop is NULL). The draws are keyed by (seed, i, k), so a   */
+/* split gives the same members' steps as one pass over all of them.             */
+/* ------------------------------------------------------------------------- */
+int orc_member_pass(int model, int d, int64_t n, const double* y, const double* aux, const double* consts,
+                    const double* params_vec, uint64_t seed, int64_t k, int64_t i0, int64_t i1,
+                    const double* theta, const double* theta_prop, double* chi, double* S, double* d_out,
+                    int64_t* accepts) {
+  problem P;
+  memset(&P, 0, sizeof(P));
+  P.model = model; P.d = d; P.n = n; P.y = y; P.aux = aux; P.consts = consts;
+  const double target_accept = params_vec[0], adapt_exponent = params_vec[1];
+  double eta = pow((double)(k + 1), -adapt_exponent); /* R1 */
+  double U[9], Y[9];
+  int64_t macc = 0;
+  for (int64_t i = i0; i < i1; ++i) {
+    double* x = chi + (int64_t)d * i;
+    double* Si = S + (int64_t)d * d * i;
+    double u;
+    orc_draw_member(seed, (uint32_t)i, (uint32_t)k, d, U, &u);
+    for (int a = 0; a < d; ++a) {
+      double t = x[a];
+      for (int b = 0; b <= a; ++b) t += Si[a * d + b] * U[b];
+      Y[a] = t;
+    }
+    double lpY = member_lp(&P, i, Y, theta);
+    double lpX = member_lp(&P, i, x, theta);
+    double delta = (lpY == -INFINITY) ? -INFINITY : lpY - lpX;
+    int acc = log(u) < delta; /* R4 */
+    double alpha = (delta >= 0.0) ? 1.0 : exp(delta);
+    if (acc) { for (int a = 0; a < d; ++a) x[a] = Y[a]; ++macc; }
+    orc_ram_update(d, Si, U, alpha, target_accept, eta);
+    if (theta_prop) {
+      double fn = logf_obj(&P, x, theta_prop);
+      d_out[i - i0] = (fn == -INFINITY) ? -INFINITY : fn - logf_obj(&P, x, theta);
+    }
+  }
+  if (accepts) *accepts += macc;
+  return 0;
+}

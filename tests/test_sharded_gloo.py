@@ -1,0 +1,113 @@
+"""The exchange step a multi-GPU split of one population would need (each rank updates its own
+members, then one exact all-reduce of their d_i = log f(chi_i;theta') - log f(chi_i;theta)
+before every rank takes the same theta decision), checked on the CPU with world_size 2 over
+gloo. The member steps come from the oracle (their draws are keyed by member and sweep, so a
+split leaves each member's step unchanged); the sum over members is exact (math.fsum, the
+correctly rounded sum, as the device's fixed-point sum is), so the split chain must equal the
+one-rank chain bit for bit: theta rows, latents and RAM factors. The one-rank driver is also
+checked against the oracle's own chain (its Neumaier sum differs only in rounding).
+
+This build runs one process per GPU with independent replicas (the pool gives one GPU per call),
+so the split is not on the device path; this test covers its logic.
+"""
+import json
+import math
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SWEEPS = 150
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _driver(data, theta0, scale, consts, seed, rank, world, allgather):
+    """NN1 chain with its members split over `world` ranks (theta step as the oracle's: RAM on
+    theta, log alpha = D + N (c(theta') - c(theta)) + ln pi(theta') - ln pi(theta), c = -ln tau)."""
+    import oracle
+    y, sig = data.y, data.sigma
+    n = y.size
+    i0, i1 = n * rank // world, n * (rank + 1) // world
+    chi = y.copy()
+    S = np.ones(n)
+    theta = np.array(theta0, dtype=np.float64)
+    Sth = np.diag(np.asarray(scale, dtype=np.float64))
+    params = np.array([0.4, 2.0 / 3.0, 0.4, 1.0])
+    lo, hi = consts[0], consts[1]
+    prior = lambda t: 0.0 if lo <= t[1] <= hi else -math.inf
+    rows = []
+    for s in range(SWEEPS):
+        k = s + 1
+        eta = (k + 1.0) ** (-2.0 / 3.0)
+        U, ut = oracle.draw(seed, 1, 0, k, 2)
+        thp = theta + Sth @ U
+        lp_new = prior(thp)
+        d_loc, _ = oracle.member_pass(oracle.NN1, y, sig, consts, params, seed, k, i0, i1, theta, thp, chi, S)
+        d_all = allgather(d_loc)
+        if lp_new == -math.inf or np.isneginf(d_all).any():
+            logalpha = -math.inf
+        else:
+            logalpha = math.fsum(d_all.tolist()) + n * (-thp[1] + theta[1]) + lp_new - prior(theta)
+        alpha = 1.0 if logalpha >= 0.0 else math.exp(logalpha)
+        if math.log(ut) < logalpha:
+            theta = thp
+        Sth = oracle.ram_update(Sth, U, alpha, 0.4, eta)
+        rows.append(theta.copy())
+    return np.array(rows), chi[i0:i1], S[i0:i1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch
+    import torch.distributed as dist
+    from paper_2105_08026_gb300 import synth
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    data = synth.nn1_data(301, seed=77)  # ragged split: 150 + 151 members
+    theta0, scale, consts = synth.nn1_settings(data)
+
+    def allgather(v):  # gloo gathers equal sizes: pad to the largest shard, then trim
+        sizes = [None] * world
+        dist.all_gather_object(sizes, int(v.size))
+        m = max(sizes)
+        pad = np.zeros(m)
+        pad[: v.size] = v
+        out = [torch.zeros(m, dtype=torch.float64) for _ in sizes]
+        dist.all_gather(out, torch.from_numpy(pad))
+        return np.concatenate([o.numpy()[:c] for o, c in zip(out, sizes)])
+
+    rows, chi, S = _driver(data, theta0, scale, consts, 5, rank, world, allgather)
+    np.savez(os.path.join(out_dir, f"rank{rank}.npz"), rows=rows, chi=chi, S=S)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.slow
+def test_split_members_equal_one_rank_bit_for_bit(tmp_path):
+    import torch.multiprocessing as mp
+    from paper_2105_08026_gb300 import synth
+
+    import oracle
+    port = _free_port()
+    mp.start_processes(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    r0, r1 = np.load(tmp_path / "rank0.npz"), np.load(tmp_path / "rank1.npz")
+    assert np.array_equal(r0["rows"], r1["rows"])  # every rank took the same theta decisions
+    data = synth.nn1_data(301, seed=77)
+    theta0, scale, consts = synth.nn1_settings(data)
+    rows1, chi1, S1 = _driver(data, theta0, scale, consts, 5, 0, 1, lambda v: v)
+    assert np.array_equal(r0["rows"], rows1)
+    assert np.array_equal(np.concatenate([r0["chi"], r1["chi"]]), chi1)
+    assert np.array_equal(np.concatenate([r0["S"], r1["S"]]), S1)
+    # the one-rank driver is the oracle's chain (Neumaier instead of an exact sum)
+    ch = oracle.Chain(oracle.NN1, data.y, data.sigma, consts, theta0, scale, 5, data.y.copy())
+    orows, _ = ch.run(0, SWEEPS)
+    assert np.allclose(rows1, orows, rtol=1e-12, atol=1e-12)
