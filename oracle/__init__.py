@@ -86,7 +86,7 @@ def lib():
             L.orc_run.argtypes = ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp,
                                    ctypes.c_uint64, _dp, _dp, _dp, _dp, _i64p, _dp,
                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _dp, _i64p, _i64p, _i64p,
-                                   ctypes.c_int64, _dp, _dp, _u8p, _dp, _dp, _dp, _dp, _u8p, _dp])
+                                   ctypes.c_int64, _dp, _dp, _u8p, _dp, _dp, _dp, _dp, _u8p, _dp, _dp, _dp, _i64p])
             L.orc_run.restype = ctypes.c_int
             L.orc_marg_logp.argtypes = [ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp]
             L.orc_marg_run.argtypes = ([ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp,
@@ -272,7 +272,7 @@ class MarginalChain:
     """theta-only chain on the marginal posterior (latents integrated out by the cubature rule)."""
 
     def __init__(self, model, y, aux, consts, theta_init, theta_prop_scale, seed, adapt_exponent=2.0 / 3.0,
-                 theta_target_accept=0.4, adapt_theta=True):
+                 theta_target_accept=0.4, adapt_theta=True, keep_chi_moments=False):
         self.model = model
         self.p = MODEL_P[model]
         self.y = _f64(y)
@@ -305,7 +305,9 @@ class MarginalChain:
         rc = lib().orc_marg_run(self.model, p, self.n, _p(self.y), _p(self.aux), _p(self.consts), _p(self.params),
                                 self.seed, _p(self.theta), _p(self.S_theta), _p(self.lp), ctypes.byref(self.sweep),
                                 ctypes.byref(self.etabar), n_burn, n_iter, thin, _p(rows), ctypes.byref(rows_out),
-                                ctypes.byref(self.theta_accepts), T, *args_tr)
+                                ctypes.byref(self.theta_accepts), T, *args_tr,
+                           _p(self.mom_mean) if self.mom_mean is not None else None,
+                           _p(self.mom_m2) if self.mom_m2 is not None else None, ctypes.byref(self.mom_n))
         if rc != 0:
             raise RuntimeError(f"oracle marginal run failed: {rc}")
         return rows[: rows_out.value].copy(), tr
@@ -317,7 +319,7 @@ class Chain:
 
     def __init__(self, model, y, aux, consts, theta_init, theta_prop_scale, seed, chi0,
                  chi_init_scale=1.0, target_accept=0.4, adapt_exponent=2.0 / 3.0,
-                 theta_target_accept=0.4, adapt_theta=True):
+                 theta_target_accept=0.4, adapt_theta=True, keep_chi_moments=False):
         self.model = model
         self.d = MODEL_D[model]
         self.p = MODEL_P[model]
@@ -339,6 +341,17 @@ class Chain:
         self.etabar = ctypes.c_double(0.0)
         self.member_accepts = ctypes.c_int64(0)
         self.theta_accepts = ctypes.c_int64(0)
+        # running moments of the latents over the kept sweeps (Welford), when asked
+        self.mom_mean = np.zeros(self.n * self.d) if keep_chi_moments else None
+        self.mom_m2 = np.zeros(self.n * self.d) if keep_chi_moments else None
+        self.mom_n = ctypes.c_int64(0)
+
+    def moments(self):
+        """(mean, var, count): per-member mean and sample variance (M2/(count - 1), 0 for one
+        sample) of every latent component over the kept sweeps so far, shaped (n, d)."""
+        m = self.mom_n.value
+        var = self.mom_m2 / (m - 1) if m > 1 else np.zeros_like(self.mom_m2)
+        return self.mom_mean.reshape(self.n, self.d).copy(), var.reshape(self.n, self.d), m
 
     def run(self, n_burn, n_iter, thin=1, trace_sweeps=0):
         n, p = self.n, self.p
@@ -359,7 +372,9 @@ class Chain:
                            self.seed, _p(self.chi), _p(self.S), _p(self.theta), _p(self.S_theta),
                            ctypes.byref(self.sweep), ctypes.byref(self.etabar), n_burn, n_iter, thin, _p(rows),
                            ctypes.byref(rows_out), ctypes.byref(self.member_accepts),
-                           ctypes.byref(self.theta_accepts), T, *args_tr)
+                           ctypes.byref(self.theta_accepts), T, *args_tr,
+                           _p(self.mom_mean) if self.mom_mean is not None else None,
+                           _p(self.mom_m2) if self.mom_m2 is not None else None, ctypes.byref(self.mom_n))
         if rc != 0:
             raise RuntimeError(f"oracle run failed: {rc}")
         return rows[: rows_out.value].copy(), tr

@@ -593,7 +593,10 @@ int orc_run(int model, int d, int p, int64_t n, const double* y, const double* a
             /* optional lockstep trace, first trace_sweeps sweeps of this call: */
             int64_t trace_sweeps, double* tr_delta, double* tr_u, uint8_t* tr_acc,
             double* tr_theta_prop, double* tr_D, double* tr_logalpha, double* tr_utheta, uint8_t* tr_tacc,
-            double* tr_etabar) {
+            double* tr_etabar,
+            /* optional running moments of the latents over the kept sweeps (n*d each, member-major,
+               continued across calls; mom_n = kept sweeps so far); NULL mom_mean: off */
+            double* mom_mean, double* mom_m2, int64_t* mom_n) {
   orc_params prm;
   prm.target_accept = params_vec[0];
   prm.adapt_exponent = params_vec[1];
@@ -692,10 +695,22 @@ int orc_run(int model, int d, int p, int64_t n, const double* y, const double* a
       if (prm.adapt_theta) orc_ram_update(p, S_theta, U, alpha, prm.theta_target_accept, eta);
     }
 
-    /* (3) record kept sweeps */
-    if (s >= n_burn && thin > 0 && ((s - n_burn + 1) % thin) == 0 && theta_rows) {
+    /* (3) record kept sweeps: the theta row and, when asked, every latent component's running
+       mean and sum of squared deviations by Welford's (1962) recurrence: with x the m-th kept
+       value, mean_m = mean_{m-1} + (x - mean_{m-1})/m and
+       M2_m = M2_{m-1} + (x - mean_{m-1})(x - mean_m) */
+    int kept = s >= n_burn && thin > 0 && ((s - n_burn + 1) % thin) == 0;
+    if (kept && theta_rows) {
       for (int a = 0; a < p; ++a) theta_rows[rows * p + a] = theta[a];
       ++rows;
+    }
+    if (kept && mom_mean) {
+      const int64_t m = ++*mom_n;
+      for (int64_t q = 0; q < n * d; ++q) {
+        const double x = chi[q], dl = x - mom_mean[q];
+        mom_mean[q] += dl / (double)m;
+        mom_m2[q] += dl * (x - mom_mean[q]);
+      }
     }
     *sweep = k;
   }
