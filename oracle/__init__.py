@@ -305,9 +305,7 @@ class MarginalChain:
         rc = lib().orc_marg_run(self.model, p, self.n, _p(self.y), _p(self.aux), _p(self.consts), _p(self.params),
                                 self.seed, _p(self.theta), _p(self.S_theta), _p(self.lp), ctypes.byref(self.sweep),
                                 ctypes.byref(self.etabar), n_burn, n_iter, thin, _p(rows), ctypes.byref(rows_out),
-                                ctypes.byref(self.theta_accepts), T, *args_tr,
-                           _p(self.mom_mean) if self.mom_mean is not None else None,
-                           _p(self.mom_m2) if self.mom_m2 is not None else None, ctypes.byref(self.mom_n))
+                                ctypes.byref(self.theta_accepts), T, *args_tr)
         if rc != 0:
             raise RuntimeError(f"oracle marginal run failed: {rc}")
         return rows[: rows_out.value].copy(), tr
