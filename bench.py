@@ -88,6 +88,7 @@ def parse():
     ap.add_argument("--no-nn3", action="store_true")
     ap.add_argument("--no-marginal", action="store_true")
     ap.add_argument("--no-nn1", action="store_true")
+    ap.add_argument("--no-moments", action="store_true")
     ap.add_argument("--marginal-burn", type=int, default=300)
     ap.add_argument("--marginal-steps", type=int, default=1500)
     ap.add_argument("--nn3-sizes", default="100,1000,10000,30000")
@@ -670,6 +671,34 @@ def run_cuda(args):
                 "dtype": "f32 member terms, f64 sums/accept/RAM/selection integral"}
         s3.close()
 
+    # the same FP64 workload keeping every member's running mean and variance of chi over the kept
+    # sweeps (thin 1: every sweep adds its latents; one read and one write of 16 B per member)
+    moments = None
+    if not args.no_moments and rank == 0:
+        s4 = cudahm.Sampler(cudahm.LF, n, theta_init=theta0, theta_prop_scale=scale, model_consts=consts,
+                            seed=chain_seed, device=local, stream=stream.cuda_stream,
+                            use_torch_allocator=True, keep_chi_moments=True)
+        cudahm.cudahm_set_data_device(s4.h, y_dev.data_ptr(), r_dev.data_ptr(), n)
+        if args.warmup > 0:
+            s4.run(args.warmup, 0)
+        m_ms = 0.0
+        for ns in chunks:
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s4.run(0, ns, 1)
+            e1.record(stream)
+            e1.synchronize()
+            m_ms += e0.elapsed_time(e1)
+        mean, var, cnt = s4.chi_moments()
+        assert cnt == K
+        moments = {"value": n * K / (m_ms * 1e-3), "unit": "object-updates/s", "ms_per_step": m_ms / K,
+                   "kept_sweeps": int(cnt), "relative_to_plain": (n * K / (m_ms * 1e-3)) / value,
+                   "dtype": "f64", "median_posterior_sd_chi": float(np.median(np.sqrt(var)))}
+        s4.close()
+
     # batched FP32 form: 256 NN1/LF populations of uneven size in one persistent launch per chunk
     batched = None
     if not args.no_batched and rank == 0:
@@ -756,7 +785,7 @@ def run_cuda(args):
                        "launch_shape": [st.grid_blocks, st.block_threads, st.objects_per_thread]},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "fp32_bulk": fp32, "batched_fp32": batched, "served_fp32": served, "mvn3": mvn3, "bb1": bb1, "nn3_ess": nn3,
-            "marginal": marg, "nn1_n1000": nn1}
+            "marginal": marg, "nn1_n1000": nn1, "chi_moments": moments}
     print(json.dumps(line), flush=True)
     s.close()
     if ws > 1:

@@ -134,6 +134,8 @@ typedef struct {
                                     timeout path); -1 = off */
   int32_t marginal;              /* 1: integrate each member's latent out by cubature and run the
                                     chain on theta alone (NN1, LF, BB1; see cudahm_eval_marginal) */
+  int32_t keep_chi_moments;      /* 1: keep every latent component's running mean and variance over
+                                    the kept sweeps (see cudahm_get_chi_moments); member form only */
 } cudahm_config;
 
 typedef struct {
@@ -187,6 +189,18 @@ int cudahm_get_samples(cudahm_t h, double* theta_host, int64_t cap_rows, int64_t
 /* Current latents (N*d doubles) and/or per-member RAM factors (N*d*d doubles, lower,
  * row-major per member); either pointer may be NULL. */
 int cudahm_get_chi(cudahm_t h, double* chi_host, double* S_host);
+
+/* Posterior summaries of the latents (Appendix A: the paper's samplers store every kept sample
+ * in memory or stream it to a file; a handle created with keep_chi_moments = 1 keeps instead,
+ * on the device, each member's running moments). Over the kept sweeps since
+ * set_data (the sweeps whose theta row is recorded, across runs; a restored checkpoint brings
+ * its own), mean_host receives each latent component's mean and var_host its sample variance
+ * (divisor count - 1; 0 when count < 2), N*d doubles each, member-major; *count_out the number
+ * of kept sweeps. Any pointer may be NULL. Computed by Welford's recurrence in binary64 (the
+ * FP32 form adds its binary32 latents exactly); the cost is one read and one write of 2 d
+ * doubles per member and kept sweep. A failed run leaves the moments of its completed launches,
+ * like the latents. CUDAHM_ESTATE without keep_chi_moments. */
+int cudahm_get_chi_moments(cudahm_t h, double* mean_host, double* var_host, int64_t* count_out);
 
 /* Current theta (p doubles) and S_theta (p*p, lower, row-major); either may be NULL. */
 int cudahm_get_theta(cudahm_t h, double* theta_host, double* S_theta_host);

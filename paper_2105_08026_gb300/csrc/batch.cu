@@ -65,7 +65,8 @@ template <class M>
 __device__ __forceinline__ void member_f64(const SweepArgs& a, unsigned int i, uint32_t k, double eta,
                                            const ThetaC& tc, const ThetaC& tcp, bool prior_ok, const double* s_math,
                                            Xacc& xd, XFlags& fd, unsigned int& neg_big, unsigned int& pos_big,
-                                           unsigned int& nan_cnt, unsigned int& acc_cnt, long long tro) {
+                                           unsigned int& nan_cnt, unsigned int& acc_cnt, long long tro,
+                                           bool keep, const MomStep& ms) {
   double chi = a.chi[i], S = a.S[i];
   const double yv = a.y[i], av = a.aux[i];
   double echi = M::kExp ? exp_tab(chi, s_math) : 0.0;
@@ -103,6 +104,7 @@ __device__ __forceinline__ void member_f64(const SweepArgs& a, unsigned int i, u
   S *= sqrt(fma(eta, alpha - a.astar, 1.0));
   a.chi[i] = chi;
   a.S[i] = S;
+  if (keep) mom_add(ms, i, chi);
   if (tro >= 0) {
     a.tr_delta[tro + i] = delta;
     a.tr_u[tro + i] = u;
@@ -125,7 +127,8 @@ template <class M>
 __device__ __forceinline__ void member_f32(const SweepArgs& a, unsigned int i, uint32_t k, double eta,
                                            const ThetaCf& tf, const ThetaCf& tpf, bool prior_ok, Xacc& xd,
                                            XFlags& fd, unsigned int& neg_big, unsigned int& pos_big,
-                                           unsigned int& nan_cnt, unsigned int& acc_cnt, long long tro) {
+                                           unsigned int& nan_cnt, unsigned int& acc_cnt, long long tro,
+                                           bool keep, const MomStep& ms) {
   float chi = static_cast<float>(a.chi[i]);
   double S = a.S[i];
   float d[M::kData32];
@@ -161,6 +164,7 @@ __device__ __forceinline__ void member_f32(const SweepArgs& a, unsigned int i, u
   S *= sqrt(fma(eta, static_cast<double>(alpha) - a.astar, 1.0));
   a.chi[i] = static_cast<double>(chi);
   a.S[i] = S;
+  if (keep) mom_add(ms, i, static_cast<double>(chi));
   if (tro >= 0) {
     a.tr_delta[tro + i] = static_cast<double>(delta);
     a.tr_u[tro + i] = static_cast<double>(u);
@@ -189,7 +193,7 @@ __device__ __forceinline__ void member3_f64(const SweepArgs& a, unsigned int i, 
                                             const ThetaC3& tc, const ThetaC3& tcp, bool prior_ok,
                                             const double* s_math, Xacc& xd, XFlags& fd, unsigned int& neg_big,
                                             unsigned int& pos_big, unsigned int& nan_cnt, unsigned int& acc_cnt,
-                                            long long tro, bool first) {
+                                            long long tro, bool first, bool keep, const MomStep& ms) {
   const size_t n = static_cast<size_t>(a.n);
   double x[3], y[3], w[3], S[6];
 #pragma unroll
@@ -244,6 +248,9 @@ __device__ __forceinline__ void member3_f64(const SweepArgs& a, unsigned int i, 
   for (int j = 0; j < 3; ++j) a.chi[j * n + i] = x[j];
 #pragma unroll
   for (int q = 0; q < 6; ++q) a.S[q * n + i] = S[q];
+  if (keep)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) mom_add(ms, j * n + i, x[j]);
   if (tro >= 0) {
     a.tr_delta[tro + i] = delta;
     a.tr_u[tro + i] = u;
@@ -281,7 +288,8 @@ template <class M>
 __device__ __forceinline__ void member3_f32(const SweepArgs& a, unsigned int i, uint32_t k, double eta,
                                             const ThetaC3f& tf, const ThetaC3f& tpf, bool prior_ok, Xacc& xd,
                                             XFlags& fd, unsigned int& neg_big, unsigned int& pos_big,
-                                            unsigned int& nan_cnt, unsigned int& acc_cnt, long long tro) {
+                                            unsigned int& nan_cnt, unsigned int& acc_cnt, long long tro,
+                                            bool keep, const MomStep& ms) {
   const size_t n = static_cast<size_t>(a.n);
   float x[3], d[M::kData32];
   double S[6];
@@ -321,6 +329,9 @@ __device__ __forceinline__ void member3_f32(const SweepArgs& a, unsigned int i, 
   for (int j = 0; j < 3; ++j) a.chi[j * n + i] = static_cast<double>(x[j]);
 #pragma unroll
   for (int q = 0; q < 6; ++q) a.S[q * n + i] = S[q];
+  if (keep)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) mom_add(ms, j * n + i, static_cast<double>(x[j]));
   if (tro >= 0) {
     a.tr_delta[tro + i] = static_cast<double>(delta);
     a.tr_u[tro + i] = static_cast<double>(u);
@@ -347,7 +358,8 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
   __shared__ TCf s_tcf, s_tcpf;
   __shared__ double s_etabar, s_logeb, s_lpri, s_lpri_new;
   __shared__ int s_stop;
-  __shared__ long long s_rows_written, s_tacc, s_k0, s_off, s_ns;
+  __shared__ long long s_rows_written, s_tacc, s_k0, s_off, s_ns, s_mom_n0;
+  __shared__ int s_mom_sel;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int p = a.p;
   constexpr bool is_lf = M::kRule;  // the model has a selection integral (LF, BB1)
@@ -369,10 +381,15 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
     s_lpri = M::logprior(s_theta, a.mc, s_math);
     s_rows_written = 0;
     s_tacc = 0;
+    s_mom_n0 = a.chain->mom_n;
+    s_mom_sel = a.chain->mom_sel;
     s_stop = 0;
   }
   __syncthreads();
   const long long ns = s_ns, k0 = s_k0, off = s_off;
+  const long long mom_n0 = s_mom_n0, thin = prog->thin;
+  const int mom_sel = s_mom_sel;
+  long long mom_k = 0;  // kept sweeps of this launch
   const long long burn_left = prog->n_burn - off;
   double* rows = a.rows ? a.rows + prog->rows * p : nullptr;
   const unsigned int nb0 = static_cast<unsigned int>((a.n * lb) / nb);
@@ -400,25 +417,30 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
     unsigned int neg_big = 0, pos_big = 0, member_nan = 0;
     const long long sg = off + s;  // sweep index within this run
     const long long tro = (sg < a.trace_T) ? sg * a.n : -1;
+    // a8 (optional): the kept sweep's latents go into the running moments
+    const bool keep = (a.mom != nullptr) && kept_sweep(s, burn_left, 0, thin);
+    MomStep ms{};
+    if (keep) ms = mom_step(a, M::kD, mom_sel, mom_n0, ++mom_k);
     if constexpr (M::kD == 3) {
       if constexpr (F32) {
         for (unsigned int i = nb0 + tid; i < nb1; i += blockDim.x)
           member3_f32<M>(a, i, k, eta, s_tcf, s_tcpf, prior_ok, xd, fd, neg_big, pos_big, member_nan, member_acc,
-                         tro);
+                         tro, keep, ms);
       } else {
         for (unsigned int i = nb0 + tid; i < nb1; i += blockDim.x)
           member3_f64<M>(a, i, k, eta, s_tc, s_tcp, prior_ok, s_math, xd, fd, neg_big, pos_big, member_nan,
-                         member_acc, tro, s == 0);
+                         member_acc, tro, s == 0, keep, ms);
       }
     } else if constexpr (F32) {
       const TCf tf = s_tcf, tpf = s_tcpf;
       for (unsigned int i = nb0 + tid; i < nb1; i += blockDim.x)
-        member_f32<M>(a, i, k, eta, tf, tpf, prior_ok, xd, fd, neg_big, pos_big, member_nan, member_acc, tro);
+        member_f32<M>(a, i, k, eta, tf, tpf, prior_ok, xd, fd, neg_big, pos_big, member_nan, member_acc, tro,
+                      keep, ms);
     } else {
       const TC tc = s_tc, tcp = s_tcp;
       for (unsigned int i = nb0 + tid; i < nb1; i += blockDim.x)
         member_f64<M>(a, i, k, eta, tc, tcp, prior_ok, s_math, xd, fd, neg_big, pos_big, member_nan, member_acc,
-                      tro);
+                      tro, keep, ms);
     }
     // a6: this block's share of the selection rule's outer nodes at theta'
     if constexpr (M::kRule)
@@ -539,6 +561,10 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
       a.chain->theta_acc += s_tacc;
       prog->off = off + ns;
       prog->rows += s_rows_written;
+      if (mom_k > 0) {  // commit the moments this launch wrote
+        a.chain->mom_n = mom_n0 + mom_k;
+        a.chain->mom_sel = 1 - mom_sel;
+      }
       prog->t_ns = globaltimer_ns() - t_start;
     }
   }

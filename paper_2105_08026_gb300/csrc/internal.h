@@ -18,7 +18,8 @@ struct ChainState {
   long long theta_acc;
   long long rows;    // rows written by the last launch
   int mcur;          // marginal form: which of the two log p_i arrays holds the current theta's
-  int pad;
+  int mom_sel;       // running moments of the latents: which of the two buffers is committed
+  long long mom_n;   // kept sweeps accumulated in the committed moments
 };
 
 // Model constants used inside kernels.
@@ -100,6 +101,9 @@ struct SweepArgs {
   const double* marg_nodes;  // marginal form: panel nodes and weights (kMargNodeWords)
   const double* marg_d32;    // marginal form, FP32 bulk, LF: per-member window data, [kMarg32Words][n]
   double* spare3;            // d = 3, FP64: the sine halves of the odd sweep's Box-Muller pairs, [3][n]
+  // running moments of the latents over the kept sweeps (nullptr: off): two buffers of
+  // [mean[d][n], M2[d][n]], the committed one named by ChainState::mom_sel
+  double* mom;
   // the rule's inner sum H(ln L) tabulated (h_ncell cells of kHDeg + 1 Chebyshev coefficients);
   // nullptr: evaluate the rule pair by pair
   const double* htab;

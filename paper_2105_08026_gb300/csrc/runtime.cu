@@ -133,6 +133,7 @@ struct cudahm {
   double* marg_nodes = nullptr;  // panel nodes and weights
   double* marg_d32 = nullptr;    // FP32 form, LF: per-member window data
   double* spare3 = nullptr;      // d = 3, FP64: the odd sweep's Box-Muller sines, [3][n]
+  double* mom = nullptr;         // running moments of the latents: two buffers of [mean[d][n], M2[d][n]]
   int mgrid = 0, mrows_smem = 1;
   bool marg_valid = false;       // marg_lp[mcur] holds log p_i at the chain's theta
   // the rule's inner sum H(ln L), tabulated (LF, BB1)
@@ -256,6 +257,8 @@ int validate(const cudahm_config* c) {
     if (!chol3_inverse(k, li)) return fail(CUDAHM_EINVAL, "NN3 needs a positive definite C_pop in consts[0..5]");
   }
   if (c->marginal != 0 && c->marginal != 1) return fail(CUDAHM_EINVAL, "marginal must be 0 or 1");
+  if (c->keep_chi_moments != 0 && c->keep_chi_moments != 1) return fail(CUDAHM_EINVAL, "keep_chi_moments must be 0 or 1");
+  if (c->keep_chi_moments && c->marginal) return fail(CUDAHM_EINVAL, "the marginal form has no latents to keep moments of");
   if (c->marginal) {
     if (c->model != CUDAHM_NN1 && c->model != CUDAHM_LF && c->model != CUDAHM_BB1)
       return fail(CUDAHM_EUNSUPPORTED, "the marginal form integrates one-dimensional latents (NN1, LF, BB1)");
@@ -383,6 +386,7 @@ SweepArgs base_args(cudahm* h) {
   a.marg_nodes = h->marg_nodes;
   a.marg_d32 = h->marg_d32;
   a.spare3 = h->spare3;
+  a.mom = h->mom;
   a.htab = h->htab;
   a.h_ua = h->h_ua;
   a.h_ub = h->h_ub;
@@ -473,6 +477,7 @@ int reset_chain(cudahm* h) {
   for (int q = 0; q < h->p; ++q) cs.theta[q] = h->cfg.theta_init[q];
   for (int q = 0; q < h->p; ++q) cs.S_theta[q * h->p + q] = h->cfg.theta_prop_scale[q];
   CU(cudaMemcpyAsync(h->chain, &cs, sizeof(cs), cudaMemcpyHostToDevice, h->stream));
+  if (h->mom) CU(cudaMemsetAsync(h->mom, 0, sizeof(double) * 4 * h->d * static_cast<size_t>(h->n), h->stream));
   CU(cudaStreamSynchronize(h->stream));
   h->sweeps = 0;
   h->rows_last = 0;
@@ -688,6 +693,7 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
   if (launch_math_table(h->math_tab, h->stream) != cudaSuccess)
     return bail(fail(CUDAHM_ECUDA, "exp/log table set-up failed: %s", cudaGetErrorString(cudaGetLastError())));
   if (h->d == 3 && cfg->precision == CUDAHM_FP64 && (rc = alloc_into(h, &h->spare3, 3ull * n))) return bail(rc);
+  if (cfg->keep_chi_moments && (rc = alloc_into(h, &h->mom, 4ull * h->d * n))) return bail(rc);
   if (cfg->model == CUDAHM_NN1 || cfg->model == CUDAHM_LF || cfg->model == CUDAHM_BB1) {  // the cubature rule
     if ((rc = alloc_into(h, &h->marg_nodes, kMargNodeWords))) return bail(rc);
     if (cfg->marginal && (rc = alloc_into(h, &h->marg_lp, 2ull * n))) return bail(rc);
@@ -907,6 +913,30 @@ int cudahm_get_chi(cudahm_t h, double* chi_host, double* S_host) {
   return CUDAHM_OK;
 }
 
+int cudahm_get_chi_moments(cudahm_t h, double* mean_host, double* var_host, int64_t* count_out) {
+  if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
+  if (!h->mom) return fail(CUDAHM_ESTATE, "the handle was created without keep_chi_moments");
+  CU(cudaSetDevice(h->cfg.device));
+  ChainState cs;
+  CU(cudaMemcpyAsync(&cs, h->chain, sizeof(cs), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  if (count_out) *count_out = cs.mom_n;
+  if (!mean_host && !var_host) return CUDAHM_OK;
+  const size_t n = static_cast<size_t>(h->n), dn = n * h->d;
+  std::vector<double> t(2 * dn);
+  CU(cudaMemcpyAsync(t.data(), h->mom + static_cast<size_t>(cs.mom_sel) * 2 * dn, sizeof(double) * 2 * dn,
+                     cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  const double m1 = static_cast<double>(cs.mom_n - 1);
+  for (size_t i = 0; i < n; ++i)
+    for (int j = 0; j < h->d; ++j) {  // per component on the device, member-major in the API
+      const size_t q = j * n + i;
+      if (mean_host) mean_host[i * h->d + j] = t[q];
+      if (var_host) var_host[i * h->d + j] = cs.mom_n > 1 ? t[dn + q] / m1 : 0.0;
+    }
+  return CUDAHM_OK;
+}
+
 int cudahm_get_theta(cudahm_t h, double* theta_host, double* S_theta_host) {
   if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
   CU(cudaSetDevice(h->cfg.device));
@@ -1042,7 +1072,8 @@ int cudahm_get_trace(cudahm_t h, double* delta, double* u, uint8_t* acc, double*
 int cudahm_checkpoint(cudahm_t h, void* buf, size_t cap, size_t* used) {
   if (!h || !used) return fail(CUDAHM_EINVAL, "NULL argument");
   const size_t nchi = static_cast<size_t>(h->n) * h->d, nS = static_cast<size_t>(h->factor_n);
-  const size_t need = 8 * sizeof(int64_t) + sizeof(ChainState) + sizeof(double) * (nchi + nS);
+  const size_t nmom = h->mom ? 2 * nchi : 0;  // the committed moments
+  const size_t need = 8 * sizeof(int64_t) + sizeof(ChainState) + sizeof(double) * (nchi + nS + nmom);
   *used = need;
   if (!buf) return CUDAHM_OK;
   if (cap < need) return fail(CUDAHM_EINVAL, "checkpoint buffer too small: need %zu bytes", need);
@@ -1058,6 +1089,14 @@ int cudahm_checkpoint(cudahm_t h, void* buf, size_t cap, size_t* used) {
   c += sizeof(double) * nchi;
   CU(cudaMemcpyAsync(c, h->S, sizeof(double) * nS, cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
+  if (nmom) {
+    c += sizeof(double) * nS;
+    ChainState cs;
+    std::memcpy(&cs, static_cast<char*>(buf) + sizeof(hdr), sizeof(cs));
+    CU(cudaMemcpyAsync(c, h->mom + static_cast<size_t>(cs.mom_sel) * nmom, sizeof(double) * nmom,
+                       cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
   return CUDAHM_OK;
 }
 
@@ -1065,7 +1104,8 @@ int cudahm_restore(cudahm_t h, const void* buf, size_t size) {
   if (!h || !buf) return fail(CUDAHM_EINVAL, "NULL argument");
   if (!h->data_set) return fail(CUDAHM_ESTATE, "restore needs set_data first");
   const size_t nchi = static_cast<size_t>(h->n) * h->d, nS = static_cast<size_t>(h->factor_n);
-  const size_t need = 8 * sizeof(int64_t) + sizeof(ChainState) + sizeof(double) * (nchi + nS);
+  const size_t nmom = h->mom ? 2 * nchi : 0;
+  const size_t need = 8 * sizeof(int64_t) + sizeof(ChainState) + sizeof(double) * (nchi + nS + nmom);
   if (size < need) return fail(CUDAHM_EINVAL, "checkpoint buffer too small");
   int64_t hdr[8];
   const char* c = static_cast<const char*>(buf);
@@ -1082,6 +1122,11 @@ int cudahm_restore(cudahm_t h, const void* buf, size_t size) {
   CU(cudaMemcpyAsync(h->chi, c, sizeof(double) * nchi, cudaMemcpyHostToDevice, h->stream));
   c += sizeof(double) * nchi;
   CU(cudaMemcpyAsync(h->S, c, sizeof(double) * nS, cudaMemcpyHostToDevice, h->stream));
+  if (nmom) {
+    c += sizeof(double) * nS;
+    CU(cudaMemcpyAsync(h->mom + static_cast<size_t>(cs.mom_sel) * nmom, c, sizeof(double) * nmom,
+                       cudaMemcpyHostToDevice, h->stream));
+  }
   CU(cudaStreamSynchronize(h->stream));
   h->sweeps = cs.sweeps;
   h->rows_last = 0;
@@ -1506,6 +1551,7 @@ size_t request_bytes(const cudahm_config& c, long long n_iter, long long thin) {
   b += static_cast<size_t>(kChunk) * (p + 3) * 8 + 64 * 1024;
   if (has_rule(c.model)) b += static_cast<size_t>(8 * 4096 + 2048 + 1024 * (kHDeg + 1)) * 8;  // rule, H table
   if (d == 3 && c.precision == CUDAHM_FP64) b += 3 * n * 8;  // Box-Muller spares
+  if (c.keep_chi_moments) b += 4 * d * n * 8;
   b += static_cast<size_t>(kMargNodeWords) * 8;
   return b;
 }
@@ -1707,6 +1753,7 @@ int cudahm_server_submit(cudahm_server_t sv, const cudahm_config* cfg, const dou
   if (cfg->device != sv->device) return fail(CUDAHM_EINVAL, "request device differs from the server's");
   if (cfg->trace_sweeps > 0) return fail(CUDAHM_EUNSUPPORTED, "served requests do not record traces");
   if (cfg->marginal) return fail(CUDAHM_EUNSUPPORTED, "served requests use the member form");
+  if (cfg->keep_chi_moments) return fail(CUDAHM_EUNSUPPORTED, "served requests return theta rows only");
   if (n_burn < 0 || n_iter < 0 || n_burn + n_iter < 1 || (n_iter > 0 && thin < 1))
     return fail(CUDAHM_EINVAL, "bad sweep counts");
   auto* r = new Request();

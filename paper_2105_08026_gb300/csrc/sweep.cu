@@ -10,7 +10,8 @@
 //   a6  LF: etabar(theta') pairs of the 2-D rule into a second exact sum (Sec. 4.2, eq. epdf)
 //   a5  block partials -> bounded grid barrier -> every block adds all partials
 //   a7  every block takes the same theta accept decision, RAM-updates S_theta
-//   a8  block 0 records the kept theta row
+//   a8  block 0 records the kept theta row; optionally every member adds its latent to its
+//       running moments (Welford)
 // Each thread keeps its K members (latent, RAM factor, cached e^chi and log l) in
 // registers for the whole launch; data are read once at launch start.
 #include <cmath>
@@ -184,7 +185,8 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   __shared__ ThetaCf s_tcf, s_tcpf;
   __shared__ double s_etabar, s_logeb, s_lpri, s_lpri_new, s_logalpha_prev;
   __shared__ int s_stop, s_pending_ram, s_fail;
-  __shared__ long long s_rows_written, s_tacc;
+  __shared__ long long s_rows_written, s_tacc, s_mom_n0;
+  __shared__ int s_mom_sel;
   __shared__ BlockRed s_red;
 
   const int tid = threadIdx.x;
@@ -232,6 +234,8 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     s_lpri = M::logprior(s_theta, a.mc, s_math);
     s_rows_written = 0;
     s_tacc = 0;
+    s_mom_n0 = a.chain->mom_n;
+    s_mom_sel = a.chain->mom_sel;
     s_stop = 0;
     s_pending_ram = 0;
     s_logalpha_prev = 0.0;
@@ -292,6 +296,9 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     }
   }
   unsigned int member_acc = 0;
+  const long long mom_n0 = s_mom_n0;
+  const int mom_sel = s_mom_sel;
+  long long mom_k = 0;  // kept sweeps of this launch
   __syncthreads();
   if (a.ns > 0)
     sweep_part_a<M, K, F32>(a, 0, nb0, nb1, chi, S, s_math, s_y, s_aux, s_zs, s_d32, s_pY, s_peY, s_pll, s_pu);
@@ -492,6 +499,15 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     }
     // arrive, prepare the next sweep's theta-independent half while the other blocks arrive, wait
     grid_arrive(a.bar, skip_me);
+    // a8 (optional): this sweep's latents into the running moments
+    if (a.mom != nullptr && kept_sweep(s, a.burn_left, a.keep_phase, a.thin)) {
+      const MomStep ms = mom_step(a, 1, mom_sel, mom_n0, ++mom_k);
+#pragma unroll
+      for (int m = 0; m < K; ++m) {
+        const unsigned int i = nb0 + tid + m * blockDim.x;
+        if (i < nb1) mom_add(ms, i, static_cast<double>(chi[m]));
+      }
+    }
     if (s + 1 < a.ns)
       sweep_part_a<M, K, F32>(a, s + 1, nb0, nb1, chi, S, s_math, s_y, s_aux, s_zs, s_d32, s_pY, s_peY, s_pll,
                               s_pu);
@@ -594,6 +610,10 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
       a.chain->sweeps = a.k0 + a.ns;
       a.chain->theta_acc += s_tacc;
       a.chain->rows = s_rows_written;
+      if (mom_k > 0) {  // commit the moments this launch wrote
+        a.chain->mom_n = mom_n0 + mom_k;
+        a.chain->mom_sel = 1 - mom_sel;
+      }
     }
   }
 }

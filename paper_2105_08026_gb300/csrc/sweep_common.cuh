@@ -624,6 +624,49 @@ __device__ __forceinline__ void etabar_terms(const ThetaC& tc, const SweepArgs& 
   }
 }
 
+// ------------------------------------------- running moments of the latents -
+// a8 (optional): every latent component's mean and sum of squared deviations M2 over the kept
+// sweeps, by Welford's (1962) recurrence: with x the m-th kept value,
+//   mean_m = mean_{m-1} + (x - mean_{m-1}) (1/m),  M2_m = M2_{m-1} + (x - mean_{m-1})(x - mean_m)
+// (the sample variance is M2/(m - 1)). The moments sit in two buffers of [mean[d][n], M2[d][n]]:
+// a launch reads the committed one (ChainState::mom_sel) at its first kept sweep, writes the
+// other, and commits that one at its successful end, so a failed launch leaves the committed
+// moments as they were, like the latents it did not write back.
+
+// Sweep s of a launch is kept when it lies past the burn-in and its post-burn index counts a
+// multiple of thin (the theta-row rule).
+__device__ __forceinline__ bool kept_sweep(long long s, long long burn_left, long long keep_phase, long long thin) {
+  const long long post = s - burn_left;
+  return post >= 0 && thin > 0 && ((keep_phase + post + 1) % thin) == 0;
+}
+
+struct MomStep {
+  const double* rd;  // mean at rd[q], M2 at rd[q + dn]
+  double* wr;
+  size_t dn;         // d n
+  double rn;         // 1/m
+};
+
+// The k-th kept sweep of a launch whose committed buffer is sel and holds m0 kept sweeps.
+__device__ __forceinline__ MomStep mom_step(const SweepArgs& a, int d, int sel, long long m0, long long k) {
+  const size_t dn = static_cast<size_t>(d) * static_cast<size_t>(a.n);
+  MomStep m;
+  m.dn = dn;
+  m.wr = a.mom + static_cast<size_t>(1 - sel) * 2 * dn;
+  m.rd = (k == 1) ? a.mom + static_cast<size_t>(sel) * 2 * dn : m.wr;
+  m.rn = 1.0 / static_cast<double>(m0 + k);
+  return m;
+}
+
+// Adds the kept value x of component entry q (j n + i).
+__device__ __forceinline__ void mom_add(const MomStep& m, size_t q, double x) {
+  const double mean = m.rd[q], m2 = m.rd[q + m.dn];
+  const double dl = x - mean;
+  const double mn = fma(dl, m.rn, mean);
+  m.wr[q] = mn;
+  m.wr[q + m.dn] = fma(dl, x - mn, m2);
+}
+
 // ------------------------------------------------- block reduce helpers ------
 struct BlockRed {
   Xacc d[32];

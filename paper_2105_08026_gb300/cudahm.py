@@ -57,6 +57,7 @@ class CudahmConfig(ctypes.Structure):
         ("barrier_timeout_ns", ctypes.c_int64),
         ("debug_skip_barrier_cta", ctypes.c_int32),
         ("marginal", ctypes.c_int32),
+        ("keep_chi_moments", ctypes.c_int32),
     ]
 
 
@@ -101,7 +102,7 @@ EXPORTED = [
     "cudahm_sizeof_config", "cudahm_sizeof_stats", "cudahm_last_error", "cudahm_destroy",
     "cudahm_lf_etabar_noalloc", "cudahm_batch_run", "cudahm_server_create", "cudahm_server_submit",
     "cudahm_server_poll", "cudahm_server_wait", "cudahm_server_result", "cudahm_server_stats",
-    "cudahm_server_destroy", "cudahm_ess", "cudahm_eval_marginal",
+    "cudahm_server_destroy", "cudahm_ess", "cudahm_eval_marginal", "cudahm_get_chi_moments",
 ]
 
 
@@ -149,6 +150,7 @@ def lib():
     L.cudahm_destroy.restype = None
     L.cudahm_ess.argtypes = [_dp, i64, i32, _dp]
     L.cudahm_eval_marginal.argtypes = [vp, _dp, _dp]
+    L.cudahm_get_chi_moments.argtypes = [vp, _dp, _dp, ctypes.POINTER(i64)]
     for name in EXPORTED:
         if name not in ("cudahm_config_init", "cudahm_sizeof_config", "cudahm_sizeof_stats", "cudahm_last_error",
                         "cudahm_destroy"):
@@ -219,6 +221,15 @@ def cudahm_get_chi(h, n: int, d: int):
     S = np.zeros(n * d * d)
     _check(lib().cudahm_get_chi(h, _dptr(chi), _dptr(S)))
     return chi, S
+
+
+def cudahm_get_chi_moments(h, n: int, d: int):
+    """(mean, var, count) of the latents over the kept sweeps; mean and var shaped (n, d)."""
+    mean = np.zeros(n * d)
+    var = np.zeros(n * d)
+    cnt = ctypes.c_int64(0)
+    _check(lib().cudahm_get_chi_moments(h, _dptr(mean), _dptr(var), ctypes.byref(cnt)))
+    return mean.reshape(n, d), var.reshape(n, d), cnt.value
 
 
 def cudahm_get_theta(h, p: int):
@@ -431,7 +442,7 @@ class Sampler:
                  target_accept: float = 0.4, theta_target_accept: float = 0.4, adapt_exponent: float = 2.0 / 3.0,
                  trace_sweeps: int = 0, device: int = 0, block_threads: int = 0, stream=None,
                  use_torch_allocator: bool = False, barrier_timeout_ns: int = 0, debug_skip_barrier_cta: int = -1,
-                 marginal: bool = False):
+                 marginal: bool = False, keep_chi_moments: bool = False):
         self.model, self.n = model, int(n)
         self.d, self.p = MODEL_D[model], MODEL_P[model]
         cfg = cudahm_config_init(model, n)
@@ -448,6 +459,7 @@ class Sampler:
         cfg.barrier_timeout_ns = barrier_timeout_ns
         cfg.debug_skip_barrier_cta = debug_skip_barrier_cta
         cfg.marginal = 1 if marginal else 0
+        cfg.keep_chi_moments = 1 if keep_chi_moments else 0
         for q, v in enumerate(_f64(theta_init)):
             cfg.theta_init[q] = v
         if theta_prop_scale is not None:
@@ -491,6 +503,11 @@ class Sampler:
     def chi(self):
         c, S = cudahm_get_chi(self.h, self.n, self.d)
         return c, S
+
+    def chi_moments(self):
+        """(mean, var, count): each latent component's mean and sample variance over the kept
+        sweeps, shaped (n, d) (needs keep_chi_moments)."""
+        return cudahm_get_chi_moments(self.h, self.n, self.d)
 
     def theta(self):
         return cudahm_get_theta(self.h, self.p)

@@ -72,6 +72,9 @@ def test_config_defaults(lib):
     (lambda c: [setattr(c, "marginal", 1), setattr(c, "model", cudahm.NN3), setattr(c, "d", 3),
                 [c.model_consts.__setitem__(q, v) for q, v in enumerate((1.0, 0.0, 1.0, 0.0, 0.0, 1.0))]] and None,
      cudahm.EUNSUPPORTED),  # the marginal form integrates 1-D latents only
+    (lambda c: setattr(c, "keep_chi_moments", 3), cudahm.EINVAL),
+    (lambda c: [setattr(c, "keep_chi_moments", 1), setattr(c, "marginal", 1)] and None,
+     cudahm.EINVAL),  # the marginal form has no latents
 ])
 def test_invalid_configs_rejected(lib, mutate, code):
     cfg = cudahm.cudahm_config_init(cudahm.NN1, 100)
