@@ -88,6 +88,8 @@ def lib():
                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _dp, _i64p, _i64p, _i64p,
                                    ctypes.c_int64, _dp, _dp, _u8p, _dp, _dp, _dp, _dp, _u8p, _dp, _dp, _dp, _i64p])
             L.orc_run.restype = ctypes.c_int
+            L.orc_twostate_run.argtypes = [ctypes.c_double, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, _i64p]
+            L.orc_twostate_run.restype = None
             L.orc_marg_logp.argtypes = [ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp]
             L.orc_marg_run.argtypes = ([ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp,
                                         ctypes.c_uint64, _dp, _dp, _dp, _i64p, _dp, ctypes.c_int64, ctypes.c_int64,
@@ -309,6 +311,14 @@ class MarginalChain:
         if rc != 0:
             raise RuntimeError(f"oracle marginal run failed: {rc}")
         return rows[: rows_out.value].copy(), tr
+
+
+def twostate_counts(pi1, n, sweeps, seed):
+    """Transition counts [[0->0, 0->1], [1->0, 1->1]] of n two-state chains run with the member
+    step's accept rule (Sec. 2.2), target (1 - pi1, pi1), flip proposal, for `sweeps` steps."""
+    c = np.zeros(4, dtype=np.int64)
+    lib().orc_twostate_run(float(pi1), int(n), int(sweeps), int(seed), c.ctypes.data_as(_i64p))
+    return c.reshape(2, 2)
 
 
 # ---------------------------------------------------------------- chain ----

@@ -722,6 +722,30 @@ int orc_run(int model, int d, int p, int64_t n, const double* y, const double* a
 }
 
 /* ------------------------------------------------------------------------- */
+/* Test model of the member accept rule (Sec. 2.2: accept with probability     */
+/* min(1, pi(Y)/pi(X)); R4: accept iff ln u < Delta). n independent chains on   */
+/* the states {0, 1} with target (1 - pi1, pi1); every step proposes the other  */
+/* state (symmetric flip), Delta = ln pi(other) - ln pi(current), u the accept  */
+/* uniform of a d = 1 member of that sweep (orc_draw_member). Chain i starts in */
+/* state i mod 2. counts[2 from + to] sums the transitions.                      */
+/* ------------------------------------------------------------------------- */
+void orc_twostate_run(double pi1, int64_t n, int64_t sweeps, uint64_t seed, int64_t* counts) {
+  const double lp[2] = {log(1.0 - pi1), log(pi1)};
+  for (int q = 0; q < 4; ++q) counts[q] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int x = (int)(i & 1);
+    for (int64_t k = 1; k <= sweeps; ++k) {
+      double z, u;
+      orc_draw_member(seed, (uint32_t)i, (uint32_t)k, 1, &z, &u);
+      const double delta = lp[1 - x] - lp[x];
+      const int y = (log(u) < delta) ? 1 - x : x;
+      counts[2 * x + y]++;
+      x = y;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Latent marginalisation by cubature (Sec. 6: for low-dimensional latents the  */
 /* members can be integrated out by quadrature, leaving an MCMC over theta      */
 /* alone). Reading R9 fixes the rule:                                           */
