@@ -245,6 +245,19 @@ int cudahm_eval_logdens(cudahm_t h, const double* theta_host, double* lp_host);
  * binary32 variant: its FP32 handles integrate in binary64. */
 int cudahm_eval_marginal(cudahm_t h, const double* theta_host, double* lp_host);
 
+/* Test model of the member accept rule (Sec. 2.2: accept with probability min(1, pi(Y)/pi(X))).
+ * Runs n_chains independent chains on two states with target (1 - pi1, pi1) for `sweeps` steps;
+ * every step proposes the other state and applies the member step's own device accept routine
+ * with Delta = ln pi(other) - ln pi(current) and the member's own accept uniform of that sweep
+ * (FP64: Philox block (1, stream 0, chain, sweep), the uniform of every d = 1 member; FP32: the
+ * bulk form's binary32 uniform and expf). Chain i starts in state i mod 2. counts_host receives
+ * 4 int64: the transitions 0->0, 0->1, 1->0, 1->1 summed over chains and sweeps. For such chains
+ * P01 = min(1, pi1/pi0), P10 = min(1, pi0/pi1) and pi0 P01 = pi1 P10 (detailed balance). Needs
+ * no handle; allocates and frees its own device buffers on `device`. EINVAL for pi1 outside
+ * (0, 1), an unknown precision, n_chains outside [1, 2^31] or sweeps outside [1, 2^32 - 2]. */
+int cudahm_twostate_run(double pi1, int32_t precision, int64_t n_chains, int64_t sweeps, uint64_t seed,
+                        int32_t device, int64_t* counts_host);
+
 /* LF and BB1: the selection integral etabar(theta) of the handle's rule at the given theta. */
 int cudahm_eval_etabar(cudahm_t h, const double* theta_host, double* out);
 

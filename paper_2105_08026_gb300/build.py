@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libcudahm.so")
 PEAKS_LIB = os.path.join(LIBDIR, "libchm_peaks.so")
-SOURCES = ["sweep.cu", "batch.cu", "runtime.cu", "noalloc.cu", "diag.cu", "marginal.cu"]
+SOURCES = ["sweep.cu", "batch.cu", "runtime.cu", "noalloc.cu", "diag.cu", "marginal.cu", "twostate.cu"]
 PEAKS_SOURCES = ["pipe_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", f"-I{INCLUDE}", f"-I{CSRC}"]

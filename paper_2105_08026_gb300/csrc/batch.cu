@@ -91,9 +91,8 @@ __device__ __forceinline__ void member_f64(const SweepArgs& a, unsigned int i, u
     lfY = M::logf(Y, eY, tc);
     delta = (llY + lfY) - (ll + lfX);
   }
-  const bool dneg = dsign(delta);
-  const double alpha = dneg ? exp_tab(delta, s_math) : 1.0;
-  const bool acc = !dneg || (__double_as_longlong(u) < __double_as_longlong(alpha));
+  double alpha;
+  const bool acc = mh_accept(delta, u, s_math, alpha);
   if (disnan(delta)) nan_cnt++;
   const double lf_cur = acc ? lfY : lfX;
   if (acc) {
@@ -153,8 +152,8 @@ __device__ __forceinline__ void member_f32(const SweepArgs& a, unsigned int i, u
     lfY = M::logf32(Y, tf);
     delta = (M::loglike32(Y, d) + lfY) - (ll + lfX);
   }
-  const float alpha = (delta >= 0.0f) ? 1.0f : expf(delta);
-  const bool acc = (delta >= 0.0f) || (u < alpha);
+  float alpha;
+  const bool acc = mh_accept32(delta, u, alpha);
   if (delta != delta) nan_cnt++;
   const float lf_cur = acc ? lfY : lfX;
   if (acc) {
@@ -231,9 +230,8 @@ __device__ __forceinline__ void member3_f64(const SweepArgs& a, unsigned int i, 
   const double Y[3] = {x[0] + v0, x[1] + v1, x[2] + v2};
   const double lfX = M::logf(x, tc), lfY = M::logf(Y, tc);
   const double delta = (M::loglike(Y, y, w) + lfY) - (M::loglike(x, y, w) + lfX);
-  const bool dneg = dsign(delta);
-  const double alpha = dneg ? exp_tab(delta, s_math) : 1.0;
-  const bool acc = !dneg || (__double_as_longlong(u) < __double_as_longlong(alpha));
+  double alpha;
+  const bool acc = mh_accept(delta, u, s_math, alpha);
   if (disnan(delta)) nan_cnt++;
   double lf_cur = lfX;
   if (acc) {
@@ -313,8 +311,8 @@ __device__ __forceinline__ void member3_f32(const SweepArgs& a, unsigned int i, 
                       __fadd_rn(x[2], static_cast<float>(v2))};
   const float lfX = M::logf32(x, tf), lfY = M::logf32(Y, tf);
   const float delta = __fsub_rn(__fadd_rn(M::loglike32(Y, d), lfY), __fadd_rn(M::loglike32(x, d), lfX));
-  const float alpha = (delta >= 0.0f) ? 1.0f : expf(delta);
-  const bool acc = (delta >= 0.0f) || (u < alpha);
+  float alpha;
+  const bool acc = mh_accept32(delta, u, alpha);
   if (delta != delta) nan_cnt++;
   float lf_cur = lfX;
   if (acc) {

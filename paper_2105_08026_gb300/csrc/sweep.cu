@@ -353,8 +353,8 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
             lfY = M::logf32(Y, tf);
             delta = (llY + lfY) - (ll[m] + lfX);
           }
-          const float alpha = (delta >= 0.0f) ? 1.0f : expf(delta);
-          const bool acc = (delta >= 0.0f) || (u < alpha);
+          float alpha;
+          const bool acc = mh_accept32(delta, u, alpha);
           if (delta != delta) member_nan++;
           if (acc) {
             chi[m] = Y;
@@ -390,9 +390,8 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
             lfY = M::logf(Y, eY, tc);
             delta = (llY + lfY) - (ll[m] + lfX);
           }
-          const bool dneg = dsign(delta);  // -inf and -0 included; NaN is counted below
-          const double alpha = dneg ? exp_tab(delta, s_math) : 1.0;
-          const bool acc = !dneg || (__double_as_longlong(u) < __double_as_longlong(alpha));  // both >= +0
+          double alpha;
+          const bool acc = mh_accept(delta, u, s_math, alpha);  // NaN is counted below
           if (disnan(delta)) member_nan++;
           if (acc) {
             chi[m] = Y;

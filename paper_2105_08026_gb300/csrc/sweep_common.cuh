@@ -624,6 +624,22 @@ __device__ __forceinline__ void etabar_terms(const ThetaC& tc, const SweepArgs& 
   }
 }
 
+// ------------------------------------------------------ member accept rule ---
+// The member step's Metropolis accept (Sec. 2.2; strict, as ln u < Delta): alpha = min(1, e^Delta)
+// (0 at Delta = -inf), accepted iff u < alpha. Binary64: every Delta with its sign bit clear
+// accepts; otherwise u and alpha are both >= +0, so their bit patterns order as their values.
+// Binary32 (bulk form): the same rule with expf.
+__device__ __forceinline__ bool mh_accept(double delta, double u, const double* s_math, double& alpha) {
+  const bool dneg = dsign(delta);  // -inf and -0 included
+  alpha = dneg ? exp_tab(delta, s_math) : 1.0;
+  return !dneg || (__double_as_longlong(u) < __double_as_longlong(alpha));
+}
+
+__device__ __forceinline__ bool mh_accept32(float delta, float u, float& alpha) {
+  alpha = (delta >= 0.0f) ? 1.0f : expf(delta);
+  return (delta >= 0.0f) || (u < alpha);
+}
+
 // ------------------------------------------- running moments of the latents -
 // a8 (optional): every latent component's mean and sum of squared deviations M2 over the kept
 // sweeps, by Welford's (1962) recurrence: with x the m-th kept value,

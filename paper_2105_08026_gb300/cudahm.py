@@ -103,6 +103,7 @@ EXPORTED = [
     "cudahm_lf_etabar_noalloc", "cudahm_batch_run", "cudahm_server_create", "cudahm_server_submit",
     "cudahm_server_poll", "cudahm_server_wait", "cudahm_server_result", "cudahm_server_stats",
     "cudahm_server_destroy", "cudahm_ess", "cudahm_eval_marginal", "cudahm_get_chi_moments",
+    "cudahm_twostate_run",
 ]
 
 
@@ -151,6 +152,7 @@ def lib():
     L.cudahm_ess.argtypes = [_dp, i64, i32, _dp]
     L.cudahm_eval_marginal.argtypes = [vp, _dp, _dp]
     L.cudahm_get_chi_moments.argtypes = [vp, _dp, _dp, ctypes.POINTER(i64)]
+    L.cudahm_twostate_run.argtypes = [ctypes.c_double, i32, i64, i64, ctypes.c_uint64, i32, ctypes.POINTER(i64)]
     for name in EXPORTED:
         if name not in ("cudahm_config_init", "cudahm_sizeof_config", "cudahm_sizeof_stats", "cudahm_last_error",
                         "cudahm_destroy"):
@@ -230,6 +232,15 @@ def cudahm_get_chi_moments(h, n: int, d: int):
     cnt = ctypes.c_int64(0)
     _check(lib().cudahm_get_chi_moments(h, _dptr(mean), _dptr(var), ctypes.byref(cnt)))
     return mean.reshape(n, d), var.reshape(n, d), cnt.value
+
+
+def cudahm_twostate_run(pi1: float, precision: int, n_chains: int, sweeps: int, seed: int = 1,
+                        device: int = 0) -> np.ndarray:
+    """Transition counts [[0->0, 0->1], [1->0, 1->1]] of the two-state test model of the accept rule."""
+    c = (ctypes.c_int64 * 4)()
+    _check(lib().cudahm_twostate_run(float(pi1), int(precision), int(n_chains), int(sweeps),
+                                     int(seed) & 0xFFFFFFFFFFFFFFFF, int(device), c))
+    return np.array(list(c), dtype=np.int64).reshape(2, 2)
 
 
 def cudahm_get_theta(h, p: int):
