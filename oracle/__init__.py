@@ -86,7 +86,8 @@ def lib():
             L.orc_run.argtypes = ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp,
                                    ctypes.c_uint64, _dp, _dp, _dp, _dp, _i64p, _dp,
                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _dp, _i64p, _i64p, _i64p,
-                                   ctypes.c_int64, _dp, _dp, _u8p, _dp, _dp, _dp, _dp, _u8p, _dp, _dp, _dp, _i64p])
+                                   ctypes.c_int64, _dp, _dp, _u8p, _dp, _dp, _dp, _dp, _u8p, _dp, _dp, _dp, _dp,
+                                   _i64p])
             L.orc_run.restype = ctypes.c_int
             L.orc_twostate_run.argtypes = [ctypes.c_double, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, _i64p]
             L.orc_twostate_run.restype = None
@@ -353,6 +354,8 @@ class Chain:
         self.mom_mean = np.zeros(self.n * self.d) if keep_chi_moments else None
         self.mom_m2 = np.zeros(self.n * self.d) if keep_chi_moments else None
         self.mom_n = ctypes.c_int64(0)
+        # theta RAM update pending from the last sweep (applied one sweep late): U, alpha, eta
+        self.theta_pend = np.zeros(self.p + 2)
 
     def moments(self):
         """(mean, var, count): per-member mean and sample variance (M2/(count - 1), 0 for one
@@ -380,7 +383,7 @@ class Chain:
                            self.seed, _p(self.chi), _p(self.S), _p(self.theta), _p(self.S_theta),
                            ctypes.byref(self.sweep), ctypes.byref(self.etabar), n_burn, n_iter, thin, _p(rows),
                            ctypes.byref(rows_out), ctypes.byref(self.member_accepts),
-                           ctypes.byref(self.theta_accepts), T, *args_tr,
+                           ctypes.byref(self.theta_accepts), T, *args_tr, _p(self.theta_pend),
                            _p(self.mom_mean) if self.mom_mean is not None else None,
                            _p(self.mom_m2) if self.mom_m2 is not None else None, ctypes.byref(self.mom_n))
         if rc != 0:

@@ -30,8 +30,12 @@
  *   R1 RAM index: sweep k = 1, 2, ... uses eta = (k+1)^(-gamma) (S_1 given, first
  *      update produces S_2).
  *   R2 adaptation runs through burn-in and sampling alike.
- *   R3 theta proposal: RAM on theta with the same eta and its own target acceptance;
- *      adapt_theta = 0 gives plain random-walk MH with fixed S_theta.
+ *   R3 theta proposal: RAM on theta with the same eta and its own target acceptance,
+ *      each step's update applied one sweep late: the proposal of sweep k + 1 uses the
+ *      factor updated with the steps up to k - 1 (S_{k+1} = RAM(S_k, U_{k-1}, alpha_{k-1},
+ *      eta_{k-1})), so that it can be formed before sweep k's accept decision (the marginal
+ *      form keeps the undelayed update); adapt_theta = 0 gives plain random-walk MH with
+ *      fixed S_theta.
  *   R4 accept iff ln u < Delta (strict), alpha = exp(min(0, Delta)), alpha = 0 off support.
  *   R5 random numbers: Philox4x32-10 (Salmon et al., SC'11), key = (seed lo, seed hi),
  *      counter = (block j, stream s, object i, sweep k); uniform u = (2m+1) 2^-53 with
@@ -594,6 +598,9 @@ int orc_run(int model, int d, int p, int64_t n, const double* y, const double* a
             int64_t trace_sweeps, double* tr_delta, double* tr_u, uint8_t* tr_acc,
             double* tr_theta_prop, double* tr_D, double* tr_logalpha, double* tr_utheta, uint8_t* tr_tacc,
             double* tr_etabar,
+            /* theta RAM update pending from the previous sweep (R3), kept across calls:
+               [U (p), alpha, eta]; eta = 0: none */
+            double* theta_pend,
             /* optional running moments of the latents over the kept sweeps (n*d each, member-major,
                continued across calls; mom_n = kept sweeps so far); NULL mom_mean: off */
             double* mom_mean, double* mom_m2, int64_t* mom_n) {
@@ -692,7 +699,13 @@ int orc_run(int model, int d, int p, int64_t n, const double* y, const double* a
         if (has_rule) *etabar_cur = eb_new;
         ++tacc;
       }
-      if (prm.adapt_theta) orc_ram_update(p, S_theta, U, alpha, prm.theta_target_accept, eta);
+      if (prm.adapt_theta) { /* R3: apply the previous step's update, keep this one for the next sweep */
+        if (theta_pend[p + 1] > 0.0)
+          orc_ram_update(p, S_theta, theta_pend, theta_pend[p], prm.theta_target_accept, theta_pend[p + 1]);
+        for (int a = 0; a < p; ++a) theta_pend[a] = U[a];
+        theta_pend[p] = alpha;
+        theta_pend[p + 1] = eta;
+      }
     }
 
     /* (3) record kept sweeps: the theta row and, when asked, every latent component's running
