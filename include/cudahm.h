@@ -131,7 +131,9 @@ typedef struct {
   void* alloc_ctx;               /* passed back to dev_alloc / dev_free */
   int64_t barrier_timeout_ns;    /* bound on every device-side wait; 0 = 2 s */
   int32_t debug_skip_barrier_cta;/* >= 0: that block never arrives at the grid barrier (tests the
-                                    timeout path); -1 = off */
+                                    timeout path); -1 = off. Block 0 of a multi-block sweep launch
+                                    holds no members and never arrives anyway (it proposes theta'
+                                    and decides), so pick a block >= 1 there */
   int32_t marginal;              /* 1: integrate each member's latent out by cubature and run the
                                     chain on theta alone (NN1, LF, BB1; see cudahm_eval_marginal) */
   int32_t keep_chi_moments;      /* 1: keep every latent component's running mean and variance over

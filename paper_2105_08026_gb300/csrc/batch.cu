@@ -355,6 +355,7 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
   __shared__ TC s_tc, s_tcp;
   __shared__ TCf s_tcf, s_tcpf;
   __shared__ double s_etabar, s_logeb, s_lpri, s_lpri_new;
+  __shared__ double s_pendU[kMaxP], s_pend_alpha, s_pend_eta;
   __shared__ int s_stop;
   __shared__ long long s_rows_written, s_tacc, s_k0, s_off, s_ns, s_mom_n0;
   __shared__ int s_mom_sel;
@@ -381,6 +382,9 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
     s_tacc = 0;
     s_mom_n0 = a.chain->mom_n;
     s_mom_sel = a.chain->mom_sel;
+    for (int q = 0; q < p; ++q) s_pendU[q] = a.chain->pend_U[q];
+    s_pend_alpha = a.chain->pend_alpha;
+    s_pend_eta = a.chain->pend_eta;
     s_stop = 0;
   }
   __syncthreads();
@@ -528,9 +532,11 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
             }
             s_tacc++;
           }
-          if (a.adapt_theta) {
-            const double alpha = (logalpha >= 0.0) ? 1.0 : exp_tab(logalpha, s_math);
-            ram_update_theta(p, s_Sth, a.tab_U + s * p, alpha, a.astar_theta, eta);
+          if (a.adapt_theta) {  // the previous step's RAM update; this step's waits one sweep
+            if (s_pend_eta > 0.0) ram_update_theta(p, s_Sth, s_pendU, s_pend_alpha, a.astar_theta, s_pend_eta);
+            s_pend_alpha = (logalpha >= 0.0) ? 1.0 : exp_tab(logalpha, s_math);
+            for (int q = 0; q < p; ++q) s_pendU[q] = __ldg(a.tab_U + s * p + q);
+            s_pend_eta = eta;
           }
           const long long post = s - burn_left;
           if (post >= 0 && prog->thin > 0 && ((post + 1) % prog->thin) == 0) {
@@ -554,6 +560,9 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
     if (lb == 0) {
       for (int q = 0; q < p; ++q) a.chain->theta[q] = s_theta[q];
       for (int q = 0; q < p * p; ++q) a.chain->S_theta[q] = s_Sth[q];
+      for (int q = 0; q < p; ++q) a.chain->pend_U[q] = s_pendU[q];
+      a.chain->pend_alpha = s_pend_alpha;
+      a.chain->pend_eta = s_pend_eta;
       a.chain->etabar = s_etabar;
       a.chain->sweeps = k0 + ns;
       a.chain->theta_acc += s_tacc;

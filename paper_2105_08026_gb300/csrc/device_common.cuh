@@ -215,7 +215,7 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
 // A grid-wide barrier in two halves, so that a block can work between its arrival and the
 // others': grid_arrive (all threads of the block; thread 0 publishes the block's writes and
 // counts it in) and grid_wait (all threads; thread 0 waits, bounded, until barrier `index` has
-// every block). grid_barrier below is the two back to back.
+// every block, or the first nb arrivals when nb > 0). grid_barrier below is the two back to back.
 __device__ __forceinline__ void grid_arrive(unsigned int* count, bool skip_arrival) {
   __syncthreads();
   if (threadIdx.x == 0 && !skip_arrival) {
@@ -223,11 +223,12 @@ __device__ __forceinline__ void grid_arrive(unsigned int* count, bool skip_arriv
     atomicAdd(count, 1u);
   }
 }
-__device__ __forceinline__ bool grid_wait(unsigned int* count, unsigned int index, int* err, long long limit_ns) {
+__device__ __forceinline__ bool grid_wait(unsigned int* count, unsigned int index, int* err, long long limit_ns,
+                                          unsigned int nb = 0u) {
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned int target = (index + 1u) * gridDim.x;
+    const unsigned int target = (index + 1u) * (nb ? nb : gridDim.x);
     const long long t0 = globaltimer_ns();
     while (true) {
       if (ld_acquire_u32(count) >= target) break;

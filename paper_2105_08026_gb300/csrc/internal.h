@@ -20,6 +20,11 @@ struct ChainState {
   int mcur;          // marginal form: which of the two log p_i arrays holds the current theta's
   int mom_sel;       // running moments of the latents: which of the two buffers is committed
   long long mom_n;   // kept sweeps accumulated in the committed moments
+  // member form: the theta RAM update of the last sweep, applied one sweep late (U, alpha, eta;
+  // pend_eta = 0: none)
+  double pend_U[kMaxP];
+  double pend_alpha;
+  double pend_eta;
 };
 
 // Model constants used inside kernels.

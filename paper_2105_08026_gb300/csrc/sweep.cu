@@ -183,8 +183,16 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   __shared__ double s_theta[kMaxP], s_thp[kMaxP], s_Sth[kMaxP * kMaxP];
   __shared__ ThetaC s_tc, s_tcp;
   __shared__ ThetaCf s_tcf, s_tcpf;
-  __shared__ double s_etabar, s_logeb, s_lpri, s_lpri_new, s_logalpha_prev;
-  __shared__ int s_stop, s_pending_ram, s_fail;
+  __shared__ double s_etabar, s_logeb, s_lpri, s_lpri_new;
+  __shared__ int s_stop, s_fail, s_acc_prev;
+  // the theta RAM update pending from the previous sweep (applied one sweep late): U (s_pend_idx
+  // >= 0: row s_pend_idx of this launch's table, else s_pendU), alpha (from s_pend_lal when
+  // s_pend_from_lal), eta (0: none)
+  __shared__ double s_pendU[kMaxP], s_pend_alpha, s_pend_lal, s_pend_eta;
+  __shared__ long long s_pend_idx;
+  __shared__ int s_pend_from_lal;
+  // block 0: the next sweep's proposal for a rejected [0] and an accepted [1] theta'
+  __shared__ ThetaPub s_cand[2];
   __shared__ long long s_rows_written, s_tacc, s_mom_n0;
   __shared__ int s_mom_sel;
   __shared__ BlockRed s_red;
@@ -199,6 +207,9 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   const unsigned int mb0 = (gridDim.x > 1) ? 1u : 0u;
   const unsigned int mgrid = gridDim.x - mb0, mblk = blockIdx.x - mb0;
   const bool leader_only = (mb0 == 1u && blockIdx.x == 0);
+  // blocks that meet at the grid barrier and hold a partial: the member blocks (block 0, when it
+  // holds no members, only proposes and decides: it waits at the barrier without arriving)
+  const unsigned int nbar = gridDim.x - mb0;
   const unsigned int nb0 = leader_only ? 0u : static_cast<unsigned int>((a.n * mblk) / mgrid);
   const unsigned int nb1 = leader_only ? 0u : static_cast<unsigned int>((a.n * (mblk + 1)) / mgrid);
   const bool skip_me = (a.skip_cta == static_cast<int>(blockIdx.x));
@@ -237,9 +248,14 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     s_mom_n0 = a.chain->mom_n;
     s_mom_sel = a.chain->mom_sel;
     s_stop = 0;
-    s_pending_ram = 0;
-    s_logalpha_prev = 0.0;
     s_fail = 0;
+    s_acc_prev = 0;
+    for (int q = 0; q < p; ++q) s_pendU[q] = a.chain->pend_U[q];
+    s_pend_alpha = a.chain->pend_alpha;
+    s_pend_eta = a.adapt_theta ? a.chain->pend_eta : 0.0;
+    s_pend_lal = 0.0;
+    s_pend_idx = -1;
+    s_pend_from_lal = 0;
     s_tcf = M::consts32(s_tc);
     // theta' of the first sweep: proposed by block 0 and fetched by the others
     double lp = -INFINITY;
@@ -308,22 +324,20 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     const bool trace = (a.trace_off + s) < a.trace_T;
     unsigned int member_nan = 0;
 
-    // deferred theta work of the previous sweep and the proposal of this one (last warp)
+    // theta' of this sweep (last warp): one proposal per sweep for the grid, prepared by block 0
+    // during the previous sweep for either outcome of its decision, picked and published here,
+    // fetched by the other blocks (whose FP64 units are left to the members)
     if (s > 0 && wid == ctrl_warp) {
       if (lane == 0) {
-        // one proposal (and one RAM update of S_theta) per sweep for the grid, made and published
-        // by block 0, fetched by the other blocks (whose FP64 units are then left to the members)
         double lp = -INFINITY;
         ThetaC tcp{};
         ThetaCf tcpf{};
         if (blockIdx.x == 0) {
-          if (s_pending_ram) {
-            const double lal = s_logalpha_prev;
-            const double alpha = (lal >= 0.0) ? 1.0 : exp_tab(lal, s_math);
-            ram_update_theta(p, s_Sth, a.tab_U + (s - 1) * p, alpha, a.astar_theta, __ldg(a.tab_eta + s - 1));
-          }
-          propose_theta<M>(a, s, p, s_theta, s_Sth, s_thp, lp, tcp, s_math);
-          tcpf = M::consts32(tcp);
+          const ThetaPub& c = s_cand[s_acc_prev];
+          for (int q = 0; q < p; ++q) s_thp[q] = c.thp[q];
+          lp = c.lpri_new;
+          tcp = c.tcp;
+          tcpf = c.tcpf;
           publish_theta(a, static_cast<unsigned int>(s + 1), s_thp, p, lp, tcp, tcpf);
         } else if (!fetch_theta(a, static_cast<unsigned int>(s + 1), s_thp, p, lp, tcp, tcpf)) {
           lp = -INFINITY;  // the run has failed; the next barrier returns
@@ -458,7 +472,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
       }
     }
     if constexpr (is_lf)
-      if (prior_ok) etabar_terms<M>(tcp, a, blockIdx.x, gridDim.x, s_math, xe, fe);
+      if (prior_ok && !leader_only) etabar_terms<M>(tcp, a, mblk, mgrid, s_math, xe, fe);
 
     // a5: block partial
     {
@@ -483,7 +497,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
           for (int q = 0; q < 4; ++q) bf[q] = s_red.f[lane][q];
         }
         warp_reduce(bd, be, bf);
-        if (lane == 0) {
+        if (lane == 0 && !leader_only) {
           unsigned long long* dst = a.partials + ((s & 1) * gridDim.x + blockIdx.x) * kPartWords;
           __stcg(dst + 0, bd.w0);
           __stcg(dst + 1, bd.w1);
@@ -497,7 +511,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
       }
     }
     // arrive, prepare the next sweep's theta-independent half while the other blocks arrive, wait
-    grid_arrive(a.bar, skip_me);
+    grid_arrive(a.bar, skip_me || leader_only);
     // a8 (optional): this sweep's latents into the running moments
     if (a.mom != nullptr && kept_sweep(s, a.burn_left, a.keep_phase, a.thin)) {
       const MomStep ms = mom_step(a, 1, mom_sel, mom_n0, ++mom_k);
@@ -510,13 +524,34 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     if (s + 1 < a.ns)
       sweep_part_a<M, K, F32>(a, s + 1, nb0, nb1, chi, S, s_math, s_y, s_aux, s_zs, s_d32, s_pY, s_peY, s_pll,
                               s_pu);
-    if (!grid_wait(a.bar, static_cast<unsigned int>(s), a.err, a.timeout_ns)) return;
+    // block 0, while the member blocks work: the theta step's serial part, off the path between
+    // the decision and the next proposal. The RAM update of S_theta pending from the previous
+    // sweep (each step's update is applied one sweep late), then the next sweep's proposal
+    // theta + S_theta U for theta = this sweep's theta (rejected; one warp) and theta'
+    // (accepted; another warp, on another SM sub-partition's FP64 unit).
+    if (blockIdx.x == 0) {
+      if (wid == ctrl_warp && lane == 0 && s_pend_eta > 0.0) {
+        const double lal = s_pend_lal;
+        const double alpha = s_pend_from_lal ? ((lal >= 0.0) ? 1.0 : exp_tab(lal, s_math)) : s_pend_alpha;
+        const double* U = (s_pend_idx >= 0) ? a.tab_U + s_pend_idx * p : s_pendU;
+        ram_update_theta(p, s_Sth, U, alpha, a.astar_theta, s_pend_eta);
+        s_pend_eta = 0.0;
+      }
+      __syncthreads();
+      if (s + 1 < a.ns && lane == 0 && (wid == ctrl_warp || wid == ctrl_warp - 1)) {
+        const int c = (wid == ctrl_warp) ? 1 : 0;
+        ThetaPub& o = s_cand[c];
+        propose_theta<M>(a, s + 1, p, c ? s_thp : s_theta, s_Sth, o.thp, o.lpri_new, o.tcp, s_math);
+        o.tcpf = M::consts32(o.tcp);
+      }
+    }
+    if (!grid_wait(a.bar, static_cast<unsigned int>(s), a.err, a.timeout_ns, nbar)) return;
 
     // a7: every block sums all partials and takes the same decision
     {
       Xacc D, E;
       unsigned int f[4];
-      sum_partials(a.partials + (s & 1) * gridDim.x * kPartWords, static_cast<int>(gridDim.x), s_red, D, E, f);
+      sum_partials(a.partials + ((s & 1) * gridDim.x + mb0) * kPartWords, static_cast<int>(nbar), s_red, D, E, f);
       if (tid == 0) {
         const long long sg = a.trace_off + s;  // sweep index within this run
         if (f[1] != 0u) {
@@ -564,8 +599,13 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
             }
             s_tacc++;
           }
-          s_logalpha_prev = logalpha;
-          s_pending_ram = a.adapt_theta;
+          s_acc_prev = acc ? 1 : 0;
+          if (a.adapt_theta) {  // this step's RAM update, applied during the next sweep
+            s_pend_lal = logalpha;
+            s_pend_from_lal = 1;
+            s_pend_idx = s;
+            s_pend_eta = __ldg(a.tab_eta + s);
+          }
           // a8: record kept sweeps
           const long long post = s - a.burn_left;
           if (post >= 0 && a.thin > 0 && ((a.keep_phase + post + 1) % a.thin) == 0) {
@@ -598,11 +638,12 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   if (tid == 0) {
     atomicAdd(reinterpret_cast<unsigned long long*>(&a.chain->member_acc), static_cast<unsigned long long>(s_macc));
     if (blockIdx.x == 0) {
-      if (s_pending_ram && a.ns > 0) {  // RAM update of the last sweep's theta step
-        const double lal = s_logalpha_prev;
-        const double alpha = (lal >= 0.0) ? 1.0 : exp_tab(lal, s_math);
-        ram_update_theta(p, s_Sth, a.tab_U + (a.ns - 1) * p, alpha, a.astar_theta, __ldg(a.tab_eta + a.ns - 1));
-      }
+      // the last step's RAM update stays pending for the next launch
+      const double lal = s_pend_lal;
+      for (int q = 0; q < p; ++q)
+        a.chain->pend_U[q] = (s_pend_idx >= 0) ? __ldg(a.tab_U + s_pend_idx * p + q) : s_pendU[q];
+      a.chain->pend_alpha = s_pend_from_lal ? ((lal >= 0.0) ? 1.0 : exp_tab(lal, s_math)) : s_pend_alpha;
+      a.chain->pend_eta = s_pend_eta;
       for (int q = 0; q < p; ++q) a.chain->theta[q] = s_theta[q];
       for (int q = 0; q < p * p; ++q) a.chain->S_theta[q] = s_Sth[q];
       a.chain->etabar = s_etabar;

@@ -212,7 +212,7 @@ def test_failed_run_commits_no_moments():
     data = synth.nn1_data(4000, seed=15)
     theta0, scale, consts = synth.nn1_settings(data)
     s = cudahm.Sampler(cudahm.NN1, 4000, theta_init=theta0, theta_prop_scale=scale, model_consts=consts,
-                       barrier_timeout_ns=200_000_000, debug_skip_barrier_cta=0, keep_chi_moments=True)
+                       barrier_timeout_ns=200_000_000, debug_skip_barrier_cta=1, keep_chi_moments=True)
     s.set_data(data.y, data.sigma)
     with pytest.raises(cudahm.CudahmError) as ei:
         s.run(0, 10)

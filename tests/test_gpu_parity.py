@@ -220,7 +220,7 @@ def test_barrier_timeout_reports_error_and_context_survives():
     data = synth.nn1_data(4000, seed=15)
     theta0, scale, consts = synth.nn1_settings(data)
     s = cudahm.Sampler(cudahm.NN1, 4000, theta_init=theta0, theta_prop_scale=scale, model_consts=consts,
-                       barrier_timeout_ns=200_000_000, debug_skip_barrier_cta=0)
+                       barrier_timeout_ns=200_000_000, debug_skip_barrier_cta=1)
     s.set_data(data.y, data.sigma)
     chi_before = s.chi()[0]
     with pytest.raises(cudahm.CudahmError) as ei:
