@@ -7,6 +7,9 @@ namespace chm {
 
 constexpr int kMaxP = 9;
 constexpr int kPartWords = 8;  // u64 words of one block's partial: D[3], E[3], flags[2]
+// grid totals of the sweep kernel, added by every member block: D and E as six 32-bit limbs each
+// (in u64 counters), the flags as two packed u64; three buffers, one per sweep mod 3
+constexpr int kAccWords = 16;
 
 // Chain state kept on the device between runs.
 struct ChainState {
@@ -57,6 +60,7 @@ struct SweepArgs {
   double* S;
   ChainState* chain;
   unsigned long long* partials;  // [2][grid][kPartWords]
+  unsigned long long* acc3;      // sweep kernel: [3][kAccWords] grid totals (zeroed before each launch)
   unsigned int* bar;
   int* err;
   const double* tab_U;    // [ns][p] theta-proposal normals

@@ -104,6 +104,7 @@ struct cudahm {
   double *y_raw = nullptr, *aux_raw = nullptr;
   ChainState* chain = nullptr;
   unsigned long long* partials = nullptr;
+  unsigned long long* acc3 = nullptr;  // sweep kernel: grid totals, one buffer per sweep mod 3
   unsigned int* bar = nullptr;
   int* err = nullptr;
   int* bad = nullptr;
@@ -354,6 +355,7 @@ SweepArgs base_args(cudahm* h) {
   a.S = h->S;
   a.chain = h->chain;
   a.partials = h->partials;
+  a.acc3 = h->acc3;
   a.bar = h->bar;
   a.err = h->err;
   a.astar = h->cfg.target_accept;
@@ -662,6 +664,7 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
       (rc = alloc_into(h, &h->chi, n * h->d)) || (rc = alloc_into(h, &h->S, h->factor_n)) ||
       (rc = alloc_into(h, &h->chain, 1)) ||
       (rc = alloc_into(h, &h->partials, 2ull * std::max(h->grid, h->mgrid) * kPartWords)) ||
+      (rc = alloc_into(h, &h->acc3, 3ull * kAccWords)) ||
       (rc = alloc_into(h, &h->bar, 4)) ||
       (rc = alloc_into(h, &h->err, 4)) || (rc = alloc_into(h, &h->bad, 4)) ||
       (rc = alloc_into(h, &h->theta_dev, kMaxP)) || (rc = alloc_into(h, &h->eval_out, 4)) ||
@@ -830,6 +833,7 @@ int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
     CU(launch_tables(h->p, a.key0, a.key1, h->sweeps, ns, h->cfg.adapt_exponent, h->tab_U, h->tab_u, h->tab_lnu,
                      h->tab_eta, h->stream));
     CU(cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned int), h->stream));  // barrier count, theta' sequence
+    CU(cudaMemsetAsync(h->acc3, 0, sizeof(unsigned long long) * 3 * kAccWords, h->stream));
     a.k0 = h->sweeps;
     a.ns = ns;
     a.burn_left = n_burn - off;

@@ -497,16 +497,19 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
           for (int q = 0; q < 4; ++q) bf[q] = s_red.f[lane][q];
         }
         warp_reduce(bd, be, bf);
-        if (lane == 0 && !leader_only) {
-          unsigned long long* dst = a.partials + ((s & 1) * gridDim.x + blockIdx.x) * kPartWords;
-          __stcg(dst + 0, bd.w0);
-          __stcg(dst + 1, bd.w1);
-          __stcg(dst + 2, bd.w2);
-          __stcg(dst + 3, be.w0);
-          __stcg(dst + 4, be.w1);
-          __stcg(dst + 5, be.w2);
-          __stcg(dst + 6, (static_cast<unsigned long long>(bf[1]) << 32) | bf[0]);
-          __stcg(dst + 7, (static_cast<unsigned long long>(bf[3]) << 32) | bf[2]);
+        if (lane == 0 && !leader_only) {  // into the grid totals of this sweep
+          unsigned long long* acc = a.acc3 + (s % 3) * kAccWords;
+          acc_add_limbs(acc, bd);
+          acc_add_limbs(acc + 6, be);
+          atomicAdd(acc + 12, (static_cast<unsigned long long>(bf[1]) << 32) | bf[0]);
+          atomicAdd(acc + 13, (static_cast<unsigned long long>(bf[3]) << 32) | bf[2]);
+        }
+        // the totals of sweep s + 1 reuse the buffer of sweep s - 2, which every block has read
+        // (the member blocks before arriving at barrier s - 1, block 0 before publishing the
+        // theta' they fetched first): the first member block clears it before it arrives here
+        if (lane == 0 && blockIdx.x == mb0) {
+          unsigned long long* nxt = a.acc3 + ((s + 1) % 3) * kAccWords;
+          for (int q = 0; q < kAccWords; ++q) __stcg(nxt + q, 0ull);
         }
       }
     }
@@ -547,12 +550,19 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     }
     if (!grid_wait(a.bar, static_cast<unsigned int>(s), a.err, a.timeout_ns, nbar)) return;
 
-    // a7: every block sums all partials and takes the same decision
+    // a7: every block reads the grid totals and takes the same decision
     {
       Xacc D, E;
       unsigned int f[4];
-      sum_partials(a.partials + ((s & 1) * gridDim.x + mb0) * kPartWords, static_cast<int>(nbar), s_red, D, E, f);
       if (tid == 0) {
+        const unsigned long long* acc = a.acc3 + (s % 3) * kAccWords;
+        acc_to_xacc(acc, D);
+        acc_to_xacc(acc + 6, E);
+        const unsigned long long f01 = __ldcg(acc + 12), f23 = __ldcg(acc + 13);
+        f[0] = static_cast<unsigned int>(f01);
+        f[1] = static_cast<unsigned int>(f01 >> 32);
+        f[2] = static_cast<unsigned int>(f23);
+        f[3] = static_cast<unsigned int>(f23 >> 32);
         const long long sg = a.trace_off + s;  // sweep index within this run
         if (f[1] != 0u) {
           atomicCAS(a.err, 0, CUDAHM_ENUMERIC);

@@ -702,6 +702,33 @@ __device__ __forceinline__ void warp_reduce(Xacc& d, Xacc& e, unsigned int f[4])
   for (int q = 0; q < 4; ++q) f[q] = __reduce_add_sync(0xffffffffu, f[q]);
 }
 
+// Grid totals by fire-and-forget atomic adds (red.global.add.u64): a block's exact partial
+// (192-bit two's complement) is split into six 32-bit limbs, each added to its own 64-bit
+// counter. No counter can overflow (fewer than 2^32 blocks add values below 2^32), and carrying
+// the counters back into 192 bits gives the exact sum modulo 2^192, the value the partials'
+// sum in any order has.
+__device__ __forceinline__ void acc_add_limbs(unsigned long long* acc, const Xacc& x) {
+  const unsigned long long w[3] = {x.w0, x.w1, x.w2};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    atomicAdd(acc + 2 * q, w[q] & 0xFFFFFFFFull);
+    atomicAdd(acc + 2 * q + 1, w[q] >> 32);
+  }
+}
+
+__device__ __forceinline__ void acc_to_xacc(const unsigned long long* acc, Xacc& x) {
+  unsigned long long w[3] = {0ull, 0ull, 0ull}, c = 0ull;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const unsigned long long t = __ldcg(acc + k) + c;
+    c = t >> 32;
+    w[k >> 1] |= (t & 0xFFFFFFFFull) << (32 * (k & 1));
+  }
+  x.w0 = w[0];
+  x.w1 = w[1];
+  x.w2 = w[2];
+}
+
 // Sum of nb consecutive per-block partials (kPartWords words each, from base) by the whole
 // block: every thread loads at most a few partials at once (the loads overlap instead of one
 // warp walking the list), then warp and block reductions. Must be called by every thread of
