@@ -273,16 +273,18 @@ __global__ void __launch_bounds__(256, 2) marg_kernel(const SweepArgs a) {
           for (int q = 0; q < 4; ++q) bf[q] = s_red.f[lane][q];
         }
         warp_reduce(bd, be, bf);
-        if (lane == 0) {
-          unsigned long long* dst = a.partials + ((s & 1) * gridDim.x + blockIdx.x) * kPartWords;
-          __stcg(dst + 0, bd.w0);
-          __stcg(dst + 1, bd.w1);
-          __stcg(dst + 2, bd.w2);
-          __stcg(dst + 3, be.w0);
-          __stcg(dst + 4, be.w1);
-          __stcg(dst + 5, be.w2);
-          __stcg(dst + 6, (static_cast<unsigned long long>(bf[1]) << 32) | bf[0]);
-          __stcg(dst + 7, (static_cast<unsigned long long>(bf[3]) << 32) | bf[2]);
+        if (lane == 0) {  // into the grid totals of this step (exact limb sums, as in the sweep kernel)
+          unsigned long long* acc = a.acc3 + (s % 3) * kAccWords;
+          acc_add_limbs(acc, bd);
+          acc_add_limbs(acc + 6, be);
+          atomicAdd(acc + 12, (static_cast<unsigned long long>(bf[1]) << 32) | bf[0]);
+          atomicAdd(acc + 13, (static_cast<unsigned long long>(bf[3]) << 32) | bf[2]);
+          // step s + 1 reuses the buffer of step s - 2, which every block read before arriving
+          // at barrier s - 1: block 0 clears it before it arrives here
+          if (blockIdx.x == 0) {
+            unsigned long long* nxt = a.acc3 + ((s + 1) % 3) * kAccWords;
+            for (int q = 0; q < kAccWords; ++q) __stcg(nxt + q, 0ull);
+          }
         }
       }
     }
@@ -290,8 +292,15 @@ __global__ void __launch_bounds__(256, 2) marg_kernel(const SweepArgs a) {
     {
       Xacc D, E;
       unsigned int f[4];
-      sum_partials(a.partials + (s & 1) * gridDim.x * kPartWords, static_cast<int>(gridDim.x), s_red, D, E, f);
       if (tid == 0) {
+        const unsigned long long* acc = a.acc3 + (s % 3) * kAccWords;
+        acc_to_xacc(acc, D);
+        acc_to_xacc(acc + 6, E);
+        const unsigned long long f01 = __ldcg(acc + 12), f23 = __ldcg(acc + 13);
+        f[0] = static_cast<unsigned int>(f01);
+        f[1] = static_cast<unsigned int>(f01 >> 32);
+        f[2] = static_cast<unsigned int>(f23);
+        f[3] = static_cast<unsigned int>(f23 >> 32);
         const long long sg = a.trace_off + s;
         if (f[1] != 0u) {
           atomicCAS(a.err, 0, CUDAHM_ENUMERIC);
