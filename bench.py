@@ -46,7 +46,7 @@ L2_FLUSH_BYTES = 256 << 20
 # dram read+write bytes of one sweep-kernel launch (ncu, profiles/sweep_kernel_lf_n300000.md): the
 # member data are read once per launch and the state stays in registers, so this does not grow
 # with the sweeps of the launch.
-DRAM_BYTES_PER_LAUNCH = 9.887e6
+DRAM_BYTES_PER_LAUNCH = 1.0118e7
 
 # FP64 floating-point work of one sweep of the LF workload (2 per DFMA, 1 per DADD/DMUL), from
 # ncu's smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on counters on the sweep kernel
