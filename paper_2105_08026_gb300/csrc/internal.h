@@ -59,7 +59,7 @@ struct SweepArgs {
   double* chi;
   double* S;
   ChainState* chain;
-  unsigned long long* partials;  // [2][grid][kPartWords]
+  unsigned long long* partials;  // streaming kernel: [2][grid][kPartWords] per-block partials
   unsigned long long* acc3;      // sweep kernel: [3][kAccWords] grid totals (zeroed before each launch)
   unsigned int* bar;
   int* err;

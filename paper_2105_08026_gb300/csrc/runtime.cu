@@ -103,7 +103,6 @@ struct cudahm {
   double *y = nullptr, *aux = nullptr, *chi = nullptr, *S = nullptr;
   double *y_raw = nullptr, *aux_raw = nullptr;
   ChainState* chain = nullptr;
-  unsigned long long* partials = nullptr;
   unsigned long long* acc3 = nullptr;  // sweep kernel: grid totals, one buffer per sweep mod 3
   unsigned int* bar = nullptr;
   int* err = nullptr;
@@ -354,7 +353,7 @@ SweepArgs base_args(cudahm* h) {
   a.chi = h->chi;
   a.S = h->S;
   a.chain = h->chain;
-  a.partials = h->partials;
+  a.partials = nullptr;  // per-block partials belong to the batched launch (BatchBufs)
   a.acc3 = h->acc3;
   a.bar = h->bar;
   a.err = h->err;
@@ -663,7 +662,6 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
   if ((rc = alloc_into(h, &h->y, n * h->d)) || (rc = alloc_into(h, &h->aux, n * h->d)) ||
       (rc = alloc_into(h, &h->chi, n * h->d)) || (rc = alloc_into(h, &h->S, h->factor_n)) ||
       (rc = alloc_into(h, &h->chain, 1)) ||
-      (rc = alloc_into(h, &h->partials, 2ull * std::max(h->grid, h->mgrid) * kPartWords)) ||
       (rc = alloc_into(h, &h->acc3, 3ull * kAccWords)) ||
       (rc = alloc_into(h, &h->bar, 4)) ||
       (rc = alloc_into(h, &h->err, 4)) || (rc = alloc_into(h, &h->bad, 4)) ||

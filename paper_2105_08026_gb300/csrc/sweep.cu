@@ -2,14 +2,16 @@
 //
 // One cooperative launch runs `ns` sweeps. Per sweep (Sec. 2.1, eqs. psi_sampling then
 // theta_sampling; Sec. 2.2 for RAM):
-//   a0  theta' = theta + S_theta U_theta           (block-redundant, from a precomputed table)
+//   a0  theta' = theta + S_theta U_theta           (block 0, one sweep ahead for both outcomes of
+//                                                   the pending decision; normals from a table)
 //   a1  every member: Y = chi + S z                 (Philox4x32-10 -> Box-Muller)
 //   a2  accept iff u < exp(lp(Y) - lp(chi))         (lp = log l_i + log f(.;theta))
 //   a3  RAM factor S <- S sqrt(1 + eta (alpha - alpha_*))   (d = 1 closed form of Sec. 2.2 step 3)
 //   a4  d_i = log f(chi_i;theta') - log f(chi_i;theta) into an exact fixed-point sum
-//   a6  LF: etabar(theta') pairs of the 2-D rule into a second exact sum (Sec. 4.2, eq. epdf)
-//   a5  block partials -> bounded grid barrier -> every block adds all partials
-//   a7  every block takes the same theta accept decision, RAM-updates S_theta
+//   a6  LF: etabar(theta') outer terms of the 2-D rule into a second exact sum (Sec. 4.2, eq. epdf)
+//   a5  block partials -> exact atomic adds into the grid totals -> bounded grid barrier
+//   a7  every block takes the same theta accept decision; block 0 applies its S_theta RAM
+//       update one sweep later
 //   a8  block 0 records the kept theta row; optionally every member adds its latent to its
 //       running moments (Welford)
 // Each thread keeps its K members (latent, RAM factor, cached e^chi and log l) in

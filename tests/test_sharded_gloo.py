@@ -31,7 +31,8 @@ def _free_port():
 
 def _driver(data, theta0, scale, consts, seed, rank, world, allgather):
     """NN1 chain with its members split over `world` ranks (theta step as the oracle's: RAM on
-    theta, log alpha = D + N (c(theta') - c(theta)) + ln pi(theta') - ln pi(theta), c = -ln tau)."""
+    theta with each step's update applied one sweep late, log alpha = D + N (c(theta') - c(theta))
+    + ln pi(theta') - ln pi(theta), c = -ln tau)."""
     import oracle
     y, sig = data.y, data.sigma
     n = y.size
@@ -44,6 +45,7 @@ def _driver(data, theta0, scale, consts, seed, rank, world, allgather):
     lo, hi = consts[0], consts[1]
     prior = lambda t: 0.0 if lo <= t[1] <= hi else -math.inf
     rows = []
+    pend = None  # the previous step's RAM update: (U, alpha, eta)
     for s in range(SWEEPS):
         k = s + 1
         eta = (k + 1.0) ** (-2.0 / 3.0)
@@ -59,7 +61,9 @@ def _driver(data, theta0, scale, consts, seed, rank, world, allgather):
         alpha = 1.0 if logalpha >= 0.0 else math.exp(logalpha)
         if math.log(ut) < logalpha:
             theta = thp
-        Sth = oracle.ram_update(Sth, U, alpha, 0.4, eta)
+        if pend is not None:
+            Sth = oracle.ram_update(Sth, pend[0], pend[1], 0.4, pend[2])
+        pend = (U, alpha, eta)
         rows.append(theta.copy())
     return np.array(rows), chi[i0:i1], S[i0:i1]
 
