@@ -118,7 +118,9 @@ typedef struct {
   double adapt_exponent;         /* gamma of eta_n = n^-gamma (Sec. 2.2: 2/3) */
   double chi_init_scale;         /* S_1 = scale * I for every member (Sec. 2.2: 1) */
   double theta_target_accept;    /* alpha_* of the theta RAM (default 0.4) */
-  int32_t adapt_theta;           /* 1: RAM on theta; 0: fixed random-walk MH */
+  int32_t adapt_theta;           /* 1: RAM on theta (member form: each step's update applied one
+                                    sweep later, so that the next proposal can be formed during
+                                    the sweep); 0: fixed random-walk MH */
   int32_t trace_sweeps;          /* >0: record a lockstep trace of the first trace_sweeps sweeps of each run */
   double theta_init[CUDAHM_MAX_P];       /* initial theta (first p entries) */
   double theta_prop_scale[CUDAHM_MAX_P]; /* S_theta,1 = diag(scale) */
