@@ -281,10 +281,12 @@ int cudahm_eval_detection(cudahm_t h, const double* F_host, double* eta_host, in
 int cudahm_get_trace(cudahm_t h, double* delta, double* u, uint8_t* acc, double* theta_prop, double* D,
                      double* logalpha, double* utheta, uint8_t* tacc, double* etabar_prop, int64_t* t_out);
 
-/* Serialise the whole chain state (latents, RAM factors, theta, S_theta, counters) into buf.
- * With buf == NULL or cap too small, *used receives the required size and the call returns
- * EINVAL (buf NULL: OK). cudahm_restore loads such a buffer into a handle created with the
- * same config and data; the continued chain is bit-identical to an uninterrupted one. */
+/* Serialise the whole chain state (latents, RAM factors, theta, S_theta, the pending theta RAM
+ * update, counters and, with keep_chi_moments, the latents' moments) into buf. With buf == NULL
+ * or cap too small, *used receives the required size and the call returns EINVAL (buf NULL:
+ * OK). cudahm_restore loads such a buffer into a handle created with the same config and data;
+ * the continued chain is bit-identical to an uninterrupted one. The buffer starts with a magic
+ * word and a layout version; restore gives EINVAL for another version or configuration. */
 int cudahm_checkpoint(cudahm_t h, void* buf, size_t cap, size_t* used);
 int cudahm_restore(cudahm_t h, const void* buf, size_t size);
 

@@ -85,6 +85,8 @@ int rule_nL(const cudahm_config& c) { return static_cast<int>(c.model_consts[c.m
 int rule_nr(const cudahm_config& c) { return static_cast<int>(c.model_consts[c.model == CUDAHM_BB1 ? 5 : 4]); }
 
 constexpr long long kChunk = 4096;  // sweeps per persistent launch
+// checkpoint layout version: 2 = ChainState with the running-moment and pending theta-update fields
+constexpr int64_t kCheckpointVersion = 2;
 
 }  // namespace
 
@@ -1080,7 +1082,7 @@ int cudahm_checkpoint(cudahm_t h, void* buf, size_t cap, size_t* used) {
   if (!buf) return CUDAHM_OK;
   if (cap < need) return fail(CUDAHM_EINVAL, "checkpoint buffer too small: need %zu bytes", need);
   CU(cudaSetDevice(h->cfg.device));
-  int64_t hdr[8] = {0x4d48414455434f4bll, 1, h->cfg.model, h->n, h->d, h->p, static_cast<int64_t>(h->cfg.seed),
+  int64_t hdr[8] = {0x4d48414455434f4bll, kCheckpointVersion, h->cfg.model, h->n, h->d, h->p, static_cast<int64_t>(h->cfg.seed),
                     h->data_set ? 1 : 0};
   char* c = static_cast<char*>(buf);
   std::memcpy(c, hdr, sizeof(hdr));
@@ -1112,7 +1114,7 @@ int cudahm_restore(cudahm_t h, const void* buf, size_t size) {
   int64_t hdr[8];
   const char* c = static_cast<const char*>(buf);
   std::memcpy(hdr, c, sizeof(hdr));
-  if (hdr[0] != 0x4d48414455434f4bll || hdr[1] != 1 || hdr[2] != h->cfg.model || hdr[3] != h->n || hdr[4] != h->d ||
+  if (hdr[0] != 0x4d48414455434f4bll || hdr[1] != kCheckpointVersion || hdr[2] != h->cfg.model || hdr[3] != h->n || hdr[4] != h->d ||
       hdr[5] != h->p || hdr[6] != static_cast<int64_t>(h->cfg.seed))
     return fail(CUDAHM_EINVAL, "checkpoint does not match this handle's configuration");
   c += sizeof(hdr);
