@@ -262,3 +262,24 @@ def test_invalid_calls():
     with pytest.raises(cudahm.CudahmError) as ei:
         s.run(0, 5, thin=0)
     assert ei.value.code == cudahm.EINVAL
+
+
+def test_restore_rejects_another_layout_version_or_config():
+    data = synth.nn1_data(500, seed=18)
+    theta0, scale, consts = synth.nn1_settings(data)
+    mk = lambda seed: cudahm.Sampler(cudahm.NN1, 500, theta_init=theta0, theta_prop_scale=scale,
+                                     model_consts=consts, seed=seed)
+    a, b, c = mk(3), mk(3), mk(4)
+    for x in (a, b, c):
+        x.set_data(data.y, data.sigma)
+    a.run(0, 20)
+    blob = bytearray(a.checkpoint())
+    b.restore(bytes(blob))  # same configuration and layout: accepted
+    assert np.array_equal(b.chi()[0], a.chi()[0])
+    with pytest.raises(cudahm.CudahmError) as ei:  # another seed: another chain
+        c.restore(bytes(blob))
+    assert ei.value.code == cudahm.EINVAL
+    blob[8:16] = (1).to_bytes(8, "little", signed=True)  # layout version 1
+    with pytest.raises(cudahm.CudahmError) as ei:
+        b.restore(bytes(blob))
+    assert ei.value.code == cudahm.EINVAL
