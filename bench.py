@@ -70,18 +70,23 @@ def parse():
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=1000)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
-    ap.add_argument("--repeats", type=int, default=5, help="timed launches the steps are split into")
+    ap.add_argument("--launch-sweeps", type=int, default=4096,
+                    help="sweeps per timed run call (the library's persistent launch holds up to 4096)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-sweeps", type=int, default=2000)
     ap.add_argument("--batched-pops", type=int, default=256)
+    ap.add_argument("--batched-nlo", type=float, default=1e3, help="smallest population of the batched leg")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-sweeps", type=int, default=5000)
     ap.add_argument("--serve-pool", type=int, default=48)
+    ap.add_argument("--serve-burst", type=int, default=96, help="requests of the saturated (all at t = 0) run")
+    ap.add_argument("--serve-seq", type=int, default=40,
+                    help="requests of the stream served by the sequential FP64 sampler")
     ap.add_argument("--cpu-sweeps", type=int, default=8)
     ap.add_argument("--no-mvn3", action="store_true")
     ap.add_argument("--no-bb1", action="store_true")
@@ -196,6 +201,17 @@ def oracle_rate(data, theta0, scale, consts, sweeps, warmup=1):
     return data.fhat.size * sweeps / dt, dt
 
 
+def oracle_rate_allcores(data, theta0, scale, consts, sweeps, threads):
+    """The oracle's LF chain on every host core: members split over threads, the theta step
+    (with the 1024 x 1024 selection rule) serial (oracle/allcores.py)."""
+    from oracle import allcores
+    from paper_2105_08026_gb300 import synth
+    chi0 = synth.lf_chi_init(data, theta0)
+    allcores.lf_run(data.fhat, data.r, consts, theta0, scale, CHAIN_SEED, chi0, 1, threads)  # untimed
+    _, _, _, dt = allcores.lf_run(data.fhat, data.r, consts, theta0, scale, CHAIN_SEED, chi0, sweeps, threads)
+    return data.fhat.size * sweeps / dt, dt
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -243,7 +259,7 @@ def run_batched(args, cudahm, stream, device):
     CUDA events on the batch stream (its autotuning launches are part of the run)."""
     import torch
     from paper_2105_08026_gb300 import synth
-    specs = synth.batch_specs(args.batched_pops, seed=2000)
+    specs = synth.batch_specs(args.batched_pops, seed=2000, n_lo=args.batched_nlo)
     samplers = []
     for sp in specs:
         y, aux, th, sc, c = synth.pop_data(sp)
@@ -540,12 +556,9 @@ def run_nn1_small(args, cudahm, stream, device):
             "launch_shape": [st.grid_blocks, st.block_threads, st.objects_per_thread]}
 
 
-def run_served(args, cudahm, device):
-    """Poisson request stream (rate 20/s for --serve-seconds) into the continuous-batching server:
-    each request is NN1 or LF with probability 1/2, N log-uniform on [1e3, 3e5], 5000 sweeps,
-    FP32, 60 GB budget. Request data come from a pre-generated pool of catalogs (each request
-    has its own chain seed). Reports completion-latency percentiles and aggregate throughput."""
-    import threading as th_
+def _serve_pool(args):
+    """Pre-generated request catalogs: NN1 or LF alternately, N log-uniform on [1e3, 3e5], the
+    single-population workloads' parameters scaled by U[0.8, 1.2]."""
     from paper_2105_08026_gb300 import synth
     g = np.random.default_rng(3000)
     pool = []
@@ -560,16 +573,24 @@ def run_served(args, cudahm, device):
                                                        r_max=4000.0 * f[3], detect_frac=0.30 * f[4]))
         y, aux, th, sc, c = synth.pop_data(sp)
         pool.append((sp, y, aux, th, sc, c))
-    sweeps = args.serve_sweeps
+    return pool
+
+
+def _pct(lat):
+    lat = np.asarray(lat, dtype=np.float64)
+    return {"p50": float(np.percentile(lat, 50)), "p95": float(np.percentile(lat, 95)),
+            "p99": float(np.percentile(lat, 99)), "max": float(lat.max())}
+
+
+def _serve_stream(cudahm, device, pool, arrivals, sweeps):
+    """Feeds (arrival s, pool index, seed) requests to a fresh continuous-batching server at their
+    arrival times (all at once when every arrival time is 0); returns latencies, work, wall time,
+    the server's stats and the largest number of requests seen on the device together."""
+    import threading as th_
     sv = cudahm.Server(60 << 30, device=device, precision=cudahm.FP32, max_active=512, sweeps_per_step=250)
-    arrivals = []
-    t = 0.0
-    while True:
-        t += g.exponential(1.0 / args.serve_rate)
-        if t > args.serve_seconds:
-            break
-        arrivals.append((t, int(g.integers(0, len(pool))), int(g.integers(1, 2**31))))
     tickets = []
+    peak = [0]
+    done = [False]
 
     def producer():
         t0 = time.perf_counter()
@@ -582,7 +603,14 @@ def run_served(args, cudahm, device):
                                      theta_prop_scale=sc, model_consts=c, seed=seed, precision=cudahm.FP32,
                                      device=device)
             tickets.append((sv.submit(cfg, y, aux, 0, sweeps, sweeps), sp.n))
+
+    def sampler():  # how many requests share the device
+        while not done[0]:
+            peak[0] = max(peak[0], sv.stats()["active"])
+            time.sleep(0.005)
     t_start = time.perf_counter()
+    mon = th_.Thread(target=sampler)
+    mon.start()
     prod = th_.Thread(target=producer)
     prod.start()
     prod.join()
@@ -594,16 +622,77 @@ def run_served(args, cudahm, device):
         lat.append(ms)
         work += n * sweeps
     wall = time.perf_counter() - t_start
+    done[0] = True
+    mon.join()
     st = sv.stats()
     sv.close()
-    lat = np.array(lat)
+    return lat, work, wall, st, peak[0]
+
+
+def run_served(args, cudahm, device):
+    """Config 4: a Poisson request stream (rate --serve-rate for --serve-seconds) into the
+    continuous-batching server: each request is NN1 or LF with probability 1/2, N log-uniform on
+    [1e3, 3e5], 5000 sweeps, FP32, 60 GB budget; request data come from a pre-generated pool of
+    catalogs (each request has its own chain seed). Reports completion-latency percentiles and
+    aggregate throughput. Beside it:
+    - saturated: --serve-burst requests of the same mix all arriving at once, so the server's own
+      capacity (not the offered load) sets the throughput;
+    - sequential_fp64: the plain FP64 sampler serving the same stream one request at a time in
+      arrival order (the first --serve-seq requests; each request's service time measured on the
+      GPU, the first-come-first-served queue then gives each completion time)."""
+    pool = _serve_pool(args)
+    sweeps = args.serve_sweeps
+    g = np.random.default_rng(3001)
+    arrivals = []
+    t = 0.0
+    while True:
+        t += g.exponential(1.0 / args.serve_rate)
+        if t > args.serve_seconds:
+            break
+        arrivals.append((t, int(g.integers(0, len(pool))), int(g.integers(1, 2**31))))
+    lat, work, wall, st, peak = _serve_stream(cudahm, device, pool, arrivals, sweeps)
     offered = args.serve_rate * float(np.mean([pool[pi][0].n for _, pi, _ in arrivals])) * sweeps
-    return {"value": work / wall, "unit": "object-updates/s", "requests": len(tickets),
-            "arrival_rate_per_s": args.serve_rate, "window_s": args.serve_seconds, "sweeps_per_request": sweeps,
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p95": float(np.percentile(lat, 95)),
-                           "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
-            "offered_object_updates_per_s": offered, "wall_s": wall, "device_busy_s": st["busy_ms"] / 1e3,
-            "dtype": "f32 member terms, f64 sums/accept/RAM/selection integral", "budget_bytes": 60 << 30}
+    out = {"value": work / wall, "unit": "object-updates/s", "requests": len(lat),
+           "arrival_rate_per_s": args.serve_rate, "window_s": args.serve_seconds, "sweeps_per_request": sweeps,
+           "latency_ms": _pct(lat), "offered_object_updates_per_s": offered, "wall_s": wall,
+           "device_busy_s": st["busy_ms"] / 1e3, "peak_requests_on_device": peak,
+           "dtype": "f32 member terms, f64 sums/accept/RAM/selection integral", "budget_bytes": 60 << 30}
+    if args.serve_burst > 0:
+        burst = [(0.0, pi, seed) for (_, pi, seed) in arrivals[: args.serve_burst]]
+        blat, bwork, bwall, bst, bpeak = _serve_stream(cudahm, device, pool, burst, sweeps)
+        out["saturated"] = {"value": bwork / bwall, "unit": "object-updates/s", "requests": len(blat),
+                            "latency_ms": _pct(blat), "wall_s": bwall, "peak_requests_on_device": bpeak,
+                            "note": "every request arrives at t = 0: the throughput is the server's capacity"}
+    if args.serve_seq > 0:
+        seq = arrivals[: args.serve_seq]
+        service = []
+        swork = 0.0
+        for (ta, pi, seed) in seq:
+            sp, y, aux, th, sc, c = pool[pi]
+            t0 = time.perf_counter()
+            sm = cudahm.Sampler(cudahm.NN1 if sp.kind == "nn1" else cudahm.LF, sp.n, theta_init=th,
+                                theta_prop_scale=sc, model_consts=c, seed=seed, precision=cudahm.FP64, device=device)
+            sm.set_data(y, aux)
+            rows = sm.run(0, sweeps, sweeps)
+            sm.close()
+            service.append(time.perf_counter() - t0)
+            assert rows.shape[0] == 1
+            swork += sp.n * sweeps
+        end = 0.0
+        slat = []
+        for (ta, _, _), sv_s in zip(seq, service):
+            end = max(end, ta) + sv_s
+            slat.append((end - ta) * 1e3)
+        out["sequential_fp64"] = {"value": swork / sum(service), "unit": "object-updates/s", "requests": len(seq),
+                                  "latency_ms": _pct(slat), "busy_s": sum(service),
+                                  "note": "plain FP64 sampler, one request at a time in arrival order (handle "
+                                          "creation, data upload, run and result read per request); latency from "
+                                          "the first-come-first-served queue of the measured service times"}
+        # the server on the same prefix of the stream, for a like-for-like comparison
+        plat, pwork, pwall, _, ppeak = _serve_stream(cudahm, device, pool, seq, sweeps)
+        out["served_same_prefix"] = {"value": pwork / pwall, "unit": "object-updates/s", "requests": len(plat),
+                                     "latency_ms": _pct(plat), "peak_requests_on_device": ppeak}
+    return out
 
 
 def run_cuda(args):
@@ -631,8 +720,10 @@ def run_cuda(args):
         s.run(args.warmup, 0)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     K = args.steps
-    R = max(1, min(args.repeats, K))
-    chunks = [K // R + (1 if j < K % R else 0) for j in range(R)]
+    # timed run calls of up to one persistent launch each (4096 sweeps), the L2 flushed before each
+    L = max(1, args.launch_sweeps)
+    chunks = [min(L, K - j) for j in range(0, K, L)]
+    R = len(chunks)
     clocks = ClockSampler(local)
     if ws > 1:
         torch.distributed.barrier()
@@ -753,7 +844,6 @@ def run_cuda(args):
     # e2e through the public API with host buffers (every iteration: H2D data, run, D2H samples)
     e2e = None
     if not args.no_e2e:
-        ke = max(1, K // R)
         s2 = cudahm.Sampler(cudahm.LF, n, theta_init=theta0, theta_prop_scale=scale, model_consts=consts,
                             seed=chain_seed, device=local, stream=stream.cuda_stream,
                             use_torch_allocator=True)
@@ -763,15 +853,15 @@ def run_cuda(args):
         s2.run(min(args.warmup, 200), 0)  # warm the selection-integral cache and the code path
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(R):
+        for ns in chunks:  # the same run calls as the device-timed leg
             s2.set_data(host_y, host_r)          # host -> device copy of the inputs
-            out = s2.run(0, ke, 1)               # device -> host copy of the theta rows
-            assert out.shape == (ke, 3)
+            out = s2.run(0, ns, 1)               # device -> host copy of the theta rows
+            assert out.shape == (ns, 3)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        e2e_val = replica_value(ws, n * ke * R, max_over_ranks(wall * 1e3))
-        e2e = {"value": e2e_val, "unit": "object-updates/s", "h2d_bytes_per_step": 2 * n * 8 / ke,
-               "d2h_bytes_per_step": 3 * 8 + 4 / ke}
+        e2e_val = replica_value(ws, n * K, max_over_ranks(wall * 1e3))
+        e2e = {"value": e2e_val, "unit": "object-updates/s", "h2d_bytes_per_step": 2 * n * 8 * R / K,
+               "d2h_bytes_per_step": 3 * 8 + 4 * R / K}
         s2.close()
 
     if rank != 0:
@@ -796,6 +886,11 @@ def run_cuda(args):
         rate, dt = oracle_rate(data, theta0, scale, consts, sweeps)
         cpu = {"value": rate, "unit": "object-updates/s", "cores": 1, "kind": "oracle",
                "sample": f"{sweeps} full sweeps of the same N={n} workload ({dt:.1f} s, single-threaded)"}
+        ncore = host_cores()
+        rate_all, dt_all = oracle_rate_allcores(data, theta0, scale, consts, sweeps, ncore)
+        cpu["all_cores"] = {"value": rate_all, "unit": "object-updates/s", "cores": ncore, "kind": "oracle",
+                            "sample": f"{sweeps} full sweeps of the same workload ({dt_all:.1f} s): members split "
+                                      f"over {ncore} threads, the theta step and its selection rule serial"}
     line = {"metric": "object-updates/s", "value": value, "unit": "object-updates/s", "n_gpus": ws, "steps": K,
             "warmup": args.warmup, "ms_per_step": t_max_ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",

@@ -94,10 +94,12 @@ typedef enum { CUDAHM_NN1 = 0, CUDAHM_MVN3 = 1, CUDAHM_LF = 2, CUDAHM_BB1 = 3, C
 /* FP64: all arithmetic in binary64.
  * FP32 (bulk form): the member step (proposal, member log target, accept) and the theta
  * partials log f(chi;theta') - log f(chi;theta) run in binary32, with binary32 draws of their
- * own (Philox block (0, stream 2, member, odd sweep): a Box-Muller pair from 24-bit uniforms,
+ * own (Philox block (0, stream 2, member, odd sweep): a Box-Muller pair from 23-bit uniforms,
  * cosine for the odd sweep and sine for the next, accept uniforms from words 2 and 3); the
  * RAM factors S, the exact sum over members, the theta accept and its RAM update, and the
- * selection integral stay binary64. Latents are binary32 values (held as doubles in the API).
+ * selection integral stay binary64 (a d = 1 factor is updated as S + S d, one binary64 FMA, with
+ * the increment d = sqrt(1 + c) - 1 = c/(1 + sqrt(1 + c)) formed in binary32). Latents are
+ * binary32 values (held as doubles in the API).
  * MVN3 in FP32 draws from Philox blocks (0, 2, member, odd sweep) and (1, 2, member, odd sweep):
  * pairs from words (0,1), (2,3) of the first and (0,1) of the second give U's three components,
  * words 2 and 3 of the second the odd and even sweep's accept uniforms; v = S U and the RAM
@@ -304,11 +306,16 @@ int cudahm_restore(cudahm_t h, const void* buf, size_t size);
  *   cuda_stream  cudaStream_t to enqueue on (NULL = the default stream); the call returns
  *                once the work is enqueued; read the result after synchronising.
  * Returns EINVAL (with a message) for rule sizes above the limit or bad constants. The
- * value equals cudahm_eval_etabar's for the same theta and constants. The first call on a
+ * value agrees with cudahm_eval_etabar's for the same theta and constants within 1e-13
+ * relative: this call sums the rule pair by pair, a handle interpolates a table of the inner
+ * sum over r. The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress, once per device, with
  * that device current); make that first call before any stream capture. Every call on a
  * device shares the array and it keeps the last call's contents (nothing in it must start
- * at zero: each call rewrites all it reads); calls that overlap on the GPU race on it. */
+ * at zero). A call rebuilds the rule tables (about a millisecond of kernels) only when n_L,
+ * n_r, r_max or sigma_F differ from the previous call's on the device; otherwise it reads the
+ * tables that call left, so when consecutive calls use different streams, let the earlier
+ * one's work finish first. Calls that overlap on the GPU race on the array. */
 #define CUDAHM_NOALLOC_MAX_NODES 1024
 int cudahm_lf_etabar_noalloc(const double* theta_dev, const double* consts_host, double* etabar_dev,
                              void* cuda_stream);

@@ -101,6 +101,11 @@ def lib():
                                           ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _dp, _dp,
                                           _dp, _dp, _dp, _i64p]
             L.orc_member_pass.restype = ctypes.c_int
+            L.orc_lf_rule_new.argtypes = [_dp]
+            L.orc_lf_rule_new.restype = ctypes.c_void_p
+            L.orc_lf_rule_etabar.argtypes = [ctypes.c_void_p, _dp, _dp]
+            L.orc_lf_rule_etabar.restype = ctypes.c_double
+            L.orc_lf_rule_free.argtypes = [ctypes.c_void_p]
             _lib = L
     return _lib
 

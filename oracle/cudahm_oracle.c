@@ -354,6 +354,22 @@ double orc_lf_etabar(const double* th, const double* consts) {
   return v;
 }
 
+/* The same rule built once, for a caller that evaluates etabar(theta) every sweep (the all-cores
+ * timing driver): orc_lf_rule_etabar(R, th) equals orc_lf_etabar(th) bit for bit. */
+void* orc_lf_rule_new(const double* consts) {
+  gl_rule* R = (gl_rule*)malloc(sizeof(gl_rule));
+  if (R) gl_rule_init(R, (int)consts[3], (int)consts[4]);
+  return R;
+}
+double orc_lf_rule_etabar(void* R, const double* th, const double* consts) {
+  return lf_etabar_rule(th, (gl_rule*)R, consts);
+}
+void orc_lf_rule_free(void* R) {
+  if (!R) return;
+  gl_rule_free((gl_rule*)R);
+  free(R);
+}
+
 /* Detection efficiency eta(F) = Phi((F - F_th)/sigma_F) (Sec. 5.2, eq. key). */
 double orc_lf_detection(double F, const double* consts) { return phi_cdf((F - consts[1]) / consts[0]); }
 

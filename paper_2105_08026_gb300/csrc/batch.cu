@@ -21,6 +21,11 @@ namespace chm {
 
 namespace {
 
+// byte offset of the member-tile stages in the dynamic shared memory (after the exp/log tables)
+__host__ __device__ constexpr unsigned int tile_offset_bytes() {
+  return (static_cast<unsigned int>(sizeof(double)) * kMathWords + 127u) & ~127u;
+}
+
 __device__ __forceinline__ int find_pop(const int* b0s, int npop, int b) {
   int lo = 0, hi = npop - 1;  // last population whose first block is <= b
   while (lo < hi) {
@@ -121,56 +126,58 @@ __device__ __forceinline__ void member_f64(const SweepArgs& a, unsigned int i, u
   }
 }
 
-// One member's sweep in the FP32 bulk form (binary32 member terms, binary64 RAM factor).
+// One member's sweep in the FP32 bulk form, d = 1, from its staged tile slot: the latent (binary32
+// state), the RAM factor (binary64) and the binary32 data. The same operations as the
+// register-resident kernel's two half-steps, so the same bits. Writes the new latent and factor.
 template <class M>
-__device__ __forceinline__ void member_f32(const SweepArgs& a, unsigned int i, uint32_t k, double eta,
-                                           const ThetaCf& tf, const ThetaCf& tpf, bool prior_ok, Xacc& xd,
-                                           XFlags& fd, unsigned int& neg_big, unsigned int& pos_big,
-                                           unsigned int& nan_cnt, unsigned int& acc_cnt, long long tro,
-                                           bool keep, const MomStep& ms) {
-  float chi = static_cast<float>(a.chi[i]);
-  double S = a.S[i];
-  float d[M::kData32];
-#pragma unroll
-  for (int c = 0; c < M::kData32; ++c) d[c] = __ldg(a.d32 + static_cast<size_t>(c) * a.n + i);
+__device__ __forceinline__ void member1_f32(const SweepArgs& a, unsigned int i, float chi, double S, const float* d,
+                                            uint32_t k, float eta_f, float astar_f, const ThetaCf& tf,
+                                            const ThetaCf& tpf, bool prior_ok, Xacc& xd, XFlags& fd,
+                                            unsigned int& neg_big, unsigned int& pos_big, unsigned int& nan_cnt,
+                                            unsigned int& acc_cnt, long long tro, bool keep, const MomStep& ms) {
   const float ll = M::loglike32(chi, d);
   const bool odd = (k & 1u) != 0u;
+  // Philox block (0, stream 2, member i, odd sweep): a Box-Muller pair from words 0 and 1 (cosine
+  // for the odd sweep, sine for the next), the accept uniforms of the two sweeps from words 2, 3
   const uint4 w = philox4x32_10(make_uint4(0u, 2u, i, odd ? k : k - 1u), a.key0, a.key1);
-  const float u1 = (static_cast<float>(w.x >> 8) + 0.5f) * 0x1p-24f;
-  const float u2 = (static_cast<float>(w.y >> 8) + 0.5f) * 0x1p-24f;
-  const float u = (static_cast<float>((odd ? w.z : w.w) >> 8) + 0.5f) * 0x1p-24f;
-  const float rad = sqrtf(-2.0f * logf(u1));
-  float sn, cs;
-  sincospif(2.0f * u2, &sn, &cs);
-  const float z = odd ? rad * cs : rad * sn;
-  const float Y = fmaf(static_cast<float>(S), z, chi);
-  float delta, lfY = 0.0f;
-  const float lfX = M::logf32(chi, tf);
+  const float u = uniform23(odd ? w.z : w.w);
+  float zc, zs;
+  box_muller32(w.x, w.y, zc, zs);
+  const float z = odd ? zc : zs;
+  const float Y = fmaf(f32_rz(S), z, chi);
+  float delta, llY = 0.0f;
+  F2 lfY{0.0f, 0.0f};
+  const F2 lfX = M::logf32p(chi, tf);
   if (!M::support32(Y, tf)) {
     delta = -INFINITY;
   } else {
-    lfY = M::logf32(Y, tf);
-    delta = (M::loglike32(Y, d) + lfY) - (ll + lfX);
+    llY = M::loglike32(Y, d);
+    lfY = M::logf32p(Y, tf);
+    delta = (llY + (lfY.hi + lfY.lo)) - (ll + (lfX.hi + lfX.lo));
   }
   float alpha;
   const bool acc = mh_accept32(delta, u, alpha);
   if (delta != delta) nan_cnt++;
-  const float lf_cur = acc ? lfY : lfX;
+  const F2 lf_cur = acc ? lfY : lfX;
   if (acc) {
     chi = Y;
     acc_cnt++;
   }
-  S *= sqrt(fma(eta, static_cast<double>(alpha) - a.astar, 1.0));
-  a.chi[i] = static_cast<double>(chi);
+  S = ram1_f32(S, alpha, eta_f, astar_f);
+  a.chi32[i] = chi;
   a.S[i] = S;
-  if (keep) mom_add(ms, i, static_cast<double>(chi));
+  if (keep) mom_add(ms, i, f64_of(chi));
   if (tro >= 0) {
     a.tr_delta[tro + i] = static_cast<double>(delta);
     a.tr_u[tro + i] = static_cast<double>(u);
     a.tr_acc[tro + i] = acc ? 1 : 0;
   }
   if (prior_ok) {
-    const float dn = M::support32(chi, tpf) ? M::logf32(chi, tpf) - lf_cur : -INFINITY;
+    float dn = -INFINITY;
+    if (M::support32(chi, tpf)) {  // (hi' - hi) + (lo' - lo): the small parts survive the difference
+      const F2 lfp = M::logf32p(chi, tpf);
+      dn = __fadd_rn(__fsub_rn(lfp.hi, lf_cur.hi), __fsub_rn(lfp.lo, lf_cur.lo));
+    }
     if (dn != dn) fd.nan++;
     else if (fabsf(dn) >= 0x1p94f) {
       if (dn < 0.0f) neg_big++;
@@ -179,6 +186,101 @@ __device__ __forceinline__ void member_f32(const SweepArgs& a, unsigned int i, u
       xacc_add_float(xd, dn, fd);
     }
   }
+}
+
+// Member tiles of the FP32 form, d = 1, in the streaming kernel. The block's members [nb0, nb1)
+// are covered by tiles of T members starting at a0 = nb0 rounded down to a multiple of 4 (so
+// every bulk copy is 16-byte aligned; the arrays are padded to n32 members). Each tile's latents,
+// RAM factors and binary32 data are brought into one of two shared-memory stages by bulk copies
+// (the TMA engine) while the block steps the members of the other stage. The few members of a
+// neighbouring block that an aligned tile covers are read but never used or written.
+struct TileRing {
+  char* buf;                // two stages of T (4 + 8 + 4 kData32) bytes
+  unsigned long long* bar;  // one mbarrier per stage
+  unsigned int T;           // members per tile
+  unsigned int count;       // tiles consumed so far: stage count & 1, phase parity (count >> 1) & 1
+  bool prefetched;          // the tile with counter `count` (the first of a sweep) is in flight
+};
+
+template <int K32>
+__device__ __forceinline__ void tile_issue(const SweepArgs& a, const TileRing& r, unsigned int b, unsigned int len,
+                                           unsigned int cnt) {
+  char* st = r.buf + static_cast<size_t>(cnt & 1u) * r.T * (12u + 4u * K32);
+  unsigned long long* bar = r.bar + (cnt & 1u);
+  mbar_arrive_expect_tx(bar, len * (12u + 4u * K32));
+  bulk_copy_g2s(st, a.chi32 + b, len * 4u, bar);
+  bulk_copy_g2s(st + 4u * r.T, a.S + b, len * 8u, bar);
+#pragma unroll
+  for (int c = 0; c < K32; ++c) bulk_copy_g2s(st + (12u + 4u * c) * r.T, a.d32 + c * a.n32 + b, len * 4u, bar);
+}
+
+// The block's member phase of one sweep (FP32 form, d = 1). Returns false if a stage wait
+// timed out (the run's error word is set; copies in flight have been waited for).
+template <class M>
+__device__ __forceinline__ bool members1_f32_tiled(const SweepArgs& a, TileRing& r, unsigned int nb0,
+                                                   unsigned int nb1, uint32_t k, float eta_f, float astar_f,
+                                                   const ThetaCf& tf, const ThetaCf& tpf, bool prior_ok, Xacc& xd,
+                                                   XFlags& fd, unsigned int& neg_big, unsigned int& pos_big,
+                                                   unsigned int& nan_cnt, unsigned int& acc_cnt, long long tro,
+                                                   bool keep, const MomStep& ms) {
+  constexpr int K32 = M::kData32;
+  if (nb1 <= nb0) return true;
+  const unsigned int a0 = nb0 & ~3u;
+  const unsigned long long a1l = (static_cast<unsigned long long>(nb1) + 3ull) & ~3ull;
+  const unsigned int a1 = static_cast<unsigned int>(a1l < static_cast<unsigned long long>(a.n32) ? a1l : a.n32);
+  const unsigned int ntiles = (a1 - a0 + r.T - 1u) / r.T;
+  if (!r.prefetched && threadIdx.x == 0) tile_issue<K32>(a, r, a0, min(r.T, a1 - a0), r.count);
+  r.prefetched = false;
+  bool ok = true;  // this thread's stage waits all completed
+  for (unsigned int t = 0; t < ntiles; ++t) {
+    const unsigned int cnt = r.count;
+    const unsigned int b = a0 + t * r.T, len = min(r.T, a1 - b);
+    if (t + 1u < ntiles && threadIdx.x == 0) tile_issue<K32>(a, r, b + r.T, min(r.T, a1 - b - r.T), cnt + 1u);
+    if (ok) ok = mbar_wait_bounded(r.bar + (cnt & 1u), (cnt >> 1) & 1u, a.err, a.timeout_ns);
+    if (!ok) {  // the run has failed: skip the members, keep the block's barriers in step
+      fence_proxy_async_global();
+      __syncthreads();
+      r.count = cnt + 1u;
+      continue;
+    }
+    const char* st = r.buf + static_cast<size_t>(cnt & 1u) * r.T * (12u + 4u * K32);
+    const float* s_chi = reinterpret_cast<const float*>(st);
+    const double* s_S = reinterpret_cast<const double*>(st + 4u * r.T);
+    const float* s_d = reinterpret_cast<const float*>(st + 12u * r.T);
+    for (unsigned int m = threadIdx.x; m < len; m += blockDim.x) {
+      const unsigned int i = b + m;
+      if (i < nb0 || i >= nb1) continue;
+      float d[K32];
+#pragma unroll
+      for (int c = 0; c < K32; ++c) d[c] = s_d[c * r.T + m];
+      member1_f32<M>(a, i, s_chi[m], s_S[m], d, k, eta_f, astar_f, tf, tpf, prior_ok, xd, fd, neg_big, pos_big,
+                     nan_cnt, acc_cnt, tro, keep, ms);
+    }
+    fence_proxy_async_global();  // this thread's writes before any later bulk copy reads them
+    __syncthreads();             // the stage is free for the tile after next
+    r.count = cnt + 1u;
+  }
+  if (__syncthreads_or(ok ? 0 : 1)) {
+    // a stage wait timed out: leave no copy in flight into this block's shared memory (every
+    // thread waits, bounded again, for the last phase issued on each stage)
+    for (unsigned int c = r.count - min(r.count, 2u); c < r.count; ++c)
+      mbar_wait_bounded(r.bar + (c & 1u), (c >> 1) & 1u, a.err, a.timeout_ns);
+    __syncthreads();
+    return false;
+  }
+  return true;
+}
+
+// Issues the first tile of the next sweep (thread 0), after every write of this sweep.
+template <class M>
+__device__ __forceinline__ void tile_prefetch_first(const SweepArgs& a, TileRing& r, unsigned int nb0,
+                                                    unsigned int nb1) {
+  if (nb1 <= nb0) return;
+  const unsigned int a0 = nb0 & ~3u;
+  const unsigned long long a1l = (static_cast<unsigned long long>(nb1) + 3ull) & ~3ull;
+  const unsigned int a1 = static_cast<unsigned int>(a1l < static_cast<unsigned long long>(a.n32) ? a1l : a.n32);
+  if (threadIdx.x == 0) tile_issue<M::kData32>(a, r, a0, min(r.T, a1 - a0), r.count);
+  r.prefetched = true;
 }
 
 // One member's sweep for the d = 3 model (FP64 form). State and data are stored per component
@@ -266,15 +368,11 @@ __device__ __forceinline__ void member3_f64(const SweepArgs& a, unsigned int i, 
   }
 }
 
-// 24-bit uniform in (0, 1) from one Philox word
-__device__ __forceinline__ float uniform24(uint32_t w) { return (static_cast<float>(w >> 8) + 0.5f) * 0x1p-24f; }
-
 // Standard normal of sweep k from one Box-Muller pair of binary32 uniforms
-__device__ __forceinline__ float bm24(uint32_t wa, uint32_t wb, bool odd) {
-  const float rad = sqrtf(-2.0f * logf(uniform24(wa)));
-  float sn, cs;
-  sincospif(2.0f * uniform24(wb), &sn, &cs);
-  return odd ? rad * cs : rad * sn;
+__device__ __forceinline__ float bm23(uint32_t wa, uint32_t wb, bool odd) {
+  float zc, zs;
+  box_muller32(wa, wb, zc, zs);
+  return odd ? zc : zs;
 }
 
 // One member's sweep for the d = 3 model in the FP32 bulk form: binary32 draws (Philox blocks
@@ -301,8 +399,8 @@ __device__ __forceinline__ void member3_f32(const SweepArgs& a, unsigned int i, 
   const uint32_t ko = odd ? k : k - 1u;
   const uint4 b0 = philox4x32_10(make_uint4(0u, 2u, i, ko), a.key0, a.key1);
   const uint4 b1 = philox4x32_10(make_uint4(1u, 2u, i, ko), a.key0, a.key1);
-  const float z0 = bm24(b0.x, b0.y, odd), z1 = bm24(b0.z, b0.w, odd), z2 = bm24(b1.x, b1.y, odd);
-  const float u = uniform24(odd ? b1.z : b1.w);
+  const float z0 = bm23(b0.x, b0.y, odd), z1 = bm23(b0.z, b0.w, odd), z2 = bm23(b1.x, b1.y, odd);
+  const float u = uniform23(odd ? b1.z : b1.w);
   const double zd0 = z0, zd1 = z1, zd2 = z2;
   const double v0 = S[0] * zd0;
   const double v1 = fma(S[1], zd0, S[2] * zd1);
@@ -397,6 +495,25 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
   const unsigned int nb0 = static_cast<unsigned int>((a.n * lb) / nb);
   const unsigned int nb1 = static_cast<unsigned int>((a.n * (lb + 1)) / nb);
   unsigned int member_acc = 0;
+  // FP32 form, d = 1: member tiles staged in shared memory by bulk copies (after the tables)
+  constexpr bool kTiled = F32 && M::kD == 1;
+  __shared__ __align__(8) unsigned long long s_tbar[2];
+  TileRing ring{};
+  if constexpr (kTiled) {
+    const size_t base = reinterpret_cast<size_t>(reinterpret_cast<char*>(s_dyn) + tile_offset_bytes());
+    ring.buf = reinterpret_cast<char*>((base + 127u) & ~static_cast<size_t>(127u));  // 16-byte copies need 16
+    ring.bar = s_tbar;
+    ring.T = 2u * blockDim.x;
+    ring.count = 0u;
+    ring.prefetched = false;
+    if (tid == 0) {
+      mbar_init(&s_tbar[0], 1u);
+      mbar_init(&s_tbar[1], 1u);
+      fence_mbar_init();
+    }
+    __syncthreads();
+  }
+  const float astar_f = __double2float_rn(a.astar);
 
   for (long long s = 0; s < ns; ++s) {
     const uint32_t k = static_cast<uint32_t>(k0 + s + 1);
@@ -435,9 +552,9 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
       }
     } else if constexpr (F32) {
       const TCf tf = s_tcf, tpf = s_tcpf;
-      for (unsigned int i = nb0 + tid; i < nb1; i += blockDim.x)
-        member_f32<M>(a, i, k, eta, tf, tpf, prior_ok, xd, fd, neg_big, pos_big, member_nan, member_acc, tro,
-                      keep, ms);
+      if (!members1_f32_tiled<M>(a, ring, nb0, nb1, k, __double2float_rn(eta), astar_f, tf, tpf, prior_ok, xd, fd,
+                                 neg_big, pos_big, member_nan, member_acc, tro, keep, ms))
+        return;  // a stage wait timed out: the run's error word is set, the population stops
     } else {
       const TC tc = s_tc, tcp = s_tcp;
       for (unsigned int i = nb0 + tid; i < nb1; i += blockDim.x)
@@ -549,6 +666,8 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
     }
     __syncthreads();
     if (s_stop) return;
+    if constexpr (kTiled)
+      if (s + 1 < ns) tile_prefetch_first<M>(a, ring, nb0, nb1);  // overlaps the next theta proposal
   }
   __shared__ unsigned int s_macc;
   if (tid == 0) s_macc = 0;
@@ -624,15 +743,19 @@ const void* batch_fn(bool f32, bool d1) {
             : reinterpret_cast<const void*>(&batch_kernel<false, false>);
 }
 
-// binary32 member data of the FP32 form (kData32 values per member, member-minor)
+// binary32 member data of the FP32 form (kData32 rows of stride n32 >= n, member-minor; the
+// padding members hold zeros)
 template <class M>
-__global__ void data32_kernel(long long n, const double* y, const double* aux, ModelConsts mc, float* d32) {
+__global__ void data32_kernel(long long n, long long n32, const double* y, const double* aux, ModelConsts mc,
+                              float* d32) {
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n32) return;
   float d[M::kData32];
-  M::data32(y[i], aux[i], mc, d);
+  if (i < n) M::data32(y[i], aux[i], mc, d);
+  else
+    for (int c = 0; c < M::kData32; ++c) d[c] = 0.0f;
 #pragma unroll
-  for (int c = 0; c < M::kData32; ++c) d32[c * n + i] = d[c];
+  for (int c = 0; c < M::kData32; ++c) d32[c * n32 + i] = d[c];
 }
 
 // binary32 member data of the d = 3 model: y_ij as hi + lo, 1/(2 s_ij^2) (inputs stored per component)
@@ -688,17 +811,47 @@ int data32_words(int model) {
   return NN1::kData32;
 }
 
-cudaError_t launch_data32(int model, long long n, const double* y, const double* aux, const ModelConsts& mc,
-                          float* d32, cudaStream_t st) {
+cudaError_t launch_data32(int model, long long n, long long n32, const double* y, const double* aux,
+                          const ModelConsts& mc, float* d32, cudaStream_t st) {
   const int blk = 256;
-  const unsigned int grid = static_cast<unsigned int>((n + blk - 1) / blk);
-  if (model == CUDAHM_LF) data32_kernel<LF><<<grid, blk, 0, st>>>(n, y, aux, mc, d32);
+  const unsigned int grid = static_cast<unsigned int>((n32 + blk - 1) / blk);
+  if (model == CUDAHM_LF) data32_kernel<LF><<<grid, blk, 0, st>>>(n, n32, y, aux, mc, d32);
   else if (model == CUDAHM_MVN3 || model == CUDAHM_NN3) data32_mvn3_kernel<<<grid, blk, 0, st>>>(n, y, aux, d32);
-  else data32_kernel<NN1><<<grid, blk, 0, st>>>(n, y, aux, mc, d32);
+  else data32_kernel<NN1><<<grid, blk, 0, st>>>(n, n32, y, aux, mc, d32);
   return cudaGetLastError();
 }
 
-size_t batch_smem_bytes(int) { return sizeof(double) * kMathWords; }
+// FP32 form, d = 1: binary32 latents into the state array (and zeros in its padding), and back
+__global__ void chi_to32_kernel(long long n, long long n32, const double* chi, float* chi32) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n32) chi32[i] = (i < n) ? static_cast<float>(chi[i]) : 0.0f;
+}
+__global__ void chi_from32_kernel(long long n, const float* chi32, double* chi) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) chi[i] = static_cast<double>(chi32[i]);
+}
+
+cudaError_t launch_chi_to32(long long n, long long n32, const double* chi, float* chi32, cudaStream_t st) {
+  chi_to32_kernel<<<static_cast<unsigned int>((n32 + 255) / 256), 256, 0, st>>>(n, n32, chi, chi32);
+  return cudaGetLastError();
+}
+cudaError_t launch_chi_from32(long long n, const float* chi32, double* chi, cudaStream_t st) {
+  chi_from32_kernel<<<static_cast<unsigned int>((n + 255) / 256), 256, 0, st>>>(n, chi32, chi);
+  return cudaGetLastError();
+}
+
+// Dynamic shared memory of the batched kernel: the exp/log tables, and in the FP32 form (whose
+// one-dimensional populations stream member tiles) two stages of 2 x block members of
+// 4 + 8 + 4 kData32 bytes, plus slack to align them to 128 bytes.
+size_t batch_smem_bytes(bool f32, bool, int block) {
+  size_t b = sizeof(double) * kMathWords;
+  if (f32) {
+    static_assert(LF::kData32 == NN1::kData32, "one tile layout for the one-dimensional models");
+    const size_t per = 12u + 4u * static_cast<size_t>(LF::kData32);
+    b = tile_offset_bytes() + 128u + 2u * (2u * static_cast<size_t>(block)) * per;
+  }
+  return b;
+}
 
 cudaError_t batch_occupancy(bool f32, bool d1, int block, int smem_bytes, int* blocks_per_sm) {
   const void* fn = batch_fn(f32, d1);

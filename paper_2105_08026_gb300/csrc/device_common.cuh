@@ -281,4 +281,57 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int i
   return s_ok != 0;
 }
 
+// ------------------------------------------------ bulk copies (TMA engine) --
+// One-dimensional bulk copies global -> shared (cp.async.bulk), completed on an mbarrier that
+// counts the bytes. Source and destination must be 16-byte aligned and the size a multiple of 16.
+__device__ __forceinline__ unsigned int smem_addr(const void* p) {
+  return static_cast<unsigned int>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" : : "r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// the issuing thread's arrival, announcing the bytes the copies on this barrier will deliver
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned int bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" : : "r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned int parity) {
+  unsigned int done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0u;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned int bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :
+               : "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+// orders this thread's earlier generic-proxy writes to global memory before later bulk copies
+// (async proxy) that read them
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" : : : "memory");
+}
+// makes mbarrier initialisation visible to the async proxy
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.proxy.async.shared::cta;" : : : "memory");
+}
+// Waits (the calling thread) until the barrier's phase `parity` has completed, bounded by
+// limit_ns of %globaltimer; on expiry records CUDAHM_ETIMEOUT and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned int parity, int* err,
+                                                  long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer_ns() - t0 > limit_ns) {
+      atomicCAS(err, 0, CUDAHM_ETIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
 }  // namespace chm

@@ -103,7 +103,10 @@ struct SweepArgs {
   long long timeout_ns;
   int skip_cta;
   double gamma;       // adaptation exponent (eta = n^-gamma)
-  const float* d32;   // FP32 form: precomputed binary32 member data (kData32 x n, member-minor)
+  const float* d32;   // FP32 form: precomputed binary32 member data (kData32 x n32, member-minor)
+  float* chi32;       // FP32 form, d = 1: the latents (binary32 state; chi is a binary64 copy for the API)
+  long long n32;      // FP32 form, d = 1: row stride of d32 and padded length of chi32 and S (a multiple
+                      // of kTilePad, so that bulk copies of aligned member tiles stay in bounds); else n
   double* pub;        // theta' of the current sweep, published by block 0 (kPubWords doubles);
                       // its sequence word is bar[1]
   double* marg_lp;           // marginal form: log p_i at two thetas, [2][n]
@@ -122,6 +125,12 @@ struct SweepArgs {
 };
 
 constexpr int kPubWords = 32;
+
+// FP32 form, d = 1: member arrays are padded to a multiple of kTilePad members, and the
+// streaming kernel stages member tiles of kTileMembers (a multiple of 4: 16-byte aligned bulk
+// copies of binary32 and binary64 arrays) through shared memory.
+constexpr long long kTilePad = 64;
+constexpr int kTileMembers = 512;
 
 // Tabulated inner sum of the selection rule: Chebyshev series of degree kHDeg on cells of
 // width kHDelta in u = ln L.
@@ -148,14 +157,16 @@ struct BatchProg {
 };
 
 // Batched launches (batch.cu).
-size_t batch_smem_bytes(int seg_slots);
+size_t batch_smem_bytes(bool f32, bool d1, int block);
 // d1: every population has a one-dimensional latent (the lighter kernel variant)
 cudaError_t batch_occupancy(bool f32, bool d1, int block, int smem_bytes, int* blocks_per_sm);
 cudaError_t launch_batch(bool f32, bool d1, const SweepArgs* pops, BatchProg* progs, const int* b0s, const int* nbs,
                          int npop, int chunk, int seg_slots, int grid, int block, int smem_bytes, cudaStream_t st);
 cudaError_t launch_batch_tables(const SweepArgs* pops, const BatchProg* progs, int npop, int chunk, cudaStream_t st);
-cudaError_t launch_data32(int model, long long n, const double* y, const double* aux, const ModelConsts& mc,
-                          float* d32, cudaStream_t st);
+cudaError_t launch_data32(int model, long long n, long long n32, const double* y, const double* aux,
+                          const ModelConsts& mc, float* d32, cudaStream_t st);
+cudaError_t launch_chi_to32(long long n, long long n32, const double* chi, float* chi32, cudaStream_t st);
+cudaError_t launch_chi_from32(long long n, const float* chi32, double* chi, cudaStream_t st);
 int data32_words(int model);
 
 // Marginal form (marginal.cu).
@@ -194,7 +205,8 @@ cudaError_t launch_gauss_legendre(int n, double* x, double* w, cudaStream_t st);
 cudaError_t launch_lf_inner(int nr, const double* xr, const double* wr, double r_max, double sigma_F, double* qs,
                             double* Wr, cudaStream_t st);
 cudaError_t launch_tables(int p, uint32_t key0, uint32_t key1, long long k0, long long ns, double gamma, double* U,
-                          double* u, double* lnu, double* eta, cudaStream_t st);
+                          double* u, double* lnu, double* eta, unsigned int* bar, unsigned long long* acc, int nacc,
+                          int* err, cudaStream_t st);
 cudaError_t launch_eval_logdens(int model, bool f32, long long n, const double* y, const double* aux,
                                 const double* chi, const double* theta_dev, const ModelConsts& mc,
                                 const double* math_tab, double* out, cudaStream_t st);

@@ -11,9 +11,12 @@
 //
 // The array belongs to every GPU that loads the library and stays allocated until the
 // process exits. All calls on a device share it and it keeps what the last call wrote;
-// nothing in it needs to start at zero (each call rewrites every table and every partial
-// it reads). Calls whose work overlaps on the GPU (two host threads, or two streams)
-// race on the array and may return wrong values: serialise them.
+// nothing in it needs to start at zero. A call rebuilds the rule tables unless the previous
+// call on the device built them for the same n_L, n_r, r_max and sigma_F (then it only
+// rewrites the partial sums it reads). Calls whose work overlaps on the GPU (two host
+// threads, or two streams) race on the array and may return wrong values: serialise them,
+// and when consecutive calls use different streams, let the earlier call's work finish
+// first (a call that reuses the tables reads what the earlier one wrote).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -39,6 +42,15 @@ static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_addr[kMaxDevices] = {nullptr};
+// What the array's rule tables were last built for, per device: the Gauss-Legendre nodes and the
+// inner-rule tables depend on (n_L, n_r, r_max, sigma_F) only; the normal-CDF and exp/log tables
+// on nothing. A call with the same constants skips the rebuild (about a millisecond of kernels).
+struct RuleTag {
+  bool valid;
+  int nL, nr;
+  double rmax, sigF;
+};
+RuleTag g_tag[kMaxDevices] = {};
 
 int noalloc_fail(int code, const char* msg) { return record_error(code, msg); }
 
@@ -65,6 +77,7 @@ extern "C" int cudahm_lf_etabar_noalloc(const double* theta_dev, const double* c
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return noalloc_fail(CUDAHM_ECUDA, "cannot query the current device");
   double* base = nullptr;
+  bool rebuild = true;
   {
     // once per device, with that device current: the device address of the fixed array
     std::lock_guard<std::mutex> lk(g_mu);
@@ -75,6 +88,9 @@ extern "C" int cudahm_lf_etabar_noalloc(const double* theta_dev, const double* c
       g_addr[dev] = static_cast<double*>(p);
     }
     base = g_addr[dev];
+    const RuleTag& t = g_tag[dev];
+    rebuild = !(t.valid && t.nL == nL && t.nr == nr && t.rmax == rmax && t.sigF == sigF);
+    g_tag[dev].valid = false;  // set again below once the rebuild is enqueued
   }
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -94,14 +110,18 @@ extern "C" int cudahm_lf_etabar_noalloc(const double* theta_dev, const double* c
   if (phi_table_words() > kPhiWordsMax) return noalloc_fail(CUDAHM_ECUDA, "normal-CDF table larger than its slot");
   if (math_table_words() > kMathWordsMax) return noalloc_fail(CUDAHM_ECUDA, "exp/log table larger than its slot");
 
-  // every table this call reads is rewritten here, on the caller's stream
-  cudaError_t e = launch_gauss_legendre(nL, xL, wL, st);
-  if (e == cudaSuccess) e = launch_gauss_legendre(nr, xr, wr, st);
-  if (e == cudaSuccess) e = launch_lf_inner(nr, xr, wr, rmax, sigF, qs, Wr, st);
-  if (e == cudaSuccess) e = launch_phi_table(phi, st);
-  if (e == cudaSuccess) e = launch_math_table(mtab, st);
-  if (e == cudaSuccess) e = launch_prefix_weights(nr, Wr, cw, st);
-  if (e != cudaSuccess) return noalloc_fail(CUDAHM_ECUDA, cudaGetErrorString(e));
+  // the rule tables, rewritten on the caller's stream unless the last call built them for the
+  // same constants
+  cudaError_t e = cudaSuccess;
+  if (rebuild) {
+    e = launch_gauss_legendre(nL, xL, wL, st);
+    if (e == cudaSuccess) e = launch_gauss_legendre(nr, xr, wr, st);
+    if (e == cudaSuccess) e = launch_lf_inner(nr, xr, wr, rmax, sigF, qs, Wr, st);
+    if (e == cudaSuccess) e = launch_phi_table(phi, st);
+    if (e == cudaSuccess) e = launch_math_table(mtab, st);
+    if (e == cudaSuccess) e = launch_prefix_weights(nr, Wr, cw, st);
+    if (e != cudaSuccess) return noalloc_fail(CUDAHM_ECUDA, cudaGetErrorString(e));
+  }
 
   SweepArgs rule{};
   rule.model = CUDAHM_LF;
@@ -121,6 +141,10 @@ extern "C" int cudahm_lf_etabar_noalloc(const double* theta_dev, const double* c
   rule.rows_smem = static_cast<int>((G + grid - 1) / grid);
   e = launch_eval_etabar(theta_dev, rule, partials, grid, etabar_dev, st);
   if (e != cudaSuccess) return noalloc_fail(CUDAHM_ECUDA, cudaGetErrorString(e));
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tag[dev] = RuleTag{true, nL, nr, rmax, sigF};
+  }
   return CUDAHM_OK;
 }
 

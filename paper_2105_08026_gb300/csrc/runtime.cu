@@ -85,8 +85,46 @@ int rule_nL(const cudahm_config& c) { return static_cast<int>(c.model_consts[c.m
 int rule_nr(const cudahm_config& c) { return static_cast<int>(c.model_consts[c.model == CUDAHM_BB1 ? 5 : 4]); }
 
 constexpr long long kChunk = 4096;  // sweeps per persistent launch
-// checkpoint layout version: 2 = ChainState with the running-moment and pending theta-update fields
-constexpr int64_t kCheckpointVersion = 2;
+// checkpoint layout version: 2 = ChainState with the running-moment and pending theta-update
+// fields; 3 = a header of 10 words with a hash of the chain's configuration
+constexpr int64_t kCheckpointVersion = 3;
+constexpr int kHeaderWords = 10;
+constexpr int64_t kCheckpointMagic = 0x4d48414455434f4bll;
+
+// model constants each model reads (the rest of model_consts is unused)
+int consts_used(int m) {
+  switch (m) {
+    case CUDAHM_NN1: return 2;
+    case CUDAHM_LF: return 6;
+    case CUDAHM_BB1: return 8;
+    case CUDAHM_NN3: return 6;
+    default: return 0;
+  }
+}
+
+// FNV-1a hash of everything a chain's continuation depends on besides its state: model, sizes,
+// precision, form, seed, the RAM settings and the model constants (the rule sizes and limits
+// among them). The start values (theta_init, its proposal scales, chi_init_scale) are not in it:
+// a restored checkpoint replaces the state they set.
+uint64_t config_hash(const cudahm_config& c) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&h](const void* p, size_t bytes) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t q = 0; q < bytes; ++q) {
+      h ^= b[q];
+      h *= 1099511628211ull;
+    }
+  };
+  const int32_t ints[7] = {c.model, c.precision, c.d, c.adapt_theta, c.marginal, c.keep_chi_moments, 0};
+  mix(ints, sizeof(ints));
+  mix(&c.n, sizeof(c.n));
+  mix(&c.seed, sizeof(c.seed));
+  mix(&c.target_accept, sizeof(double));
+  mix(&c.adapt_exponent, sizeof(double));
+  mix(&c.theta_target_accept, sizeof(double));
+  mix(c.model_consts, sizeof(double) * consts_used(c.model));
+  return h;
+}
 
 }  // namespace
 
@@ -126,6 +164,10 @@ struct cudahm {
   double* phi_coef = nullptr;
   double* cw = nullptr;
   float* d32 = nullptr;
+  // FP32 form, d = 1: the binary32 latent state (chi holds its binary64 copy for the API; it is
+  // refreshed before every read and copied in after every write of chi) and the padded length
+  float* chi32 = nullptr;
+  long long n32 = 0;
   double* math_tab = nullptr;
   double* pub = nullptr;  // theta' published by block 0 of the sweep kernel
   unsigned long long* eb_partials = nullptr;
@@ -381,6 +423,8 @@ SweepArgs base_args(cudahm* h) {
   a.skip_cta = h->cfg.debug_skip_barrier_cta;
   a.gamma = h->cfg.adapt_exponent;
   a.d32 = h->d32;
+  a.chi32 = h->chi32;
+  a.n32 = h->n32;
   a.tab_U = h->tab_U;
   a.tab_u = h->tab_u;
   a.tab_lnu = h->tab_lnu;
@@ -404,7 +448,74 @@ SweepArgs base_args(cudahm* h) {
 // above ub every pair has x >= 8.5 (Phi = 1; LF: L q_min >= F_th + 8.5 sigma_F, BB1:
 // L q_min >= F_pre), or, for BB1 when x never reaches 8.5, x has reached its limit 1/alpha to
 // rounding (L q_min >= 2^56 F_th).
+// Set-up tables computed on the device once per process and then kept on the host: a handle
+// that needs a table already computed (a Gauss-Legendre rule of the same size, the tabulated
+// inner sum of the same selection rule) gets it by a host-to-device copy instead of the kernels
+// (about half a millisecond per 1024-node rule, 0.4 ms per tabulated rule: a served request
+// creates its handle on the request's path). The values are the ones the kernels gave, bit for
+// bit. At most kTabCacheMax tables are kept (the cache starts over when full).
+constexpr size_t kTabCacheMax = 256;
+std::mutex g_tab_mu;
+std::map<std::string, std::vector<double>> g_tab_cache;
+
+std::string tab_key(const char* kind, int model, const double* v, int nv, long long extra) {
+  std::string k(kind);
+  k.append(reinterpret_cast<const char*>(&model), sizeof(model));
+  k.append(reinterpret_cast<const char*>(&extra), sizeof(extra));
+  k.append(reinterpret_cast<const char*>(v), sizeof(double) * static_cast<size_t>(nv));
+  return k;
+}
+bool tab_get(const std::string& key, std::vector<double>& out) {
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  auto it = g_tab_cache.find(key);
+  if (it == g_tab_cache.end()) return false;
+  out = it->second;
+  return true;
+}
+void tab_put(const std::string& key, std::vector<double> v) {
+  std::lock_guard<std::mutex> lk(g_tab_mu);
+  if (g_tab_cache.size() >= kTabCacheMax) g_tab_cache.clear();
+  g_tab_cache[key] = std::move(v);
+}
+
+// n-node Gauss-Legendre rule on [-1, 1] into x, w (device)
+int gl_rule(cudahm* h, int n, double* x, double* w) {
+  const std::string key = tab_key("gl", 0, nullptr, 0, n);
+  std::vector<double> v;
+  if (tab_get(key, v)) {
+    CU(cudaMemcpyAsync(x, v.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(w, v.data() + n, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));  // the host copy is not pinned
+    return CUDAHM_OK;
+  }
+  CU(launch_gauss_legendre(n, x, w, h->stream));
+  v.resize(2 * static_cast<size_t>(n));
+  CU(cudaMemcpyAsync(v.data(), x, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaMemcpyAsync(v.data() + n, w, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  tab_put(key, std::move(v));
+  return CUDAHM_OK;
+}
+
 int build_htab(cudahm* h) {
+  // cached: [ua, ub, h_lo, h_hi, ncell, coefficients of every cell, the two end values]
+  const std::string key = tab_key("htab", h->cfg.model, h->cfg.model_consts, consts_used(h->cfg.model), 0);
+  {
+    std::vector<double> v;
+    if (tab_get(key, v)) {
+      const int ncell = static_cast<int>(v[4]);
+      const size_t words = static_cast<size_t>(ncell) * (kHDeg + 1) + 2;
+      TRY(alloc_into(h, &h->htab, words));
+      CU(cudaMemcpyAsync(h->htab, v.data() + 5, sizeof(double) * words, cudaMemcpyHostToDevice, h->stream));
+      CU(cudaStreamSynchronize(h->stream));
+      h->h_ua = v[0];
+      h->h_ub = v[1];
+      h->h_lo = v[2];
+      h->h_hi = v[3];
+      h->h_ncell = ncell;
+      return CUDAHM_OK;
+    }
+  }
   const int nr = rule_nr(h->cfg);
   std::vector<double> qs(static_cast<size_t>(nr));
   CU(cudaMemcpyAsync(qs.data(), h->qs, sizeof(double) * nr, cudaMemcpyDeviceToHost, h->stream));
@@ -440,6 +551,16 @@ int build_htab(cudahm* h) {
   h->h_lo = ends[0];
   h->h_hi = ends[1];
   h->h_ncell = ncell;
+  const size_t words = static_cast<size_t>(ncell) * (kHDeg + 1) + 2;
+  std::vector<double> v(5 + words);
+  v[0] = h->h_ua;
+  v[1] = h->h_ub;
+  v[2] = h->h_lo;
+  v[3] = h->h_hi;
+  v[4] = ncell;
+  CU(cudaMemcpyAsync(v.data() + 5, h->htab, sizeof(double) * words, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  tab_put(key, std::move(v));
   return CUDAHM_OK;
 }
 
@@ -526,6 +647,19 @@ int compute_etabar_into(cudahm* h, const double* theta_dev, double* out_dev) {
   return CUDAHM_OK;
 }
 
+// FP32 form with d = 1: the binary32 latents are the state
+bool has_chi32(const cudahm* h) { return h->chi32 != nullptr; }
+// chi (binary64 copy) -> chi32 after chi was written
+int chi_to_state(cudahm* h) {
+  if (has_chi32(h)) CU(launch_chi_to32(h->n, h->n32, h->chi, h->chi32, h->stream));
+  return CUDAHM_OK;
+}
+// chi32 -> chi before chi is read
+int chi_from_state(cudahm* h) {
+  if (has_chi32(h)) CU(launch_chi_from32(h->n, h->chi32, h->chi, h->stream));
+  return CUDAHM_OK;
+}
+
 int prepare(cudahm* h, const double* y_dev_raw, const double* aux_dev_raw, int set_default) {
   CU(cudaMemsetAsync(h->bad, 0, sizeof(int), h->stream));
   CU(launch_prepare(h->cfg.model, h->n, y_dev_raw, aux_dev_raw, h->y, h->aux, h->chi, h->S, h->mc, h->cfg.theta_init,
@@ -536,9 +670,10 @@ int prepare(cudahm* h, const double* y_dev_raw, const double* aux_dev_raw, int s
   bad = *h->host_err;
   if (bad)
     return fail(CUDAHM_EINVAL, "%d members have non-finite data or a non-positive scale (or, marginal LF, flux)", bad);
+  if (set_default) TRY(chi_to_state(h));
   if (h->cfg.precision == CUDAHM_FP32) {  // binary32 member data for the batched FP32 form
-    if (!h->d32) TRY(alloc_into(h, &h->d32, static_cast<size_t>(data32_words(h->cfg.model)) * h->n));
-    CU(launch_data32(h->cfg.model, h->n, h->y, h->aux, h->mc, h->d32, h->stream));
+    if (!h->d32) TRY(alloc_into(h, &h->d32, static_cast<size_t>(data32_words(h->cfg.model)) * h->n32));
+    CU(launch_data32(h->cfg.model, h->n, h->n32, h->y, h->aux, h->mc, h->d32, h->stream));
     if (h->cfg.marginal && h->cfg.model == CUDAHM_LF) {  // the FP32 marginal form's window data
       if (!h->marg_d32) TRY(alloc_into(h, &h->marg_d32, static_cast<size_t>(kMarg32Words) * h->n));
       CU(launch_marg_data32(h->n, h->y, h->aux, h->mc, h->math_tab, h->marg_d32, h->stream));
@@ -661,8 +796,13 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
   const long long n = h->n;
   const int p = h->p;
   h->factor_n = n * factor_words(h->d);
+  // FP32 form, d = 1: member arrays padded to whole aligned tiles (bulk copies stay in bounds)
+  const bool tiled = cfg->precision == CUDAHM_FP32 && h->d == 1 && !cfg->marginal;
+  h->n32 = tiled ? (n + kTilePad - 1) / kTilePad * kTilePad : n;
   if ((rc = alloc_into(h, &h->y, n * h->d)) || (rc = alloc_into(h, &h->aux, n * h->d)) ||
-      (rc = alloc_into(h, &h->chi, n * h->d)) || (rc = alloc_into(h, &h->S, h->factor_n)) ||
+      (rc = alloc_into(h, &h->chi, n * h->d)) ||
+      (rc = alloc_into(h, &h->S, tiled ? h->n32 : h->factor_n)) ||
+      (tiled && (rc = alloc_into(h, &h->chi32, h->n32))) ||
       (rc = alloc_into(h, &h->chain, 1)) ||
       (rc = alloc_into(h, &h->acc3, 3ull * kAccWords)) ||
       (rc = alloc_into(h, &h->bar, 4)) ||
@@ -686,9 +826,9 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
       return bail(rc);
     if (launch_phi_table(h->phi_coef, h->stream) != cudaSuccess)
       return bail(fail(CUDAHM_ECUDA, "normal-CDF table set-up failed: %s", cudaGetErrorString(cudaGetLastError())));
-    if (launch_gauss_legendre(nL, h->xL, h->wL, h->stream) != cudaSuccess ||
-        launch_gauss_legendre(nr, h->xr, h->wr, h->stream) != cudaSuccess ||
-        launch_lf_inner(nr, h->xr, h->wr, r_max, sigma_F, h->qs, h->Wr, h->stream) != cudaSuccess ||
+    if ((rc = gl_rule(h, nL, h->xL, h->wL)) != CUDAHM_OK || (rc = gl_rule(h, nr, h->xr, h->wr)) != CUDAHM_OK)
+      return bail(rc);
+    if (launch_lf_inner(nr, h->xr, h->wr, r_max, sigma_F, h->qs, h->Wr, h->stream) != cudaSuccess ||
         launch_prefix_weights(nr, h->Wr, h->cw, h->stream) != cudaSuccess)
       return bail(fail(CUDAHM_ECUDA, "quadrature set-up failed: %s", cudaGetErrorString(cudaGetLastError())));
     if ((rc = build_htab(h)) != CUDAHM_OK) return bail(rc);
@@ -763,6 +903,7 @@ int cudahm_set_chi(cudahm_t h, const double* chi_host, int64_t n) {
     return fail(CUDAHM_EINVAL, "%d latents are non-finite or off the support at theta", *h->host_err);
   }
   CU(cudaMemcpyAsync(h->chi, tmp, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, h->stream));
+  TRY(chi_to_state(h));
   CU(cudaStreamSynchronize(h->stream));
   h->dfree(tmp);
   return CUDAHM_OK;
@@ -791,7 +932,6 @@ int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
   }
   const long long T = std::min<long long>(h->cfg.trace_sweeps, total);
   TRY(ensure_trace(h, T));
-  CU(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
   CU(cudaEventRecord(h->ev0, h->stream));
   if (has_rule(h->cfg.model) && !h->etabar_valid) {
     // selection integral at the current theta, once per chain (kept on the device afterwards)
@@ -828,12 +968,13 @@ int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
   a.tab_lnu = h->tab_lnu;
   a.tab_eta = h->tab_eta;
   long long off = 0, rows_done = 0;
+  if (total == 0) CU(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));  // else cleared by the first chunk
   while (off < total) {
     const long long ns = std::min<long long>(kChunk, total - off);
+    // theta tables of this chunk; also clears the barrier count and theta' sequence, the grid
+    // totals, and (first chunk) the run's error word
     CU(launch_tables(h->p, a.key0, a.key1, h->sweeps, ns, h->cfg.adapt_exponent, h->tab_U, h->tab_u, h->tab_lnu,
-                     h->tab_eta, h->stream));
-    CU(cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned int), h->stream));  // barrier count, theta' sequence
-    CU(cudaMemsetAsync(h->acc3, 0, sizeof(unsigned long long) * 3 * kAccWords, h->stream));
+                     h->tab_eta, h->bar, h->acc3, 3 * kAccWords, off == 0 ? h->err : nullptr, h->stream));
     a.k0 = h->sweeps;
     a.ns = ns;
     a.burn_left = n_burn - off;
@@ -909,8 +1050,10 @@ int cudahm_get_chi(cudahm_t h, double* chi_host, double* S_host) {
     }
     return CUDAHM_OK;
   }
-  if (chi_host)
+  if (chi_host) {
+    TRY(chi_from_state(h));
     CU(cudaMemcpyAsync(chi_host, h->chi, sizeof(double) * h->n * h->d, cudaMemcpyDeviceToHost, h->stream));
+  }
   if (S_host)
     CU(cudaMemcpyAsync(S_host, h->S, sizeof(double) * h->n * h->d * h->d, cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
@@ -1001,6 +1144,7 @@ int cudahm_eval_logdens(cudahm_t h, const double* theta_host, double* lp_host) {
   double* out = nullptr;
   TRY(alloc_into(h, &out, h->n));
   CU(cudaMemcpyAsync(h->theta_dev, theta_host, sizeof(double) * h->p, cudaMemcpyHostToDevice, h->stream));
+  TRY(chi_from_state(h));
   CU(launch_eval_logdens(h->cfg.model, h->cfg.precision == CUDAHM_FP32, h->n, h->y, h->aux, h->chi, h->theta_dev,
                          h->mc, h->math_tab, out, h->stream));
   CU(cudaMemcpyAsync(lp_host, out, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->stream));
@@ -1071,24 +1215,27 @@ int cudahm_get_trace(cudahm_t h, double* delta, double* u, uint8_t* acc, double*
   return CUDAHM_OK;
 }
 
-// Checkpoint layout: header (8 x int64), ChainState, then the latents and RAM factors as the
-// device holds them (d = 1: chi[n], S[n]; d = 3: chi[3][n], S[6][n]).
+// Checkpoint layout: header (10 x int64: magic, layout version, model, n, d, p, seed, data set,
+// configuration hash, 0), ChainState, then the latents and RAM factors as the device holds them
+// (d = 1: chi[n], S[n]; d = 3: chi[3][n], S[6][n]), then the committed moments when kept.
 int cudahm_checkpoint(cudahm_t h, void* buf, size_t cap, size_t* used) {
   if (!h || !used) return fail(CUDAHM_EINVAL, "NULL argument");
   const size_t nchi = static_cast<size_t>(h->n) * h->d, nS = static_cast<size_t>(h->factor_n);
   const size_t nmom = h->mom ? 2 * nchi : 0;  // the committed moments
-  const size_t need = 8 * sizeof(int64_t) + sizeof(ChainState) + sizeof(double) * (nchi + nS + nmom);
+  const size_t need = kHeaderWords * sizeof(int64_t) + sizeof(ChainState) + sizeof(double) * (nchi + nS + nmom);
   *used = need;
   if (!buf) return CUDAHM_OK;
   if (cap < need) return fail(CUDAHM_EINVAL, "checkpoint buffer too small: need %zu bytes", need);
   CU(cudaSetDevice(h->cfg.device));
-  int64_t hdr[8] = {0x4d48414455434f4bll, kCheckpointVersion, h->cfg.model, h->n, h->d, h->p, static_cast<int64_t>(h->cfg.seed),
-                    h->data_set ? 1 : 0};
+  int64_t hdr[kHeaderWords] = {kCheckpointMagic, kCheckpointVersion, h->cfg.model, h->n, h->d, h->p,
+                               static_cast<int64_t>(h->cfg.seed), h->data_set ? 1 : 0,
+                               static_cast<int64_t>(config_hash(h->cfg)), 0};
   char* c = static_cast<char*>(buf);
   std::memcpy(c, hdr, sizeof(hdr));
   c += sizeof(hdr);
   CU(cudaMemcpyAsync(c, h->chain, sizeof(ChainState), cudaMemcpyDeviceToHost, h->stream));
   c += sizeof(ChainState);
+  TRY(chi_from_state(h));
   CU(cudaMemcpyAsync(c, h->chi, sizeof(double) * nchi, cudaMemcpyDeviceToHost, h->stream));
   c += sizeof(double) * nchi;
   CU(cudaMemcpyAsync(c, h->S, sizeof(double) * nS, cudaMemcpyDeviceToHost, h->stream));
@@ -1109,21 +1256,33 @@ int cudahm_restore(cudahm_t h, const void* buf, size_t size) {
   if (!h->data_set) return fail(CUDAHM_ESTATE, "restore needs set_data first");
   const size_t nchi = static_cast<size_t>(h->n) * h->d, nS = static_cast<size_t>(h->factor_n);
   const size_t nmom = h->mom ? 2 * nchi : 0;
-  const size_t need = 8 * sizeof(int64_t) + sizeof(ChainState) + sizeof(double) * (nchi + nS + nmom);
-  if (size < need) return fail(CUDAHM_EINVAL, "checkpoint buffer too small");
-  int64_t hdr[8];
+  const size_t need = kHeaderWords * sizeof(int64_t) + sizeof(ChainState) + sizeof(double) * (nchi + nS + nmom);
+  if (size < kHeaderWords * sizeof(int64_t)) return fail(CUDAHM_EINVAL, "checkpoint buffer too small");
+  int64_t hdr[kHeaderWords];
   const char* c = static_cast<const char*>(buf);
   std::memcpy(hdr, c, sizeof(hdr));
-  if (hdr[0] != 0x4d48414455434f4bll || hdr[1] != kCheckpointVersion || hdr[2] != h->cfg.model || hdr[3] != h->n || hdr[4] != h->d ||
-      hdr[5] != h->p || hdr[6] != static_cast<int64_t>(h->cfg.seed))
+  if (hdr[0] != kCheckpointMagic || hdr[1] != kCheckpointVersion)
+    return fail(CUDAHM_EINVAL, "not a checkpoint of this layout version (%d)", static_cast<int>(kCheckpointVersion));
+  if (hdr[2] != h->cfg.model || hdr[3] != h->n || hdr[4] != h->d || hdr[5] != h->p ||
+      hdr[6] != static_cast<int64_t>(h->cfg.seed) || hdr[8] != static_cast<int64_t>(config_hash(h->cfg)))
     return fail(CUDAHM_EINVAL, "checkpoint does not match this handle's configuration");
+  if (size < need) return fail(CUDAHM_EINVAL, "checkpoint buffer too small");
   c += sizeof(hdr);
   ChainState cs;
   std::memcpy(&cs, c, sizeof(cs));
+  // the chain state indexes device buffers and sizes launches: check it before any copy
+  bool ok = (cs.mom_sel == 0 || cs.mom_sel == 1) && (cs.mcur == 0 || cs.mcur == 1) && cs.sweeps >= 0 &&
+            cs.sweeps < (1ll << 32) - 2 && cs.mom_n >= 0 && cs.mom_n <= cs.sweeps && cs.member_acc >= 0 &&
+            cs.theta_acc >= 0 && cs.rows >= 0 && std::isfinite(cs.pend_alpha) && std::isfinite(cs.pend_eta) &&
+            cs.pend_eta >= 0.0 && std::isfinite(cs.etabar) && cs.etabar >= 0.0;
+  for (int q = 0; q < h->p && ok; ++q) ok = std::isfinite(cs.theta[q]) && std::isfinite(cs.pend_U[q]);
+  for (int q = 0; q < h->p * h->p && ok; ++q) ok = std::isfinite(cs.S_theta[q]);
+  if (!ok) return fail(CUDAHM_EINVAL, "checkpoint chain state is out of range");
   CU(cudaSetDevice(h->cfg.device));
   CU(cudaMemcpyAsync(h->chain, c, sizeof(ChainState), cudaMemcpyHostToDevice, h->stream));
   c += sizeof(ChainState);
   CU(cudaMemcpyAsync(h->chi, c, sizeof(double) * nchi, cudaMemcpyHostToDevice, h->stream));
+  TRY(chi_to_state(h));
   c += sizeof(double) * nchi;
   CU(cudaMemcpyAsync(h->S, c, sizeof(double) * nS, cudaMemcpyHostToDevice, h->stream));
   if (nmom) {
@@ -1134,7 +1293,9 @@ int cudahm_restore(cudahm_t h, const void* buf, size_t size) {
   CU(cudaStreamSynchronize(h->stream));
   h->sweeps = cs.sweeps;
   h->rows_last = 0;
-  h->etabar_valid = (cs.etabar != 0.0);
+  // etabar(theta) is recomputed by this handle's own rule before the next run (the same bits as
+  // the stored value when the rule is the same, which the configuration hash checks)
+  h->etabar_valid = false;
   h->marg_valid = false;  // log p_i is recomputed at the restored theta before the next run
   return CUDAHM_OK;
 }
@@ -1254,7 +1415,6 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
   }
 
   const int R = 128;  // segment slots per block
-  const int smem = static_cast<int>(batch_smem_bytes(R));
   int sms = h0->sms;
 
   BatchBufs bb;
@@ -1319,6 +1479,7 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
     return CUDAHM_OK;
   };
   auto enqueue = [&](int blk, int ch, int grid_) -> cudaError_t {
+    const int smem = static_cast<int>(batch_smem_bytes(f32, d1, blk));
     cudaError_t e = cudaMemsetAsync(bb.bars, 0, sizeof(unsigned int) * k, st);
     if (e == cudaSuccess) e = launch_batch_tables(bb.pops, bb.progs, k, ch, st);
     if (e == cudaSuccess) e = launch_batch(f32, d1, bb.pops, bb.progs, bb.b0s, bb.nbs, k, ch, R, grid_, blk, smem, st);
@@ -1326,7 +1487,7 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
   };
   auto grid_for = [&](int blk, int* out) -> int {
     int bps = 0;
-    CU(batch_occupancy(f32, d1, blk, smem, &bps));
+    CU(batch_occupancy(f32, d1, blk, static_cast<int>(batch_smem_bytes(f32, d1, blk)), &bps));
     if (bps < 1) return fail(CUDAHM_EUNSUPPORTED, "batched kernel does not fit on this device");
     *out = std::min(bps * sms, blk == 128 ? max_grid : max_grid / 2);
     return CUDAHM_OK;
@@ -1477,9 +1638,9 @@ int batch_step(const std::vector<cudahm*>& hs, std::vector<BatchProg>& progs, in
                int max_grid, cudaStream_t st, bool f32) {
   const int k = static_cast<int>(hs.size());
   const int R = 128;
-  const int smem = static_cast<int>(batch_smem_bytes(R));
   bool d1 = true;
   for (const cudahm* h : hs) d1 = d1 && h->d == 1;
+  const int smem = static_cast<int>(batch_smem_bytes(f32, d1, block));
   int bps = 0;
   CU(batch_occupancy(f32, d1, block, smem, &bps));
   if (bps < 1) return fail(CUDAHM_EUNSUPPORTED, "batched kernel does not fit on this device");

@@ -97,13 +97,17 @@ cudaError_t launch_prefix_weights(int nr, const double* Wr, double* cw, cudaStre
 // itself sits between the grid barrier and the next member phase.
 // The RAM factor update of a member's previous step, S <- S sqrt(1 + eta (alpha - alpha_*))
 // (Sec. 2.2, d = 1), with alpha kept in the member's slot of pu (binary64; binary32 in the upper
-// half of the slot array in the FP32 form).
+// half of the slot array in the FP32 form, which takes the one-FMA form ram1_f32 with eta and
+// alpha_* rounded to binary32).
 template <bool F32>
 __device__ __forceinline__ double ram_pending(const SweepArgs& a, double S, double eta, const double* s_pu,
                                               unsigned int q) {
-  const double alpha =
-      F32 ? static_cast<double>(reinterpret_cast<const float*>(s_pu)[a.mpb + q]) : s_pu[q];
-  return S * sqrt(fma(eta, alpha - a.astar, 1.0));
+  if constexpr (F32) {
+    return ram1_f32(S, reinterpret_cast<const float*>(s_pu)[a.mpb + q], __double2float_rn(eta),
+                    __double2float_rn(a.astar));
+  } else {
+    return S * sqrt(fma(eta, s_pu[q] - a.astar, 1.0));
+  }
 }
 
 // The theta-independent half of each member's step for sweep sa of this launch
@@ -128,7 +132,7 @@ __device__ __forceinline__ void sweep_part_a(const SweepArgs& a, long long sa, u
       const unsigned int q = i - nb0;
       if (sa > 0) S[m] = ram_pending<F32>(a, S[m], eta_prev, s_pu, q);
       if constexpr (F32) {
-        // Philox block (0, stream 2, member i, odd sweep k_o): a Box-Muller pair from 24-bit
+        // Philox block (0, stream 2, member i, odd sweep k_o): a Box-Muller pair from 23-bit
         // uniforms of words 0 and 1 (cosine for k_o, sine for k_o + 1), the accept uniforms of
         // k_o (word 2) and k_o + 1 (word 3)
         float d[M::kData32];
@@ -136,14 +140,11 @@ __device__ __forceinline__ void sweep_part_a(const SweepArgs& a, long long sa, u
         for (int c = 0; c < M::kData32; ++c) d[c] = s_d32[c * a.mpb + q];
         const uint4 w = philox4x32_10(make_uint4(0u, 2u, static_cast<uint32_t>(i), odd ? k : k - 1u), a.key0,
                                       a.key1);
-        const float u1 = (static_cast<float>(w.x >> 8) + 0.5f) * 0x1p-24f;
-        const float u2 = (static_cast<float>(w.y >> 8) + 0.5f) * 0x1p-24f;
-        const float u = (static_cast<float>((odd ? w.z : w.w) >> 8) + 0.5f) * 0x1p-24f;
-        const float rad = sqrtf(-2.0f * logf(u1));
-        float sn, cs;
-        sincospif(2.0f * u2, &sn, &cs);
-        const float z = odd ? rad * cs : rad * sn;
-        const float Y = fmaf(static_cast<float>(S[m]), z, chi[m]);
+        const float u = uniform23(odd ? w.z : w.w);
+        float zc, zs;
+        box_muller32(w.x, w.y, zc, zs);
+        const float z = odd ? zc : zs;
+        const float Y = fmaf(f32_rz(S[m]), z, chi[m]);
         // binary32 views of the slots (a conversion to binary64 and back would cost FP64 issue)
         reinterpret_cast<float*>(s_pY)[q] = Y;
         reinterpret_cast<float*>(s_pll)[q] = M::loglike32(Y, d);
@@ -296,7 +297,8 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   for (int m = 0; m < K; ++m) {
     const unsigned int i = nb0 + tid + m * blockDim.x;
     if (i < nb1) {
-      chi[m] = static_cast<R>(a.chi[i]);
+      if constexpr (F32) chi[m] = a.chi32[i];  // the FP32 form's latent state is binary32
+      else chi[m] = a.chi[i];
       S[m] = a.S[i];
       if constexpr (F32) {
         float d[M::kData32];
@@ -360,14 +362,15 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         if (i < nb1) {
           const float Y = reinterpret_cast<const float*>(s_pY)[i - nb0];
           const float u = reinterpret_cast<const float*>(s_pu)[i - nb0];
-          float delta, llY = 0.0f, lfY = 0.0f;
-          const float lfX = M::logf32(chi[m], tf);
+          float delta, llY = 0.0f;
+          F2 lfY{0.0f, 0.0f};
+          const F2 lfX = M::logf32p(chi[m], tf);
           if (!M::support32(Y, tf)) {
             delta = -INFINITY;
           } else {
             llY = reinterpret_cast<const float*>(s_pll)[i - nb0];
-            lfY = M::logf32(Y, tf);
-            delta = (llY + lfY) - (ll[m] + lfX);
+            lfY = M::logf32p(Y, tf);
+            delta = (llY + (lfY.hi + lfY.lo)) - (ll[m] + (lfX.hi + lfX.lo));
           }
           float alpha;
           const bool acc = mh_accept32(delta, u, alpha);
@@ -377,7 +380,9 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
             ll[m] = llY;
             member_acc++;
           }
-          s_lf32[i - nb0] = acc ? lfY : lfX;
+          const F2 lfc = acc ? lfY : lfX;  // hi in the first half of the slots, lo in the second
+          s_lf32[i - nb0] = lfc.hi;
+          s_lf32[a.mpb + (i - nb0)] = lfc.lo;
           reinterpret_cast<float*>(s_pu)[a.mpb + (i - nb0)] = alpha;  // RAM update in the next half-step
           if (trace) {
             const long long o = (a.trace_off + s) * a.n + static_cast<long long>(i);
@@ -443,7 +448,11 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         const unsigned int i = nb0 + tid + m * blockDim.x;
         if (i < nb1) {
           const float c = static_cast<float>(chi[m]);
-          const float dn = M::support32(c, tpf) ? M::logf32(c, tpf) - s_lf32[i - nb0] : -INFINITY;
+          float dn = -INFINITY;
+          if (M::support32(c, tpf)) {  // (hi' - hi) + (lo' - lo), as the streaming kernel forms it
+            const F2 lfp = M::logf32p(c, tpf);
+            dn = __fadd_rn(__fsub_rn(lfp.hi, s_lf32[i - nb0]), __fsub_rn(lfp.lo, s_lf32[a.mpb + (i - nb0)]));
+          }
           if (dn != dn) fd.nan++;
           else if (fabsf(dn) >= 0x1p94f) {
             if (dn < 0.0f) neg_big++;
@@ -523,7 +532,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
 #pragma unroll
       for (int m = 0; m < K; ++m) {
         const unsigned int i = nb0 + tid + m * blockDim.x;
-        if (i < nb1) mom_add(ms, i, static_cast<double>(chi[m]));
+        if (i < nb1) mom_add(ms, i, F32 ? f64_of(static_cast<float>(chi[m])) : static_cast<double>(chi[m]));
       }
     }
     if (s + 1 < a.ns)
@@ -638,7 +647,8 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   for (int m = 0; m < K; ++m) {
     const unsigned int i = nb0 + tid + m * blockDim.x;
     if (i < nb1) {
-      a.chi[i] = static_cast<double>(chi[m]);
+      if constexpr (F32) a.chi32[i] = chi[m];
+      else a.chi[i] = chi[m];
       a.S[i] = (a.ns > 0) ? ram_pending<F32>(a, S[m], eta_last, s_pu, i - nb0) : S[m];
     }
   }
@@ -898,9 +908,18 @@ cudaError_t launch_lf_inner(int nr, const double* xr, const double* wr, double r
 
 // Per-sweep theta tables: p normals (Philox stream 1, member index 0, sweep k; block j gives
 // normals 2j, 2j+1), the accept uniform (first uniform of block ceil(p/2)), eta = (k+1)^-gamma.
+// Thread 0 also resets what the next persistent launch counts from: the grid barrier and theta'
+// sequence words, the grid totals of its first sweeps, and (when given) the run's error word.
 __global__ void tables_kernel(int p, uint32_t key0, uint32_t key1, long long k0, long long ns, double gamma,
-                              double* U, double* u, double* lnu, double* eta) {
+                              double* U, double* u, double* lnu, double* eta, unsigned int* bar,
+                              unsigned long long* acc, int nacc, int* err) {
   const long long s = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s == 0) {
+    bar[0] = 0u;
+    bar[1] = 0u;
+    for (int q = 0; q < nacc; ++q) acc[q] = 0ull;
+    if (err) *err = 0;
+  }
   if (s >= ns) return;
   const uint32_t k = static_cast<uint32_t>(k0 + s + 1);
   const int nblk = (p + 1) / 2;
@@ -920,10 +939,12 @@ __global__ void tables_kernel(int p, uint32_t key0, uint32_t key1, long long k0,
 }
 
 cudaError_t launch_tables(int p, uint32_t key0, uint32_t key1, long long k0, long long ns, double gamma, double* U,
-                          double* u, double* lnu, double* eta, cudaStream_t st) {
+                          double* u, double* lnu, double* eta, unsigned int* bar, unsigned long long* acc, int nacc,
+                          int* err, cudaStream_t st) {
   const int blk = 128;
-  tables_kernel<<<static_cast<unsigned int>((ns + blk - 1) / blk), blk, 0, st>>>(p, key0, key1, k0, ns, gamma, U, u,
-                                                                                 lnu, eta);
+  const long long nthr = ns > 0 ? ns : 1;
+  tables_kernel<<<static_cast<unsigned int>((nthr + blk - 1) / blk), blk, 0, st>>>(p, key0, key1, k0, ns, gamma, U,
+                                                                                   u, lnu, eta, bar, acc, nacc, err);
   return cudaGetLastError();
 }
 
@@ -946,7 +967,8 @@ __global__ void eval_logdens_kernel(long long n, const double* y, const double* 
     }
     float d[M::kData32];
     M::data32(y[i], aux[i], mc, d);
-    out[i] = static_cast<double>(M::loglike32(c, d)) + static_cast<double>(M::logf32(c, tf));
+    const F2 lf = M::logf32p(c, tf);
+    out[i] = static_cast<double>(M::loglike32(c, d)) + (static_cast<double>(lf.hi) + static_cast<double>(lf.lo));
     return;
   }
   const double c = chi[i];

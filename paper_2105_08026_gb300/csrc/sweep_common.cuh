@@ -7,6 +7,7 @@
 #include <type_traits>
 
 #include "device_common.cuh"
+#include "fp32_math.cuh"
 #include "fp64_math.cuh"
 #include "internal.h"
 
@@ -41,6 +42,13 @@ __device__ __forceinline__ void sub2x(float chi, float hi, float lo, float& r_hi
   r_lo = __fsub_rn(err, lo);
 }
 
+// A binary32 value carried as an unevaluated sum hi + lo: lo holds terms below hi's rounding that
+// have the same sign for every member (the rounding parts of a shared constant). Added into hi
+// they would be lost, always the same way, and the sum over members would drift with N.
+struct F2 {
+  float hi, lo;
+};
+
 struct NN1 {
   // a0 = mu, a1 = 1/(2 tau^2)
   using TC = ThetaC;
@@ -62,6 +70,7 @@ struct NN1 {
     const float r2 = __fmaf_rn(rh, rh, __fmul_rn(__fmul_rn(2.0f, rh), rl));
     return -__fmaf_rn(c.sc_hi, r2, __fmul_rn(c.sc_lo, r2));  // the scale's rounding would bias every member alike
   }
+  __device__ static F2 logf32p(float chi, const ThetaCf& c) { return F2{logf32(chi, c), 0.0f}; }
   // member data d[0], d[1] = y_i as hi + lo, d[2] = 1/(2 sigma_i^2)
   static constexpr int kData32 = 3;
   __device__ static void data32(double y, double aux, const ModelConsts&, float* d) {
@@ -114,34 +123,42 @@ struct LF {
     return f;
   }
   __device__ static bool support32(float chi, const ThetaCf& c) { return (chi - c.low_hi) > c.low_lo; }
-  __device__ static float logf32(float chi, const ThetaCf& c) {
+  // log f = sc x - e^x with x = xh + xl and sc = sc_hi + sc_lo, as hi = sc_hi xh - e^xh (one
+  // rounding) plus lo = sc_hi xl + sc_lo xh - e^xh xl (e^(xh + xl) to first order in xl): the
+  // small terms share a sign across members (xl and sc_lo are the roundings of ln L* and beta + 1)
+  // and would be rounded away in hi
+  __device__ static F2 logf32p(float chi, const ThetaCf& c) {
     float xh, xl;
     sub2x(chi, c.loc_hi, c.loc_lo, xh, xl);
-    const float e = expf(xh);
-    const float ex = __fmaf_rn(e, xl, e);  // e^(xh + xl) to first order in xl
-    return __fmaf_rn(c.sc_hi, xh, __fmaf_rn(c.sc_hi, xl, __fmaf_rn(c.sc_lo, xh, -ex)));
+    const float e = exp32(xh);
+    return F2{__fmaf_rn(c.sc_hi, xh, -e), __fmaf_rn(c.sc_hi, xl, __fmaf_rn(c.sc_lo, xh, -__fmul_rn(e, xl)))};
   }
-  // member data: d[0], d[1] = ln(Fhat_i/q_i) as hi + lo, d[2] = Fhat_i^2/(2 sigma_F^2), so that
-  // log l_i = -d[2] expm1(chi - ln(Fhat_i/q_i))^2 keeps binary32 relative accuracy however large
-  // Fhat_i/sigma_F is; members with Fhat_i <= 0 use d[3] = Fhat_i, d[4] = q_i directly (d[2] < 0).
-  static constexpr int kData32 = 5;
+  __device__ static float logf32(float chi, const ThetaCf& c) {
+    const F2 v = logf32p(chi, c);
+    return __fadd_rn(v.hi, v.lo);
+  }
+  // member data: d[0], d[1] = ln(Fhat_i/q_i) as hi + lo, d[2] = Fhat_i^2/(2 sigma_F^2) > 0, so
+  // that log l_i = -d[2] expm1(chi - ln(Fhat_i/q_i))^2 keeps binary32 relative accuracy however
+  // large Fhat_i/sigma_F is; a member with Fhat_i/sigma_F below 1e-3 (none is detected there)
+  // holds d[0] = Fhat_i, d[1] = q_i and the marker d[2] = -1/(2 sigma_F^2) < 0, and evaluates
+  // -(Fhat_i - e^chi q_i)^2/(2 sigma_F^2) directly. Three floats: 12 bytes per member-update.
+  static constexpr int kData32 = 3;
   __device__ static void data32(double y, double aux, const ModelConsts& mc, float* d) {
-    if (y > 0.0) {
+    if (y > 0.0 && y * y * mc.inv2sig2 >= 5e-7) {
       split_f(log(y / aux), d[0], d[1]);
       d[2] = static_cast<float>(y * y * mc.inv2sig2);
-    } else {  // marker: d[2] < 0 holds -1/(2 sigma_F^2)
-      d[0] = d[1] = 0.0f;
+    } else {
+      d[0] = static_cast<float>(y);
+      d[1] = static_cast<float>(aux);
       d[2] = static_cast<float>(-mc.inv2sig2);
     }
-    d[3] = static_cast<float>(y);
-    d[4] = static_cast<float>(aux);
   }
   __device__ static float loglike32(float chi, const float* d) {
-    if (d[2] > 0.0f) {
-      const float e = expm1f(sub2(chi, d[0], d[1]));
+    if (!(d[2] < 0.0f)) {
+      const float e = expm1_32(sub2(chi, d[0], d[1]));
       return __fmul_rn(-d[2], __fmul_rn(e, e));
     }
-    const float r = __fmaf_rn(-expf(chi), d[4], d[3]);
+    const float r = __fmaf_rn(-exp32(chi), d[1], d[0]);
     return __fmul_rn(__fmul_rn(r, r), d[2]);
   }
   __device__ static ThetaC consts(const double* th, const ModelConsts&, const double* T) {
@@ -219,6 +236,7 @@ struct BB1 {
   __device__ static ThetaCf consts32(const ThetaC&) { return ThetaCf{}; }
   __device__ static bool support32(float, const ThetaCf&) { return true; }
   __device__ static float logf32(float, const ThetaCf&) { return 0.0f; }
+  __device__ static F2 logf32p(float, const ThetaCf&) { return F2{0.0f, 0.0f}; }
   __device__ static void data32(double, double, const ModelConsts&, float* d) { d[0] = 0.0f; }
   __device__ static float loglike32(float, const float*) { return 0.0f; }
 };
@@ -628,7 +646,7 @@ __device__ __forceinline__ void etabar_terms(const ThetaC& tc, const SweepArgs& 
 // The member step's Metropolis accept (Sec. 2.2; strict, as ln u < Delta): alpha = min(1, e^Delta)
 // (0 at Delta = -inf), accepted iff u < alpha. Binary64: every Delta with its sign bit clear
 // accepts; otherwise u and alpha are both >= +0, so their bit patterns order as their values.
-// Binary32 (bulk form): the same rule with expf.
+// Binary32 (bulk form): the same rule with the special-function unit's exponential.
 __device__ __forceinline__ bool mh_accept(double delta, double u, const double* s_math, double& alpha) {
   const bool dneg = dsign(delta);  // -inf and -0 included
   alpha = dneg ? exp_tab(delta, s_math) : 1.0;
@@ -636,8 +654,71 @@ __device__ __forceinline__ bool mh_accept(double delta, double u, const double* 
 }
 
 __device__ __forceinline__ bool mh_accept32(float delta, float u, float& alpha) {
-  alpha = (delta >= 0.0f) ? 1.0f : expf(delta);
+  alpha = (delta >= 0.0f) ? 1.0f : __expf(delta);  // the special-function unit's 2^x (a few ulp)
   return (delta >= 0.0f) || (u < alpha);
+}
+
+// Binary32 uniform in (0, 1) of the FP32 bulk form from one Philox word: (m + 1/2) 2^-23 with m the
+// word's top 23 bits, assembled from the bits (1 + m 2^-23, then 1 - 2^-24 subtracted: exact by
+// Sterbenz's lemma), with no integer-to-float conversion instruction.
+__device__ __forceinline__ float uniform23(uint32_t w) {
+  return __fsub_rn(__uint_as_float(0x3F800000u | (w >> 9)), 0x1.fffffep-1f);
+}
+
+// A standard normal pair of the FP32 bulk form by Box-Muller from two uniforms: radius
+// sqrt(-2 ln u1) (ln by CUDA's logf: -2 ln u1 >= 2^-23 > 0 for every u1 uniform23 gives), angle
+// 2 pi u2 taken as pi (2 u2 - 1) + pi, so that the special-function unit's sine and cosine see an
+// argument in [-pi, pi) (absolute error ~2^-21); the square root from the reciprocal square
+// root. The draws of the FP32 form are held to statistics, not to bit-parity with the oracle.
+__device__ __forceinline__ void box_muller32(uint32_t wa, uint32_t wb, float& z_cos, float& z_sin) {
+  const float t = __fmul_rn(-2.0f, logf(uniform23(wa)));
+  const float rad = __fmul_rn(t, rsqrtf(t));
+  float sn, cs;
+  __sincosf(__fmul_rn(3.14159265358979323846f, __fsub_rn(__fmul_rn(2.0f, uniform23(wb)), 1.0f)), &sn, &cs);
+  z_cos = -__fmul_rn(rad, cs);  // cos(a + pi) = -cos a, sin(a + pi) = -sin a
+  z_sin = -__fmul_rn(rad, sn);
+}
+
+// ------------------------------------ FP32 bulk form: the d = 1 RAM factor ---
+// The FP32 form keeps S in binary64 and steps members in binary32. The conversions between the
+// two run on the integer pipe (GB300's FP64 pipe is the scarce unit), and the factor update
+// S <- S sqrt(1 + c), c = eta (alpha - alpha_*) (Sec. 2.2, d = 1) costs one binary64 FMA:
+// S + S d with the increment d = sqrt(1 + c) - 1 = c / (1 + sqrt(1 + c)) formed in binary32
+// (no cancellation; alpha is a binary32 value, so c carries binary32 error anyway). The update
+// is then exact to ~1e-7 |c| relative, and S itself never loses binary64 precision.
+
+// binary64 -> binary32 rounded toward zero, on the integer pipe (the proposal scale of a member;
+// any positive scale gives a valid proposal). Values outside binary32's normal range take the
+// conversion instruction.
+__device__ __forceinline__ float f32_rz(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int e = static_cast<int>((b >> 52) & 0x7ff) - 1023 + 127;
+  if (e >= 1 && e <= 254)
+    return __uint_as_float((static_cast<unsigned int>(b >> 32) & 0x80000000u) | (static_cast<unsigned int>(e) << 23) |
+                           static_cast<unsigned int>((b >> 29) & 0x7FFFFFull));
+  return __double2float_rz(x);
+}
+
+// binary32 -> binary64, exact, on the integer pipe (zeros and normal values; the rest take the
+// conversion instruction)
+__device__ __forceinline__ double f64_of(float v) {
+  const unsigned int u = __float_as_uint(v);
+  const unsigned int e = (u >> 23) & 0xffu;
+  const unsigned long long sign = static_cast<unsigned long long>(u >> 31) << 63;
+  if (e == 0u && (u & 0x7FFFFFu) == 0u) return __longlong_as_double(static_cast<long long>(sign));
+  if (e == 0u || e == 0xffu) return static_cast<double>(v);
+  return __longlong_as_double(static_cast<long long>(sign | (static_cast<unsigned long long>(e + 896u) << 52) |
+                                                     (static_cast<unsigned long long>(u & 0x7FFFFFu) << 29)));
+}
+
+// One RAM step of a d = 1 factor in the FP32 form: S + S d, d = c / (1 + sqrt(1 + c)) (1 + c >= 0.6:
+// the square root from the reciprocal square root, the quotient by the fast reciprocal; d keeps
+// a few binary32 ulp, far below the step's own randomness).
+__device__ __forceinline__ double ram1_f32(double S, float alpha, float eta, float astar) {
+  const float c = __fmul_rn(eta, __fsub_rn(alpha, astar));
+  const float x = __fadd_rn(1.0f, c);
+  const float d = __fdividef(c, __fadd_rn(1.0f, __fmul_rn(x, rsqrtf(x))));
+  return __fma_rn(S, f64_of(d), S);
 }
 
 // ------------------------------------------- running moments of the latents -

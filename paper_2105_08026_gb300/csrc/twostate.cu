@@ -37,7 +37,7 @@ __global__ void twostate_kernel(long long n, long long T, double lp0, double lp1
         const float delta = x ? static_cast<float>(lp0 - lp1) : static_cast<float>(lp1 - lp0);
         const bool odd = (kk & 1u) != 0u;
         const uint4 w = philox4x32_10(make_uint4(0u, 2u, static_cast<uint32_t>(i), odd ? kk : kk - 1u), key0, key1);
-        const float u = (static_cast<float>((odd ? w.z : w.w) >> 8) + 0.5f) * 0x1p-24f;
+        const float u = uniform23(odd ? w.z : w.w);
         float alpha;
         acc = mh_accept32(delta, u, alpha);
       } else {

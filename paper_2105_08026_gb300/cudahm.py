@@ -297,7 +297,9 @@ def cudahm_ess(x) -> np.ndarray:
 def cudahm_lf_etabar_noalloc(theta_dev_ptr: int, consts, etabar_dev_ptr: int, stream_ptr: int = 0):
     """Selection integral into caller-owned device memory, with no device allocation
     (theta_dev_ptr: 3 doubles, etabar_dev_ptr: 1 double, both on the current device)."""
-    c = _f64(consts)
+    c = _f64(consts).reshape(-1)
+    if c.size != 6:
+        raise ValueError(f"consts must hold 6 values (sigma_F, F_th, r_max, n_L, n_r, ln(upper/L*)), got {c.size}")
     _check(lib().cudahm_lf_etabar_noalloc(ctypes.c_void_p(theta_dev_ptr), _dptr(c), ctypes.c_void_p(etabar_dev_ptr),
                                           ctypes.c_void_p(stream_ptr) if stream_ptr else None))
 

@@ -36,6 +36,35 @@ extern "C" int probe_fp64_math(int which, const double* x_host, double* y_host, 
   return e == cudaSuccess ? 0 : -2;
 }
 
+// The FP32 form's binary32 exponentials next to CUDA's expf / expm1f on the same arguments.
+#include "fp32_math.cuh"
+
+namespace {
+__global__ void probe32_kernel(int which, const float* x, float* y, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  switch (which) {
+    case 0: y[i] = chm::exp32(x[i]); break;
+    case 1: y[i] = chm::expm1_32(x[i]); break;
+    case 2: y[i] = expf(x[i]); break;
+    default: y[i] = expm1f(x[i]); break;
+  }
+}
+}  // namespace
+
+extern "C" int probe_fp32_math(int which, const float* x_host, float* y_host, int n) {
+  float *x = nullptr, *y = nullptr;
+  if (cudaMalloc(&x, sizeof(float) * n) != cudaSuccess) return -1;
+  if (cudaMalloc(&y, sizeof(float) * n) != cudaSuccess) return -1;
+  cudaMemcpy(x, x_host, sizeof(float) * n, cudaMemcpyHostToDevice);
+  probe32_kernel<<<(n + 255) / 256, 256>>>(which, x, y, n);
+  cudaMemcpy(y_host, y, sizeof(float) * n, cudaMemcpyDeviceToHost);
+  const cudaError_t e = cudaGetLastError();
+  cudaFree(x);
+  cudaFree(y);
+  return e == cudaSuccess ? 0 : -2;
+}
+
 // The sampler's Philox4x32-10 block next to cuRAND's Philox4_32_10 generator (its device API),
 // for the same key and 128-bit counter: curand_init(seed = key1:key0, subsequence = c3:c2,
 // offset = 4 (c1:c0)) puts the generator at counter (c0, c1, c2, c3) (c1 < 2^30, so that the

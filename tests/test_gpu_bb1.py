@@ -37,6 +37,15 @@ def test_bb1_full_size_lockstep_n100000():
     _check_lockstep(*out, d_atol=1e-9)
 
 
+def test_bb1_lockstep_1000_sweeps_full_rule():
+    """The paper's model with the full 1024 x 1024 rule (sigma(F) in every pair), 1000 sweeps in
+    lockstep (N = 5000: the oracle's cost is the rule's 2^20 pairs per sweep)."""
+    data = synth.bb1_data(5000, seed=1006)
+    theta0, scale, consts = synth.bb1_settings(data)
+    out = _lockstep(oracle.BB1, data.fhat, data.r, consts, theta0, scale, 8, synth.bb1_chi_init(data), 1000)
+    _check_lockstep(*out, d_atol=1e-9)
+
+
 def test_bb1_etabar_and_detection_match_oracle():
     data = synth.bb1_data(500, seed=22)
     theta0, scale, consts = synth.bb1_settings(data)

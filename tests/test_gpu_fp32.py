@@ -3,7 +3,7 @@
 Bar (binary32 member terms, binary64 accumulation, accept and RAM factors):
 - per-member log density within 1e-5 relative (|a - b| <= 1e-5 max(1, |b|)) of the FP64
   oracle evaluated at the same latents (the binary32 values, exactly as doubles) and theta;
-- |sum of per-member log densities - oracle's sum| <= 1e-3 at N = 6e5;
+- |sum of per-member log densities - oracle's sum| <= 1e-3 at N = 6e5 (NN1) and N = 1e6 (LF);
 - theta posterior means within 4 Monte Carlo standard errors of the exact posterior (NN1,
   closed form) or of the FP64 chain (LF), variances within 4 of their standard errors.
 """
@@ -56,6 +56,27 @@ def test_fp32_nn1_logdens_and_sum_n600000():
     err = _rel_ok(lp32, lp64, 1e-5)
     assert err <= 1e-5, err
     assert abs(math.fsum(lp32) - math.fsum(lp64)) <= 1e-3
+
+
+def test_fp32_lf_logdens_and_sum_n1000000():
+    """The luminosity model at N = 1e6 (its log targets span the widest range of the three
+    models): per-member error within 1e-5 and the sum within 1e-3 of the oracle's."""
+    data = synth.lf_data(1_000_000, seed=1008)
+    theta0, scale, consts = synth.lf_settings(data)
+    s = cudahm.Sampler(cudahm.LF, data.fhat.size, theta_init=theta0, theta_prop_scale=scale, model_consts=consts,
+                       precision=cudahm.FP32, seed=10)
+    s.set_data(data.fhat, data.r)
+    s.run(0, 30)
+    chi, _ = s.chi()
+    assert np.array_equal(chi, chi.astype(np.float32).astype(np.float64))
+    th, _ = s.theta()
+    lp32 = s.logdens(th)
+    lp64 = oracle.member_logdens(oracle.LF, data.fhat, data.r, consts, chi, th)
+    err = _rel_ok(lp32, lp64, 1e-5)
+    assert err <= 1e-5, err
+    dsum = math.fsum(lp32) - math.fsum(lp64)
+    print("FP32 LF N=1e6: max rel", err, "sum error", dsum)
+    assert abs(dsum) <= 1e-3, dsum
 
 
 def _check_moments(x, E, V):

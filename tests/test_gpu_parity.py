@@ -2,7 +2,10 @@
 
 FP64 acceptance bar:
 - member and theta accept decisions identical at every (sweep, member), except where
-  |Delta - ln u| < 1e-9 (a near tie, which rounding may flip);
+  |Delta - ln u| < 1e-9 (a near tie, which rounding may flip); after a member's near tie that
+  member is masked and the others are still compared, a theta near tie ends the comparison at
+  that sweep (both reported, never skipped);
+- D and log alpha_theta within 1e-10 sqrt(N/1e4) absolute (below the near-tie band);
 - per-member log densities within 1e-12 relative (|a - b| <= 1e-12 max(1, |a|));
 - the selection integral etabar(theta) within 1e-13 relative of the oracle's rule;
 - theta rows, latents and RAM factors within 1e-12 relative.
@@ -15,93 +18,9 @@ import pytest
 import oracle
 from paper_2105_08026_gb300 import cudahm, synth
 
+from lockstep import DELTA_REL, NEAR_TIE, REL, _check_lockstep, _close, _lockstep, d_tolerance  # noqa: F401
+
 pytestmark = pytest.mark.gpu
-
-REL = 1e-12       # latents, RAM factors, theta rows, per-member log densities
-DELTA_REL = 1e-11  # member Delta = lp(Y) - lp(X): ~10 ulp of log targets of size ~1e3
-NEAR_TIE = 1e-9
-
-
-def _close(a, b, rel=REL):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    both_inf = np.isinf(a) & np.isinf(b) & (np.sign(a) == np.sign(b))
-    err = np.abs(a - b)
-    tol = rel * np.maximum(1.0, np.maximum(np.abs(a), np.abs(b)))
-    return np.all(both_inf | (err <= tol)), float(np.max(np.where(both_inf, 0.0, err / tol), initial=0.0))
-
-
-def _lockstep(model, y, aux, consts, theta0, scale, seed, chi0, sweeps, adapt_theta=True, block_threads=0):
-    n = np.asarray(y).shape[0]
-    s = cudahm.Sampler(model, n, theta_init=theta0, theta_prop_scale=scale, model_consts=consts, seed=seed,
-                       trace_sweeps=sweeps, adapt_theta=adapt_theta, block_threads=block_threads)
-    s.set_data(y, aux)
-    s.set_chi(chi0)
-    rows = s.run(0, sweeps)
-    tr = s.trace(sweeps)
-    ch = oracle.Chain(model, y, aux, consts, theta0, scale, seed, chi0, adapt_theta=adapt_theta)
-    orows, otr = ch.run(0, sweeps, trace_sweeps=sweeps)
-    return s, ch, rows, orows, tr, otr
-
-
-def _check_lockstep(s, ch, rows, orows, tr, otr, d_atol=None):
-    # member decisions
-    diff = tr["acc"] != otr["acc"]
-    if diff.any():
-        k, i = np.argwhere(diff)[0]
-        gap = abs(otr["delta"][k, i] - math.log(otr["u"][k, i]))
-        assert gap < NEAR_TIE, f"member decision differs at sweep {k}, member {i}: |Delta - ln u| = {gap}"
-        pytest.skip(f"near tie at sweep {k}, member {i}; chains legitimately diverge afterwards")
-    assert np.array_equal(tr["u"], otr["u"]), "accept uniforms differ (RNG layout)"
-    ok, worst = _close(tr["delta"], otr["delta"], rel=DELTA_REL)
-    assert ok, f"member Delta differs: worst {worst:.3g} x tolerance"
-    # theta decisions
-    tdiff = tr["tacc"] != otr["tacc"]
-    if tdiff.any():
-        k = int(np.argwhere(tdiff)[0][0])
-        gap = abs(otr["logalpha"][k] - math.log(otr["utheta"][k]))
-        assert gap < NEAR_TIE, f"theta decision differs at sweep {k}: |log alpha - ln u| = {gap}"
-        pytest.skip(f"theta near tie at sweep {k}")
-    assert np.array_equal(tr["utheta"], otr["utheta"])
-    ok, worst = _close(tr["theta_prop"], otr["theta_prop"])
-    assert ok, f"theta proposals differ: {worst:.3g} x tol"
-    # D and log alpha are sums over members of terms that each carry a few ulp of formula
-    # rounding: a bound linear in N (1e-10 at N <= 1e4) keeps them 10x inside the near-tie band.
-    # Models with a steeper member likelihood pass their own bound (see the caller).
-    atol = (1e-10 if d_atol is None else d_atol) * max(1.0, s.n / 1e4)
-    for key in ("D", "logalpha"):
-        a, b = tr[key], otr[key]
-        fin = np.isfinite(a) & np.isfinite(b)
-        assert np.array_equal(np.isfinite(a), np.isfinite(b)), key
-        assert np.array_equal(a[~fin], b[~fin]), key
-        err = np.max(np.abs(a[fin] - b[fin]), initial=0.0)
-        assert err <= atol, f"{key} differs by {err:.3g} > {atol:.3g}"
-    # the selection integral at each traced proposal, against the oracle's rule at the same proposal
-    # (the chains' theta' agree to the 1e-12 above; the integral is compared as arithmetic)
-    eb = tr["etabar"]
-    if ch.model in (oracle.LF, oracle.BB1):
-        rule = oracle.lf_etabar if ch.model == oracle.LF else oracle.bb1_etabar
-        ks = np.nonzero(eb > 0)[0]
-        assert ks.size > 0
-        ref = np.array([rule(tr["theta_prop"][k], ch.consts) for k in ks])
-        assert np.all(np.abs(eb[ks] - ref) <= 1e-13 * ref), "selection integral differs"
-    ok, worst = _close(rows, orows)
-    assert ok, f"theta rows differ: {worst:.3g} x tol"
-    chi, S = s.chi()
-    ok, worst = _close(chi, ch.chi)
-    assert ok, f"latents differ: {worst:.3g} x tol"
-    ok, worst = _close(S, ch.S)
-    assert ok, f"RAM factors differ: {worst:.3g} x tol"
-    th, Sth = s.theta()
-    ok, _ = _close(th, ch.theta)
-    assert ok
-    ok, _ = _close(Sth.reshape(-1), ch.S_theta)
-    assert ok
-    # per-member log targets of the device against the oracle's formula at the same (device) state
-    lp = s.logdens(th)
-    olp = oracle.member_logdens(ch.model, ch.y, ch.aux, ch.consts, chi, th)
-    ok, worst = _close(lp, olp)
-    assert ok, f"per-member log densities differ: {worst:.3g} x tol"
 
 
 def test_nn1_lockstep_normal_normal_n1000():
@@ -134,6 +53,26 @@ def test_lf_lockstep_small_rule():
     theta0, scale, consts = synth.lf_settings(data, nL=256, nr=256)
     chi0 = synth.lf_chi_init(data, theta0)
     out = _lockstep(oracle.LF, data.fhat, data.r, consts, theta0, scale, 2, chi0, 120)
+    _check_lockstep(*out)
+
+
+def test_lf_lockstep_1000_sweeps_full_rule_n10000():
+    """Luminosity model, N = 1e4, the full 1024 x 1024 rule, 1000 sweeps in lockstep: the RAM
+    adaptation's later steps of every member and of theta, every decision compared."""
+    data = synth.lf_data(10_000, seed=1005)
+    theta0, scale, consts = synth.lf_settings(data)
+    chi0 = synth.lf_chi_init(data, theta0)
+    out = _lockstep(oracle.LF, data.fhat, data.r, consts, theta0, scale, 2, chi0, 1000)
+    _check_lockstep(*out)
+
+
+def test_lf_lockstep_across_launch_boundary():
+    """Luminosity model, 4200 sweeps: the chain continues across the boundary of a persistent
+    launch (4096 sweeps), in lockstep (N = 2000, 128 x 128 rule)."""
+    data = synth.lf_data(2000, seed=1007)
+    theta0, scale, consts = synth.lf_settings(data, nL=128, nr=128)
+    chi0 = synth.lf_chi_init(data, theta0)
+    out = _lockstep(oracle.LF, data.fhat, data.r, consts, theta0, scale, 6, chi0, 4200)
     _check_lockstep(*out)
 
 
@@ -279,7 +218,68 @@ def test_restore_rejects_another_layout_version_or_config():
     with pytest.raises(cudahm.CudahmError) as ei:  # another seed: another chain
         c.restore(bytes(blob))
     assert ei.value.code == cudahm.EINVAL
-    blob[8:16] = (1).to_bytes(8, "little", signed=True)  # layout version 1
+    blob[8:16] = (2).to_bytes(8, "little", signed=True)  # layout version 2
     with pytest.raises(cudahm.CudahmError) as ei:
         b.restore(bytes(blob))
     assert ei.value.code == cudahm.EINVAL
+
+
+# checkpoint layout (version 3): 10 header words, then ChainState: theta[9], S_theta[81], etabar,
+# sweeps, member_acc, theta_acc, rows (8 bytes each), mcur, mom_sel (4 bytes each), mom_n, ...
+_HDR = 80
+_OFF_SWEEPS = _HDR + 8 * (9 + 81 + 1)
+_OFF_MCUR = _HDR + 8 * (9 + 81 + 5)
+_OFF_MOMSEL = _OFF_MCUR + 4
+
+
+def test_restore_rejects_a_corrupted_chain_state():
+    """Fields that index device buffers or size launches are checked before anything is copied."""
+    data = synth.nn1_data(500, seed=18)
+    theta0, scale, consts = synth.nn1_settings(data)
+    mk = lambda: cudahm.Sampler(cudahm.NN1, 500, theta_init=theta0, theta_prop_scale=scale,
+                                model_consts=consts, seed=3, keep_chi_moments=True)
+    a, b = mk(), mk()
+    for x in (a, b):
+        x.set_data(data.y, data.sigma)
+    a.run(0, 20)
+    good = bytes(a.checkpoint())
+    assert int.from_bytes(good[_OFF_SWEEPS:_OFF_SWEEPS + 8], "little") == 20  # the layout assumed here
+    chi_before = b.chi()[0]
+    for off, width, val in ((_OFF_MOMSEL, 4, 2), (_OFF_MOMSEL, 4, -1), (_OFF_MCUR, 4, 7),
+                            (_OFF_SWEEPS, 8, -5), (_OFF_SWEEPS, 8, 1 << 33)):
+        blob = bytearray(good)
+        blob[off:off + width] = val.to_bytes(width, "little", signed=True)
+        with pytest.raises(cudahm.CudahmError) as ei:
+            b.restore(bytes(blob))
+        assert ei.value.code == cudahm.EINVAL, (off, val)
+    blob = bytearray(good)
+    blob[_HDR:_HDR + 8] = np.array([np.nan]).tobytes()  # theta[0]
+    with pytest.raises(cudahm.CudahmError):
+        b.restore(bytes(blob))
+    assert np.array_equal(b.chi()[0], chi_before)  # nothing was copied
+    b.restore(good)
+    assert np.array_equal(b.chi()[0], a.chi()[0])
+
+
+def test_restore_rejects_other_model_constants_or_form():
+    """A checkpoint continues only the chain it was taken from: another selection rule, another
+    precision or another moments setting is rejected."""
+    data = synth.lf_data(800, seed=19)
+    theta0, scale, consts = synth.lf_settings(data, nL=64, nr=64)
+    mk = lambda c, **kw: cudahm.Sampler(cudahm.LF, 800, theta_init=theta0, theta_prop_scale=scale,
+                                        model_consts=c, seed=3, **kw)
+    a = mk(consts)
+    a.set_data(data.fhat, data.r)
+    a.run(0, 10)
+    blob = a.checkpoint()
+    other = consts.copy()
+    other[3] = 128  # another outer rule size
+    for b in (mk(other), mk(consts, precision=cudahm.FP32), mk(consts, keep_chi_moments=True)):
+        b.set_data(data.fhat, data.r)
+        with pytest.raises(cudahm.CudahmError) as ei:
+            b.restore(blob)
+        assert ei.value.code == cudahm.EINVAL
+    c = mk(consts)
+    c.set_data(data.fhat, data.r)
+    c.restore(blob)
+    assert np.array_equal(c.run(0, 15), a.run(0, 15))

@@ -39,14 +39,24 @@ def _alone(r):
 
 
 def test_served_results_equal_running_alone():
+    """Staggered arrivals: later requests are admitted while earlier ones are on the GPU (the
+    server reports several requests on the device at once), and every result is still the chain
+    the request gives alone."""
     reqs = _requests()
+    reqs[0]["iters"] = 4000  # a long first request that the later ones join
     sv = cudahm.Server(8 << 30, precision=cudahm.FP32, max_active=64, sweeps_per_step=37)
     tickets = []
-    for r in reqs:  # staggered arrivals: later requests join while earlier ones are on the GPU
+    peak = 0
+    for r in reqs:
         tickets.append(sv.submit(r["cfg"], r["y"], r["aux"], r["burn"], r["iters"], r["thin"]))
-        time.sleep(0.01)
-    for t in tickets:
-        sv.wait(t, 120_000)
+        t_end = time.perf_counter() + 0.01
+        while time.perf_counter() < t_end:
+            peak = max(peak, sv.stats()["active"])
+            time.sleep(0.0005)
+    while not all(sv.poll(t) for t in tickets):
+        peak = max(peak, sv.stats()["active"])
+        time.sleep(0.0005)
+    assert peak >= 2, f"requests never shared the device (peak active {peak})"
     for r, t in zip(reqs, tickets):
         rows, lat = sv.result(t)
         assert lat > 0

@@ -144,24 +144,33 @@ def _lf_member_logp(data, theta, q):
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("adapt", [False, True])
 @pytest.mark.parametrize("j,scale", [(0, 0.3), (1, 0.6), (2, 0.5)])
-def test_lf_single_component_posterior_tiny_n(j, scale):
+def test_lf_single_component_posterior_tiny_n(j, scale, adapt):
     """LF theta step at tiny N (20 detected objects, 64 x 64 rule): with the other two components
     fixed, the chain's marginal of theta_j matches brute-force quadrature of
     pi(theta) prod_i p_i(theta) / etabar(theta)^N (eq. epdf), p_i the 1-D integral of each
     member's likelihood times the population density in ln L, within 4 MCSE in mean and
     variance. This pins the theta step's prior, its truncations, the -N ln etabar term and the
-    exact sum over members together with the member steps."""
+    exact sum over members together with the member steps.
+
+    adapt: the theta step as the chain runs it by default, its RAM adaptation applied one sweep
+    late (reading R3). The other two components then get proposal scales of 1e-10 (RAM needs
+    every scale positive): the rank-one updates scale the factor along S U, which stays along
+    theta_j, so they move by less than 1e-5 over the run (measured: 3e-7), nothing against the
+    posterior widths (0.1 to 0.6). A wrong
+    adaptation (one that lets the proposal depend on the current state) biases the stationary
+    law and fails the comparison."""
     data = synth.lf_data(20, seed=515)
     theta0, _, consts = synth.lf_settings(data, nL=64, nr=64)
     q = 1.0 / (4 * math.pi * data.r**2)
-    prop = np.zeros(3)
+    prop = np.full(3, 1e-10) if adapt else np.zeros(3)
     prop[j] = scale
-    ch = oracle.Chain(oracle.LF, data.fhat, data.r, consts, theta0, prop, 41 + j, synth.lf_chi_init(data, theta0),
-                      adapt_theta=False)
+    ch = oracle.Chain(oracle.LF, data.fhat, data.r, consts, theta0, prop, 41 + j + (10 if adapt else 0),
+                      synth.lf_chi_init(data, theta0), adapt_theta=adapt)
     rows, _ = ch.run(2000, 24000)
     x = rows[:, j]
-    assert np.all(np.delete(rows, j, axis=1) == np.delete(theta0, j))
+    assert np.allclose(np.delete(rows, j, axis=1), np.delete(theta0, j), rtol=0, atol=1e-5)
     sd0 = max(x.std(), 1e-3)
     lo, hi = x.mean() - 12 * sd0, x.mean() + 12 * sd0
     if j == 0:  # -2 < beta < 0
@@ -183,5 +192,8 @@ def test_lf_single_component_posterior_tiny_n(j, scale):
     V = np.trapezoid(p * (grid - E) ** 2, grid)
     se = stats.mcse(x)
     assert abs(x.mean() - E) < 4 * se, (x.mean(), E, se)
-    ess = stats.ess_geyer(x)
-    assert abs(x.var() - V) < 4 * V * math.sqrt(2.0 / ess), (x.var(), V, ess)
+    # the variance's Monte Carlo error from the squared deviations themselves (their batch means
+    # carry the autocorrelation and the posterior's heavy upper tail in ln L*)
+    se_v = stats.mcse((x - x.mean()) ** 2)
+    assert abs(x.var() - V) < 4 * se_v, (x.var(), V, se_v)
+

@@ -50,3 +50,33 @@ def test_noalloc_rejects_rule_beyond_fixed_limit():
         cudahm.cudahm_lf_etabar_noalloc(th.data_ptr(), consts, out.data_ptr(), 0)
     assert ei.value.code == cudahm.EINVAL
     assert "1024" in str(ei.value)
+
+
+def test_noalloc_follows_a_change_of_rule():
+    """Consecutive calls with the same rule reuse the array's tables; a call with another rule
+    size or another sigma_F rebuilds them. Each value matches the handle built for its constants."""
+    torch = pytest.importorskip("torch")
+    data = synth.lf_data(2000, seed=22)
+    theta0, scale, consts_a = synth.lf_settings(data)
+    consts_b = consts_a.copy()
+    consts_b[0] *= 1.1   # sigma_F
+    consts_b[3] = 512    # n_L
+    consts_b[4] = 768    # n_r
+    expected = {}
+    for name, c in (("a", consts_a), ("b", consts_b)):
+        s = cudahm.Sampler(cudahm.LF, data.fhat.size, theta_init=theta0, theta_prop_scale=scale, model_consts=c)
+        s.set_data(data.fhat, data.r)
+        expected[name] = s.etabar(theta0)
+    torch.cuda.set_device(0)
+    th = torch.tensor(theta0, dtype=torch.float64, device="cuda")
+    seq = ["a", "a", "b", "b", "a"]
+    out = torch.zeros(len(seq), dtype=torch.float64, device="cuda")
+    for q, name in enumerate(seq):
+        cudahm.cudahm_lf_etabar_noalloc(th.data_ptr(), consts_a if name == "a" else consts_b,
+                                        out[q:q + 1].data_ptr(), 0)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for g, name in zip(got, seq):
+        e = expected[name]
+        assert abs(g - e) <= 1e-13 * abs(e), (name, g, e)
+    assert expected["a"] != expected["b"]
