@@ -169,9 +169,18 @@ class ClockSampler:
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 8:
-                self.rows.append(parts)
+                self.rows.append((time.perf_counter(), parts))
 
-    def stop(self):
+    def wait_first(self, limit_s=10.0):
+        """Returns once the sampler has produced a row: the nvidia-smi process has started, so its
+        start-up does not compete with the timed region's host work."""
+        t_end = time.perf_counter() + limit_s
+        while self.proc is not None and not self.rows and time.perf_counter() < t_end:
+            time.sleep(0.05)
+
+    def stop(self, t_lo=None, t_hi=None):
+        """Median SM clock and throttle reasons over the samples taken in [t_lo, t_hi] (the timed
+        region, widened by one sampling period on each side; all samples when none fall there)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         time.sleep(0.25)
@@ -180,12 +189,17 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        rows = self.rows
+        if t_lo is not None and t_hi is not None:
+            inside = [r for r in self.rows if t_lo - 0.25 <= r[0] <= t_hi + 0.25]
+            rows = inside or self.rows
+        rows = [r[1] for r in rows]
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[j] for r in self.rows for j in range(4) if r[4 + j].lower() == "active"})
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[4 + j].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(rows)}
 
 
 # -------------------------------------------------------------- CPU oracle ---
@@ -288,7 +302,7 @@ def run_batched(args, cudahm, stream, device):
             "populations": len(specs), "members": members, "lf_populations": sum(sp.kind == "lf" for sp in specs),
             "steps": K, "launch": {"block_threads": chosen.block_threads,
                                    "sweeps_per_launch": chosen.sweeps_per_launch,
-                                   "graph": bool(chosen.use_graph), "blocks": chosen.reserved},
+                                   "graph": bool(chosen.use_graph), "blocks": chosen.grid_blocks},
             "dtype": "f32 member terms, f64 sums/accept/RAM/selection integral (1024x1024 rule per LF population)"}
 
 
@@ -479,7 +493,7 @@ def run_nn3_ess(args, cudahm, stream, device):
                         "time_to_ess1000_s": 1e-3 * ms * 1000.0 / float(ess.min()),
                         "object_updates_per_s": R * n * K / (ms * 1e-3),
                         "launch": {"block_threads": tune.block_threads, "sweeps_per_launch": tune.sweeps_per_launch,
-                                   "graph": bool(tune.use_graph), "blocks": tune.reserved}})
+                                   "graph": bool(tune.use_graph), "blocks": tune.grid_blocks}})
     return {"workload": "normal-normal benchmark (paper Sec. 3), d=3, C_pop known, theta=mu",
             "metric": "post-burn-in seconds to ESS=1000 (min over mu components)", "runs": out}
 
@@ -715,6 +729,10 @@ def run_cuda(args):
     r_dev = torch.from_numpy(data.r).cuda()
     cudahm.cudahm_set_data_device(s.h, y_dev.data_ptr(), r_dev.data_ptr(), n)
     torch.cuda.synchronize()
+    # the clock sampler runs from before the warm-up, so that its start-up is over when timing starts
+    clocks = ClockSampler(local)
+    clocks.start()
+    clocks.wait_first()
     # warm-up: burn-in sweeps (untimed)
     if args.warmup > 0:
         s.run(args.warmup, 0)
@@ -724,11 +742,10 @@ def run_cuda(args):
     L = max(1, args.launch_sweeps)
     chunks = [min(L, K - j) for j in range(0, K, L)]
     R = len(chunks)
-    clocks = ClockSampler(local)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    t_timed0 = time.perf_counter()
     total_ms = 0.0
     kernel_ms = 0.0
     launches = 0
@@ -752,7 +769,7 @@ def run_cuda(args):
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(t_timed0, time.perf_counter())
     assert rows_total == K
     t_max_ms = max_over_ranks(total_ms)
     value = replica_value(ws, n * K, t_max_ms)

@@ -320,17 +320,22 @@ int cudahm_restore(cudahm_t h, const void* buf, size_t size);
 int cudahm_lf_etabar_noalloc(const double* theta_dev, const double* consts_host, double* etabar_dev,
                              void* cuda_stream);
 
-/* Launch shape of a batched run. Zero fields are chosen automatically: the block size by two
- * 16-sweep trial launches at the start of the run (128 and 256 threads; the faster device
- * time per sweep wins and is cached per (precision, number of populations, LF count, size
- * class) for the process), the sweeps per launch as clamp(total/4, 256, 4096). A
- * population's chain does not depend on the launch shape (all sums are exact), so the trial
- * launches are ordinary sweeps of the run. */
+/* Launch shape of a batched run. Zero fields are chosen automatically, and a tuned shape is
+ * cached per (precision, number of populations, LF count, size class) for the process:
+ *  - block size and grid: trial launches of 16 sweeps each at the start of the run (they are
+ *    ordinary sweeps of it) over 128 and 256 threads x the largest grid the occupancy allows and
+ *    half of it; the fastest device time per sweep wins;
+ *  - then two launches of 32 sweeps whose per-population device times (like the trials')
+ *    rebalance each population's share of the blocks (the first share comes from a cost model);
+ *  - then launches of sweeps_per_launch sweeps: enough that the measured host cost of a launch
+ *    (synchronisation, graph launch, the error words) is about 1% of its device time, 64..4096.
+ * A population's chain does not depend on the launch shape (all sums are exact). */
 typedef struct {
   int32_t block_threads;      /* 128 or 256; 0 = tune */
-  int32_t sweeps_per_launch;  /* sweeps between launches (each launch ends with a grid-wide sync); 0 = tune */
+  int32_t sweeps_per_launch;  /* sweeps of each long launch (each launch ends with a grid-wide sync); 0 = tune */
   int32_t use_graph;          /* 1: replay the launch sequence from a captured CUDA graph */
-  int32_t reserved;           /* out: number of blocks of the launch */
+  int32_t grid_blocks;        /* blocks of the launch (at most what the occupancy allows); 0 = tune;
+                                 out: the blocks used */
 } cudahm_tune;
 
 /* Run n_burn + n_iter sweeps of k populations (handles created and loaded as usual, on one

@@ -132,7 +132,8 @@ __device__ __forceinline__ void member_f64(const SweepArgs& a, unsigned int i, u
 template <class M>
 __device__ __forceinline__ void member1_f32(const SweepArgs& a, unsigned int i, float chi, double S, const float* d,
                                             uint32_t k, float eta_f, float astar_f, const ThetaCf& tf,
-                                            const ThetaCf& tpf, bool prior_ok, Xacc& xd, XFlags& fd,
+                                            const ThetaCf& tpf, const ThetaDf& tdf, bool prior_ok, Xacc& xd,
+                                            XFlags& fd,
                                             unsigned int& neg_big, unsigned int& pos_big, unsigned int& nan_cnt,
                                             unsigned int& acc_cnt, long long tro, bool keep, const MomStep& ms) {
   const float ll = M::loglike32(chi, d);
@@ -145,20 +146,19 @@ __device__ __forceinline__ void member1_f32(const SweepArgs& a, unsigned int i, 
   box_muller32(w.x, w.y, zc, zs);
   const float z = odd ? zc : zs;
   const float Y = fmaf(f32_rz(S), z, chi);
-  float delta, llY = 0.0f;
-  F2 lfY{0.0f, 0.0f};
-  const F2 lfX = M::logf32p(chi, tf);
+  float delta, llY = 0.0f, lfY = 0.0f, cY = 0.0f, cX;
+  const float lfX = M::logf32_e(chi, tf, cX);
   if (!M::support32(Y, tf)) {
     delta = -INFINITY;
   } else {
     llY = M::loglike32(Y, d);
-    lfY = M::logf32p(Y, tf);
-    delta = (llY + (lfY.hi + lfY.lo)) - (ll + (lfX.hi + lfX.lo));
+    lfY = M::logf32_e(Y, tf, cY);
+    delta = (llY + lfY) - (ll + lfX);
   }
   float alpha;
   const bool acc = mh_accept32(delta, u, alpha);
   if (delta != delta) nan_cnt++;
-  const F2 lf_cur = acc ? lfY : lfX;
+  const float carry = acc ? cY : cX;
   if (acc) {
     chi = Y;
     acc_cnt++;
@@ -173,11 +173,7 @@ __device__ __forceinline__ void member1_f32(const SweepArgs& a, unsigned int i, 
     a.tr_acc[tro + i] = acc ? 1 : 0;
   }
   if (prior_ok) {
-    float dn = -INFINITY;
-    if (M::support32(chi, tpf)) {  // (hi' - hi) + (lo' - lo): the small parts survive the difference
-      const F2 lfp = M::logf32p(chi, tpf);
-      dn = __fadd_rn(__fsub_rn(lfp.hi, lf_cur.hi), __fsub_rn(lfp.lo, lf_cur.lo));
-    }
+    const float dn = M::support32(chi, tpf) ? M::dtheta32(chi, carry, tf, tpf, tdf) : -INFINITY;
     if (dn != dn) fd.nan++;
     else if (fabsf(dn) >= 0x1p94f) {
       if (dn < 0.0f) neg_big++;
@@ -219,7 +215,8 @@ __device__ __forceinline__ void tile_issue(const SweepArgs& a, const TileRing& r
 template <class M>
 __device__ __forceinline__ bool members1_f32_tiled(const SweepArgs& a, TileRing& r, unsigned int nb0,
                                                    unsigned int nb1, uint32_t k, float eta_f, float astar_f,
-                                                   const ThetaCf& tf, const ThetaCf& tpf, bool prior_ok, Xacc& xd,
+                                                   const ThetaCf& tf, const ThetaCf& tpf, const ThetaDf& tdf,
+                                                   bool prior_ok, Xacc& xd,
                                                    XFlags& fd, unsigned int& neg_big, unsigned int& pos_big,
                                                    unsigned int& nan_cnt, unsigned int& acc_cnt, long long tro,
                                                    bool keep, const MomStep& ms) {
@@ -253,8 +250,8 @@ __device__ __forceinline__ bool members1_f32_tiled(const SweepArgs& a, TileRing&
       float d[K32];
 #pragma unroll
       for (int c = 0; c < K32; ++c) d[c] = s_d[c * r.T + m];
-      member1_f32<M>(a, i, s_chi[m], s_S[m], d, k, eta_f, astar_f, tf, tpf, prior_ok, xd, fd, neg_big, pos_big,
-                     nan_cnt, acc_cnt, tro, keep, ms);
+      member1_f32<M>(a, i, s_chi[m], s_S[m], d, k, eta_f, astar_f, tf, tpf, tdf, prior_ok, xd, fd, neg_big,
+                     pos_big, nan_cnt, acc_cnt, tro, keep, ms);
     }
     fence_proxy_async_global();  // this thread's writes before any later bulk copy reads them
     __syncthreads();             // the stage is free for the tile after next
@@ -452,6 +449,7 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
   using TCf = typename M::TCf;
   __shared__ TC s_tc, s_tcp;
   __shared__ TCf s_tcf, s_tcpf;
+  __shared__ ThetaDf s_tdf;  // FP32 form, d = 1: constants of this sweep's step theta -> theta'
   __shared__ double s_etabar, s_logeb, s_lpri, s_lpri_new;
   __shared__ double s_pendU[kMaxP], s_pend_alpha, s_pend_eta;
   __shared__ int s_stop;
@@ -526,6 +524,7 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
       s_lpri_new = lp;
       s_tcp = tcp;
       s_tcpf = M::consts32(tcp);
+      if constexpr (F32 && M::kD == 1) s_tdf = M::dconsts32(s_tc, tcp);
     }
     __syncthreads();
     const bool prior_ok = (s_lpri_new != -INFINITY);
@@ -552,8 +551,9 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
       }
     } else if constexpr (F32) {
       const TCf tf = s_tcf, tpf = s_tcpf;
-      if (!members1_f32_tiled<M>(a, ring, nb0, nb1, k, __double2float_rn(eta), astar_f, tf, tpf, prior_ok, xd, fd,
-                                 neg_big, pos_big, member_nan, member_acc, tro, keep, ms))
+      const ThetaDf tdf = s_tdf;
+      if (!members1_f32_tiled<M>(a, ring, nb0, nb1, k, __double2float_rn(eta), astar_f, tf, tpf, tdf, prior_ok, xd,
+                                 fd, neg_big, pos_big, member_nan, member_acc, tro, keep, ms))
         return;  // a stage wait timed out: the run's error word is set, the population stops
     } else {
       const TC tc = s_tc, tcp = s_tcp;
@@ -840,12 +840,12 @@ cudaError_t launch_chi_from32(long long n, const float* chi32, double* chi, cuda
   return cudaGetLastError();
 }
 
-// Dynamic shared memory of the batched kernel: the exp/log tables, and in the FP32 form (whose
-// one-dimensional populations stream member tiles) two stages of 2 x block members of
+// Dynamic shared memory of the batched kernel: the exp/log tables, and when the FP32 form has
+// one-dimensional populations (they stream member tiles) two stages of 2 x block members of
 // 4 + 8 + 4 kData32 bytes, plus slack to align them to 128 bytes.
-size_t batch_smem_bytes(bool f32, bool, int block) {
+size_t batch_smem_bytes(bool f32, bool any_d1, int block) {
   size_t b = sizeof(double) * kMathWords;
-  if (f32) {
+  if (f32 && any_d1) {
     static_assert(LF::kData32 == NN1::kData32, "one tile layout for the one-dimensional models");
     const size_t per = 12u + 4u * static_cast<size_t>(LF::kData32);
     b = tile_offset_bytes() + 128u + 2u * (2u * static_cast<size_t>(block)) * per;

@@ -157,7 +157,7 @@ struct BatchProg {
 };
 
 // Batched launches (batch.cu).
-size_t batch_smem_bytes(bool f32, bool d1, int block);
+size_t batch_smem_bytes(bool f32, bool any_d1, int block);
 // d1: every population has a one-dimensional latent (the lighter kernel variant)
 cudaError_t batch_occupancy(bool f32, bool d1, int block, int smem_bytes, int* blocks_per_sm);
 cudaError_t launch_batch(bool f32, bool d1, const SweepArgs* pops, BatchProg* progs, const int* b0s, const int* nbs,

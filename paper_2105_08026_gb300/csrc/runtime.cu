@@ -1312,7 +1312,7 @@ struct TuneKey {
 };
 struct TuneEntry {
   TuneKey key;
-  int block, chunk;
+  int block, chunk, grid;
 };
 std::vector<TuneEntry> g_tune_cache;  // decisions of the autotuner for this process
 
@@ -1356,7 +1356,11 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
   }
   const bool f32 = h0->cfg.precision == CUDAHM_FP32;
   bool d1 = true;  // one-dimensional latents only: the lighter kernel variant
-  for (int q = 0; q < k; ++q) d1 = d1 && hs[q]->d == 1;
+  bool any1 = false;  // some one-dimensional population (FP32: member tiles in shared memory)
+  for (int q = 0; q < k; ++q) {
+    d1 = d1 && hs[q]->d == 1;
+    any1 = any1 || hs[q]->d == 1;
+  }
   CU(cudaSetDevice(h0->cfg.device));
   cudaStream_t st = h0->stream;
   for (int q = 0; q < k; ++q) CU(cudaStreamSynchronize(hs[q]->stream));
@@ -1382,7 +1386,7 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
     CU(cudaStreamSynchronize(h->stream));
   }
 
-  // launch shape: tuned or asked for
+  // launch shape: asked for, cached from an earlier tuned run of the same kind, or tuned here
   int nlf = 0;
   long long ntot = 0;
   for (int q = 0; q < k; ++q) {
@@ -1392,26 +1396,20 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
   TuneKey key{h0->cfg.precision, k, nlf, static_cast<long long>(std::log2(static_cast<double>(ntot) + 1.0))};
   int block = tune && tune->block_threads ? tune->block_threads : 0;
   int chunk = tune && tune->sweeps_per_launch ? tune->sweeps_per_launch : 0;
+  int grid_ask = tune && tune->grid_blocks ? tune->grid_blocks : 0;
   const bool use_graph = !tune || tune->use_graph != 0 || (tune->block_threads == 0 && tune->sweeps_per_launch == 0);
   if (block && block != 128 && block != 256) return fail(CUDAHM_EINVAL, "block_threads must be 128 or 256");
   if (chunk < 0 || chunk > kChunk) return fail(CUDAHM_EINVAL, "sweeps_per_launch must be in [1, %lld]", kChunk);
-  if (!block || !chunk) {
+  if (grid_ask < 0) return fail(CUDAHM_EINVAL, "grid_blocks must be >= 0");
+  bool cached = false;
+  if (!block || !chunk || !grid_ask) {
     for (const TuneEntry& e : g_tune_cache)
       if (e.key == key) {
         if (!block) block = e.block;
         if (!chunk) chunk = e.chunk;
+        if (!grid_ask) grid_ask = e.grid;
+        cached = true;
       }
-  }
-  // sweeps per launch: enough launches to rebalance a few times, long enough to amortise a launch
-  if (!chunk) chunk = static_cast<int>(std::min<long long>(kChunk, std::max<long long>(256, total / 4)));
-  // block size: measured on two short launches at the start of the run (they are part of it)
-  const int kTrialSweeps = 16;
-  std::vector<std::pair<int, int>> trials;
-  if (!block) {
-    trials.push_back({128, kTrialSweeps});
-    trials.push_back({256, kTrialSweeps});
-  } else {
-    trials.push_back({block, chunk});
   }
 
   const int R = 128;  // segment slots per block
@@ -1462,6 +1460,48 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
   CU(cudaMemcpyAsync(bb.progs, progs.data(), sizeof(BatchProg) * k, cudaMemcpyHostToDevice, st));
   CU(cudaMemsetAsync(bb.errs, 0, sizeof(int) * k, st));
 
+  // the largest grid the occupancy allows for a block size (128-thread blocks up to 8 per SM)
+  auto grid_max = [&](int blk, int* out) -> int {
+    int bps = 0;
+    CU(batch_occupancy(f32, d1, blk, static_cast<int>(batch_smem_bytes(f32, any1, blk)), &bps));
+    if (bps < 1) return fail(CUDAHM_EUNSUPPORTED, "batched kernel does not fit on this device");
+    *out = std::min(bps * sms, blk == 128 ? max_grid : max_grid / 2);
+    return CUDAHM_OK;
+  };
+
+  // The plan of launches. Autotuning (no shape asked for and none cached): trial launches of
+  // kTrialSweeps sweeps, part of the run, over block sizes {128, 256} x grids {the occupancy's
+  // maximum, half of it}; the fastest device time per sweep wins. Then (tuned or not) a few short
+  // launches whose per-population device times rebalance the blocks, then long launches. Sweeps
+  // per launch of the long launches (asked for, else cached, else tuned): enough that the measured
+  // host cost of a launch (synchronisation, graph launch, reading the error words) stays near 1%
+  // of its device time, at most 4096.
+  struct Shape {
+    int block, grid;
+  };
+  const int kTrialSweeps = 16, kBalanceSweeps = 32;
+  std::vector<Shape> trials;
+  const bool tuning = !cached && (!block || !grid_ask || !chunk);
+  if (tuning) {
+    for (int blk : {128, 256}) {
+      if (block && blk != block) continue;
+      int g = 0;
+      TRY(grid_max(blk, &g));
+      if (grid_ask) {
+        trials.push_back({blk, std::min(grid_ask, g)});
+      } else {
+        trials.push_back({blk, g});
+        if (g / 2 >= k) trials.push_back({blk, g / 2});
+      }
+    }
+  }
+  Shape best{block ? block : 128, 0};
+  if (!tuning) {
+    int g = 0;
+    TRY(grid_max(best.block, &g));
+    best.grid = grid_ask ? std::min(grid_ask, g) : g;
+  }
+
   cudaGraphExec_t gexec = nullptr;
   int g_block = 0, g_chunk = 0, g_grid = 0;
   std::vector<int> nb;
@@ -1479,23 +1519,16 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
     return CUDAHM_OK;
   };
   auto enqueue = [&](int blk, int ch, int grid_) -> cudaError_t {
-    const int smem = static_cast<int>(batch_smem_bytes(f32, d1, blk));
+    const int smem = static_cast<int>(batch_smem_bytes(f32, any1, blk));
     cudaError_t e = cudaMemsetAsync(bb.bars, 0, sizeof(unsigned int) * k, st);
     if (e == cudaSuccess) e = launch_batch_tables(bb.pops, bb.progs, k, ch, st);
     if (e == cudaSuccess) e = launch_batch(f32, d1, bb.pops, bb.progs, bb.b0s, bb.nbs, k, ch, R, grid_, blk, smem, st);
     return e;
   };
-  auto grid_for = [&](int blk, int* out) -> int {
-    int bps = 0;
-    CU(batch_occupancy(f32, d1, blk, static_cast<int>(batch_smem_bytes(f32, d1, blk)), &bps));
-    if (bps < 1) return fail(CUDAHM_EUNSUPPORTED, "batched kernel does not fit on this device");
-    *out = std::min(bps * sms, blk == 128 ? max_grid : max_grid / 2);
-    return CUDAHM_OK;
-  };
 
   long long done = 0;
-  double best_ms = 1e300;
-  int best_block = trials[0].first, best_chunk = chunk;
+  double best_ms = 1e300, host_ms_per_launch = 0.0;
+  int host_samples = 0;
   bool graph_ok = use_graph;
   float run_ms_total = 0.f;
   cudaEvent_t ea, eb;
@@ -1507,39 +1540,45 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
     if (gexec) cudaGraphExecDestroy(gexec);
   };
   int rc = CUDAHM_OK;
-  // trial launches (autotuning) on the run's first chunks, then the rest with the winner
   size_t ti = 0;
-  int rebalance_left = 2;
+  int balance_left = (k > 1) ? 2 : 0;
   while (done < total && rc == CUDAHM_OK) {
-    int blk, ch;
-    if (ti < trials.size() && trials.size() > 1) {
-      blk = trials[ti].first;
-      ch = trials[ti].second;
+    const bool trial = ti < trials.size();
+    const bool balance = !trial && balance_left > 0;
+    const Shape sh = trial ? trials[ti] : best;
+    const long long left = total - done;
+    long long ns;
+    if (trial) {
+      ns = std::min<long long>(kTrialSweeps, left);
+    } else if (balance) {
+      ns = std::min<long long>(kBalanceSweeps, left);
     } else {
-      blk = best_block;
-      ch = best_chunk;
+      if (!chunk) {  // the measured host cost of a launch against the device time of a sweep
+        const double per = best_ms < 1e299 ? best_ms : 1.0;
+        const double hms = host_samples ? host_ms_per_launch / host_samples : 0.05;
+        chunk = static_cast<int>(std::min<double>(kChunk, std::max(64.0, std::ceil(100.0 * hms / per))));
+      }
+      ns = std::min<long long>(chunk, left);
     }
-    int grid = 0;
-    if ((rc = grid_for(blk, &grid)) != CUDAHM_OK) break;
-    if (nb.empty() || grid != g_grid) {
-      nb = allocate_blocks(cost, cap, grid);
-      if ((rc = set_alloc(grid)) != CUDAHM_OK) break;
-      if (gexec && grid != g_grid) {
+    if (nb.empty() || sh.grid != g_grid) {
+      nb = allocate_blocks(cost, cap, sh.grid);
+      if ((rc = set_alloc(sh.grid)) != CUDAHM_OK) break;
+      if (gexec && sh.grid != g_grid) {
         cudaGraphExecDestroy(gexec);
         gexec = nullptr;
       }
     }
-    const long long ns = std::min<long long>(ch, total - done);
+    const auto h0t = std::chrono::steady_clock::now();
     cudaError_t e = cudaSuccess;
     CU(cudaEventRecord(ea, st));
-    if (graph_ok && (ti >= trials.size() || trials.size() == 1)) {
-      if (!gexec || g_block != blk || g_chunk != ch || g_grid != grid) {
+    if (graph_ok && !trial) {
+      if (!gexec || g_block != sh.block || g_chunk != ns || g_grid != sh.grid) {
         if (gexec) cudaGraphExecDestroy(gexec);
         gexec = nullptr;
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-          const cudaError_t e2 = enqueue(blk, ch, grid);
+          const cudaError_t e2 = enqueue(sh.block, static_cast<int>(ns), sh.grid);
           e = cudaStreamEndCapture(st, &graph);
           if (e2 != cudaSuccess) e = e2;
         }
@@ -1550,19 +1589,19 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
           if (gexec) cudaGraphExecDestroy(gexec);
           gexec = nullptr;
           graph_ok = false;
-          e = enqueue(blk, ch, grid);
+          e = enqueue(sh.block, static_cast<int>(ns), sh.grid);
         } else {
-          g_block = blk;
-          g_chunk = ch;
+          g_block = sh.block;
+          g_chunk = static_cast<int>(ns);
           e = cudaGraphLaunch(gexec, st);
         }
       } else {
         e = cudaGraphLaunch(gexec, st);
       }
     } else {
-      e = enqueue(blk, ch, grid);
+      e = enqueue(sh.block, static_cast<int>(ns), sh.grid);
     }
-    g_grid = grid;
+    g_grid = sh.grid;
     if (e != cudaSuccess) {
       rc = fail(CUDAHM_ECUDA, "batched launch failed: %s", cudaGetErrorString(e));
       break;
@@ -1579,30 +1618,43 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
     for (int q = 0; q < k && rc == CUDAHM_OK; ++q)
       if (errs[q] != 0) rc = fail(errs[q], "population %d failed with device error %d", q, errs[q]);
     if (rc != CUDAHM_OK) break;
-    if (ti < trials.size() && trials.size() > 1) {
+    const double wall_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0t).count();
+    host_ms_per_launch += std::max(0.0, wall_ms - ms);
+    ++host_samples;
+    if (trial) {
       const double per = ms / static_cast<double>(ns);
       if (per < best_ms) {
         best_ms = per;
-        best_block = blk;
+        best = sh;
       }
       ++ti;
-      if (ti == trials.size()) g_tune_cache.push_back(TuneEntry{key, best_block, best_chunk});
-      continue;
+    } else if (balance) {
+      --balance_left;
+      if (best_ms >= 1e299) best_ms = ms / static_cast<double>(ns);
     }
-    ti = trials.size();
-    // rebalance from the measured device time of each population (work ~ time x blocks)
-    if (rebalance_left > 0 && k > 1 && done < total) {
-      --rebalance_left;
+    // rebalance from the measured device time of each population (work ~ time x blocks), after
+    // every trial and balancing launch
+    if (k > 1 && done < total && (trial || balance)) {
       std::vector<BatchProg> pr(k);
       CU(cudaMemcpy(pr.data(), bb.progs, sizeof(BatchProg) * k, cudaMemcpyDeviceToHost));
       bool ok = true;
       for (int q = 0; q < k; ++q) ok = ok && pr[q].t_ns > 0;
       if (ok) {
         for (int q = 0; q < k; ++q) cost[q] = static_cast<double>(pr[q].t_ns) * nb[q];
-        nb = allocate_blocks(cost, cap, grid);
-        if ((rc = set_alloc(grid)) != CUDAHM_OK) break;
+        const int gnext = (ti < trials.size()) ? trials[ti].grid : best.grid;
+        nb = allocate_blocks(cost, cap, gnext);
+        if ((rc = set_alloc(gnext)) != CUDAHM_OK) break;
+        g_grid = gnext;
+        if (gexec) {
+          cudaGraphExecDestroy(gexec);
+          gexec = nullptr;
+        }
       }
     }
+  }
+  if (rc == CUDAHM_OK && tuning) {
+    g_tune_cache.push_back(TuneEntry{key, best.block, chunk ? chunk : static_cast<int>(kChunk), best.grid});
   }
   cleanup_events();
   if (rc != CUDAHM_OK) {
@@ -1622,10 +1674,10 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
     h->last_run_ms = run_ms_total;
   }
   if (chosen) {
-    chosen->block_threads = best_block;
-    chosen->sweeps_per_launch = best_chunk;
+    chosen->block_threads = best.block;
+    chosen->sweeps_per_launch = chunk ? chunk : static_cast<int>(std::min<long long>(total, kChunk));
     chosen->use_graph = graph_ok ? 1 : 0;
-    chosen->reserved = g_grid;
+    chosen->grid_blocks = best.grid;
   }
   return CUDAHM_OK;
 }
@@ -1638,9 +1690,12 @@ int batch_step(const std::vector<cudahm*>& hs, std::vector<BatchProg>& progs, in
                int max_grid, cudaStream_t st, bool f32) {
   const int k = static_cast<int>(hs.size());
   const int R = 128;
-  bool d1 = true;
-  for (const cudahm* h : hs) d1 = d1 && h->d == 1;
-  const int smem = static_cast<int>(batch_smem_bytes(f32, d1, block));
+  bool d1 = true, any1 = false;
+  for (const cudahm* h : hs) {
+    d1 = d1 && h->d == 1;
+    any1 = any1 || h->d == 1;
+  }
+  const int smem = static_cast<int>(batch_smem_bytes(f32, any1, block));
   int bps = 0;
   CU(batch_occupancy(f32, d1, block, smem, &bps));
   if (bps < 1) return fail(CUDAHM_EUNSUPPORTED, "batched kernel does not fit on this device");

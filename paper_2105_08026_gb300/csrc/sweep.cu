@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   __shared__ double s_theta[kMaxP], s_thp[kMaxP], s_Sth[kMaxP * kMaxP];
   __shared__ ThetaC s_tc, s_tcp;
   __shared__ ThetaCf s_tcf, s_tcpf;
+  __shared__ ThetaDf s_tdf;  // FP32 form: constants of this sweep's step theta -> theta'
   __shared__ double s_etabar, s_logeb, s_lpri, s_lpri_new;
   __shared__ int s_stop, s_fail, s_acc_prev;
   // the theta RAM update pending from the previous sweep (applied one sweep late): U (s_pend_idx
@@ -264,16 +265,19 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     double lp = -INFINITY;
     ThetaC tcp{};
     ThetaCf tcpf{};
+    ThetaDf tdf{};
     if (blockIdx.x == 0) {
       propose_theta<M>(a, 0, p, s_theta, s_Sth, s_thp, lp, tcp, s_math);
       tcpf = M::consts32(tcp);
-      publish_theta(a, 1u, s_thp, p, lp, tcp, tcpf);
-    } else if (!fetch_theta(a, 1u, s_thp, p, lp, tcp, tcpf)) {
+      if (F32) tdf = M::dconsts32(s_tc, tcp);
+      publish_theta(a, 1u, s_thp, p, lp, tcp, tcpf, tdf);
+    } else if (!fetch_theta(a, 1u, s_thp, p, lp, tcp, tcpf, tdf)) {
       s_fail = 1;
     }
     s_lpri_new = lp;
     s_tcp = tcp;
     s_tcpf = tcpf;
+    s_tdf = tdf;
   }
   __syncthreads();
   if (s_fail) return;
@@ -336,19 +340,22 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         double lp = -INFINITY;
         ThetaC tcp{};
         ThetaCf tcpf{};
+        ThetaDf tdf{};
         if (blockIdx.x == 0) {
           const ThetaPub& c = s_cand[s_acc_prev];
           for (int q = 0; q < p; ++q) s_thp[q] = c.thp[q];
           lp = c.lpri_new;
           tcp = c.tcp;
           tcpf = c.tcpf;
-          publish_theta(a, static_cast<unsigned int>(s + 1), s_thp, p, lp, tcp, tcpf);
-        } else if (!fetch_theta(a, static_cast<unsigned int>(s + 1), s_thp, p, lp, tcp, tcpf)) {
+          tdf = c.tdf;
+          publish_theta(a, static_cast<unsigned int>(s + 1), s_thp, p, lp, tcp, tcpf, tdf);
+        } else if (!fetch_theta(a, static_cast<unsigned int>(s + 1), s_thp, p, lp, tcp, tcpf, tdf)) {
           lp = -INFINITY;  // the run has failed; the next barrier returns
         }
         s_lpri_new = lp;
         s_tcp = tcp;
         s_tcpf = tcpf;
+        s_tdf = tdf;
       }
     }
 
@@ -362,15 +369,14 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         if (i < nb1) {
           const float Y = reinterpret_cast<const float*>(s_pY)[i - nb0];
           const float u = reinterpret_cast<const float*>(s_pu)[i - nb0];
-          float delta, llY = 0.0f;
-          F2 lfY{0.0f, 0.0f};
-          const F2 lfX = M::logf32p(chi[m], tf);
+          float delta, llY = 0.0f, lfY = 0.0f, cY = 0.0f, cX;
+          const float lfX = M::logf32_e(chi[m], tf, cX);
           if (!M::support32(Y, tf)) {
             delta = -INFINITY;
           } else {
             llY = reinterpret_cast<const float*>(s_pll)[i - nb0];
-            lfY = M::logf32p(Y, tf);
-            delta = (llY + (lfY.hi + lfY.lo)) - (ll[m] + (lfX.hi + lfX.lo));
+            lfY = M::logf32_e(Y, tf, cY);
+            delta = (llY + lfY) - (ll[m] + lfX);
           }
           float alpha;
           const bool acc = mh_accept32(delta, u, alpha);
@@ -380,9 +386,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
             ll[m] = llY;
             member_acc++;
           }
-          const F2 lfc = acc ? lfY : lfX;  // hi in the first half of the slots, lo in the second
-          s_lf32[i - nb0] = lfc.hi;
-          s_lf32[a.mpb + (i - nb0)] = lfc.lo;
+          s_lf32[i - nb0] = acc ? cY : cX;  // what the theta' partial needs of the new state
           reinterpret_cast<float*>(s_pu)[a.mpb + (i - nb0)] = alpha;  // RAM update in the next half-step
           if (trace) {
             const long long o = (a.trace_off + s) * a.n + static_cast<long long>(i);
@@ -442,17 +446,14 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     XFlags fd = {0u, 0u, 0u}, fe = {0u, 0u, 0u};
     unsigned int neg_big = 0, pos_big = 0;
     if (prior_ok && F32) {
-      const ThetaCf tpf = s_tcpf;
+      const ThetaCf tpf = s_tcpf, tf = s_tcf;
+      const ThetaDf tdf = s_tdf;
 #pragma unroll
       for (int m = 0; m < K; ++m) {
         const unsigned int i = nb0 + tid + m * blockDim.x;
         if (i < nb1) {
           const float c = static_cast<float>(chi[m]);
-          float dn = -INFINITY;
-          if (M::support32(c, tpf)) {  // (hi' - hi) + (lo' - lo), as the streaming kernel forms it
-            const F2 lfp = M::logf32p(c, tpf);
-            dn = __fadd_rn(__fsub_rn(lfp.hi, s_lf32[i - nb0]), __fsub_rn(lfp.lo, s_lf32[a.mpb + (i - nb0)]));
-          }
+          const float dn = M::support32(c, tpf) ? M::dtheta32(c, s_lf32[i - nb0], tf, tpf, tdf) : -INFINITY;
           if (dn != dn) fd.nan++;
           else if (fabsf(dn) >= 0x1p94f) {
             if (dn < 0.0f) neg_big++;
@@ -557,6 +558,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         ThetaPub& o = s_cand[c];
         propose_theta<M>(a, s + 1, p, c ? s_thp : s_theta, s_Sth, o.thp, o.lpri_new, o.tcp, s_math);
         o.tcpf = M::consts32(o.tcp);
+        if (F32) o.tdf = M::dconsts32(c ? s_tcp : s_tc, o.tcp);  // the step from that outcome's theta
       }
     }
     if (!grid_wait(a.bar, static_cast<unsigned int>(s), a.err, a.timeout_ns, nbar)) return;

@@ -24,6 +24,11 @@ struct ThetaC {
 struct ThetaCf {
   float sc_hi, sc_lo, loc_hi, loc_lo, low_hi, low_lo;  // scale, location, lower bound (hi + lo)
 };
+// binary32 constants of one theta step (theta -> theta'), each as hi + lo: the FP32 form's
+// d_i = log f(chi;theta') - log f(chi;theta) is formed from them directly (LF; unused by NN1)
+struct ThetaDf {
+  float dsc_hi, dsc_lo, c_hi, c_lo, em_hi, em_lo;
+};
 __device__ __forceinline__ void split_f(double v, float& hi, float& lo) {
   hi = static_cast<float>(v);
   lo = static_cast<float>(v - static_cast<double>(hi));
@@ -71,6 +76,15 @@ struct NN1 {
     return -__fmaf_rn(c.sc_hi, r2, __fmul_rn(c.sc_lo, r2));  // the scale's rounding would bias every member alike
   }
   __device__ static F2 logf32p(float chi, const ThetaCf& c) { return F2{logf32(chi, c), 0.0f}; }
+  // the member step's log f and what the theta' partial needs of the state: here log f itself
+  __device__ static float logf32_e(float chi, const ThetaCf& c, float& carry) {
+    carry = logf32(chi, c);
+    return carry;
+  }
+  __device__ static ThetaDf dconsts32(const ThetaC&, const ThetaC&) { return ThetaDf{}; }
+  __device__ static float dtheta32(float chi, float lf_cur, const ThetaCf&, const ThetaCf& cp, const ThetaDf&) {
+    return __fsub_rn(logf32(chi, cp), lf_cur);
+  }
   // member data d[0], d[1] = y_i as hi + lo, d[2] = 1/(2 sigma_i^2)
   static constexpr int kData32 = 3;
   __device__ static void data32(double y, double aux, const ModelConsts&, float* d) {
@@ -133,9 +147,37 @@ struct LF {
     const float e = exp32(xh);
     return F2{__fmaf_rn(c.sc_hi, xh, -e), __fmaf_rn(c.sc_hi, xl, __fmaf_rn(c.sc_lo, xh, -__fmul_rn(e, xl)))};
   }
-  __device__ static float logf32(float chi, const ThetaCf& c) {
-    const F2 v = logf32p(chi, c);
-    return __fadd_rn(v.hi, v.lo);
+  // the member step's log f (one binary32 value; the accept needs no more) and e^x, which the
+  // theta' partial of the state needs
+  __device__ static float logf32_e(float chi, const ThetaCf& c, float& carry) {
+    float xh, xl;
+    sub2x(chi, c.loc_hi, c.loc_lo, xh, xl);
+    const float e = exp32(xh);
+    carry = e;
+    const float ex = __fmaf_rn(e, xl, e);  // e^(xh + xl) to first order in xl
+    return __fmaf_rn(c.sc_hi, xh, __fmaf_rn(c.sc_hi, xl, __fmaf_rn(c.sc_lo, xh, -ex)));
+  }
+  // theta -> theta' constants in binary64, each rounded to hi + lo: dsc = beta' - beta,
+  // c = (beta' + 1)(ln L*' - ln L*), em = e^(ln L* - ln L*') - 1
+  __device__ static ThetaDf dconsts32(const ThetaC& t, const ThetaC& tp) {
+    ThetaDf d{};
+    const double dL = tp.a1 - t.a1;
+    split_f(tp.a0 - t.a0, d.dsc_hi, d.dsc_lo);
+    split_f(tp.a0 * dL, d.c_hi, d.c_lo);
+    split_f(expm1(-dL), d.em_hi, d.em_lo);
+    return d;
+  }
+  // d_i = log f(chi;theta') - log f(chi;theta) = dsc x - c - e^x em with x = chi - ln L* (xh + xl)
+  // and e = e^xh (e^x = e (1 + xl) to first order): the small terms (the lo parts, xl) are summed
+  // first and enter the large ones inside single roundings, so none is rounded away alike for
+  // every member; the difference of two O(1) log f values would lose ~1e-7 of each
+  __device__ static float dtheta32(float chi, float e, const ThetaCf& c, const ThetaCf&, const ThetaDf& d) {
+    float xh, xl;
+    sub2x(chi, c.loc_hi, c.loc_lo, xh, xl);
+    float b = __fmaf_rn(-e, __fmaf_rn(xl, d.em_hi, d.em_lo), -d.c_lo);
+    b = __fmaf_rn(d.dsc_lo, xh, b);
+    b = __fmaf_rn(d.dsc_hi, xl, b);
+    return __fmaf_rn(d.dsc_hi, xh, __fmaf_rn(-e, d.em_hi, __fsub_rn(b, d.c_hi)));
   }
   // member data: d[0], d[1] = ln(Fhat_i/q_i) as hi + lo, d[2] = Fhat_i^2/(2 sigma_F^2) > 0, so
   // that log l_i = -d[2] expm1(chi - ln(Fhat_i/q_i))^2 keeps binary32 relative accuracy however
@@ -237,6 +279,12 @@ struct BB1 {
   __device__ static bool support32(float, const ThetaCf&) { return true; }
   __device__ static float logf32(float, const ThetaCf&) { return 0.0f; }
   __device__ static F2 logf32p(float, const ThetaCf&) { return F2{0.0f, 0.0f}; }
+  __device__ static float logf32_e(float, const ThetaCf&, float& carry) {
+    carry = 0.0f;
+    return 0.0f;
+  }
+  __device__ static ThetaDf dconsts32(const ThetaC&, const ThetaC&) { return ThetaDf{}; }
+  __device__ static float dtheta32(float, float, const ThetaCf&, const ThetaCf&, const ThetaDf&) { return 0.0f; }
   __device__ static void data32(double, double, const ModelConsts&, float* d) { d[0] = 0.0f; }
   __device__ static float loglike32(float, const float*) { return 0.0f; }
 };
@@ -687,28 +735,39 @@ __device__ __forceinline__ void box_muller32(uint32_t wa, uint32_t wb, float& z_
 // (no cancellation; alpha is a binary32 value, so c carries binary32 error anyway). The update
 // is then exact to ~1e-7 |c| relative, and S itself never loses binary64 precision.
 
-// binary64 -> binary32 rounded toward zero, on the integer pipe (the proposal scale of a member;
-// any positive scale gives a valid proposal). Values outside binary32's normal range take the
-// conversion instruction.
+// binary64 -> binary32 rounded toward zero, on the integer pipe only (the proposal scale of a
+// member; any positive scale gives a valid proposal): magnitudes beyond binary32's normal range
+// clamp to its largest or smallest normal value.
 __device__ __forceinline__ float f32_rz(double x) {
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
   const int e = static_cast<int>((b >> 52) & 0x7ff) - 1023 + 127;
-  if (e >= 1 && e <= 254)
-    return __uint_as_float((static_cast<unsigned int>(b >> 32) & 0x80000000u) | (static_cast<unsigned int>(e) << 23) |
-                           static_cast<unsigned int>((b >> 29) & 0x7FFFFFull));
-  return __double2float_rz(x);
+  const unsigned int sign = static_cast<unsigned int>(b >> 32) & 0x80000000u;
+  const unsigned int body = (e >= 255) ? 0x7F7FFFFFu
+                            : (e <= 0) ? 0x00800000u
+                                       : (static_cast<unsigned int>(e) << 23) |
+                                             static_cast<unsigned int>((b >> 29) & 0x7FFFFFull);
+  return __uint_as_float(sign | body);
 }
 
-// binary32 -> binary64, exact, on the integer pipe (zeros and normal values; the rest take the
-// conversion instruction)
+// binary32 -> binary64, exact, on the integer pipe only (every class: zeros, subnormals
+// normalised by a leading-zero count, normal values, infinities and NaN)
 __device__ __forceinline__ double f64_of(float v) {
   const unsigned int u = __float_as_uint(v);
-  const unsigned int e = (u >> 23) & 0xffu;
+  const unsigned int e = (u >> 23) & 0xffu, m = u & 0x7FFFFFu;
   const unsigned long long sign = static_cast<unsigned long long>(u >> 31) << 63;
-  if (e == 0u && (u & 0x7FFFFFu) == 0u) return __longlong_as_double(static_cast<long long>(sign));
-  if (e == 0u || e == 0xffu) return static_cast<double>(v);
-  return __longlong_as_double(static_cast<long long>(sign | (static_cast<unsigned long long>(e + 896u) << 52) |
-                                                     (static_cast<unsigned long long>(u & 0x7FFFFFu) << 29)));
+  unsigned long long body;
+  if (e == 0xffu) {
+    body = (0x7FFull << 52) | (static_cast<unsigned long long>(m) << 29);
+  } else if (e != 0u) {
+    body = (static_cast<unsigned long long>(e + 896u) << 52) | (static_cast<unsigned long long>(m) << 29);
+  } else if (m != 0u) {  // m 2^-149: shift the leading bit to position 23
+    const unsigned int k = static_cast<unsigned int>(__clz(m)) - 8u;
+    body = (static_cast<unsigned long long>(897u - k) << 52) |
+           (static_cast<unsigned long long>((m << k) & 0x7FFFFFu) << 29);
+  } else {
+    body = 0ull;
+  }
+  return __longlong_as_double(static_cast<long long>(sign | body));
 }
 
 // One RAM step of a d = 1 factor in the FP32 form: S + S d, d = c / (1 + sqrt(1 + c)) (1 + c >= 0.6:
@@ -872,12 +931,14 @@ struct ThetaPub {
   double lpri_new;
   ThetaC tcp;
   ThetaCf tcpf;
+  ThetaDf tdf;  // FP32 form: constants of the step from the sweep's theta to this theta'
 };
 static_assert(sizeof(ThetaPub) <= sizeof(double) * kPubWords, "ThetaPub does not fit its buffer");
 
 // Block 0: write theta' of the launch's sweep s1 (1-based), then release its sequence number.
 __device__ __forceinline__ void publish_theta(const SweepArgs& a, unsigned int s1, const double* thp, int p,
-                                              double lpri_new, const ThetaC& tcp, const ThetaCf& tcpf) {
+                                              double lpri_new, const ThetaC& tcp, const ThetaCf& tcpf,
+                                              const ThetaDf& tdf) {
   ThetaPub* pub = reinterpret_cast<ThetaPub*>(a.pub);
   for (int q = 0; q < p; ++q) __stcg(pub->thp + q, thp[q]);
   __stcg(&pub->lpri_new, lpri_new);
@@ -889,6 +950,9 @@ __device__ __forceinline__ void publish_theta(const SweepArgs& a, unsigned int s
   const float* f = &tcpf.sc_hi;
   float* g = &pub->tcpf.sc_hi;
   for (int q = 0; q < 6; ++q) __stcg(g + q, f[q]);
+  const float* fd = &tdf.dsc_hi;
+  float* gd = &pub->tdf.dsc_hi;
+  for (int q = 0; q < 6; ++q) __stcg(gd + q, fd[q]);
   __threadfence();
   st_release_u32(a.bar + 1, s1);
 }
@@ -896,7 +960,7 @@ __device__ __forceinline__ void publish_theta(const SweepArgs& a, unsigned int s
 // Other blocks: wait (bounded) until block 0 has published sweep s1, then read it. Returns false
 // if the run failed meanwhile or the wait ran out (the run's error word then says why).
 __device__ __forceinline__ bool fetch_theta(const SweepArgs& a, unsigned int s1, double* thp, int p, double& lpri_new,
-                                            ThetaC& tcp, ThetaCf& tcpf) {
+                                            ThetaC& tcp, ThetaCf& tcpf, ThetaDf& tdf) {
   const long long t0 = globaltimer_ns();
   while (ld_acquire_u32(a.bar + 1) < s1) {
     if (ld_volatile_i32(a.err) != 0) return false;
@@ -917,6 +981,9 @@ __device__ __forceinline__ bool fetch_theta(const SweepArgs& a, unsigned int s1,
   const float* g = &pub->tcpf.sc_hi;
   float* f = &tcpf.sc_hi;
   for (int q = 0; q < 6; ++q) f[q] = __ldcg(g + q);
+  const float* gd = &pub->tdf.dsc_hi;
+  float* fd = &tdf.dsc_hi;
+  for (int q = 0; q < 6; ++q) fd[q] = __ldcg(gd + q);
   return true;
 }
 

@@ -72,7 +72,7 @@ class CudahmStats(ctypes.Structure):
         ("grid_blocks", ctypes.c_int32),
         ("block_threads", ctypes.c_int32),
         ("objects_per_thread", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("grid_blocks", ctypes.c_int32),
     ]
 
 
@@ -81,7 +81,7 @@ class CudahmTune(ctypes.Structure):
         ("block_threads", ctypes.c_int32),
         ("sweeps_per_launch", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("grid_blocks", ctypes.c_int32),
     ]
 
 

@@ -59,17 +59,19 @@ def test_batch_equals_each_population_alone(precision):
 def test_batch_result_does_not_depend_on_launch_shape():
     specs = _populations(cudahm.FP32, seed0=7)
     runs = []
-    for block, chunk in ((128, 17), (256, 1000)):
+    for block, chunk, grid in ((128, 17, 0), (256, 1000, 0), (128, 33, 200)):
         ss = [_make(sp, cudahm.FP32) for sp in specs]
-        tune = cudahm.CudahmTune(block, chunk, 0, 0)
+        tune = cudahm.CudahmTune(block, chunk, 0, grid)
         rows, chosen = cudahm.batch_run(ss, 0, 60, 1, tune)
         assert chosen.block_threads == block and chosen.sweeps_per_launch == chunk
+        assert chosen.grid_blocks == grid if grid else chosen.grid_blocks >= len(specs)
         runs.append((rows, [_state(s) for s in ss]))
-    for a, b in zip(runs[0][0], runs[1][0]):
-        assert np.array_equal(a, b)
-    for sa, sb in zip(runs[0][1], runs[1][1]):
-        for x, y in zip(sa, sb):
-            assert np.array_equal(x, y)
+    for r in runs[1:]:
+        for a, b in zip(runs[0][0], r[0]):
+            assert np.array_equal(a, b)
+        for sa, sb in zip(runs[0][1], r[1]):
+            for x, y in zip(sa, sb):
+                assert np.array_equal(x, y)
 
 
 def test_batch_rejects_mixed_precision():
