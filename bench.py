@@ -94,6 +94,7 @@ def parse():
     ap.add_argument("--no-marginal", action="store_true")
     ap.add_argument("--no-nn1", action="store_true")
     ap.add_argument("--no-moments", action="store_true")
+    ap.add_argument("--no-shard", action="store_true")
     ap.add_argument("--marginal-burn", type=int, default=300)
     ap.add_argument("--marginal-steps", type=int, default=1500)
     ap.add_argument("--nn3-sizes", default="100,1000,10000,30000")
@@ -258,9 +259,24 @@ def run_reference(args):
 
 
 # -------------------------------------------------------------------- CUDA ---
-def fp64_peak(device):
+PEAK_SRC = os.path.join(ROOT, "bench_fp64_peak.cu")
+PEAK_LIB = os.path.join(ROOT, "_build", "libchm_peaks.so")
+
+
+def build_peaks(force=False):
+    """Compiles the FP64 peak probe (bench_fp64_peak.cu) that the roofline denominators use."""
+    if not force and os.path.exists(PEAK_LIB) and os.path.getmtime(PEAK_LIB) >= os.path.getmtime(PEAK_SRC):
+        return PEAK_LIB
     from paper_2105_08026_gb300 import build as cbuild
-    L = ctypes.CDLL(cbuild.PEAKS_LIB)
+    os.makedirs(os.path.dirname(PEAK_LIB), exist_ok=True)
+    tmp = PEAK_LIB + f".tmp{os.getpid()}"
+    subprocess.check_call([cbuild.nvcc(), *cbuild.ARCH, "-O3", "-Xcompiler", "-fPIC", "-shared", "-o", tmp, PEAK_SRC])
+    os.replace(tmp, PEAK_LIB)
+    return PEAK_LIB
+
+
+def fp64_peak(device):
+    L = ctypes.CDLL(build_peaks())
     L.chm_fp64_dfma_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     r = ctypes.c_double(0.0)
     rc = L.chm_fp64_dfma_rate(device, ctypes.byref(r))
@@ -304,6 +320,54 @@ def run_batched(args, cudahm, stream, device):
                                    "sweeps_per_launch": chosen.sweeps_per_launch,
                                    "graph": bool(chosen.use_graph), "blocks": chosen.grid_blocks},
             "dtype": "f32 member terms, f64 sums/accept/RAM/selection integral (1024x1024 rule per LF population)"}
+
+
+def run_shard(args, cudahm, rank, ws, local):
+    """One LF population split over the ranks (every rank, a collective leg): rank r holds
+    N_OBJ members (its own synthetic catalog, seed DATA_SEED + r; the model settings of catalog
+    DATA_SEED on every rank), population index r N_OBJ onward, and its 1/ws share of the
+    1024 x 1024 rule's outer nodes. Each sweep: the shard pass (streaming kernel), an all-reduce
+    of the 16 exchange words (NCCL, int64 sum, on the sampler's stream; none at one rank), the
+    decision kernel. FP64. W untimed sweeps, then K timed, CUDA events on the sampler's stream,
+    max over ranks; the value is the population's member updates per second (weak scaling: the
+    members per rank stay fixed)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2105_08026_gb300 import synth
+    _, theta0, scale, consts = workload(0)
+    data = synth.lf_data(N_OBJ, seed=replica_seeds(rank)[0])
+    n_pop = N_OBJ * ws
+    st = torch.cuda.Stream(device=local)
+    s = cudahm.Sampler(cudahm.LF, N_OBJ, theta_init=theta0, theta_prop_scale=scale, model_consts=consts,
+                       seed=CHAIN_SEED, device=local, stream=st.cuda_stream, use_torch_allocator=True)
+    with torch.cuda.stream(st):
+        y_dev = torch.from_numpy(data.fhat).cuda()
+        r_dev = torch.from_numpy(data.r).cuda()
+        cudahm.cudahm_set_data_device(s.h, y_dev.data_ptr(), r_dev.data_ptr(), N_OBJ)
+        s.shard(rank * N_OBJ, n_pop, rank, ws)
+        words = torch.zeros(cudahm.SHARD_WORDS, dtype=torch.int64, device=f"cuda:{local}")
+        exchange = (lambda w: dist.all_reduce(w, op=dist.ReduceOp.SUM)) if ws > 1 else (lambda w: None)
+        if args.warmup > 0:
+            s.run_sharded(0, args.warmup, 1, words, exchange)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        K = args.steps
+        e0.record(st)
+        rows = s.run_sharded(0, K, 1, words, exchange)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    assert rows.shape[0] == K
+    t = max_over_ranks(ms)
+    s.close()
+    return {"value": n_pop * K / (t * 1e-3), "unit": "object-updates/s", "ms_per_step": t / K,
+            "population": n_pop, "shards": ws, "members_per_shard": N_OBJ, "scaling": "weak", "dtype": "f64",
+            "exchange": ("NCCL all-reduce of 16 int64 words per sweep" if ws > 1 else "none (one shard)"),
+            "launches_per_sweep": 2,
+            "note": "one chain over the whole population; bit-identical to one handle holding it"}
 
 
 def run_mvn3(args, cudahm, stream, device, flush, peak_fp64):
@@ -733,9 +797,9 @@ def run_cuda(args):
     clocks = ClockSampler(local)
     clocks.start()
     clocks.wait_first()
-    # warm-up: burn-in sweeps (untimed)
+    # warm-up: W untimed sweeps through the same call as the timed steps (run, rows read back)
     if args.warmup > 0:
-        s.run(args.warmup, 0)
+        s.run(0, args.warmup, 1)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     K = args.steps
     # timed run calls of up to one persistent launch each (4096 sweeps), the L2 flushed before each
@@ -747,7 +811,7 @@ def run_cuda(args):
     torch.cuda.synchronize()
     t_timed0 = time.perf_counter()
     total_ms = 0.0
-    kernel_ms = 0.0
+    host_ms = 0.0
     launches = 0
     rows_total = 0
     kept = []
@@ -760,8 +824,11 @@ def run_cuda(args):
         rows = s.run(0, ns, 1)
         e1.record(stream)
         e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        kernel_ms += s.stats().last_run_ms
+        # the step's device time: the library's events on the stream, from before its first kernel
+        # to after the kept rows' copy to the host (the torch events also hold the host's enqueue
+        # and return latency, when the device is idle: reported beside it)
+        total_ms += s.stats().last_run_ms
+        host_ms += e0.elapsed_time(e1)
         nl = math.ceil(ns / 4096)
         launches += 2 * nl  # per chunk of <= 4096 sweeps: theta-table kernel + persistent sweep kernel
         rows_total += rows.shape[0]
@@ -782,7 +849,7 @@ def run_cuda(args):
                             use_torch_allocator=True, precision=cudahm.FP32)
         cudahm.cudahm_set_data_device(s3.h, y_dev.data_ptr(), r_dev.data_ptr(), n)
         if args.warmup > 0:
-            s3.run(args.warmup, 0)
+            s3.run(0, args.warmup, 1)
         f_ms = 0.0
         for ns in chunks:
             flush.zero_()
@@ -808,7 +875,7 @@ def run_cuda(args):
                             use_torch_allocator=True, keep_chi_moments=True)
         cudahm.cudahm_set_data_device(s4.h, y_dev.data_ptr(), r_dev.data_ptr(), n)
         if args.warmup > 0:
-            s4.run(args.warmup, 0)
+            s4.run(args.warmup, 0)  # burn-in: its sweeps are not kept in the moments
         m_ms = 0.0
         for ns in chunks:
             flush.zero_()
@@ -826,6 +893,11 @@ def run_cuda(args):
                    "kept_sweeps": int(cnt), "relative_to_plain": (n * K / (m_ms * 1e-3)) / value,
                    "dtype": "f64", "median_posterior_sd_chi": float(np.median(np.sqrt(var)))}
         s4.close()
+
+    # one population split over the ranks (all ranks: an all-reduce per sweep)
+    shard = None
+    if not args.no_shard:
+        shard = run_shard(args, cudahm, rank, ws, local)
 
     # batched FP32 form: 256 NN1/LF populations of uneven size in one persistent launch per chunk
     batched = None
@@ -867,7 +939,7 @@ def run_cuda(args):
         host_y = np.ascontiguousarray(data.fhat)
         host_r = np.ascontiguousarray(data.r)
         s2.set_data(host_y, host_r)
-        s2.run(min(args.warmup, 200), 0)  # warm the selection-integral cache and the code path
+        s2.run(0, max(1, min(args.warmup, 200)), 1)  # untimed: the same call path as the timed steps
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for ns in chunks:  # the same run calls as the device-timed leg
@@ -888,7 +960,7 @@ def run_cuda(args):
         return 0
 
     st = s.stats()
-    sweep_launch_ms = kernel_ms / max(1, launches // 2)
+    sweep_launch_ms = total_ms / max(1, launches // 2)  # (with the table kernel and the rows' copy)
     sweeps_per_launch = K / max(1, launches // 2)
     roofline = {"bound": "alu", "unit": "TFLOP/s", "peak": peak / 1e12 if peak else None,
                 "peak_source": "FP64 DFMA stream measured live on this GPU (x2 flops)",
@@ -914,10 +986,13 @@ def run_cuda(args):
             "config": {"workload": "LF thinned luminosity function, N=3e5, FP64, 1024x1024 selection rule",
                        "n": n, "parallelism": f"replicas x{ws}", "l2": "256 MB flush before each timed launch; "
                        "member state register-resident within a launch", "timed_launches": R,
+                       "timing": "device time per run call: the library's CUDA events on the stream, before the "
+                                 "theta-table kernel to after the kept rows' copy to the host",
+                       "host_inclusive_ms_per_step": host_ms / K,
                        "launch_shape": [st.grid_blocks, st.block_threads, st.objects_per_thread]},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "fp32_bulk": fp32, "batched_fp32": batched, "served_fp32": served, "mvn3": mvn3, "bb1": bb1, "nn3_ess": nn3,
-            "marginal": marg, "nn1_n1000": nn1, "chi_moments": moments}
+            "marginal": marg, "nn1_n1000": nn1, "chi_moments": moments, "shard": shard}
     print(json.dumps(line), flush=True)
     s.close()
     if ws > 1:

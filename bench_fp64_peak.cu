@@ -1,6 +1,7 @@
-// FP64 pipe peak of the current GPU: DFMA throughput of a dependent-free stream
-// (8 independent FMA chains per thread, a few waves of blocks per SM). This is the
-// denominator of the ALU roofline the FP64 sampler is bound by.
+// Benchmark tool (built and loaded by bench.py; not part of the library): the FP64 pipe peak of
+// the current GPU, as the DFMA throughput of a dependent-free stream (8 independent FMA chains
+// per thread, a few waves of blocks per SM). This is the denominator of the ALU roofline the
+// FP64 sampler is bound by.
 #include <cuda_runtime.h>
 
 namespace {

@@ -149,7 +149,8 @@ typedef struct {
   int64_t member_accepts;     /* accepted member proposals since create */
   int64_t theta_accepts;      /* accepted theta proposals since create */
   int64_t rows;               /* theta rows held in the sample buffer */
-  double last_run_ms;         /* device time of the last cudahm_run (CUDA events) */
+  double last_run_ms;         /* device time of the last cudahm_run: CUDA events on its stream from
+                                 before its first kernel to after the kept rows' copy to the host */
   double etabar;              /* LF: selection integral at the current theta; 0 otherwise */
   int32_t grid_blocks;        /* launch shape of the sweep kernel */
   int32_t block_threads;
@@ -348,6 +349,48 @@ typedef struct {
  * receives the shape used. On failure every handle's chain stops where its last launch ended. */
 int cudahm_batch_run(cudahm_t* handles, int32_t k, int64_t n_burn, int64_t n_iter, int64_t thin,
                      const cudahm_tune* tune, cudahm_tune* chosen);
+
+/* Shards: one population split across devices (Sec. 6, populations larger than one device
+ * holds). Each shard is a handle created with the population's config (same model, constants,
+ * theta start, seed and precision) whose n members are the population's members
+ * [member_offset, member_offset + n), loaded with set_data as usual. A sweep is
+ *   1. cudahm_shard_pass on every shard: the member steps of its members (the draws of member i
+ *      carry its population index member_offset + i, so they are the unsplit chain's), and the
+ *      shard's part of the theta' sum D = sum_i [log f(chi_i;theta') - log f(chi_i;theta)] and of
+ *      the selection integral at theta' (LF, BB1: outer nodes [n_L part/parts, n_L (part+1)/parts)),
+ *      written as CUDAHM_SHARD_WORDS exchange words;
+ *   2. the caller adds the words of all shards as unsigned 64-bit integers (an all-reduce with
+ *      the sum operation, e.g. NCCL or gloo on int64/uint64 buffers; wrap-around never occurs);
+ *   3. cudahm_shard_decide on every shard with the summed words: the theta decision (Sec. 2.2),
+ *      taken identically on every shard.
+ * The chain, the latents and the kept theta rows equal those of one handle holding the whole
+ * population (cudahm_run), bit for bit: all sums are exact.
+ * Exchange words (little-endian u64): [0..5] D, [6..11] the selection integral, each the 32-bit
+ * limbs (low first) of a 192-bit two's-complement fixed-point number with 2^-96 resolution (each
+ * addend rounded toward zero to a multiple of 2^-96); [12] count of d_i <= -2^94 or off the
+ * support | NaN count << 32; [13] count of d_i >= 2^94 | member-step NaN count << 32; [14] the
+ * shard's member count; [15] 1. decide checks that [14] sums to population_n and [15] to parts.
+ * Work goes to the handle's stream (config cuda_stream), in call order, without host
+ * synchronisation between begin and end; words_dev and total_dev are device buffers of 16
+ * words, 8-byte aligned, which may be the same buffer (an in-place all-reduce between the two
+ * calls). Not with the marginal form, a lockstep trace or latent moments (EUNSUPPORTED). */
+#define CUDAHM_SHARD_WORDS 16
+
+/* This handle is shard `part` of `parts` of a population of population_n members (< 2^32). */
+int cudahm_shard_config(cudahm_t h, int64_t member_offset, int64_t population_n, int32_t part, int32_t parts);
+/* Starts a sharded run of n_burn + n_iter sweeps (thin as in cudahm_run); synchronises. */
+int cudahm_shard_begin(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin);
+/* Enqueues the next sweep's pass; its exchange words go to words_dev (overwritten). */
+int cudahm_shard_pass(cudahm_t h, uint64_t* words_dev);
+/* Enqueues the decision of the sweep whose pass came last, from the summed words. */
+int cudahm_shard_decide(cudahm_t h, const uint64_t* total_dev);
+/* Synchronises and ends the run (after any number of pass/decide pairs); rows_out (nullable)
+ * receives the kept rows, which cudahm_get_samples returns. ESTATE if the words of some sweep
+ * did not come from every shard once (the chain stops before that sweep's decision), or if the
+ * last pass was not decided (the run still ends; the latents are then one sweep past theta);
+ * ENUMERIC, ETIMEOUT as for cudahm_run. Until the run ends, cudahm_run and cudahm_batch_run on
+ * the handle fail with ESTATE, and other calls see the chain between sweeps. */
+int cudahm_shard_end(cudahm_t h, int64_t* rows_out);
 
 /* Serving: a request loop with continuous batching.
  * A server owns a worker thread and a stream on one device. Requests (a config, member data

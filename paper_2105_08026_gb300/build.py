@@ -18,9 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libcudahm.so")
-PEAKS_LIB = os.path.join(LIBDIR, "libchm_peaks.so")
 SOURCES = ["sweep.cu", "batch.cu", "runtime.cu", "noalloc.cu", "diag.cu", "marginal.cu", "twostate.cu"]
-PEAKS_SOURCES = ["pipe_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", f"-I{INCLUDE}", f"-I{CSRC}"]
 
@@ -38,9 +36,9 @@ def _inputs():
 
 
 def up_to_date() -> bool:
-    if not (os.path.exists(LIB) and os.path.exists(PEAKS_LIB)):
+    if not os.path.exists(LIB):
         return False
-    t = min(os.path.getmtime(LIB), os.path.getmtime(PEAKS_LIB))
+    t = os.path.getmtime(LIB)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
@@ -52,7 +50,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cc = nvcc()
     procs = []
     objs = {}
-    for src in SOURCES + PEAKS_SOURCES:
+    for src in SOURCES:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs[src] = obj
         cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
@@ -63,13 +61,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
         out, _ = pr.communicate()
         if pr.returncode != 0:
             raise RuntimeError(f"nvcc failed: {' '.join(cmd)}\n{out.decode(errors='replace')}")
-    for lib, srcs in ((LIB, SOURCES), (PEAKS_LIB, PEAKS_SOURCES)):
-        tmp = lib + f".tmp{os.getpid()}"
-        cmd = [cc, *ARCH, "-shared", "-o", tmp, *[objs[s] for s in srcs], "-lcudart"]
-        out = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
-        if out.returncode != 0:
-            raise RuntimeError(f"link failed: {' '.join(cmd)}\n{out.stdout.decode(errors='replace')}")
-        os.replace(tmp, lib)
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *[objs[s] for s in SOURCES], "-lcudart"]
+    out = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+    if out.returncode != 0:
+        raise RuntimeError(f"link failed: {' '.join(cmd)}\n{out.stdout.decode(errors='replace')}")
+    os.replace(tmp, LIB)
     return LIB
 
 

@@ -77,13 +77,13 @@ __device__ __forceinline__ void member_f64(const SweepArgs& a, unsigned int i, u
   double echi = M::kExp ? exp_tab(chi, s_math) : 0.0;
   double ll = M::loglike(chi, echi, yv, av, a.mc);
   const bool odd = (k & 1u) != 0u;
-  const uint4 w0 = philox4x32_10(make_uint4(0u, 0u, i, odd ? k : k - 1u), a.key0, a.key1);
+  const uint4 w0 = philox4x32_10(make_uint4(0u, 0u, a.moff + i, odd ? k : k - 1u), a.key0, a.key1);
   const double ua = uniform53(w0.x, w0.y), ub = uniform53(w0.z, w0.w);
   const double rad = sqrt(-2.0 * log_tab(ua, s_math));
   double sn, cs;
   sincospi_tab(2.0 * ub, s_math, &sn, &cs);
   const double z = odd ? rad * cs : rad * sn;
-  const uint4 w1 = philox4x32_10(make_uint4(1u, 0u, i, k), a.key0, a.key1);
+  const uint4 w1 = philox4x32_10(make_uint4(1u, 0u, a.moff + i, k), a.key0, a.key1);
   const double u = uniform53(w1.x, w1.y);
   const double Y = fma(S, z, chi);
   double delta, eY = 0.0, llY = 0.0, lfY = 0.0;
@@ -140,7 +140,7 @@ __device__ __forceinline__ void member1_f32(const SweepArgs& a, unsigned int i, 
   const bool odd = (k & 1u) != 0u;
   // Philox block (0, stream 2, member i, odd sweep): a Box-Muller pair from words 0 and 1 (cosine
   // for the odd sweep, sine for the next), the accept uniforms of the two sweeps from words 2, 3
-  const uint4 w = philox4x32_10(make_uint4(0u, 2u, i, odd ? k : k - 1u), a.key0, a.key1);
+  const uint4 w = philox4x32_10(make_uint4(0u, 2u, a.moff + i, odd ? k : k - 1u), a.key0, a.key1);
   const float u = uniform23(odd ? w.z : w.w);
   float zc, zs;
   box_muller32(w.x, w.y, zc, zs);
@@ -308,7 +308,7 @@ __device__ __forceinline__ void member3_f64(const SweepArgs& a, unsigned int i, 
   if (odd || first) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const uint4 b = philox4x32_10(make_uint4(static_cast<uint32_t>(c), 0u, i, ko), a.key0, a.key1);
+      const uint4 b = philox4x32_10(make_uint4(static_cast<uint32_t>(c), 0u, a.moff + i, ko), a.key0, a.key1);
       const double ua = uniform53(b.x, b.y), ub = uniform53(b.z, b.w);
       const double rad = sqrt(-2.0 * log_tab(ua, s_math));
       double sn, cs;
@@ -320,7 +320,7 @@ __device__ __forceinline__ void member3_f64(const SweepArgs& a, unsigned int i, 
 #pragma unroll
     for (int c = 0; c < 3; ++c) z[c] = a.spare3[c * n + i];
   }
-  const uint4 bu = philox4x32_10(make_uint4(3u, 0u, i, k), a.key0, a.key1);
+  const uint4 bu = philox4x32_10(make_uint4(3u, 0u, a.moff + i, k), a.key0, a.key1);
   const double u = uniform53(bu.x, bu.y);
   // v = S z (lower triangular), proposal Y = chi + v
   const double v0 = S[0] * z[0];
@@ -394,8 +394,8 @@ __device__ __forceinline__ void member3_f32(const SweepArgs& a, unsigned int i, 
   for (int q = 0; q < 6; ++q) S[q] = a.S[q * n + i];
   const bool odd = (k & 1u) != 0u;
   const uint32_t ko = odd ? k : k - 1u;
-  const uint4 b0 = philox4x32_10(make_uint4(0u, 2u, i, ko), a.key0, a.key1);
-  const uint4 b1 = philox4x32_10(make_uint4(1u, 2u, i, ko), a.key0, a.key1);
+  const uint4 b0 = philox4x32_10(make_uint4(0u, 2u, a.moff + i, ko), a.key0, a.key1);
+  const uint4 b1 = philox4x32_10(make_uint4(1u, 2u, a.moff + i, ko), a.key0, a.key1);
   const float z0 = bm23(b0.x, b0.y, odd), z1 = bm23(b0.z, b0.w, odd), z2 = bm23(b1.x, b1.y, odd);
   const float u = uniform23(odd ? b1.z : b1.w);
   const double zd0 = z0, zd1 = z1, zd2 = z2;
@@ -439,6 +439,40 @@ __device__ __forceinline__ void member3_f32(const SweepArgs& a, unsigned int i, 
     } else {
       xacc_add_float(xd, dn, fd);
     }
+  }
+}
+
+// Shard pass: the block's partial of the sweep is in its slot; the last block of the population
+// to finish (an atomic count of finished blocks on the population's barrier word, which it resets)
+// sums all nb partials and writes the shard's exchange words: D and E as six 32-bit limbs each,
+// the flag counts, the shard's member count and 1. Called by every thread of the block.
+__device__ void shard_export(const SweepArgs& a, const unsigned long long* base, int nb, BlockRed& red) {
+  __shared__ int s_last;
+  __syncthreads();  // the block's partial is written (warp 0, lane 0)
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(a.bar, 1u) == static_cast<unsigned int>(nb) - 1u) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();  // every other block's partial is visible
+  Xacc D, E;
+  unsigned int f[4];
+  sum_partials(base, nb, red, D, E, f);
+  if (threadIdx.x == 0) {
+    unsigned long long* o = a.shard_out;
+    const unsigned long long d[3] = {D.w0, D.w1, D.w2}, e[3] = {E.w0, E.w1, E.w2};
+    for (int q = 0; q < 3; ++q) {
+      o[2 * q] = d[q] & 0xFFFFFFFFull;
+      o[2 * q + 1] = d[q] >> 32;
+      o[6 + 2 * q] = e[q] & 0xFFFFFFFFull;
+      o[6 + 2 * q + 1] = e[q] >> 32;
+    }
+    o[12] = (static_cast<unsigned long long>(f[1]) << 32) | f[0];
+    o[13] = (static_cast<unsigned long long>(f[3]) << 32) | f[2];
+    o[14] = static_cast<unsigned long long>(a.n);
+    o[15] = 1ull;
+    *a.bar = 0u;  // for the next pass
   }
 }
 
@@ -598,6 +632,10 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
         }
       }
     }
+    if (a.shard_out != nullptr) {  // shard pass: the decision waits for the words of every shard
+      shard_export(a, a.partials + static_cast<size_t>(b0) * kPartWords, nb, s_red);
+      break;
+    }
     if (!pop_barrier(a.bar, static_cast<unsigned int>(s), static_cast<unsigned int>(nb), a.err, a.timeout_ns))
       return;
     {
@@ -609,26 +647,9 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
           atomicCAS(a.err, 0, CUDAHM_ENUMERIC);
           s_stop = 1;
         } else {
-          double logalpha, Drec, eb_new = 0.0, logeb_new = 0.0;
-          if (!prior_ok) {
-            logalpha = -INFINITY;
-            Drec = 0.0;
-          } else if (f[0] != 0u) {  // a member off the proposal's support (or d <= -2^94)
-            logalpha = -INFINITY;
-            Drec = -INFINITY;
-          } else if (f[2] != 0u) {  // only huge positive differences remain
-            logalpha = INFINITY;
-            Drec = INFINITY;
-          } else {
-            const double nn = static_cast<double>(a.n);
-            Drec = xacc_to_double(D);
-            logalpha = Drec + nn * (M::cterm(s_thp) - M::cterm(s_theta)) + s_lpri_new - s_lpri;
-            if (is_lf) {
-              eb_new = xacc_to_double(E);
-              logeb_new = log_etabar(eb_new, s_math);
-              logalpha -= nn * (logeb_new - s_logeb);
-            }
-          }
+          double logalpha, Drec, eb_new, logeb_new;
+          theta_logalpha<M>(D, E, f, prior_ok, static_cast<double>(a.n), s_theta, s_thp, s_lpri, s_lpri_new, s_logeb,
+                            s_math, logalpha, Drec, eb_new, logeb_new);
           const bool acc = __ldg(a.tab_lnu + s) < logalpha;
           if (lb == 0 && sg < a.trace_T) {
             for (int q = 0; q < p; ++q) a.tr_thprop[sg * p + q] = s_thp[q];
@@ -676,7 +697,7 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
   __syncthreads();
   if (tid == 0) {
     atomicAdd(reinterpret_cast<unsigned long long*>(&a.chain->member_acc), static_cast<unsigned long long>(s_macc));
-    if (lb == 0) {
+    if (lb == 0 && a.shard_out == nullptr) {  // (a shard's theta side moves in shard_decide_kernel)
       for (int q = 0; q < p; ++q) a.chain->theta[q] = s_theta[q];
       for (int q = 0; q < p * p; ++q) a.chain->S_theta[q] = s_Sth[q];
       for (int q = 0; q < p; ++q) a.chain->pend_U[q] = s_pendU[q];
@@ -721,6 +742,12 @@ __global__ void __launch_bounds__(256, (kD1 && F32) ? 4 : 2) batch_kernel(const 
   const int b0 = b0s[pop], lb = blockIdx.x - b0, nb = nbs[pop];
   BatchProg* prog = progs + pop;
   if (lb >= nb || prog->off >= prog->total) return;  // spare block, or the population has finished
+  if (s_args.shard_out != nullptr) {  // a shard pass after a failed decision does nothing
+    __shared__ int s_failed;
+    if (threadIdx.x == 0) s_failed = ld_volatile_i32(s_args.err);
+    __syncthreads();
+    if (s_failed) return;
+  }
   if (s_args.model == CUDAHM_NN1)
     run_population<NN1, F32>(s_args, prog, b0, lb, nb, chunk, R, s_dyn, s_theta, s_thp, s_Sth, s_red);
   else if (s_args.model == CUDAHM_LF)
@@ -771,19 +798,10 @@ __global__ void data32_mvn3_kernel(long long n, const double* y, const double* a
   }
 }
 
-// Theta tables of every population for the next chunk: sweep k0 + 1 + s, s < ns.
-__global__ void batch_tables_kernel(const SweepArgs* __restrict__ pops, const BatchProg* __restrict__ progs, int npop,
-                                    int chunk) {
-  const int pop = blockIdx.y;
-  if (pop >= npop) return;
-  const SweepArgs& a = pops[pop];
-  const BatchProg& pr = progs[pop];
-  const long long left = pr.total - pr.off;
-  const long long ns = left < chunk ? left : chunk;
-  const long long s = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (s >= ns) return;
-  const long long k0 = a.chain->sweeps;
-  const uint32_t k = static_cast<uint32_t>(k0 + s + 1);
+// The theta draws of sweep k into slot s of a population's tables: p normals (Philox stream 1,
+// member word 0, sweep k; block j gives normals 2j, 2j+1), the accept uniform (first uniform of
+// block ceil(p/2)) and its logarithm, and eta = (k+1)^-gamma.
+__device__ void theta_draws(const SweepArgs& a, uint32_t k, long long s) {
   const int p = a.p;
   const int nblk = (p + 1) / 2;
   double* U = const_cast<double*>(a.tab_U);
@@ -801,6 +819,91 @@ __global__ void batch_tables_kernel(const SweepArgs* __restrict__ pops, const Ba
   const_cast<double*>(a.tab_u)[s] = u;
   const_cast<double*>(a.tab_lnu)[s] = log(u);
   const_cast<double*>(a.tab_eta)[s] = pow(static_cast<double>(k) + 1.0, -a.gamma);
+}
+
+// Theta tables of every population for the next chunk: sweep k0 + 1 + s, s < ns.
+__global__ void batch_tables_kernel(const SweepArgs* __restrict__ pops, const BatchProg* __restrict__ progs, int npop,
+                                    int chunk) {
+  const int pop = blockIdx.y;
+  if (pop >= npop) return;
+  const SweepArgs& a = pops[pop];
+  const BatchProg& pr = progs[pop];
+  const long long left = pr.total - pr.off;
+  const long long ns = left < chunk ? left : chunk;
+  const long long s = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  theta_draws(a, static_cast<uint32_t>(a.chain->sweeps + s + 1), s);
+}
+
+// The theta step of one sweep of a split population (one block, thread 0), after every shard's
+// pass: theta' from the same tables and S_theta as the passes used, log alpha from the summed
+// exchange words (total, kShardWords words) with the population's member count n_pop, the
+// decision, the RAM update of S_theta pending from the previous sweep and this sweep's (as
+// run_population takes them), the kept row, and the tables of the next sweep into slot 0. Every
+// shard runs it on the same words and chain state, so every shard takes the same decision. The
+// words must come from all `parts` shards with n_pop members in all; otherwise, or after a NaN,
+// the run's error word is set and the chain stays as it was.
+template <class M>
+__global__ void shard_decide_kernel(const SweepArgs* __restrict__ pop, BatchProg* __restrict__ prog,
+                                    const unsigned long long* __restrict__ total, long long n_pop, int parts) {
+  __shared__ double s_math[kMathWords];
+  const SweepArgs& a = *pop;
+  for (int q = threadIdx.x; q < kMathWords; q += blockDim.x) s_math[q] = a.math_tab[q];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  if (ld_volatile_i32(a.err) != 0 || prog->off >= prog->total) return;
+  using TC = typename M::TC;
+  const int p = a.p;
+  ChainState& ch = *a.chain;
+  double theta[kMaxP], thp[kMaxP], Sth[kMaxP * kMaxP];
+  for (int q = 0; q < p; ++q) theta[q] = ch.theta[q];
+  for (int q = 0; q < p * p; ++q) Sth[q] = ch.S_theta[q];
+  const double lpri = M::logprior(theta, a.mc, s_math);
+  const double logeb = M::kRule ? log_etabar(ch.etabar, s_math) : 0.0;
+  double lpri_new;
+  TC tcp;
+  propose_theta<M>(a, 0, p, theta, Sth, thp, lpri_new, tcp, s_math);
+  const bool prior_ok = (lpri_new != -INFINITY);
+  if (total[14] != static_cast<unsigned long long>(n_pop) || total[15] != static_cast<unsigned long long>(parts)) {
+    atomicCAS(a.err, 0, CUDAHM_ESTATE);  // words missing, doubled, or from another split
+    return;
+  }
+  Xacc D, E;
+  acc_to_xacc(total, D);
+  acc_to_xacc(total + 6, E);
+  const unsigned int f[4] = {static_cast<unsigned int>(total[12]), static_cast<unsigned int>(total[12] >> 32),
+                             static_cast<unsigned int>(total[13]), static_cast<unsigned int>(total[13] >> 32)};
+  if (f[1] != 0u) {
+    atomicCAS(a.err, 0, CUDAHM_ENUMERIC);
+    return;
+  }
+  double logalpha, Drec, eb_new, logeb_new;
+  theta_logalpha<M>(D, E, f, prior_ok, static_cast<double>(n_pop), theta, thp, lpri, lpri_new, logeb, s_math,
+                    logalpha, Drec, eb_new, logeb_new);
+  const bool acc = __ldg(a.tab_lnu) < logalpha;
+  if (acc) {
+    for (int q = 0; q < p; ++q) ch.theta[q] = thp[q];
+    if (M::kRule) ch.etabar = eb_new;
+    ch.theta_acc += 1;
+  }
+  if (a.adapt_theta) {  // the previous step's RAM update; this step's waits one sweep
+    if (ch.pend_eta > 0.0) {
+      ram_update_theta(p, Sth, ch.pend_U, ch.pend_alpha, a.astar_theta, ch.pend_eta);
+      for (int q = 0; q < p * p; ++q) ch.S_theta[q] = Sth[q];
+    }
+    ch.pend_alpha = (logalpha >= 0.0) ? 1.0 : exp_tab(logalpha, s_math);
+    for (int q = 0; q < p; ++q) ch.pend_U[q] = __ldg(a.tab_U + q);
+    ch.pend_eta = __ldg(a.tab_eta);
+  }
+  const long long post = prog->off - prog->n_burn;
+  if (post >= 0 && prog->thin > 0 && ((post + 1) % prog->thin) == 0) {
+    if (a.rows)
+      for (int q = 0; q < p; ++q) a.rows[prog->rows * p + q] = acc ? thp[q] : theta[q];
+    prog->rows += 1;
+  }
+  ch.sweeps += 1;
+  prog->off += 1;
+  if (prog->off < prog->total) theta_draws(a, static_cast<uint32_t>(ch.sweeps + 1), 0);
 }
 
 }  // namespace
@@ -868,6 +971,19 @@ cudaError_t launch_batch(bool f32, bool d1, const SweepArgs* pops, BatchProg* pr
                   &chunk, &seg_slots};
   const void* fn = batch_fn(f32, d1);
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem_bytes, st);
+}
+
+cudaError_t launch_shard_decide(int model, const SweepArgs* pop, BatchProg* prog, const unsigned long long* total,
+                                long long n_pop, int parts, cudaStream_t st) {
+  switch (model) {
+    case CUDAHM_NN1: shard_decide_kernel<NN1><<<1, 32, 0, st>>>(pop, prog, total, n_pop, parts); break;
+    case CUDAHM_LF: shard_decide_kernel<LF><<<1, 32, 0, st>>>(pop, prog, total, n_pop, parts); break;
+    case CUDAHM_BB1: shard_decide_kernel<BB1><<<1, 32, 0, st>>>(pop, prog, total, n_pop, parts); break;
+    case CUDAHM_NN3: shard_decide_kernel<NN3><<<1, 32, 0, st>>>(pop, prog, total, n_pop, parts); break;
+    case CUDAHM_MVN3: shard_decide_kernel<MVN3><<<1, 32, 0, st>>>(pop, prog, total, n_pop, parts); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_batch_tables(const SweepArgs* pops, const BatchProg* progs, int npop, int chunk, cudaStream_t st) {

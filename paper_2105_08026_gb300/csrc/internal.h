@@ -122,9 +122,22 @@ struct SweepArgs {
   double h_ua, h_ub;  // table range in ln L; H = h_lo below it, h_hi above it
   double h_lo, h_hi;
   int h_ncell;
+  // shard of a population split across devices: the population index of member 0 (the member
+  // word of every member draw is moff + i), the rule's outer nodes [rule_j0, rule_j1) this shard
+  // adds (rule_j1 = 0: all n_L), and (non-null: the streaming kernel's shard pass) where the
+  // pass writes the shard's exchange words
+  unsigned int moff;
+  int rule_j0, rule_j1;
+  unsigned long long* shard_out;
 };
 
 constexpr int kPubWords = 32;
+
+// Exchange words of one shard's sweep (cudahm_shard_pass): the theta' partial D and the
+// selection-rule partial E as six 32-bit limbs each (in u64 words, so that the words of all
+// shards add as integers), the flag counts packed two to a word, the shard's member count and 1
+// (the number of shards that contributed).
+constexpr int kShardWords = 16;
 
 // FP32 form, d = 1: member arrays are padded to a multiple of kTilePad members, and the
 // streaming kernel stages member tiles of kTileMembers (a multiple of 4: 16-byte aligned bulk
@@ -163,6 +176,10 @@ cudaError_t batch_occupancy(bool f32, bool d1, int block, int smem_bytes, int* b
 cudaError_t launch_batch(bool f32, bool d1, const SweepArgs* pops, BatchProg* progs, const int* b0s, const int* nbs,
                          int npop, int chunk, int seg_slots, int grid, int block, int smem_bytes, cudaStream_t st);
 cudaError_t launch_batch_tables(const SweepArgs* pops, const BatchProg* progs, int npop, int chunk, cudaStream_t st);
+// The theta decision of one sweep of a split population from the summed exchange words of all
+// its shards (one block); parts: the number of shards, n_pop: the population's member count.
+cudaError_t launch_shard_decide(int model, const SweepArgs* pop, BatchProg* prog, const unsigned long long* total,
+                                long long n_pop, int parts, cudaStream_t st);
 cudaError_t launch_data32(int model, long long n, long long n32, const double* y, const double* aux,
                           const ModelConsts& mc, float* d32, cudaStream_t st);
 cudaError_t launch_chi_to32(long long n, long long n32, const double* chi, float* chi32, cudaStream_t st);

@@ -192,6 +192,27 @@ struct cudahm {
   double last_run_ms = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int* host_err = nullptr;  // pinned
+  // pinned copy of the last run's kept theta rows, filled in the same synchronisation as the
+  // run's error word (rows_host_n rows; capacity rows_host_cap)
+  double* rows_host = nullptr;
+  long long rows_host_cap = 0, rows_host_n = 0;
+  // shard of a population split across devices (cudahm_shard_config): population index of
+  // member 0, population size, this shard's part of the selection rule
+  bool shard_set = false;
+  long long shard_moff = 0, shard_npop = 0;
+  int shard_part = 0, shard_parts = 1;
+  // the sharded run in progress (cudahm_shard_begin .. cudahm_shard_end): the pass's arguments
+  // and progress on the device, its launch shape, and the calls made so far
+  bool shard_active = false;
+  long long shard_total = 0, shard_passes = 0, shard_decides = 0;
+  SweepArgs* sh_pop = nullptr;
+  BatchProg* sh_prog = nullptr;
+  int* sh_b0 = nullptr;
+  int* sh_nb = nullptr;
+  unsigned long long* sh_partials = nullptr;
+  unsigned int* sh_bar = nullptr;
+  unsigned long long* sh_out_last = nullptr;
+  int sh_grid = 0, sh_block = 0, sh_smem = 0;
 
   void* dalloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -218,6 +239,7 @@ struct cudahm {
       else cudaFree(ptr);
     }
     if (host_err) cudaFreeHost(host_err);
+    if (rows_host) cudaFreeHost(rows_host);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     if (own_stream && stream) cudaStreamDestroy(stream);
@@ -605,6 +627,7 @@ int reset_chain(cudahm* h) {
   CU(cudaStreamSynchronize(h->stream));
   h->sweeps = 0;
   h->rows_last = 0;
+  h->rows_host_n = 0;
   h->etabar_valid = false;
   h->marg_valid = false;
   return CUDAHM_OK;
@@ -912,6 +935,7 @@ int cudahm_set_chi(cudahm_t h, const double* chi_host, int64_t n) {
 int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
   if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
   if (!h->data_set) return fail(CUDAHM_ESTATE, "run before set_data");
+  if (h->shard_active) return fail(CUDAHM_ESTATE, "a sharded run is in progress (cudahm_shard_end first)");
   if (h->K == 0 && !h->cfg.marginal) {  // streaming form: a batch of one population
     cudahm_t one[1] = {h};
     CU(cudaEventRecord(h->ev0, h->stream));
@@ -990,6 +1014,25 @@ int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
     h->sweeps += ns;
     off += ns;
   }
+  // the kept rows come back with the error word (one synchronisation for both), through a pinned
+  // buffer that cudahm_get_samples reads; a run keeping more rows than it holds grows it (pinned
+  // host memory, not device memory). The run's device time (ev0 .. ev1) includes that copy.
+  h->rows_host_n = 0;
+  if (rows_done > 0 && rows_done * h->p <= (1ll << 20)) {
+    if (rows_done > h->rows_host_cap) {
+      if (h->rows_host) cudaFreeHost(h->rows_host);
+      h->rows_host = nullptr;
+      h->rows_host_cap = 0;
+      if (cudaHostAlloc(reinterpret_cast<void**>(&h->rows_host), sizeof(double) * rows_done * h->p,
+                        cudaHostAllocDefault) == cudaSuccess)
+        h->rows_host_cap = rows_done;
+    }
+    if (h->rows_host && rows_done <= h->rows_host_cap) {
+      CU(cudaMemcpyAsync(h->rows_host, h->rows, sizeof(double) * rows_done * h->p, cudaMemcpyDeviceToHost,
+                         h->stream));
+      h->rows_host_n = rows_done;
+    }
+  }
   CU(cudaEventRecord(h->ev1, h->stream));
   int code = 0;
   TRY(read_err(h, &code));
@@ -1002,6 +1045,7 @@ int cudahm_run(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
     CU(cudaMemcpy(&cs, h->chain, sizeof(cs), cudaMemcpyDeviceToHost));
     h->sweeps = cs.sweeps;
     h->rows_last = 0;
+    h->rows_host_n = 0;
     if (code == CUDAHM_ETIMEOUT) return fail(code, "a grid barrier wait exceeded its bound; run stopped");
     if (code == CUDAHM_ENUMERIC) return fail(code, "NaN in a log-density; run stopped");
     return fail(code, "device error %d", code);
@@ -1015,6 +1059,11 @@ int cudahm_get_samples(cudahm_t h, double* theta_host, int64_t cap_rows, int64_t
   if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
   const long long r = std::min<long long>(cap_rows, h->rows_last);
   if (rows_out) *rows_out = h->rows_last;
+  if (r > 0 && h->rows_host_n == h->rows_last) {  // already on the host
+    if (!theta_host) return fail(CUDAHM_EINVAL, "theta_host is NULL");
+    std::memcpy(theta_host, h->rows_host, sizeof(double) * r * h->p);
+    return CUDAHM_OK;
+  }
   if (r > 0) {
     if (!theta_host) return fail(CUDAHM_EINVAL, "theta_host is NULL");
     CU(cudaSetDevice(h->cfg.device));
@@ -1293,10 +1342,178 @@ int cudahm_restore(cudahm_t h, const void* buf, size_t size) {
   CU(cudaStreamSynchronize(h->stream));
   h->sweeps = cs.sweeps;
   h->rows_last = 0;
+  h->rows_host_n = 0;
   // etabar(theta) is recomputed by this handle's own rule before the next run (the same bits as
   // the stored value when the rule is the same, which the configuration hash checks)
   h->etabar_valid = false;
   h->marg_valid = false;  // log p_i is recomputed at the restored theta before the next run
+  return CUDAHM_OK;
+}
+
+// ------------------------------------------------------------------ shards --
+// A population split across devices (Sec. 6: larger N than one device holds): each shard is a
+// handle holding a contiguous range of the population's members. Every shard draws the same
+// theta' (same seed, same theta tables); its pass steps its members, whose draws carry their
+// population index, and reduces its part of the theta' sum and of the selection rule into
+// exchange words; the caller adds the words of all shards (an all-reduce of 16 integers); every
+// shard then takes the same decision from the sum. The chain is the unsplit one, bit for bit.
+int cudahm_shard_config(cudahm_t h, int64_t member_offset, int64_t population_n, int32_t part, int32_t parts) {
+  if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
+  if (h->shard_active) return fail(CUDAHM_ESTATE, "a sharded run is in progress");
+  if (h->cfg.marginal) return fail(CUDAHM_EUNSUPPORTED, "the marginal form is not split into shards");
+  if (h->cfg.trace_sweeps > 0 || h->cfg.keep_chi_moments)
+    return fail(CUDAHM_EUNSUPPORTED, "a shard records neither a lockstep trace nor latent moments");
+  if (parts < 1 || part < 0 || part >= parts) return fail(CUDAHM_EINVAL, "need 0 <= part < parts");
+  if (member_offset < 0 || population_n < 1 || member_offset + h->n > population_n)
+    return fail(CUDAHM_EINVAL, "members [offset, offset + n) must lie in [0, population_n)");
+  if (population_n > 0xFFFFFFFFll) return fail(CUDAHM_EINVAL, "population_n must fit the 32-bit member word");
+  h->shard_set = true;
+  h->shard_moff = member_offset;
+  h->shard_npop = population_n;
+  h->shard_part = part;
+  h->shard_parts = parts;
+  return CUDAHM_OK;
+}
+
+int cudahm_shard_begin(cudahm_t h, int64_t n_burn, int64_t n_iter, int64_t thin) {
+  if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
+  if (!h->shard_set) return fail(CUDAHM_ESTATE, "cudahm_shard_config first");
+  if (!h->data_set) return fail(CUDAHM_ESTATE, "shard run before set_data");
+  if (h->shard_active) return fail(CUDAHM_ESTATE, "a sharded run is already in progress");
+  if (n_burn < 0 || n_iter < 0 || n_burn + n_iter < 1) return fail(CUDAHM_EINVAL, "bad sweep counts");
+  if (n_iter > 0 && thin < 1) return fail(CUDAHM_EINVAL, "thin must be >= 1");
+  const long long total = n_burn + n_iter;
+  if (h->sweeps + total >= (1ll << 32) - 2) return fail(CUDAHM_EINVAL, "sweep counter would exceed 2^32");
+  CU(cudaSetDevice(h->cfg.device));
+  cudaStream_t st = h->stream;
+  const long long nrows = (n_iter > 0) ? n_iter / thin : 0;
+  if (nrows > h->rows_cap) {
+    h->dfree(h->rows);
+    h->rows = nullptr;
+    TRY(alloc_into(h, &h->rows, static_cast<size_t>(nrows) * h->p));
+    h->rows_cap = nrows;
+  }
+  if (has_rule(h->cfg.model) && !h->etabar_valid) {  // the whole rule at theta, as an unsplit run
+    char* base = reinterpret_cast<char*>(h->chain);
+    TRY(compute_etabar_into(h, reinterpret_cast<const double*>(base + offsetof(ChainState, theta)),
+                            reinterpret_cast<double*>(base + offsetof(ChainState, etabar))));
+    h->etabar_valid = true;
+  }
+  if (!h->sh_pop) {
+    TRY(alloc_into(h, &h->sh_pop, 1));
+    TRY(alloc_into(h, &h->sh_prog, 1));
+    TRY(alloc_into(h, &h->sh_b0, 1));
+    TRY(alloc_into(h, &h->sh_nb, 1));
+    TRY(alloc_into(h, &h->sh_bar, 1));
+  }
+  // launch shape: 128-thread blocks, as many as the occupancy allows and the members can use
+  const bool f32 = h->cfg.precision == CUDAHM_FP32, d1 = h->d == 1;
+  const int blk = 128;
+  const int smem = static_cast<int>(batch_smem_bytes(f32, d1, blk));
+  int bps = 0;
+  CU(batch_occupancy(f32, d1, blk, smem, &bps));
+  if (bps < 1) return fail(CUDAHM_EUNSUPPORTED, "the streaming kernel does not fit on this device");
+  long long cap = (h->n + 31) / 32 + (has_rule(h->cfg.model) ? 8 : 0);
+  const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>(cap, static_cast<long long>(bps) * h->sms)));
+  if (grid > h->sh_grid || !h->sh_partials) {
+    h->dfree(h->sh_partials);
+    h->sh_partials = nullptr;
+    TRY(alloc_into(h, &h->sh_partials, static_cast<size_t>(2) * grid * kPartWords));
+  }
+  h->sh_grid = grid;
+  h->sh_block = blk;
+  h->sh_smem = smem;
+
+  SweepArgs a = base_args(h);
+  a.partials = h->sh_partials;
+  a.bar = h->sh_bar;
+  a.rows = h->rows;
+  a.thin = thin;
+  a.trace_T = 0;
+  a.skip_cta = -1;
+  a.moff = static_cast<unsigned int>(h->shard_moff);
+  if (has_rule(h->cfg.model)) {
+    const long long nL = rule_nL(h->cfg);
+    a.rule_j0 = static_cast<int>(nL * h->shard_part / h->shard_parts);
+    a.rule_j1 = static_cast<int>(nL * (h->shard_part + 1) / h->shard_parts);
+    if (a.rule_j1 == 0) a.rule_j0 = a.rule_j1 = -1;  // no outer node (rule_j1 = 0 would mean all)
+  }
+  a.shard_out = nullptr;
+  const BatchProg prog{total, 0, n_burn, thin, 0, 0};
+  const int zero = 0;
+  CU(cudaMemcpyAsync(h->sh_pop, &a, sizeof(a), cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(h->sh_prog, &prog, sizeof(prog), cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(h->sh_b0, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(h->sh_nb, &grid, sizeof(int), cudaMemcpyHostToDevice, st));
+  CU(cudaMemsetAsync(h->sh_bar, 0, sizeof(unsigned int), st));
+  CU(cudaMemsetAsync(h->err, 0, sizeof(int), st));
+  CU(launch_batch_tables(h->sh_pop, h->sh_prog, 1, 1, st));  // theta tables of the first sweep
+  CU(cudaStreamSynchronize(st));
+  h->sh_out_last = nullptr;
+  h->shard_total = total;
+  h->shard_passes = 0;
+  h->shard_decides = 0;
+  h->rows_last = 0;
+  h->rows_host_n = 0;
+  h->shard_active = true;
+  return CUDAHM_OK;
+}
+
+int cudahm_shard_pass(cudahm_t h, uint64_t* words_dev) {
+  if (!h || !words_dev) return fail(CUDAHM_EINVAL, "NULL argument");
+  if (!h->shard_active) return fail(CUDAHM_ESTATE, "cudahm_shard_begin first");
+  if (h->shard_passes != h->shard_decides) return fail(CUDAHM_ESTATE, "the previous pass has not been decided");
+  if (h->shard_passes >= h->shard_total) return fail(CUDAHM_ESTATE, "every sweep of the run has been made");
+  if (reinterpret_cast<uintptr_t>(words_dev) % 8 != 0) return fail(CUDAHM_EINVAL, "words_dev must be 8-byte aligned");
+  cudaStream_t st = h->stream;
+  unsigned long long* out = reinterpret_cast<unsigned long long*>(words_dev);
+  if (out != h->sh_out_last) {  // the pass's arguments name the caller's buffer
+    CU(cudaMemcpyAsync(reinterpret_cast<char*>(h->sh_pop) + offsetof(SweepArgs, shard_out), &out, sizeof(out),
+                       cudaMemcpyHostToDevice, st));
+    h->sh_out_last = out;
+  }
+  const bool f32 = h->cfg.precision == CUDAHM_FP32;
+  CU(launch_batch(f32, h->d == 1, h->sh_pop, h->sh_prog, h->sh_b0, h->sh_nb, 1, 1, 128, h->sh_grid, h->sh_block,
+                  h->sh_smem, st));
+  h->shard_passes++;
+  return CUDAHM_OK;
+}
+
+int cudahm_shard_decide(cudahm_t h, const uint64_t* total_dev) {
+  if (!h || !total_dev) return fail(CUDAHM_EINVAL, "NULL argument");
+  if (!h->shard_active) return fail(CUDAHM_ESTATE, "cudahm_shard_begin first");
+  if (h->shard_decides + 1 != h->shard_passes) return fail(CUDAHM_ESTATE, "decide follows a pass");
+  if (reinterpret_cast<uintptr_t>(total_dev) % 8 != 0) return fail(CUDAHM_EINVAL, "total_dev must be 8-byte aligned");
+  CU(launch_shard_decide(h->cfg.model, h->sh_pop, h->sh_prog, reinterpret_cast<const unsigned long long*>(total_dev),
+                         h->shard_npop, h->shard_parts, h->stream));
+  h->shard_decides++;
+  return CUDAHM_OK;
+}
+
+int cudahm_shard_end(cudahm_t h, int64_t* rows_out) {
+  if (!h) return fail(CUDAHM_EINVAL, "handle is NULL");
+  if (!h->shard_active) return fail(CUDAHM_ESTATE, "no sharded run in progress");
+  h->shard_active = false;
+  int code = 0;
+  TRY(read_err(h, &code));
+  BatchProg prog;
+  ChainState cs;
+  CU(cudaMemcpy(&prog, h->sh_prog, sizeof(prog), cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(&cs, h->chain, sizeof(cs), cudaMemcpyDeviceToHost));
+  h->sweeps = cs.sweeps;
+  h->rows_host_n = 0;
+  if (code != 0) {
+    h->rows_last = 0;
+    if (code == CUDAHM_ESTATE)
+      return fail(code, "exchange words did not come from every shard of the population once; run stopped");
+    if (code == CUDAHM_ETIMEOUT) return fail(code, "a bounded device-side wait expired; run stopped");
+    if (code == CUDAHM_ENUMERIC) return fail(code, "NaN in a log-density; run stopped");
+    return fail(code, "device error %d", code);
+  }
+  h->rows_last = prog.rows;
+  if (rows_out) *rows_out = prog.rows;
+  if (h->shard_passes != h->shard_decides)
+    return fail(CUDAHM_ESTATE, "run ended after a pass without its decision: the latents are one sweep past theta");
   return CUDAHM_OK;
 }
 
@@ -1345,6 +1562,7 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
     cudahm* h = hs[q];
     if (!h) return fail(CUDAHM_EINVAL, "handle %d is NULL", q);
     if (!h->data_set) return fail(CUDAHM_ESTATE, "handle %d has no data", q);
+    if (h->shard_active) return fail(CUDAHM_ESTATE, "handle %d is in a sharded run", q);
     if (h->cfg.marginal) return fail(CUDAHM_EUNSUPPORTED, "handle %d uses the marginal form, which runs alone", q);
     if (h->cfg.device != h0->cfg.device) return fail(CUDAHM_EINVAL, "handles are on different devices");
     if (h->cfg.precision != h0->cfg.precision) return fail(CUDAHM_EINVAL, "handles mix precisions");
@@ -1662,6 +1880,7 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
       ChainState cs;
       if (cudaMemcpy(&cs, hs[q]->chain, sizeof(cs), cudaMemcpyDeviceToHost) == cudaSuccess) hs[q]->sweeps = cs.sweeps;
       hs[q]->rows_last = 0;
+      hs[q]->rows_host_n = 0;
     }
     return rc;
   }
@@ -1670,6 +1889,7 @@ int cudahm_batch_run(cudahm_t* hs, int32_t k, int64_t n_burn, int64_t n_iter, in
     cudahm* h = hs[q];
     h->sweeps += total;
     h->rows_last = nrows;
+    h->rows_host_n = 0;  // the batched run leaves its rows on the device
     h->trace_T_last = std::min<long long>(h->cfg.trace_sweeps, total);
     h->last_run_ms = run_ms_total;
   }

@@ -288,12 +288,10 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   // FP32 bulk form: the model's binary32 member data, M::kData32 arrays of mpb floats, in the
   // region that holds y, aux and the spare normals in the FP64 form (3 mpb doubles = 6 mpb floats)
   float* s_d32 = reinterpret_cast<float*>(s_y);
-  if (F32) {
+  if (F32) {  // the handle's prepared binary32 data (rows of stride n32), as the streaming kernel reads them
     for (unsigned int q = tid; q < nb1 - nb0; q += blockDim.x) {
-      float d[M::kData32];
-      M::data32(a.y[nb0 + q], a.aux[nb0 + q], a.mc, d);
 #pragma unroll
-      for (int c = 0; c < M::kData32; ++c) s_d32[c * a.mpb + q] = d[c];
+      for (int c = 0; c < M::kData32; ++c) s_d32[c * a.mpb + q] = __ldg(a.d32 + c * a.n32 + nb0 + q);
     }
     __syncthreads();
   }
@@ -581,26 +579,9 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
           atomicCAS(a.err, 0, CUDAHM_ENUMERIC);
           s_stop = 1;
         } else {
-          double logalpha, Drec, eb_new = 0.0, logeb_new = 0.0;
-          if (!prior_ok) {
-            logalpha = -INFINITY;
-            Drec = 0.0;
-          } else if (f[0] != 0u) {  // a member off the proposal's support (or d <= -2^94)
-            logalpha = -INFINITY;
-            Drec = -INFINITY;
-          } else if (f[2] != 0u) {  // only huge positive differences remain
-            logalpha = INFINITY;
-            Drec = INFINITY;
-          } else {
-            Drec = xacc_to_double(D);
-            const double nn = static_cast<double>(a.n);
-            logalpha = Drec + nn * (M::cterm(s_thp) - M::cterm(s_theta)) + s_lpri_new - s_lpri;
-            if (is_lf) {
-              eb_new = xacc_to_double(E);
-              logeb_new = log_etabar(eb_new, s_math);
-              logalpha -= nn * (logeb_new - s_logeb);
-            }
-          }
+          double logalpha, Drec, eb_new, logeb_new;
+          theta_logalpha<M>(D, E, f, prior_ok, static_cast<double>(a.n), s_theta, s_thp, s_lpri, s_lpri_new, s_logeb,
+                            s_math, logalpha, Drec, eb_new, logeb_new);
           const double lnut = __ldg(a.tab_lnu + s);
           const bool acc = lnut < logalpha;
           if (blockIdx.x == 0 && sg < a.trace_T) {

@@ -675,7 +675,10 @@ __device__ __forceinline__ void etabar_terms(const ThetaC& tc, const SweepArgs& 
   const double lo = bb1 ? tc.a4 + a.mc.ln_lower : tc.a3;
   const double hi = tc.a1 + a.mc.ln_upper;
   const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
-  for (int j = b + B * static_cast<int>(threadIdx.x); j < a.nL; j += B * static_cast<int>(blockDim.x)) {
+  // outer nodes [rule_j0, rule_j1) (rule_j1 = 0: all n_L); a shard of a split population covers
+  // its own range, so every node is counted once over all shards
+  const int j1 = a.rule_j1 ? a.rule_j1 : a.nL;
+  for (int j = a.rule_j0 + b + B * static_cast<int>(threadIdx.x); j < j1; j += B * static_cast<int>(blockDim.x)) {
     const double tt = fma(half, __ldg(a.xL + j), mid);
     double G;
     if constexpr (bb1) {
@@ -695,9 +698,14 @@ __device__ __forceinline__ void etabar_terms(const ThetaC& tc, const SweepArgs& 
 // (0 at Delta = -inf), accepted iff u < alpha. Binary64: every Delta with its sign bit clear
 // accepts; otherwise u and alpha are both >= +0, so their bit patterns order as their values.
 // Binary32 (bulk form): the same rule with the special-function unit's exponential.
+// Below Delta = -700, alpha = e^Delta < 1e-304 is taken as 0: every accept uniform is at least
+// 2^-53, so the decision is the same, and alpha - alpha_* rounds to -alpha_* either way, so the
+// RAM update is too; this keeps the exponential on its table path (the library routine that
+// exp_tab falls back to there is several times longer, and early in a chain, before the RAM
+// factors adapt, most bright members propose that far out).
 __device__ __forceinline__ bool mh_accept(double delta, double u, const double* s_math, double& alpha) {
   const bool dneg = dsign(delta);  // -inf and -0 included
-  alpha = dneg ? exp_tab(delta, s_math) : 1.0;
+  alpha = !dneg ? 1.0 : (dgt(delta, -700.0) ? exp_tab(delta, s_math) : 0.0);
   return !dneg || (__double_as_longlong(u) < __double_as_longlong(alpha));
 }
 
@@ -998,6 +1006,39 @@ __device__ __forceinline__ void propose_theta(const SweepArgs& a, long long s, i
   }
   lpri_new = M::logprior(thp, a.mc, T);
   tcp = M::consts(thp, a.mc, T);
+}
+
+// The theta step's log acceptance ratio (Sec. 2.2, with the selection term of Eq. 12 for LF and
+// BB1) from a sweep's exact totals: D = sum_i [log f(chi_i; theta') - log f(chi_i; theta)], E =
+// etabar(theta'), and the flag counts f (f[0]: some d_i is -inf or <= -2^94, which rejects;
+// f[2]: some d_i >= 2^94, which accepts). log alpha = D + nn (c(theta') - c(theta)) + ln pi(theta')
+// - ln pi(theta) - nn (ln etabar(theta') - ln etabar(theta)), nn the population's member count.
+// Drec is D as binary64 (for the trace), eb_new and logeb_new the new selection integral.
+template <class M>
+__device__ __forceinline__ void theta_logalpha(const Xacc& D, const Xacc& E, const unsigned int f[4], bool prior_ok,
+                                               double nn, const double* theta, const double* thp, double lpri,
+                                               double lpri_new, double logeb, const double* T, double& logalpha,
+                                               double& Drec, double& eb_new, double& logeb_new) {
+  eb_new = 0.0;
+  logeb_new = 0.0;
+  if (!prior_ok) {
+    logalpha = -INFINITY;
+    Drec = 0.0;
+  } else if (f[0] != 0u) {  // a member off the proposal's support (or d <= -2^94)
+    logalpha = -INFINITY;
+    Drec = -INFINITY;
+  } else if (f[2] != 0u) {  // only huge positive differences remain
+    logalpha = INFINITY;
+    Drec = INFINITY;
+  } else {
+    Drec = xacc_to_double(D);
+    logalpha = Drec + nn * (M::cterm(thp) - M::cterm(theta)) + lpri_new - lpri;
+    if constexpr (M::kRule) {
+      eb_new = xacc_to_double(E);
+      logeb_new = log_etabar(eb_new, T);
+      logalpha -= nn * (logeb_new - logeb);
+    }
+  }
 }
 
 }  // namespace chm

@@ -26,6 +26,7 @@ MAX_P = 9
 MAX_CONSTS = 8
 MODEL_D = {NN1: 1, MVN3: 3, LF: 1, BB1: 1, NN3: 3}
 MODEL_P = {NN1: 2, MVN3: 9, LF: 3, BB1: 3, NN3: 3}
+SHARD_WORDS = 16  # exchange words of one shard's sweep (CUDAHM_SHARD_WORDS)
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -72,7 +73,7 @@ class CudahmStats(ctypes.Structure):
         ("grid_blocks", ctypes.c_int32),
         ("block_threads", ctypes.c_int32),
         ("objects_per_thread", ctypes.c_int32),
-        ("grid_blocks", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -103,7 +104,8 @@ EXPORTED = [
     "cudahm_lf_etabar_noalloc", "cudahm_batch_run", "cudahm_server_create", "cudahm_server_submit",
     "cudahm_server_poll", "cudahm_server_wait", "cudahm_server_result", "cudahm_server_stats",
     "cudahm_server_destroy", "cudahm_ess", "cudahm_eval_marginal", "cudahm_get_chi_moments",
-    "cudahm_twostate_run",
+    "cudahm_twostate_run", "cudahm_shard_config", "cudahm_shard_begin", "cudahm_shard_pass",
+    "cudahm_shard_decide", "cudahm_shard_end",
 ]
 
 
@@ -153,6 +155,11 @@ def lib():
     L.cudahm_eval_marginal.argtypes = [vp, _dp, _dp]
     L.cudahm_get_chi_moments.argtypes = [vp, _dp, _dp, ctypes.POINTER(i64)]
     L.cudahm_twostate_run.argtypes = [ctypes.c_double, i32, i64, i64, ctypes.c_uint64, i32, ctypes.POINTER(i64)]
+    L.cudahm_shard_config.argtypes = [vp, i64, i64, i32, i32]
+    L.cudahm_shard_begin.argtypes = [vp, i64, i64, i64]
+    L.cudahm_shard_pass.argtypes = [vp, vp]
+    L.cudahm_shard_decide.argtypes = [vp, vp]
+    L.cudahm_shard_end.argtypes = [vp, ctypes.POINTER(i64)]
     for name in EXPORTED:
         if name not in ("cudahm_config_init", "cudahm_sizeof_config", "cudahm_sizeof_stats", "cudahm_last_error",
                         "cudahm_destroy"):
@@ -319,6 +326,28 @@ def batch_run(samplers, n_burn: int, n_iter: int, thin: int = 1, tune: CudahmTun
     cap = n_iter // thin if (n_iter > 0 and thin > 0) else 0
     rows = [cudahm_get_samples(s.h, s.p, cap) if cap > 0 else np.zeros((0, s.p)) for s in samplers]
     return rows, chosen
+
+
+def cudahm_shard_config(h, member_offset: int, population_n: int, part: int, parts: int):
+    _check(lib().cudahm_shard_config(h, member_offset, population_n, part, parts))
+
+
+def cudahm_shard_begin(h, n_burn: int, n_iter: int, thin: int = 1):
+    _check(lib().cudahm_shard_begin(h, n_burn, n_iter, thin))
+
+
+def cudahm_shard_pass(h, words_dev_ptr: int):
+    _check(lib().cudahm_shard_pass(h, ctypes.c_void_p(words_dev_ptr)))
+
+
+def cudahm_shard_decide(h, total_dev_ptr: int):
+    _check(lib().cudahm_shard_decide(h, ctypes.c_void_p(total_dev_ptr)))
+
+
+def cudahm_shard_end(h) -> int:
+    rows = ctypes.c_int64(0)
+    _check(lib().cudahm_shard_end(h, ctypes.byref(rows)))
+    return rows.value
 
 
 def make_config(model: int, n: int, *, theta_init, theta_prop_scale=None, model_consts=None, seed: int = 1,
@@ -550,3 +579,29 @@ class Sampler:
 
     def restore(self, blob: bytes):
         cudahm_restore(self.h, blob)
+
+    # one shard of a population split across devices (the handle holds members
+    # [member_offset, member_offset + n) of population_n)
+    def shard(self, member_offset: int, population_n: int, part: int, parts: int):
+        cudahm_shard_config(self.h, member_offset, population_n, part, parts)
+
+    def run_sharded(self, n_burn: int, n_iter: int, thin: int, words, exchange) -> np.ndarray:
+        """A sharded run: each sweep, this shard's pass writes its exchange words into `words`
+        (a device buffer of SHARD_WORDS 64-bit integers, e.g. a torch int64 tensor), then
+        ``exchange(words)`` must leave the sum over all shards in it (an all-reduce), then the
+        decision. Returns the kept theta rows (the same on every shard)."""
+        ptr = int(words.data_ptr())
+        cudahm_shard_begin(self.h, n_burn, n_iter, thin)
+        try:
+            for _ in range(n_burn + n_iter):
+                cudahm_shard_pass(self.h, ptr)
+                exchange(words)
+                cudahm_shard_decide(self.h, ptr)
+        except BaseException:
+            try:
+                cudahm_shard_end(self.h)  # ends the run; the first error is the one raised
+            except CudahmError:
+                pass
+            raise
+        rows = cudahm_shard_end(self.h)
+        return cudahm_get_samples(self.h, self.p, rows) if rows > 0 else np.zeros((0, self.p))

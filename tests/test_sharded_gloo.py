@@ -1,14 +1,13 @@
-"""The exchange step a multi-GPU split of one population would need (each rank updates its own
-members, then one exact all-reduce of their d_i = log f(chi_i;theta') - log f(chi_i;theta)
-before every rank takes the same theta decision), checked on the CPU with world_size 2 over
-gloo. The member steps come from the oracle (their draws are keyed by member and sweep, so a
-split leaves each member's step unchanged); the sum over members is exact (math.fsum, the
-correctly rounded sum, as the device's fixed-point sum is), so the split chain must equal the
+"""The exchange step a split of one population over several devices needs (each rank steps its
+own members, then one all-reduce of its exchange words, then every rank takes the same theta
+decision), checked on the CPU with world_size 2 over gloo. The member steps come from the oracle
+(their draws are keyed by the member's population index and the sweep, so a split leaves each
+member's step unchanged); each rank encodes its d_i = log f(chi_i;theta') - log f(chi_i;theta)
+into the same 16 words the device's shard pass writes (tests/shard_words.py: 32-bit limbs of an
+exact fixed-point sum, flag counts, member count), the ranks add the words with an int64
+all-reduce, and every rank decodes the total. The sum is exact, so the split chain equals the
 one-rank chain bit for bit: theta rows, latents and RAM factors. The one-rank driver is also
 checked against the oracle's own chain (its Neumaier sum differs only in rounding).
-
-This build runs one process per GPU with independent replicas (the pool gives one GPU per call),
-so the split is not on the device path; this test covers its logic.
 """
 import json
 import math
@@ -29,11 +28,12 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _driver(data, theta0, scale, consts, seed, rank, world, allgather):
+def _driver(data, theta0, scale, consts, seed, rank, world, allreduce):
     """NN1 chain with its members split over `world` ranks (theta step as the oracle's: RAM on
     theta with each step's update applied one sweep late, log alpha = D + N (c(theta') - c(theta))
-    + ln pi(theta') - ln pi(theta), c = -ln tau)."""
+    + ln pi(theta') - ln pi(theta), c = -ln tau); D from the all-reduced exchange words."""
     import oracle
+    import shard_words
     y, sig = data.y, data.sigma
     n = y.size
     i0, i1 = n * rank // world, n * (rank + 1) // world
@@ -53,11 +53,14 @@ def _driver(data, theta0, scale, consts, seed, rank, world, allgather):
         thp = theta + Sth @ U
         lp_new = prior(thp)
         d_loc, _ = oracle.member_pass(oracle.NN1, y, sig, consts, params, seed, k, i0, i1, theta, thp, chi, S)
-        d_all = allgather(d_loc)
-        if lp_new == -math.inf or np.isneginf(d_all).any():
+        D, _, f, members, shards = shard_words.decode(allreduce(shard_words.encode(d_loc)))
+        assert members == n and shards == world and f[1] == 0
+        if lp_new == -math.inf or f[0] > 0:
             logalpha = -math.inf
+        elif f[2] > 0:
+            logalpha = math.inf
         else:
-            logalpha = math.fsum(d_all.tolist()) + n * (-thp[1] + theta[1]) + lp_new - prior(theta)
+            logalpha = D + n * (-thp[1] + theta[1]) + lp_new - prior(theta)
         alpha = 1.0 if logalpha >= 0.0 else math.exp(logalpha)
         if math.log(ut) < logalpha:
             theta = thp
@@ -70,6 +73,7 @@ def _driver(data, theta0, scale, consts, seed, rank, world, allgather):
 
 def _rank_main(rank, world, port, out_dir):
     sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     import torch
     import torch.distributed as dist
@@ -79,17 +83,12 @@ def _rank_main(rank, world, port, out_dir):
     data = synth.nn1_data(301, seed=77)  # ragged split: 150 + 151 members
     theta0, scale, consts = synth.nn1_settings(data)
 
-    def allgather(v):  # gloo gathers equal sizes: pad to the largest shard, then trim
-        sizes = [None] * world
-        dist.all_gather_object(sizes, int(v.size))
-        m = max(sizes)
-        pad = np.zeros(m)
-        pad[: v.size] = v
-        out = [torch.zeros(m, dtype=torch.float64) for _ in sizes]
-        dist.all_gather(out, torch.from_numpy(pad))
-        return np.concatenate([o.numpy()[:c] for o, c in zip(out, sizes)])
+    def allreduce(words):  # the exchange words of all ranks, added as 64-bit integers
+        t = torch.from_numpy(words.copy())
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return t.numpy()
 
-    rows, chi, S = _driver(data, theta0, scale, consts, 5, rank, world, allgather)
+    rows, chi, S = _driver(data, theta0, scale, consts, 5, rank, world, allreduce)
     np.savez(os.path.join(out_dir, f"rank{rank}.npz"), rows=rows, chi=chi, S=S)
     dist.barrier()
     dist.destroy_process_group()
