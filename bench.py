@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--batched-sweeps", type=int, default=2000)
     ap.add_argument("--batched-pops", type=int, default=256)
     ap.add_argument("--batched-nlo", type=float, default=1e3, help="smallest population of the batched leg")
+    ap.add_argument("--batched-block", type=int, default=0, help="batched leg launch shape (0: tuned)")
+    ap.add_argument("--batched-grid", type=int, default=0)
+    ap.add_argument("--batched-chunk", type=int, default=0)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--serve-rate", type=float, default=20.0)
@@ -301,13 +304,17 @@ def run_batched(args, cudahm, stream, device):
     members = sum(sp.n for sp in specs)
     K = args.batched_sweeps
     W = min(args.warmup, 50)
+    tune = None
+    if args.batched_block or args.batched_grid or args.batched_chunk:  # a fixed shape (profiling)
+        tune = cudahm.CudahmTune(block_threads=args.batched_block, sweeps_per_launch=args.batched_chunk,
+                                 use_graph=1, grid_blocks=args.batched_grid)
     if W > 0:
-        cudahm.batch_run(samplers, W, 0)
+        cudahm.batch_run(samplers, W, 0, tune=tune)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    rows, chosen = cudahm.batch_run(samplers, 0, K, 1)
+    rows, chosen = cudahm.batch_run(samplers, 0, K, 1, tune=tune)
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1)

@@ -223,27 +223,32 @@ __device__ __forceinline__ void grid_arrive(unsigned int* count, bool skip_arriv
     atomicAdd(count, 1u);
   }
 }
+// Thread 0's bounded wait for grid barrier `index` (nb arrivals per barrier; 0: the grid): true
+// once every block has arrived, false if the run failed meanwhile or the wait ran out (the
+// run's error word then says why). Nothing else of the block waits.
+__device__ __forceinline__ bool grid_poll(unsigned int* count, unsigned int index, int* err, long long limit_ns,
+                                          unsigned int nb) {
+  const unsigned int target = (index + 1u) * (nb ? nb : gridDim.x);
+  const long long t0 = globaltimer_ns();
+  bool ok = true;
+  while (true) {
+    if (ld_acquire_u32(count) >= target) break;
+    if (ld_volatile_i32(err) != 0) { ok = false; break; }
+    if (globaltimer_ns() - t0 > limit_ns) {
+      atomicCAS(err, 0, CUDAHM_ETIMEOUT);
+      ok = false;
+      break;
+    }
+    __nanosleep(64);
+  }
+  if (ld_volatile_i32(err) != 0) ok = false;
+  __threadfence();
+  return ok;
+}
 __device__ __forceinline__ bool grid_wait(unsigned int* count, unsigned int index, int* err, long long limit_ns,
                                           unsigned int nb = 0u) {
   __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned int target = (index + 1u) * (nb ? nb : gridDim.x);
-    const long long t0 = globaltimer_ns();
-    while (true) {
-      if (ld_acquire_u32(count) >= target) break;
-      if (ld_volatile_i32(err) != 0) { ok = 0; break; }
-      if (globaltimer_ns() - t0 > limit_ns) {
-        atomicCAS(err, 0, CUDAHM_ETIMEOUT);
-        ok = 0;
-        break;
-      }
-      __nanosleep(64);
-    }
-    if (ld_volatile_i32(err) != 0) ok = 0;
-    __threadfence();
-    s_ok = ok;
-  }
+  if (threadIdx.x == 0) s_ok = grid_poll(count, index, err, limit_ns, nb) ? 1 : 0;
   __syncthreads();
   return s_ok != 0;
 }

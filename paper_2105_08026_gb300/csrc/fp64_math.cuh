@@ -114,4 +114,31 @@ __device__ __forceinline__ void sincospi_tab(double a, const double* __restrict_
   *cs = fma(cj, ct, -sj * st);
 }
 
+// e^x - 1 for the theta step's constants (a dependent chain on one lane, so short matters more
+// than throughput): for |x| <= 1/2 the Taylor series x (1 + x/2! + ... + x^15/16!) by Horner
+// (remainder below 1e-18 relative), else the library routine.
+__device__ __forceinline__ double expm1_theta(double x) {
+  if (!(fabs(x) <= 0.5)) return expm1(x);
+  constexpr double c[16] = {1.0,
+                            1.0 / 2.0,
+                            1.0 / 6.0,
+                            1.0 / 24.0,
+                            1.0 / 120.0,
+                            1.0 / 720.0,
+                            1.0 / 5040.0,
+                            1.0 / 40320.0,
+                            1.0 / 362880.0,
+                            1.0 / 3628800.0,
+                            1.0 / 39916800.0,
+                            1.0 / 479001600.0,
+                            1.0 / 6227020800.0,
+                            1.0 / 87178291200.0,
+                            1.0 / 1307674368000.0,
+                            1.0 / 20922789888000.0};
+  double q = c[15];
+#pragma unroll
+  for (int k = 14; k >= 0; --k) q = fma(q, x, c[k]);
+  return q * x;
+}
+
 }  // namespace chm

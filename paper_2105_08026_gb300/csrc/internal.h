@@ -7,9 +7,12 @@ namespace chm {
 
 constexpr int kMaxP = 9;
 constexpr int kPartWords = 8;  // u64 words of one block's partial: D[3], E[3], flags[2]
-// grid totals of the sweep kernel, added by every member block: D and E as six 32-bit limbs each
-// (in u64 counters), the flags as two packed u64; three buffers, one per sweep mod 3
-constexpr int kAccWords = 16;
+// grid totals of the persistent kernels, added by every member block: D and E as six 32-bit
+// limbs each (in u64 counters) in words 0-5 and 6-11, the flags as two packed u64 in 12-13; the
+// sweep kernel's selection integral at the sweep's other possible theta' in 14-19 (E at the
+// proposal made for a rejected theta in 6-11, for an accepted one in 14-19) and their flag
+// counts in 20; three buffers, one per sweep mod 3
+constexpr int kAccWords = 22;
 
 // Chain state kept on the device between runs.
 struct ChainState {
@@ -107,7 +110,7 @@ struct SweepArgs {
   float* chi32;       // FP32 form, d = 1: the latents (binary32 state; chi is a binary64 copy for the API)
   long long n32;      // FP32 form, d = 1: row stride of d32 and padded length of chi32 and S (a multiple
                       // of kTilePad, so that bulk copies of aligned member tiles stay in bounds); else n
-  double* pub;        // theta' of the current sweep, published by block 0 (kPubWords doubles);
+  double* pub;        // theta' proposals published by block 0 (kPubSlots slots of kPubWords doubles);
                       // its sequence word is bar[1]
   double* marg_lp;           // marginal form: log p_i at two thetas, [2][n]
   const double* marg_nodes;  // marginal form: panel nodes and weights (kMargNodeWords)
@@ -131,7 +134,10 @@ struct SweepArgs {
   unsigned long long* shard_out;
 };
 
-constexpr int kPubWords = 32;
+constexpr int kPubWords = 32;  // doubles per publication slot of the sweep kernel
+// slots: 0 the launch's first theta'; 1 + 2 (t & 1) + c the proposal of sweep t for outcome c of
+// the decision before it
+constexpr int kPubSlots = 5;
 
 // Exchange words of one shard's sweep (cudahm_shard_pass): the theta' partial D and the
 // selection-rule partial E as six 32-bit limbs each (in u64 words, so that the words of all

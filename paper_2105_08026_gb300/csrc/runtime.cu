@@ -834,7 +834,7 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
       (rc = alloc_into(h, &h->tab_U, kChunk * p)) || (rc = alloc_into(h, &h->tab_u, kChunk)) ||
       (rc = alloc_into(h, &h->tab_lnu, kChunk)) ||
       (rc = alloc_into(h, &h->math_tab, static_cast<size_t>(math_table_words()))) ||
-      (rc = alloc_into(h, &h->pub, kPubWords)) ||
+      (rc = alloc_into(h, &h->pub, static_cast<size_t>(kPubWords) * kPubSlots)) ||
       (rc = alloc_into(h, &h->tab_eta, kChunk)))
     return bail(rc);
   if (has_rule(cfg->model)) {

@@ -138,12 +138,26 @@ __device__ __forceinline__ void sweep_part_a(const SweepArgs& a, long long sa, u
         float d[M::kData32];
 #pragma unroll
         for (int c = 0; c < M::kData32; ++c) d[c] = s_d32[c * a.mpb + q];
-        const uint4 w = philox4x32_10(make_uint4(0u, 2u, static_cast<uint32_t>(i), odd ? k : k - 1u), a.key0,
-                                      a.key1);
-        const float u = uniform23(odd ? w.z : w.w);
-        float zc, zs;
-        box_muller32(w.x, w.y, zc, zs);
-        const float z = odd ? zc : zs;
+        // the odd sweep keeps the pair's sine and the even sweep's uniform in shared memory (the
+        // binary32 views of the spare-normal slots) for the next sweep; a launch that starts on an
+        // even sweep recomputes them
+        float* s_even = reinterpret_cast<float*>(s_zs);
+        float z, u;
+        if (odd || sa == 0) {
+          const uint4 w = philox4x32_10(make_uint4(0u, 2u, static_cast<uint32_t>(i), odd ? k : k - 1u), a.key0,
+                                        a.key1);
+          float zc, zs;
+          box_muller32(w.x, w.y, zc, zs);
+          z = odd ? zc : zs;
+          u = uniform23(odd ? w.z : w.w);
+          if (odd) {
+            s_even[q] = zs;
+            s_even[a.mpb + q] = uniform23(w.w);
+          }
+        } else {
+          z = s_even[q];
+          u = s_even[a.mpb + q];
+        }
         const float Y = fmaf(f32_rz(S[m]), z, chi[m]);
         // binary32 views of the slots (a conversion to binary64 and back would cost FP64 issue)
         reinterpret_cast<float*>(s_pY)[q] = Y;
@@ -193,6 +207,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   // >= 0: row s_pend_idx of this launch's table, else s_pendU), alpha (from s_pend_lal when
   // s_pend_from_lal), eta (0: none)
   __shared__ double s_pendU[kMaxP], s_pend_alpha, s_pend_lal, s_pend_eta;
+  __shared__ double s_Unext[kMaxP];  // block 0: the table row of the next sweep's proposal
   __shared__ long long s_pend_idx;
   __shared__ int s_pend_from_lal;
   // block 0: the next sweep's proposal for a rejected [0] and an accepted [1] theta'
@@ -200,6 +215,11 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   __shared__ long long s_rows_written, s_tacc, s_mom_n0;
   __shared__ int s_mom_sel;
   __shared__ BlockRed s_red;
+  // this block's share of the selection integral at the sweep's two possible theta' (rejected,
+  // accepted outcome of the decision before it), evaluated by the last warp while thread 0 takes
+  // that decision, and their NaN / out-of-range counts
+  __shared__ Xacc s_e[2];
+  __shared__ unsigned int s_ef[2];
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
@@ -262,22 +282,23 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     s_pend_from_lal = 0;
     s_tcf = M::consts32(s_tc);
     // theta' of the first sweep: proposed by block 0 and fetched by the others
-    double lp = -INFINITY;
-    ThetaC tcp{};
-    ThetaCf tcpf{};
-    ThetaDf tdf{};
+    ThetaPub& first = s_cand[0];
     if (blockIdx.x == 0) {
-      propose_theta<M>(a, 0, p, s_theta, s_Sth, s_thp, lp, tcp, s_math);
-      tcpf = M::consts32(tcp);
-      if (F32) tdf = M::dconsts32(s_tc, tcp);
-      publish_theta(a, 1u, s_thp, p, lp, tcp, tcpf, tdf);
-    } else if (!fetch_theta(a, 1u, s_thp, p, lp, tcp, tcpf, tdf)) {
+      propose_theta<M>(a, 0, p, s_theta, s_Sth, first.thp, first.lpri_new, first.tcp, s_math);
+      first.tcpf = M::consts32(first.tcp);
+      if (F32) first.tdf = M::dconsts32(s_tc, first.tcp);
+      put_pub(pub_slot(a, 0), first, p);
+      release_pub(a, 1u);
+    } else if (wait_pub(a, 1u)) {
+      get_pub(first, pub_slot(a, 0), p);
+    } else {
       s_fail = 1;
     }
-    s_lpri_new = lp;
-    s_tcp = tcp;
-    s_tcpf = tcpf;
-    s_tdf = tdf;
+    for (int q = 0; q < p; ++q) s_thp[q] = first.thp[q];
+    s_lpri_new = first.lpri_new;
+    s_tcp = first.tcp;
+    s_tcpf = first.tcpf;
+    s_tdf = first.tdf;
   }
   __syncthreads();
   if (s_fail) return;
@@ -325,37 +346,103 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   if (a.ns > 0)
     sweep_part_a<M, K, F32>(a, 0, nb0, nb1, chi, S, s_math, s_y, s_aux, s_zs, s_d32, s_pY, s_peY, s_pll, s_pu);
 
+  // The last warp's share of the selection rule (LF, BB1) at the two possible theta' of a sweep:
+  // this block's outer nodes j = rule_j0 + mblk + mgrid k, for both proposals, one (node,
+  // proposal) pair per lane, reduced over the warp into s_e (the first sweep of a launch has one
+  // theta', as the first).
+  auto rule_terms = [&](const ThetaPub* cand, int ncand) {
+    Xacc xe0, xe1;
+    xacc_zero(xe0);
+    xacc_zero(xe1);
+    XFlags fe0 = {0u, 0u, 0u}, fe1 = {0u, 0u, 0u};
+    const int j1 = a.rule_j1 ? a.rule_j1 : a.nL;
+    const int nk = (j1 - a.rule_j0 - static_cast<int>(mblk) + static_cast<int>(mgrid) - 1) / static_cast<int>(mgrid);
+    for (int idx = lane; idx < ncand * nk; idx += 32) {
+      const int c = idx % ncand, k = idx / ncand;
+      const int j = a.rule_j0 + static_cast<int>(mblk) + static_cast<int>(mgrid) * k;
+      if (j < j1 && cand[c].lpri_new != -INFINITY) {
+        // one code path for both proposals (lanes of a warp on different paths would run one
+        // after the other): the term into a temporary, then added to its proposal's sum
+        Xacc t;
+        xacc_zero(t);
+        XFlags ft = {0u, 0u, 0u};
+        etabar_node<M>(cand[c].tcp, a, j, s_math, t, ft);
+        Xacc z;
+        xacc_zero(z);
+        xacc_add(xe0, c == 0 ? t : z);
+        xacc_add(xe1, c == 0 ? z : t);
+        fe0.nan += (c == 0) ? ft.nan + ft.big : 0u;
+        fe1.nan += (c == 0) ? 0u : ft.nan + ft.big;
+      }
+    }
+    unsigned int f[4] = {fe0.nan, fe1.nan, 0u, 0u};
+    warp_reduce(xe0, xe1, f);
+    if (lane == 0) {
+      s_e[0] = xe0;
+      s_e[1] = xe1;
+      s_ef[0] = f[0];
+      s_ef[1] = f[1];
+    }
+  };
+  // FP32 form: the rule's share is evaluated a decision ahead (during the decision before the
+  // sweep, by one warp, whose FP64 unit is idle then: off the path from the decision to the
+  // partial sums); on two blocks per SM the second block's warp sits on another SM sub-partition.
+  // FP64 form: with the partial sums (the decision window's FP64 units are shared there).
+  constexpr bool kRuleAhead = F32 && is_lf;
+  const int rule_warp = ctrl_warp - ((gridDim.x >= 2 && blockIdx.x >= gridDim.x / 2) ? 1 : 0);
+  if (kRuleAhead && wid == rule_warp && !leader_only) rule_terms(s_cand, 1);  // theta' of the first sweep
+
   for (long long s = 0; s < a.ns; ++s) {
+    // theta' of this sweep (s > 0): the proposal prepared for the outcome of the last decision
+    if (s > 0 && tid == 0) {
+      const ThetaPub& c = s_cand[s_acc_prev];
+      for (int q = 0; q < p; ++q) s_thp[q] = c.thp[q];
+      s_lpri_new = c.lpri_new;
+      s_tcp = c.tcp;
+      s_tcpf = c.tcpf;
+      s_tdf = c.tdf;
+    }
+    // block 0, from the start of the sweep (while the member blocks work): the theta step's
+    // serial part, off the path between the decision and the next proposal. The RAM update of
+    // S_theta pending from the previous decision (each step's update is applied one sweep late),
+    // then the next sweep's proposal theta + S_theta U for both outcomes of this sweep's decision
+    // (theta rejected, theta' accepted), each split into three tasks (propose_part) on lane 0 of
+    // six different warps (lanes of one warp would run divergent tasks one after another), and
+    // released to the other blocks, which fetch them before this sweep's decision.
+    if (blockIdx.x == 0) {
+      // the table rows it reads, staged in shared memory first (one load per lane)
+      if (tid < p) {
+        if (s + 1 < a.ns) s_Unext[tid] = __ldg(a.tab_U + (s + 1) * p + tid);
+        if (s_pend_idx >= 0) s_pendU[tid] = __ldg(a.tab_U + s_pend_idx * p + tid);
+      }
+      __syncthreads();  // this sweep's theta' and the rows are in place
+      if (wid == ctrl_warp && lane == 0 && s_pend_eta > 0.0) {
+        const double lal = s_pend_lal;
+        const double alpha = s_pend_from_lal ? ((lal >= 0.0) ? 1.0 : exp_tab(lal, s_math)) : s_pend_alpha;
+        ram_update_theta(p, s_Sth, s_pendU, alpha, a.astar_theta, s_pend_eta);
+        s_pend_eta = 0.0;
+      }
+      __syncthreads();
+      if (s + 1 < a.ns) {
+        // task t: outcome c = t & 1, part 2 - (t >> 1) (the longest first); on 8 warps tasks 4, 5
+        // go to warps 6, 7, so that each SM sub-partition's FP64 unit runs at most one long task
+        const int nw = blockDim.x >> 5;
+        for (int t = 0; t < 6; ++t) {
+          const int w = (nw == 8) ? (t < 4 ? t : t + 2) : (t % nw);
+          if (wid == w && lane == 0) {
+            const int c = t & 1;
+            propose_part<M, F32>(a, s_Unext, p, 2 - (t >> 1), c ? s_thp : s_theta, s_Sth, c ? s_tcp : s_tc,
+                                 s_cand[c], s_math);
+          }
+        }
+        __syncthreads();
+        if (gridDim.x > 1 && wid == ctrl_warp)
+          pub2_put(a, 1 + 2 * static_cast<int>((s + 1) & 1), s_cand, static_cast<unsigned int>(s + 2), lane);
+      }
+    }
     const ThetaC tc = s_tc;
     const bool trace = (a.trace_off + s) < a.trace_T;
     unsigned int member_nan = 0;
-
-    // theta' of this sweep (last warp): one proposal per sweep for the grid, prepared by block 0
-    // during the previous sweep for either outcome of its decision, picked and published here,
-    // fetched by the other blocks (whose FP64 units are left to the members)
-    if (s > 0 && wid == ctrl_warp) {
-      if (lane == 0) {
-        double lp = -INFINITY;
-        ThetaC tcp{};
-        ThetaCf tcpf{};
-        ThetaDf tdf{};
-        if (blockIdx.x == 0) {
-          const ThetaPub& c = s_cand[s_acc_prev];
-          for (int q = 0; q < p; ++q) s_thp[q] = c.thp[q];
-          lp = c.lpri_new;
-          tcp = c.tcp;
-          tcpf = c.tcpf;
-          tdf = c.tdf;
-          publish_theta(a, static_cast<unsigned int>(s + 1), s_thp, p, lp, tcp, tcpf, tdf);
-        } else if (!fetch_theta(a, static_cast<unsigned int>(s + 1), s_thp, p, lp, tcp, tcpf, tdf)) {
-          lp = -INFINITY;  // the run has failed; the next barrier returns
-        }
-        s_lpri_new = lp;
-        s_tcp = tcp;
-        s_tcpf = tcpf;
-        s_tdf = tdf;
-      }
-    }
 
     if constexpr (F32) {
       // a1-a3 in binary32 (FP32 bulk form), the theta-dependent half (the draws, Y and its
@@ -481,7 +568,8 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         }
       }
     }
-    if constexpr (is_lf)
+
+    if constexpr (is_lf && !kRuleAhead)
       if (prior_ok && !leader_only) etabar_terms<M>(tcp, a, mblk, mgrid, s_math, xe, fe);
 
     // a5: block partial
@@ -510,9 +598,15 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         if (lane == 0 && !leader_only) {  // into the grid totals of this sweep
           unsigned long long* acc = a.acc3 + (s % 3) * kAccWords;
           acc_add_limbs(acc, bd);
-          acc_add_limbs(acc + 6, be);
           atomicAdd(acc + 12, (static_cast<unsigned long long>(bf[1]) << 32) | bf[0]);
           atomicAdd(acc + 13, (static_cast<unsigned long long>(bf[3]) << 32) | bf[2]);
+          if constexpr (kRuleAhead) {  // the rule's share, evaluated during the previous decision
+            acc_add_limbs(acc + 6, s_e[0]);
+            acc_add_limbs(acc + 14, s_e[1]);
+            atomicAdd(acc + 20, (static_cast<unsigned long long>(s_ef[1]) << 32) | s_ef[0]);
+          } else if constexpr (is_lf) {
+            acc_add_limbs(acc + 6, be);
+          }
         }
         // the totals of sweep s + 1 reuse the buffer of sweep s - 2, which every block has read
         // (the member blocks before arriving at barrier s - 1, block 0 before publishing the
@@ -523,6 +617,66 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
         }
       }
     }
+    // a7: every block reads the grid totals and takes the same decision (thread 0)
+    auto decide = [&]() {
+      const double lnut = __ldg(a.tab_lnu + s), eta_s = __ldg(a.tab_eta + s);  // loads issued first
+      Xacc D, E;
+      unsigned int f[4];
+      const unsigned long long* acc = a.acc3 + (s % 3) * kAccWords;
+      // the rule's total at this sweep's theta' (evaluated ahead: the proposal for the last outcome)
+      const int ec = kRuleAhead ? s_acc_prev : 0;
+      acc_to_xacc(acc, D);
+      acc_to_xacc(acc + (ec ? 14 : 6), E);
+      const unsigned long long f01 = __ldcg(acc + 12), f23 = __ldcg(acc + 13);
+      f[0] = static_cast<unsigned int>(f01);
+      f[1] = static_cast<unsigned int>(f01 >> 32);
+      if (kRuleAhead) f[1] += static_cast<unsigned int>(__ldcg(acc + 20) >> (ec ? 32 : 0));
+      f[2] = static_cast<unsigned int>(f23);
+      f[3] = static_cast<unsigned int>(f23 >> 32);
+      const long long sg = a.trace_off + s;  // sweep index within this run
+      if (f[1] != 0u) {
+        atomicCAS(a.err, 0, CUDAHM_ENUMERIC);
+        s_stop = 1;
+      } else {
+        double logalpha, Drec, eb_new, logeb_new;
+        theta_logalpha<M>(D, E, f, prior_ok, static_cast<double>(a.n), s_theta, s_thp, s_lpri, s_lpri_new, s_logeb,
+                          s_math, logalpha, Drec, eb_new, logeb_new);
+        const bool acc = lnut < logalpha;
+        if (blockIdx.x == 0 && sg < a.trace_T) {
+          for (int q = 0; q < p; ++q) a.tr_thprop[sg * p + q] = s_thp[q];
+          a.tr_D[sg] = Drec;
+          a.tr_logalpha[sg] = logalpha;
+          a.tr_ut[sg] = __ldg(a.tab_u + s);
+          a.tr_tacc[sg] = acc ? 1 : 0;
+          a.tr_eb[sg] = eb_new;
+        }
+        if (acc) {
+          for (int q = 0; q < p; ++q) s_theta[q] = s_thp[q];
+          s_tc = s_tcp;
+          s_tcf = s_tcpf;
+          s_lpri = s_lpri_new;
+          if (is_lf) {
+            s_etabar = eb_new;
+            s_logeb = logeb_new;
+          }
+          s_tacc++;
+        }
+        if (a.adapt_theta) {  // this step's RAM update, applied during the next sweep
+          s_pend_lal = logalpha;
+          s_pend_from_lal = 1;
+          s_pend_idx = s;
+          s_pend_eta = eta_s;
+        }
+        // a8: record kept sweeps
+        const long long post = s - a.burn_left;
+        if (post >= 0 && a.thin > 0 && ((a.keep_phase + post + 1) % a.thin) == 0) {
+          if (blockIdx.x == 0)
+            for (int q = 0; q < p; ++q) a.rows[s_rows_written * p + q] = s_theta[q];
+          s_rows_written++;
+        }
+        s_acc_prev = acc ? 1 : 0;
+      }
+    };
     // arrive, prepare the next sweep's theta-independent half while the other blocks arrive, wait
     grid_arrive(a.bar, skip_me || leader_only);
     // a8 (optional): this sweep's latents into the running moments
@@ -537,89 +691,17 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     if (s + 1 < a.ns)
       sweep_part_a<M, K, F32>(a, s + 1, nb0, nb1, chi, S, s_math, s_y, s_aux, s_zs, s_d32, s_pY, s_peY, s_pll,
                               s_pu);
-    // block 0, while the member blocks work: the theta step's serial part, off the path between
-    // the decision and the next proposal. The RAM update of S_theta pending from the previous
-    // sweep (each step's update is applied one sweep late), then the next sweep's proposal
-    // theta + S_theta U for theta = this sweep's theta (rejected; one warp) and theta'
-    // (accepted; another warp, on another SM sub-partition's FP64 unit).
-    if (blockIdx.x == 0) {
-      if (wid == ctrl_warp && lane == 0 && s_pend_eta > 0.0) {
-        const double lal = s_pend_lal;
-        const double alpha = s_pend_from_lal ? ((lal >= 0.0) ? 1.0 : exp_tab(lal, s_math)) : s_pend_alpha;
-        const double* U = (s_pend_idx >= 0) ? a.tab_U + s_pend_idx * p : s_pendU;
-        ram_update_theta(p, s_Sth, U, alpha, a.astar_theta, s_pend_eta);
-        s_pend_eta = 0.0;
-      }
-      __syncthreads();
-      if (s + 1 < a.ns && lane == 0 && (wid == ctrl_warp || wid == ctrl_warp - 1)) {
-        const int c = (wid == ctrl_warp) ? 1 : 0;
-        ThetaPub& o = s_cand[c];
-        propose_theta<M>(a, s + 1, p, c ? s_thp : s_theta, s_Sth, o.thp, o.lpri_new, o.tcp, s_math);
-        o.tcpf = M::consts32(o.tcp);
-        if (F32) o.tdf = M::dconsts32(c ? s_tcp : s_tc, o.tcp);  // the step from that outcome's theta
-      }
+    // the other blocks fetch both proposals of the next sweep while the barrier completes (block
+    // 0 released them early in this sweep; a failed wait sets the error word, which the barrier
+    // wait sees)
+    if (blockIdx.x != 0 && s + 1 < a.ns && wid == ctrl_warp) {
+      const bool ok = (lane == 0) ? wait_pub(a, static_cast<unsigned int>(s + 2)) : false;
+      if (__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) pub2_get(a, 1 + 2 * static_cast<int>((s + 1) & 1), s_cand, lane);
     }
     if (!grid_wait(a.bar, static_cast<unsigned int>(s), a.err, a.timeout_ns, nbar)) return;
-
-    // a7: every block reads the grid totals and takes the same decision
-    {
-      Xacc D, E;
-      unsigned int f[4];
-      if (tid == 0) {
-        const unsigned long long* acc = a.acc3 + (s % 3) * kAccWords;
-        acc_to_xacc(acc, D);
-        acc_to_xacc(acc + 6, E);
-        const unsigned long long f01 = __ldcg(acc + 12), f23 = __ldcg(acc + 13);
-        f[0] = static_cast<unsigned int>(f01);
-        f[1] = static_cast<unsigned int>(f01 >> 32);
-        f[2] = static_cast<unsigned int>(f23);
-        f[3] = static_cast<unsigned int>(f23 >> 32);
-        const long long sg = a.trace_off + s;  // sweep index within this run
-        if (f[1] != 0u) {
-          atomicCAS(a.err, 0, CUDAHM_ENUMERIC);
-          s_stop = 1;
-        } else {
-          double logalpha, Drec, eb_new, logeb_new;
-          theta_logalpha<M>(D, E, f, prior_ok, static_cast<double>(a.n), s_theta, s_thp, s_lpri, s_lpri_new, s_logeb,
-                            s_math, logalpha, Drec, eb_new, logeb_new);
-          const double lnut = __ldg(a.tab_lnu + s);
-          const bool acc = lnut < logalpha;
-          if (blockIdx.x == 0 && sg < a.trace_T) {
-            for (int q = 0; q < p; ++q) a.tr_thprop[sg * p + q] = s_thp[q];
-            a.tr_D[sg] = Drec;
-            a.tr_logalpha[sg] = logalpha;
-            a.tr_ut[sg] = __ldg(a.tab_u + s);
-            a.tr_tacc[sg] = acc ? 1 : 0;
-            a.tr_eb[sg] = eb_new;
-          }
-          if (acc) {
-            for (int q = 0; q < p; ++q) s_theta[q] = s_thp[q];
-            s_tc = s_tcp;
-            s_tcf = s_tcpf;
-            s_lpri = s_lpri_new;
-            if (is_lf) {
-              s_etabar = eb_new;
-              s_logeb = logeb_new;
-            }
-            s_tacc++;
-          }
-          s_acc_prev = acc ? 1 : 0;
-          if (a.adapt_theta) {  // this step's RAM update, applied during the next sweep
-            s_pend_lal = logalpha;
-            s_pend_from_lal = 1;
-            s_pend_idx = s;
-            s_pend_eta = __ldg(a.tab_eta + s);
-          }
-          // a8: record kept sweeps
-          const long long post = s - a.burn_left;
-          if (post >= 0 && a.thin > 0 && ((a.keep_phase + post + 1) % a.thin) == 0) {
-            if (blockIdx.x == 0)
-              for (int q = 0; q < p; ++q) a.rows[s_rows_written * p + q] = s_theta[q];
-            s_rows_written++;
-          }
-        }
-      }
-    }
+    if (tid == 0) decide();
+    // while thread 0 decides: the rule's share at both possible theta' of the next sweep
+    if (kRuleAhead && wid == rule_warp && !leader_only && s + 1 < a.ns) rule_terms(s_cand, 2);
     __syncthreads();
     if (s_stop) return;
   }

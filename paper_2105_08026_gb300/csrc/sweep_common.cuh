@@ -164,7 +164,7 @@ struct LF {
     const double dL = tp.a1 - t.a1;
     split_f(tp.a0 - t.a0, d.dsc_hi, d.dsc_lo);
     split_f(tp.a0 * dL, d.c_hi, d.c_lo);
-    split_f(expm1(-dL), d.em_hi, d.em_lo);
+    split_f(expm1_theta(-dL), d.em_hi, d.em_lo);
     return d;
   }
   // d_i = log f(chi;theta') - log f(chi;theta) = dsc x - c - e^x em with x = chi - ln L* (xh + xl)
@@ -666,31 +666,37 @@ __device__ __forceinline__ double htab_eval(double u, const SweepArgs& a) {
 }
 
 // The outer node j's term G_j H(t_j) (LF: G_j = half w_j e^{(beta+1)(t - ln L*) - e^{t - ln L*}};
-// BB1: half w_j (1 - e^{-L/l}) e^{beta (t - ln u) - L/u + t}), the outer nodes spread over the
-// threads of all B blocks (block b, thread t: j = b + B t). Adds them exactly to xe.
+// BB1: half w_j (1 - e^{-L/l}) e^{beta (t - ln u) - L/u + t}), added exactly to xe.
 template <class M>
-__device__ __forceinline__ void etabar_terms(const ThetaC& tc, const SweepArgs& a, int b, int B,
-                                             const double* __restrict__ T, Xacc& xe, XFlags& fe) {
+__device__ __forceinline__ void etabar_node(const ThetaC& tc, const SweepArgs& a, int j, const double* __restrict__ T,
+                                            Xacc& xe, XFlags& fe) {
   constexpr bool bb1 = std::is_same<M, BB1>::value;
   const double lo = bb1 ? tc.a4 + a.mc.ln_lower : tc.a3;
   const double hi = tc.a1 + a.mc.ln_upper;
   const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
-  // outer nodes [rule_j0, rule_j1) (rule_j1 = 0: all n_L); a shard of a split population covers
-  // its own range, so every node is counted once over all shards
-  const int j1 = a.rule_j1 ? a.rule_j1 : a.nL;
-  for (int j = a.rule_j0 + b + B * static_cast<int>(threadIdx.x); j < j1; j += B * static_cast<int>(blockDim.x)) {
-    const double tt = fma(half, __ldg(a.xL + j), mid);
-    double G;
-    if constexpr (bb1) {
-      const double L = exp_tab(tt, T);
-      const double lg = BB1::log1mexp(L * tc.a3);
-      G = half * __ldg(a.wL + j) * exp_tab(lg + fma(tc.a0, tt - tc.a1, -L * tc.a2) + tt, T);
-    } else {
-      const double x = tt - tc.a1;
-      G = half * __ldg(a.wL + j) * exp_tab(fma(tc.a0, x, -exp_tab(x, T)), T);
-    }
-    xacc_add_double(xe, G * htab_eval(tt, a), fe);
+  const double tt = fma(half, __ldg(a.xL + j), mid);
+  double G;
+  if constexpr (bb1) {
+    const double L = exp_tab(tt, T);
+    const double lg = BB1::log1mexp(L * tc.a3);
+    G = half * __ldg(a.wL + j) * exp_tab(lg + fma(tc.a0, tt - tc.a1, -L * tc.a2) + tt, T);
+  } else {
+    const double x = tt - tc.a1;
+    G = half * __ldg(a.wL + j) * exp_tab(fma(tc.a0, x, -exp_tab(x, T)), T);
   }
+  xacc_add_double(xe, G * htab_eval(tt, a), fe);
+}
+
+// The outer nodes of the selection rule spread over the threads of all B blocks (block b, thread
+// t: j = rule_j0 + b + B t), each node's term etabar_node added exactly to xe. A shard of a split
+// population covers its own range [rule_j0, rule_j1) (rule_j1 = 0: all n_L), so that every node
+// is counted once over all shards.
+template <class M>
+__device__ __forceinline__ void etabar_terms(const ThetaC& tc, const SweepArgs& a, int b, int B,
+                                             const double* __restrict__ T, Xacc& xe, XFlags& fe) {
+  const int j1 = a.rule_j1 ? a.rule_j1 : a.nL;
+  for (int j = a.rule_j0 + b + B * static_cast<int>(threadIdx.x); j < j1; j += B * static_cast<int>(blockDim.x))
+    etabar_node<M>(tc, a, j, T, xe, fe);
 }
 
 // ------------------------------------------------------ member accept rule ---
@@ -943,34 +949,78 @@ struct ThetaPub {
 };
 static_assert(sizeof(ThetaPub) <= sizeof(double) * kPubWords, "ThetaPub does not fit its buffer");
 
-// Block 0: write theta' of the launch's sweep s1 (1-based), then release its sequence number.
-__device__ __forceinline__ void publish_theta(const SweepArgs& a, unsigned int s1, const double* thp, int p,
-                                              double lpri_new, const ThetaC& tcp, const ThetaCf& tcpf,
-                                              const ThetaDf& tdf) {
-  ThetaPub* pub = reinterpret_cast<ThetaPub*>(a.pub);
-  for (int q = 0; q < p; ++q) __stcg(pub->thp + q, thp[q]);
-  __stcg(&pub->lpri_new, lpri_new);
-  __stcg(&pub->tcp.a0, tcp.a0);
-  __stcg(&pub->tcp.a1, tcp.a1);
-  __stcg(&pub->tcp.a2, tcp.a2);
-  __stcg(&pub->tcp.a3, tcp.a3);
-  __stcg(&pub->tcp.a4, tcp.a4);
-  const float* f = &tcpf.sc_hi;
-  float* g = &pub->tcpf.sc_hi;
-  for (int q = 0; q < 6; ++q) __stcg(g + q, f[q]);
-  const float* fd = &tdf.dsc_hi;
-  float* gd = &pub->tdf.dsc_hi;
-  for (int q = 0; q < 6; ++q) __stcg(gd + q, fd[q]);
-  __threadfence();
-  st_release_u32(a.bar + 1, s1);
+// Publication of theta' proposals by block 0 to the other blocks of the sweep kernel: slots of
+// kPubWords doubles in a.pub (slot 0: the launch's first theta'; slot 1 + 2 (t & 1) + c: the
+// proposal of the launch's sweep t for outcome c of the decision before it), released by the
+// sequence word a.bar[1] = t + 1 once sweep t's slots are written. Parity slots suffice: block 0
+// writes sweep t + 2's after barrier t, which every block passes only after reading sweep t's.
+__device__ __forceinline__ ThetaPub* pub_slot(const SweepArgs& a, int slot) {
+  return reinterpret_cast<ThetaPub*>(a.pub + static_cast<size_t>(slot) * kPubWords);
 }
-
-// Other blocks: wait (bounded) until block 0 has published sweep s1, then read it. Returns false
-// if the run failed meanwhile or the wait ran out (the run's error word then says why).
-__device__ __forceinline__ bool fetch_theta(const SweepArgs& a, unsigned int s1, double* thp, int p, double& lpri_new,
-                                            ThetaC& tcp, ThetaCf& tcpf, ThetaDf& tdf) {
+__device__ __forceinline__ void put_pub(ThetaPub* dst, const ThetaPub& v, int p) {
+  for (int q = 0; q < p; ++q) __stcg(dst->thp + q, v.thp[q]);
+  __stcg(&dst->lpri_new, v.lpri_new);
+  __stcg(&dst->tcp.a0, v.tcp.a0);
+  __stcg(&dst->tcp.a1, v.tcp.a1);
+  __stcg(&dst->tcp.a2, v.tcp.a2);
+  __stcg(&dst->tcp.a3, v.tcp.a3);
+  __stcg(&dst->tcp.a4, v.tcp.a4);
+  const float* f = &v.tcpf.sc_hi;
+  float* g = &dst->tcpf.sc_hi;
+  for (int q = 0; q < 6; ++q) __stcg(g + q, f[q]);
+  const float* fd = &v.tdf.dsc_hi;
+  float* gd = &dst->tdf.dsc_hi;
+  for (int q = 0; q < 6; ++q) __stcg(gd + q, fd[q]);
+}
+__device__ __forceinline__ void get_pub(ThetaPub& v, const ThetaPub* src, int p) {
+  for (int q = 0; q < p; ++q) v.thp[q] = __ldcg(src->thp + q);
+  v.lpri_new = __ldcg(&src->lpri_new);
+  v.tcp.a0 = __ldcg(&src->tcp.a0);
+  v.tcp.a1 = __ldcg(&src->tcp.a1);
+  v.tcp.a2 = __ldcg(&src->tcp.a2);
+  v.tcp.a3 = __ldcg(&src->tcp.a3);
+  v.tcp.a4 = __ldcg(&src->tcp.a4);
+  const float* g = &src->tcpf.sc_hi;
+  float* f = &v.tcpf.sc_hi;
+  for (int q = 0; q < 6; ++q) f[q] = __ldcg(g + q);
+  const float* gd = &src->tdf.dsc_hi;
+  float* fd = &v.tdf.dsc_hi;
+  for (int q = 0; q < 6; ++q) fd[q] = __ldcg(gd + q);
+}
+// Both proposals of a sweep, word by word over the 32 lanes of a warp (every lane calls):
+// pub2_put writes them to slots base and base + 1 and releases seq (each lane fences its own
+// stores before the warp meets; then lane 0 releases); pub2_get reads them after the release.
+constexpr int kPubU32 = static_cast<int>(sizeof(ThetaPub) / 4);
+static_assert(sizeof(ThetaPub) % 8 == 0, "ThetaPub is copied as 32-bit words");
+__device__ __forceinline__ void pub2_put(const SweepArgs& a, int base, const ThetaPub* cand, unsigned int seq,
+                                         int lane) {
+  for (int w = lane; w < 2 * kPubU32; w += 32) {
+    const int c = w / kPubU32, o = w - c * kPubU32;
+    __stcg(reinterpret_cast<unsigned int*>(pub_slot(a, base + c)) + o,
+           reinterpret_cast<const unsigned int*>(cand + c)[o]);
+  }
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) st_release_u32(a.bar + 1, seq);
+}
+__device__ __forceinline__ void pub2_get(const SweepArgs& a, int base, ThetaPub* cand, int lane) {
+  (void)ld_acquire_u32(a.bar + 1);  // this lane's loads are ordered after the release it saw
+  for (int w = lane; w < 2 * kPubU32; w += 32) {
+    const int c = w / kPubU32, o = w - c * kPubU32;
+    reinterpret_cast<unsigned int*>(cand + c)[o] =
+        __ldcg(reinterpret_cast<const unsigned int*>(pub_slot(a, base + c)) + o);
+  }
+}
+// Block 0: release sequence number seq after writing its slots.
+__device__ __forceinline__ void release_pub(const SweepArgs& a, unsigned int seq) {
+  __threadfence();
+  st_release_u32(a.bar + 1, seq);
+}
+// Other blocks: wait (bounded) until block 0 has released seq. Returns false if the run failed
+// meanwhile or the wait ran out (the run's error word then says why).
+__device__ __forceinline__ bool wait_pub(const SweepArgs& a, unsigned int seq) {
   const long long t0 = globaltimer_ns();
-  while (ld_acquire_u32(a.bar + 1) < s1) {
+  while (ld_acquire_u32(a.bar + 1) < seq) {
     if (ld_volatile_i32(a.err) != 0) return false;
     if (globaltimer_ns() - t0 > a.timeout_ns) {
       atomicCAS(a.err, 0, CUDAHM_ETIMEOUT);
@@ -978,20 +1028,6 @@ __device__ __forceinline__ bool fetch_theta(const SweepArgs& a, unsigned int s1,
     }
     __nanosleep(32);
   }
-  const ThetaPub* pub = reinterpret_cast<const ThetaPub*>(a.pub);
-  for (int q = 0; q < p; ++q) thp[q] = __ldcg(pub->thp + q);
-  lpri_new = __ldcg(&pub->lpri_new);
-  tcp.a0 = __ldcg(&pub->tcp.a0);
-  tcp.a1 = __ldcg(&pub->tcp.a1);
-  tcp.a2 = __ldcg(&pub->tcp.a2);
-  tcp.a3 = __ldcg(&pub->tcp.a3);
-  tcp.a4 = __ldcg(&pub->tcp.a4);
-  const float* g = &pub->tcpf.sc_hi;
-  float* f = &tcpf.sc_hi;
-  for (int q = 0; q < 6; ++q) f[q] = __ldcg(g + q);
-  const float* gd = &pub->tdf.dsc_hi;
-  float* fd = &tdf.dsc_hi;
-  for (int q = 0; q < 6; ++q) fd[q] = __ldcg(gd + q);
   return true;
 }
 
@@ -1006,6 +1042,33 @@ __device__ __forceinline__ void propose_theta(const SweepArgs& a, long long s, i
   }
   lpri_new = M::logprior(thp, a.mc, T);
   tcp = M::consts(thp, a.mc, T);
+}
+
+// One lane's part of the theta proposal theta' = theta + S_theta U (U: a row of the tables, staged
+// in shared memory: a chain of global loads would dominate), so that
+// three lanes share its serial chain: role 0 the log prior, role 1 theta' and the model
+// constants (binary64 and binary32 pairs), role 2 (FP32 form) the constants of the step from
+// tc_from to theta'. Each role forms theta' itself, with the operations of propose_theta (the
+// same bits).
+template <class M, bool F32>
+__device__ __forceinline__ void propose_part(const SweepArgs& a, const double* U, int p, int role, const double* theta,
+                                             const double* Sth, const typename M::TC& tc_from, ThetaPub& o,
+                                             const double* T) {
+  double thp[kMaxP];
+  for (int q = 0; q < p; ++q) {
+    double t = theta[q];
+    for (int b = 0; b <= q; ++b) t = fma(Sth[q * p + b], U[b], t);
+    thp[q] = t;
+  }
+  if (role == 0) {
+    o.lpri_new = M::logprior(thp, a.mc, T);
+  } else if (role == 1) {
+    for (int q = 0; q < p; ++q) o.thp[q] = thp[q];
+    o.tcp = M::consts(thp, a.mc, T);
+    o.tcpf = M::consts32(o.tcp);
+  } else {
+    if constexpr (F32) o.tdf = M::dconsts32(tc_from, M::consts(thp, a.mc, T));
+  }
 }
 
 // The theta step's log acceptance ratio (Sec. 2.2, with the selection term of Eq. 12 for LF and
