@@ -835,23 +835,18 @@ __global__ void batch_tables_kernel(const SweepArgs* __restrict__ pops, const Ba
   theta_draws(a, static_cast<uint32_t>(a.chain->sweeps + s + 1), s);
 }
 
-// The theta step of one sweep of a split population (one block, thread 0), after every shard's
-// pass: theta' from the same tables and S_theta as the passes used, log alpha from the summed
-// exchange words (total, kShardWords words) with the population's member count n_pop, the
-// decision, the RAM update of S_theta pending from the previous sweep and this sweep's (as
-// run_population takes them), the kept row, and the tables of the next sweep into slot 0. Every
+// The theta step of one sweep of a split population (thread 0 of shard_decide_kernel), after
+// every shard's pass: theta' from the same tables and S_theta as the passes used, log alpha from
+// the summed exchange words (total, kShardWords words) with the population's member count n_pop,
+// the decision, the RAM update of S_theta pending from the previous sweep and this sweep's (as
+// run_population takes them), and the kept row. Every
 // shard runs it on the same words and chain state, so every shard takes the same decision. The
 // words must come from all `parts` shards with n_pop members in all; otherwise, or after a NaN,
 // the run's error word is set and the chain stays as it was.
 template <class M>
-__global__ void shard_decide_kernel(const SweepArgs* __restrict__ pop, BatchProg* __restrict__ prog,
-                                    const unsigned long long* __restrict__ total, long long n_pop, int parts) {
-  __shared__ double s_math[kMathWords];
-  const SweepArgs& a = *pop;
-  for (int q = threadIdx.x; q < kMathWords; q += blockDim.x) s_math[q] = a.math_tab[q];
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  if (ld_volatile_i32(a.err) != 0 || prog->off >= prog->total) return;
+__device__ void shard_decide_one(const SweepArgs& a, BatchProg* __restrict__ prog,
+                                 const unsigned long long* __restrict__ total, long long n_pop, int parts,
+                                 const double* s_math) {
   using TC = typename M::TC;
   const int p = a.p;
   ChainState& ch = *a.chain;
@@ -903,7 +898,39 @@ __global__ void shard_decide_kernel(const SweepArgs* __restrict__ pop, BatchProg
   }
   ch.sweeps += 1;
   prog->off += 1;
-  if (prog->off < prog->total) theta_draws(a, static_cast<uint32_t>(ch.sweeps + 1), 0);
+}
+
+// One block of two warps: thread 0 takes the decision (shard_decide_one) while warp 1 draws the
+// next sweep's theta tables into slot 1 (they do not depend on the decision), which thread 0
+// then moves to slot 0, where the next pass and decision read them.
+template <class M>
+__global__ void shard_decide_kernel(const SweepArgs* __restrict__ pop, BatchProg* __restrict__ prog,
+                                    const unsigned long long* __restrict__ total, long long n_pop, int parts) {
+  __shared__ double s_math[kMathWords];
+  __shared__ long long s_off, s_total, s_k;
+  __shared__ int s_run;
+  const SweepArgs& a = *pop;
+  if (threadIdx.x == 0) {
+    s_off = prog->off;
+    s_total = prog->total;
+    s_k = a.chain->sweeps;
+    s_run = (ld_volatile_i32(a.err) == 0 && s_off < s_total) ? 1 : 0;
+  }
+  for (int q = threadIdx.x; q < kMathWords; q += blockDim.x) s_math[q] = a.math_tab[q];
+  __syncthreads();
+  if (!s_run) return;
+  const bool next = s_off + 1 < s_total;
+  if (threadIdx.x == 32 && next) theta_draws(a, static_cast<uint32_t>(s_k + 2), 1);
+  if (threadIdx.x == 0) shard_decide_one<M>(a, prog, total, n_pop, parts, s_math);
+  __syncthreads();
+  if (threadIdx.x == 0 && next) {
+    const int p = a.p;
+    double* U = const_cast<double*>(a.tab_U);
+    for (int q = 0; q < p; ++q) U[q] = U[p + q];
+    const_cast<double*>(a.tab_u)[0] = a.tab_u[1];
+    const_cast<double*>(a.tab_lnu)[0] = a.tab_lnu[1];
+    const_cast<double*>(a.tab_eta)[0] = a.tab_eta[1];
+  }
 }
 
 }  // namespace
@@ -976,11 +1003,11 @@ cudaError_t launch_batch(bool f32, bool d1, const SweepArgs* pops, BatchProg* pr
 cudaError_t launch_shard_decide(int model, const SweepArgs* pop, BatchProg* prog, const unsigned long long* total,
                                 long long n_pop, int parts, cudaStream_t st) {
   switch (model) {
-    case CUDAHM_NN1: shard_decide_kernel<NN1><<<1, 32, 0, st>>>(pop, prog, total, n_pop, parts); break;
-    case CUDAHM_LF: shard_decide_kernel<LF><<<1, 32, 0, st>>>(pop, prog, total, n_pop, parts); break;
-    case CUDAHM_BB1: shard_decide_kernel<BB1><<<1, 32, 0, st>>>(pop, prog, total, n_pop, parts); break;
-    case CUDAHM_NN3: shard_decide_kernel<NN3><<<1, 32, 0, st>>>(pop, prog, total, n_pop, parts); break;
-    case CUDAHM_MVN3: shard_decide_kernel<MVN3><<<1, 32, 0, st>>>(pop, prog, total, n_pop, parts); break;
+    case CUDAHM_NN1: shard_decide_kernel<NN1><<<1, 64, 0, st>>>(pop, prog, total, n_pop, parts); break;
+    case CUDAHM_LF: shard_decide_kernel<LF><<<1, 64, 0, st>>>(pop, prog, total, n_pop, parts); break;
+    case CUDAHM_BB1: shard_decide_kernel<BB1><<<1, 64, 0, st>>>(pop, prog, total, n_pop, parts); break;
+    case CUDAHM_NN3: shard_decide_kernel<NN3><<<1, 64, 0, st>>>(pop, prog, total, n_pop, parts); break;
+    case CUDAHM_MVN3: shard_decide_kernel<MVN3><<<1, 64, 0, st>>>(pop, prog, total, n_pop, parts); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
