@@ -21,6 +21,9 @@ namespace chm {
 
 namespace {
 
+// members per staged tile, per thread of the block (two stages of them)
+constexpr unsigned int kTileFactor = 2u;
+
 // byte offset of the member-tile stages in the dynamic shared memory (after the exp/log tables)
 __host__ __device__ constexpr unsigned int tile_offset_bytes() {
   return (static_cast<unsigned int>(sizeof(double)) * kMathWords + 127u) & ~127u;
@@ -131,20 +134,12 @@ __device__ __forceinline__ void member_f64(const SweepArgs& a, unsigned int i, u
 // register-resident kernel's two half-steps, so the same bits. Writes the new latent and factor.
 template <class M>
 __device__ __forceinline__ void member1_f32(const SweepArgs& a, unsigned int i, float chi, double S, const float* d,
-                                            uint32_t k, float eta_f, float astar_f, const ThetaCf& tf,
+                                            float z, float u, float eta_f, float astar_f, const ThetaCf& tf,
                                             const ThetaCf& tpf, const ThetaDf& tdf, bool prior_ok, Xacc& xd,
                                             XFlags& fd,
                                             unsigned int& neg_big, unsigned int& pos_big, unsigned int& nan_cnt,
                                             unsigned int& acc_cnt, long long tro, bool keep, const MomStep& ms) {
   const float ll = M::loglike32(chi, d);
-  const bool odd = (k & 1u) != 0u;
-  // Philox block (0, stream 2, member i, odd sweep): a Box-Muller pair from words 0 and 1 (cosine
-  // for the odd sweep, sine for the next), the accept uniforms of the two sweeps from words 2, 3
-  const uint4 w = philox4x32_10(make_uint4(0u, 2u, a.moff + i, odd ? k : k - 1u), a.key0, a.key1);
-  const float u = uniform23(odd ? w.z : w.w);
-  float zc, zs;
-  box_muller32(w.x, w.y, zc, zs);
-  const float z = odd ? zc : zs;
   const float Y = fmaf(f32_rz(S), z, chi);
   float delta, llY = 0.0f, lfY = 0.0f, cY = 0.0f, cX;
   const float lfX = M::logf32_e(chi, tf, cX);
@@ -191,48 +186,69 @@ __device__ __forceinline__ void member1_f32(const SweepArgs& a, unsigned int i, 
 // (the TMA engine) while the block steps the members of the other stage. The few members of a
 // neighbouring block that an aligned tile covers are read but never used or written.
 struct TileRing {
-  char* buf;                // two stages of T (4 + 8 + 4 kData32) bytes
+  char* buf;                // two stages of T (4 + 8 + 4 kData32 + 8) bytes
   unsigned long long* bar;  // one mbarrier per stage
   unsigned int T;           // members per tile
   unsigned int count;       // tiles consumed so far: stage count & 1, phase parity (count >> 1) & 1
   bool prefetched;          // the tile with counter `count` (the first of a sweep) is in flight
 };
 
+// bytes of one member in a stage: latent, RAM factor, data, and the even sweep's two draws
+template <int K32>
+__host__ __device__ constexpr unsigned int tile_member_bytes() {
+  return 12u + 4u * K32 + 8u;
+}
+
+// Issues the tile of len members from b into stage cnt & 1; `even`: also the two draws the odd
+// sweep before stored for each member (a.even32), which an even sweep reads instead of drawing.
 template <int K32>
 __device__ __forceinline__ void tile_issue(const SweepArgs& a, const TileRing& r, unsigned int b, unsigned int len,
-                                           unsigned int cnt) {
-  char* st = r.buf + static_cast<size_t>(cnt & 1u) * r.T * (12u + 4u * K32);
+                                           unsigned int cnt, bool even) {
+  constexpr unsigned int mb = tile_member_bytes<K32>();
+  char* st = r.buf + static_cast<size_t>(cnt & 1u) * r.T * mb;
   unsigned long long* bar = r.bar + (cnt & 1u);
-  mbar_arrive_expect_tx(bar, len * (12u + 4u * K32));
+  mbar_arrive_expect_tx(bar, len * (even ? mb : mb - 8u));
   bulk_copy_g2s(st, a.chi32 + b, len * 4u, bar);
   bulk_copy_g2s(st + 4u * r.T, a.S + b, len * 8u, bar);
 #pragma unroll
   for (int c = 0; c < K32; ++c) bulk_copy_g2s(st + (12u + 4u * c) * r.T, a.d32 + c * a.n32 + b, len * 4u, bar);
+  if (even) {
+    bulk_copy_g2s(st + (12u + 4u * K32) * r.T, a.even32 + b, len * 4u, bar);
+    bulk_copy_g2s(st + (16u + 4u * K32) * r.T, a.even32 + a.n32 + b, len * 4u, bar);
+  }
 }
 
 // The block's member phase of one sweep (FP32 form, d = 1). Returns false if a stage wait
 // timed out (the run's error word is set; copies in flight have been waited for).
+// The draws of an odd sweep k (Philox block (0, stream 2, member word, k)) give that sweep's
+// normal (the Box-Muller cosine) and uniform (word 2) and the next sweep's (the sine, word 3).
+// `cached`: an even sweep whose odd predecessor ran in this launch, so its two draws are in the
+// stage (written to a.even32 by that sweep) instead of being drawn again; the first sweep of a
+// launch always draws (a.even32 may hold another chain's or run's values).
 template <class M>
 __device__ __forceinline__ bool members1_f32_tiled(const SweepArgs& a, TileRing& r, unsigned int nb0,
-                                                   unsigned int nb1, uint32_t k, float eta_f, float astar_f,
-                                                   const ThetaCf& tf, const ThetaCf& tpf, const ThetaDf& tdf,
-                                                   bool prior_ok, Xacc& xd,
+                                                   unsigned int nb1, uint32_t k, bool cached, float eta_f,
+                                                   float astar_f, const ThetaCf& tf, const ThetaCf& tpf,
+                                                   const ThetaDf& tdf, bool prior_ok, Xacc& xd,
                                                    XFlags& fd, unsigned int& neg_big, unsigned int& pos_big,
                                                    unsigned int& nan_cnt, unsigned int& acc_cnt, long long tro,
                                                    bool keep, const MomStep& ms) {
   constexpr int K32 = M::kData32;
+  constexpr unsigned int mb = tile_member_bytes<K32>();
   if (nb1 <= nb0) return true;
+  const bool odd = (k & 1u) != 0u;
   const unsigned int a0 = nb0 & ~3u;
   const unsigned long long a1l = (static_cast<unsigned long long>(nb1) + 3ull) & ~3ull;
   const unsigned int a1 = static_cast<unsigned int>(a1l < static_cast<unsigned long long>(a.n32) ? a1l : a.n32);
   const unsigned int ntiles = (a1 - a0 + r.T - 1u) / r.T;
-  if (!r.prefetched && threadIdx.x == 0) tile_issue<K32>(a, r, a0, min(r.T, a1 - a0), r.count);
+  if (!r.prefetched && threadIdx.x == 0) tile_issue<K32>(a, r, a0, min(r.T, a1 - a0), r.count, cached);
   r.prefetched = false;
   bool ok = true;  // this thread's stage waits all completed
   for (unsigned int t = 0; t < ntiles; ++t) {
     const unsigned int cnt = r.count;
     const unsigned int b = a0 + t * r.T, len = min(r.T, a1 - b);
-    if (t + 1u < ntiles && threadIdx.x == 0) tile_issue<K32>(a, r, b + r.T, min(r.T, a1 - b - r.T), cnt + 1u);
+    if (t + 1u < ntiles && threadIdx.x == 0)
+      tile_issue<K32>(a, r, b + r.T, min(r.T, a1 - b - r.T), cnt + 1u, cached);
     if (ok) ok = mbar_wait_bounded(r.bar + (cnt & 1u), (cnt >> 1) & 1u, a.err, a.timeout_ns);
     if (!ok) {  // the run has failed: skip the members, keep the block's barriers in step
       fence_proxy_async_global();
@@ -240,23 +256,42 @@ __device__ __forceinline__ bool members1_f32_tiled(const SweepArgs& a, TileRing&
       r.count = cnt + 1u;
       continue;
     }
-    const char* st = r.buf + static_cast<size_t>(cnt & 1u) * r.T * (12u + 4u * K32);
+    const char* st = r.buf + static_cast<size_t>(cnt & 1u) * r.T * mb;
     const float* s_chi = reinterpret_cast<const float*>(st);
     const double* s_S = reinterpret_cast<const double*>(st + 4u * r.T);
     const float* s_d = reinterpret_cast<const float*>(st + 12u * r.T);
+    const float* s_ev = reinterpret_cast<const float*>(st + (12u + 4u * K32) * r.T);
     for (unsigned int m = threadIdx.x; m < len; m += blockDim.x) {
       const unsigned int i = b + m;
       if (i < nb0 || i >= nb1) continue;
       float d[K32];
 #pragma unroll
       for (int c = 0; c < K32; ++c) d[c] = s_d[c * r.T + m];
-      member1_f32<M>(a, i, s_chi[m], s_S[m], d, k, eta_f, astar_f, tf, tpf, tdf, prior_ok, xd, fd, neg_big,
+      float z, u;
+      if (cached) {
+        z = s_ev[m];
+        u = s_ev[r.T + m];
+      } else {
+        const uint4 w = philox4x32_10(make_uint4(0u, 2u, a.moff + i, odd ? k : k - 1u), a.key0, a.key1);
+        float zc, zs;
+        box_muller32(w.x, w.y, zc, zs);
+        z = odd ? zc : zs;
+        u = uniform23(odd ? w.z : w.w);
+        if (odd) {  // the next sweep's two draws
+          a.even32[i] = zs;
+          a.even32[a.n32 + i] = uniform23(w.w);
+        }
+      }
+      member1_f32<M>(a, i, s_chi[m], s_S[m], d, z, u, eta_f, astar_f, tf, tpf, tdf, prior_ok, xd, fd, neg_big,
                      pos_big, nan_cnt, acc_cnt, tro, keep, ms);
     }
-    fence_proxy_async_global();  // this thread's writes before any later bulk copy reads them
-    __syncthreads();             // the stage is free for the tile after next
+    __syncthreads();  // the stage is free for the tile after next
     r.count = cnt + 1u;
   }
+  // this thread's writes of the sweep before any later bulk copy reads them (within the sweep the
+  // copies read only other members: a block's tiles are disjoint, and the few members of a
+  // neighbouring block that an aligned tile covers are never used)
+  fence_proxy_async_global();
   if (__syncthreads_or(ok ? 0 : 1)) {
     // a stage wait timed out: leave no copy in flight into this block's shared memory (every
     // thread waits, bounded again, for the last phase issued on each stage)
@@ -268,15 +303,16 @@ __device__ __forceinline__ bool members1_f32_tiled(const SweepArgs& a, TileRing&
   return true;
 }
 
-// Issues the first tile of the next sweep (thread 0), after every write of this sweep.
+// Issues the first tile of the next sweep (thread 0), after every write of this sweep; `cached`
+// as for members1_f32_tiled, for the next sweep.
 template <class M>
 __device__ __forceinline__ void tile_prefetch_first(const SweepArgs& a, TileRing& r, unsigned int nb0,
-                                                    unsigned int nb1) {
+                                                    unsigned int nb1, bool cached) {
   if (nb1 <= nb0) return;
   const unsigned int a0 = nb0 & ~3u;
   const unsigned long long a1l = (static_cast<unsigned long long>(nb1) + 3ull) & ~3ull;
   const unsigned int a1 = static_cast<unsigned int>(a1l < static_cast<unsigned long long>(a.n32) ? a1l : a.n32);
-  if (threadIdx.x == 0) tile_issue<M::kData32>(a, r, a0, min(r.T, a1 - a0), r.count);
+  if (threadIdx.x == 0) tile_issue<M::kData32>(a, r, a0, min(r.T, a1 - a0), r.count, cached);
   r.prefetched = true;
 }
 
@@ -535,7 +571,7 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
     const size_t base = reinterpret_cast<size_t>(reinterpret_cast<char*>(s_dyn) + tile_offset_bytes());
     ring.buf = reinterpret_cast<char*>((base + 127u) & ~static_cast<size_t>(127u));  // 16-byte copies need 16
     ring.bar = s_tbar;
-    ring.T = 2u * blockDim.x;
+    ring.T = kTileFactor * blockDim.x;
     ring.count = 0u;
     ring.prefetched = false;
     if (tid == 0) {
@@ -586,8 +622,9 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
     } else if constexpr (F32) {
       const TCf tf = s_tcf, tpf = s_tcpf;
       const ThetaDf tdf = s_tdf;
-      if (!members1_f32_tiled<M>(a, ring, nb0, nb1, k, __double2float_rn(eta), astar_f, tf, tpf, tdf, prior_ok, xd,
-                                 fd, neg_big, pos_big, member_nan, member_acc, tro, keep, ms))
+      const bool cached = (k & 1u) == 0u && s > 0;  // the odd sweep before ran in this launch
+      if (!members1_f32_tiled<M>(a, ring, nb0, nb1, k, cached, __double2float_rn(eta), astar_f, tf, tpf, tdf,
+                                 prior_ok, xd, fd, neg_big, pos_big, member_nan, member_acc, tro, keep, ms))
         return;  // a stage wait timed out: the run's error word is set, the population stops
     } else {
       const TC tc = s_tc, tcp = s_tcp;
@@ -688,7 +725,7 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
     __syncthreads();
     if (s_stop) return;
     if constexpr (kTiled)
-      if (s + 1 < ns) tile_prefetch_first<M>(a, ring, nb0, nb1);  // overlaps the next theta proposal
+      if (s + 1 < ns) tile_prefetch_first<M>(a, ring, nb0, nb1, ((k + 1u) & 1u) == 0u);  // overlaps the next proposal
   }
   __shared__ unsigned int s_macc;
   if (tid == 0) s_macc = 0;
@@ -971,14 +1008,14 @@ cudaError_t launch_chi_from32(long long n, const float* chi32, double* chi, cuda
 }
 
 // Dynamic shared memory of the batched kernel: the exp/log tables, and when the FP32 form has
-// one-dimensional populations (they stream member tiles) two stages of 2 x block members of
+// one-dimensional populations (they stream member tiles) two stages of kTileFactor x block members of
 // 4 + 8 + 4 kData32 bytes, plus slack to align them to 128 bytes.
 size_t batch_smem_bytes(bool f32, bool any_d1, int block) {
   size_t b = sizeof(double) * kMathWords;
   if (f32 && any_d1) {
     static_assert(LF::kData32 == NN1::kData32, "one tile layout for the one-dimensional models");
-    const size_t per = 12u + 4u * static_cast<size_t>(LF::kData32);
-    b = tile_offset_bytes() + 128u + 2u * (2u * static_cast<size_t>(block)) * per;
+    const size_t per = tile_member_bytes<LF::kData32>();
+    b = tile_offset_bytes() + 128u + 2u * (kTileFactor * static_cast<size_t>(block)) * per;
   }
   return b;
 }

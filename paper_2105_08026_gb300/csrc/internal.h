@@ -108,6 +108,8 @@ struct SweepArgs {
   double gamma;       // adaptation exponent (eta = n^-gamma)
   const float* d32;   // FP32 form: precomputed binary32 member data (kData32 x n32, member-minor)
   float* chi32;       // FP32 form, d = 1: the latents (binary32 state; chi is a binary64 copy for the API)
+  float* even32;      // FP32 form, d = 1: the streaming kernel's cache of each member's next (even) sweep
+                      // normal and accept uniform, written by the odd sweep before it, [2][n32]
   long long n32;      // FP32 form, d = 1: row stride of d32 and padded length of chi32 and S (a multiple
                       // of kTilePad, so that bulk copies of aligned member tiles stay in bounds); else n
   double* pub;        // theta' proposals published by block 0 (kPubSlots slots of kPubWords doubles);
@@ -145,11 +147,10 @@ constexpr int kPubSlots = 5;
 // (the number of shards that contributed).
 constexpr int kShardWords = 16;
 
-// FP32 form, d = 1: member arrays are padded to a multiple of kTilePad members, and the
-// streaming kernel stages member tiles of kTileMembers (a multiple of 4: 16-byte aligned bulk
-// copies of binary32 and binary64 arrays) through shared memory.
+// FP32 form, d = 1: member arrays are padded to a multiple of kTilePad members, so that the
+// streaming kernel's bulk copies of member tiles (starting at multiples of 4 members: 16-byte
+// aligned for binary32 and binary64 arrays) stay in bounds.
 constexpr long long kTilePad = 64;
-constexpr int kTileMembers = 512;
 
 // Tabulated inner sum of the selection rule: Chebyshev series of degree kHDeg on cells of
 // width kHDelta in u = ln L.

@@ -167,6 +167,7 @@ struct cudahm {
   // FP32 form, d = 1: the binary32 latent state (chi holds its binary64 copy for the API; it is
   // refreshed before every read and copied in after every write of chi) and the padded length
   float* chi32 = nullptr;
+  float* even32 = nullptr;  // the streaming kernel's even-sweep draws, [2][n32]
   long long n32 = 0;
   double* math_tab = nullptr;
   double* pub = nullptr;  // theta' published by block 0 of the sweep kernel
@@ -446,6 +447,7 @@ SweepArgs base_args(cudahm* h) {
   a.gamma = h->cfg.adapt_exponent;
   a.d32 = h->d32;
   a.chi32 = h->chi32;
+  a.even32 = h->even32;
   a.n32 = h->n32;
   a.tab_U = h->tab_U;
   a.tab_u = h->tab_u;
@@ -826,6 +828,7 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
       (rc = alloc_into(h, &h->chi, n * h->d)) ||
       (rc = alloc_into(h, &h->S, tiled ? h->n32 : h->factor_n)) ||
       (tiled && (rc = alloc_into(h, &h->chi32, h->n32))) ||
+      (tiled && (rc = alloc_into(h, &h->even32, 2 * h->n32))) ||
       (rc = alloc_into(h, &h->chain, 1)) ||
       (rc = alloc_into(h, &h->acc3, 3ull * kAccWords)) ||
       (rc = alloc_into(h, &h->bar, 4)) ||
@@ -1986,7 +1989,7 @@ struct Request {
 size_t request_bytes(const cudahm_config& c, long long n_iter, long long thin) {
   const size_t n = static_cast<size_t>(c.n), d = c.d;
   const size_t p = model_p(c.model);
-  size_t b = n * (4 * 8 + d * 8 + d * d * 8) + (c.precision == CUDAHM_FP32 ? n * 5 * 4 : 0);
+  size_t b = n * (4 * 8 + d * 8 + d * d * 8) + (c.precision == CUDAHM_FP32 ? n * 7 * 4 : 0);  // FP32: data, latent, draws
   b += static_cast<size_t>(n_iter / std::max<long long>(thin, 1)) * p * 8;
   b += static_cast<size_t>(kChunk) * (p + 3) * 8 + 64 * 1024;
   if (has_rule(c.model)) b += static_cast<size_t>(8 * 4096 + 2048 + 1024 * (kHDeg + 1)) * 8;  // rule, H table
