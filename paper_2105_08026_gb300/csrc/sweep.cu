@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
   // >= 0: row s_pend_idx of this launch's table, else s_pendU), alpha (from s_pend_lal when
   // s_pend_from_lal), eta (0: none)
   __shared__ double s_pendU[kMaxP], s_pend_alpha, s_pend_lal, s_pend_eta;
-  __shared__ double s_Unext[kMaxP];  // block 0: the table row of the next sweep's proposal
+  __shared__ double s_Unext[kMaxP], s_Ucur[kMaxP];  // block 0: the table rows of the next and this sweep
   __shared__ long long s_pend_idx;
   __shared__ int s_pend_from_lal;
   // block 0: the next sweep's proposal for a rejected [0] and an accepted [1] theta'
@@ -413,6 +413,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
       // the table rows it reads, staged in shared memory first (one load per lane)
       if (tid < p) {
         if (s + 1 < a.ns) s_Unext[tid] = __ldg(a.tab_U + (s + 1) * p + tid);
+        s_Ucur[tid] = __ldg(a.tab_U + s * p + tid);
         if (s_pend_idx >= 0) s_pendU[tid] = __ldg(a.tab_U + s_pend_idx * p + tid);
       }
       __syncthreads();  // this sweep's theta' and the rows are in place
@@ -666,6 +667,14 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
           s_pend_from_lal = 1;
           s_pend_idx = s;
           s_pend_eta = eta_s;
+          // block 0 applies it at once (the proposal of the next sweep, prepared before this
+          // decision, used S_theta without it; the one after uses it): off its path to the next
+          // proposals. The last sweep of a launch keeps it pending for the next launch.
+          if (blockIdx.x == 0 && s + 1 < a.ns) {
+            ram_update_theta(p, s_Sth, s_Ucur, (logalpha >= 0.0) ? 1.0 : exp_tab(logalpha, s_math), a.astar_theta,
+                             eta_s);
+            s_pend_eta = 0.0;
+          }
         }
         // a8: record kept sweeps
         const long long post = s - a.burn_left;
