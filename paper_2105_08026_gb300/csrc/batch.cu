@@ -15,14 +15,25 @@
 // is replayed for every chunk of sweeps.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "sweep_common.cuh"
 
 namespace chm {
 
 namespace {
 
-// members per staged tile, per thread of the block (two stages of them)
+// members per staged tile, per lane of a warp (two stages of them per warp)
 constexpr unsigned int kTileFactor = 2u;
+constexpr int kMaxBlockWarps = 8;  // blocks of at most 256 threads
+
+// The luminosity model's log l_i (an e^x - 1 in binary32, ~25 instructions) is kept from one
+// sweep of a launch to the next in row 2 of a.even32 (4 bytes read and 4 written per member-update)
+// instead of being recomputed from the latent: the same routine on the same latent and data, so
+// the same bits. The first sweep of a launch computes it (the row may hold another chain's or
+// run's values). The normal-normal model's log l_i costs four operations and is recomputed.
+template <class M>
+constexpr bool kCacheLL = std::is_same<M, LF>::value;
 
 // byte offset of the member-tile stages in the dynamic shared memory (after the exp/log tables)
 __host__ __device__ constexpr unsigned int tile_offset_bytes() {
@@ -134,12 +145,11 @@ __device__ __forceinline__ void member_f64(const SweepArgs& a, unsigned int i, u
 // register-resident kernel's two half-steps, so the same bits. Writes the new latent and factor.
 template <class M>
 __device__ __forceinline__ void member1_f32(const SweepArgs& a, unsigned int i, float chi, double S, const float* d,
-                                            float z, float u, float eta_f, float astar_f, const ThetaCf& tf,
-                                            const ThetaCf& tpf, const ThetaDf& tdf, bool prior_ok, Xacc& xd,
-                                            XFlags& fd,
+                                            float ll, float z, float u, float eta_f, float astar_f,
+                                            const ThetaCf& tf, const ThetaCf& tpf, const ThetaDf& tdf,
+                                            bool prior_ok, Xacc& xd, long long& xq, XFlags& fd,
                                             unsigned int& neg_big, unsigned int& pos_big, unsigned int& nan_cnt,
                                             unsigned int& acc_cnt, long long tro, bool keep, const MomStep& ms) {
-  const float ll = M::loglike32(chi, d);
   const float Y = fmaf(f32_rz(S), z, chi);
   float delta, llY = 0.0f, lfY = 0.0f, cY = 0.0f, cX;
   const float lfX = M::logf32_e(chi, tf, cX);
@@ -161,6 +171,7 @@ __device__ __forceinline__ void member1_f32(const SweepArgs& a, unsigned int i, 
   S = ram1_f32(S, alpha, eta_f, astar_f);
   a.chi32[i] = chi;
   a.S[i] = S;
+  if constexpr (kCacheLL<M>) a.even32[2 * a.n32 + i] = acc ? llY : ll;  // log l at the new latent
   if (keep) mom_add(ms, i, f64_of(chi));
   if (tro >= 0) {
     a.tr_delta[tro + i] = static_cast<double>(delta);
@@ -174,40 +185,69 @@ __device__ __forceinline__ void member1_f32(const SweepArgs& a, unsigned int i, 
       if (dn < 0.0f) neg_big++;
       else pos_big++;
     } else {
-      xacc_add_float(xd, dn, fd);
+      xacc_add_float_q(xd, xq, dn, fd);
     }
   }
 }
 
-// Member tiles of the FP32 form, d = 1, in the streaming kernel. The block's members [nb0, nb1)
-// are covered by tiles of T members starting at a0 = nb0 rounded down to a multiple of 4 (so
-// every bulk copy is 16-byte aligned; the arrays are padded to n32 members). Each tile's latents,
-// RAM factors and binary32 data are brought into one of two shared-memory stages by bulk copies
-// (the TMA engine) while the block steps the members of the other stage. The few members of a
-// neighbouring block that an aligned tile covers are read but never used or written.
+// Member tiles of the FP32 form, d = 1, in the streaming kernel, staged per warp. The block's
+// members [nb0, nb1) lie in the aligned range [a0, a1): nb0 rounded down and nb1 rounded up to a
+// multiple of 4 (the arrays are padded to n32 members). Warp w takes the stretch
+// [a0 + w C, a0 + (w + 1) C) of it (C a multiple of 4, clipped to a1) in tiles of T = kTileFactor x 32
+// members. Lane 0 brings each tile's latents, RAM factors and binary32 data (and on even sweeps
+// the two cached draws, and from the second sweep of a launch the cached log l_i) into one of the warp's two shared-memory stages by bulk copies (the TMA
+// engine) while the warp steps the members of its other stage. A warp waits only for its own
+// tiles, so the warps of a block do not wait for one another during the member phase. Every copy
+// starts on a 16-byte boundary and moves a multiple of 16 bytes. The few members of a neighbouring
+// block that the first or last aligned tile covers are read but never used or written.
 struct TileRing {
-  char* buf;                // two stages of T (4 + 8 + 4 kData32 + 8) bytes
-  unsigned long long* bar;  // one mbarrier per stage
+  char* buf;                // this warp's two stages of T tile_member_bytes<M>() bytes
+  unsigned long long* bar;  // this warp's mbarriers, one per stage
   unsigned int T;           // members per tile
-  unsigned int count;       // tiles consumed so far: stage count & 1, phase parity (count >> 1) & 1
-  bool prefetched;          // the tile with counter `count` (the first of a sweep) is in flight
+  unsigned int count;       // tiles this warp consumed so far: stage count & 1, phase parity (count >> 1) & 1
+  bool prefetched;          // the warp's first tile of a sweep (counter `count`) is in flight
 };
 
-// bytes of one member in a stage: latent, RAM factor, data, and the even sweep's two draws
-template <int K32>
+// the calling warp's stretch [w0, w1) of the block's aligned range [a0, a1)
+__device__ __forceinline__ void warp_stretch(unsigned int a0, unsigned int a1, unsigned int& w0, unsigned int& w1) {
+  const unsigned int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
+  const unsigned int C = ((a1 - a0 + nw - 1u) / nw + 3u) & ~3u;
+  w0 = min(a0 + w * C, a1);
+  w1 = min(w0 + C, a1);
+}
+
+// the block's aligned range [a0, a1) of its members [nb0, nb1), nb1 > nb0
+__device__ __forceinline__ void tile_range(const SweepArgs& a, unsigned int nb0, unsigned int nb1, unsigned int& a0,
+                                           unsigned int& a1) {
+  a0 = nb0 & ~3u;
+  const unsigned long long a1l = (static_cast<unsigned long long>(nb1) + 3ull) & ~3ull;
+  a1 = static_cast<unsigned int>(a1l < static_cast<unsigned long long>(a.n32) ? a1l : a.n32);
+}
+
+// the theta' partials of at most this many tiles (kTileFactor addends per lane each) share one
+// 64-bit word before it is folded into the lane's exact sum (xacc_add_float_q: at most 127)
+constexpr unsigned int kFoldTiles = 64u / kTileFactor;
+static_assert(kTileFactor >= 1u && kTileFactor <= 64u, "fold interval");
+
+// bytes of one member in a stage: latent, RAM factor, data, the even sweep's two draws and the
+// cached log l_i (models with kCacheLL)
+template <class M>
 __host__ __device__ constexpr unsigned int tile_member_bytes() {
-  return 12u + 4u * K32 + 8u;
+  return 12u + 4u * M::kData32 + 8u + (kCacheLL<M> ? 4u : 0u);
 }
 
 // Issues the tile of len members from b into stage cnt & 1; `even`: also the two draws the odd
-// sweep before stored for each member (a.even32), which an even sweep reads instead of drawing.
-template <int K32>
+// sweep before stored for each member (a.even32), which an even sweep reads instead of drawing;
+// `llc`: also the cached log l_i (row 2 of a.even32, written by the sweep before in this launch).
+template <class M>
 __device__ __forceinline__ void tile_issue(const SweepArgs& a, const TileRing& r, unsigned int b, unsigned int len,
-                                           unsigned int cnt, bool even) {
-  constexpr unsigned int mb = tile_member_bytes<K32>();
+                                           unsigned int cnt, bool even, bool llc) {
+  constexpr int K32 = M::kData32;
+  constexpr unsigned int mb = tile_member_bytes<M>();
+  const bool ll = kCacheLL<M> && llc;
   char* st = r.buf + static_cast<size_t>(cnt & 1u) * r.T * mb;
   unsigned long long* bar = r.bar + (cnt & 1u);
-  mbar_arrive_expect_tx(bar, len * (even ? mb : mb - 8u));
+  mbar_arrive_expect_tx(bar, len * (12u + 4u * K32 + (even ? 8u : 0u) + (ll ? 4u : 0u)));
   bulk_copy_g2s(st, a.chi32 + b, len * 4u, bar);
   bulk_copy_g2s(st + 4u * r.T, a.S + b, len * 8u, bar);
 #pragma unroll
@@ -216,6 +256,7 @@ __device__ __forceinline__ void tile_issue(const SweepArgs& a, const TileRing& r
     bulk_copy_g2s(st + (12u + 4u * K32) * r.T, a.even32 + b, len * 4u, bar);
     bulk_copy_g2s(st + (16u + 4u * K32) * r.T, a.even32 + a.n32 + b, len * 4u, bar);
   }
+  if (ll) bulk_copy_g2s(st + (20u + 4u * K32) * r.T, a.even32 + 2 * a.n32 + b, len * 4u, bar);
 }
 
 // The block's member phase of one sweep (FP32 form, d = 1). Returns false if a stage wait
@@ -224,35 +265,37 @@ __device__ __forceinline__ void tile_issue(const SweepArgs& a, const TileRing& r
 // normal (the Box-Muller cosine) and uniform (word 2) and the next sweep's (the sine, word 3).
 // `cached`: an even sweep whose odd predecessor ran in this launch, so its two draws are in the
 // stage (written to a.even32 by that sweep) instead of being drawn again; the first sweep of a
-// launch always draws (a.even32 may hold another chain's or run's values).
+// launch always draws (a.even32 may hold another chain's or run's values). `llc`: not the first
+// sweep of the launch, so the cached log l_i is in the stage (kCacheLL models).
 template <class M>
 __device__ __forceinline__ bool members1_f32_tiled(const SweepArgs& a, TileRing& r, unsigned int nb0,
-                                                   unsigned int nb1, uint32_t k, bool cached, float eta_f,
+                                                   unsigned int nb1, uint32_t k, bool cached, bool llc,
+                                                   float eta_f,
                                                    float astar_f, const ThetaCf& tf, const ThetaCf& tpf,
                                                    const ThetaDf& tdf, bool prior_ok, Xacc& xd,
                                                    XFlags& fd, unsigned int& neg_big, unsigned int& pos_big,
                                                    unsigned int& nan_cnt, unsigned int& acc_cnt, long long tro,
                                                    bool keep, const MomStep& ms) {
   constexpr int K32 = M::kData32;
-  constexpr unsigned int mb = tile_member_bytes<K32>();
+  constexpr unsigned int mb = tile_member_bytes<M>();
   if (nb1 <= nb0) return true;
   const bool odd = (k & 1u) != 0u;
-  const unsigned int a0 = nb0 & ~3u;
-  const unsigned long long a1l = (static_cast<unsigned long long>(nb1) + 3ull) & ~3ull;
-  const unsigned int a1 = static_cast<unsigned int>(a1l < static_cast<unsigned long long>(a.n32) ? a1l : a.n32);
-  const unsigned int ntiles = (a1 - a0 + r.T - 1u) / r.T;
-  if (!r.prefetched && threadIdx.x == 0) tile_issue<K32>(a, r, a0, min(r.T, a1 - a0), r.count, cached);
+  const unsigned int lane = threadIdx.x & 31u;
+  unsigned int a0, a1, w0, w1;
+  tile_range(a, nb0, nb1, a0, a1);
+  warp_stretch(a0, a1, w0, w1);
+  const unsigned int ntiles = (w1 - w0 + r.T - 1u) / r.T;
+  if (ntiles > 0u && !r.prefetched && lane == 0u) tile_issue<M>(a, r, w0, min(r.T, w1 - w0), r.count, cached, llc);
   r.prefetched = false;
-  bool ok = true;  // this thread's stage waits all completed
+  bool ok = true;  // this lane's stage waits all completed
+  long long xq = 0;
   for (unsigned int t = 0; t < ntiles; ++t) {
     const unsigned int cnt = r.count;
-    const unsigned int b = a0 + t * r.T, len = min(r.T, a1 - b);
-    if (t + 1u < ntiles && threadIdx.x == 0)
-      tile_issue<K32>(a, r, b + r.T, min(r.T, a1 - b - r.T), cnt + 1u, cached);
+    const unsigned int b = w0 + t * r.T, len = min(r.T, w1 - b);
+    if (t + 1u < ntiles && lane == 0u) tile_issue<M>(a, r, b + r.T, min(r.T, w1 - b - r.T), cnt + 1u, cached, llc);
     if (ok) ok = mbar_wait_bounded(r.bar + (cnt & 1u), (cnt >> 1) & 1u, a.err, a.timeout_ns);
-    if (!ok) {  // the run has failed: skip the members, keep the block's barriers in step
-      fence_proxy_async_global();
-      __syncthreads();
+    if (!ok) {  // the run has failed: skip the members, keep the warp's stages in step
+      __syncwarp();
       r.count = cnt + 1u;
       continue;
     }
@@ -261,7 +304,8 @@ __device__ __forceinline__ bool members1_f32_tiled(const SweepArgs& a, TileRing&
     const double* s_S = reinterpret_cast<const double*>(st + 4u * r.T);
     const float* s_d = reinterpret_cast<const float*>(st + 12u * r.T);
     const float* s_ev = reinterpret_cast<const float*>(st + (12u + 4u * K32) * r.T);
-    for (unsigned int m = threadIdx.x; m < len; m += blockDim.x) {
+    const float* s_ll = reinterpret_cast<const float*>(st + (20u + 4u * K32) * r.T);
+    for (unsigned int m = lane; m < len; m += 32u) {
       const unsigned int i = b + m;
       if (i < nb0 || i >= nb1) continue;
       float d[K32];
@@ -282,19 +326,23 @@ __device__ __forceinline__ bool members1_f32_tiled(const SweepArgs& a, TileRing&
           a.even32[a.n32 + i] = uniform23(w.w);
         }
       }
-      member1_f32<M>(a, i, s_chi[m], s_S[m], d, z, u, eta_f, astar_f, tf, tpf, tdf, prior_ok, xd, fd, neg_big,
+      const float chi = s_chi[m];
+      const float ll = (kCacheLL<M> && llc) ? s_ll[m] : M::loglike32(chi, d);
+      member1_f32<M>(a, i, chi, s_S[m], d, ll, z, u, eta_f, astar_f, tf, tpf, tdf, prior_ok, xd, xq, fd, neg_big,
                      pos_big, nan_cnt, acc_cnt, tro, keep, ms);
     }
-    __syncthreads();  // the stage is free for the tile after next
+    if ((t + 1u) % kFoldTiles == 0u) xacc_fold_q(xd, xq);
+    __syncwarp();  // the stage is free for the warp's tile after next
     r.count = cnt + 1u;
   }
+  xacc_fold_q(xd, xq);
   // this thread's writes of the sweep before any later bulk copy reads them (within the sweep the
-  // copies read only other members: a block's tiles are disjoint, and the few members of a
+  // copies read only other members: the warps' stretches are disjoint, and the few members of a
   // neighbouring block that an aligned tile covers are never used)
   fence_proxy_async_global();
   if (__syncthreads_or(ok ? 0 : 1)) {
     // a stage wait timed out: leave no copy in flight into this block's shared memory (every
-    // thread waits, bounded again, for the last phase issued on each stage)
+    // lane waits, bounded again, for the last phase issued on each of its warp's stages)
     for (unsigned int c = r.count - min(r.count, 2u); c < r.count; ++c)
       mbar_wait_bounded(r.bar + (c & 1u), (c >> 1) & 1u, a.err, a.timeout_ns);
     __syncthreads();
@@ -303,16 +351,17 @@ __device__ __forceinline__ bool members1_f32_tiled(const SweepArgs& a, TileRing&
   return true;
 }
 
-// Issues the first tile of the next sweep (thread 0), after every write of this sweep; `cached`
-// as for members1_f32_tiled, for the next sweep.
+// Issues the warp's first tile of the next sweep (lane 0), after every write of this sweep;
+// `cached` as for members1_f32_tiled, for the next sweep (which has the cached log l_i).
 template <class M>
 __device__ __forceinline__ void tile_prefetch_first(const SweepArgs& a, TileRing& r, unsigned int nb0,
                                                     unsigned int nb1, bool cached) {
   if (nb1 <= nb0) return;
-  const unsigned int a0 = nb0 & ~3u;
-  const unsigned long long a1l = (static_cast<unsigned long long>(nb1) + 3ull) & ~3ull;
-  const unsigned int a1 = static_cast<unsigned int>(a1l < static_cast<unsigned long long>(a.n32) ? a1l : a.n32);
-  if (threadIdx.x == 0) tile_issue<M::kData32>(a, r, a0, min(r.T, a1 - a0), r.count, cached);
+  unsigned int a0, a1, w0, w1;
+  tile_range(a, nb0, nb1, a0, a1);
+  warp_stretch(a0, a1, w0, w1);
+  if (w1 <= w0) return;
+  if ((threadIdx.x & 31u) == 0u) tile_issue<M>(a, r, w0, min(r.T, w1 - w0), r.count, cached, true);
   r.prefetched = true;
 }
 
@@ -565,18 +614,20 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
   unsigned int member_acc = 0;
   // FP32 form, d = 1: member tiles staged in shared memory by bulk copies (after the tables)
   constexpr bool kTiled = F32 && M::kD == 1;
-  __shared__ __align__(8) unsigned long long s_tbar[2];
+  __shared__ __align__(8) unsigned long long s_tbar[2 * kMaxBlockWarps];  // two per warp
   TileRing ring{};
   if constexpr (kTiled) {
     const size_t base = reinterpret_cast<size_t>(reinterpret_cast<char*>(s_dyn) + tile_offset_bytes());
-    ring.buf = reinterpret_cast<char*>((base + 127u) & ~static_cast<size_t>(127u));  // 16-byte copies need 16
-    ring.bar = s_tbar;
-    ring.T = kTileFactor * blockDim.x;
+    ring.T = kTileFactor * 32u;
+    // this warp's two stages (16-byte copies need 16-byte alignment: the base is 128-aligned and
+    // a stage is a multiple of 128 bytes)
+    ring.buf = reinterpret_cast<char*>((base + 127u) & ~static_cast<size_t>(127u)) +
+               static_cast<size_t>(wid) * 2u * ring.T * tile_member_bytes<M>();
+    ring.bar = s_tbar + 2 * wid;
     ring.count = 0u;
     ring.prefetched = false;
     if (tid == 0) {
-      mbar_init(&s_tbar[0], 1u);
-      mbar_init(&s_tbar[1], 1u);
+      for (int q = 0; q < 2 * (static_cast<int>(blockDim.x) >> 5); ++q) mbar_init(&s_tbar[q], 1u);
       fence_mbar_init();
     }
     __syncthreads();
@@ -623,7 +674,7 @@ __device__ void run_population(const SweepArgs& a, BatchProg* prog, int b0, int 
       const TCf tf = s_tcf, tpf = s_tcpf;
       const ThetaDf tdf = s_tdf;
       const bool cached = (k & 1u) == 0u && s > 0;  // the odd sweep before ran in this launch
-      if (!members1_f32_tiled<M>(a, ring, nb0, nb1, k, cached, __double2float_rn(eta), astar_f, tf, tpf, tdf,
+      if (!members1_f32_tiled<M>(a, ring, nb0, nb1, k, cached, s > 0, __double2float_rn(eta), astar_f, tf, tpf, tdf,
                                  prior_ok, xd, fd, neg_big, pos_big, member_nan, member_acc, tro, keep, ms))
         return;  // a stage wait timed out: the run's error word is set, the population stops
     } else {
@@ -1014,7 +1065,7 @@ size_t batch_smem_bytes(bool f32, bool any_d1, int block) {
   size_t b = sizeof(double) * kMathWords;
   if (f32 && any_d1) {
     static_assert(LF::kData32 == NN1::kData32, "one tile layout for the one-dimensional models");
-    const size_t per = tile_member_bytes<LF::kData32>();
+    const size_t per = tile_member_bytes<LF>();
     b = tile_offset_bytes() + 128u + 2u * (kTileFactor * static_cast<size_t>(block)) * per;
   }
   return b;

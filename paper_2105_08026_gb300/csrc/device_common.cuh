@@ -142,6 +142,35 @@ __device__ __forceinline__ void xacc_add_float(Xacc& a, float v, XFlags& f) {
   xacc_add(a, t);
 }
 
+// A binary32 addend v = m 2^(e - 150) (m the 24-bit significand, e the biased exponent field) with
+// e in [102, 134], i.e. 2^-25 <= |v| < 2^8, is the integer m 2^(e - 102) < 2^56 times 2^-48. Such
+// addends (nearly every theta' partial of a sweep) are summed exactly in one signed 64-bit word q
+// (value q 2^-48) with a shift, a conditional negate and one 64-bit add, instead of the 192-bit
+// add; the rest take xacc_add_float. The caller folds q into the Xacc (xacc_fold_q) after at most
+// 127 additions, so q cannot overflow. xacc_add_float adds these addends without rounding too, so
+// the total is the same to the last bit.
+__device__ __forceinline__ void xacc_add_float_q(Xacc& a, long long& q, float v, XFlags& f) {
+  const unsigned int u = __float_as_uint(v);
+  const unsigned int sh = ((u >> 23) & 0xffu) - 102u;  // wraps for e < 102
+  if (sh <= 32u) {
+    const long long t =
+        static_cast<long long>(static_cast<unsigned long long>((u & 0x007FFFFFu) | 0x00800000u) << sh);
+    q += (u >> 31) ? -t : t;
+  } else {
+    xacc_add_float(a, v, f);
+  }
+}
+
+// Adds q 2^-48 (as the 192-bit value q 2^48 times 2^-96, sign-extended) into a and clears q.
+__device__ __forceinline__ void xacc_fold_q(Xacc& a, long long& q) {
+  Xacc t;
+  t.w0 = static_cast<unsigned long long>(q) << 48;
+  t.w1 = static_cast<unsigned long long>(q >> 16);
+  t.w2 = static_cast<unsigned long long>(q >> 63);
+  xacc_add(a, t);
+  q = 0;
+}
+
 // Round-to-nearest-even conversion of the fixed-point value to binary64.
 __device__ __forceinline__ double xacc_to_double(Xacc a) {
   const bool neg = (a.w2 >> 63) != 0;

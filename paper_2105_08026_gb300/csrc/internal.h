@@ -109,7 +109,8 @@ struct SweepArgs {
   const float* d32;   // FP32 form: precomputed binary32 member data (kData32 x n32, member-minor)
   float* chi32;       // FP32 form, d = 1: the latents (binary32 state; chi is a binary64 copy for the API)
   float* even32;      // FP32 form, d = 1: the streaming kernel's cache of each member's next (even) sweep
-                      // normal and accept uniform, written by the odd sweep before it, [2][n32]
+                      // normal and accept uniform, written by the odd sweep before it (rows 0, 1), and of
+                      // its log l_i at the current latent (row 2, luminosity model), [3][n32]
   long long n32;      // FP32 form, d = 1: row stride of d32 and padded length of chi32 and S (a multiple
                       // of kTilePad, so that bulk copies of aligned member tiles stay in bounds); else n
   double* pub;        // theta' proposals published by block 0 (kPubSlots slots of kPubWords doubles);

@@ -167,7 +167,7 @@ struct cudahm {
   // FP32 form, d = 1: the binary32 latent state (chi holds its binary64 copy for the API; it is
   // refreshed before every read and copied in after every write of chi) and the padded length
   float* chi32 = nullptr;
-  float* even32 = nullptr;  // the streaming kernel's even-sweep draws, [2][n32]
+  float* even32 = nullptr;  // the streaming kernel's even-sweep draws and cached log l_i, [3][n32]
   long long n32 = 0;
   double* math_tab = nullptr;
   double* pub = nullptr;  // theta' published by block 0 of the sweep kernel
@@ -828,7 +828,7 @@ int cudahm_create(const cudahm_config* cfg, cudahm_t* out) {
       (rc = alloc_into(h, &h->chi, n * h->d)) ||
       (rc = alloc_into(h, &h->S, tiled ? h->n32 : h->factor_n)) ||
       (tiled && (rc = alloc_into(h, &h->chi32, h->n32))) ||
-      (tiled && (rc = alloc_into(h, &h->even32, 2 * h->n32))) ||
+      (tiled && (rc = alloc_into(h, &h->even32, 3 * h->n32))) ||
       (rc = alloc_into(h, &h->chain, 1)) ||
       (rc = alloc_into(h, &h->acc3, 3ull * kAccWords)) ||
       (rc = alloc_into(h, &h->bar, 4)) ||

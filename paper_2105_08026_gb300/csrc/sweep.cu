@@ -534,6 +534,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
     if (prior_ok && F32) {
       const ThetaCf tpf = s_tcpf, tf = s_tcf;
       const ThetaDf tdf = s_tdf;
+      long long xq = 0;  // K <= 8 addends: one fold after the loop
 #pragma unroll
       for (int m = 0; m < K; ++m) {
         const unsigned int i = nb0 + tid + m * blockDim.x;
@@ -545,10 +546,11 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const SweepArgs a) {
             if (dn < 0.0f) neg_big++;
             else pos_big++;
           } else {
-            xacc_add_float(xd, dn, fd);
+            xacc_add_float_q(xd, xq, dn, fd);
           }
         }
       }
+      xacc_fold_q(xd, xq);
     }
     if (prior_ok && !F32) {
 #pragma unroll
