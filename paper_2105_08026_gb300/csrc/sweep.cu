@@ -984,22 +984,27 @@ cudaError_t launch_lf_inner(int nr, const double* xr, const double* wr, double r
 
 // Per-sweep theta tables: p normals (Philox stream 1, member index 0, sweep k; block j gives
 // normals 2j, 2j+1), the accept uniform (first uniform of block ceil(p/2)), eta = (k+1)^-gamma.
+// One thread per (sweep, task): task j < ceil(p/2) the normal pair of block j, the next task the
+// uniform and its logarithm, the last eta, so that a row's serial FP64 chain is one of these
+// (the longest, pow) rather than all of them one after another.
 // Thread 0 also resets what the next persistent launch counts from: the grid barrier and theta'
 // sequence words, the grid totals of its first sweeps, and (when given) the run's error word.
 __global__ void tables_kernel(int p, uint32_t key0, uint32_t key1, long long k0, long long ns, double gamma,
                               double* U, double* u, double* lnu, double* eta, unsigned int* bar,
                               unsigned long long* acc, int nacc, int* err) {
-  const long long s = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (s == 0) {
+  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t == 0) {
     bar[0] = 0u;
     bar[1] = 0u;
     for (int q = 0; q < nacc; ++q) acc[q] = 0ull;
     if (err) *err = 0;
   }
+  const int nblk = (p + 1) / 2, ntask = nblk + 2;
+  const long long s = t / ntask;
+  const int j = static_cast<int>(t - s * ntask);
   if (s >= ns) return;
   const uint32_t k = static_cast<uint32_t>(k0 + s + 1);
-  const int nblk = (p + 1) / 2;
-  for (int j = 0; j < nblk; ++j) {
+  if (j < nblk) {
     const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(j), 1u, 0u, k), key0, key1);
     const double ua = uniform53(w.x, w.y), ub = uniform53(w.z, w.w);
     const double rad = sqrt(-2.0 * log(ua));
@@ -1007,18 +1012,21 @@ __global__ void tables_kernel(int p, uint32_t key0, uint32_t key1, long long k0,
     sincospi(2.0 * ub, &sn, &cs);
     U[s * p + 2 * j] = rad * cs;
     if (2 * j + 1 < p) U[s * p + 2 * j + 1] = rad * sn;
+  } else if (j == nblk) {
+    const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(nblk), 1u, 0u, k), key0, key1);
+    const double us = uniform53(w.x, w.y);
+    u[s] = us;
+    lnu[s] = log(us);
+  } else {
+    eta[s] = pow(static_cast<double>(k) + 1.0, -gamma);
   }
-  const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(nblk), 1u, 0u, k), key0, key1);
-  u[s] = uniform53(w.x, w.y);
-  lnu[s] = log(u[s]);
-  eta[s] = pow(static_cast<double>(k) + 1.0, -gamma);
 }
 
 cudaError_t launch_tables(int p, uint32_t key0, uint32_t key1, long long k0, long long ns, double gamma, double* U,
                           double* u, double* lnu, double* eta, unsigned int* bar, unsigned long long* acc, int nacc,
                           int* err, cudaStream_t st) {
   const int blk = 128;
-  const long long nthr = ns > 0 ? ns : 1;
+  const long long nthr = ns > 0 ? ns * ((p + 1) / 2 + 2) : 1;
   tables_kernel<<<static_cast<unsigned int>((nthr + blk - 1) / blk), blk, 0, st>>>(p, key0, key1, k0, ns, gamma, U,
                                                                                    u, lnu, eta, bar, acc, nacc, err);
   return cudaGetLastError();
