@@ -113,3 +113,48 @@ extern "C" int probe_philox(const uint32_t* ctr_host, uint32_t k0, uint32_t k1, 
   cudaFree(ref);
   return e == cudaSuccess ? 0 : -2;
 }
+
+// The theta' partial's exact sum of binary32 addends, two ways: xacc_add_float alone, and the
+// 64-bit fast path (xacc_add_float_q, folded every `fold_every` additions) that the FP32 kernels
+// use. One thread adds the n values in order. out: the two 192-bit sums (limbs w0, w1, w2 each)
+// and their flag counts (nan, neg_inf, big each).
+namespace {
+__global__ void xacc32_kernel(const float* v, int n, int fold_every, unsigned long long* out, unsigned int* flags) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  chm::Xacc a, b;
+  chm::xacc_zero(a);
+  chm::xacc_zero(b);
+  chm::XFlags fa = {0u, 0u, 0u}, fb = {0u, 0u, 0u};
+  long long q = 0;
+  for (int i = 0; i < n; ++i) {
+    chm::xacc_add_float(a, v[i], fa);
+    chm::xacc_add_float_q(b, q, v[i], fb);
+    if ((i + 1) % fold_every == 0) chm::xacc_fold_q(b, q);
+  }
+  chm::xacc_fold_q(b, q);
+  out[0] = a.w0; out[1] = a.w1; out[2] = a.w2;
+  out[3] = b.w0; out[4] = b.w1; out[5] = b.w2;
+  flags[0] = fa.nan; flags[1] = fa.neg_inf; flags[2] = fa.big;
+  flags[3] = fb.nan; flags[4] = fb.neg_inf; flags[5] = fb.big;
+}
+}  // namespace
+
+extern "C" int probe_xacc_f32(const float* v_host, int n, int fold_every, unsigned long long* out_host,
+                              unsigned int* flags_host) {
+  if (n < 1 || fold_every < 1 || fold_every > 127) return -3;
+  float* v = nullptr;
+  unsigned long long* out = nullptr;
+  unsigned int* flags = nullptr;
+  if (cudaMalloc(&v, sizeof(float) * n) != cudaSuccess) return -1;
+  if (cudaMalloc(&out, sizeof(unsigned long long) * 6) != cudaSuccess) return -1;
+  if (cudaMalloc(&flags, sizeof(unsigned int) * 6) != cudaSuccess) return -1;
+  cudaMemcpy(v, v_host, sizeof(float) * n, cudaMemcpyHostToDevice);
+  xacc32_kernel<<<1, 32>>>(v, n, fold_every, out, flags);
+  cudaMemcpy(out_host, out, sizeof(unsigned long long) * 6, cudaMemcpyDeviceToHost);
+  cudaMemcpy(flags_host, flags, sizeof(unsigned int) * 6, cudaMemcpyDeviceToHost);
+  const cudaError_t e = cudaGetLastError();
+  cudaFree(v);
+  cudaFree(out);
+  cudaFree(flags);
+  return e == cudaSuccess ? 0 : -2;
+}

@@ -45,8 +45,19 @@ def probe(tmp_path_factory):
         y = np.zeros_like(x)
         assert L.probe_fp32_math(which, x.ctypes.data_as(fp), y.ctypes.data_as(fp), x.size) == 0
         return y
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    L.probe_xacc_f32.argtypes = [fp, ctypes.c_int, ctypes.c_int, u64p, u32p]
+
+    def xacc32(v, fold_every):
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        out = np.zeros(6, dtype=np.uint64)
+        flags = np.zeros(6, dtype=np.uint32)
+        assert L.probe_xacc_f32(v.ctypes.data_as(fp), v.size, fold_every, out.ctypes.data_as(u64p),
+                                flags.ctypes.data_as(u32p)) == 0
+        return out, flags
     run.lib = L
     run.f32 = run32
+    run.xacc32 = xacc32
     return run
 
 
@@ -180,3 +191,61 @@ def test_binary32_exponentials_within_1ulp_and_unbiased(probe):
     assert np.isfinite(y[4]) and y[5] == 0.0 and y[6] == np.inf and y[7] == 0.0 and np.isnan(y[8])
     z = probe.f32(1, np.array([0.0, -0.0, np.nan, -np.inf], dtype=np.float32))
     assert z[0] == 0.0 and z[1] == 0.0 and np.isnan(z[2]) and z[3] == -1.0
+
+
+def _signed192(w0, w1, w2):
+    v = int(w0) | (int(w1) << 64) | (int(w2) << 128)
+    return v - (1 << 192) if v >> 191 else v
+
+
+def _exact_sum96(v):
+    """The exact sum of binary32 addends, each rounded toward zero to a multiple of 2^-96 (as an
+    integer count of 2^-96), with the NaN / -inf / out-of-range counts: the definition both of the
+    device's exact-sum routines follow."""
+    from fractions import Fraction
+    tot, nan, ninf, big = 0, 0, 0, 0
+    for x in np.asarray(v, dtype=np.float32).tolist():
+        if math.isnan(x):
+            nan += 1
+        elif x == -math.inf:
+            ninf += 1
+        elif abs(x) >= 2.0 ** 94:
+            big += 1
+        else:
+            t = Fraction(x) * (1 << 96)
+            tot += math.trunc(t)
+    return tot, (nan, ninf, big)
+
+
+def test_binary32_exact_sum_fast_path_equals_the_definition(probe):
+    """The FP32 kernels add most binary32 theta' partials (2^-25 <= |d| < 2^8) in one 64-bit word
+    (value x 2^48) that they fold into the 192-bit sum; the rest take the 192-bit add. Both must
+    give the exact sum to the last bit, with the same flag counts, for addends of every exponent
+    (subnormal to past 2^94, both signs, the window's edges, zeros, infinities, NaN), folding as
+    the kernels do (every 64 additions) and at the documented limit (127 additions of the
+    largest window magnitude without a fold)."""
+    rng = np.random.default_rng(20260)
+    mag = np.exp2(rng.uniform(-150, 100, 30000))
+    v = (mag * rng.choice([-1.0, 1.0], mag.size)).astype(np.float32)
+    edges = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 2.0 ** -25, -(2.0 ** -25), 2.0 ** 8, -(2.0 ** 8),
+                      np.nextafter(np.float32(2.0 ** -25), np.float32(0)),
+                      np.nextafter(np.float32(2.0 ** 8), np.float32(0)),
+                      -np.nextafter(np.float32(2.0 ** 8), np.float32(0)),
+                      2.0 ** 94, -(2.0 ** 94), np.nextafter(np.float32(2.0 ** 94), np.float32(0)),
+                      np.float32(1e-45), -np.float32(1e-45), 2.0 ** -96, 2.0 ** -97, 3.0 * 2.0 ** -97],
+                     dtype=np.float32)
+    # sums whose carries cross the 64-bit limbs (window values of one sign, then the other)
+    mid = rng.uniform(2.0 ** 6, 2.0 ** 8, 4000).astype(np.float32)
+    cases = [(np.concatenate([v, edges]), 64), (np.concatenate([edges, v[:5000]]), 1),
+             (np.concatenate([mid, -mid, mid[:7]]), 64), (np.concatenate([-mid, mid[:1000]]), 64)]
+    top = np.nextafter(np.float32(2.0 ** 8), np.float32(0))
+    cases += [(np.full(127, top, dtype=np.float32), 127), (np.full(127, -top, dtype=np.float32), 127)]
+    for vals, fold in cases:
+        out, flags = probe.xacc32(vals, fold)
+        want, wf = _exact_sum96(vals)
+        want %= 1 << 192
+        slow = _signed192(*out[:3]) % (1 << 192)
+        fast = _signed192(*out[3:]) % (1 << 192)
+        assert slow == want, "192-bit add differs from the exact sum"
+        assert fast == want, "64-bit fast path differs from the exact sum"
+        assert tuple(flags[:3].tolist()) == wf and tuple(flags[3:].tolist()) == wf
