@@ -244,7 +244,7 @@ def run_reference(args):
         return 0
     data, theta0, scale, consts = workload(0)
     # a bounded sample of the workload: at most 15 timed and 3 untimed full sweeps (~0.1 s each on
-    # the machine's host cores), so that the run ends within a few minutes whatever --steps asks
+    # one host core), so that the run ends within a few minutes whatever --steps asks
     sweeps = max(1, min(args.steps, 15))
     warm = max(1, min(args.warmup, 3))
     rate, dt = oracle_rate(data, theta0, scale, consts, sweeps, warm)

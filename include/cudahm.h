@@ -51,7 +51,7 @@ extern "C" {
 #define CUDAHM_ETIMEOUT (-4)     /* a bounded device-side wait expired (grid barrier) */
 #define CUDAHM_ENUMERIC (-5)     /* NaN in a log-density or a non-finite theta */
 #define CUDAHM_ESTATE (-6)       /* call out of order (e.g. run before set_data) */
-#define CUDAHM_EUNSUPPORTED (-7) /* valid request this build does not handle */
+#define CUDAHM_EUNSUPPORTED (-7) /* valid request the library does not handle */
 
 #define CUDAHM_MAX_P 9      /* largest theta dimension (d = 3 normal model) */
 #define CUDAHM_MAX_CONSTS 8 /* model constants */

@@ -1,8 +1,8 @@
-"""The all-cores timing driver of the oracle's LF chain (the CPU baseline's all-cores leg).
+"""The all-cores timing runner of the oracle's LF chain (the CPU baseline's all-cores leg).
 
 Members split over threads step exactly as in one thread (draws keyed by member and sweep, the
 theta step serial with an order-free correctly rounded sum), so any thread count gives the same
-chain bit for bit; and the driver is the oracle's own chain up to the rounding of the sum over
+chain bit for bit; and the runner is the oracle's own chain up to the rounding of the sum over
 members (math.fsum here, Neumaier's method in the chain)."""
 import numpy as np
 
