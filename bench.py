@@ -59,6 +59,30 @@ FP64_FLOP_PER_SWEEP = 3.449e7
 MVN3_F32_FP64_FLOP_PER_UPDATE = 98.4
 MVN3_F32_DRAM_BYTES_PER_UPDATE = 127.6
 
+# Algorithmic HBM traffic of one member-update of the batched FP32 form (d = 1): binary32 data
+# 16 B read, binary32 latent 4 B and binary64 RAM factor 8 B read and written.
+BATCHED_F32_BYTES_PER_UPDATE = 40.0
+HBM_FALLBACK_GBS = 6800.0
+
+
+def hbm_peak():
+    """The measured HBM copy bandwidth (GB/s) of this GPU type, from the peaks file beside this
+    script, else the fallback figure; with a note saying which."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured (copy bandwidth)"
+    except (OSError, KeyError, ValueError, TypeError):
+        return HBM_FALLBACK_GBS, "of fallback (6.8 TB/s)"
+
+
+def batched_roofline(updates_per_s):
+    """HBM roofline of the batched FP32 leg at the algorithmic 40 B per member-update."""
+    peak, src = hbm_peak()
+    ach = BATCHED_F32_BYTES_PER_UPDATE * updates_per_s / 1e9
+    return {"bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": peak, "frac": ach / peak, "peak_source": src,
+            "bytes_per_update": BATCHED_F32_BYTES_PER_UPDATE, "kernel": "batch_kernel<FP32, d = 1>"}
+
+
 # FP64 work of one member integral of the marginal form on the LF workload (96 nodes, with the
 # step's share of the selection rule), from ncu's smsp__sass_thread_inst_executed_op_d{fma,add,mul}
 # counters on marg_kernel<LF> (profiles/marg_kernel_lf_n300000.md): 2 DFMA + DADD + DMUL.
@@ -322,7 +346,8 @@ def run_batched(args, cudahm, stream, device):
     assert all(r.shape[0] == K for r in rows)
     for s in samplers:
         s.close()
-    return {"value": members * K / (ms * 1e-3), "unit": "object-updates/s", "ms_per_step": ms / K,
+    value = members * K / (ms * 1e-3)
+    return {"value": value, "unit": "object-updates/s", "ms_per_step": ms / K, "roofline": batched_roofline(value),
             "populations": len(specs), "members": members, "lf_populations": sum(sp.kind == "lf" for sp in specs),
             "steps": K, "launch": {"block_threads": chosen.block_threads,
                                    "sweeps_per_launch": chosen.sweeps_per_launch,
