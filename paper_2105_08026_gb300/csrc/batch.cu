@@ -193,13 +193,14 @@ __device__ __forceinline__ void member1_f32(const SweepArgs& a, unsigned int i, 
 // Member tiles of the FP32 form, d = 1, in the streaming kernel, staged per warp. The block's
 // members [nb0, nb1) lie in the aligned range [a0, a1): nb0 rounded down and nb1 rounded up to a
 // multiple of 4 (the arrays are padded to n32 members). Warp w takes the stretch
-// [a0 + w C, a0 + (w + 1) C) of it (C a multiple of 4, clipped to a1) in tiles of T = kTileFactor x 32
-// members. Lane 0 brings each tile's latents, RAM factors and binary32 data (and on even sweeps
-// the two cached draws, and from the second sweep of a launch the cached log l_i) into one of the warp's two shared-memory stages by bulk copies (the TMA
-// engine) while the warp steps the members of its other stage. A warp waits only for its own
-// tiles, so the warps of a block do not wait for one another during the member phase. Every copy
-// starts on a 16-byte boundary and moves a multiple of 16 bytes. The few members of a neighbouring
-// block that the first or last aligned tile covers are read but never used or written.
+// [a0 + w C, a0 + (w + 1) C) of it (C a multiple of 4, clipped to a1) in tiles of
+// T = kTileFactor x 32 members. Lane 0 brings each tile's latents, RAM factors and binary32 data
+// (on even sweeps also the two cached draws, from the second sweep of a launch also the cached
+// log l_i) into one of the warp's two shared-memory stages by bulk copies (the TMA engine) while
+// the warp steps the members of its other stage. A warp waits only for its own tiles, so the
+// warps of a block do not wait for one another during the member phase. Every copy starts on a
+// 16-byte boundary and moves a multiple of 16 bytes. The few members of a neighbouring block
+// that the first or last aligned tile covers are read but never used or written.
 struct TileRing {
   char* buf;                // this warp's two stages of T tile_member_bytes<M>() bytes
   unsigned long long* bar;  // this warp's mbarriers, one per stage
